@@ -1,0 +1,385 @@
+#!/usr/bin/env python
+"""Benchmark of the visibility MABS / 3D bispectrum hot path on GB300.
+
+Metric: MABS bin-triple x channel evaluations per second (one evaluation = one
+ring triple with at least one closed triangle x one ordered channel triple,
+i.e. one value of Eq. estimator_t of arXiv:2506.10526).
+
+Workload (default ``mwa``): the MWA-like configuration -- 256^2 uv grid,
+768 channels, 20 log-spaced rings in |U| from 4.41 to 128 grid units,
+image side M = 384, seeded quadratic non-Gaussian sky (f_NG = 0.5,
+P(k) ~ k^-2), no flagging.  The full job is every ring triple x every channel
+triple (768^3), far more than a minute of work, so one step is one pass of the
+whole hot path over one channel block of the job: the grid load of all 768
+channels (shell masks + inverse FFTs of all 15,360 fields), the triple
+contraction of every closable ring triple over one BxBxB channel block, the
+collapse into the (dnu1, dnu2) plane and the delay transform of Eq. (dft).
+Consecutive steps (and ranks) take consecutive blocks of the job.
+
+Timing: W untimed warm-up steps, then K steps between CUDA events on the
+launching stream with a device synchronise and a barrier on both sides;
+inputs (403 MB of visibilities, 9 GB of fields) exceed the 129 MB L2.
+``e2e`` repeats the steps through the same C ABI starting from host memory:
+each step copies the visibilities host->device and reads the 3D bispectrum
+back.  ``--impl reference`` times the FP64 CPU oracle (the only reference
+implementation: the paper ships no code) on a bounded sample of the same
+workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "mwa": dict(nt=256, nc=768, nb=20, edges=("log", 4.41, 128.0), block=64,
+                desc="MWA-like: 256^2 uv grid, 768 channels (30.72 MHz at 40 kHz), 20 log rings "
+                     "|U| in [4.41, 128), no flagging"),
+    "tiny": dict(nt=64, nc=16, nb=8, edges=("linear", 0.0, 32.0), block=16,
+                 desc="tiny: 64^2 uv grid, 16 channels, 8 linear rings |U| < 32, no flagging"),
+}
+SMS = 152
+FP32_LANES_PER_SM = 128
+PROFILE = os.path.join(ROOT, "profiles", "contract_simt_mwa.txt")
+KERNEL_SRC = os.path.join(ROOT, "paper_2506_10526_gb300", "csrc", "contract_simt.cu")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="mwa", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "split_bf16"])
+    ap.add_argument("--block", type=int, default=0, help="channel block side (0 = workload default)")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU baseline budget")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def edges_of(w):
+    import synth
+    kind, lo, hi = w["edges"]
+    return synth.edges_log(w["nb"], lo, hi) if kind == "log" else synth.edges_linear(w["nb"], hi)
+
+
+def make_vis(w, seed):
+    import numpy as np
+    import synth
+    return synth.sky_visibilities(w["nt"], w["nc"], seed, f_ng=0.5, sigma=0.5).astype(np.complex64)
+
+
+def blocks_of(nc, bsz):
+    nb_ = (nc + bsz - 1) // bsz
+    out = []
+    for a in range(nb_):
+        for b in range(nb_):
+            for c in range(nb_):
+                out.append((a * bsz, min(nc, (a + 1) * bsz), b * bsz, min(nc, (b + 1) * bsz),
+                            c * bsz, min(nc, (c + 1) * bsz)))
+    return out
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm = [float(r[0]) for r in self.rows if len(r) >= 8 and r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if len(r) >= 8 and r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            if len(r) < 8:
+                continue
+            for k, n in enumerate(names):
+                if r[4 + k].lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return {}
+
+
+def profile_traffic():
+    """DRAM bytes per launch of the contraction from the committed ncu summary,
+    valid only while the kernel source still has the hash recorded there."""
+    if not os.path.exists(PROFILE):
+        return None
+    h = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+    vals = {}
+    for line in open(PROFILE):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_sha256_16") != h:
+        return None
+    try:
+        return {"bytes_per_unit": float(vals["dram_bytes_per_eval"])}
+    except (KeyError, ValueError):
+        return None
+
+
+def cpu_baseline(w, seconds, vis=None):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload:
+    uniformly sampled closable ring triples x the channel triples of the first
+    4 channels, enumerated with all host cores until the time budget is used."""
+    import numpy as np
+    import oracle
+    edges = edges_of(w)
+    nsub = min(4, w["nc"])
+    if vis is None:
+        vis = make_vis(w, seed=2000)
+    v = np.ascontiguousarray(vis[:nsub]).astype(np.complex128)
+    T = oracle.counts(w["nt"], edges)
+    trips = [t for t in oracle.ring_triples(w["nb"]) if T[t] > 0]
+    rng = np.random.default_rng(12345)
+    order = rng.permutation(len(trips))
+    cores = os.cpu_count() or 1
+    done = 0
+    t0 = time.perf_counter()
+    k = 0
+    while k < len(order) and time.perf_counter() - t0 < seconds:
+        chunk = [trips[i] for i in order[k:k + cores]]
+        oracle.mabs_full(v, edges, triples=chunk, nthreads=cores)
+        done += len(chunk)
+        k += cores
+    dt = time.perf_counter() - t0
+    evals = done * nsub ** 3
+    return {"value": evals / dt, "unit": "evals/s", "cores": cores, "kind": "oracle",
+            "sample": f"FP64 closed-triangle enumeration of {done} uniformly sampled closable ring "
+                      f"triples x {nsub}^3 channel triples (channels 0-{nsub - 1}) of the "
+                      f"{w['nt']}^2 grid, {dt:.1f} s"}
+
+
+def run_reference(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    per = max(2.0, min(20.0, 90.0 / max(1, args.steps + args.warmup)))
+    vis = make_vis(w, seed=2000)
+    for _ in range(args.warmup):
+        cpu_baseline(w, per / 4, vis)
+    vals = []
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(w, per, vis))
+    value = statistics.mean(v["value"] for v in vals)
+    line = {"impl": "reference", "metric": "mabs_bin_triple_x_channel_evals_per_s", "value": value,
+            "unit": "evals/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": w["desc"], "sample": vals[-1]["sample"]},
+            "cpu_baseline": {"kind": "oracle", "cores": vals[-1]["cores"], "value": value,
+                             "unit": "evals/s", "sample": vals[-1]["sample"]},
+            "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    w = dict(WORKLOADS[args.workload])
+    if args.block:
+        w["block"] = args.block
+    if args.impl == "reference":
+        run_reference(args, w)
+        return
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_2506_10526_gb300 as bs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    edges = edges_of(w)
+    nt, nc = w["nt"], w["nc"]
+    prec = bs.PREC_FP32 if args.precision == "fp32" else bs.PREC_SPLIT_BF16
+    vis = make_vis(w, seed=1000 * 2 + rank)
+    plan = bs.Plan(nt, nc, edges, precision=prec)
+    stream = torch.cuda.current_stream()
+    vis_h = torch.from_numpy(vis[None]).pin_memory()
+    vis_d = vis_h.to(dev)
+    out_delta = torch.empty((1, plan.ntrip, 2 * nc - 1, 2 * nc - 1), dtype=torch.float64, device=dev)
+    out3d = torch.empty((1, plan.ntrip, nc, nc), dtype=torch.float64, device=dev)
+    plan.grid_load(vis_d)
+    tri, _ = plan.counts()
+    nclos = int((tri > 0).sum())
+    jobs = blocks_of(nc, w["block"])
+
+    def block_evals(b):
+        return nclos * (b[1] - b[0]) * (b[3] - b[2]) * (b[5] - b[4])
+
+    def step(i, e2e=False, ev=None):
+        b = jobs[(i * world + rank) % len(jobs)]
+        if e2e:
+            vis_d.copy_(vis_h, non_blocking=True)
+        plan.grid_load(vis_d)
+        if ev is not None:
+            ev[0].record(stream)
+        plan.mabs(block=b, accumulate=True)
+        if ev is not None:
+            ev[1].record(stream)
+        plan.mabs_delta(out_delta)
+        plan.bs3d(out3d)
+        if e2e:
+            res_h.copy_(out3d, non_blocking=True)
+        return block_evals(b)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    barrier()
+    t0.record(stream)
+    evals = 0
+    for i in range(args.steps):
+        evals += step(args.warmup + i, ev=kev[i])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = t0.elapsed_time(t1)
+    kms = [a.elapsed_time(b) for a, b in kev]
+    if world > 1:
+        tt = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+        ev_t = torch.tensor([float(evals)], dtype=torch.float64, device=dev)
+        dist.all_reduce(ev_t)
+        evals = float(ev_t.item())
+    value = evals / (ms / 1e3)
+
+    e2e = None
+    if not args.no_e2e:
+        res_h = torch.empty(out3d.shape, dtype=out3d.dtype).pin_memory()
+        step(0, e2e=True)
+        torch.cuda.synchronize()
+        barrier()
+        e0 = time.perf_counter()
+        ev2 = 0
+        for i in range(args.steps):
+            ev2 += step(args.warmup + args.steps + i, e2e=True)
+            torch.cuda.synchronize()  # the host reads the step's result
+        barrier()
+        edt = time.perf_counter() - e0
+        if world > 1:
+            tt = torch.tensor([edt, float(ev2)], dtype=torch.float64, device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            edt = float(tt[0].item())
+            ev2 = ev2 * world
+        e2e = {"value": ev2 / edt, "unit": "evals/s", "h2d_bytes_per_step": vis_h.numel() * 8,
+               "d2h_bytes_per_step": res_h.numel() * 8}
+
+    # roofline of the contraction (dominant kernel): algorithmic FLOPs = 2 M^2 per evaluation
+    M = plan.M
+    per_launch_evals = block_evals(jobs[0])
+    avg_ms = statistics.mean(kms)
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    if args.precision == "fp32":
+        peak = SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+        roof = {"bound": "alu", "peak_source": f"FP32 FMA: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 "
+                f"flop x {sm_max:.0f} MHz"}
+    else:
+        peak = float(peaks.get("bf16_tflops", 1900.0)) / 3.0
+        roof = {"bound": "tensor", "peak_source": "measured bf16 burst / 3 (three split products)"}
+    achieved = per_launch_evals * 2.0 * M * M / (avg_ms / 1e3) / 1e12
+    tr = profile_traffic()
+    roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                 "kernel": "k_contract_simt" if args.precision == "fp32" else "k_contract_tc",
+                 "avg_launch_ms": avg_ms,
+                 "traffic": None if tr is None else tr["bytes_per_unit"] * per_launch_evals})
+
+    line = {
+        "metric": "mabs_bin_triple_x_channel_evals_per_s",
+        "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "bf16x3",
+        "data": "synthetic",
+        "config": {"workload": w["desc"], "M": M, "channel_block": w["block"],
+                   "closable_ring_triples": nclos, "ring_triples": plan.ntrip,
+                   "evals_per_step_per_gpu": per_launch_evals, "precision": args.precision,
+                   "l2": "inputs larger than L2 (403 MB visibilities, 9 GB fields)",
+                   "parallelism": f"blocks of the channel cube sharded over {world} GPU(s)"},
+        "roofline": roof, "clocks": clk,
+        "gpu_launches": 6 * args.steps,
+        "e2e": e2e,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds, vis)
+    plan.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,193 @@
+/*
+ * bs.h -- C ABI of libbs, the GB300 (sm_103a) implementation of the
+ * visibility-based multi-frequency angular bispectrum (MABS) and 3D
+ * bispectrum estimator of arXiv:2506.10526, Section 3.2.
+ *
+ * Pipeline (each stage runs in the library's own CUDA kernels):
+ *   bs_grid_load  ring (shell) masking with weights W = 1/N_g  (Eq. vg, Eq. iFT)
+ *                 + inverse 2D FFT of every (ring, channel) to a real
+ *                   image-plane field F (Eq. iFT; Eq. iFT_I for unit masks)
+ *   bs_counts     exact integer closed-triangle counts T(i,j,l), which equal
+ *                 the I-field triple sums of Eq. (estimator_t) divided by the
+ *                 pixel count, and the sampling N_nu of Fig. Nv
+ *   bs_mabs       triple contraction  S = sum_x F_i F_j F_l  over the image
+ *                 pixels for every ring triple i <= j <= l and every ordered
+ *                 channel triple of a channel block, normalised to Eq.
+ *                 (estimator_t): B_A = S / (A M^2 T); optionally accumulated
+ *                 into the (dnu1, dnu2) collapse of Section 3.2
+ *   bs_mabs_delta folded, collapsed MABS B_A(l1,l2,l3, dnu1, dnu2)
+ *   bs_bs3d       Eq. (dft): 2D DFT over (dnu1, dnu2) to (k_par1, k_par2)
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Grids are centred: element [v + nt/2][u + nt/2] holds grid point
+ *    U_g = (u, v), u, v integers in [-nt/2, nt/2).  Ring m holds the cells with
+ *    e_m <= |U_g| < e_{m+1} (|U_g|^2, an exact integer, compared with e^2 in
+ *    FP64); U_g = 0 and cells with a component equal to -nt/2 are never binned.
+ *  - Visibilities must be Hermitian, V(-U) = conj V(U) (the sky is real).  The
+ *    library reads only the u >= 0 half-plane and mirrors it; bs_check_hermitian
+ *    tests the assumption.
+ *  - Ring triples are enumerated lexicographically over i <= j <= l:
+ *    trip = 0 for (0,0,0), 1 for (0,0,1), ...  Channel triples are ordered
+ *    (nu1, nu2, nu3), nu1 slowest.
+ *  - "dev" pointers are CUDA device pointers on the plan's device, "host"
+ *    pointers are host memory.  The caller owns every buffer passed in; the
+ *    plan owns its workspace.  Device work is asynchronous on the given
+ *    cudaStream_t (passed as void*; NULL = legacy default stream) unless a
+ *    function says it synchronises.
+ *  - Undefined estimates (no closed triangle, a flagged channel, or no sampled
+ *    channel triple) are NaN.
+ *  - Every function returns a bs_status.  A failure stores a message that
+ *    bs_last_error returns; CUDA errors are sticky for the plan (later calls
+ *    return BS_ERR_STATE) until it is destroyed.  No call falls back to a CPU
+ *    path: without a usable sm_103a device, bs_plan_create returns
+ *    BS_ERR_NO_DEVICE.
+ *  - Not thread-safe per plan: one host thread at a time may use a plan.
+ */
+#ifndef BS_H_
+#define BS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BS_ABI_VERSION 1
+
+typedef struct bs_plan_s *bs_plan;
+
+typedef enum {
+    BS_OK = 0,
+    BS_ERR_ARG = 1,           /* invalid argument (size, range, NULL, alignment) */
+    BS_ERR_NO_DEVICE = 2,     /* no CUDA device, or not compute capability 10.3 */
+    BS_ERR_CUDA = 3,          /* a CUDA runtime call or kernel launch failed */
+    BS_ERR_OOM = 4,           /* device allocation failed */
+    BS_ERR_NOT_HERMITIAN = 5, /* bs_check_hermitian found V(-U) != conj V(U) */
+    BS_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up */
+    BS_ERR_STATE = 7,         /* call out of order (e.g. no grid loaded) or sticky error */
+    BS_ERR_UNSUPPORTED = 8    /* valid request this build does not implement */
+} bs_status;
+
+/* Arithmetic of the triple contraction (bs_mabs). */
+enum {
+    BS_PREC_FP32 = 0,       /* FP32 SIMT FMA, FP32 partial sums, FP64 across tiles */
+    BS_PREC_SPLIT_BF16 = 1  /* tcgen05 tensor cores: pair and field operands split
+                               into BF16 hi + lo, three products (hi.hi + hi.lo +
+                               lo.hi) accumulated in FP32 TMEM, FP64 across tiles */
+};
+
+typedef struct {
+    int nt;                  /* N_t: uv grid side, even, 8..1024 */
+    int nchan;               /* N_c: channels, 1..4096 */
+    int nbins;               /* n_b: annular rings, 1..32 */
+    const double *bin_edges; /* host, nbins+1 strictly ascending ring edges in grid
+                                units of |U|; copied at create */
+    int fft_m;               /* image-plane FFT side M; 0 = smallest M = 2^a 3^b 5^c,
+                                M % 4 == 0, with M > 3 * (largest |u| or |v| of a
+                                binned cell), which makes the pixel sum count only
+                                exactly closed triangles (no wrap-around) */
+    int precision;           /* BS_PREC_* */
+    int batch;               /* realisations processed together, >= 1 */
+    double norm_A;           /* A of Eq. (estimator_t); <= 0 means 1 */
+    double r, rprime, dnu_c; /* comoving distance r, r' = dr/dnu, channel width:
+                                Eq. (dft) multiplies by (r^2 r' dnu_c)^2; <= 0 means 1 */
+} bs_plan_desc;
+
+/* ABI version this library was built with (BS_ABI_VERSION). */
+int bs_abi_version(void);
+
+/* Create a plan on the current CUDA device.  Host-side work: ring labels,
+ * alias-free FFT size, twiddle tables, ring-triple list.  Device workspace is
+ * allocated lazily at the first device call, or taken from
+ * bs_plan_set_workspace.  Errors: BS_ERR_ARG (desc out of range, edges not
+ * ascending), BS_ERR_NO_DEVICE (no device / not sm_103), BS_ERR_UNSUPPORTED. */
+bs_status bs_plan_create(const bs_plan_desc *desc, bs_plan *out);
+
+/* Release the plan and any workspace it allocated itself.  NULL is a no-op. */
+bs_status bs_plan_destroy(bs_plan plan);
+
+/* Message of the last failure on this plan (or of the last failed
+ * bs_plan_create on this thread when plan is NULL).  Never NULL. */
+const char *bs_last_error(bs_plan plan);
+
+/* Plan facts, written to info_host[0..n) (int64):
+ *  [0] M (FFT side)          [1] number of ring triples T_r
+ *  [2] fields per realisation (nbins*nchan)   [3] workspace bytes needed
+ *  [4] u columns kept per field (largest |u| of a binned cell + 1)
+ *  [5] number of ring triples with at least one closed triangle
+ *      (valid after the first bs_grid_load or bs_counts), else -1 */
+bs_status bs_plan_info(bs_plan plan, int64_t *info_host, int n);
+
+/* Hand the plan a caller-owned device workspace of at least info[3] bytes,
+ * 256-byte aligned, valid until bs_plan_destroy (e.g. a torch uint8 tensor).
+ * Must be called before the first device call; otherwise the plan allocates
+ * its own with cudaMalloc.  Errors: BS_ERR_ARG (too small / misaligned),
+ * BS_ERR_STATE (workspace already in place). */
+bs_status bs_plan_set_workspace(bs_plan plan, void *workspace_dev, size_t bytes);
+
+/* Eq. (vg) weights + Eq. (iFT) fields for every realisation.
+ *  vis_dev        complex64 [batch][nchan][nt][nt] (interleaved re, im floats),
+ *                 centred, Hermitian; 8-byte aligned.
+ *  ngrid_dev      float [nt][nt]: visibilities per grid cell N_g (same in every
+ *                 channel); W = 1/N_g where N_g > 0, else the cell is empty
+ *                 (W = 0 and it takes no part in the counts).  NULL = every
+ *                 cell holds one visibility.
+ *  chan_flag_host uint8 [nchan], nonzero = channel flagged (W = 0 for the whole
+ *                 channel: its triples are undefined).  NULL = none flagged.
+ * Image-plane fields of side M are kept in the plan workspace.  Triangle
+ * counts are recomputed when ngrid_dev is not NULL.  Resets the collapse
+ * accumulators (as bs_delta_reset). */
+bs_status bs_grid_load(bs_plan plan, const void *vis_dev, const float *ngrid_dev,
+                       const uint8_t *chan_flag_host, void *cuda_stream);
+
+/* Host copies of the integer counts of the last load (synchronises):
+ *  tri_host  int64 [T_r]: ordered closed triangles per ring triple (or NULL)
+ *  nnu_host  int64 [(2nchan-1)^2]: folded N_nu(dnu1, dnu2) of the channel
+ *            triples accumulated since the last reset, indexed
+ *            [(dnu1 + nchan-1)*(2nchan-1) + dnu2 + nchan-1] (or NULL). */
+bs_status bs_counts(bs_plan plan, int64_t *tri_host, int64_t *nnu_host);
+
+/* Triple contraction for one channel block (Eq. estimator_t).
+ *  block_host  int32 [6] = {nu1_lo, nu1_hi, nu2_lo, nu2_hi, nu3_lo, nu3_hi},
+ *              half-open channel ranges; NULL = every channel for all three.
+ *  out_full_dev  double [batch][T_r][nchan][nchan][nchan] or NULL: entries of the
+ *              block are overwritten with B_A (NaN where undefined); entries
+ *              outside the block are left untouched.
+ *  accumulate  nonzero: add the block's pixel sums and sampling to the
+ *              collapse accumulators used by bs_mabs_delta / bs_bs3d.
+ * Errors: BS_ERR_STATE (no grid loaded), BS_ERR_ARG (block out of range). */
+bs_status bs_mabs(bs_plan plan, const int32_t *block_host, double *out_full_dev,
+                  int accumulate, void *cuda_stream);
+
+/* Zero the collapse accumulators and the accumulated sampling. */
+bs_status bs_delta_reset(bs_plan plan, void *cuda_stream);
+
+/* Folded collapsed MABS (Section 3.2; fold of Fig. Nv) from the accumulated
+ * blocks: for every ring triple and separation (d1, d2) in [-(nchan-1),
+ * nchan-1]^2, the mean of B_A over the accumulated valid channel triples with
+ * (nu1-nu3, nu2-nu3) = (d1, d2) or (-d1, -d2).
+ *  out_dev  double [batch][T_r][2nchan-1][2nchan-1], index [d1+nchan-1][d2+nchan-1];
+ *           the plane is point symmetric; NaN where no triple was sampled. */
+bs_status bs_mabs_delta(bs_plan plan, double *out_dev, void *cuda_stream);
+
+/* Eq. (dft) applied to the folded collapsed MABS:
+ *   B(a, b) = (r^2 r' dnu_c)^2 sum_{n,m} exp(-2 pi i (n a + m b)/nchan) B_A(n, m)
+ * with n, m over the integers of [-nchan/2, nchan/2] (both ends, as the limits
+ * of Eq. dft state; unsampled separations contribute nothing) and
+ * a, b in [-nchan/2, nchan/2).  The input plane is point symmetric, so B is
+ * real.  k_par a = 2 pi a / (r' nchan dnu_c).
+ *  out_dev  double [batch][T_r][nchan][nchan], index [a + nchan/2][b + nchan/2]. */
+bs_status bs_bs3d(bs_plan plan, double *out_dev, void *cuda_stream);
+
+/* Check V(-U) = conj V(U) on every binned cell of every channel and
+ * realisation: |V(-U) - conj V(U)| <= tol * max|V| (synchronises).
+ * Returns BS_OK or BS_ERR_NOT_HERMITIAN. */
+bs_status bs_check_hermitian(bs_plan plan, const void *vis_dev, double tol, void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BS_H_ */

@@ -1,0 +1,202 @@
+"""GB300 (sm_103a) visibility bispectrum estimator: Python binding of libbs.
+
+Thin ctypes layer over the C ABI in ``include/bs.h`` (arXiv:2506.10526,
+Section 3.2).  It only marshals arguments: every step of the estimator runs
+in libbs's own CUDA kernels.  PyTorch provides device memory (tensors whose
+``data_ptr()`` is passed down) and streams.  There is no CPU fallback: if
+libbs.so is missing or no sm_103a device is present, calls raise.
+
+Names follow the C entry points: ``bs_plan_create`` -> :class:`Plan`,
+``bs_grid_load`` -> :meth:`Plan.grid_load`, ``bs_counts`` ->
+:meth:`Plan.counts`, ``bs_mabs`` -> :meth:`Plan.mabs`, ``bs_mabs_delta`` ->
+:meth:`Plan.mabs_delta`, ``bs_bs3d`` -> :meth:`Plan.bs3d`.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libbs.so")
+
+BS_OK = 0
+STATUS = {0: "BS_OK", 1: "BS_ERR_ARG", 2: "BS_ERR_NO_DEVICE", 3: "BS_ERR_CUDA", 4: "BS_ERR_OOM",
+          5: "BS_ERR_NOT_HERMITIAN", 6: "BS_ERR_TIMEOUT", 7: "BS_ERR_STATE",
+          8: "BS_ERR_UNSUPPORTED"}
+PREC_FP32 = 0
+PREC_SPLIT_BF16 = 1
+
+# every symbol declared in include/bs.h
+EXPORTS = ("bs_abi_version", "bs_plan_create", "bs_plan_destroy", "bs_last_error",
+           "bs_plan_info", "bs_plan_set_workspace", "bs_grid_load", "bs_counts", "bs_mabs",
+           "bs_delta_reset", "bs_mabs_delta", "bs_bs3d", "bs_check_hermitian")
+
+_lib = None
+_lock = threading.Lock()
+
+
+class BsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class PlanDesc(ctypes.Structure):
+    _fields_ = [("nt", ctypes.c_int), ("nchan", ctypes.c_int), ("nbins", ctypes.c_int),
+                ("bin_edges", ctypes.POINTER(ctypes.c_double)), ("fft_m", ctypes.c_int),
+                ("precision", ctypes.c_int), ("batch", ctypes.c_int),
+                ("norm_A", ctypes.c_double), ("r", ctypes.c_double),
+                ("rprime", ctypes.c_double), ("dnu_c", ctypes.c_double)]
+
+
+def lib() -> ctypes.CDLL:
+    """Load libbs.so (built in-tree by ``build.py``); raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libbs.so not built ({LIB_PATH}); run "
+                                   "`python -c 'import __graft_entry__ as g; g.build()'`")
+            L = ctypes.CDLL(LIB_PATH)
+            P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+            L.bs_abi_version.restype = I
+            L.bs_plan_create.argtypes = [ctypes.POINTER(PlanDesc), ctypes.POINTER(P)]
+            L.bs_plan_destroy.argtypes = [P]
+            L.bs_last_error.argtypes = [P]
+            L.bs_last_error.restype = ctypes.c_char_p
+            L.bs_plan_info.argtypes = [P, P, I]
+            L.bs_plan_set_workspace.argtypes = [P, P, ctypes.c_size_t]
+            L.bs_grid_load.argtypes = [P, P, P, P, P]
+            L.bs_counts.argtypes = [P, P, P]
+            L.bs_mabs.argtypes = [P, P, P, I, P]
+            L.bs_delta_reset.argtypes = [P, P]
+            L.bs_mabs_delta.argtypes = [P, P, P]
+            L.bs_bs3d.argtypes = [P, P, P]
+            L.bs_check_hermitian.argtypes = [P, P, D, P]
+            for name in EXPORTS:
+                if name not in ("bs_abi_version", "bs_last_error"):
+                    getattr(L, name).restype = I
+            _lib = L
+    return _lib
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+
+
+def _dptr(t):
+    """Device pointer of a CUDA tensor (or None)."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Plan:
+    """bs_plan_create / bs_plan_destroy.  Workspace comes from torch."""
+
+    def __init__(self, nt: int, nchan: int, edges, precision: int = PREC_FP32, batch: int = 1,
+                 fft_m: int = 0, norm_A: float = 1.0, r: float = 1.0, rprime: float = 1.0,
+                 dnu_c: float = 1.0, torch_workspace: bool = True):
+        import torch
+        L = lib()
+        self._L = L
+        e = [float(x) for x in edges]
+        self._edges = (ctypes.c_double * len(e))(*e)
+        d = PlanDesc(nt, nchan, len(e) - 1, self._edges, fft_m, precision, batch, norm_A, r,
+                     rprime, dnu_c)
+        h = ctypes.c_void_p()
+        st = L.bs_plan_create(ctypes.byref(d), ctypes.byref(h))
+        if st != BS_OK:
+            raise BsError(st, L.bs_last_error(None).decode())
+        self._h = h
+        self.nt, self.nchan, self.nbins, self.batch = nt, nchan, len(e) - 1, batch
+        self.precision = precision
+        info = self.info()
+        self.M, self.ntrip, self.nfields, self.ws_bytes, self.ucols = info[:5]
+        self._ws = None
+        if torch_workspace:
+            self._ws = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device="cuda")
+            base = self._ws.data_ptr()
+            off = (-base) % 256
+            self._check(L.bs_plan_set_workspace(self._h, ctypes.c_void_p(base + off),
+                                                ctypes.c_size_t(self.ws_bytes)))
+
+    def _check(self, st):
+        if st != BS_OK:
+            raise BsError(st, self._L.bs_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.bs_plan_destroy(self._h)
+            self._h = None
+            self._ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        arr = (ctypes.c_int64 * 6)()
+        self._check(self._L.bs_plan_info(self._h, arr, 6))
+        return list(arr)
+
+    def grid_load(self, vis, ngrid=None, chan_flags=None, stream=None):
+        """bs_grid_load: vis complex64 CUDA tensor [batch, nchan, nt, nt]."""
+        import numpy as np
+        flags = None
+        if chan_flags is not None:
+            f = np.ascontiguousarray(np.asarray(chan_flags, dtype=np.uint8))
+            if f.size != self.nchan:
+                raise ValueError("chan_flags must have nchan entries")
+            self._flags = f
+            flags = f.ctypes.data_as(ctypes.c_void_p)
+        self._check(self._L.bs_grid_load(self._h, _dptr(vis), _dptr(ngrid), flags,
+                                         _stream_ptr(stream)))
+
+    def counts(self):
+        """bs_counts: (T [ntrip] int64, folded N_nu [(2nc-1)^2] int64) as numpy."""
+        import numpy as np
+        tri = np.zeros(self.ntrip, np.int64)
+        nnu = np.zeros((2 * self.nchan - 1) ** 2, np.int64)
+        self._check(self._L.bs_counts(self._h, tri.ctypes.data_as(ctypes.c_void_p),
+                                      nnu.ctypes.data_as(ctypes.c_void_p)))
+        return tri, nnu.reshape(2 * self.nchan - 1, 2 * self.nchan - 1)
+
+    def mabs(self, block=None, out_full=None, accumulate=True, stream=None):
+        """bs_mabs over channel block (nu1_lo, nu1_hi, nu2_lo, nu2_hi, nu3_lo, nu3_hi)."""
+        blk = None
+        if block is not None:
+            self._blk = (ctypes.c_int32 * 6)(*[int(x) for x in block])
+            blk = self._blk
+        self._check(self._L.bs_mabs(self._h, blk, _dptr(out_full), 1 if accumulate else 0,
+                                    _stream_ptr(stream)))
+
+    def delta_reset(self, stream=None):
+        self._check(self._L.bs_delta_reset(self._h, _stream_ptr(stream)))
+
+    def mabs_delta(self, out, stream=None):
+        """bs_mabs_delta: out float64 CUDA [batch, ntrip, 2nc-1, 2nc-1]."""
+        self._check(self._L.bs_mabs_delta(self._h, _dptr(out), _stream_ptr(stream)))
+
+    def bs3d(self, out, stream=None):
+        """bs_bs3d: out float64 CUDA [batch, ntrip, nc, nc]."""
+        self._check(self._L.bs_bs3d(self._h, _dptr(out), _stream_ptr(stream)))
+
+    def check_hermitian(self, vis, tol=1e-6, stream=None):
+        """bs_check_hermitian; returns True when Hermitian within tol."""
+        st = self._L.bs_check_hermitian(self._h, _dptr(vis), ctypes.c_double(tol),
+                                        _stream_ptr(stream))
+        if st == 5:
+            return False
+        self._check(st)
+        return True

@@ -1,0 +1,90 @@
+// Internal declarations shared by the libbs translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "bs.h"
+
+namespace bsi {
+
+// Mixed-radix factorisation of a transform length (radices 4, 2, 3, 5).
+struct Radices {
+  int n = 0;
+  int r[24] = {0};
+};
+
+// One column of the triple contraction: field (l, nu3) and its ring triple.
+struct ColEntry {
+  int field;  // l * nchan + nu3
+  int trip;   // ring-triple index of (i, j, l)
+  int nu3;
+  int pad;
+};
+
+// A (ring pair, column tile) work item of the contraction.
+struct PairTile {
+  int ri, rj;    // rings of the pair operand
+  int col_off;   // offset of this pair's column list in the column array
+  int ncol;      // columns in the pair's list
+  int col0;      // first column of this tile
+  int pad[3];
+};
+
+// Geometry shared by the field kernels.
+struct GridGeom {
+  int nt, nc, nb, M, UC;  // UC: u >= 0 columns stored per field
+  int batch;
+};
+
+// Contraction launch arguments.
+struct ContractArgs {
+  const float *F;          // fields [batch][nb*nc][M*M]
+  long long fstride;       // M*M
+  long long bstride;       // nb*nc*M*M
+  int M2, nc;
+  const ColEntry *cols;
+  const PairTile *ptiles;
+  int nu1_lo, nu1_hi, nu2_lo, nu2_hi;
+  int n_r2;                // number of nu2 row blocks
+  int kseg_len, nkseg;
+  const double *tnorm;     // per ring triple: 1/(A M^2 T), 0 when T == 0
+  double *out_full;        // [batch][ntrip][nc][nc][nc] or null
+  long long full_bstride;  // ntrip*nc^3
+  double *dsum;            // [batch][ntrip][2nc-1][2nc-1] or null
+  long long dsum_bstride;  // ntrip*(2nc-1)^2
+};
+
+// ---- kernels / launchers (each returns cudaGetLastError after launch) ----
+cudaError_t launch_colpass(const GridGeom &g, const float2 *vis, const float *ngrid,
+                           const uint8_t *valid, const int8_t *label, const int *uext,
+                           const float2 *twM, const Radices &radM, float2 *G,
+                           cudaStream_t s);
+cudaError_t launch_rowpass(const GridGeom &g, const float2 *G, const uint8_t *valid,
+                           const int *uext, const float2 *twM, const Radices &radM,
+                           float *F, uint16_t *Fhi, uint16_t *Flo, cudaStream_t s);
+cudaError_t launch_effective_label(int ncell, const int8_t *label, const float *ngrid,
+                                  int8_t *out, cudaStream_t s);
+cudaError_t launch_counts(int nt, int nb, const int8_t *label, const int *cells, int ncells,
+                          const int *trip_of, unsigned long long *T, cudaStream_t s);
+cudaError_t launch_contract_simt(const ContractArgs &a, int ntiles_row, int npt,
+                                 int batch, cudaStream_t s);
+cudaError_t launch_full_fill(double *out, long long bstride, int batch, int ntrip, int nc,
+                             const int *blk, double value, cudaStream_t s);
+cudaError_t launch_full_finalize(double *out, long long bstride, int batch, int ntrip,
+                                 int nc, const int *blk, const uint8_t *valid,
+                                 const double *tnorm, cudaStream_t s);
+cudaError_t launch_delta_norm(const double *dsum, const long long *nnu, const double *tnorm,
+                              double *out, int batch, int ntrip, int nc, cudaStream_t s);
+cudaError_t launch_bs3d(const double *dsum, const long long *nnu, const double *tnorm,
+                        float2 *tmp, double *out, int batch, int ntrip, int nc,
+                        const float2 *twN, const Radices &radN, double scale,
+                        cudaStream_t s);
+cudaError_t launch_hermitian_check(const float2 *vis, int batch, int nc, int nt,
+                                   const int8_t *label, float *maxdiff, float *maxabs,
+                                   cudaStream_t s);
+
+}  // namespace bsi

@@ -1,0 +1,222 @@
+// Collapse, fold and delay transform (Section 3.2, Eq. dft), plus the FULL
+// layout fill / finalise of Eq. (estimator_t).
+//
+// Accumulators: dsum[b][trip][d1+nc-1][d2+nc-1] holds the pixel sums S of all
+// accumulated channel triples with (nu1-nu3, nu2-nu3) = (d1, d2); nnu[] the
+// number of valid such triples (unfolded).  Every valid triple of a ring
+// triple has the same denominator A M^2 T (channel-independent occupancy), so
+//   Bbar(d) = (S(d) + S(-d)) / (A M^2 T (N(d) + N(-d)))       (d != 0)
+//   Bbar(0) = S(0) / (A M^2 T N(0))
+// is the mean of B_A over the valid triples at +-d: the fold of Fig. Nv.
+//
+// Delay transform: the inclusive square n, m in [-nc/2, nc/2] is summed onto
+// Z_nc (n mod nc; for even nc the two ends +-nc/2 share index nc/2), then a
+// forward 2D DFT of length nc (Stockham, FP32) gives
+//   B(a, b) = (r^2 r' dnu_c)^2 sum_{n,m} exp(-2 pi i (n a + m b)/nc) Bbar(n, m).
+// Unsampled separations contribute zero.  Non-smooth nc use a direct DFT.
+#include "bs_internal.h"
+#include "fft_smem.cuh"
+
+namespace bsi {
+
+namespace {
+
+__device__ __forceinline__ double folded_bbar(const double *__restrict__ ds,
+                                              const long long *__restrict__ nnu, double tn, int nc,
+                                              int i1, int i2) {
+  const int n2 = 2 * nc - 1;
+  const int j1 = n2 - 1 - i1, j2 = n2 - 1 - i2;
+  long long cnt = nnu[i1 * n2 + i2];
+  double s = ds[(long long)i1 * n2 + i2];
+  if (j1 != i1 || j2 != i2) {
+    cnt += nnu[j1 * n2 + j2];
+    s += ds[(long long)j1 * n2 + j2];
+  }
+  if (cnt <= 0 || tn == 0.0) return __longlong_as_double(0x7ff8000000000000LL);
+  return s * tn / (double)cnt;
+}
+
+__global__ void k_delta_norm(const double *__restrict__ dsum, const long long *__restrict__ nnu,
+                             const double *__restrict__ tnorm, double *__restrict__ out, int ntrip,
+                             int nc) {
+  const int n2 = 2 * nc - 1;
+  const long long plane = (long long)n2 * n2;
+  const int trip = blockIdx.y, b = blockIdx.z;
+  const double *ds = dsum + ((long long)b * ntrip + trip) * plane;
+  double *o = out + ((long long)b * ntrip + trip) * plane;
+  const double tn = tnorm[trip];
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < plane;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i1 = (int)(t / n2), i2 = (int)(t - (long long)i1 * n2);
+    o[t] = folded_bbar(ds, nnu, tn, nc, i1, i2);
+  }
+}
+
+__device__ void dft_direct(const float2 *x, float2 *y, int N, const float2 *tw, float sign) {
+  for (int k = threadIdx.x; k < N; k += blockDim.x) {
+    float2 acc = make_float2(0.f, 0.f);
+    int idx = 0;
+    for (int j = 0; j < N; ++j) {
+      float2 w = tw[idx];
+      w.y *= sign;
+      acc = cadd(acc, cmul(x[j], w));
+      idx += k;
+      if (idx >= N) idx -= N;
+    }
+    y[k] = acc;
+  }
+  __syncthreads();
+}
+
+__global__ void k_bs3d_rows(const double *__restrict__ dsum, const long long *__restrict__ nnu,
+                            const double *__restrict__ tnorm, float2 *__restrict__ tmp, int ntrip,
+                            int nc, const float2 *__restrict__ twN, Radices radN) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2 *tw = reinterpret_cast<float2 *>(smem_raw);
+  float2 *bufA = tw + nc;
+  float2 *bufB = bufA + nc;
+  const int nidx = blockIdx.x, trip = blockIdx.y, b = blockIdx.z;
+  const int n2 = 2 * nc - 1, h = nc / 2;
+  const double *ds = dsum + ((long long)b * ntrip + trip) * (long long)n2 * n2;
+  const double tn = tnorm[trip];
+  for (int t = threadIdx.x; t < nc; t += blockDim.x) tw[t] = twN[t];
+  for (int m = threadIdx.x; m < nc; m += blockDim.x) {
+    double acc = 0.0;
+    for (int sa = 0; sa < 2; ++sa) {
+      const int np = sa ? nidx - nc : nidx;
+      if (np < -h || np > h) continue;
+      for (int sb = 0; sb < 2; ++sb) {
+        const int mp = sb ? m - nc : m;
+        if (mp < -h || mp > h) continue;
+        const double v = folded_bbar(ds, nnu, tn, nc, np + nc - 1, mp + nc - 1);
+        if (v == v) acc += v;
+      }
+    }
+    bufA[m] = make_float2((float)acc, 0.f);
+  }
+  __syncthreads();
+  float2 *res;
+  if (radN.n > 0) {
+    res = stockham(bufA, bufB, 1, nc, radN, tw, -1.0f);
+  } else {
+    dft_direct(bufA, bufB, nc, tw, -1.0f);
+    res = bufB;
+  }
+  float2 *tb = tmp + ((long long)b * ntrip + trip) * (long long)nc * nc;
+  for (int k = threadIdx.x; k < nc; k += blockDim.x) tb[(long long)k * nc + nidx] = res[k];
+}
+
+__global__ void k_bs3d_cols(const float2 *__restrict__ tmp, double *__restrict__ out, int ntrip,
+                            int nc, const float2 *__restrict__ twN, Radices radN, double scale) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2 *tw = reinterpret_cast<float2 *>(smem_raw);
+  float2 *bufA = tw + nc;
+  float2 *bufB = bufA + nc;
+  const int bb = blockIdx.x, trip = blockIdx.y, b = blockIdx.z;
+  const int h = nc / 2;
+  const float2 *tb = tmp + ((long long)b * ntrip + trip) * (long long)nc * nc + (long long)bb * nc;
+  for (int t = threadIdx.x; t < nc; t += blockDim.x) {
+    tw[t] = twN[t];
+    bufA[t] = tb[t];
+  }
+  __syncthreads();
+  float2 *res;
+  if (radN.n > 0) {
+    res = stockham(bufA, bufB, 1, nc, radN, tw, -1.0f);
+  } else {
+    dft_direct(bufA, bufB, nc, tw, -1.0f);
+    res = bufB;
+  }
+  double *ob = out + ((long long)b * ntrip + trip) * (long long)nc * nc;
+  const int bidx = (bb < nc - h) ? bb + h : bb - nc + h;
+  for (int k = threadIdx.x; k < nc; k += blockDim.x) {
+    const int aidx = (k < nc - h) ? k + h : k - nc + h;
+    ob[(long long)aidx * nc + bidx] = scale * (double)res[k].x;
+  }
+}
+
+__global__ void k_full_fill(double *__restrict__ out, long long bstride, int ntrip, int nc, int b0,
+                            int b1, int b2, int b3, int b4, int b5, double value) {
+  const int trip = blockIdx.y, b = blockIdx.z;
+  const int w1 = b1 - b0, w2 = b3 - b2, w3 = b5 - b4;
+  const long long n = (long long)w1 * w2 * w3;
+  double *o = out + (long long)b * bstride + (long long)trip * nc * nc * nc;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i3 = (int)(t % w3);
+    const long long r = t / w3;
+    const int i2 = (int)(r % w2), i1 = (int)(r / w2);
+    o[((long long)(b0 + i1) * nc + (b2 + i2)) * nc + (b4 + i3)] = value;
+  }
+}
+
+__global__ void k_full_finalize(double *__restrict__ out, long long bstride, int ntrip, int nc,
+                                int b0, int b1, int b2, int b3, int b4, int b5,
+                                const uint8_t *__restrict__ valid,
+                                const double *__restrict__ tnorm) {
+  const int trip = blockIdx.y, b = blockIdx.z;
+  const int w1 = b1 - b0, w2 = b3 - b2, w3 = b5 - b4;
+  const long long n = (long long)w1 * w2 * w3;
+  double *o = out + (long long)b * bstride + (long long)trip * nc * nc * nc;
+  const bool tok = tnorm[trip] != 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i3 = (int)(t % w3);
+    const long long r = t / w3;
+    const int i2 = (int)(r % w2), i1 = (int)(r / w2);
+    const int n1 = b0 + i1, nn2 = b2 + i2, n3 = b4 + i3;
+    if (!tok || !valid[n1] || !valid[nn2] || !valid[n3])
+      o[((long long)n1 * nc + nn2) * nc + n3] = __longlong_as_double(0x7ff8000000000000LL);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_delta_norm(const double *dsum, const long long *nnu, const double *tnorm,
+                              double *out, int batch, int ntrip, int nc, cudaStream_t s) {
+  const long long plane = (long long)(2 * nc - 1) * (2 * nc - 1);
+  dim3 grid((unsigned)std::min<long long>((plane + 255) / 256, 1024), ntrip, batch);
+  k_delta_norm<<<grid, 256, 0, s>>>(dsum, nnu, tnorm, out, ntrip, nc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bs3d(const double *dsum, const long long *nnu, const double *tnorm, float2 *tmp,
+                        double *out, int batch, int ntrip, int nc, const float2 *twN,
+                        const Radices &radN, double scale, cudaStream_t s) {
+  const size_t smem = (size_t)3 * nc * sizeof(float2);
+  cudaError_t e = cudaFuncSetAttribute(k_bs3d_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_bs3d_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int threads = nc >= 256 ? 256 : (nc >= 64 ? 64 : 32);
+  dim3 grid(nc, ntrip, batch);
+  k_bs3d_rows<<<grid, threads, smem, s>>>(dsum, nnu, tnorm, tmp, ntrip, nc, twN, radN);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_bs3d_cols<<<grid, threads, smem, s>>>(tmp, out, ntrip, nc, twN, radN, scale);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_full_fill(double *out, long long bstride, int batch, int ntrip, int nc,
+                             const int *blk, double value, cudaStream_t s) {
+  const long long n = (long long)(blk[1] - blk[0]) * (blk[3] - blk[2]) * (blk[5] - blk[4]);
+  if (n == 0) return cudaSuccess;
+  dim3 grid((unsigned)std::min<long long>((n + 255) / 256, 1024), ntrip, batch);
+  k_full_fill<<<grid, 256, 0, s>>>(out, bstride, ntrip, nc, blk[0], blk[1], blk[2], blk[3], blk[4],
+                                   blk[5], value);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_full_finalize(double *out, long long bstride, int batch, int ntrip, int nc,
+                                 const int *blk, const uint8_t *valid, const double *tnorm,
+                                 cudaStream_t s) {
+  const long long n = (long long)(blk[1] - blk[0]) * (blk[3] - blk[2]) * (blk[5] - blk[4]);
+  if (n == 0) return cudaSuccess;
+  dim3 grid((unsigned)std::min<long long>((n + 255) / 256, 1024), ntrip, batch);
+  k_full_finalize<<<grid, 256, 0, s>>>(out, bstride, ntrip, nc, blk[0], blk[1], blk[2], blk[3],
+                                       blk[4], blk[5], valid, tnorm);
+  return cudaGetLastError();
+}
+
+}  // namespace bsi

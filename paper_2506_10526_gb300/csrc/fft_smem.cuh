@@ -1,0 +1,137 @@
+// Shared-memory Stockham autosort FFT (radix 4, 2, 3, 5), FP32, used by the
+// image-plane field kernels (Eq. iFT) and by the delay transform (Eq. dft).
+//
+// Formulation: for a length-N transform with radices R_1 ... R_s and
+// p = R_1 ... R_{t-1} before stage t, every butterfly index i in [0, N/R)
+// reads x[i + q N/R] (q < R), multiplies input q by w^(q k), k = i mod p,
+// w = exp(sign 2 pi i / (p R)), applies the radix-R DFT and writes
+// y[(i - k) R + k + q p].  Input and output of a stage ping-pong between two
+// shared buffers; the result needs no bit reversal.  Twiddles come from a
+// table tw[t] = exp(+2 pi i t / N) (FP64 on the host, rounded to FP32);
+// sign = -1 uses the conjugate.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "bs_internal.h"
+
+namespace bsi {
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// multiply by sign * i
+__device__ __forceinline__ float2 cmuli(float2 a, float sign) { return make_float2(-sign * a.y, sign * a.x); }
+
+template <int R>
+__device__ __forceinline__ void butterfly(float2 *u, float sign);
+
+template <>
+__device__ __forceinline__ void butterfly<2>(float2 *u, float) {
+  float2 a = u[0], b = u[1];
+  u[0] = cadd(a, b);
+  u[1] = csub(a, b);
+}
+
+template <>
+__device__ __forceinline__ void butterfly<4>(float2 *u, float sign) {
+  float2 s02 = cadd(u[0], u[2]), d02 = csub(u[0], u[2]);
+  float2 s13 = cadd(u[1], u[3]), d13 = cmuli(csub(u[1], u[3]), sign);
+  u[0] = cadd(s02, s13);
+  u[2] = csub(s02, s13);
+  u[1] = cadd(d02, d13);
+  u[3] = csub(d02, d13);
+}
+
+template <>
+__device__ __forceinline__ void butterfly<3>(float2 *u, float sign) {
+  // w = exp(sign 2 pi i / 3) = -1/2 + sign i sqrt(3)/2
+  const float c = -0.5f, s = 0.86602540378443864676f * sign;
+  float2 a = u[0], b = u[1], d = u[2];
+  float2 t = cadd(b, d);
+  float2 m = make_float2(a.x + c * t.x, a.y + c * t.y);
+  float2 q = csub(b, d);
+  float2 rq = make_float2(-s * q.y, s * q.x);  // i s (b - d)
+  u[0] = cadd(a, t);
+  u[1] = cadd(m, rq);
+  u[2] = csub(m, rq);
+}
+
+template <>
+__device__ __forceinline__ void butterfly<5>(float2 *u, float sign) {
+  // cos(2pi/5) = (sqrt5 - 1)/4, cos(4pi/5) = -(sqrt5 + 1)/4,
+  // sin(2pi/5), sin(4pi/5) from sin^2 = 1 - cos^2.
+  const float c1 = 0.30901699437494742410f, c2 = -0.80901699437494742410f;
+  const float s1 = 0.95105651629515357212f * sign, s2 = 0.58778525229247312917f * sign;
+  float2 a = u[0];
+  float2 t1 = cadd(u[1], u[4]), t2 = cadd(u[2], u[3]);
+  float2 d1 = csub(u[1], u[4]), d2 = csub(u[2], u[3]);
+  float2 m1 = make_float2(a.x + c1 * t1.x + c2 * t2.x, a.y + c1 * t1.y + c2 * t2.y);
+  float2 m2 = make_float2(a.x + c2 * t1.x + c1 * t2.x, a.y + c2 * t1.y + c1 * t2.y);
+  // i (s1 d1 + s2 d2) and i (s2 d1 - s1 d2)
+  float2 e1 = make_float2(-(s1 * d1.y + s2 * d2.y), s1 * d1.x + s2 * d2.x);
+  float2 e2 = make_float2(-(s2 * d1.y - s1 * d2.y), s2 * d1.x - s1 * d2.x);
+  u[0] = cadd(a, cadd(t1, t2));
+  u[1] = cadd(m1, e1);
+  u[4] = csub(m1, e1);
+  u[2] = cadd(m2, e2);
+  u[3] = csub(m2, e2);
+}
+
+template <int R>
+__device__ __forceinline__ void stockham_stage(const float2 *__restrict__ x, float2 *__restrict__ y,
+                                               int nrows, int N, int p, const float2 *tw,
+                                               float sign) {
+  const int NR = N / R;
+  const int tstride = N / (p * R);
+  const int total = nrows * NR;
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int row = idx / NR;
+    const int i = idx - row * NR;
+    const float2 *xr = x + row * N;
+    float2 *yr = y + row * N;
+    const int k = i % p;
+    float2 u[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) u[q] = xr[i + q * NR];
+    if (k != 0) {
+#pragma unroll
+      for (int q = 1; q < R; ++q) {
+        float2 w = tw[q * k * tstride];
+        w.y *= sign;
+        u[q] = cmul(u[q], w);
+      }
+    }
+    butterfly<R>(u, sign);
+    const int j = (i - k) * R + k;
+#pragma unroll
+    for (int q = 0; q < R; ++q) yr[j + q * p] = u[q];
+  }
+}
+
+// In-place (ping-pong) transform of nrows rows of length N stored
+// contiguously in x; y is scratch of the same size.  All threads of the block
+// must call it.  Returns the buffer that holds the result.
+__device__ __forceinline__ float2 *stockham(float2 *x, float2 *y, int nrows, int N,
+                                            const Radices &rad, const float2 *tw, float sign) {
+  int p = 1;
+  for (int s = 0; s < rad.n; ++s) {
+    const int R = rad.r[s];
+    switch (R) {
+      case 4: stockham_stage<4>(x, y, nrows, N, p, tw, sign); break;
+      case 2: stockham_stage<2>(x, y, nrows, N, p, tw, sign); break;
+      case 3: stockham_stage<3>(x, y, nrows, N, p, tw, sign); break;
+      default: stockham_stage<5>(x, y, nrows, N, p, tw, sign); break;
+    }
+    __syncthreads();
+    float2 *t = x;
+    x = y;
+    y = t;
+    p *= R;
+  }
+  return x;
+}
+
+}  // namespace bsi

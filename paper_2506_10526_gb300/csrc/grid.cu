@@ -1,0 +1,329 @@
+// Image-plane fields of Eq. (iFT): for ring m and channel nu,
+//   F_{m,nu}(x, y) = sum_{g in ring m} W_g V_g(nu) exp(+2 pi i (u x + v y) / M),
+// an unnormalised inverse 2D DFT of side M, real because the ring and the
+// visibilities are Hermitian.  Two passes through the plan workspace:
+//
+//  colpass  (shell mask + weights + FFT along v)
+//           G_{m,nu}(u, y) = sum_v X(u, v) exp(+2 pi i v y / M),  u >= 0,
+//           X = W V restricted to ring m (W = 1/N_g, 0 for an empty cell or a
+//           flagged channel).  One CTA: one channel, UB consecutive u columns,
+//           all rings; the visibility tile is read once and masked per ring.
+//           Output G[b][m][nu][y][u] (u fastest, UC columns).
+//  rowpass  (Hermitian C2R along u)
+//           F(x, y) = sum_{|u| < uext(m)} G(u, y) exp(+2 pi i u x / M) with
+//           G(-u, y) = conj G(u, y); two rows y, y+1 share one complex FFT
+//           (z = A + i B, F(., y) = Re z, F(., y+1) = Im z).  Output
+//           F[b][m*nc+nu][y*M + x]; in split-precision plans also the BF16
+//           hi / lo parts (hi = round(F), lo = round(F - hi)).
+//
+// Also: exact closed-triangle counts and the Hermitian check.
+#include <cuda_bf16.h>
+
+#include "bs_internal.h"
+#include "fft_smem.cuh"
+
+namespace bsi {
+
+namespace {
+
+__global__ void __launch_bounds__(256) k_colpass(GridGeom g, int UB, const float2 *__restrict__ vis,
+                                                 const float *__restrict__ ngrid,
+                                                 const uint8_t *__restrict__ valid,
+                                                 const int8_t *__restrict__ label,
+                                                 const int *__restrict__ uext,
+                                                 const float2 *__restrict__ twM, Radices radM,
+                                                 float2 *__restrict__ G) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int M = g.M, nt = g.nt, h = nt / 2;
+  const int u0 = blockIdx.x * UB;
+  const int nu = blockIdx.y;
+  const int b = blockIdx.z;
+  if (!valid[nu]) return;  // fields of a flagged channel are written as zeros by rowpass
+  float2 *tw = reinterpret_cast<float2 *>(smem_raw);
+  float2 *bufA = tw + M;
+  float2 *bufB = bufA + UB * M;
+  float2 *xt = bufB + UB * M;                                   // [nt][UB] weighted visibilities
+  int8_t *lt = reinterpret_cast<int8_t *>(xt + nt * UB);        // [nt][UB] ring labels
+  for (int t = threadIdx.x; t < M; t += blockDim.x) tw[t] = twM[t];
+  const float2 *vb = vis + ((long long)b * g.nc + nu) * (long long)nt * nt;
+  for (int t = threadIdx.x; t < nt * UB; t += blockDim.x) {
+    const int iv = t / UB, c = t - iv * UB;
+    const int u = u0 + c;
+    float2 x = make_float2(0.f, 0.f);
+    int8_t lab = -1;
+    if (u < h) {
+      const int cell = iv * nt + (u + h);
+      lab = label[cell];
+      if (lab >= 0) {
+        const float n = ngrid ? ngrid[cell] : 1.0f;
+        if (n > 0.f) {
+          const float w = 1.0f / n;
+          const float2 v = vb[cell];
+          x = make_float2(w * v.x, w * v.y);
+        } else {
+          lab = -1;
+        }
+      }
+    }
+    xt[t] = x;
+    lt[t] = lab;
+  }
+  __syncthreads();
+  for (int m = 0; m < g.nb; ++m) {
+    const int ue = uext[m];
+    if (u0 >= ue) continue;  // block-uniform
+    for (int t = threadIdx.x; t < UB * M; t += blockDim.x) bufA[t] = make_float2(0.f, 0.f);
+    __syncthreads();
+    for (int t = threadIdx.x; t < nt * UB; t += blockDim.x) {
+      if (lt[t] == m) {
+        const int iv = t / UB, c = t - iv * UB;
+        int y = iv - h;
+        if (y < 0) y += M;
+        bufA[c * M + y] = xt[t];
+      }
+    }
+    __syncthreads();
+    float2 *res = stockham(bufA, bufB, UB, M, radM, tw, +1.0f);
+    float2 *Gm = G + (((long long)b * g.nb + m) * g.nc + nu) * (long long)M * g.UC;
+    const int ncols = min(UB, g.UC - u0);
+    for (int t = threadIdx.x; t < M * UB; t += blockDim.x) {
+      const int y = t / UB, c = t - y * UB;
+      if (c < ncols) Gm[(long long)y * g.UC + u0 + c] = res[c * M + y];
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ uint16_t bf16_bits(float x) {
+  __nv_bfloat16 h = __float2bfloat16_rn(x);
+  return *reinterpret_cast<uint16_t *>(&h);
+}
+__device__ __forceinline__ float bf16_val(uint16_t b) {
+  return __uint_as_float(((uint32_t)b) << 16);
+}
+
+__global__ void __launch_bounds__(256) k_rowpass(GridGeom g, int RPB, const float2 *__restrict__ G,
+                                                 const uint8_t *__restrict__ valid,
+                                                 const int *__restrict__ uext,
+                                                 const float2 *__restrict__ twM, Radices radM,
+                                                 float *__restrict__ F, uint16_t *__restrict__ Fhi,
+                                                 uint16_t *__restrict__ Flo) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int M = g.M;
+  const int f = blockIdx.y;  // m * nc + nu
+  const int m = f / g.nc, nu = f - m * g.nc;
+  const int b = blockIdx.z;
+  const int y0 = blockIdx.x * 2 * RPB;
+  const int npair = min(RPB, (M - y0) / 2);
+  const long long fbase = ((long long)b * g.nb * g.nc + f) * (long long)M * M;
+  const int ue = uext[m];
+  if (!valid[nu] || ue == 0) {
+    for (int t = threadIdx.x; t < 2 * npair * M; t += blockDim.x) {
+      const long long o = fbase + (long long)y0 * M + t;
+      F[o] = 0.f;
+      if (Fhi) {
+        Fhi[o] = 0;
+        Flo[o] = 0;
+      }
+    }
+    return;
+  }
+  float2 *tw = reinterpret_cast<float2 *>(smem_raw);
+  float2 *bufA = tw + M;
+  float2 *bufB = bufA + RPB * M;
+  for (int t = threadIdx.x; t < M; t += blockDim.x) tw[t] = twM[t];
+  for (int t = threadIdx.x; t < RPB * M; t += blockDim.x) bufA[t] = make_float2(0.f, 0.f);
+  __syncthreads();
+  const float2 *Gm = G + (((long long)b * g.nb + m) * g.nc + nu) * (long long)M * g.UC;
+  for (int t = threadIdx.x; t < npair * ue; t += blockDim.x) {
+    const int p = t / ue, u = t - p * ue;
+    const int y = y0 + 2 * p;
+    const float2 a = Gm[(long long)y * g.UC + u];
+    const float2 c = Gm[(long long)(y + 1) * g.UC + u];
+    float2 *z = bufA + p * M;
+    if (u == 0) {
+      z[0] = make_float2(a.x, c.x);
+    } else {
+      z[u] = make_float2(a.x - c.y, a.y + c.x);      // A(u) + i B(u)
+      z[M - u] = make_float2(a.x + c.y, c.x - a.y);  // conj A(u) + i conj B(u)
+    }
+  }
+  __syncthreads();
+  float2 *res = stockham(bufA, bufB, RPB, M, radM, tw, +1.0f);
+  for (int t = threadIdx.x; t < npair * 2 * M; t += blockDim.x) {
+    const int p = t / (2 * M), r = t - p * 2 * M;
+    const int which = r / M, x = r - which * M;
+    const float2 z = res[p * M + x];
+    const float v = which ? z.y : z.x;
+    const long long o = fbase + (long long)(y0 + 2 * p + which) * M + x;
+    F[o] = v;
+    if (Fhi) {
+      const uint16_t hb = bf16_bits(v);
+      Fhi[o] = hb;
+      Flo[o] = bf16_bits(v - bf16_val(hb));
+    }
+  }
+}
+
+// Effective ring labels: the plan's labels with empty cells (N_g <= 0) removed.
+__global__ void k_effective_label(int ncell, const int8_t *__restrict__ label,
+                                  const float *__restrict__ ngrid, int8_t *__restrict__ out) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ncell; t += gridDim.x * blockDim.x)
+    out[t] = (ngrid && !(ngrid[t] > 0.f)) ? (int8_t)-1 : label[t];
+}
+
+// Closed-triangle counts: every ordered pair (g1, g2) of binned, filled cells
+// is tested once; the closing point g3 = -g1 - g2 is looked up in the label
+// table; when (ring(g1), ring(g2), ring(g3)) is a listed triple i <= j <= l its
+// counter is incremented.  A CTA takes P1 first corners and sweeps all second
+// corners; 32-bit shared counters, 64-bit global sums.
+constexpr int kCountP1 = 32;
+
+__global__ void __launch_bounds__(256) k_counts(int nt, int nb, const int8_t *__restrict__ label,
+                                                const int *__restrict__ cells, int ncells,
+                                                const int *__restrict__ trip_of,
+                                                unsigned long long *__restrict__ T, int ntrip,
+                                                int label_in_smem) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned int *cnt = reinterpret_cast<unsigned int *>(smem_raw);
+  int *tof = reinterpret_cast<int *>(cnt + ntrip);
+  int8_t *lab_s = reinterpret_cast<int8_t *>(tof + nb * nb * nb);
+  __shared__ int su1[kCountP1], sv1[kCountP1], sr1[kCountP1];
+  const int h = nt / 2;
+  const int nb3 = nb * nb * nb;
+  for (int t = threadIdx.x; t < ntrip; t += blockDim.x) cnt[t] = 0;
+  for (int t = threadIdx.x; t < nb3; t += blockDim.x) tof[t] = trip_of[t];
+  if (label_in_smem)
+    for (int t = threadIdx.x; t < nt * nt; t += blockDim.x) lab_s[t] = label[t];
+  const int8_t *lab = label_in_smem ? lab_s : label;
+  if (threadIdx.x < kCountP1) {
+    const int p = blockIdx.x * kCountP1 + threadIdx.x;
+    int r = -1, u = 0, v = 0;
+    if (p < ncells) {
+      const int c = cells[p];
+      u = (c & 0xffff) - 32768;
+      v = ((c >> 16) & 0xffff) - 32768;
+      r = label[(v + h) * nt + (u + h)];
+    }
+    su1[threadIdx.x] = u;
+    sv1[threadIdx.x] = v;
+    sr1[threadIdx.x] = r;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < ncells; q += blockDim.x) {
+    const int c2 = cells[q];
+    const int u2 = (c2 & 0xffff) - 32768, v2 = ((c2 >> 16) & 0xffff) - 32768;
+    const int r2 = lab[(v2 + h) * nt + (u2 + h)];
+    if (r2 < 0) continue;
+#pragma unroll 4
+    for (int p = 0; p < kCountP1; ++p) {
+      const int r1 = sr1[p];
+      if (r1 < 0) continue;
+      const int u3 = -su1[p] - u2, v3 = -sv1[p] - v2;
+      if (u3 <= -h || u3 >= h || v3 <= -h || v3 >= h) continue;
+      const int r3 = lab[(v3 + h) * nt + (u3 + h)];
+      if (r3 < 0) continue;
+      const int t = tof[(r1 * nb + r2) * nb + r3];
+      if (t >= 0) atomicAdd(&cnt[t], 1u);
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < ntrip; t += blockDim.x)
+    if (cnt[t]) atomicAdd(&T[t], (unsigned long long)cnt[t]);
+}
+
+__device__ __forceinline__ void atomic_max_float(float *addr, float v) {
+  // v >= 0: the IEEE bit pattern orders like an unsigned integer
+  atomicMax(reinterpret_cast<unsigned int *>(addr), __float_as_uint(v));
+}
+
+__global__ void k_hermitian(const float2 *__restrict__ vis, int nc, int nt,
+                            const int8_t *__restrict__ label, float *maxdiff, float *maxabs) {
+  const int h = nt / 2;
+  float md = 0.f, ma = 0.f;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)nc * nt * nt;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int cell = (int)(t % ((long long)nt * nt));
+    const long long base = (long long)blockIdx.y * nc * nt * nt + (t - cell);
+    const float2 a = vis[base + cell];
+    ma = fmaxf(ma, fabsf(a.x) + fabsf(a.y));
+    if (label[cell] < 0) continue;
+    const int iu = cell % nt, iv = cell / nt;
+    const int mirror = (2 * h - iv) * nt + (2 * h - iu);
+    const float2 c = vis[base + mirror];
+    md = fmaxf(md, fabsf(a.x - c.x) + fabsf(a.y + c.y));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    md = fmaxf(md, __shfl_xor_sync(0xffffffffu, md, o));
+    ma = fmaxf(ma, __shfl_xor_sync(0xffffffffu, ma, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomic_max_float(maxdiff, md);
+    atomic_max_float(maxabs, ma);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_colpass(const GridGeom &g, const float2 *vis, const float *ngrid,
+                           const uint8_t *valid, const int8_t *label, const int *uext,
+                           const float2 *twM, const Radices &radM, float2 *G, cudaStream_t s) {
+  int UB = 16;
+  while (UB > 1 && (size_t)(2 * UB * g.M + g.M + UB * g.nt) * sizeof(float2) + UB * g.nt >
+                       (size_t)200 * 1024)
+    UB /= 2;
+  const size_t smem = (size_t)(g.M + 2 * UB * g.M + g.nt * UB) * sizeof(float2) + (size_t)g.nt * UB;
+  cudaError_t e = cudaFuncSetAttribute(k_colpass, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((g.UC + UB - 1) / UB, g.nc, g.batch);
+  k_colpass<<<grid, 256, smem, s>>>(g, UB, vis, ngrid, valid, label, uext, twM, radM, G);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rowpass(const GridGeom &g, const float2 *G, const uint8_t *valid,
+                           const int *uext, const float2 *twM, const Radices &radM, float *F,
+                           uint16_t *Fhi, uint16_t *Flo, cudaStream_t s) {
+  int RPB = 8;
+  while (RPB > 1 && (size_t)(2 * RPB * g.M + g.M) * sizeof(float2) > (size_t)96 * 1024) RPB /= 2;
+  const size_t smem = (size_t)(2 * RPB * g.M + g.M) * sizeof(float2);
+  cudaError_t e = cudaFuncSetAttribute(k_rowpass, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((g.M / 2 + RPB - 1) / RPB, g.nb * g.nc, g.batch);
+  k_rowpass<<<grid, 256, smem, s>>>(g, RPB, G, valid, uext, twM, radM, F, Fhi, Flo);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_effective_label(int ncell, const int8_t *label, const float *ngrid,
+                                  int8_t *out, cudaStream_t s) {
+  k_effective_label<<<(ncell + 255) / 256, 256, 0, s>>>(ncell, label, ngrid, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_counts(int nt, int nb, const int8_t *label, const int *cells, int ncells,
+                          const int *trip_of, unsigned long long *T, cudaStream_t s) {
+  const int ntrip = nb * (nb + 1) * (nb + 2) / 6;
+  if (ncells == 0) return cudaSuccess;
+  const size_t base = (size_t)ntrip * sizeof(unsigned int) + (size_t)nb * nb * nb * sizeof(int);
+  const int in_smem = base + (size_t)nt * nt <= (size_t)160 * 1024;
+  const size_t smem = base + (in_smem ? (size_t)nt * nt : 0);
+  cudaError_t e = cudaFuncSetAttribute(k_counts, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((ncells + kCountP1 - 1) / kCountP1);
+  k_counts<<<grid, 256, smem, s>>>(nt, nb, label, cells, ncells, trip_of, T, ntrip, in_smem);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hermitian_check(const float2 *vis, int batch, int nc, int nt,
+                                   const int8_t *label, float *maxdiff, float *maxabs,
+                                   cudaStream_t s) {
+  const long long n = (long long)nc * nt * nt;
+  int blocks = (int)std::min<long long>((n + 255) / 256, 4096);
+  dim3 grid(blocks, batch);
+  k_hermitian<<<grid, 256, 0, s>>>(vis, nc, nt, label, maxdiff, maxabs);
+  return cudaGetLastError();
+}
+
+}  // namespace bsi

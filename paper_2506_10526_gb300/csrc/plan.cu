@@ -1,0 +1,654 @@
+// C ABI of libbs (include/bs.h): plan construction (host), workspace
+// layout, and the orchestration of the device stages of Section 3.2.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "bs_internal.h"
+
+using namespace bsi;
+
+namespace {
+
+thread_local std::string g_create_error = "no error";
+
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+bool factor_radices(int n, Radices &r) {
+  r.n = 0;
+  if (n <= 0) return false;
+  int m = n;
+  while (m % 4 == 0 && r.n < 24) {
+    r.r[r.n++] = 4;
+    m /= 4;
+  }
+  while (m % 2 == 0 && r.n < 24) {
+    r.r[r.n++] = 2;
+    m /= 2;
+  }
+  while (m % 3 == 0 && r.n < 24) {
+    r.r[r.n++] = 3;
+    m /= 3;
+  }
+  while (m % 5 == 0 && r.n < 24) {
+    r.r[r.n++] = 5;
+    m /= 5;
+  }
+  if (m != 1) {
+    r.n = 0;
+    return false;
+  }
+  return true;
+}
+
+bool is_smooth(int n) {
+  Radices r;
+  return n == 1 || factor_radices(n, r);
+}
+
+// exp(+2 pi i t / n), t in [0, n), FP64 then rounded to FP32
+std::vector<float2> twiddles(int n) {
+  std::vector<float2> tw(n);
+  for (int t = 0; t < n; ++t) {
+    const double x = 2.0 * (double)t / (double)n;  // angle / pi
+    tw[t] = make_float2((float)std::cos(M_PI * x), (float)std::sin(M_PI * x));
+  }
+  return tw;
+}
+
+struct WsLayout {
+  size_t label, efflabel, cells, uext, tripof, valid, twM, twN, tnorm, T, nnu, cols, ptiles, G, F,
+      Fhi, Flo, dsum, tmp3d, herm, total;
+};
+
+}  // namespace
+
+struct bs_plan_s {
+  bs_plan_desc d{};
+  std::vector<double> edges;
+  int nt = 0, nc = 0, nb = 0, M = 0, UC = 0, batch = 1, ntrip = 0, nf = 0;
+  int device = 0;
+  double normA = 1, scale3d = 1;
+  Radices radM, radN;
+  std::vector<int8_t> label;     // [nt*nt]
+  std::vector<int> cells;        // packed (u + 32768) | (v + 32768) << 16 of binned cells
+  std::vector<int> uext;         // [nb]
+  std::vector<int> trips;        // [ntrip][3]
+  std::vector<int> trip_of;      // [nb^3] -> trip index of sorted (i<=j<=l), else -1
+  std::vector<long long> T;      // [ntrip] closed-triangle counts
+  std::vector<double> tnorm;     // [ntrip]
+  std::vector<uint8_t> valid;    // [nc]
+  std::vector<long long> nnu;    // [(2nc-1)^2] accumulated unfolded sampling
+  bool counts_ready = false, counts_default = false, nnu_dirty = true, loaded = false;
+  bool sticky = false;
+  std::string err = "no error";
+  // workspace
+  WsLayout L{};
+  unsigned char *ws = nullptr;
+  bool ws_owned = false;
+  size_t max_cols = 0, max_ptiles = 0;
+  std::vector<ColEntry> h_cols;
+  std::vector<PairTile> h_ptiles;
+
+  template <class T_>
+  T_ *at(size_t off) const {
+    return reinterpret_cast<T_ *>(ws + off);
+  }
+};
+
+namespace {
+
+bs_status fail(bs_plan p, bs_status s, const std::string &msg) {
+  if (p)
+    p->err = msg;
+  else
+    g_create_error = msg;
+  return s;
+}
+
+bs_status cuda_fail(bs_plan p, cudaError_t e, const char *where) {
+  p->sticky = true;
+  return fail(p, BS_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define BS_CUDA(call)                                   \
+  do {                                                  \
+    cudaError_t e__ = (call);                           \
+    if (e__ != cudaSuccess) return cuda_fail(p, e__, #call); \
+  } while (0)
+
+void compute_layout(bs_plan p) {
+  WsLayout &L = p->L;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t r = o;
+    o += align256(bytes);
+    return r;
+  };
+  const size_t n2 = (size_t)(2 * p->nc - 1);
+  L.label = take((size_t)p->nt * p->nt);
+  L.efflabel = take((size_t)p->nt * p->nt);
+  L.cells = take(p->cells.size() * sizeof(int) + 4);
+  L.uext = take((size_t)p->nb * sizeof(int));
+  L.tripof = take((size_t)p->nb * p->nb * p->nb * sizeof(int));
+  L.valid = take((size_t)p->nc);
+  L.twM = take((size_t)p->M * sizeof(float2));
+  L.twN = take((size_t)p->nc * sizeof(float2));
+  L.tnorm = take((size_t)p->ntrip * sizeof(double));
+  L.T = take((size_t)p->ntrip * sizeof(unsigned long long));
+  L.nnu = take(n2 * n2 * sizeof(long long));
+  L.cols = take(p->max_cols * sizeof(ColEntry));
+  L.ptiles = take(p->max_ptiles * sizeof(PairTile));
+  L.G = take((size_t)p->batch * p->nb * p->nc * (size_t)p->M * p->UC * sizeof(float2));
+  L.F = take((size_t)p->batch * p->nf * (size_t)p->M * p->M * sizeof(float));
+  const bool split = p->d.precision == BS_PREC_SPLIT_BF16;
+  L.Fhi = take(split ? (size_t)p->batch * p->nf * (size_t)p->M * p->M * 2 : 0);
+  L.Flo = take(split ? (size_t)p->batch * p->nf * (size_t)p->M * p->M * 2 : 0);
+  L.dsum = take((size_t)p->batch * p->ntrip * n2 * n2 * sizeof(double));
+  L.tmp3d = take((size_t)p->batch * p->ntrip * (size_t)p->nc * p->nc * sizeof(float2));
+  L.herm = take(2 * sizeof(float));
+  L.total = o;
+}
+
+bs_status ensure_workspace(bs_plan p) {
+  if (p->ws) return BS_OK;
+  void *w = nullptr;
+  cudaError_t e = cudaMalloc(&w, p->L.total);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(p, BS_ERR_OOM, "workspace allocation of " + std::to_string(p->L.total) +
+                                   " bytes failed: " + cudaGetErrorString(e));
+  }
+  p->ws = static_cast<unsigned char *>(w);
+  p->ws_owned = true;
+  return BS_OK;
+}
+
+// Upload the constant tables into a fresh workspace.
+bs_status init_tables(bs_plan p, cudaStream_t s) {
+  const WsLayout &L = p->L;
+  BS_CUDA(cudaMemcpyAsync(p->at<int8_t>(L.label), p->label.data(), p->label.size(),
+                          cudaMemcpyHostToDevice, s));
+  if (!p->cells.empty())
+    BS_CUDA(cudaMemcpyAsync(p->at<int>(L.cells), p->cells.data(), p->cells.size() * sizeof(int),
+                            cudaMemcpyHostToDevice, s));
+  BS_CUDA(cudaMemcpyAsync(p->at<int>(L.uext), p->uext.data(), p->uext.size() * sizeof(int),
+                          cudaMemcpyHostToDevice, s));
+  BS_CUDA(cudaMemcpyAsync(p->at<int>(L.tripof), p->trip_of.data(),
+                          p->trip_of.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  std::vector<float2> twm = twiddles(p->M), twn = twiddles(p->nc);
+  BS_CUDA(cudaMemcpyAsync(p->at<float2>(L.twM), twm.data(), twm.size() * sizeof(float2),
+                          cudaMemcpyHostToDevice, s));
+  BS_CUDA(cudaMemcpyAsync(p->at<float2>(L.twN), twn.data(), twn.size() * sizeof(float2),
+                          cudaMemcpyHostToDevice, s));
+  BS_CUDA(cudaStreamSynchronize(s));  // host vectors above are temporaries
+  return BS_OK;
+}
+
+bs_status prepare(bs_plan p, cudaStream_t s) {
+  if (p->sticky) return fail(p, BS_ERR_STATE, "plan has a sticky CUDA error: " + p->err);
+  BS_CUDA(cudaSetDevice(p->device));
+  if (!p->ws) {
+    bs_status st = ensure_workspace(p);
+    if (st != BS_OK) return st;
+    st = init_tables(p, s);
+    if (st != BS_OK) return st;
+  }
+  return BS_OK;
+}
+
+// Triangle counts on the device with the given label table; T and tnorm on host.
+bs_status run_counts(bs_plan p, const int8_t *lab_dev, cudaStream_t s) {
+  unsigned long long *Td = p->at<unsigned long long>(p->L.T);
+  BS_CUDA(cudaMemsetAsync(Td, 0, (size_t)p->ntrip * sizeof(unsigned long long), s));
+  BS_CUDA(launch_counts(p->nt, p->nb, lab_dev, p->at<int>(p->L.cells), (int)p->cells.size(),
+                        p->at<int>(p->L.tripof), Td, s));
+  std::vector<unsigned long long> th(p->ntrip);
+  BS_CUDA(cudaMemcpyAsync(th.data(), Td, th.size() * sizeof(unsigned long long),
+                          cudaMemcpyDeviceToHost, s));
+  BS_CUDA(cudaStreamSynchronize(s));
+  p->T.assign(th.begin(), th.end());
+  p->tnorm.resize(p->ntrip);
+  const double m2 = (double)p->M * (double)p->M;
+  for (int t = 0; t < p->ntrip; ++t)
+    p->tnorm[t] = p->T[t] > 0 ? 1.0 / (p->normA * m2 * (double)p->T[t]) : 0.0;
+  BS_CUDA(cudaMemcpyAsync(p->at<double>(p->L.tnorm), p->tnorm.data(), p->ntrip * sizeof(double),
+                          cudaMemcpyHostToDevice, s));
+  BS_CUDA(cudaStreamSynchronize(s));
+  p->counts_ready = true;
+  return BS_OK;
+}
+
+// Unfolded sampling of a channel block: cnt[d1][d2] += #{nu3 in B3 : nu3+d1 in
+// B1, nu3+d2 in B2, all three valid}, with 64-bit words of channel bits.
+void accumulate_block_nnu(bs_plan p, const int *blk) {
+  const int nc = p->nc, n2 = 2 * nc - 1;
+  const int W = (nc + 63) / 64;
+  auto bits = [&](int lo, int hi) {
+    std::vector<uint64_t> b(W, 0);
+    for (int c = lo; c < hi; ++c)
+      if (p->valid[c]) b[c >> 6] |= uint64_t(1) << (c & 63);
+    return b;
+  };
+  const std::vector<uint64_t> b1 = bits(blk[0], blk[1]), b2 = bits(blk[2], blk[3]),
+                              b3 = bits(blk[4], blk[5]);
+  // shifted(src, d)[nu3] = src[nu3 + d]
+  auto shifted = [&](const std::vector<uint64_t> &src, int d, uint64_t *out) {
+    for (int w = 0; w < W; ++w) {
+      const long long s0 = (long long)w * 64 + d;  // source bit of out bit 0 of word w
+      uint64_t v = 0;
+      const long long q = s0 >= 0 ? s0 / 64 : -((-s0 + 63) / 64);
+      const int r = (int)(s0 - q * 64);
+      auto word = [&](long long k) -> uint64_t { return (k >= 0 && k < W) ? src[k] : 0; };
+      if (r == 0)
+        v = word(q);
+      else
+        v = (word(q) >> r) | (word(q + 1) << (64 - r));
+      out[w] = v;
+    }
+  };
+  // reachable separations: d = nu - nu3 with nu in [lo, hi), nu3 in [blk[4], blk[5])
+  const int d1lo = std::max(-(nc - 1), blk[0] - blk[5] + 1), d1hi = std::min(nc - 1, blk[1] - 1 - blk[4]);
+  const int d2lo = std::max(-(nc - 1), blk[2] - blk[5] + 1), d2hi = std::min(nc - 1, blk[3] - 1 - blk[4]);
+  if (d1lo > d1hi || d2lo > d2hi) return;
+  std::vector<uint64_t> s2((size_t)n2 * W), p1(W);
+  for (int d2 = d2lo; d2 <= d2hi; ++d2) shifted(b2, d2, &s2[(size_t)(d2 + nc - 1) * W]);
+  for (int d1 = d1lo; d1 <= d1hi; ++d1) {
+    shifted(b1, d1, p1.data());
+    bool any = false;
+    for (int w = 0; w < W; ++w) {
+      p1[w] &= b3[w];
+      any |= p1[w] != 0;
+    }
+    if (!any) continue;
+    long long *row = &p->nnu[(size_t)(d1 + nc - 1) * n2];
+    for (int d2i = d2lo + nc - 1; d2i <= d2hi + nc - 1; ++d2i) {
+      const uint64_t *q = &s2[(size_t)d2i * W];
+      long long c = 0;
+      for (int w = 0; w < W; ++w) c += __builtin_popcountll(p1[w] & q[w]);
+      row[d2i] += c;
+    }
+  }
+  p->nnu_dirty = true;
+}
+
+bs_status upload_nnu(bs_plan p, cudaStream_t s) {
+  if (!p->nnu_dirty) return BS_OK;
+  BS_CUDA(cudaMemcpyAsync(p->at<long long>(p->L.nnu), p->nnu.data(),
+                          p->nnu.size() * sizeof(long long), cudaMemcpyHostToDevice, s));
+  BS_CUDA(cudaStreamSynchronize(s));
+  p->nnu_dirty = false;
+  return BS_OK;
+}
+
+bs_status delta_reset(bs_plan p, cudaStream_t s) {
+  std::fill(p->nnu.begin(), p->nnu.end(), 0LL);
+  p->nnu_dirty = true;
+  const size_t n2 = (size_t)(2 * p->nc - 1);
+  BS_CUDA(cudaMemsetAsync(p->at<double>(p->L.dsum), 0,
+                          (size_t)p->batch * p->ntrip * n2 * n2 * sizeof(double), s));
+  return BS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bs_abi_version(void) { return BS_ABI_VERSION; }
+
+const char *bs_last_error(bs_plan plan) {
+  return plan ? plan->err.c_str() : g_create_error.c_str();
+}
+
+bs_status bs_plan_create(const bs_plan_desc *desc, bs_plan *out) {
+  if (!desc || !out) return fail(nullptr, BS_ERR_ARG, "desc and out must not be NULL");
+  *out = nullptr;
+  const bs_plan_desc &d = *desc;
+  if (d.nt < 8 || d.nt > 1024 || (d.nt & 1))
+    return fail(nullptr, BS_ERR_ARG, "nt must be even and in [8, 1024]");
+  if (d.nchan < 1 || d.nchan > 4096) return fail(nullptr, BS_ERR_ARG, "nchan must be in [1, 4096]");
+  if (d.nbins < 1 || d.nbins > 32) return fail(nullptr, BS_ERR_ARG, "nbins must be in [1, 32]");
+  if (!d.bin_edges) return fail(nullptr, BS_ERR_ARG, "bin_edges must not be NULL");
+  if (d.batch < 1) return fail(nullptr, BS_ERR_ARG, "batch must be >= 1");
+  if (d.precision != BS_PREC_FP32 && d.precision != BS_PREC_SPLIT_BF16)
+    return fail(nullptr, BS_ERR_ARG, "unknown precision");
+  for (int m = 0; m <= d.nbins; ++m)
+    if (!std::isfinite(d.bin_edges[m]) || d.bin_edges[m] < 0 ||
+        (m > 0 && !(d.bin_edges[m] > d.bin_edges[m - 1])))
+      return fail(nullptr, BS_ERR_ARG, "bin_edges must be finite, >= 0 and strictly ascending");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return fail(nullptr, BS_ERR_NO_DEVICE, "no CUDA device is available");
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(nullptr, BS_ERR_NO_DEVICE, "cannot query the CUDA device");
+  }
+  if (!(prop.major == 10 && prop.minor == 3))
+    return fail(nullptr, BS_ERR_NO_DEVICE,
+                "libbs is built for sm_103a (GB300); device is sm_" + std::to_string(prop.major) +
+                    std::to_string(prop.minor));
+
+  bs_plan p = new bs_plan_s();
+  p->d = d;
+  p->device = dev;
+  p->nt = d.nt;
+  p->nc = d.nchan;
+  p->nb = d.nbins;
+  p->batch = d.batch;
+  p->edges.assign(d.bin_edges, d.bin_edges + d.nbins + 1);
+  p->d.bin_edges = nullptr;
+  p->normA = d.norm_A > 0 ? d.norm_A : 1.0;
+  const double r = d.r > 0 ? d.r : 1.0, rp = d.rprime > 0 ? d.rprime : 1.0,
+               dnu = d.dnu_c > 0 ? d.dnu_c : 1.0;
+  p->scale3d = (r * r * rp * dnu) * (r * r * rp * dnu);
+
+  // ring labels: e_m <= |U| < e_{m+1}, |U|^2 (exact integer) against e^2 (FP64)
+  const int nt = p->nt, h = nt / 2;
+  p->label.assign((size_t)nt * nt, -1);
+  p->uext.assign(p->nb, 0);
+  int cmax = 0;
+  std::vector<double> e2(p->nb + 1);
+  for (int m = 0; m <= p->nb; ++m) e2[m] = p->edges[m] * p->edges[m];
+  for (int iv = 1; iv < nt; ++iv)
+    for (int iu = 1; iu < nt; ++iu) {
+      const int u = iu - h, v = iv - h;
+      if (u == 0 && v == 0) continue;
+      const double q = (double)((long long)u * u + (long long)v * v);
+      int ring = -1;
+      for (int m = 0; m < p->nb; ++m)
+        if (q >= e2[m] && q < e2[m + 1]) {
+          ring = m;
+          break;
+        }
+      if (ring < 0) continue;
+      p->label[(size_t)iv * nt + iu] = (int8_t)ring;
+      p->cells.push_back((u + 32768) | ((v + 32768) << 16));
+      p->uext[ring] = std::max(p->uext[ring], std::abs(u) + 1);
+      cmax = std::max(cmax, std::max(std::abs(u), std::abs(v)));
+    }
+  p->UC = 0;
+  for (int m = 0; m < p->nb; ++m) p->UC = std::max(p->UC, p->uext[m]);
+  p->UC = std::max(p->UC, 1);
+  // alias-free image side: M > 3 cmax, M % 4 == 0, smooth
+  if (d.fft_m > 0) {
+    if (d.fft_m % 4 || !factor_radices(d.fft_m, p->radM) || d.fft_m <= 3 * cmax || d.fft_m > 4096) {
+      delete p;
+      return fail(nullptr, BS_ERR_ARG,
+                  "fft_m must be a multiple of 4, a product of 2, 3, 5, at most 4096 and > 3 * " +
+                      std::to_string(cmax));
+    }
+    p->M = d.fft_m;
+  } else {
+    int m = std::max(8, 3 * cmax + 1);
+    m = (m + 3) & ~3;
+    while (!is_smooth(m)) m += 4;
+    p->M = m;
+    factor_radices(p->M, p->radM);
+  }
+  if (p->M > 4096) {
+    delete p;
+    return fail(nullptr, BS_ERR_UNSUPPORTED, "image side M above 4096");
+  }
+  if (!factor_radices(p->nc, p->radN)) p->radN.n = 0;  // direct DFT for non-smooth nchan
+  // ring triples i <= j <= l, lexicographic
+  p->trip_of.assign((size_t)p->nb * p->nb * p->nb, -1);
+  for (int i = 0; i < p->nb; ++i)
+    for (int j = i; j < p->nb; ++j)
+      for (int l = j; l < p->nb; ++l) {
+        p->trip_of[((size_t)i * p->nb + j) * p->nb + l] = (int)(p->trips.size() / 3);
+        p->trips.push_back(i);
+        p->trips.push_back(j);
+        p->trips.push_back(l);
+      }
+  p->ntrip = (int)(p->trips.size() / 3);
+  p->nf = p->nb * p->nc;
+  p->valid.assign(p->nc, 1);
+  p->nnu.assign((size_t)(2 * p->nc - 1) * (2 * p->nc - 1), 0);
+  const int npairs = p->nb * (p->nb + 1) / 2;
+  p->max_cols = (size_t)npairs * p->nb * p->nc;
+  p->max_ptiles = (size_t)npairs * ((size_t)p->nb * p->nc / 128 + 1);
+  compute_layout(p);
+  *out = p;
+  return BS_OK;
+}
+
+bs_status bs_plan_destroy(bs_plan p) {
+  if (!p) return BS_OK;
+  if (p->ws && p->ws_owned) {
+    cudaSetDevice(p->device);
+    cudaFree(p->ws);
+  }
+  delete p;
+  return BS_OK;
+}
+
+bs_status bs_plan_info(bs_plan p, int64_t *info, int n) {
+  if (!p || !info || n < 0) return fail(p, BS_ERR_ARG, "bad arguments");
+  int64_t v[6] = {p->M, p->ntrip, p->nf, (int64_t)p->L.total, p->UC, -1};
+  if (p->counts_ready) {
+    int64_t c = 0;
+    for (long long t : p->T) c += t > 0;
+    v[5] = c;
+  }
+  for (int k = 0; k < n && k < 6; ++k) info[k] = v[k];
+  return BS_OK;
+}
+
+bs_status bs_plan_set_workspace(bs_plan p, void *ws, size_t bytes) {
+  if (!p) return BS_ERR_ARG;
+  if (p->ws) return fail(p, BS_ERR_STATE, "workspace already in place");
+  if (!ws || bytes < p->L.total || (reinterpret_cast<uintptr_t>(ws) & 255))
+    return fail(p, BS_ERR_ARG, "workspace must be 256-byte aligned and at least " +
+                                   std::to_string(p->L.total) + " bytes");
+  p->ws = static_cast<unsigned char *>(ws);
+  p->ws_owned = false;
+  cudaStream_t s = nullptr;
+  cudaSetDevice(p->device);
+  return init_tables(p, s);
+}
+
+bs_status bs_grid_load(bs_plan p, const void *vis, const float *ngrid, const uint8_t *flags,
+                       void *stream) {
+  if (!p) return BS_ERR_ARG;
+  if (!vis || (reinterpret_cast<uintptr_t>(vis) & 7))
+    return fail(p, BS_ERR_ARG, "vis_dev must be a non-NULL 8-byte aligned device pointer");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  bs_status st = prepare(p, s);
+  if (st != BS_OK) return st;
+  const WsLayout &L = p->L;
+  for (int c = 0; c < p->nc; ++c) p->valid[c] = flags ? (flags[c] ? 0 : 1) : 1;
+  BS_CUDA(cudaMemcpyAsync(p->at<uint8_t>(L.valid), p->valid.data(), p->nc,
+                          cudaMemcpyHostToDevice, s));
+  const int8_t *lab = p->at<int8_t>(L.label);
+  if (ngrid) {
+    BS_CUDA(launch_effective_label(p->nt * p->nt, lab, ngrid, p->at<int8_t>(L.efflabel), s));
+    st = run_counts(p, p->at<int8_t>(L.efflabel), s);
+    if (st != BS_OK) return st;
+    p->counts_default = false;
+  } else if (!p->counts_ready || !p->counts_default) {
+    st = run_counts(p, lab, s);
+    if (st != BS_OK) return st;
+    p->counts_default = true;
+  }
+  GridGeom g{p->nt, p->nc, p->nb, p->M, p->UC, p->batch};
+  BS_CUDA(launch_colpass(g, static_cast<const float2 *>(vis), ngrid, p->at<uint8_t>(L.valid), lab,
+                         p->at<int>(L.uext), p->at<float2>(L.twM), p->radM, p->at<float2>(L.G),
+                         s));
+  const bool split = p->d.precision == BS_PREC_SPLIT_BF16;
+  BS_CUDA(launch_rowpass(g, p->at<float2>(L.G), p->at<uint8_t>(L.valid), p->at<int>(L.uext),
+                         p->at<float2>(L.twM), p->radM, p->at<float>(L.F),
+                         split ? p->at<uint16_t>(L.Fhi) : nullptr,
+                         split ? p->at<uint16_t>(L.Flo) : nullptr, s));
+  st = delta_reset(p, s);
+  if (st != BS_OK) return st;
+  p->loaded = true;
+  return BS_OK;
+}
+
+bs_status bs_counts(bs_plan p, int64_t *tri, int64_t *nnu_host) {
+  if (!p) return BS_ERR_ARG;
+  if (p->sticky) return fail(p, BS_ERR_STATE, "plan has a sticky CUDA error: " + p->err);
+  if (!p->counts_ready) {
+    cudaStream_t s = nullptr;
+    bs_status st = prepare(p, s);
+    if (st != BS_OK) return st;
+    st = run_counts(p, p->at<int8_t>(p->L.label), s);
+    if (st != BS_OK) return st;
+    p->counts_default = true;
+  }
+  if (tri)
+    for (int t = 0; t < p->ntrip; ++t) tri[t] = p->T[t];
+  if (nnu_host) {
+    const int nc = p->nc, n2 = 2 * nc - 1;
+    for (int i1 = 0; i1 < n2; ++i1)
+      for (int i2 = 0; i2 < n2; ++i2) {
+        const int j1 = n2 - 1 - i1, j2 = n2 - 1 - i2;
+        long long c = p->nnu[(size_t)i1 * n2 + i2];
+        if (j1 != i1 || j2 != i2) c += p->nnu[(size_t)j1 * n2 + j2];
+        nnu_host[(size_t)i1 * n2 + i2] = c;
+      }
+  }
+  return BS_OK;
+}
+
+bs_status bs_mabs(bs_plan p, const int32_t *block, double *out_full, int accumulate, void *stream) {
+  if (!p) return BS_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!p->loaded) return fail(p, BS_ERR_STATE, "bs_mabs before bs_grid_load");
+  bs_status st = prepare(p, s);
+  if (st != BS_OK) return st;
+  const int nc = p->nc;
+  int blk[6] = {0, nc, 0, nc, 0, nc};
+  if (block)
+    for (int k = 0; k < 6; ++k) blk[k] = block[k];
+  for (int k = 0; k < 6; k += 2)
+    if (blk[k] < 0 || blk[k + 1] > nc || blk[k] > blk[k + 1])
+      return fail(p, BS_ERR_ARG, "channel block out of range");
+  if (p->d.precision != BS_PREC_FP32 && p->d.precision != BS_PREC_SPLIT_BF16)
+    return fail(p, BS_ERR_UNSUPPORTED, "precision");
+  if (!out_full && !accumulate) return BS_OK;
+  const WsLayout &L = p->L;
+  const long long full_bstride = (long long)p->ntrip * nc * nc * nc;
+  if (out_full) BS_CUDA(launch_full_fill(out_full, full_bstride, p->batch, p->ntrip, nc, blk, 0.0, s));
+  // work list: ring pairs (i <= j) x column tiles over (l, nu3), T(i,j,l) > 0, nu3 valid
+  p->h_cols.clear();
+  p->h_ptiles.clear();
+  const int nb = p->nb;
+  for (int i = 0; i < nb; ++i)
+    for (int j = i; j < nb; ++j) {
+      const int off = (int)p->h_cols.size();
+      for (int l = j; l < nb; ++l) {
+        const int t = p->trip_of[((size_t)i * nb + j) * nb + l];
+        if (p->T[t] <= 0) continue;
+        for (int n3 = blk[4]; n3 < blk[5]; ++n3)
+          if (p->valid[n3]) p->h_cols.push_back(ColEntry{l * nc + n3, t, n3, 0});
+      }
+      const int ncol = (int)p->h_cols.size() - off;
+      for (int c0 = 0; c0 < ncol; c0 += 128) p->h_ptiles.push_back(PairTile{i, j, off, ncol, c0, {0, 0, 0}});
+    }
+  const int n_r1 = (blk[1] - blk[0] + 15) / 16, n_r2 = (blk[3] - blk[2] + 7) / 8;
+  const int npt = (int)p->h_ptiles.size();
+  if (npt > 0 && n_r1 > 0 && n_r2 > 0) {
+    if (npt > 65535) return fail(p, BS_ERR_UNSUPPORTED, "too many column tiles in one block");
+    BS_CUDA(cudaMemcpyAsync(p->at<ColEntry>(L.cols), p->h_cols.data(),
+                            p->h_cols.size() * sizeof(ColEntry), cudaMemcpyHostToDevice, s));
+    BS_CUDA(cudaMemcpyAsync(p->at<PairTile>(L.ptiles), p->h_ptiles.data(),
+                            p->h_ptiles.size() * sizeof(PairTile), cudaMemcpyHostToDevice, s));
+    ContractArgs a{};
+    a.F = p->at<float>(L.F);
+    a.fstride = (long long)p->M * p->M;
+    a.bstride = (long long)p->nf * p->M * p->M;
+    a.M2 = p->M * p->M;
+    a.nc = nc;
+    a.cols = p->at<ColEntry>(L.cols);
+    a.ptiles = p->at<PairTile>(L.ptiles);
+    a.nu1_lo = blk[0];
+    a.nu1_hi = blk[1];
+    a.nu2_lo = blk[2];
+    a.nu2_hi = blk[3];
+    a.n_r2 = n_r2;
+    // split K until the launch covers several waves of 152 SMs
+    const long long ctas = (long long)n_r1 * n_r2 * npt * p->batch;
+    int nk = 1;
+    const int nchunks = a.M2 / 16;
+    while (ctas * nk < 4 * 152 && nk * 2 <= nchunks / 16 && nk < 64) nk *= 2;
+    while ((long long)nk * p->batch > 65535) nk /= 2;
+    a.nkseg = nk;
+    a.kseg_len = ((nchunks + nk - 1) / nk) * 16;
+    a.tnorm = p->at<double>(L.tnorm);
+    a.out_full = out_full;
+    a.full_bstride = full_bstride;
+    a.dsum = accumulate ? p->at<double>(L.dsum) : nullptr;
+    a.dsum_bstride = (long long)p->ntrip * (2 * nc - 1) * (2 * nc - 1);
+    BS_CUDA(launch_contract_simt(a, n_r1 * n_r2, npt, p->batch, s));
+  }
+  if (out_full)
+    BS_CUDA(launch_full_finalize(out_full, full_bstride, p->batch, p->ntrip, nc, blk,
+                                 p->at<uint8_t>(L.valid), p->at<double>(L.tnorm), s));
+  if (accumulate) accumulate_block_nnu(p, blk);
+  return BS_OK;
+}
+
+bs_status bs_delta_reset(bs_plan p, void *stream) {
+  if (!p) return BS_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  bs_status st = prepare(p, s);
+  if (st != BS_OK) return st;
+  return delta_reset(p, s);
+}
+
+bs_status bs_mabs_delta(bs_plan p, double *out, void *stream) {
+  if (!p || !out) return fail(p, BS_ERR_ARG, "out_dev must not be NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!p->loaded) return fail(p, BS_ERR_STATE, "bs_mabs_delta before bs_grid_load");
+  bs_status st = prepare(p, s);
+  if (st != BS_OK) return st;
+  st = upload_nnu(p, s);
+  if (st != BS_OK) return st;
+  BS_CUDA(launch_delta_norm(p->at<double>(p->L.dsum), p->at<long long>(p->L.nnu),
+                            p->at<double>(p->L.tnorm), out, p->batch, p->ntrip, p->nc, s));
+  return BS_OK;
+}
+
+bs_status bs_bs3d(bs_plan p, double *out, void *stream) {
+  if (!p || !out) return fail(p, BS_ERR_ARG, "out_dev must not be NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!p->loaded) return fail(p, BS_ERR_STATE, "bs_bs3d before bs_grid_load");
+  bs_status st = prepare(p, s);
+  if (st != BS_OK) return st;
+  st = upload_nnu(p, s);
+  if (st != BS_OK) return st;
+  BS_CUDA(launch_bs3d(p->at<double>(p->L.dsum), p->at<long long>(p->L.nnu),
+                      p->at<double>(p->L.tnorm), p->at<float2>(p->L.tmp3d), out, p->batch,
+                      p->ntrip, p->nc, p->at<float2>(p->L.twN), p->radN, p->scale3d, s));
+  return BS_OK;
+}
+
+bs_status bs_check_hermitian(bs_plan p, const void *vis, double tol, void *stream) {
+  if (!p || !vis) return fail(p, BS_ERR_ARG, "vis_dev must not be NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  bs_status st = prepare(p, s);
+  if (st != BS_OK) return st;
+  float *hm = p->at<float>(p->L.herm);
+  BS_CUDA(cudaMemsetAsync(hm, 0, 2 * sizeof(float), s));
+  BS_CUDA(launch_hermitian_check(static_cast<const float2 *>(vis), p->batch, p->nc, p->nt,
+                                 p->at<int8_t>(p->L.label), hm, hm + 1, s));
+  float h[2];
+  BS_CUDA(cudaMemcpyAsync(h, hm, sizeof(h), cudaMemcpyDeviceToHost, s));
+  BS_CUDA(cudaStreamSynchronize(s));
+  if (h[0] > tol * h[1])
+    return fail(p, BS_ERR_NOT_HERMITIAN,
+                "max |V(-U) - conj V(U)| = " + std::to_string(h[0]) + " exceeds tol * max|V| = " +
+                    std::to_string(tol * h[1]));
+  return BS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,63 @@
+"""CPU-side checks of the C-ABI library: it builds, loads, exports every
+symbol that include/bs.h declares, and refuses cleanly (no CPU fallback)
+when no sm_103a device is present.  No compute call runs here."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2506_10526_gb300 as bs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2506_10526_gb300 import build
+    build.build()
+    return bs.lib()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "bs.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(bs_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declarations_exported(lib):
+    names = _declared()
+    assert set(names) == set(bs.EXPORTS), names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_abi_version(lib):
+    assert lib.bs_abi_version() == 1
+
+
+def test_desc_validation_and_no_device(lib):
+    import torch
+    edges = (ctypes.c_double * 3)(0.0, 2.0, 4.0)
+    h = ctypes.c_void_p()
+    bad = bs.PlanDesc(7, 4, 2, edges, 0, 0, 1, 1, 1, 1, 1)  # odd nt
+    assert lib.bs_plan_create(ctypes.byref(bad), ctypes.byref(h)) == 1
+    assert b"nt" in lib.bs_last_error(None)
+    desc_edges = (ctypes.c_double * 3)(0.0, 4.0, 2.0)  # not ascending
+    bad = bs.PlanDesc(16, 4, 2, desc_edges, 0, 0, 1, 1, 1, 1, 1)
+    assert lib.bs_plan_create(ctypes.byref(bad), ctypes.byref(h)) == 1
+    good = bs.PlanDesc(16, 4, 2, edges, 0, 0, 1, 1, 1, 1, 1)
+    st = lib.bs_plan_create(ctypes.byref(good), ctypes.byref(h))
+    if not torch.cuda.is_available():
+        assert st == 2  # BS_ERR_NO_DEVICE: no CPU fallback
+        with pytest.raises(bs.BsError):
+            bs.Plan(16, 4, [0.0, 2.0, 4.0])
+    else:
+        assert st == 0
+        lib.bs_plan_destroy(h)
+
+
+def test_null_handles(lib):
+    assert lib.bs_plan_destroy(None) == 0
+    assert lib.bs_grid_load(None, None, None, None, None) == 1
+    assert lib.bs_mabs(None, None, None, 0, None) == 1

@@ -1,0 +1,215 @@
+"""GPU parity: libbs (through its C ABI) against the FP64 oracle on the same
+seeded inputs.
+
+Error measure (per estimator bin): the oracle evaluates Eq. (estimator_t)
+twice, on V and on |V|; the second gives B_abs = (1/A) sum_t |X1 X2 X3| / T,
+the size of the terms that cancel in the bin.  The kappa-normalised error
+e = |B_gpu - B_fp64| / B_abs must stay below 1e-5 for the FP32 path (the
+FP32 target; the FFTs and the contraction round at ~6e-8 relative to the
+terms, times the log2 M FFT stages and the growth of long FP32 sums).
+Counts are integers and must be bit-exact; undefined bins must coincide."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL_FP32 = 1e-5
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def _run(vis, edges, flags=None, ngrid=None, precision=0, block=None, full=True, batch_vis=None,
+         norm_A=1.0, r=1.0, rprime=1.0, dnu_c=1.0):
+    torch = _torch()
+    import paper_2506_10526_gb300 as bs
+    v = vis if batch_vis is None else batch_vis
+    if v.ndim == 3:
+        v = v[None]
+    batch, nc, nt, _ = v.shape
+    plan = bs.Plan(nt, nc, edges, precision=precision, batch=batch, norm_A=norm_A, r=r,
+                   rprime=rprime, dnu_c=dnu_c)
+    vd = torch.from_numpy(np.ascontiguousarray(v.astype(np.complex64))).cuda()
+    gd = None if ngrid is None else torch.from_numpy(ngrid.astype(np.float32)).cuda()
+    plan.grid_load(vd, ngrid=gd, chan_flags=flags)
+    out = {}
+    fd = None
+    if full:
+        fd = torch.full((batch, plan.ntrip, nc, nc, nc), 12345.0, dtype=torch.float64,
+                        device="cuda")
+    plan.mabs(block=block, out_full=fd, accumulate=True)
+    dd = torch.empty((batch, plan.ntrip, 2 * nc - 1, 2 * nc - 1), dtype=torch.float64,
+                     device="cuda")
+    plan.mabs_delta(dd)
+    bd = torch.empty((batch, plan.ntrip, nc, nc), dtype=torch.float64, device="cuda")
+    plan.bs3d(bd)
+    torch.cuda.synchronize()
+    out["full"] = None if fd is None else fd.cpu().numpy()
+    out["delta"] = dd.cpu().numpy()
+    out["bs3d"] = bd.cpu().numpy()
+    out["T"], out["nnu"] = plan.counts()
+    out["M"] = plan.M
+    plan.close()
+    return out
+
+
+def _kappa_err(got, want, babs):
+    ok = ~np.isnan(want)
+    assert np.array_equal(np.isnan(got), np.isnan(want)), "undefined bins differ"
+    return np.max(np.abs(got[ok] - want[ok]) / babs[ok]) if ok.any() else 0.0
+
+
+def _oracle(vis, edges, flags=None, ngrid=None, norm_A=1.0):
+    ref = oracle.mabs_full(vis.astype(np.complex128), edges, chan_flags=flags, ngrid=ngrid,
+                           norm_A=norm_A)
+    babs = oracle.mabs_full(np.abs(vis).astype(np.complex128), edges, chan_flags=flags,
+                            ngrid=ngrid, norm_A=norm_A)["B"].real
+    return ref, babs
+
+
+def test_three_mode_golden_gpu():
+    nt = 8
+    vis = np.zeros((1, nt, nt), np.complex64)
+    for (u, v), z in (((1, 0), 1 + 2j), ((1, 1), 0.5 - 1j), ((-2, -1), -1 + 0.25j)):
+        vis[0, v + nt // 2, u + nt // 2] = z
+        vis[0, -v + nt // 2, -u + nt // 2] = np.conj(z)
+    out = _run(vis, [1, 2, 3, 4])
+    assert out["T"][0] == 24 and out["T"][1] == 32  # (0,0,0), (0,0,1): hand counts
+    assert out["full"][0, 1, 0, 0, 0] == pytest.approx(-0.3125, abs=1e-6)
+    assert abs(out["full"][0, 0, 0, 0, 0]) < 1e-6
+
+
+@pytest.mark.parametrize("flagged", [False, True])
+def test_tiny_config_full_cube(flagged):
+    """64^2 grid, 16 channels, 8 linear rings (and the coarse-band flags):
+    every ring triple x channel triple against the oracle."""
+    nt, nc = 64, 16
+    edges = synth.edges_linear(8, 32)
+    vis = synth.sky_visibilities(nt, nc, seed=1001)
+    flags = synth.flag_mask_coarse_band(nc) if flagged else None
+    out = _run(vis, edges, flags=flags)
+    ref, babs = _oracle(vis, edges, flags)
+    np.testing.assert_array_equal(out["T"], ref["T"])
+    e = _kappa_err(out["full"][0], ref["B"].real, babs)
+    assert e < TOL_FP32, e
+    bbar, cnt = oracle.collapse_fold(ref["B"].real)
+    bbar_abs, _ = oracle.collapse_fold(babs)
+    k0 = int(np.argmax(ref["T"] > 0))
+    np.testing.assert_array_equal(out["nnu"], cnt[k0])
+    e = _kappa_err(out["delta"][0], bbar, bbar_abs)
+    assert e < TOL_FP32, e
+    b3 = oracle.delay_dft(bbar, nc).real
+    b3_scale = np.abs(oracle.delay_dft(bbar_abs, nc)).max(axis=(-1, -2), keepdims=True)
+    keep = ref["T"] > 0
+    err3 = np.abs(out["bs3d"][0][keep] - b3[keep]) / b3_scale[keep]
+    assert err3.max() < TOL_FP32, err3.max()
+
+
+def test_ragged_sizes_occupancy_and_blocks():
+    """Non-tile-multiple sizes: nt = 40, 11 channels (non-smooth: direct DFT in
+    the delay transform), log rings, empty cells with N_g in {0, 1, 2, 3},
+    one flagged channel, and three overlapping channel blocks."""
+    nt, nc = 40, 11
+    edges = synth.edges_log(5, 1.5, 19.0)
+    vis = synth.sky_visibilities(nt, nc, seed=42)
+    r = synth.rng(43)
+    ngrid = r.integers(0, 4, size=(nt, nt)).astype(np.float32)
+    # same sampling at U and -U: cell (iv, iu) pairs with (nt - iv, nt - iu)
+    ngrid[1:, 1:] = np.maximum(ngrid[1:, 1:], ngrid[1:, 1:][::-1, ::-1])
+    flags = np.zeros(nc, np.uint8)
+    flags[4] = 1
+    ref, babs = _oracle(vis, edges, flags, ngrid=ngrid)
+    occ = oracle.ring_labels(nt, edges, occupancy=ngrid > 0)
+    torch = _torch()
+    import paper_2506_10526_gb300 as bs
+    plan = bs.Plan(nt, nc, edges)
+    plan.grid_load(torch.from_numpy(vis[None]).cuda(), ngrid=torch.from_numpy(ngrid).cuda(),
+                   chan_flags=flags)
+    full = torch.full((1, plan.ntrip, nc, nc, nc), np.nan, dtype=torch.float64, device="cuda")
+    for blk in [(0, 5, 0, 11, 0, 11), (5, 11, 0, 7, 0, 11), (5, 11, 7, 11, 0, 11)]:
+        plan.mabs(block=blk, out_full=full, accumulate=True)
+    dd = torch.empty((1, plan.ntrip, 2 * nc - 1, 2 * nc - 1), dtype=torch.float64, device="cuda")
+    plan.mabs_delta(dd)
+    bd = torch.empty((1, plan.ntrip, nc, nc), dtype=torch.float64, device="cuda")
+    plan.bs3d(bd)
+    tri, nnu = plan.counts()
+    torch.cuda.synchronize()
+    Tocc = oracle.counts(nt, edges, occupancy=ngrid > 0)
+    trips = oracle.ring_triples(len(edges) - 1)
+    np.testing.assert_array_equal(tri, [Tocc[t] for t in trips])
+    assert occ is not None
+    e = _kappa_err(full[0].cpu().numpy(), ref["B"].real, babs)
+    assert e < TOL_FP32, e
+    bbar, cnt = oracle.collapse_fold(ref["B"].real)
+    bbar_abs, _ = oracle.collapse_fold(babs)
+    np.testing.assert_array_equal(nnu, cnt[int(np.argmax(ref["T"] > 0))])
+    e = _kappa_err(dd[0].cpu().numpy(), bbar, bbar_abs)
+    assert e < TOL_FP32, e
+    b3 = oracle.delay_dft(bbar, nc).real
+    b3_scale = np.abs(oracle.delay_dft(bbar_abs, nc)).max(axis=(-1, -2), keepdims=True)
+    keep = ref["T"] > 0
+    err3 = np.abs(bd[0].cpu().numpy()[keep] - b3[keep]) / b3_scale[keep]
+    assert err3.max() < TOL_FP32, err3.max()
+    plan.close()
+
+
+def test_batch_and_scales():
+    """Two realisations in one plan; A, r, r', dnu_c scale factors."""
+    nt, nc = 32, 8
+    edges = synth.edges_linear(4, 16)
+    v = np.stack([synth.sky_visibilities(nt, nc, seed=s) for s in (3, 4)])
+    A, r, rp, dnu = 2.0, 1.5, 0.8, 0.25
+    out = _run(None, edges, batch_vis=v, norm_A=A, r=r, rprime=rp, dnu_c=dnu)
+    for b in range(2):
+        ref, babs = _oracle(v[b], edges, norm_A=A)
+        e = _kappa_err(out["full"][b], ref["B"].real, babs)
+        assert e < TOL_FP32, (b, e)
+        bbar, _ = oracle.collapse_fold(ref["B"].real)
+        b3 = oracle.delay_dft(bbar, nc, r, rp, dnu).real
+        b3_scale = np.abs(oracle.delay_dft(oracle.collapse_fold(babs)[0], nc, r, rp, dnu)).max()
+        keep = ref["T"] > 0
+        assert np.abs(out["bs3d"][b][keep] - b3[keep]).max() / b3_scale < TOL_FP32
+
+
+def test_degenerate_cases():
+    """One channel (the single-frequency ABS special case), a single ring,
+    an empty ring, every channel flagged, and the constant field (B = 1/A)."""
+    nt = 16
+    vis = synth.sky_visibilities(nt, 1, seed=9)
+    edges = [1.0, 3.0, 3.1, 7.0]  # ring 1 holds no cell
+    out = _run(vis, edges)
+    ref, babs = _oracle(vis, edges)
+    assert _kappa_err(out["full"][0], ref["B"].real, babs) < TOL_FP32
+    out = _run(vis, [1.0, 7.0])
+    ref, babs = _oracle(vis, [1.0, 7.0])
+    assert _kappa_err(out["full"][0], ref["B"].real, babs) < TOL_FP32
+    vis4 = synth.sky_visibilities(nt, 4, seed=10)
+    out = _run(vis4, [1.0, 4.0, 7.0], flags=np.ones(4, np.uint8))
+    assert np.all(np.isnan(out["full"])) and np.all(np.isnan(out["delta"]))
+    assert np.all(out["bs3d"] == 0)
+    ones = np.ones((3, nt, nt), np.complex64)
+    out = _run(ones, [1.0, 4.0, 7.0], norm_A=4.0)
+    f = out["full"][0]
+    ok = ~np.isnan(f)
+    np.testing.assert_allclose(f[ok], 0.25, rtol=1e-5)
+
+
+def test_hermitian_check():
+    torch = _torch()
+    import paper_2506_10526_gb300 as bs
+    nt, nc = 16, 2
+    vis = synth.sky_visibilities(nt, nc, seed=1)
+    plan = bs.Plan(nt, nc, [1.0, 4.0, 7.0])
+    v = torch.from_numpy(vis[None]).cuda()
+    assert plan.check_hermitian(v, 1e-5)
+    bad = vis.copy()
+    bad[0, nt // 2 + 2, nt // 2 + 1] += 5.0
+    assert not plan.check_hermitian(torch.from_numpy(bad[None]).cuda(), 1e-5)
+    plan.close()
