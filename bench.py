@@ -45,6 +45,9 @@ WORKLOADS = {
     "mwa": dict(nt=256, nc=768, nb=20, edges=("log", 4.41, 128.0), block=64,
                 desc="MWA-like: 256^2 uv grid, 768 channels (30.72 MHz at 40 kHz), 20 log rings "
                      "|U| in [4.41, 128), no flagging"),
+    "small": dict(nt=128, nc=128, nb=12, edges=("log", 2.2, 64.0), block=32,
+                  desc="profiling case: 128^2 uv grid, 128 channels, 12 log rings |U| in "
+                       "[2.2, 64), no flagging"),
     "tiny": dict(nt=64, nc=16, nb=8, edges=("linear", 0.0, 32.0), block=16,
                  desc="tiny: 64^2 uv grid, 16 channels, 8 linear rings |U| < 32, no flagging"),
 }
