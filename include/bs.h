@@ -186,6 +186,31 @@ bs_status bs_bs3d(bs_plan plan, double *out_dev, void *cuda_stream);
  * Returns BS_OK or BS_ERR_NOT_HERMITIAN. */
 bs_status bs_check_hermitian(bs_plan plan, const void *vis_dev, double tol, void *cuda_stream);
 
+/* Closed-triangle counts T(i,j,l) without any device allocation.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc (a pipeline bound to its own pre-allocated memory
+ * pool, or a host that must not touch the CUDA allocator while it shares the
+ * device).  It computes the same counts as bs_counts -- ordered closed
+ * triangles U_g1 + U_g2 + U_g3 = 0 with U_gk in the listed rings, empty cells
+ * excluded -- with no plan: its scratch (ring labels, binned-cell list,
+ * ring-triple table) is a fixed static device array of 5,374,208 bytes that
+ * every device loading libbs holds until the process exits.
+ *  nt              uv grid side, even, 8..1024 (larger: BS_ERR_ARG)
+ *  nbins           rings, 1..32 (larger: BS_ERR_ARG)
+ *  bin_edges_host  nbins+1 strictly ascending edges (|U| grid units)
+ *  ngrid_dev       float [nt][nt] or NULL, as in bs_grid_load
+ *  tri_dev         int64 [nbins(nbins+1)(nbins+2)/6] device output, ring
+ *                  triples i <= j <= l in lexicographic order; overwritten
+ * Runs on the current device, asynchronously on cuda_stream.  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  The array is shared by
+ * all calls and keeps the last call's contents (the call clears what must
+ * start at zero): calls that overlap on the GPU, from any stream or thread,
+ * race and must be serialised by the caller.
+ * Errors: BS_ERR_ARG, BS_ERR_NO_DEVICE, BS_ERR_CUDA. */
+bs_status bs_counts_noalloc(int nt, int nbins, const double *bin_edges_host,
+                            const float *ngrid_dev, int64_t *tri_dev, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

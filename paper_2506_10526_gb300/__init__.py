@@ -30,7 +30,8 @@ PREC_SPLIT_BF16 = 1
 # every symbol declared in include/bs.h
 EXPORTS = ("bs_abi_version", "bs_plan_create", "bs_plan_destroy", "bs_last_error",
            "bs_plan_info", "bs_plan_set_workspace", "bs_grid_load", "bs_counts", "bs_mabs",
-           "bs_delta_reset", "bs_mabs_delta", "bs_bs3d", "bs_check_hermitian")
+           "bs_delta_reset", "bs_mabs_delta", "bs_bs3d", "bs_check_hermitian",
+           "bs_counts_noalloc")
 
 _lib = None
 _lock = threading.Lock()
@@ -74,6 +75,7 @@ def lib() -> ctypes.CDLL:
             L.bs_mabs_delta.argtypes = [P, P, P]
             L.bs_bs3d.argtypes = [P, P, P]
             L.bs_check_hermitian.argtypes = [P, P, D, P]
+            L.bs_counts_noalloc.argtypes = [I, I, P, P, P, P]
             for name in EXPORTS:
                 if name not in ("bs_abi_version", "bs_last_error"):
                     getattr(L, name).restype = I
@@ -200,3 +202,15 @@ class Plan:
             return False
         self._check(st)
         return True
+
+
+def counts_noalloc(nt: int, edges, tri_out, ngrid=None, stream=None):
+    """bs_counts_noalloc: closed-triangle counts into a caller-owned int64 CUDA
+    tensor of nbins(nbins+1)(nbins+2)/6 entries; allocates no device memory."""
+    import numpy as np
+    e = np.ascontiguousarray(np.asarray(edges, dtype=np.float64))
+    st = lib().bs_counts_noalloc(int(nt), int(e.size - 1), e.ctypes.data_as(ctypes.c_void_p),
+                                 _dptr(ngrid), _dptr(tri_out), _stream_ptr(stream))
+    if st != BS_OK:
+        raise BsError(st, "bs_counts_noalloc failed (sizes beyond nt <= 1024, nbins <= 32 are "
+                          "rejected)")
