@@ -58,6 +58,35 @@ struct ContractArgs {
   long long dsum_bstride;  // ntrip*(2nc-1)^2
 };
 
+// A tensor-core contraction tile: ring pair, pair rectangle origin, a
+// 128-entry window of the pair's column list, K segment.
+struct TcTile {
+  int ri, rj;
+  int nu1_0, nu2_0;
+  int col_off, ncol, col0;
+  int kseg;
+};
+
+struct TcArgs {
+  const float *F;          // FP32 fields (pair operand source)
+  long long fstride;       // M*M
+  long long bstride;       // nf*M*M
+  int nf, batch, M2, Kpad, nc;
+  const ColEntry *cols;    // per ring pair: runs of fields (l, nu3), padded to multiples of 8
+  const TcTile *tiles;
+  int ntiles;
+  int nu1_hi, nu2_hi;
+  int kseg_len;
+  const double *tnorm;
+  double *out_full;
+  long long full_bstride;
+  double *dsum;
+  long long dsum_bstride;
+  int *err;                // device error word: 1 = a bounded wait gave up
+  long long wait_limit_ns;
+  int stall_test;          // failure injection: the MMA thread waits on a barrier nobody arrives at
+};
+
 // ---- kernels / launchers (each returns cudaGetLastError after launch) ----
 cudaError_t launch_colpass(const GridGeom &g, const float2 *vis, const float *ngrid,
                            const uint8_t *valid, const int8_t *label, const int *uext,
@@ -83,6 +112,10 @@ cudaError_t launch_bs3d(const double *dsum, const long long *nnu, const double *
                         float2 *tmp, double *out, int batch, int ntrip, int nc,
                         const float2 *twN, const Radices &radN, double scale,
                         cudaStream_t s);
+int tc_smem_bytes();
+cudaError_t launch_contract_tc(const struct CUtensorMap_st &map_hi,
+                               const struct CUtensorMap_st &map_lo, const TcArgs &a, int nsm,
+                               cudaStream_t s);
 cudaError_t launch_hermitian_check(const float2 *vis, int batch, int nc, int nt,
                                    const int8_t *label, float *maxdiff, float *maxabs,
                                    cudaStream_t s);

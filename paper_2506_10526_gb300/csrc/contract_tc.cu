@@ -1,0 +1,553 @@
+// Triple contraction of Eq. (estimator_t) on the 5th-generation tensor cores
+// (tcgen05, sm_103a), split-BF16 precision:
+//
+//   S(l nu3; i nu1, j nu2) = sum_x F_{l,nu3}(x) * P_{nu1 nu2}(x),
+//   P(x) = F_{i,nu1}(x) F_{j,nu2}(x)      (pair product, FP32)
+//
+// Each FP32 operand is split into BF16 hi + lo (hi = round(v),
+// lo = round(v - hi)); three products hi.hi + hi.lo + lo.hi accumulate in
+// FP32 in tensor memory (the lo.lo term is below the BF16 split's own error).
+//
+// Tile (one CTA per SM, persistent over a static tile list):
+//   A = 128 fields (l, nu3) of the third ring          -> TMEM lanes
+//   B = 512 channel pairs: nu1 in 32 x nu2 in 16        -> 2 x 256 TMEM columns
+//   K = image pixels in chunks of 32 (64-byte rows, 64B swizzle, K-major)
+// A hi/lo come from the field arrays the row pass writes, by TMA in boxes of
+// 8 fields x 32 pixels.  B hi/lo are made on the fly: 8 producer warps load
+// the FP32 rows of F_i and F_j, multiply, split and store them in the same
+// swizzled layout.  One thread issues 12 MMAs (M128 N256 K16) per stage.
+// Two pipeline stages; mbarriers hand stages between TMA, producers and MMA.
+//
+// Epilogue (the producer warps): tcgen05.ld of the 128 x 512 FP32 tile,
+// shared-memory pre-reduction keyed by (ring triple segment, nu1-nu2,
+// nu2-nu3) into the idle B buffers, then FP64 global atomics into the
+// collapse sums (and, when asked, FP64 atomics into the FULL cube).
+//
+// Every mbarrier wait is bounded by %globaltimer.  A wait that gives up sets
+// the CTA's abort flag and the plan's error word; all roles then run their
+// loops to the end without waiting or issuing work, the TMA thread waits
+// (bounded) for its own copies in flight, the MMA thread for its last
+// commit, and TMEM is freed before the CTA exits.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "bs_internal.h"
+
+namespace bsi {
+
+namespace {
+
+constexpr int KC = 32;                    // BF16 elements per K chunk = 64 bytes
+constexpr int MROWS = 128;                // fields per tile
+constexpr int P1 = 32, P2 = 16;           // pair rectangle
+constexpr int NPAIR = P1 * P2;            // 512
+constexpr int STAGES = 2;
+constexpr int NPROD = 8;                  // producer / epilogue warps
+constexpr int NTHREADS = 32 * (2 + NPROD);
+constexpr int GROUP = 8;                  // fields per TMA box
+constexpr int NGROUP = MROWS / GROUP;
+constexpr int A_BYTES = MROWS * KC * 2;   // 8 KB (hi or lo)
+constexpr int B_BYTES = NPAIR * KC * 2;   // 32 KB (hi or lo)
+constexpr int RAW_ROWS = 4 + P2;          // per warp: 4 nu1 rows + 16 nu2 rows
+constexpr int RAW_STRIDE = KC + 4;        // floats (padding against bank conflicts)
+constexpr int RED_CAP = STAGES * 2 * B_BYTES / 4;  // floats in the B buffers
+
+constexpr int OFF_A = 0;
+constexpr int OFF_B = OFF_A + STAGES * 2 * A_BYTES;
+constexpr int OFF_RAW = OFF_B + STAGES * 2 * B_BYTES;
+constexpr int OFF_ROW = OFF_RAW + NPROD * RAW_ROWS * RAW_STRIDE * 4;
+constexpr int OFF_SEG = OFF_ROW + MROWS * 16;
+constexpr int MAX_SEG = 16;
+constexpr int OFF_BAR = OFF_SEG + MAX_SEG * 16;
+constexpr int NBAR = 3 * STAGES + 3;      // a_full, b_full, empty per stage; acc_full, acc_empty, stall
+constexpr int OFF_MISC = OFF_BAR + NBAR * 8;
+constexpr int SMEM_BYTES = OFF_MISC + 64 + 1024;  // + alignment slack
+
+// instruction descriptor, kind::f16: D f32, A bf16, B bf16, both K-major, N = 256, M = 128
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((256u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t gtime() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait; false on timeout or when the CTA is aborting.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit_ns,
+                                          volatile int *abort_flag) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = gtime();
+  while (true) {
+    if (mbar_try(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if ((long long)(gtime() - t0) > limit_ns) return false;
+  }
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(IDESC), "r"(acc));
+}
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   bar)
+               : "memory");
+}
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+// Shared-memory matrix descriptor: K-major, 64-byte swizzle, 8-row groups 512 B apart.
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t addr) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
+}
+// Byte offset of 16-byte chunk c (0..3) of row r in a 64B-swizzled K-major tile.
+__device__ __forceinline__ uint32_t sw64_off(int r, int c) {
+  return (uint32_t)(r * 64 + ((c ^ ((r >> 1) & 3)) << 4));
+}
+// BF16 hi/lo split of two FP32 values, packed (element 0 in the low half).
+__device__ __forceinline__ void split2(float v0, float v1, uint32_t &hi, uint32_t &lo) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+  hi = *reinterpret_cast<uint32_t *>(&h);
+  const float h0 = __uint_as_float(hi << 16), h1 = __uint_as_float(hi & 0xffff0000u);
+  __nv_bfloat162 l = __floats2bfloat162_rn(v0 - h0, v1 - h1);
+  lo = *reinterpret_cast<uint32_t *>(&l);
+}
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_contract_tc(const __grid_constant__ CUtensorMap map_hi,
+                  const __grid_constant__ CUtensorMap map_lo, TcArgs a) {
+  extern __shared__ unsigned char smem_dyn[];
+  unsigned char *sm = reinterpret_cast<unsigned char *>(
+      (reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t sA = smem_u32(sm + OFF_A), sB = smem_u32(sm + OFF_B);
+  const uint32_t sBar = smem_u32(sm + OFF_BAR);
+  auto a_full = [&](int s) { return sBar + 8 * s; };
+  auto b_full = [&](int s) { return sBar + 8 * (STAGES + s); };
+  auto empty = [&](int s) { return sBar + 8 * (2 * STAGES + s); };
+  const uint32_t acc_full = sBar + 8 * (3 * STAGES), acc_empty = acc_full + 8, stall_bar = acc_full + 16;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + OFF_MISC);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(sm + OFF_MISC + 4);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(a_full(s), 1);
+      mbar_init(b_full(s), NPROD);
+      mbar_init(empty(s), 1);
+    }
+    mbar_init(acc_full, 1);
+    mbar_init(acc_empty, NPROD);
+    mbar_init(stall_bar, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const long long limit = a.wait_limit_ns;
+  const int ntot = a.ntiles * a.batch;
+
+  auto fail = [&]() {
+    *abort_flag = 1;
+    atomicExch(a.err, 1);
+  };
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer (A)
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&map_hi) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&map_lo) : "memory");
+      uint32_t it = 0;
+      int armed[STAGES] = {0, 0};
+      for (int gt = blockIdx.x; gt < ntot; gt += gridDim.x) {
+        const TcTile t = a.tiles[gt % a.ntiles];
+        const int b = gt / a.ntiles;
+        int rowc[NGROUP];
+        for (int g = 0; g < NGROUP; ++g) {
+          const int e = t.col0 + g * GROUP;
+          int f = -1;
+          if (e < t.ncol) f = a.cols[t.col_off + e].field;
+          rowc[g] = f >= 0 ? b * a.nf + f : a.batch * a.nf;  // out of range: TMA fills zeros
+        }
+        const int k0 = t.kseg * a.kseg_len, k1 = min(a.Kpad, k0 + a.kseg_len);
+        for (int kc = k0; kc < k1; kc += KC, ++it) {
+          const int s = it & 1;
+          const uint32_t ph = (it >> 1) & 1;
+          if (*abort_flag) continue;
+          if (!mbar_wait(empty(s), ph ^ 1, limit, abort_flag)) {
+            fail();
+            continue;
+          }
+          mbar_expect_tx(a_full(s), 2 * A_BYTES);
+          ++armed[s];
+          const uint32_t dh = sA + s * 2 * A_BYTES, dl = dh + A_BYTES;
+          for (int g = 0; g < NGROUP; ++g) {
+            tma_load_2d(dh + g * GROUP * 64, &map_hi, kc, rowc[g], a_full(s));
+            tma_load_2d(dl + g * GROUP * 64, &map_lo, kc, rowc[g], a_full(s));
+          }
+        }
+      }
+      // copies in flight land before the CTA can exit
+      for (int s = 0; s < STAGES; ++s)
+        if (armed[s]) {
+          volatile int never = 0;
+          if (!mbar_wait(a_full(s), (armed[s] - 1) & 1, limit, &never)) atomicExch(a.err, 1);
+        }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      uint32_t it = 0, tc = 0;
+      uint32_t last_bar = 0, last_par = 0;
+      bool committed = false;
+      if (a.stall_test) {  // failure-injection test: a barrier nothing arrives at
+        if (!mbar_wait(stall_bar, 0, limit, abort_flag)) fail();
+      }
+      for (int gt = blockIdx.x; gt < ntot; gt += gridDim.x, ++tc) {
+        const TcTile t = a.tiles[gt % a.ntiles];
+        const int k0 = t.kseg * a.kseg_len, k1 = min(a.Kpad, k0 + a.kseg_len);
+        const int nst = (k1 - k0) / KC;
+        bool ok = !*abort_flag;
+        if (ok && !mbar_wait(acc_empty, (tc & 1) ^ 1, limit, abort_flag)) {
+          fail();
+          ok = false;
+        }
+        tc_fence_after();
+        for (int st = 0; st < nst; ++st, ++it) {
+          const int s = it & 1;
+          const uint32_t ph = (it >> 1) & 1;
+          if (!ok || *abort_flag) {
+            ok = false;
+            continue;
+          }
+          if (!mbar_wait(a_full(s), ph, limit, abort_flag) ||
+              !mbar_wait(b_full(s), ph, limit, abort_flag)) {
+            fail();
+            ok = false;
+            continue;
+          }
+          tc_fence_after();
+          const uint32_t ah = sA + s * 2 * A_BYTES, al = ah + A_BYTES;
+          const uint32_t bh = sB + s * 2 * B_BYTES, bl = bh + B_BYTES;
+#pragma unroll
+          for (int kk = 0; kk < KC / 16; ++kk) {
+            const uint64_t dah = sw64_desc(ah + kk * 32), dal = sw64_desc(al + kk * 32);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const uint64_t dbh = sw64_desc(bh + h * 256 * 64 + kk * 32);
+              const uint64_t dbl = sw64_desc(bl + h * 256 * 64 + kk * 32);
+              const uint32_t d = tmem + h * 256;
+              tc_mma(d, dah, dbh, (st == 0 && kk == 0) ? 0u : 1u);
+              tc_mma(d, dah, dbl, 1u);
+              tc_mma(d, dal, dbh, 1u);
+            }
+          }
+          tc_commit(empty(s));
+          last_bar = empty(s);
+          last_par = ph;
+          committed = true;
+        }
+        if (ok && !*abort_flag) {
+          tc_commit(acc_full);
+          last_bar = acc_full;
+          last_par = tc & 1;
+          committed = true;
+        }
+      }
+      if (committed) {  // every MMA issued has finished before TMEM is freed
+        volatile int never = 0;
+        if (!mbar_wait(last_bar, last_par, limit, &never)) atomicExch(a.err, 1);
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ producers + epilogue
+    const int pw = warp - 2;  // 0..7
+    const int ptid = threadIdx.x - 64;
+    float *raw = reinterpret_cast<float *>(sm + OFF_RAW) + pw * RAW_ROWS * RAW_STRIDE;
+    int4 *rowinfo = reinterpret_cast<int4 *>(sm + OFF_ROW);  // (C_m, E_m, trip, nu3 | -1)
+    int4 *seginfo = reinterpret_cast<int4 *>(sm + OFF_SEG);  // (base, E, trip, hi)
+    int *nseg_s = reinterpret_cast<int *>(sm + OFF_MISC + 8);
+    int *total_s = reinterpret_cast<int *>(sm + OFF_MISC + 12);
+    float *red = reinterpret_cast<float *>(sm + OFF_B);
+    // compute mapping: lane -> (a-pair ap, b-quad bq, k-chunk kc); warp covers nu1 rows 4pw..4pw+3
+    const int kcq = lane & 3, bq = (lane >> 2) & 3, ap = lane >> 4;
+    uint32_t it = 0, tc = 0;
+    for (int gt = blockIdx.x; gt < ntot; gt += gridDim.x, ++tc) {
+      const TcTile t = a.tiles[gt % a.ntiles];
+      const int b = gt / a.ntiles;
+      const float *Fb = a.F + (long long)b * a.bstride;
+      const int k0 = t.kseg * a.kseg_len, k1 = min(a.Kpad, k0 + a.kseg_len);
+      // raw rows of this warp: r < 4 -> F_i[nu1_0 + 4pw + r], r >= 4 -> F_j[nu2_0 + r - 4]
+      auto row_ptr = [&](int r) -> const float * {
+        if (r < 4) {
+          const int nu1 = t.nu1_0 + 4 * pw + r;
+          return nu1 < a.nu1_hi ? Fb + ((long long)t.ri * a.nc + nu1) * a.fstride : nullptr;
+        }
+        const int nu2 = t.nu2_0 + r - 4;
+        return nu2 < a.nu2_hi ? Fb + ((long long)t.rj * a.nc + nu2) * a.fstride : nullptr;
+      };
+      // 20 rows x 8 float4 = 160 float4 per warp per stage: 5 per lane
+      float4 pre[5];
+      auto load_raw = [&](int kc) {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+          const int idx = lane + 32 * q;
+          const int r = idx >> 3, c4 = idx & 7;
+          const float *p = row_ptr(r);
+          const int k = kc + 4 * c4;
+          pre[q] = (p && k < a.M2) ? __ldg(reinterpret_cast<const float4 *>(p + k))
+                                   : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+      };
+      load_raw(k0);
+      for (int kc = k0; kc < k1; kc += KC, ++it) {
+        const int s = it & 1;
+        const uint32_t ph = (it >> 1) & 1;
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+          const int idx = lane + 32 * q;
+          const int r = idx >> 3, c4 = idx & 7;
+          *reinterpret_cast<float4 *>(raw + r * RAW_STRIDE + 4 * c4) = pre[q];
+        }
+        __syncwarp();
+        if (kc + KC < k1) load_raw(kc + KC);
+        bool ok = !*abort_flag;
+        if (ok && !mbar_wait(empty(s), ph ^ 1, limit, abort_flag)) {
+          fail();
+          ok = false;
+        }
+        if (ok) {
+          // 2 nu1 x 4 nu2 pairs x 8 pixels per lane
+          float fi[2][8], fj[4][8];
+#pragma unroll
+          for (int x = 0; x < 2; ++x) {
+            const float4 u = *reinterpret_cast<const float4 *>(raw + (2 * ap + x) * RAW_STRIDE + 8 * kcq);
+            const float4 v = *reinterpret_cast<const float4 *>(raw + (2 * ap + x) * RAW_STRIDE + 8 * kcq + 4);
+            fi[x][0] = u.x; fi[x][1] = u.y; fi[x][2] = u.z; fi[x][3] = u.w;
+            fi[x][4] = v.x; fi[x][5] = v.y; fi[x][6] = v.z; fi[x][7] = v.w;
+          }
+#pragma unroll
+          for (int y = 0; y < 4; ++y) {
+            const float *rp = raw + (4 + 4 * bq + y) * RAW_STRIDE + 8 * kcq;
+            const float4 u = *reinterpret_cast<const float4 *>(rp);
+            const float4 v = *reinterpret_cast<const float4 *>(rp + 4);
+            fj[y][0] = u.x; fj[y][1] = u.y; fj[y][2] = u.z; fj[y][3] = u.w;
+            fj[y][4] = v.x; fj[y][5] = v.y; fj[y][6] = v.z; fj[y][7] = v.w;
+          }
+          unsigned char *bh = sm + OFF_B + s * 2 * B_BYTES;
+          unsigned char *bl = bh + B_BYTES;
+#pragma unroll
+          for (int x = 0; x < 2; ++x)
+#pragma unroll
+            for (int y = 0; y < 4; ++y) {
+              const int p = (4 * pw + 2 * ap + x) * P2 + 4 * bq + y;  // pair row
+              uint4 H, L;
+              split2(fi[x][0] * fj[y][0], fi[x][1] * fj[y][1], H.x, L.x);
+              split2(fi[x][2] * fj[y][2], fi[x][3] * fj[y][3], H.y, L.y);
+              split2(fi[x][4] * fj[y][4], fi[x][5] * fj[y][5], H.z, L.z);
+              split2(fi[x][6] * fj[y][6], fi[x][7] * fj[y][7], H.w, L.w);
+              const uint32_t o = sw64_off(p, kcq);
+              *reinterpret_cast<uint4 *>(bh + o) = H;
+              *reinterpret_cast<uint4 *>(bl + o) = L;
+            }
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        }
+        __syncwarp();
+        if (lane == 0 && ok) mbar_arrive(b_full(s));
+      }
+
+      // ---------------------------------------------------------- epilogue
+      bool ok = !*abort_flag;
+      if (ok && !mbar_wait(acc_full, tc & 1, limit, abort_flag)) {
+        fail();
+        ok = false;
+      }
+      ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
+      tc_fence_after();
+      asm volatile("bar.sync 1, 256;" ::: "memory");
+      if (ptid == 0) {
+        // segments of consecutive rows with one ring triple
+        int ns = 0, base = 0, m = 0;
+        while (m < MROWS) {
+          const int e = t.col0 + m;
+          if (e >= t.ncol) break;
+          const ColEntry c0 = a.cols[t.col_off + e];
+          if (c0.field < 0) {
+            ++m;
+            continue;
+          }
+          int lo = c0.nu3, hi = c0.nu3, q = m;
+          while (q + 1 < MROWS && t.col0 + q + 1 < t.ncol) {
+            const ColEntry cn = a.cols[t.col_off + t.col0 + q + 1];
+            if (cn.field >= 0 && cn.trip != c0.trip) break;
+            ++q;
+            if (cn.field >= 0) {
+              lo = min(lo, cn.nu3);
+              hi = max(hi, cn.nu3);
+            }
+          }
+          const int E = (P2 - 1) + (hi - lo) + 1;
+          if (ns < MAX_SEG) seginfo[ns] = make_int4(base, E, c0.trip, hi);
+          for (int r = m; r <= q; ++r) {
+            const int ee = t.col0 + r;
+            const ColEntry cr = a.cols[t.col_off + ee];
+            if (cr.field < 0)
+              rowinfo[r] = make_int4(0, 0, cr.trip, -1);
+            else if (ns >= MAX_SEG)  // no reduction slot: direct atomics (total > RED_CAP)
+              rowinfo[r] = make_int4(0, 0, cr.trip, cr.nu3);
+            else
+              rowinfo[r] = make_int4(base + (P2 - 1) * E + hi - cr.nu3, E, cr.trip, cr.nu3);
+          }
+          base += (P1 + P2 - 1) * E;
+          ++ns;
+          m = q + 1;
+        }
+        for (int r = m; r < MROWS; ++r) rowinfo[r] = make_int4(0, 0, 0, -1);
+        *nseg_s = ns;
+        *total_s = (ns <= MAX_SEG) ? base : RED_CAP + 1;
+      }
+      asm volatile("bar.sync 1, 256;" ::: "memory");
+      const int total = *total_s;
+      const bool use_red = a.dsum != nullptr && total <= RED_CAP;
+      if (use_red)
+        for (int q = ptid; q < total; q += 256) red[q] = 0.f;
+      asm volatile("bar.sync 1, 256;" ::: "memory");
+      // TMEM: warp -> lane quadrant (warp % 4) and column half
+      const int quad = warp & 3, half = pw >> 2;
+      const int m = 32 * quad + lane;
+      const int4 ri = rowinfo[m];
+      const bool row_ok = ri.w >= 0;
+      const double tn = (a.out_full && row_ok) ? a.tnorm[ri.z] : 0.0;
+      const int n2 = 2 * a.nc - 1;
+      for (int ch = 0; ch < 256 / 32; ++ch) {
+        uint32_t v[32];
+        if (ok) tc_ld32(tmem + ((uint32_t)(32 * quad) << 16) + half * 256 + ch * 32, v);
+        if (!ok || !row_ok) continue;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int p = half * 256 + ch * 32 + j;
+          const int pa = p >> 4, pb = p & 15;
+          const int nu1 = t.nu1_0 + pa, nu2 = t.nu2_0 + pb;
+          if (nu1 >= a.nu1_hi || nu2 >= a.nu2_hi) continue;
+          const float s = __uint_as_float(v[j]);
+          if (a.dsum) {
+            if (use_red) {
+              atomicAdd(red + ri.x + (pa - pb) * ri.y + pb, s);
+            } else {
+              const long long o = (long long)b * a.dsum_bstride +
+                                  ((long long)ri.z * n2 + (nu1 - ri.w + a.nc - 1)) * n2 +
+                                  (nu2 - ri.w + a.nc - 1);
+              atomicAdd(a.dsum + o, (double)s);
+            }
+          }
+          if (a.out_full) {
+            const long long o = (long long)b * a.full_bstride +
+                                (((long long)ri.z * a.nc + nu1) * a.nc + nu2) * a.nc + ri.w;
+            atomicAdd(a.out_full + o, (double)s * tn);
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0 && ok) mbar_arrive(acc_empty);
+      asm volatile("bar.sync 1, 256;" ::: "memory");
+      if (use_red && ok) {
+        const int ns = *nseg_s;
+        for (int q = ptid; q < total; q += 256) {
+          const float v = red[q];
+          if (v == 0.f) continue;
+          int sg = 0;
+          while (sg + 1 < ns && seginfo[sg + 1].x <= q) ++sg;
+          const int4 si = seginfo[sg];
+          const int off = q - si.x;
+          const int dd = off / si.y, e2 = off - dd * si.y;
+          const int d = dd - (P2 - 1) + t.nu1_0 - t.nu2_0;  // nu1 - nu2
+          const int d2 = e2 + t.nu2_0 - si.w;                // nu2 - nu3
+          const int d1 = d + d2;
+          const long long o = (long long)b * a.dsum_bstride +
+                              ((long long)si.z * n2 + (d1 + a.nc - 1)) * n2 + (d2 + a.nc - 1);
+          atomicAdd(a.dsum + o, (double)v);
+        }
+      }
+      asm volatile("bar.sync 1, 256;" ::: "memory");
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
+}  // namespace
+
+int tc_smem_bytes() { return SMEM_BYTES; }
+
+cudaError_t launch_contract_tc(const CUtensorMap &map_hi, const CUtensorMap &map_lo,
+                               const TcArgs &a, int nsm, cudaStream_t s) {
+  if (a.ntiles == 0) return cudaSuccess;
+  cudaError_t e =
+      cudaFuncSetAttribute(k_contract_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  if (e != cudaSuccess) return e;
+  const long long ntot = (long long)a.ntiles * a.batch;
+  const int grid = (int)std::min<long long>(ntot, nsm);
+  k_contract_tc<<<grid, NTHREADS, SMEM_BYTES, s>>>(map_hi, map_lo, a);
+  return cudaGetLastError();
+}
+
+}  // namespace bsi

@@ -1,7 +1,10 @@
 // C ABI of libbs (include/bs.h): plan construction (host), workspace
 // layout, and the orchestration of the device stages of Section 3.2.
+#include <cuda.h>
+
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -60,9 +63,14 @@ std::vector<float2> twiddles(int n) {
 }
 
 struct WsLayout {
-  size_t label, efflabel, cells, uext, tripof, valid, twM, twN, tnorm, T, nnu, cols, ptiles, G, F,
-      Fhi, Flo, dsum, tmp3d, herm, total;
+  size_t label, efflabel, cells, uext, tripof, valid, twM, twN, tnorm, T, nnu, cols, ptiles, tctiles,
+      G, F, Fhi, Flo, dsum, tmp3d, herm, err, total;
 };
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 }  // namespace
 
@@ -89,9 +97,13 @@ struct bs_plan_s {
   WsLayout L{};
   unsigned char *ws = nullptr;
   bool ws_owned = false;
-  size_t max_cols = 0, max_ptiles = 0;
+  size_t max_cols = 0, max_ptiles = 0, max_tctiles = 0;
   std::vector<ColEntry> h_cols;
   std::vector<PairTile> h_ptiles;
+  std::vector<TcTile> h_tctiles;
+  CUtensorMap map_hi{}, map_lo{};
+  bool maps_ready = false;
+  int nsm = 152;
 
   template <class T_>
   T_ *at(size_t off) const {
@@ -142,6 +154,7 @@ void compute_layout(bs_plan p) {
   L.nnu = take(n2 * n2 * sizeof(long long));
   L.cols = take(p->max_cols * sizeof(ColEntry));
   L.ptiles = take(p->max_ptiles * sizeof(PairTile));
+  L.tctiles = take(p->max_tctiles * sizeof(TcTile));
   L.G = take((size_t)p->batch * p->nb * p->nc * (size_t)p->M * p->UC * sizeof(float2));
   L.F = take((size_t)p->batch * p->nf * (size_t)p->M * p->M * sizeof(float));
   const bool split = p->d.precision == BS_PREC_SPLIT_BF16;
@@ -150,6 +163,7 @@ void compute_layout(bs_plan p) {
   L.dsum = take((size_t)p->batch * p->ntrip * n2 * n2 * sizeof(double));
   L.tmp3d = take((size_t)p->batch * p->ntrip * (size_t)p->nc * p->nc * sizeof(float2));
   L.herm = take(2 * sizeof(float));
+  L.err = take(sizeof(int));
   L.total = o;
 }
 
@@ -184,7 +198,54 @@ bs_status init_tables(bs_plan p, cudaStream_t s) {
                           cudaMemcpyHostToDevice, s));
   BS_CUDA(cudaMemcpyAsync(p->at<float2>(L.twN), twn.data(), twn.size() * sizeof(float2),
                           cudaMemcpyHostToDevice, s));
+  BS_CUDA(cudaMemsetAsync(p->at<int>(L.err), 0, sizeof(int), s));
   BS_CUDA(cudaStreamSynchronize(s));  // host vectors above are temporaries
+  return BS_OK;
+}
+
+// Read and clear the device error word (synchronises): a bounded wait in a
+// kernel gave up since the last check.
+bs_status check_device_error(bs_plan p, cudaStream_t s) {
+  int h = 0;
+  BS_CUDA(cudaMemcpyAsync(&h, p->at<int>(p->L.err), sizeof(int), cudaMemcpyDeviceToHost, s));
+  BS_CUDA(cudaStreamSynchronize(s));
+  if (h != 0) {
+    BS_CUDA(cudaMemsetAsync(p->at<int>(p->L.err), 0, sizeof(int), s));
+    BS_CUDA(cudaStreamSynchronize(s));
+    return fail(p, BS_ERR_TIMEOUT,
+                "a bounded wait in the tensor-core contraction gave up; its results are invalid");
+  }
+  return BS_OK;
+}
+
+// Tensor maps over the BF16 hi / lo field arrays: rows = batch * nf fields,
+// inner dimension = M^2 pixels; boxes of 32 pixels x 8 fields, 64-byte swizzle.
+bs_status ensure_tensor_maps(bs_plan p) {
+  if (p->maps_ready) return BS_OK;
+  void *fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                   cudaEnableDefault, &q);
+  if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
+    cudaGetLastError();
+    return fail(p, BS_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  }
+  EncodeTiledFn enc = reinterpret_cast<EncodeTiledFn>(fn);
+  const cuuint64_t M2 = (cuuint64_t)p->M * p->M;
+  cuuint64_t dims[2] = {M2, (cuuint64_t)p->batch * p->nf};
+  cuuint64_t strides[1] = {M2 * 2};
+  cuuint32_t box[2] = {32, 8};
+  cuuint32_t estr[2] = {1, 1};
+  for (int w = 0; w < 2; ++w) {
+    void *base = w == 0 ? (void *)p->at<uint16_t>(p->L.Fhi) : (void *)p->at<uint16_t>(p->L.Flo);
+    CUresult r = enc(w == 0 ? &p->map_hi : &p->map_lo, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base,
+                     dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+      return fail(p, BS_ERR_CUDA, "cuTensorMapEncodeTiled failed with code " + std::to_string((int)r));
+  }
+  p->maps_ready = true;
   return BS_OK;
 }
 
@@ -290,6 +351,88 @@ bs_status delta_reset(bs_plan p, cudaStream_t s) {
   const size_t n2 = (size_t)(2 * p->nc - 1);
   BS_CUDA(cudaMemsetAsync(p->at<double>(p->L.dsum), 0,
                           (size_t)p->batch * p->ntrip * n2 * n2 * sizeof(double), s));
+  return BS_OK;
+}
+
+// Tensor-core contraction of one channel block (split BF16).
+bs_status mabs_tc(bs_plan p, const int *blk, double *out_full, int accumulate,
+                  long long full_bstride, cudaStream_t s) {
+  bs_status st = ensure_tensor_maps(p);
+  if (st != BS_OK) return st;
+  const int nc = p->nc, nb = p->nb;
+  const WsLayout &L = p->L;
+  p->h_cols.clear();
+  p->h_tctiles.clear();
+  const int w3 = blk[5] - blk[4];
+  const int run = ((w3 + 7) / 8) * 8;
+  const int M2 = p->M * p->M;
+  const int Kpad = ((M2 + 31) / 32) * 32;
+  struct PairList {
+    int i, j, off, n;
+  };
+  std::vector<PairList> pl;
+  for (int i = 0; i < nb; ++i)
+    for (int j = i; j < nb; ++j) {
+      const int off = (int)p->h_cols.size();
+      for (int l = j; l < nb; ++l) {
+        const int t = p->trip_of[((size_t)i * nb + j) * nb + l];
+        if (p->T[t] <= 0) continue;
+        for (int q = 0; q < run; ++q) {
+          const int n3 = blk[4] + q;
+          p->h_cols.push_back(ColEntry{q < w3 ? l * nc + n3 : -1, t, n3, 0});
+        }
+      }
+      const int n = (int)p->h_cols.size() - off;
+      if (n > 0) pl.push_back(PairList{i, j, off, n});
+    }
+  const int n1b = (blk[1] - blk[0] + 31) / 32, n2b = (blk[3] - blk[2] + 15) / 16;
+  long long base_tiles = 0;
+  for (const PairList &q : pl) base_tiles += (long long)n1b * n2b * ((q.n + 127) / 128);
+  if (base_tiles == 0 || w3 == 0) return BS_OK;
+  // split K until every SM has a few tiles
+  int nk = 1;
+  while (base_tiles * nk * p->batch < 2LL * p->nsm && nk < 64 && Kpad / (32 * nk * 2) >= 8) nk *= 2;
+  const int kseg_len = ((Kpad / 32 + nk - 1) / nk) * 32;
+  nk = (Kpad + kseg_len - 1) / kseg_len;
+  for (const PairList &q : pl)
+    for (int c0 = 0; c0 < q.n; c0 += 128)
+      for (int a1 = 0; a1 < n1b; ++a1)
+        for (int a2 = 0; a2 < n2b; ++a2)
+          for (int k = 0; k < nk; ++k)
+            p->h_tctiles.push_back(TcTile{q.i, q.j, blk[0] + 32 * a1, blk[2] + 16 * a2, q.off, q.n,
+                                          c0, k});
+  if (p->h_tctiles.size() > p->max_tctiles || p->h_cols.size() > p->max_cols)
+    return fail(p, BS_ERR_UNSUPPORTED, "tensor-core tile list exceeds the plan's capacity");
+  BS_CUDA(cudaMemcpyAsync(p->at<ColEntry>(L.cols), p->h_cols.data(),
+                          p->h_cols.size() * sizeof(ColEntry), cudaMemcpyHostToDevice, s));
+  BS_CUDA(cudaMemcpyAsync(p->at<TcTile>(L.tctiles), p->h_tctiles.data(),
+                          p->h_tctiles.size() * sizeof(TcTile), cudaMemcpyHostToDevice, s));
+  TcArgs a{};
+  a.F = p->at<float>(L.F);
+  a.fstride = M2;
+  a.bstride = (long long)p->nf * M2;
+  a.nf = p->nf;
+  a.batch = p->batch;
+  a.M2 = M2;
+  a.Kpad = Kpad;
+  a.nc = nc;
+  a.cols = p->at<ColEntry>(L.cols);
+  a.tiles = p->at<TcTile>(L.tctiles);
+  a.ntiles = (int)p->h_tctiles.size();
+  a.nu1_hi = blk[1];
+  a.nu2_hi = blk[3];
+  a.kseg_len = kseg_len;
+  a.tnorm = p->at<double>(L.tnorm);
+  a.out_full = out_full;
+  a.full_bstride = full_bstride;
+  a.dsum = accumulate ? p->at<double>(L.dsum) : nullptr;
+  a.dsum_bstride = (long long)p->ntrip * (2 * nc - 1) * (2 * nc - 1);
+  a.err = p->at<int>(L.err);
+  a.wait_limit_ns = 2000000000LL;
+  const char *inj = std::getenv("BS_INJECT_MMA_STALL");
+  a.stall_test = (inj && inj[0] == '1') ? 1 : 0;
+  if (a.stall_test) a.wait_limit_ns = 50000000LL;
+  BS_CUDA(launch_contract_tc(p->map_hi, p->map_lo, a, p->nsm, s));
   return BS_OK;
 }
 
@@ -415,6 +558,15 @@ bs_status bs_plan_create(const bs_plan_desc *desc, bs_plan *out) {
   const int npairs = p->nb * (p->nb + 1) / 2;
   p->max_cols = (size_t)npairs * p->nb * p->nc;
   p->max_ptiles = (size_t)npairs * ((size_t)p->nb * p->nc / 128 + 1);
+  // tensor-core tiles: pair rectangles (32 x 16) x 128-entry column windows (runs padded to 8)
+  cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (p->d.precision == BS_PREC_SPLIT_BF16) {
+    // largest block: the full cube; K splitting only happens while tiles < 2 per SM
+    const size_t runs = (size_t)p->nb * (((p->nc + 7) / 8) * 8);
+    const size_t full = (size_t)npairs * ((p->nc + 31) / 32) * ((p->nc + 15) / 16) * ((runs + 127) / 128);
+    p->max_tctiles = std::min<size_t>(full + 4 * (size_t)p->nsm, (size_t)1 << 22);
+    p->max_cols = (size_t)npairs * runs;
+  }
   compute_layout(p);
   *out = p;
   return BS_OK;
@@ -538,57 +690,62 @@ bs_status bs_mabs(bs_plan p, const int32_t *block, double *out_full, int accumul
   const WsLayout &L = p->L;
   const long long full_bstride = (long long)p->ntrip * nc * nc * nc;
   if (out_full) BS_CUDA(launch_full_fill(out_full, full_bstride, p->batch, p->ntrip, nc, blk, 0.0, s));
-  // work list: ring pairs (i <= j) x column tiles over (l, nu3), T(i,j,l) > 0, nu3 valid
-  p->h_cols.clear();
-  p->h_ptiles.clear();
-  const int nb = p->nb;
-  for (int i = 0; i < nb; ++i)
-    for (int j = i; j < nb; ++j) {
-      const int off = (int)p->h_cols.size();
-      for (int l = j; l < nb; ++l) {
-        const int t = p->trip_of[((size_t)i * nb + j) * nb + l];
-        if (p->T[t] <= 0) continue;
-        for (int n3 = blk[4]; n3 < blk[5]; ++n3)
-          if (p->valid[n3]) p->h_cols.push_back(ColEntry{l * nc + n3, t, n3, 0});
+  if (p->d.precision == BS_PREC_SPLIT_BF16) {
+    st = mabs_tc(p, blk, out_full, accumulate, full_bstride, s);
+    if (st != BS_OK) return st;
+  } else {
+    // work list: ring pairs (i <= j) x column tiles over (l, nu3), T(i,j,l) > 0, nu3 valid
+    p->h_cols.clear();
+    p->h_ptiles.clear();
+    const int nb = p->nb;
+    for (int i = 0; i < nb; ++i)
+      for (int j = i; j < nb; ++j) {
+        const int off = (int)p->h_cols.size();
+        for (int l = j; l < nb; ++l) {
+          const int t = p->trip_of[((size_t)i * nb + j) * nb + l];
+          if (p->T[t] <= 0) continue;
+          for (int n3 = blk[4]; n3 < blk[5]; ++n3)
+            if (p->valid[n3]) p->h_cols.push_back(ColEntry{l * nc + n3, t, n3, 0});
+        }
+        const int ncol = (int)p->h_cols.size() - off;
+        for (int c0 = 0; c0 < ncol; c0 += 128) p->h_ptiles.push_back(PairTile{i, j, off, ncol, c0, {0, 0, 0}});
       }
-      const int ncol = (int)p->h_cols.size() - off;
-      for (int c0 = 0; c0 < ncol; c0 += 128) p->h_ptiles.push_back(PairTile{i, j, off, ncol, c0, {0, 0, 0}});
+    const int n_r1 = (blk[1] - blk[0] + 15) / 16, n_r2 = (blk[3] - blk[2] + 7) / 8;
+    const int npt = (int)p->h_ptiles.size();
+    if (npt > 0 && n_r1 > 0 && n_r2 > 0) {
+      if (npt > 65535) return fail(p, BS_ERR_UNSUPPORTED, "too many column tiles in one block");
+      BS_CUDA(cudaMemcpyAsync(p->at<ColEntry>(L.cols), p->h_cols.data(),
+                              p->h_cols.size() * sizeof(ColEntry), cudaMemcpyHostToDevice, s));
+      BS_CUDA(cudaMemcpyAsync(p->at<PairTile>(L.ptiles), p->h_ptiles.data(),
+                              p->h_ptiles.size() * sizeof(PairTile), cudaMemcpyHostToDevice, s));
+      ContractArgs a{};
+      a.F = p->at<float>(L.F);
+      a.fstride = (long long)p->M * p->M;
+      a.bstride = (long long)p->nf * p->M * p->M;
+      a.M2 = p->M * p->M;
+      a.nc = nc;
+      a.cols = p->at<ColEntry>(L.cols);
+      a.ptiles = p->at<PairTile>(L.ptiles);
+      a.nu1_lo = blk[0];
+      a.nu1_hi = blk[1];
+      a.nu2_lo = blk[2];
+      a.nu2_hi = blk[3];
+      a.n_r2 = n_r2;
+      // split K until the launch covers several waves of 152 SMs
+      const long long ctas = (long long)n_r1 * n_r2 * npt * p->batch;
+      int nk = 1;
+      const int nchunks = a.M2 / 16;
+      while (ctas * nk < 4 * 152 && nk * 2 <= nchunks / 16 && nk < 64) nk *= 2;
+      while ((long long)nk * p->batch > 65535) nk /= 2;
+      a.nkseg = nk;
+      a.kseg_len = ((nchunks + nk - 1) / nk) * 16;
+      a.tnorm = p->at<double>(L.tnorm);
+      a.out_full = out_full;
+      a.full_bstride = full_bstride;
+      a.dsum = accumulate ? p->at<double>(L.dsum) : nullptr;
+      a.dsum_bstride = (long long)p->ntrip * (2 * nc - 1) * (2 * nc - 1);
+      BS_CUDA(launch_contract_simt(a, n_r1 * n_r2, npt, p->batch, s));
     }
-  const int n_r1 = (blk[1] - blk[0] + 15) / 16, n_r2 = (blk[3] - blk[2] + 7) / 8;
-  const int npt = (int)p->h_ptiles.size();
-  if (npt > 0 && n_r1 > 0 && n_r2 > 0) {
-    if (npt > 65535) return fail(p, BS_ERR_UNSUPPORTED, "too many column tiles in one block");
-    BS_CUDA(cudaMemcpyAsync(p->at<ColEntry>(L.cols), p->h_cols.data(),
-                            p->h_cols.size() * sizeof(ColEntry), cudaMemcpyHostToDevice, s));
-    BS_CUDA(cudaMemcpyAsync(p->at<PairTile>(L.ptiles), p->h_ptiles.data(),
-                            p->h_ptiles.size() * sizeof(PairTile), cudaMemcpyHostToDevice, s));
-    ContractArgs a{};
-    a.F = p->at<float>(L.F);
-    a.fstride = (long long)p->M * p->M;
-    a.bstride = (long long)p->nf * p->M * p->M;
-    a.M2 = p->M * p->M;
-    a.nc = nc;
-    a.cols = p->at<ColEntry>(L.cols);
-    a.ptiles = p->at<PairTile>(L.ptiles);
-    a.nu1_lo = blk[0];
-    a.nu1_hi = blk[1];
-    a.nu2_lo = blk[2];
-    a.nu2_hi = blk[3];
-    a.n_r2 = n_r2;
-    // split K until the launch covers several waves of 152 SMs
-    const long long ctas = (long long)n_r1 * n_r2 * npt * p->batch;
-    int nk = 1;
-    const int nchunks = a.M2 / 16;
-    while (ctas * nk < 4 * 152 && nk * 2 <= nchunks / 16 && nk < 64) nk *= 2;
-    while ((long long)nk * p->batch > 65535) nk /= 2;
-    a.nkseg = nk;
-    a.kseg_len = ((nchunks + nk - 1) / nk) * 16;
-    a.tnorm = p->at<double>(L.tnorm);
-    a.out_full = out_full;
-    a.full_bstride = full_bstride;
-    a.dsum = accumulate ? p->at<double>(L.dsum) : nullptr;
-    a.dsum_bstride = (long long)p->ntrip * (2 * nc - 1) * (2 * nc - 1);
-    BS_CUDA(launch_contract_simt(a, n_r1 * n_r2, npt, p->batch, s));
   }
   if (out_full)
     BS_CUDA(launch_full_finalize(out_full, full_bstride, p->batch, p->ntrip, nc, blk,
@@ -611,6 +768,8 @@ bs_status bs_mabs_delta(bs_plan p, double *out, void *stream) {
   if (!p->loaded) return fail(p, BS_ERR_STATE, "bs_mabs_delta before bs_grid_load");
   bs_status st = prepare(p, s);
   if (st != BS_OK) return st;
+  st = check_device_error(p, s);
+  if (st != BS_OK) return st;
   st = upload_nnu(p, s);
   if (st != BS_OK) return st;
   BS_CUDA(launch_delta_norm(p->at<double>(p->L.dsum), p->at<long long>(p->L.nnu),
@@ -623,6 +782,8 @@ bs_status bs_bs3d(bs_plan p, double *out, void *stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (!p->loaded) return fail(p, BS_ERR_STATE, "bs_bs3d before bs_grid_load");
   bs_status st = prepare(p, s);
+  if (st != BS_OK) return st;
+  st = check_device_error(p, s);
   if (st != BS_OK) return st;
   st = upload_nnu(p, s);
   if (st != BS_OK) return st;
