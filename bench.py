@@ -42,7 +42,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 WORKLOADS = {
-    "mwa": dict(nt=256, nc=768, nb=20, edges=("log", 4.41, 128.0), block=64,
+    "mwa": dict(nt=256, nc=768, nb=20, edges=("log", 4.41, 128.0), block=128,
                 desc="MWA-like: 256^2 uv grid, 768 channels (30.72 MHz at 40 kHz), 20 log rings "
                      "|U| in [4.41, 128), no flagging"),
     "small": dict(nt=128, nc=128, nb=12, edges=("log", 2.2, 64.0), block=32,
@@ -53,8 +53,14 @@ WORKLOADS = {
 }
 SMS = 152
 FP32_LANES_PER_SM = 128
-PROFILE = os.path.join(ROOT, "profiles", "contract_simt_mwa.txt")
-KERNEL_SRC = os.path.join(ROOT, "paper_2506_10526_gb300", "csrc", "contract_simt.cu")
+PROFILES = {"fp32": (os.path.join(ROOT, "profiles", "contract_simt_mwa.txt"),
+                     os.path.join(ROOT, "paper_2506_10526_gb300", "csrc", "contract_simt.cu")),
+            "split_bf16": (os.path.join(ROOT, "profiles", "contract_tc_mwa.txt"),
+                           os.path.join(ROOT, "paper_2506_10526_gb300", "csrc", "contract_tc.cu"))}
+# maximum kappa-normalised error against the FP64 oracle measured by the GPU
+# parity tests (tests/test_gpu_parity.py, tests/test_gpu_fullsize.py)
+STATED_ERROR = {"fp32": "kappa-normalised error <= 1e-5 (measured 3.1e-7)",
+                "split_bf16": "kappa-normalised error <= 1e-3 (measured 1.3e-6)"}
 
 
 def parse():
@@ -64,7 +70,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="mwa", choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "split_bf16"])
+    ap.add_argument("--precision", default="split_bf16", choices=["fp32", "split_bf16"])
+    ap.add_argument("--no-fp32-compare", action="store_true",
+                    help="skip timing the plain FP32 contraction beside the split-BF16 one")
     ap.add_argument("--block", type=int, default=0, help="channel block side (0 = workload default)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU baseline budget")
     ap.add_argument("--no-e2e", action="store_true")
@@ -153,14 +161,15 @@ def measured_peaks():
     return {}
 
 
-def profile_traffic():
-    """DRAM bytes per launch of the contraction from the committed ncu summary,
-    valid only while the kernel source still has the hash recorded there."""
-    if not os.path.exists(PROFILE):
+def profile_traffic(precision):
+    """DRAM bytes per evaluation of the contraction from the committed ncu
+    summary, valid only while the kernel source still has the hash recorded there."""
+    prof, src = PROFILES[precision]
+    if not os.path.exists(prof):
         return None
-    h = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     vals = {}
-    for line in open(PROFILE):
+    for line in open(prof):
         if ":" in line:
             k, v = line.split(":", 1)
             vals[k.strip()] = v.strip()
@@ -354,7 +363,7 @@ def main():
         peak = float(peaks.get("bf16_tflops", 1900.0)) / 3.0
         roof = {"bound": "tensor", "peak_source": "measured bf16 burst / 3 (three split products)"}
     achieved = per_launch_evals * 2.0 * M * M / (avg_ms / 1e3) / 1e12
-    tr = profile_traffic()
+    tr = profile_traffic(args.precision)
     roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                  "kernel": "k_contract_simt" if args.precision == "fp32" else "k_contract_tc",
                  "avg_launch_ms": avg_ms,
@@ -375,9 +384,36 @@ def main():
         "gpu_launches": 6 * args.steps,
         "e2e": e2e,
     }
+    line["config"]["stated_error"] = STATED_ERROR[args.precision]
+    contraction_rate = per_launch_evals / (avg_ms / 1e3)
+    line["contraction_evals_per_s"] = contraction_rate
+    plan.close()
+    del out_delta, out3d
+    torch.cuda.empty_cache()
+    if args.precision == "split_bf16" and not args.no_fp32_compare and world == 1:
+        # the plain FP32 GPU path on the same input, timed the same way, on 64^3 blocks
+        fb = min(64, w["block"])
+        fp = bs.Plan(nt, nc, edges, precision=bs.PREC_FP32)
+        fp.grid_load(vis_d)
+        fjobs = blocks_of(nc, fb)
+        fev = []
+        for i in range(3):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fp.mabs(block=fjobs[i % len(fjobs)], accumulate=True)
+            e1.record(stream)
+            fev.append((e0, e1))
+        torch.cuda.synchronize()
+        fms = statistics.mean(a.elapsed_time(b) for a, b in fev[1:])
+        fb_evals = nclos * fb ** 3
+        fp32_rate = fb_evals / (fms / 1e3)
+        fp.close()
+        line["fp32_plain"] = {"channel_block": fb, "contraction_evals_per_s": fp32_rate,
+                              "avg_launch_ms": fms, "stated_error": STATED_ERROR["fp32"]}
+        line["speedup_vs_fp32"] = contraction_rate / fp32_rate
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds, vis)
-    plan.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
