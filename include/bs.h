@@ -186,6 +186,59 @@ bs_status bs_bs3d(bs_plan plan, double *out_dev, void *cuda_stream);
  * Returns BS_OK or BS_ERR_NOT_HERMITIAN. */
 bs_status bs_check_hermitian(bs_plan plan, const void *vis_dev, double tol, void *cuda_stream);
 
+/* ---------------------------------------------------------------------------
+ * Batched Monte Carlo (Section 4: ensemble mean and 1-sigma of the MABS and
+ * the 3D bispectrum over many realisations).  An ensemble holds shape groups
+ * (uneven grid sides, channel counts and ring sets); group g processes
+ * desc[g].batch realisations per run.  A run loads every group's fields,
+ * contracts the full channel cube of every realisation of every group in ONE
+ * persistent tensor-core launch (split BF16 only), forms the folded collapsed
+ * plane and Eq. (dft), and adds each realisation to per-bin Welford
+ * statistics (FP64 mean and M2).  The first run executes eagerly; later runs
+ * with use_graph replay a captured CUDA graph of the same launches.
+ * ------------------------------------------------------------------------- */
+typedef struct bs_mc_s *bs_mc;
+
+/* Create the ensemble: one plan per group (each desc must use
+ * BS_PREC_SPLIT_BF16), device input buffers, statistics.  Allocates device
+ * memory.  Errors: as bs_plan_create, BS_ERR_OOM. */
+bs_status bs_mc_create(const bs_plan_desc *group_descs, int ngroups, bs_mc *out);
+bs_status bs_mc_destroy(bs_mc mc);
+/* Message of the last failure on this ensemble; never NULL. */
+const char *bs_mc_last_error(bs_mc mc);
+/* bs_plan_info of group g's plan. */
+bs_status bs_mc_info(bs_mc mc, int group, int64_t *info_host, int n);
+/* Register group g's input: a caller-owned device buffer of complex64
+ * [batch][nchan][nt][nt] visibilities, centred, Hermitian, 8-byte aligned.
+ * The caller writes the next realisations there before each bs_mc_run and
+ * keeps the buffer alive; registering a different pointer drops the captured
+ * graph (it is captured again on the next graph run). */
+bs_status bs_mc_set_input(bs_mc mc, int group, const void *vis_dev);
+/* Tuning knob chosen by the autotuner: split K until the contraction has at
+ * least tiles_per_sm tiles per SM (1..64).  Only before the first run. */
+bs_status bs_mc_set_tuning(bs_mc mc, int tiles_per_sm);
+/* Autotuner: time each candidate K-split target (tiles per SM in
+ * {1, 2, 4, 8, 16}) on the registered inputs (one warm-up and two timed runs
+ * each), keep the fastest and store it in the JSON file cache_path under the
+ * ensemble's shape signature (NULL: no cache); a cached signature is applied
+ * without timing.  Resets the statistics; writes the choice to *chosen.
+ * Synchronises. */
+bs_status bs_mc_autotune(bs_mc mc, const char *cache_path, int *chosen, void *cuda_stream);
+/* One Monte Carlo step over all groups (asynchronous on cuda_stream). */
+bs_status bs_mc_run(bs_mc mc, int use_graph, void *cuda_stream);
+/* Zero the statistics. */
+bs_status bs_mc_reset(bs_mc mc, void *cuda_stream);
+/* Per-bin statistics of group g over all realisations accumulated so far:
+ *  which = 0: folded collapsed MABS, bins [T_r][2nchan-1][2nchan-1]
+ *  which = 1: 3D bispectrum of Eq. (dft), bins [T_r][nchan][nchan]
+ *  mean_dev / var_dev: double device arrays of that size (either may be
+ *  NULL); var is the unbiased sample variance; NaN where fewer than 1 (mean)
+ *  or 2 (var) defined values.  realisations_host (or NULL): realisations of
+ *  group g accumulated.  Synchronises to read the device error word; returns
+ *  BS_ERR_TIMEOUT if a bounded wait gave up. */
+bs_status bs_mc_stats(bs_mc mc, int group, int which, double *mean_dev, double *var_dev,
+                      int64_t *realisations_host, void *cuda_stream);
+
 /* Closed-triangle counts T(i,j,l) without any device allocation.
  * The paper has no counterpart: this entry point exists for callers that
  * cannot call cudaMalloc (a pipeline bound to its own pre-allocated memory

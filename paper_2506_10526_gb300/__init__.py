@@ -31,6 +31,8 @@ PREC_SPLIT_BF16 = 1
 EXPORTS = ("bs_abi_version", "bs_plan_create", "bs_plan_destroy", "bs_last_error",
            "bs_plan_info", "bs_plan_set_workspace", "bs_grid_load", "bs_counts", "bs_mabs",
            "bs_delta_reset", "bs_mabs_delta", "bs_bs3d", "bs_check_hermitian",
+           "bs_mc_create", "bs_mc_destroy", "bs_mc_last_error", "bs_mc_info", "bs_mc_set_input",
+           "bs_mc_set_tuning", "bs_mc_autotune", "bs_mc_run", "bs_mc_reset", "bs_mc_stats",
            "bs_counts_noalloc")
 
 _lib = None
@@ -76,8 +78,19 @@ def lib() -> ctypes.CDLL:
             L.bs_bs3d.argtypes = [P, P, P]
             L.bs_check_hermitian.argtypes = [P, P, D, P]
             L.bs_counts_noalloc.argtypes = [I, I, P, P, P, P]
+            L.bs_mc_create.argtypes = [P, I, ctypes.POINTER(P)]
+            L.bs_mc_destroy.argtypes = [P]
+            L.bs_mc_last_error.argtypes = [P]
+            L.bs_mc_last_error.restype = ctypes.c_char_p
+            L.bs_mc_info.argtypes = [P, I, P, I]
+            L.bs_mc_set_input.argtypes = [P, I, P]
+            L.bs_mc_set_tuning.argtypes = [P, I]
+            L.bs_mc_run.argtypes = [P, I, P]
+            L.bs_mc_autotune.argtypes = [P, ctypes.c_char_p, ctypes.POINTER(I), P]
+            L.bs_mc_reset.argtypes = [P, P]
+            L.bs_mc_stats.argtypes = [P, I, I, P, P, P, P]
             for name in EXPORTS:
-                if name not in ("bs_abi_version", "bs_last_error"):
+                if name not in ("bs_abi_version", "bs_last_error", "bs_mc_last_error"):
                     getattr(L, name).restype = I
             _lib = L
     return _lib
@@ -214,3 +227,91 @@ def counts_noalloc(nt: int, edges, tri_out, ngrid=None, stream=None):
     if st != BS_OK:
         raise BsError(st, "bs_counts_noalloc failed (sizes beyond nt <= 1024, nbins <= 32 are "
                           "rejected)")
+
+
+class Ensemble:
+    """bs_mc_*: batched Monte Carlo over shape groups.
+
+    groups: list of dicts with keys nt, nchan, edges, batch (and optionally
+    fft_m, norm_A, r, rprime, dnu_c).  All groups use the split-BF16 path."""
+
+    def __init__(self, groups, tiles_per_sm=None):
+        import torch
+        L = lib()
+        self._L = L
+        n = len(groups)
+        descs = (PlanDesc * n)()
+        self._edges = []
+        for g, spec in enumerate(groups):
+            e = [float(x) for x in spec["edges"]]
+            arr = (ctypes.c_double * len(e))(*e)
+            self._edges.append(arr)
+            descs[g] = PlanDesc(spec["nt"], spec["nchan"], len(e) - 1, arr, spec.get("fft_m", 0),
+                                PREC_SPLIT_BF16, spec["batch"], spec.get("norm_A", 1.0),
+                                spec.get("r", 1.0), spec.get("rprime", 1.0), spec.get("dnu_c", 1.0))
+        h = ctypes.c_void_p()
+        st = L.bs_mc_create(descs, n, ctypes.byref(h))
+        if st != BS_OK:
+            raise BsError(st, L.bs_last_error(None).decode())
+        self._h = h
+        self.groups = [dict(g) for g in groups]
+        for g, spec in enumerate(self.groups):
+            info = (ctypes.c_int64 * 6)()
+            self._check(L.bs_mc_info(h, g, info, 6))
+            spec["M"], spec["ntrip"] = info[0], info[1]
+        if tiles_per_sm is not None:
+            self._check(L.bs_mc_set_tuning(h, int(tiles_per_sm)))
+        self._torch = torch
+
+    def _check(self, st):
+        if st != BS_OK:
+            raise BsError(st, self._L.bs_mc_last_error(self._h).decode())
+
+    def set_input(self, g, vis):
+        """bs_mc_set_input: vis is a complex64 CUDA tensor [batch, nchan, nt, nt]
+        that the caller keeps alive and refills before each run."""
+        spec = self.groups[g]
+        want = (spec["batch"], spec["nchan"], spec["nt"], spec["nt"])
+        if tuple(vis.shape) != want:
+            raise ValueError(f"group {g} expects {want}, got {tuple(vis.shape)}")
+        self._inputs = getattr(self, "_inputs", {})
+        self._inputs[g] = vis
+        self._check(self._L.bs_mc_set_input(self._h, g, _dptr(vis)))
+
+    def autotune(self, cache_path=None, stream=None):
+        """bs_mc_autotune: returns the chosen tiles-per-SM target."""
+        c = ctypes.c_int()
+        path = None if cache_path is None else str(cache_path).encode()
+        self._check(self._L.bs_mc_autotune(self._h, path, ctypes.byref(c), _stream_ptr(stream)))
+        return c.value
+
+    def run(self, use_graph=True, stream=None):
+        self._check(self._L.bs_mc_run(self._h, 1 if use_graph else 0, _stream_ptr(stream)))
+
+    def reset(self, stream=None):
+        self._check(self._L.bs_mc_reset(self._h, _stream_ptr(stream)))
+
+    def stats(self, g, which=0, stream=None):
+        """(mean, var, realisations) of group g: which=0 collapsed plane, 1 = 3D BS."""
+        torch = self._torch
+        spec = self.groups[g]
+        nc, nt_ = spec["nchan"], spec["ntrip"]
+        shape = (nt_, 2 * nc - 1, 2 * nc - 1) if which == 0 else (nt_, nc, nc)
+        mean = torch.empty(shape, dtype=torch.float64, device="cuda")
+        var = torch.empty(shape, dtype=torch.float64, device="cuda")
+        n = ctypes.c_int64()
+        self._check(self._L.bs_mc_stats(self._h, g, which, _dptr(mean), _dptr(var),
+                                        ctypes.byref(n), _stream_ptr(stream)))
+        torch.cuda.synchronize()
+        return mean.cpu().numpy(), var.cpu().numpy(), n.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.bs_mc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -58,34 +58,60 @@ struct ContractArgs {
   long long dsum_bstride;  // ntrip*(2nc-1)^2
 };
 
-// A tensor-core contraction tile: ring pair, pair rectangle origin, a
-// 128-entry window of the pair's column list, K segment.
+// A tensor-core contraction tile: shape group, realisation, ring pair, pair
+// rectangle origin, a 128-entry window of the pair's column list, K segment.
 struct TcTile {
+  int group, b;
   int ri, rj;
   int nu1_0, nu2_0;
   int col_off, ncol, col0;
   int kseg;
+  int pad[2];
 };
 
-struct TcArgs {
+// Per shape group (one plan): where its fields, lists and outputs live.
+struct TcGroup {
   const float *F;          // FP32 fields (pair operand source)
   long long fstride;       // M*M
   long long bstride;       // nf*M*M
   int nf, batch, M2, Kpad, nc;
-  const ColEntry *cols;    // per ring pair: runs of fields (l, nu3), padded to multiples of 8
-  const TcTile *tiles;
-  int ntiles;
-  int nu1_hi, nu2_hi;
+  int nu1_hi, nu2_hi;      // block upper bounds (pairs beyond are skipped)
   int kseg_len;
+  const ColEntry *cols;    // per ring pair: runs of fields (l, nu3), padded to multiples of 8
   const double *tnorm;
   double *out_full;
   long long full_bstride;
   double *dsum;
   long long dsum_bstride;
+};
+
+struct TcArgs {
+  const TcGroup *groups;   // device
+  const void *maps;        // device: 2 CUtensorMap (hi, lo) per group, 64-byte aligned
+  const TcTile *tiles;     // device
+  int ntiles;
   int *err;                // device error word: 1 = a bounded wait gave up
   long long wait_limit_ns;
   int stall_test;          // failure injection: the MMA thread waits on a barrier nobody arrives at
 };
+
+// Set a kernel's dynamic shared-memory limit to the device's opt-in maximum,
+// once per process (so that launches can be captured in CUDA graphs).
+template <class K>
+inline cudaError_t smem_optin_once(K kernel) {
+  static cudaError_t done = cudaErrorNotReady;
+  if (done == cudaErrorNotReady) {
+    int dev = 0, mx = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    done = cudaFuncGetAttributes(&fa, kernel);
+    if (done == cudaSuccess)  // dynamic + static shared memory must fit the opt-in limit
+      done = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  mx - (int)fa.sharedSizeBytes);
+  }
+  return done;
+}
 
 // ---- kernels / launchers (each returns cudaGetLastError after launch) ----
 cudaError_t launch_colpass(const GridGeom &g, const float2 *vis, const float *ngrid,
@@ -113,9 +139,7 @@ cudaError_t launch_bs3d(const double *dsum, const long long *nnu, const double *
                         const float2 *twN, const Radices &radN, double scale,
                         cudaStream_t s);
 int tc_smem_bytes();
-cudaError_t launch_contract_tc(const struct CUtensorMap_st &map_hi,
-                               const struct CUtensorMap_st &map_lo, const TcArgs &a, int nsm,
-                               cudaStream_t s);
+cudaError_t launch_contract_tc(const TcArgs &a, int nsm, cudaStream_t s);
 cudaError_t launch_hermitian_check(const float2 *vis, int batch, int nc, int nt,
                                    const int8_t *label, float *maxdiff, float *maxabs,
                                    cudaStream_t s);

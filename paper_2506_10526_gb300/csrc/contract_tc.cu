@@ -160,9 +160,7 @@ __device__ __forceinline__ void split2(float v0, float v1, uint32_t &hi, uint32_
   lo = *reinterpret_cast<uint32_t *>(&l);
 }
 
-__global__ void __launch_bounds__(NTHREADS, 1)
-    k_contract_tc(const __grid_constant__ CUtensorMap map_hi,
-                  const __grid_constant__ CUtensorMap map_lo, TcArgs a) {
+__global__ void __launch_bounds__(NTHREADS, 1) k_contract_tc(const __grid_constant__ TcArgs a) {
   extern __shared__ unsigned char smem_dyn[];
   unsigned char *sm = reinterpret_cast<unsigned char *>(
       (reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
@@ -200,7 +198,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const long long limit = a.wait_limit_ns;
-  const int ntot = a.ntiles * a.batch;
+  const int ntot = a.ntiles;
+  const CUtensorMap *maps = reinterpret_cast<const CUtensorMap *>(a.maps);
 
   auto fail = [&]() {
     *abort_flag = 1;
@@ -210,21 +209,20 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer (A)
     if (lane == 0) {
-      asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&map_hi) : "memory");
-      asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&map_lo) : "memory");
       uint32_t it = 0;
       int armed[STAGES] = {0, 0};
       for (int gt = blockIdx.x; gt < ntot; gt += gridDim.x) {
-        const TcTile t = a.tiles[gt % a.ntiles];
-        const int b = gt / a.ntiles;
+        const TcTile t = a.tiles[gt];
+        const TcGroup &G = a.groups[t.group];
+        const CUtensorMap *map_hi = maps + 2 * t.group, *map_lo = map_hi + 1;
         int rowc[NGROUP];
         for (int g = 0; g < NGROUP; ++g) {
           const int e = t.col0 + g * GROUP;
           int f = -1;
-          if (e < t.ncol) f = a.cols[t.col_off + e].field;
-          rowc[g] = f >= 0 ? b * a.nf + f : a.batch * a.nf;  // out of range: TMA fills zeros
+          if (e < t.ncol) f = G.cols[t.col_off + e].field;
+          rowc[g] = f >= 0 ? t.b * G.nf + f : G.batch * G.nf;  // out of range: TMA fills zeros
         }
-        const int k0 = t.kseg * a.kseg_len, k1 = min(a.Kpad, k0 + a.kseg_len);
+        const int k0 = t.kseg * G.kseg_len, k1 = min(G.Kpad, k0 + G.kseg_len);
         for (int kc = k0; kc < k1; kc += KC, ++it) {
           const int s = it & 1;
           const uint32_t ph = (it >> 1) & 1;
@@ -237,8 +235,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           ++armed[s];
           const uint32_t dh = sA + s * 2 * A_BYTES, dl = dh + A_BYTES;
           for (int g = 0; g < NGROUP; ++g) {
-            tma_load_2d(dh + g * GROUP * 64, &map_hi, kc, rowc[g], a_full(s));
-            tma_load_2d(dl + g * GROUP * 64, &map_lo, kc, rowc[g], a_full(s));
+            tma_load_2d(dh + g * GROUP * 64, map_hi, kc, rowc[g], a_full(s));
+            tma_load_2d(dl + g * GROUP * 64, map_lo, kc, rowc[g], a_full(s));
           }
         }
       }
@@ -259,8 +257,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (!mbar_wait(stall_bar, 0, limit, abort_flag)) fail();
       }
       for (int gt = blockIdx.x; gt < ntot; gt += gridDim.x, ++tc) {
-        const TcTile t = a.tiles[gt % a.ntiles];
-        const int k0 = t.kseg * a.kseg_len, k1 = min(a.Kpad, k0 + a.kseg_len);
+        const TcTile t = a.tiles[gt];
+        const TcGroup &G = a.groups[t.group];
+        const int k0 = t.kseg * G.kseg_len, k1 = min(G.Kpad, k0 + G.kseg_len);
         const int nst = (k1 - k0) / KC;
         bool ok = !*abort_flag;
         if (ok && !mbar_wait(acc_empty, (tc & 1) ^ 1, limit, abort_flag)) {
@@ -324,22 +323,26 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     int *nseg_s = reinterpret_cast<int *>(sm + OFF_MISC + 8);
     int *total_s = reinterpret_cast<int *>(sm + OFF_MISC + 12);
     float *red = reinterpret_cast<float *>(sm + OFF_B);
-    // compute mapping: lane -> (a-pair ap, b-quad bq, k-chunk kc); warp covers nu1 rows 4pw..4pw+3
+    // compute mapping: lane -> (a-pair ap, b-offset bq, k-chunk kcq); warp covers nu1 rows
+    // 4pw..4pw+3; a lane takes nu2 = bq + 4y (y = 0..3).  Within each quarter-warp the raw
+    // rows read differ by one row (4 banks apart with the 36-float stride) and the pair
+    // rows stored alternate in parity, so loads and swizzled stores are conflict-free.
     const int kcq = lane & 3, bq = (lane >> 2) & 3, ap = lane >> 4;
     uint32_t it = 0, tc = 0;
     for (int gt = blockIdx.x; gt < ntot; gt += gridDim.x, ++tc) {
-      const TcTile t = a.tiles[gt % a.ntiles];
-      const int b = gt / a.ntiles;
-      const float *Fb = a.F + (long long)b * a.bstride;
-      const int k0 = t.kseg * a.kseg_len, k1 = min(a.Kpad, k0 + a.kseg_len);
+      const TcTile t = a.tiles[gt];
+      const TcGroup &G = a.groups[t.group];
+      const int b = t.b;
+      const float *Fb = G.F + (long long)b * G.bstride;
+      const int k0 = t.kseg * G.kseg_len, k1 = min(G.Kpad, k0 + G.kseg_len);
       // raw rows of this warp: r < 4 -> F_i[nu1_0 + 4pw + r], r >= 4 -> F_j[nu2_0 + r - 4]
       auto row_ptr = [&](int r) -> const float * {
         if (r < 4) {
           const int nu1 = t.nu1_0 + 4 * pw + r;
-          return nu1 < a.nu1_hi ? Fb + ((long long)t.ri * a.nc + nu1) * a.fstride : nullptr;
+          return nu1 < G.nu1_hi ? Fb + ((long long)t.ri * G.nc + nu1) * G.fstride : nullptr;
         }
         const int nu2 = t.nu2_0 + r - 4;
-        return nu2 < a.nu2_hi ? Fb + ((long long)t.rj * a.nc + nu2) * a.fstride : nullptr;
+        return nu2 < G.nu2_hi ? Fb + ((long long)t.rj * G.nc + nu2) * G.fstride : nullptr;
       };
       // 20 rows x 8 float4 = 160 float4 per warp per stage: 5 per lane
       float4 pre[5];
@@ -350,7 +353,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           const int r = idx >> 3, c4 = idx & 7;
           const float *p = row_ptr(r);
           const int k = kc + 4 * c4;
-          pre[q] = (p && k < a.M2) ? __ldg(reinterpret_cast<const float4 *>(p + k))
+          pre[q] = (p && k < G.M2) ? __ldg(reinterpret_cast<const float4 *>(p + k))
                                    : make_float4(0.f, 0.f, 0.f, 0.f);
         }
       };
@@ -383,7 +386,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           }
 #pragma unroll
           for (int y = 0; y < 4; ++y) {
-            const float *rp = raw + (4 + 4 * bq + y) * RAW_STRIDE + 8 * kcq;
+            const float *rp = raw + (4 + bq + 4 * y) * RAW_STRIDE + 8 * kcq;
             const float4 u = *reinterpret_cast<const float4 *>(rp);
             const float4 v = *reinterpret_cast<const float4 *>(rp + 4);
             fj[y][0] = u.x; fj[y][1] = u.y; fj[y][2] = u.z; fj[y][3] = u.w;
@@ -395,7 +398,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           for (int x = 0; x < 2; ++x)
 #pragma unroll
             for (int y = 0; y < 4; ++y) {
-              const int p = (4 * pw + 2 * ap + x) * P2 + 4 * bq + y;  // pair row
+              const int p = (4 * pw + 2 * ap + x) * P2 + bq + 4 * y;  // pair row
               uint4 H, L;
               split2(fi[x][0] * fj[y][0], fi[x][1] * fj[y][1], H.x, L.x);
               split2(fi[x][2] * fj[y][2], fi[x][3] * fj[y][3], H.y, L.y);
@@ -426,14 +429,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         while (m < MROWS) {
           const int e = t.col0 + m;
           if (e >= t.ncol) break;
-          const ColEntry c0 = a.cols[t.col_off + e];
+          const ColEntry c0 = G.cols[t.col_off + e];
           if (c0.field < 0) {
             ++m;
             continue;
           }
           int lo = c0.nu3, hi = c0.nu3, q = m;
           while (q + 1 < MROWS && t.col0 + q + 1 < t.ncol) {
-            const ColEntry cn = a.cols[t.col_off + t.col0 + q + 1];
+            const ColEntry cn = G.cols[t.col_off + t.col0 + q + 1];
             if (cn.field >= 0 && cn.trip != c0.trip) break;
             ++q;
             if (cn.field >= 0) {
@@ -445,7 +448,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           if (ns < MAX_SEG) seginfo[ns] = make_int4(base, E, c0.trip, hi);
           for (int r = m; r <= q; ++r) {
             const int ee = t.col0 + r;
-            const ColEntry cr = a.cols[t.col_off + ee];
+            const ColEntry cr = G.cols[t.col_off + ee];
             if (cr.field < 0)
               rowinfo[r] = make_int4(0, 0, cr.trip, -1);
             else if (ns >= MAX_SEG)  // no reduction slot: direct atomics (total > RED_CAP)
@@ -463,7 +466,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       }
       asm volatile("bar.sync 1, 256;" ::: "memory");
       const int total = *total_s;
-      const bool use_red = a.dsum != nullptr && total <= RED_CAP;
+      const bool use_red = G.dsum != nullptr && total <= RED_CAP;
       if (use_red)
         for (int q = ptid; q < total; q += 256) red[q] = 0.f;
       asm volatile("bar.sync 1, 256;" ::: "memory");
@@ -472,8 +475,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const int m = 32 * quad + lane;
       const int4 ri = rowinfo[m];
       const bool row_ok = ri.w >= 0;
-      const double tn = (a.out_full && row_ok) ? a.tnorm[ri.z] : 0.0;
-      const int n2 = 2 * a.nc - 1;
+      const double tn = (G.out_full && row_ok) ? G.tnorm[ri.z] : 0.0;
+      const int n2 = 2 * G.nc - 1;
       for (int ch = 0; ch < 256 / 32; ++ch) {
         uint32_t v[32];
         if (ok) tc_ld32(tmem + ((uint32_t)(32 * quad) << 16) + half * 256 + ch * 32, v);
@@ -483,22 +486,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           const int p = half * 256 + ch * 32 + j;
           const int pa = p >> 4, pb = p & 15;
           const int nu1 = t.nu1_0 + pa, nu2 = t.nu2_0 + pb;
-          if (nu1 >= a.nu1_hi || nu2 >= a.nu2_hi) continue;
+          if (nu1 >= G.nu1_hi || nu2 >= G.nu2_hi) continue;
           const float s = __uint_as_float(v[j]);
-          if (a.dsum) {
+          if (G.dsum) {
             if (use_red) {
               atomicAdd(red + ri.x + (pa - pb) * ri.y + pb, s);
             } else {
-              const long long o = (long long)b * a.dsum_bstride +
-                                  ((long long)ri.z * n2 + (nu1 - ri.w + a.nc - 1)) * n2 +
-                                  (nu2 - ri.w + a.nc - 1);
-              atomicAdd(a.dsum + o, (double)s);
+              const long long o = (long long)b * G.dsum_bstride +
+                                  ((long long)ri.z * n2 + (nu1 - ri.w + G.nc - 1)) * n2 +
+                                  (nu2 - ri.w + G.nc - 1);
+              atomicAdd(G.dsum + o, (double)s);
             }
           }
-          if (a.out_full) {
-            const long long o = (long long)b * a.full_bstride +
-                                (((long long)ri.z * a.nc + nu1) * a.nc + nu2) * a.nc + ri.w;
-            atomicAdd(a.out_full + o, (double)s * tn);
+          if (G.out_full) {
+            const long long o = (long long)b * G.full_bstride +
+                                (((long long)ri.z * G.nc + nu1) * G.nc + nu2) * G.nc + ri.w;
+            atomicAdd(G.out_full + o, (double)s * tn);
           }
         }
       }
@@ -519,9 +522,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           const int d = dd - (P2 - 1) + t.nu1_0 - t.nu2_0;  // nu1 - nu2
           const int d2 = e2 + t.nu2_0 - si.w;                // nu2 - nu3
           const int d1 = d + d2;
-          const long long o = (long long)b * a.dsum_bstride +
-                              ((long long)si.z * n2 + (d1 + a.nc - 1)) * n2 + (d2 + a.nc - 1);
-          atomicAdd(a.dsum + o, (double)v);
+          const long long o = (long long)b * G.dsum_bstride +
+                              ((long long)si.z * n2 + (d1 + G.nc - 1)) * n2 + (d2 + G.nc - 1);
+          atomicAdd(G.dsum + o, (double)v);
         }
       }
       asm volatile("bar.sync 1, 256;" ::: "memory");
@@ -538,15 +541,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
 int tc_smem_bytes() { return SMEM_BYTES; }
 
-cudaError_t launch_contract_tc(const CUtensorMap &map_hi, const CUtensorMap &map_lo,
-                               const TcArgs &a, int nsm, cudaStream_t s) {
+cudaError_t launch_contract_tc(const TcArgs &a, int nsm, cudaStream_t s) {
   if (a.ntiles == 0) return cudaSuccess;
   cudaError_t e =
-      cudaFuncSetAttribute(k_contract_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+      smem_optin_once(k_contract_tc);
   if (e != cudaSuccess) return e;
-  const long long ntot = (long long)a.ntiles * a.batch;
-  const int grid = (int)std::min<long long>(ntot, nsm);
-  k_contract_tc<<<grid, NTHREADS, SMEM_BYTES, s>>>(map_hi, map_lo, a);
+  const int grid = std::min(a.ntiles, nsm);
+  k_contract_tc<<<grid, NTHREADS, SMEM_BYTES, s>>>(a);
   return cudaGetLastError();
 }
 

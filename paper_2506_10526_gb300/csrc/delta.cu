@@ -184,10 +184,9 @@ cudaError_t launch_bs3d(const double *dsum, const long long *nnu, const double *
                         double *out, int batch, int ntrip, int nc, const float2 *twN,
                         const Radices &radN, double scale, cudaStream_t s) {
   const size_t smem = (size_t)3 * nc * sizeof(float2);
-  cudaError_t e = cudaFuncSetAttribute(k_bs3d_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = smem_optin_once(k_bs3d_rows);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_bs3d_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = smem_optin_once(k_bs3d_cols);
   if (e != cudaSuccess) return e;
   const int threads = nc >= 256 ? 256 : (nc >= 64 ? 64 : 32);
   dim3 grid(nc, ntrip, batch);

@@ -273,8 +273,7 @@ cudaError_t launch_colpass(const GridGeom &g, const float2 *vis, const float *ng
                        (size_t)200 * 1024)
     UB /= 2;
   const size_t smem = (size_t)(g.M + 2 * UB * g.M + g.nt * UB) * sizeof(float2) + (size_t)g.nt * UB;
-  cudaError_t e = cudaFuncSetAttribute(k_colpass, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = smem_optin_once(k_colpass);
   if (e != cudaSuccess) return e;
   dim3 grid((g.UC + UB - 1) / UB, g.nc, g.batch);
   k_colpass<<<grid, 256, smem, s>>>(g, UB, vis, ngrid, valid, label, uext, twM, radM, G);
@@ -287,8 +286,7 @@ cudaError_t launch_rowpass(const GridGeom &g, const float2 *G, const uint8_t *va
   int RPB = 8;
   while (RPB > 1 && (size_t)(2 * RPB * g.M + g.M) * sizeof(float2) > (size_t)96 * 1024) RPB /= 2;
   const size_t smem = (size_t)(2 * RPB * g.M + g.M) * sizeof(float2);
-  cudaError_t e = cudaFuncSetAttribute(k_rowpass, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = smem_optin_once(k_rowpass);
   if (e != cudaSuccess) return e;
   dim3 grid((g.M / 2 + RPB - 1) / RPB, g.nb * g.nc, g.batch);
   k_rowpass<<<grid, 256, smem, s>>>(g, RPB, G, valid, uext, twM, radM, F, Fhi, Flo);
@@ -308,8 +306,7 @@ cudaError_t launch_counts(int nt, int nb, const int8_t *label, const int *cells,
   const size_t base = (size_t)ntrip * sizeof(unsigned int) + (size_t)nb * nb * nb * sizeof(int);
   const int in_smem = base + (size_t)nt * nt <= (size_t)160 * 1024;
   const size_t smem = base + (in_smem ? (size_t)nt * nt : 0);
-  cudaError_t e = cudaFuncSetAttribute(k_counts, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = smem_optin_once(k_counts);
   if (e != cudaSuccess) return e;
   dim3 grid((ncells + kCountP1 - 1) / kCountP1);
   k_counts<<<grid, 256, smem, s>>>(nt, nb, label, cells, ncells, trip_of, T, ntrip, in_smem);

@@ -10,7 +10,7 @@
 #include <string>
 #include <vector>
 
-#include "bs_internal.h"
+#include "plan_internal.h"
 
 using namespace bsi;
 
@@ -62,56 +62,9 @@ std::vector<float2> twiddles(int n) {
   return tw;
 }
 
-struct WsLayout {
-  size_t label, efflabel, cells, uext, tripof, valid, twM, twN, tnorm, T, nnu, cols, ptiles, tctiles,
-      G, F, Fhi, Flo, dsum, tmp3d, herm, err, total;
-};
-
-typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
-                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
-                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
 }  // namespace
 
-struct bs_plan_s {
-  bs_plan_desc d{};
-  std::vector<double> edges;
-  int nt = 0, nc = 0, nb = 0, M = 0, UC = 0, batch = 1, ntrip = 0, nf = 0;
-  int device = 0;
-  double normA = 1, scale3d = 1;
-  Radices radM, radN;
-  std::vector<int8_t> label;     // [nt*nt]
-  std::vector<int> cells;        // packed (u + 32768) | (v + 32768) << 16 of binned cells
-  std::vector<int> uext;         // [nb]
-  std::vector<int> trips;        // [ntrip][3]
-  std::vector<int> trip_of;      // [nb^3] -> trip index of sorted (i<=j<=l), else -1
-  std::vector<long long> T;      // [ntrip] closed-triangle counts
-  std::vector<double> tnorm;     // [ntrip]
-  std::vector<uint8_t> valid;    // [nc]
-  std::vector<long long> nnu;    // [(2nc-1)^2] accumulated unfolded sampling
-  bool counts_ready = false, counts_default = false, nnu_dirty = true, loaded = false;
-  bool sticky = false;
-  std::string err = "no error";
-  // workspace
-  WsLayout L{};
-  unsigned char *ws = nullptr;
-  bool ws_owned = false;
-  size_t max_cols = 0, max_ptiles = 0, max_tctiles = 0;
-  std::vector<ColEntry> h_cols;
-  std::vector<PairTile> h_ptiles;
-  std::vector<TcTile> h_tctiles;
-  CUtensorMap map_hi{}, map_lo{};
-  bool maps_ready = false;
-  int nsm = 152;
-
-  template <class T_>
-  T_ *at(size_t off) const {
-    return reinterpret_cast<T_ *>(ws + off);
-  }
-};
-
-namespace {
+namespace bsi {
 
 bs_status fail(bs_plan p, bs_status s, const std::string &msg) {
   if (p)
@@ -164,6 +117,8 @@ void compute_layout(bs_plan p) {
   L.tmp3d = take((size_t)p->batch * p->ntrip * (size_t)p->nc * p->nc * sizeof(float2));
   L.herm = take(2 * sizeof(float));
   L.err = take(sizeof(int));
+  L.maps = take(2 * sizeof(CUtensorMap));
+  L.tcgroup = take(sizeof(TcGroup));
   L.total = o;
 }
 
@@ -220,7 +175,7 @@ bs_status check_device_error(bs_plan p, cudaStream_t s) {
 
 // Tensor maps over the BF16 hi / lo field arrays: rows = batch * nf fields,
 // inner dimension = M^2 pixels; boxes of 32 pixels x 8 fields, 64-byte swizzle.
-bs_status ensure_tensor_maps(bs_plan p) {
+bs_status ensure_tensor_maps(bs_plan p, cudaStream_t s) {
   if (p->maps_ready) return BS_OK;
   void *fn = nullptr;
   cudaDriverEntryPointQueryResult q;
@@ -238,13 +193,15 @@ bs_status ensure_tensor_maps(bs_plan p) {
   cuuint32_t estr[2] = {1, 1};
   for (int w = 0; w < 2; ++w) {
     void *base = w == 0 ? (void *)p->at<uint16_t>(p->L.Fhi) : (void *)p->at<uint16_t>(p->L.Flo);
-    CUresult r = enc(w == 0 ? &p->map_hi : &p->map_lo, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base,
-                     dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                     CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r = enc(&p->maps[w], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box,
+                     estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS)
       return fail(p, BS_ERR_CUDA, "cuTensorMapEncodeTiled failed with code " + std::to_string((int)r));
   }
+  BS_CUDA(cudaMemcpyAsync(p->at<unsigned char>(p->L.maps), p->maps, sizeof(p->maps),
+                          cudaMemcpyHostToDevice, s));
+  BS_CUDA(cudaStreamSynchronize(s));
   p->maps_ready = true;
   return BS_OK;
 }
@@ -354,89 +311,105 @@ bs_status delta_reset(bs_plan p, cudaStream_t s) {
   return BS_OK;
 }
 
-// Tensor-core contraction of one channel block (split BF16).
-bs_status mabs_tc(bs_plan p, const int *blk, double *out_full, int accumulate,
-                  long long full_bstride, cudaStream_t s) {
-  bs_status st = ensure_tensor_maps(p);
-  if (st != BS_OK) return st;
+TcGroup build_tc_work(bs_plan p, const int *blk, int group, std::vector<ColEntry> &cols,
+                      const ColEntry *cols_dev, std::vector<TcTile> &tiles, double *out_full,
+                      int accumulate, int min_tiles) {
   const int nc = p->nc, nb = p->nb;
-  const WsLayout &L = p->L;
-  p->h_cols.clear();
-  p->h_tctiles.clear();
   const int w3 = blk[5] - blk[4];
   const int run = ((w3 + 7) / 8) * 8;
   const int M2 = p->M * p->M;
   const int Kpad = ((M2 + 31) / 32) * 32;
+  TcGroup G{};
+  G.F = p->at<float>(p->L.F);
+  G.fstride = M2;
+  G.bstride = (long long)p->nf * M2;
+  G.nf = p->nf;
+  G.batch = p->batch;
+  G.M2 = M2;
+  G.Kpad = Kpad;
+  G.nc = nc;
+  G.nu1_hi = blk[1];
+  G.nu2_hi = blk[3];
+  G.cols = cols_dev;
+  G.tnorm = p->at<double>(p->L.tnorm);
+  G.out_full = out_full;
+  G.full_bstride = (long long)p->ntrip * nc * nc * nc;
+  G.dsum = accumulate ? p->at<double>(p->L.dsum) : nullptr;
+  G.dsum_bstride = (long long)p->ntrip * (2 * nc - 1) * (2 * nc - 1);
+  G.kseg_len = Kpad;
+  if (w3 == 0 || blk[1] <= blk[0] || blk[3] <= blk[2]) return G;
   struct PairList {
     int i, j, off, n;
   };
   std::vector<PairList> pl;
   for (int i = 0; i < nb; ++i)
     for (int j = i; j < nb; ++j) {
-      const int off = (int)p->h_cols.size();
+      const int off = (int)cols.size();
       for (int l = j; l < nb; ++l) {
         const int t = p->trip_of[((size_t)i * nb + j) * nb + l];
         if (p->T[t] <= 0) continue;
         for (int q = 0; q < run; ++q) {
           const int n3 = blk[4] + q;
-          p->h_cols.push_back(ColEntry{q < w3 ? l * nc + n3 : -1, t, n3, 0});
+          cols.push_back(ColEntry{q < w3 ? l * nc + n3 : -1, t, n3, 0});
         }
       }
-      const int n = (int)p->h_cols.size() - off;
+      const int n = (int)cols.size() - off;
       if (n > 0) pl.push_back(PairList{i, j, off, n});
     }
   const int n1b = (blk[1] - blk[0] + 31) / 32, n2b = (blk[3] - blk[2] + 15) / 16;
   long long base_tiles = 0;
   for (const PairList &q : pl) base_tiles += (long long)n1b * n2b * ((q.n + 127) / 128);
-  if (base_tiles == 0 || w3 == 0) return BS_OK;
-  // split K until every SM has a few tiles
+  base_tiles *= p->batch;
+  // split K until the launch has min_tiles tiles
   int nk = 1;
-  while (base_tiles * nk * p->batch < 2LL * p->nsm && nk < 64 && Kpad / (32 * nk * 2) >= 8) nk *= 2;
-  const int kseg_len = ((Kpad / 32 + nk - 1) / nk) * 32;
-  nk = (Kpad + kseg_len - 1) / kseg_len;
-  for (const PairList &q : pl)
-    for (int c0 = 0; c0 < q.n; c0 += 128)
-      for (int a1 = 0; a1 < n1b; ++a1)
-        for (int a2 = 0; a2 < n2b; ++a2)
-          for (int k = 0; k < nk; ++k)
-            p->h_tctiles.push_back(TcTile{q.i, q.j, blk[0] + 32 * a1, blk[2] + 16 * a2, q.off, q.n,
-                                          c0, k});
+  while (base_tiles * nk < min_tiles && nk < 64 && Kpad / (32 * nk * 2) >= 8) nk *= 2;
+  G.kseg_len = ((Kpad / 32 + nk - 1) / nk) * 32;
+  nk = (Kpad + G.kseg_len - 1) / G.kseg_len;
+  for (int b = 0; b < p->batch; ++b)
+    for (const PairList &q : pl)
+      for (int c0 = 0; c0 < q.n; c0 += 128)
+        for (int a1 = 0; a1 < n1b; ++a1)
+          for (int a2 = 0; a2 < n2b; ++a2)
+            for (int k = 0; k < nk; ++k)
+              tiles.push_back(TcTile{group, b, q.i, q.j, blk[0] + 32 * a1, blk[2] + 16 * a2, q.off,
+                                     q.n, c0, k, {0, 0}});
+  return G;
+}
+
+// Tensor-core contraction of one channel block of one plan (split BF16).
+bs_status mabs_tc(bs_plan p, const int *blk, double *out_full, int accumulate, cudaStream_t s) {
+  bs_status st = ensure_tensor_maps(p, s);
+  if (st != BS_OK) return st;
+  const WsLayout &L = p->L;
+  p->h_cols.clear();
+  p->h_tctiles.clear();
+  TcGroup G = build_tc_work(p, blk, 0, p->h_cols, p->at<ColEntry>(L.cols), p->h_tctiles, out_full,
+                            accumulate, 2 * p->nsm);
+  if (p->h_tctiles.empty()) return BS_OK;
   if (p->h_tctiles.size() > p->max_tctiles || p->h_cols.size() > p->max_cols)
     return fail(p, BS_ERR_UNSUPPORTED, "tensor-core tile list exceeds the plan's capacity");
   BS_CUDA(cudaMemcpyAsync(p->at<ColEntry>(L.cols), p->h_cols.data(),
                           p->h_cols.size() * sizeof(ColEntry), cudaMemcpyHostToDevice, s));
   BS_CUDA(cudaMemcpyAsync(p->at<TcTile>(L.tctiles), p->h_tctiles.data(),
                           p->h_tctiles.size() * sizeof(TcTile), cudaMemcpyHostToDevice, s));
+  p->h_group = G;
+  BS_CUDA(cudaMemcpyAsync(p->at<TcGroup>(L.tcgroup), &p->h_group, sizeof(TcGroup),
+                          cudaMemcpyHostToDevice, s));
   TcArgs a{};
-  a.F = p->at<float>(L.F);
-  a.fstride = M2;
-  a.bstride = (long long)p->nf * M2;
-  a.nf = p->nf;
-  a.batch = p->batch;
-  a.M2 = M2;
-  a.Kpad = Kpad;
-  a.nc = nc;
-  a.cols = p->at<ColEntry>(L.cols);
+  a.groups = p->at<TcGroup>(L.tcgroup);
+  a.maps = p->at<unsigned char>(L.maps);
   a.tiles = p->at<TcTile>(L.tctiles);
   a.ntiles = (int)p->h_tctiles.size();
-  a.nu1_hi = blk[1];
-  a.nu2_hi = blk[3];
-  a.kseg_len = kseg_len;
-  a.tnorm = p->at<double>(L.tnorm);
-  a.out_full = out_full;
-  a.full_bstride = full_bstride;
-  a.dsum = accumulate ? p->at<double>(L.dsum) : nullptr;
-  a.dsum_bstride = (long long)p->ntrip * (2 * nc - 1) * (2 * nc - 1);
   a.err = p->at<int>(L.err);
   a.wait_limit_ns = 2000000000LL;
   const char *inj = std::getenv("BS_INJECT_MMA_STALL");
   a.stall_test = (inj && inj[0] == '1') ? 1 : 0;
   if (a.stall_test) a.wait_limit_ns = 50000000LL;
-  BS_CUDA(launch_contract_tc(p->map_hi, p->map_lo, a, p->nsm, s));
+  BS_CUDA(launch_contract_tc(a, p->nsm, s));
   return BS_OK;
 }
 
-}  // namespace
+}  // namespace bsi
 
 extern "C" {
 
@@ -691,7 +664,7 @@ bs_status bs_mabs(bs_plan p, const int32_t *block, double *out_full, int accumul
   const long long full_bstride = (long long)p->ntrip * nc * nc * nc;
   if (out_full) BS_CUDA(launch_full_fill(out_full, full_bstride, p->batch, p->ntrip, nc, blk, 0.0, s));
   if (p->d.precision == BS_PREC_SPLIT_BF16) {
-    st = mabs_tc(p, blk, out_full, accumulate, full_bstride, s);
+    st = mabs_tc(p, blk, out_full, accumulate, s);
     if (st != BS_OK) return st;
   } else {
     // work list: ring pairs (i <= j) x column tiles over (l, nu3), T(i,j,l) > 0, nu3 valid

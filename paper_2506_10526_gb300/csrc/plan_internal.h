@@ -1,0 +1,84 @@
+// Internal plan state shared by the libbs translation units.
+#pragma once
+
+#include <cuda.h>
+
+#include <string>
+#include <vector>
+
+#include "bs_internal.h"
+
+namespace bsi {
+
+struct WsLayout {
+  size_t label, efflabel, cells, uext, tripof, valid, twM, twN, tnorm, T, nnu, cols, ptiles, tctiles,
+      G, F, Fhi, Flo, dsum, tmp3d, herm, err, maps, tcgroup, total;
+};
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+
+}  // namespace bsi
+
+using namespace bsi;  // internal header: plan state uses the library types unqualified
+
+struct bs_plan_s {
+  bs_plan_desc d{};
+  std::vector<double> edges;
+  int nt = 0, nc = 0, nb = 0, M = 0, UC = 0, batch = 1, ntrip = 0, nf = 0;
+  int device = 0;
+  double normA = 1, scale3d = 1;
+  Radices radM, radN;
+  std::vector<int8_t> label;     // [nt*nt]
+  std::vector<int> cells;        // packed (u + 32768) | (v + 32768) << 16 of binned cells
+  std::vector<int> uext;         // [nb]
+  std::vector<int> trips;        // [ntrip][3]
+  std::vector<int> trip_of;      // [nb^3] -> trip index of sorted (i<=j<=l), else -1
+  std::vector<long long> T;      // [ntrip] closed-triangle counts
+  std::vector<double> tnorm;     // [ntrip]
+  std::vector<uint8_t> valid;    // [nc]
+  std::vector<long long> nnu;    // [(2nc-1)^2] accumulated unfolded sampling
+  bool counts_ready = false, counts_default = false, nnu_dirty = true, loaded = false;
+  bool sticky = false;
+  std::string err = "no error";
+  // workspace
+  WsLayout L{};
+  unsigned char *ws = nullptr;
+  bool ws_owned = false;
+  size_t max_cols = 0, max_ptiles = 0, max_tctiles = 0;
+  std::vector<ColEntry> h_cols;
+  std::vector<PairTile> h_ptiles;
+  std::vector<TcTile> h_tctiles;
+  CUtensorMap maps[2]{};  // hi, lo (host copies; device copies at L.maps)
+  bool maps_ready = false;
+  TcGroup h_group{};
+  int nsm = 152;
+
+  template <class T_>
+  T_ *at(size_t off) const {
+    return reinterpret_cast<T_ *>(ws + off);
+  }
+};
+
+
+namespace bsi {
+// helpers implemented in plan.cu
+bs_status fail(bs_plan p, bs_status s, const std::string &msg);
+bs_status cuda_fail(bs_plan p, cudaError_t e, const char *where);
+bs_status prepare(bs_plan p, cudaStream_t s);
+bs_status run_counts(bs_plan p, const int8_t *lab_dev, cudaStream_t s);
+bs_status ensure_tensor_maps(bs_plan p, cudaStream_t s);
+bs_status check_device_error(bs_plan p, cudaStream_t s);
+void accumulate_block_nnu(bs_plan p, const int *blk);
+bs_status upload_nnu(bs_plan p, cudaStream_t s);
+// Append the tensor-core work of one channel block of plan p (all realisations)
+// as shape group `group`; column entries are appended to cols, tiles to tiles.
+// Returns the group descriptor (device pointers of p, column list offset
+// relative to the concatenated list on the device at cols_dev).
+TcGroup build_tc_work(bs_plan p, const int *blk, int group, std::vector<ColEntry> &cols,
+                      const ColEntry *cols_dev, std::vector<TcTile> &tiles, double *out_full,
+                      int accumulate, int min_tiles);
+}  // namespace bsi

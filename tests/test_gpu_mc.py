@@ -1,0 +1,107 @@
+"""Batched Monte Carlo (bs_mc_*): two shape groups of uneven sizes, several
+runs, per-bin Welford mean and variance of the collapsed plane and the 3D
+bispectrum against numpy statistics of the FP64 oracle evaluated on every
+realisation; graph replay against eager runs."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+GROUPS = [dict(nt=32, nchan=8, edges=list(synth.edges_linear(4, 16)), batch=3),
+          dict(nt=40, nchan=6, edges=list(synth.edges_log(5, 1.5, 19.0)), batch=2)]
+
+
+def _realisation(g, k):
+    spec = GROUPS[g]
+    return synth.sky_visibilities(spec["nt"], spec["nchan"], 7000 + 100 * g + k)
+
+
+def _run_ensemble(runs, use_graph):
+    import torch
+    import paper_2506_10526_gb300 as bs
+    ens = bs.Ensemble(GROUPS)
+    bufs = [torch.empty((s["batch"], s["nchan"], s["nt"], s["nt"]), dtype=torch.complex64,
+                        device="cuda") for s in GROUPS]
+    for g in range(len(GROUPS)):
+        ens.set_input(g, bufs[g])
+    for r in range(runs):
+        for g, spec in enumerate(GROUPS):
+            v = np.stack([_realisation(g, r * spec["batch"] + b) for b in range(spec["batch"])])
+            bufs[g].copy_(torch.from_numpy(v))
+        ens.run(use_graph=use_graph)
+    out = [(ens.stats(g, 0), ens.stats(g, 1)) for g in range(len(GROUPS))]
+    ens.close()
+    return out
+
+
+def test_mc_statistics_match_oracle_and_graph_replay():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    runs = 3
+    eager = _run_ensemble(runs, use_graph=False)
+    graph = _run_ensemble(runs, use_graph=True)
+    for g, spec in enumerate(GROUPS):
+        n = runs * spec["batch"]
+        planes, b3s, abs_planes = [], [], []
+        for k in range(n):
+            vis = _realisation(g, k).astype(np.complex128)
+            res = oracle.mabs_full(vis, spec["edges"])
+            bbar, _ = oracle.collapse_fold(res["B"].real)
+            planes.append(bbar)
+            b3s.append(oracle.delay_dft(bbar, spec["nchan"]).real)
+            babs = oracle.mabs_full(np.abs(vis), spec["edges"])["B"].real
+            abs_planes.append(oracle.collapse_fold(babs)[0])
+        planes, b3s = np.array(planes), np.array(b3s)
+        scale = np.nanmax(np.array(abs_planes), axis=0)
+        for which, ref in ((0, planes), (1, b3s)):
+            (mean_e, var_e, n_e) = eager[g][which]
+            (mean_g, var_g, n_g) = graph[g][which]
+            assert n_e == n and n_g == n
+            want_m = ref.mean(axis=0)
+            want_v = ref.var(axis=0, ddof=1)
+            ok = ~np.isnan(want_m)
+            assert np.array_equal(np.isnan(mean_e), np.isnan(want_m))
+            if which == 0:
+                tol = 1e-3 * scale[ok]
+            else:
+                tol = 1e-3 * np.abs(np.array([oracle.delay_dft(a, spec["nchan"]) for a in abs_planes])).max()
+            assert np.all(np.abs(mean_e[ok] - want_m[ok]) <= tol)
+            dv = np.abs(var_e[ok] - want_v[ok])
+            assert np.all(dv <= 2 * np.sqrt(want_v[ok]) * tol + tol ** 2 + 1e-300)
+            # graph replay runs the same launches
+            np.testing.assert_allclose(mean_g[ok], mean_e[ok], rtol=1e-9,
+                                       atol=1e-12 * np.nanmax(np.abs(mean_e)))
+
+
+def test_mc_autotuner_cache(tmp_path):
+    """The autotuner times its candidates, writes the choice to a JSON cache,
+    and a second ensemble of the same shapes reuses the cached choice;
+    tuning runs do not count as realisations."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import json
+    import paper_2506_10526_gb300 as bs
+    cache = tmp_path / "tune.json"
+    chosen = []
+    for _ in range(2):
+        ens = bs.Ensemble(GROUPS)
+        bufs = []
+        for g, s in enumerate(GROUPS):
+            v = np.stack([_realisation(g, b) for b in range(s["batch"])])
+            bufs.append(torch.from_numpy(v).cuda())
+            ens.set_input(g, bufs[-1])
+        chosen.append(ens.autotune(cache))
+        mean, var, n = ens.stats(0, 0)
+        assert n == 0
+        ens.run()
+        mean, var, n = ens.stats(0, 0)
+        assert n == GROUPS[0]["batch"]
+        ens.close()
+    assert chosen[0] == chosen[1] and chosen[0] in (1, 2, 4, 8, 16)
+    data = json.loads(cache.read_text())
+    assert len(data) == 1 and list(data.values())[0]["tiles_per_sm"] == chosen[0]
