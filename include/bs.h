@@ -214,6 +214,11 @@ bs_status bs_mc_info(bs_mc mc, int group, int64_t *info_host, int n);
  * keeps the buffer alive; registering a different pointer drops the captured
  * graph (it is captured again on the next graph run). */
 bs_status bs_mc_set_input(bs_mc mc, int group, const void *vis_dev);
+/* Channel flags of group g (uint8 [nchan], nonzero = flagged; NULL = none):
+ * flagged channels have W = 0 (Eq. vg), so their triples are undefined and
+ * the collapse and Eq. (dft) use only sampled separations.  Drops prepared
+ * work and the captured graph. */
+bs_status bs_mc_set_flags(bs_mc mc, int group, const uint8_t *flags_host);
 /* Tuning knob chosen by the autotuner: split K until the contraction has at
  * least tiles_per_sm tiles per SM (1..64).  Only before the first run. */
 bs_status bs_mc_set_tuning(bs_mc mc, int tiles_per_sm);
@@ -238,6 +243,56 @@ bs_status bs_mc_reset(bs_mc mc, void *cuda_stream);
  *  BS_ERR_TIMEOUT if a bounded wait gave up. */
 bs_status bs_mc_stats(bs_mc mc, int group, int which, double *mean_dev, double *var_dev,
                       int64_t *realisations_host, void *cuda_stream);
+
+/* ---------------------------------------------------------------------------
+ * Error-bar surrogate (not in the paper, whose error bars are brute Monte
+ * Carlo over 250 realisations, Section 4): a 3-layer MLP
+ *   xn = (x - mu_x)/sd_x; h1 = tanh(W1 xn + b1); h2 = tanh(W2 h1 + b2);
+ *   y = mu_y + sd_y (w3 . h2 + b3)
+ * with BF16 weights (rounded from FP32 masters) and FP32 accumulation,
+ * trained by the library's own forward, backward and Adam kernels on the
+ * per-bin log variances that bs_mc_stats produces.  Monte Carlo remains the
+ * fallback and the judge of its error.  Flat parameter vector (float):
+ *   W1 [w][d] | b1 [w] | W2 [w][w] | b2 [w] | w3 [w] | b3 | mu_x [d] | sd_x [d] | mu_y | sd_y
+ * ------------------------------------------------------------------------- */
+#define BS_MLP_FEATURES 42
+typedef struct bs_mlp_s *bs_mlp;
+
+/* Features of every 3D-bispectrum bin (trip, a, b) of a plan, float
+ * [T_r*nchan*nchan][42] on the device, rows in bs_bs3d order:
+ *  0 log k1, 1 t = k2/k1, 2 mu = (k1^2+k2^2-k3^2)/(2 k1 k2) (Eq. shape), where
+ *    k_n = sqrt(k_perp n^2 + k_par n^2), k_perp = 2 pi Ubar_ring / r (ring-mean
+ *    |U|), k_par a = 2 pi a / (r' nchan dnu_c), k_par 3 = -k_par a - k_par b,
+ *    sorted k1 >= k2 >= k3;
+ *  3 flagged fraction; 4 log T(i,j,l); 5 |k_par a|; 6 |k_par b|;
+ *  7..9 log k_perp of rings i, j, l; 10..41 fraction of channels flagged at
+ *  each position c mod 32 of the coarse bands.
+ * Rows of ring triples without closed triangles are NaN.  Synchronises. */
+bs_status bs_mlp_features(bs_plan plan, const uint8_t *chan_flag_host, float *feat_dev,
+                          void *cuda_stream);
+/* Network with d_in inputs (<= 64) and width hidden units (<= 128), Glorot
+ * initialisation from a SplitMix64 stream of seed.  Allocates device memory. */
+bs_status bs_mlp_create(int d_in, int width, uint64_t seed, bs_mlp *out);
+bs_status bs_mlp_destroy(bs_mlp mlp);
+const char *bs_mlp_last_error(bs_mlp mlp);
+/* Copy the flat parameter vector (see above; n = total length) to the host
+ * (set = 0) or from the host (set = 1, also resets the Adam state). */
+bs_status bs_mlp_params(bs_mlp mlp, float *params_host, int64_t n, int set);
+/* Input and target normalisation from data: x_dev float [n][d_in], t_dev [n]. */
+bs_status bs_mlp_fit_norm(bs_mlp mlp, const float *x_dev, const float *t_dev, int n,
+                          void *cuda_stream);
+/* y_dev[n] = network(x_dev[n][d_in]). */
+bs_status bs_mlp_forward(bs_mlp mlp, const float *x_dev, int n, float *y_dev, void *cuda_stream);
+/* Full-batch loss (mean squared error on the normalised target) and its
+ * gradient w.r.t. the weights and biases (first part of the flat vector),
+ * copied to the host.  Synchronises. */
+bs_status bs_mlp_grad(bs_mlp mlp, const float *x_dev, const float *t_dev, int n,
+                      float *grad_host, float *loss_host, void *cuda_stream);
+/* `steps` Adam steps (beta 0.9/0.999) on minibatches of `batch` rows drawn
+ * with replacement by a counter-based hash of (seed, step, slot); loss of the
+ * last minibatch to loss_host (or NULL; synchronises when given). */
+bs_status bs_mlp_train(bs_mlp mlp, const float *x_dev, const float *t_dev, int n, int steps,
+                       int batch, float lr, uint64_t seed, float *loss_host, void *cuda_stream);
 
 /* Closed-triangle counts T(i,j,l) without any device allocation.
  * The paper has no counterpart: this entry point exists for callers that

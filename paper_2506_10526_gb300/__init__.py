@@ -32,7 +32,10 @@ EXPORTS = ("bs_abi_version", "bs_plan_create", "bs_plan_destroy", "bs_last_error
            "bs_plan_info", "bs_plan_set_workspace", "bs_grid_load", "bs_counts", "bs_mabs",
            "bs_delta_reset", "bs_mabs_delta", "bs_bs3d", "bs_check_hermitian",
            "bs_mc_create", "bs_mc_destroy", "bs_mc_last_error", "bs_mc_info", "bs_mc_set_input",
-           "bs_mc_set_tuning", "bs_mc_autotune", "bs_mc_run", "bs_mc_reset", "bs_mc_stats",
+           "bs_mc_set_flags", "bs_mc_set_tuning", "bs_mc_autotune", "bs_mc_run", "bs_mc_reset",
+           "bs_mc_stats",
+           "bs_mlp_features", "bs_mlp_create", "bs_mlp_destroy", "bs_mlp_last_error",
+           "bs_mlp_params", "bs_mlp_fit_norm", "bs_mlp_forward", "bs_mlp_grad", "bs_mlp_train",
            "bs_counts_noalloc")
 
 _lib = None
@@ -85,12 +88,24 @@ def lib() -> ctypes.CDLL:
             L.bs_mc_info.argtypes = [P, I, P, I]
             L.bs_mc_set_input.argtypes = [P, I, P]
             L.bs_mc_set_tuning.argtypes = [P, I]
+            L.bs_mc_set_flags.argtypes = [P, I, P]
             L.bs_mc_run.argtypes = [P, I, P]
             L.bs_mc_autotune.argtypes = [P, ctypes.c_char_p, ctypes.POINTER(I), P]
             L.bs_mc_reset.argtypes = [P, P]
             L.bs_mc_stats.argtypes = [P, I, I, P, P, P, P]
+            L.bs_mlp_features.argtypes = [P, P, P, P]
+            L.bs_mlp_create.argtypes = [I, I, ctypes.c_uint64, ctypes.POINTER(P)]
+            L.bs_mlp_destroy.argtypes = [P]
+            L.bs_mlp_last_error.argtypes = [P]
+            L.bs_mlp_last_error.restype = ctypes.c_char_p
+            L.bs_mlp_params.argtypes = [P, P, ctypes.c_int64, I]
+            L.bs_mlp_fit_norm.argtypes = [P, P, P, I, P]
+            L.bs_mlp_forward.argtypes = [P, P, I, P, P]
+            L.bs_mlp_grad.argtypes = [P, P, P, I, P, P, P]
+            L.bs_mlp_train.argtypes = [P, P, P, I, I, I, ctypes.c_float, ctypes.c_uint64, P, P]
             for name in EXPORTS:
-                if name not in ("bs_abi_version", "bs_last_error", "bs_mc_last_error"):
+                if name not in ("bs_abi_version", "bs_last_error", "bs_mc_last_error",
+                                "bs_mlp_last_error"):
                     getattr(L, name).restype = I
             _lib = L
     return _lib
@@ -207,6 +222,19 @@ class Plan:
         """bs_bs3d: out float64 CUDA [batch, ntrip, nc, nc]."""
         self._check(self._L.bs_bs3d(self._h, _dptr(out), _stream_ptr(stream)))
 
+    def mlp_features(self, chan_flags=None, stream=None):
+        """bs_mlp_features: float32 CUDA tensor [ntrip*nc*nc, 42] (NaN rows: no triangle)."""
+        import numpy as np
+        import torch
+        out = torch.empty((self.ntrip * self.nchan * self.nchan, 42), dtype=torch.float32,
+                          device="cuda")
+        fl = None
+        if chan_flags is not None:
+            self._mflags = np.ascontiguousarray(np.asarray(chan_flags, dtype=np.uint8))
+            fl = self._mflags.ctypes.data_as(ctypes.c_void_p)
+        self._check(self._L.bs_mlp_features(self._h, fl, _dptr(out), _stream_ptr(stream)))
+        return out
+
     def check_hermitian(self, vis, tol=1e-6, stream=None):
         """bs_check_hermitian; returns True when Hermitian within tol."""
         st = self._L.bs_check_hermitian(self._h, _dptr(vis), ctypes.c_double(tol),
@@ -278,6 +306,17 @@ class Ensemble:
         self._inputs[g] = vis
         self._check(self._L.bs_mc_set_input(self._h, g, _dptr(vis)))
 
+    def set_flags(self, g, flags):
+        """bs_mc_set_flags: uint8 [nchan] (1 = flagged) or None."""
+        import numpy as np
+        if flags is None:
+            self._check(self._L.bs_mc_set_flags(self._h, g, None))
+            return
+        f = np.ascontiguousarray(np.asarray(flags, dtype=np.uint8))
+        if f.size != self.groups[g]["nchan"]:
+            raise ValueError("flags must have nchan entries")
+        self._check(self._L.bs_mc_set_flags(self._h, g, f.ctypes.data_as(ctypes.c_void_p)))
+
     def autotune(self, cache_path=None, stream=None):
         """bs_mc_autotune: returns the chosen tiles-per-SM target."""
         c = ctypes.c_int()
@@ -308,6 +347,78 @@ class Ensemble:
     def close(self):
         if getattr(self, "_h", None):
             self._L.bs_mc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Surrogate:
+    """bs_mlp_*: the error-bar network (d_in inputs, width hidden units)."""
+
+    def __init__(self, d_in=42, width=128, seed=1):
+        L = lib()
+        self._L = L
+        h = ctypes.c_void_p()
+        st = L.bs_mlp_create(int(d_in), int(width), ctypes.c_uint64(seed), ctypes.byref(h))
+        if st != BS_OK:
+            raise BsError(st, "bs_mlp_create failed")
+        self._h = h
+        self.d, self.w = int(d_in), int(width)
+        self.n_weights = self.w * self.d + self.w + self.w * self.w + self.w + self.w + 1
+        self.n_total = self.n_weights + 2 * self.d + 2
+
+    def _check(self, st):
+        if st != BS_OK:
+            raise BsError(st, self._L.bs_mlp_last_error(self._h).decode())
+
+    def params(self):
+        import numpy as np
+        p = np.empty(self.n_total, np.float32)
+        self._check(self._L.bs_mlp_params(self._h, p.ctypes.data_as(ctypes.c_void_p),
+                                          self.n_total, 0))
+        return p
+
+    def set_params(self, p):
+        import numpy as np
+        p = np.ascontiguousarray(np.asarray(p, dtype=np.float32))
+        self._check(self._L.bs_mlp_params(self._h, p.ctypes.data_as(ctypes.c_void_p),
+                                          self.n_total, 1))
+
+    def fit_norm(self, x, t, stream=None):
+        self._check(self._L.bs_mlp_fit_norm(self._h, _dptr(x), _dptr(t), int(x.shape[0]),
+                                            _stream_ptr(stream)))
+
+    def forward(self, x, stream=None):
+        import torch
+        y = torch.empty(x.shape[0], dtype=torch.float32, device="cuda")
+        self._check(self._L.bs_mlp_forward(self._h, _dptr(x), int(x.shape[0]), _dptr(y),
+                                           _stream_ptr(stream)))
+        return y
+
+    def grad(self, x, t, stream=None):
+        import numpy as np
+        g = np.empty(self.n_weights, np.float32)
+        loss = np.zeros(1, np.float32)
+        self._check(self._L.bs_mlp_grad(self._h, _dptr(x), _dptr(t), int(x.shape[0]),
+                                        g.ctypes.data_as(ctypes.c_void_p),
+                                        loss.ctypes.data_as(ctypes.c_void_p), _stream_ptr(stream)))
+        return float(loss[0]), g
+
+    def train(self, x, t, steps, batch=8192, lr=2e-3, seed=7, stream=None):
+        import numpy as np
+        loss = np.zeros(1, np.float32)
+        self._check(self._L.bs_mlp_train(self._h, _dptr(x), _dptr(t), int(x.shape[0]), int(steps),
+                                         int(batch), ctypes.c_float(lr), ctypes.c_uint64(seed),
+                                         loss.ctypes.data_as(ctypes.c_void_p), _stream_ptr(stream)))
+        return float(loss[0])
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.bs_mlp_destroy(self._h)
             self._h = None
 
     def __del__(self):

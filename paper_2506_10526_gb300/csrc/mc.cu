@@ -60,6 +60,7 @@ __global__ void k_welford_final(long long n, const double *cnt, const double *me
 
 struct Group {
   bs_plan plan = nullptr;
+  std::vector<uint8_t> flags;   // [nc], 1 = flagged (empty = none)
   const void *vis = nullptr;    // [batch][nc][nt][nt] c64, caller-owned
   double *dout = nullptr;       // [batch][ntrip][n2][n2]
   double *bout = nullptr;       // [batch][ntrip][nc][nc]
@@ -129,8 +130,9 @@ bs_status mc_prepare(bs_mc m, cudaStream_t s) {
     }
     st = ensure_tensor_maps(p, s);
     if (st != BS_OK) return plan_status(m, p, st);
-    // every channel valid; the full cube of each realisation is contracted
-    std::fill(p->valid.begin(), p->valid.end(), (uint8_t)1);
+    // channel validity from the group's flags; the full cube is contracted
+    const std::vector<uint8_t> &fl = m->groups[g].flags;
+    for (int c = 0; c < p->nc; ++c) p->valid[c] = (fl.empty() || !fl[c]) ? 1 : 0;
     MC_CUDA(cudaMemcpyAsync(p->at<uint8_t>(p->L.valid), p->valid.data(), p->nc,
                             cudaMemcpyHostToDevice, s));
     std::fill(p->nnu.begin(), p->nnu.end(), 0LL);
@@ -417,6 +419,18 @@ bs_status bs_mc_set_input(bs_mc m, int group, const void *vis_dev) {
     m->graph = nullptr;
   }
   m->groups[group].vis = vis_dev;
+  return BS_OK;
+}
+
+bs_status bs_mc_set_flags(bs_mc m, int group, const uint8_t *flags_host) {
+  if (!m || group < 0 || group >= (int)m->groups.size())
+    return m ? mfail(m, BS_ERR_ARG, "bad group") : BS_ERR_ARG;
+  Group &gr = m->groups[group];
+  if (flags_host)
+    gr.flags.assign(flags_host, flags_host + gr.plan->nc);
+  else
+    gr.flags.clear();
+  mc_unprepare(m);  // validity, sampling and the graph depend on the flags
   return BS_OK;
 }
 

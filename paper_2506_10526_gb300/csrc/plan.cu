@@ -119,6 +119,7 @@ void compute_layout(bs_plan p) {
   L.err = take(sizeof(int));
   L.maps = take(2 * sizeof(CUtensorMap));
   L.tcgroup = take(sizeof(TcGroup));
+  L.mlptab = take(((size_t)p->ntrip * 4 + 33) * sizeof(float));
   L.total = o;
 }
 
@@ -490,6 +491,18 @@ bs_status bs_plan_create(const bs_plan_desc *desc, bs_plan *out) {
       p->uext[ring] = std::max(p->uext[ring], std::abs(u) + 1);
       cmax = std::max(cmax, std::max(std::abs(u), std::abs(v)));
     }
+  p->umean.assign(p->nb, 0.0);
+  {
+    std::vector<long long> nin(p->nb, 0);
+    for (int c : p->cells) {
+      const int u = (c & 0xffff) - 32768, v = ((c >> 16) & 0xffff) - 32768;
+      const int m = p->label[(size_t)(v + h) * nt + (u + h)];
+      p->umean[m] += std::sqrt((double)u * u + (double)v * v);
+      ++nin[m];
+    }
+    for (int m = 0; m < p->nb; ++m)
+      p->umean[m] = nin[m] ? p->umean[m] / nin[m] : 0.5 * (p->edges[m] + p->edges[m + 1]);
+  }
   p->UC = 0;
   for (int m = 0; m < p->nb; ++m) p->UC = std::max(p->UC, p->uext[m]);
   p->UC = std::max(p->UC, 1);

@@ -12,7 +12,7 @@ namespace bsi {
 
 struct WsLayout {
   size_t label, efflabel, cells, uext, tripof, valid, twM, twN, tnorm, T, nnu, cols, ptiles, tctiles,
-      G, F, Fhi, Flo, dsum, tmp3d, herm, err, maps, tcgroup, total;
+      G, F, Fhi, Flo, dsum, tmp3d, herm, err, maps, tcgroup, mlptab, total;
 };
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
@@ -35,6 +35,7 @@ struct bs_plan_s {
   std::vector<int8_t> label;     // [nt*nt]
   std::vector<int> cells;        // packed (u + 32768) | (v + 32768) << 16 of binned cells
   std::vector<int> uext;         // [nb]
+  std::vector<double> umean;     // [nb] mean |U| of each ring's cells
   std::vector<int> trips;        // [ntrip][3]
   std::vector<int> trip_of;      // [nb^3] -> trip index of sorted (i<=j<=l), else -1
   std::vector<long long> T;      // [ntrip] closed-triangle counts
