@@ -71,6 +71,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="mwa", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="split_bf16", choices=["fp32", "split_bf16"])
+    ap.add_argument("--no-multires", action="store_true",
+                    help="one image side for every ring triple (split-BF16 path)")
     ap.add_argument("--no-fp32-compare", action="store_true",
                     help="skip timing the plain FP32 contraction beside the split-BF16 one")
     ap.add_argument("--block", type=int, default=0, help="channel block side (0 = workload default)")
@@ -267,7 +269,8 @@ def main():
     nt, nc = w["nt"], w["nc"]
     prec = bs.PREC_FP32 if args.precision == "fp32" else bs.PREC_SPLIT_BF16
     vis = make_vis(w, seed=1000 * 2 + rank)
-    plan = bs.Plan(nt, nc, edges, precision=prec)
+    multires = args.precision == "split_bf16" and not args.no_multires
+    plan = bs.Plan(nt, nc, edges, precision=prec, multires=multires)
     stream = torch.cuda.current_stream()
     vis_h = torch.from_numpy(vis[None]).pin_memory()
     vis_d = vis_h.to(dev)
@@ -276,6 +279,8 @@ def main():
     plan.grid_load(vis_d)
     tri, _ = plan.counts()
     nclos = int((tri > 0).sum())
+    sides = plan.trip_sides()
+    flops_per_chan_triple = float(np.sum(2.0 * sides[tri > 0].astype(np.float64) ** 2))
     jobs = blocks_of(nc, w["block"])
 
     def block_evals(b):
@@ -362,7 +367,9 @@ def main():
     else:
         peak = float(peaks.get("bf16_tflops", 1900.0)) / 3.0
         roof = {"bound": "tensor", "peak_source": "measured bf16 burst / 3 (three split products)"}
-    achieved = per_launch_evals * 2.0 * M * M / (avg_ms / 1e3) / 1e12
+    b0 = jobs[0]
+    achieved = flops_per_chan_triple * (b0[1] - b0[0]) * (b0[3] - b0[2]) * (b0[5] - b0[4]) / (
+        avg_ms / 1e3) / 1e12
     tr = profile_traffic(args.precision)
     roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                  "kernel": "k_contract_simt" if args.precision == "fp32" else "k_contract_tc",
@@ -375,7 +382,9 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "bf16x3",
         "data": "synthetic",
-        "config": {"workload": w["desc"], "M": M, "channel_block": w["block"],
+        "config": {"workload": w["desc"], "M": M, "multires": multires,
+                   "image_sides": sorted(set(int(x) for x in sides[tri > 0])),
+                   "channel_block": w["block"],
                    "closable_ring_triples": nclos, "ring_triples": plan.ntrip,
                    "evals_per_step_per_gpu": per_launch_evals, "precision": args.precision,
                    "l2": "inputs larger than L2 (403 MB visibilities, 9 GB fields)",

@@ -54,7 +54,7 @@
 extern "C" {
 #endif
 
-#define BS_ABI_VERSION 1
+#define BS_ABI_VERSION 2
 
 typedef struct bs_plan_s *bs_plan;
 
@@ -93,6 +93,12 @@ typedef struct {
     double norm_A;           /* A of Eq. (estimator_t); <= 0 means 1 */
     double r, rprime, dnu_c; /* comoving distance r, r' = dr/dnu, channel width:
                                 Eq. (dft) multiplies by (r^2 r' dnu_c)^2; <= 0 means 1 */
+    int multires;            /* 1: every ring triple (i,j,l) uses its own image side, the
+                                smallest M = 2^a x {8, 12} with M > c_i + c_j + c_l and
+                                M > 2 max(c) (c = largest |u| or |v| in a ring): closure
+                                stays exact, the pixel sums shrink with the rings;
+                                fields are kept at each side that some triple needs.
+                                Split-BF16 only.  0: one M for all (fft_m rule). */
 } bs_plan_desc;
 
 /* ABI version this library was built with (BS_ABI_VERSION). */
@@ -117,8 +123,13 @@ const char *bs_last_error(bs_plan plan);
  *  [2] fields per realisation (nbins*nchan)   [3] workspace bytes needed
  *  [4] u columns kept per field (largest |u| of a binned cell + 1)
  *  [5] number of ring triples with at least one closed triangle
- *      (valid after the first bs_grid_load or bs_counts), else -1 */
+ *      (valid after the first bs_grid_load or bs_counts), else -1
+ *  [6] number of image sides (levels) the plan keeps fields at */
 bs_status bs_plan_info(bs_plan plan, int64_t *info_host, int n);
+
+/* Image side M used for each ring triple, int64 [T_r] (0: the triple's annuli
+ * cannot form a triangle).  Equal to info[0] for every triple unless multires. */
+bs_status bs_plan_trip_sides(bs_plan plan, int64_t *side_host);
 
 /* Hand the plan a caller-owned device workspace of at least info[3] bytes,
  * 256-byte aligned, valid until bs_plan_destroy (e.g. a torch uint8 tensor).

@@ -29,7 +29,7 @@ PREC_SPLIT_BF16 = 1
 
 # every symbol declared in include/bs.h
 EXPORTS = ("bs_abi_version", "bs_plan_create", "bs_plan_destroy", "bs_last_error",
-           "bs_plan_info", "bs_plan_set_workspace", "bs_grid_load", "bs_counts", "bs_mabs",
+           "bs_plan_info", "bs_plan_trip_sides", "bs_plan_set_workspace", "bs_grid_load", "bs_counts", "bs_mabs",
            "bs_delta_reset", "bs_mabs_delta", "bs_bs3d", "bs_check_hermitian",
            "bs_mc_create", "bs_mc_destroy", "bs_mc_last_error", "bs_mc_info", "bs_mc_set_input",
            "bs_mc_set_flags", "bs_mc_set_tuning", "bs_mc_autotune", "bs_mc_run", "bs_mc_reset",
@@ -53,7 +53,8 @@ class PlanDesc(ctypes.Structure):
                 ("bin_edges", ctypes.POINTER(ctypes.c_double)), ("fft_m", ctypes.c_int),
                 ("precision", ctypes.c_int), ("batch", ctypes.c_int),
                 ("norm_A", ctypes.c_double), ("r", ctypes.c_double),
-                ("rprime", ctypes.c_double), ("dnu_c", ctypes.c_double)]
+                ("rprime", ctypes.c_double), ("dnu_c", ctypes.c_double),
+                ("multires", ctypes.c_int)]
 
 
 def lib() -> ctypes.CDLL:
@@ -72,6 +73,7 @@ def lib() -> ctypes.CDLL:
             L.bs_last_error.argtypes = [P]
             L.bs_last_error.restype = ctypes.c_char_p
             L.bs_plan_info.argtypes = [P, P, I]
+            L.bs_plan_trip_sides.argtypes = [P, P]
             L.bs_plan_set_workspace.argtypes = [P, P, ctypes.c_size_t]
             L.bs_grid_load.argtypes = [P, P, P, P, P]
             L.bs_counts.argtypes = [P, P, P]
@@ -134,14 +136,14 @@ class Plan:
 
     def __init__(self, nt: int, nchan: int, edges, precision: int = PREC_FP32, batch: int = 1,
                  fft_m: int = 0, norm_A: float = 1.0, r: float = 1.0, rprime: float = 1.0,
-                 dnu_c: float = 1.0, torch_workspace: bool = True):
+                 dnu_c: float = 1.0, torch_workspace: bool = True, multires: bool = False):
         import torch
         L = lib()
         self._L = L
         e = [float(x) for x in edges]
         self._edges = (ctypes.c_double * len(e))(*e)
         d = PlanDesc(nt, nchan, len(e) - 1, self._edges, fft_m, precision, batch, norm_A, r,
-                     rprime, dnu_c)
+                     rprime, dnu_c, 1 if multires else 0)
         h = ctypes.c_void_p()
         st = L.bs_plan_create(ctypes.byref(d), ctypes.byref(h))
         if st != BS_OK:
@@ -176,9 +178,16 @@ class Plan:
             pass
 
     def info(self):
-        arr = (ctypes.c_int64 * 6)()
-        self._check(self._L.bs_plan_info(self._h, arr, 6))
+        arr = (ctypes.c_int64 * 7)()
+        self._check(self._L.bs_plan_info(self._h, arr, 7))
         return list(arr)
+
+    def trip_sides(self):
+        """bs_plan_trip_sides: image side M of every ring triple (numpy int64)."""
+        import numpy as np
+        out = np.zeros(self.ntrip, np.int64)
+        self._check(self._L.bs_plan_trip_sides(self._h, out.ctypes.data_as(ctypes.c_void_p)))
+        return out
 
     def grid_load(self, vis, ngrid=None, chan_flags=None, stream=None):
         """bs_grid_load: vis complex64 CUDA tensor [batch, nchan, nt, nt]."""
@@ -276,7 +285,8 @@ class Ensemble:
             self._edges.append(arr)
             descs[g] = PlanDesc(spec["nt"], spec["nchan"], len(e) - 1, arr, spec.get("fft_m", 0),
                                 PREC_SPLIT_BF16, spec["batch"], spec.get("norm_A", 1.0),
-                                spec.get("r", 1.0), spec.get("rprime", 1.0), spec.get("dnu_c", 1.0))
+                                spec.get("r", 1.0), spec.get("rprime", 1.0), spec.get("dnu_c", 1.0),
+                                1 if spec.get("multires", False) else 0)
         h = ctypes.c_void_p()
         st = L.bs_mc_create(descs, n, ctypes.byref(h))
         if st != BS_OK:
@@ -284,8 +294,8 @@ class Ensemble:
         self._h = h
         self.groups = [dict(g) for g in groups]
         for g, spec in enumerate(self.groups):
-            info = (ctypes.c_int64 * 6)()
-            self._check(L.bs_mc_info(h, g, info, 6))
+            info = (ctypes.c_int64 * 7)()
+            self._check(L.bs_mc_info(h, g, info, 7))
             spec["M"], spec["ntrip"] = info[0], info[1]
         if tiles_per_sm is not None:
             self._check(L.bs_mc_set_tuning(h, int(tiles_per_sm)))

@@ -34,10 +34,15 @@ struct PairTile {
   int pad[3];
 };
 
-// Geometry shared by the field kernels.
+// Geometry shared by the field kernels.  A plan may hold fields at several
+// image sizes (levels); at each level only some rings have fields, stored in
+// slots: slot_of[ring] (-1: no field at this level), ring_of[slot].
 struct GridGeom {
   int nt, nc, nb, M, UC;  // UC: u >= 0 columns stored per field
   int batch;
+  int nslot;              // rings with fields at this level
+  const int *slot_of;     // device [nb]
+  const int *ring_of;     // device [nslot]
 };
 
 // Contraction launch arguments.

@@ -71,7 +71,8 @@ __global__ void __launch_bounds__(256) k_colpass(GridGeom g, int UB, const float
   __syncthreads();
   for (int m = 0; m < g.nb; ++m) {
     const int ue = uext[m];
-    if (u0 >= ue) continue;  // block-uniform
+    const int slot = g.slot_of[m];
+    if (slot < 0 || u0 >= ue) continue;  // block-uniform
     for (int t = threadIdx.x; t < UB * M; t += blockDim.x) bufA[t] = make_float2(0.f, 0.f);
     __syncthreads();
     for (int t = threadIdx.x; t < nt * UB; t += blockDim.x) {
@@ -84,7 +85,7 @@ __global__ void __launch_bounds__(256) k_colpass(GridGeom g, int UB, const float
     }
     __syncthreads();
     float2 *res = stockham(bufA, bufB, UB, M, radM, tw, +1.0f);
-    float2 *Gm = G + (((long long)b * g.nb + m) * g.nc + nu) * (long long)M * g.UC;
+    float2 *Gm = G + (((long long)b * g.nslot + slot) * g.nc + nu) * (long long)M * g.UC;
     const int ncols = min(UB, g.UC - u0);
     for (int t = threadIdx.x; t < M * UB; t += blockDim.x) {
       const int y = t / UB, c = t - y * UB;
@@ -110,13 +111,14 @@ __global__ void __launch_bounds__(256) k_rowpass(GridGeom g, int RPB, const floa
                                                  uint16_t *__restrict__ Flo) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int M = g.M;
-  const int f = blockIdx.y;  // m * nc + nu
-  const int m = f / g.nc, nu = f - m * g.nc;
+  const int f = blockIdx.y;  // slot * nc + nu
+  const int slot = f / g.nc, nu = f - slot * g.nc;
+  const int m = g.ring_of[slot];
   const int b = blockIdx.z;
   const int y0 = blockIdx.x * 2 * RPB;
   const int npair = min(RPB, (M - y0) / 2);
-  const long long fbase = ((long long)b * g.nb * g.nc + f) * (long long)M * M;
-  const int ue = uext[m];
+  const long long fbase = ((long long)b * g.nslot * g.nc + f) * (long long)M * M;
+  const int ue = min(uext[m], g.UC);
   if (!valid[nu] || ue == 0) {
     for (int t = threadIdx.x; t < 2 * npair * M; t += blockDim.x) {
       const long long o = fbase + (long long)y0 * M + t;
@@ -134,7 +136,7 @@ __global__ void __launch_bounds__(256) k_rowpass(GridGeom g, int RPB, const floa
   for (int t = threadIdx.x; t < M; t += blockDim.x) tw[t] = twM[t];
   for (int t = threadIdx.x; t < RPB * M; t += blockDim.x) bufA[t] = make_float2(0.f, 0.f);
   __syncthreads();
-  const float2 *Gm = G + (((long long)b * g.nb + m) * g.nc + nu) * (long long)M * g.UC;
+  const float2 *Gm = G + (((long long)b * g.nslot + slot) * g.nc + nu) * (long long)M * g.UC;
   for (int t = threadIdx.x; t < npair * ue; t += blockDim.x) {
     const int p = t / ue, u = t - p * ue;
     const int y = y0 + 2 * p;
@@ -288,7 +290,7 @@ cudaError_t launch_rowpass(const GridGeom &g, const float2 *G, const uint8_t *va
   const size_t smem = (size_t)(2 * RPB * g.M + g.M) * sizeof(float2);
   cudaError_t e = smem_optin_once(k_rowpass);
   if (e != cudaSuccess) return e;
-  dim3 grid((g.M / 2 + RPB - 1) / RPB, g.nb * g.nc, g.batch);
+  dim3 grid((g.M / 2 + RPB - 1) / RPB, g.nslot * g.nc, g.batch);
   k_rowpass<<<grid, 256, smem, s>>>(g, RPB, G, valid, uext, twM, radM, F, Fhi, Flo);
   return cudaGetLastError();
 }

@@ -13,6 +13,7 @@
 // Tile lists, counts and the sampling N_nu depend only on the shapes and are
 // built once.  The first run executes eagerly; later runs with use_graph
 // replay the captured graph.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -141,24 +142,29 @@ bs_status mc_prepare(bs_mc m, cudaStream_t s) {
     st = upload_nnu(p, s);
     if (st != BS_OK) return plan_status(m, p, st);
   }
-  // pass 2: tiles (column pointers are fixed up after the device buffer exists)
-  std::vector<std::pair<size_t, size_t>> col_ranges;
+  // pass 2: tiles of every (group, level); column pointers fixed up after the
+  // device buffer exists
   for (size_t g = 0; g < m->groups.size(); ++g) {
     bs_plan p = m->groups[g].plan;
     const size_t c0 = cols.size();
     const int blk[6] = {0, p->nc, 0, p->nc, 0, p->nc};
     std::vector<ColEntry> gc;
     std::vector<TcTile> gt;
-    TcGroup G = build_tc_work(p, blk, (int)g, gc, nullptr, gt, nullptr, 1,
-                              m->min_tiles_factor * m->nsm);
+    std::vector<TcGroup> G = build_tc_work(p, blk, (int)tgs.size(), gc, nullptr, gt, nullptr, 1,
+                                           m->min_tiles_factor * m->nsm);
     for (TcTile &t : gt) t.col_off += (int)c0;  // offsets into the concatenated list
     cols.insert(cols.end(), gc.begin(), gc.end());
     tiles.insert(tiles.end(), gt.begin(), gt.end());
-    tgs.push_back(G);
-    col_ranges.push_back({c0, gc.size()});
-    const unsigned char *mp = reinterpret_cast<const unsigned char *>(p->maps);
-    maps.insert(maps.end(), mp, mp + sizeof(p->maps));
+    tgs.insert(tgs.end(), G.begin(), G.end());
+    for (const Level &lv : p->levels) {
+      const unsigned char *mp = reinterpret_cast<const unsigned char *>(lv.maps);
+      maps.insert(maps.end(), mp, mp + sizeof(lv.maps));
+    }
   }
+  // heaviest tiles first across all groups (balance of the persistent launch)
+  std::stable_sort(tiles.begin(), tiles.end(), [&](const TcTile &x, const TcTile &y) {
+    return tgs[x.group].kseg_len > tgs[y.group].kseg_len;
+  });
   MC_CUDA(cudaMalloc(&m->cols, std::max<size_t>(1, cols.size()) * sizeof(ColEntry)));
   MC_CUDA(cudaMalloc(&m->tiles, std::max<size_t>(1, tiles.size()) * sizeof(TcTile)));
   MC_CUDA(cudaMalloc(&m->tcgroups, tgs.size() * sizeof(TcGroup)));
@@ -181,16 +187,10 @@ bs_status mc_prepare(bs_mc m, cudaStream_t s) {
 bs_status mc_enqueue(bs_mc m, cudaStream_t s) {
   for (Group &gr : m->groups) {
     bs_plan p = gr.plan;
-    GridGeom geo{p->nt, p->nc, p->nb, p->M, p->UC, p->batch};
-    const WsLayout &L = p->L;
-    MC_CUDA(launch_colpass(geo, static_cast<const float2 *>(gr.vis), nullptr,
-                           p->at<uint8_t>(L.valid), p->at<int8_t>(L.label), p->at<int>(L.uext),
-                           p->at<float2>(L.twM), p->radM, p->at<float2>(L.G), s));
-    MC_CUDA(launch_rowpass(geo, p->at<float2>(L.G), p->at<uint8_t>(L.valid), p->at<int>(L.uext),
-                           p->at<float2>(L.twM), p->radM, p->at<float>(L.F),
-                           p->at<uint16_t>(L.Fhi), p->at<uint16_t>(L.Flo), s));
+    bs_status st = enqueue_fields(p, gr.vis, nullptr, s);
+    if (st != BS_OK) return plan_status(m, p, st);
     const size_t n2 = (size_t)(2 * p->nc - 1);
-    MC_CUDA(cudaMemsetAsync(p->at<double>(L.dsum), 0,
+    MC_CUDA(cudaMemsetAsync(p->at<double>(p->L.dsum), 0,
                             (size_t)p->batch * p->ntrip * n2 * n2 * sizeof(double), s));
   }
   TcArgs a{};

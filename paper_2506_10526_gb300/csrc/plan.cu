@@ -100,7 +100,6 @@ void compute_layout(bs_plan p) {
   L.uext = take((size_t)p->nb * sizeof(int));
   L.tripof = take((size_t)p->nb * p->nb * p->nb * sizeof(int));
   L.valid = take((size_t)p->nc);
-  L.twM = take((size_t)p->M * sizeof(float2));
   L.twN = take((size_t)p->nc * sizeof(float2));
   L.tnorm = take((size_t)p->ntrip * sizeof(double));
   L.T = take((size_t)p->ntrip * sizeof(unsigned long long));
@@ -108,17 +107,30 @@ void compute_layout(bs_plan p) {
   L.cols = take(p->max_cols * sizeof(ColEntry));
   L.ptiles = take(p->max_ptiles * sizeof(PairTile));
   L.tctiles = take(p->max_tctiles * sizeof(TcTile));
-  L.G = take((size_t)p->batch * p->nb * p->nc * (size_t)p->M * p->UC * sizeof(float2));
-  L.F = take((size_t)p->batch * p->nf * (size_t)p->M * p->M * sizeof(float));
+  size_t gmax = 0;
   const bool split = p->d.precision == BS_PREC_SPLIT_BF16;
-  L.Fhi = take(split ? (size_t)p->batch * p->nf * (size_t)p->M * p->M * 2 : 0);
-  L.Flo = take(split ? (size_t)p->batch * p->nf * (size_t)p->M * p->M * 2 : 0);
+  for (Level &lv : p->levels) {
+    const size_t nfl = (size_t)lv.nslot * p->nc, m2 = (size_t)lv.M * lv.M;
+    gmax = std::max(gmax, (size_t)p->batch * nfl * lv.M * lv.UC * sizeof(float2));
+    lv.offF = take((size_t)p->batch * nfl * m2 * sizeof(float));
+    lv.offFhi = take(split ? (size_t)p->batch * nfl * m2 * 2 : 0);
+    lv.offFlo = take(split ? (size_t)p->batch * nfl * m2 * 2 : 0);
+    lv.offTw = take((size_t)lv.M * sizeof(float2));
+    lv.offSlot = take((size_t)p->nb * sizeof(int));
+    lv.offRing = take((size_t)std::max(1, lv.nslot) * sizeof(int));
+  }
+  L.G = take(gmax);
+  // level 0 doubles as the single-level layout of the FP32 path
+  L.F = p->levels[0].offF;
+  L.Fhi = p->levels[0].offFhi;
+  L.Flo = p->levels[0].offFlo;
+  L.twM = p->levels[0].offTw;
   L.dsum = take((size_t)p->batch * p->ntrip * n2 * n2 * sizeof(double));
   L.tmp3d = take((size_t)p->batch * p->ntrip * (size_t)p->nc * p->nc * sizeof(float2));
   L.herm = take(2 * sizeof(float));
   L.err = take(sizeof(int));
-  L.maps = take(2 * sizeof(CUtensorMap));
-  L.tcgroup = take(sizeof(TcGroup));
+  L.maps = take(2 * p->levels.size() * sizeof(CUtensorMap));
+  L.tcgroup = take(p->levels.size() * sizeof(TcGroup));
   L.mlptab = take(((size_t)p->ntrip * 4 + 33) * sizeof(float));
   L.total = o;
 }
@@ -149,9 +161,18 @@ bs_status init_tables(bs_plan p, cudaStream_t s) {
                           cudaMemcpyHostToDevice, s));
   BS_CUDA(cudaMemcpyAsync(p->at<int>(L.tripof), p->trip_of.data(),
                           p->trip_of.size() * sizeof(int), cudaMemcpyHostToDevice, s));
-  std::vector<float2> twm = twiddles(p->M), twn = twiddles(p->nc);
-  BS_CUDA(cudaMemcpyAsync(p->at<float2>(L.twM), twm.data(), twm.size() * sizeof(float2),
-                          cudaMemcpyHostToDevice, s));
+  std::vector<std::vector<float2>> twl;
+  for (const Level &lv : p->levels) {
+    twl.push_back(twiddles(lv.M));
+    BS_CUDA(cudaMemcpyAsync(p->at<float2>(lv.offTw), twl.back().data(),
+                            twl.back().size() * sizeof(float2), cudaMemcpyHostToDevice, s));
+    BS_CUDA(cudaMemcpyAsync(p->at<int>(lv.offSlot), lv.slot_of.data(), lv.slot_of.size() * sizeof(int),
+                            cudaMemcpyHostToDevice, s));
+    if (lv.nslot > 0)
+      BS_CUDA(cudaMemcpyAsync(p->at<int>(lv.offRing), lv.ring_of.data(),
+                              lv.ring_of.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  }
+  std::vector<float2> twn = twiddles(p->nc);
   BS_CUDA(cudaMemcpyAsync(p->at<float2>(L.twN), twn.data(), twn.size() * sizeof(float2),
                           cudaMemcpyHostToDevice, s));
   BS_CUDA(cudaMemsetAsync(p->at<int>(L.err), 0, sizeof(int), s));
@@ -187,23 +208,46 @@ bs_status ensure_tensor_maps(bs_plan p, cudaStream_t s) {
     return fail(p, BS_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
   }
   EncodeTiledFn enc = reinterpret_cast<EncodeTiledFn>(fn);
-  const cuuint64_t M2 = (cuuint64_t)p->M * p->M;
-  cuuint64_t dims[2] = {M2, (cuuint64_t)p->batch * p->nf};
-  cuuint64_t strides[1] = {M2 * 2};
-  cuuint32_t box[2] = {32, 8};
-  cuuint32_t estr[2] = {1, 1};
-  for (int w = 0; w < 2; ++w) {
-    void *base = w == 0 ? (void *)p->at<uint16_t>(p->L.Fhi) : (void *)p->at<uint16_t>(p->L.Flo);
-    CUresult r = enc(&p->maps[w], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box,
-                     estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
-                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS)
-      return fail(p, BS_ERR_CUDA, "cuTensorMapEncodeTiled failed with code " + std::to_string((int)r));
+  std::vector<CUtensorMap> all;
+  for (Level &lv : p->levels) {
+    const cuuint64_t M2 = (cuuint64_t)lv.M * lv.M;
+    cuuint64_t dims[2] = {M2, (cuuint64_t)p->batch * std::max(1, lv.nslot) * p->nc};
+    cuuint64_t strides[1] = {M2 * 2};
+    cuuint32_t box[2] = {32, 8};
+    cuuint32_t estr[2] = {1, 1};
+    for (int w = 0; w < 2; ++w) {
+      void *base = p->at<uint16_t>(w == 0 ? lv.offFhi : lv.offFlo);
+      CUresult r = enc(&lv.maps[w], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box,
+                       estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS)
+        return fail(p, BS_ERR_CUDA,
+                    "cuTensorMapEncodeTiled failed with code " + std::to_string((int)r));
+      all.push_back(lv.maps[w]);
+    }
   }
-  BS_CUDA(cudaMemcpyAsync(p->at<unsigned char>(p->L.maps), p->maps, sizeof(p->maps),
+  BS_CUDA(cudaMemcpyAsync(p->at<unsigned char>(p->L.maps), all.data(), all.size() * sizeof(CUtensorMap),
                           cudaMemcpyHostToDevice, s));
   BS_CUDA(cudaStreamSynchronize(s));
   p->maps_ready = true;
+  return BS_OK;
+}
+
+bs_status enqueue_fields(bs_plan p, const void *vis, const float *ngrid, cudaStream_t s) {
+  const WsLayout &L = p->L;
+  const bool split = p->d.precision == BS_PREC_SPLIT_BF16;
+  for (const Level &lv : p->levels) {
+    if (lv.nslot == 0) continue;
+    GridGeom g{p->nt, p->nc, p->nb, lv.M, lv.UC, p->batch, lv.nslot, p->at<int>(lv.offSlot),
+               p->at<int>(lv.offRing)};
+    BS_CUDA(launch_colpass(g, static_cast<const float2 *>(vis), ngrid, p->at<uint8_t>(L.valid),
+                           p->at<int8_t>(L.label), p->at<int>(L.uext), p->at<float2>(lv.offTw),
+                           lv.rad, p->at<float2>(L.G), s));
+    BS_CUDA(launch_rowpass(g, p->at<float2>(L.G), p->at<uint8_t>(L.valid), p->at<int>(L.uext),
+                           p->at<float2>(lv.offTw), lv.rad, p->at<float>(lv.offF),
+                           split ? p->at<uint16_t>(lv.offFhi) : nullptr,
+                           split ? p->at<uint16_t>(lv.offFlo) : nullptr, s));
+  }
   return BS_OK;
 }
 
@@ -231,9 +275,12 @@ bs_status run_counts(bs_plan p, const int8_t *lab_dev, cudaStream_t s) {
   BS_CUDA(cudaStreamSynchronize(s));
   p->T.assign(th.begin(), th.end());
   p->tnorm.resize(p->ntrip);
-  const double m2 = (double)p->M * (double)p->M;
-  for (int t = 0; t < p->ntrip; ++t)
-    p->tnorm[t] = p->T[t] > 0 ? 1.0 / (p->normA * m2 * (double)p->T[t]) : 0.0;
+  for (int t = 0; t < p->ntrip; ++t) {
+    const int lv = p->lev_of_trip[t];
+    if (p->T[t] > 0 && lv < 0) return fail(p, BS_ERR_STATE, "closable ring triple without a level");
+    const double m = lv >= 0 ? (double)p->levels[lv].M : 1.0;
+    p->tnorm[t] = p->T[t] > 0 ? 1.0 / (p->normA * m * m * (double)p->T[t]) : 0.0;
+  }
   BS_CUDA(cudaMemcpyAsync(p->at<double>(p->L.tnorm), p->tnorm.data(), p->ntrip * sizeof(double),
                           cudaMemcpyHostToDevice, s));
   BS_CUDA(cudaStreamSynchronize(s));
@@ -312,69 +359,91 @@ bs_status delta_reset(bs_plan p, cudaStream_t s) {
   return BS_OK;
 }
 
-TcGroup build_tc_work(bs_plan p, const int *blk, int group, std::vector<ColEntry> &cols,
-                      const ColEntry *cols_dev, std::vector<TcTile> &tiles, double *out_full,
-                      int accumulate, int min_tiles) {
+std::vector<TcGroup> build_tc_work(bs_plan p, const int *blk, int group_base,
+                                   std::vector<ColEntry> &cols, const ColEntry *cols_dev,
+                                   std::vector<TcTile> &tiles, double *out_full, int accumulate,
+                                   int min_tiles) {
   const int nc = p->nc, nb = p->nb;
   const int w3 = blk[5] - blk[4];
   const int run = ((w3 + 7) / 8) * 8;
-  const int M2 = p->M * p->M;
-  const int Kpad = ((M2 + 31) / 32) * 32;
-  TcGroup G{};
-  G.F = p->at<float>(p->L.F);
-  G.fstride = M2;
-  G.bstride = (long long)p->nf * M2;
-  G.nf = p->nf;
-  G.batch = p->batch;
-  G.M2 = M2;
-  G.Kpad = Kpad;
-  G.nc = nc;
-  G.nu1_hi = blk[1];
-  G.nu2_hi = blk[3];
-  G.cols = cols_dev;
-  G.tnorm = p->at<double>(p->L.tnorm);
-  G.out_full = out_full;
-  G.full_bstride = (long long)p->ntrip * nc * nc * nc;
-  G.dsum = accumulate ? p->at<double>(p->L.dsum) : nullptr;
-  G.dsum_bstride = (long long)p->ntrip * (2 * nc - 1) * (2 * nc - 1);
-  G.kseg_len = Kpad;
-  if (w3 == 0 || blk[1] <= blk[0] || blk[3] <= blk[2]) return G;
+  const int nlev = (int)p->levels.size();
+  std::vector<TcGroup> groups(nlev);
+  for (int lv = 0; lv < nlev; ++lv) {
+    const Level &L = p->levels[lv];
+    const int M2 = L.M * L.M;
+    TcGroup &G = groups[lv];
+    G.F = p->at<float>(L.offF);
+    G.fstride = M2;
+    G.bstride = (long long)std::max(1, L.nslot) * nc * M2;
+    G.nf = std::max(1, L.nslot) * nc;
+    G.batch = p->batch;
+    G.M2 = M2;
+    G.Kpad = ((M2 + 31) / 32) * 32;
+    G.nc = nc;
+    G.nu1_hi = blk[1];
+    G.nu2_hi = blk[3];
+    G.cols = cols_dev;
+    G.tnorm = p->at<double>(p->L.tnorm);
+    G.out_full = out_full;
+    G.full_bstride = (long long)p->ntrip * nc * nc * nc;
+    G.dsum = accumulate ? p->at<double>(p->L.dsum) : nullptr;
+    G.dsum_bstride = (long long)p->ntrip * (2 * nc - 1) * (2 * nc - 1);
+    G.kseg_len = G.Kpad;
+  }
+  if (w3 == 0 || blk[1] <= blk[0] || blk[3] <= blk[2]) return groups;
+  // column lists per (level, ring pair): fields (l, nu3) of the level's slots,
+  // runs padded to multiples of 8 so TMA boxes of 8 fields never straddle rings
   struct PairList {
-    int i, j, off, n;
+    int lv, si, sj, off, n;
   };
   std::vector<PairList> pl;
-  for (int i = 0; i < nb; ++i)
-    for (int j = i; j < nb; ++j) {
-      const int off = (int)cols.size();
-      for (int l = j; l < nb; ++l) {
-        const int t = p->trip_of[((size_t)i * nb + j) * nb + l];
-        if (p->T[t] <= 0) continue;
-        for (int q = 0; q < run; ++q) {
-          const int n3 = blk[4] + q;
-          cols.push_back(ColEntry{q < w3 ? l * nc + n3 : -1, t, n3, 0});
+  for (int lv = 0; lv < nlev; ++lv) {
+    const Level &L = p->levels[lv];
+    for (int i = 0; i < nb; ++i)
+      for (int j = i; j < nb; ++j) {
+        if (L.slot_of[i] < 0 || L.slot_of[j] < 0) continue;
+        const int off = (int)cols.size();
+        for (int l = j; l < nb; ++l) {
+          const int t = p->trip_of[((size_t)i * nb + j) * nb + l];
+          if (p->T[t] <= 0 || p->lev_of_trip[t] != lv) continue;
+          for (int q = 0; q < run; ++q) {
+            const int n3 = blk[4] + q;
+            cols.push_back(ColEntry{q < w3 ? L.slot_of[l] * nc + n3 : -1, t, n3, 0});
+          }
         }
+        const int n = (int)cols.size() - off;
+        if (n > 0) pl.push_back(PairList{lv, L.slot_of[i], L.slot_of[j], off, n});
       }
-      const int n = (int)cols.size() - off;
-      if (n > 0) pl.push_back(PairList{i, j, off, n});
-    }
+  }
   const int n1b = (blk[1] - blk[0] + 31) / 32, n2b = (blk[3] - blk[2] + 15) / 16;
   long long base_tiles = 0;
   for (const PairList &q : pl) base_tiles += (long long)n1b * n2b * ((q.n + 127) / 128);
   base_tiles *= p->batch;
-  // split K until the launch has min_tiles tiles
+  // split K (the same factor on every level) until the launch has min_tiles tiles
   int nk = 1;
-  while (base_tiles * nk < min_tiles && nk < 64 && Kpad / (32 * nk * 2) >= 8) nk *= 2;
-  G.kseg_len = ((Kpad / 32 + nk - 1) / nk) * 32;
-  nk = (Kpad + G.kseg_len - 1) / G.kseg_len;
+  int kmin = 1 << 30;
+  for (const TcGroup &G : groups) kmin = std::min(kmin, G.Kpad);
+  while (base_tiles * nk < min_tiles && nk < 64 && kmin / (32 * nk * 2) >= 8) nk *= 2;
+  std::vector<int> nks(nlev);
+  for (int lv = 0; lv < nlev; ++lv) {
+    TcGroup &G = groups[lv];
+    G.kseg_len = ((G.Kpad / 32 + nk - 1) / nk) * 32;
+    nks[lv] = (G.Kpad + G.kseg_len - 1) / G.kseg_len;
+  }
+  const size_t t0 = tiles.size();
   for (int b = 0; b < p->batch; ++b)
     for (const PairList &q : pl)
       for (int c0 = 0; c0 < q.n; c0 += 128)
         for (int a1 = 0; a1 < n1b; ++a1)
           for (int a2 = 0; a2 < n2b; ++a2)
-            for (int k = 0; k < nk; ++k)
-              tiles.push_back(TcTile{group, b, q.i, q.j, blk[0] + 32 * a1, blk[2] + 16 * a2, q.off,
-                                     q.n, c0, k, {0, 0}});
-  return G;
+            for (int k = 0; k < nks[q.lv]; ++k)
+              tiles.push_back(TcTile{group_base + q.lv, b, q.si, q.sj, blk[0] + 32 * a1,
+                                     blk[2] + 16 * a2, q.off, q.n, c0, k, {0, 0}});
+  // heaviest tiles first: static round-robin over persistent CTAs then balances
+  std::stable_sort(tiles.begin() + t0, tiles.end(), [&](const TcTile &x, const TcTile &y) {
+    return groups[x.group - group_base].kseg_len > groups[y.group - group_base].kseg_len;
+  });
+  return groups;
 }
 
 // Tensor-core contraction of one channel block of one plan (split BF16).
@@ -384,8 +453,8 @@ bs_status mabs_tc(bs_plan p, const int *blk, double *out_full, int accumulate, c
   const WsLayout &L = p->L;
   p->h_cols.clear();
   p->h_tctiles.clear();
-  TcGroup G = build_tc_work(p, blk, 0, p->h_cols, p->at<ColEntry>(L.cols), p->h_tctiles, out_full,
-                            accumulate, 2 * p->nsm);
+  p->h_groups = build_tc_work(p, blk, 0, p->h_cols, p->at<ColEntry>(L.cols), p->h_tctiles,
+                              out_full, accumulate, 2 * p->nsm);
   if (p->h_tctiles.empty()) return BS_OK;
   if (p->h_tctiles.size() > p->max_tctiles || p->h_cols.size() > p->max_cols)
     return fail(p, BS_ERR_UNSUPPORTED, "tensor-core tile list exceeds the plan's capacity");
@@ -393,9 +462,8 @@ bs_status mabs_tc(bs_plan p, const int *blk, double *out_full, int accumulate, c
                           p->h_cols.size() * sizeof(ColEntry), cudaMemcpyHostToDevice, s));
   BS_CUDA(cudaMemcpyAsync(p->at<TcTile>(L.tctiles), p->h_tctiles.data(),
                           p->h_tctiles.size() * sizeof(TcTile), cudaMemcpyHostToDevice, s));
-  p->h_group = G;
-  BS_CUDA(cudaMemcpyAsync(p->at<TcGroup>(L.tcgroup), &p->h_group, sizeof(TcGroup),
-                          cudaMemcpyHostToDevice, s));
+  BS_CUDA(cudaMemcpyAsync(p->at<TcGroup>(L.tcgroup), p->h_groups.data(),
+                          p->h_groups.size() * sizeof(TcGroup), cudaMemcpyHostToDevice, s));
   TcArgs a{};
   a.groups = p->at<TcGroup>(L.tcgroup);
   a.maps = p->at<unsigned char>(L.maps);
@@ -539,6 +607,100 @@ bs_status bs_plan_create(const bs_plan_desc *desc, bs_plan *out) {
       }
   p->ntrip = (int)(p->trips.size() / 3);
   p->nf = p->nb * p->nc;
+  // image levels
+  p->cring.assign(p->nb, -1);
+  std::vector<double> rmin(p->nb, 1e300), rmax(p->nb, -1.0);
+  for (int c : p->cells) {
+    const int u = (c & 0xffff) - 32768, v = ((c >> 16) & 0xffff) - 32768;
+    const int m = p->label[(size_t)(v + h) * nt + (u + h)];
+    p->cring[m] = std::max(p->cring[m], std::max(std::abs(u), std::abs(v)));
+    const double r = std::sqrt((double)u * u + (double)v * v);
+    rmin[m] = std::min(rmin[m], r);
+    rmax[m] = std::max(rmax[m], r);
+  }
+  p->multires = d.multires != 0;
+  if (p->multires && d.precision != BS_PREC_SPLIT_BF16) {
+    delete p;
+    return fail(nullptr, BS_ERR_UNSUPPORTED, "multires needs the split-BF16 tensor-core path");
+  }
+  p->lev_of_trip.assign(p->ntrip, -1);
+  if (!p->multires) {
+    Level lv;
+    lv.M = p->M;
+    lv.rad = p->radM;
+    lv.UC = p->UC;
+    lv.nslot = p->nb;
+    for (int m = 0; m < p->nb; ++m) {
+      lv.slot_of.push_back(m);
+      lv.ring_of.push_back(m);
+    }
+    p->levels.push_back(lv);
+    std::fill(p->lev_of_trip.begin(), p->lev_of_trip.end(), 0);
+  } else {
+    // per ring triple the smallest M = 2^a x {8, 12} with M > c_i + c_j + c_l (exact
+    // closure) and M > 2 max(c) (Hermitian halves of a ring never overlap); triples
+    // whose annuli cannot form a triangle (|g3| <= |g1| + |g2| and permutations)
+    // have no closed triangle and get no level
+    std::vector<int> cand;
+    for (int b = 8; b <= 4096; b *= 2) {
+      cand.push_back(b);
+      if (b * 3 / 2 <= 4096) cand.push_back(b * 3 / 2);
+    }
+    std::sort(cand.begin(), cand.end());
+    std::vector<int> tripM(p->ntrip, 0);
+    for (int t = 0; t < p->ntrip; ++t) {
+      const int i = p->trips[3 * t], j = p->trips[3 * t + 1], l = p->trips[3 * t + 2];
+      if (p->cring[i] < 0 || p->cring[j] < 0 || p->cring[l] < 0) continue;
+      if (rmin[l] > rmax[i] + rmax[j] + 1e-9 || rmin[i] > rmax[j] + rmax[l] + 1e-9 ||
+          rmin[j] > rmax[i] + rmax[l] + 1e-9)
+        continue;
+      const int need = std::max(p->cring[i] + p->cring[j] + p->cring[l],
+                                2 * std::max(p->cring[i], std::max(p->cring[j], p->cring[l])));
+      int M = 0;
+      for (int c : cand)
+        if (c > need) {
+          M = c;
+          break;
+        }
+      if (M == 0) {
+        delete p;
+        return fail(nullptr, BS_ERR_UNSUPPORTED, "a ring triple needs an image side above 4096");
+      }
+      tripM[t] = M;
+    }
+    std::vector<int> used;
+    for (int M : tripM)
+      if (M && std::find(used.begin(), used.end(), M) == used.end()) used.push_back(M);
+    std::sort(used.begin(), used.end());
+    for (int M : used) {
+      Level lv;
+      lv.M = M;
+      factor_radices(M, lv.rad);
+      lv.slot_of.assign(p->nb, -1);
+      p->levels.push_back(lv);
+    }
+    for (int t = 0; t < p->ntrip; ++t) {
+      if (!tripM[t]) continue;
+      const int lvi = (int)(std::find(used.begin(), used.end(), tripM[t]) - used.begin());
+      p->lev_of_trip[t] = lvi;
+      Level &lv = p->levels[lvi];
+      for (int q = 0; q < 3; ++q) {
+        const int m = p->trips[3 * t + q];
+        if (lv.slot_of[m] < 0) {
+          lv.slot_of[m] = lv.nslot++;
+          lv.ring_of.push_back(m);
+          lv.UC = std::max(lv.UC, p->uext[m]);
+        }
+      }
+    }
+    if (p->levels.empty()) {  // nothing can close: one empty level keeps the layout valid
+      Level lv;
+      lv.M = 8;
+      factor_radices(8, lv.rad);
+      lv.slot_of.assign(p->nb, -1);
+      p->levels.push_back(lv);
+    }
+  }
   p->valid.assign(p->nc, 1);
   p->nnu.assign((size_t)(2 * p->nc - 1) * (2 * p->nc - 1), 0);
   const int npairs = p->nb * (p->nb + 1) / 2;
@@ -570,13 +732,23 @@ bs_status bs_plan_destroy(bs_plan p) {
 
 bs_status bs_plan_info(bs_plan p, int64_t *info, int n) {
   if (!p || !info || n < 0) return fail(p, BS_ERR_ARG, "bad arguments");
-  int64_t v[6] = {p->M, p->ntrip, p->nf, (int64_t)p->L.total, p->UC, -1};
+  int64_t v[7] = {p->M, p->ntrip, p->nf, (int64_t)p->L.total, p->UC, -1,
+                  (int64_t)p->levels.size()};
   if (p->counts_ready) {
     int64_t c = 0;
     for (long long t : p->T) c += t > 0;
     v[5] = c;
   }
-  for (int k = 0; k < n && k < 6; ++k) info[k] = v[k];
+  for (int k = 0; k < n && k < 7; ++k) info[k] = v[k];
+  return BS_OK;
+}
+
+bs_status bs_plan_trip_sides(bs_plan p, int64_t *side_host) {
+  if (!p || !side_host) return fail(p, BS_ERR_ARG, "side_host must not be NULL");
+  for (int t = 0; t < p->ntrip; ++t) {
+    const int lv = p->lev_of_trip[t];
+    side_host[t] = lv >= 0 ? p->levels[lv].M : 0;
+  }
   return BS_OK;
 }
 
@@ -616,15 +788,8 @@ bs_status bs_grid_load(bs_plan p, const void *vis, const float *ngrid, const uin
     if (st != BS_OK) return st;
     p->counts_default = true;
   }
-  GridGeom g{p->nt, p->nc, p->nb, p->M, p->UC, p->batch};
-  BS_CUDA(launch_colpass(g, static_cast<const float2 *>(vis), ngrid, p->at<uint8_t>(L.valid), lab,
-                         p->at<int>(L.uext), p->at<float2>(L.twM), p->radM, p->at<float2>(L.G),
-                         s));
-  const bool split = p->d.precision == BS_PREC_SPLIT_BF16;
-  BS_CUDA(launch_rowpass(g, p->at<float2>(L.G), p->at<uint8_t>(L.valid), p->at<int>(L.uext),
-                         p->at<float2>(L.twM), p->radM, p->at<float>(L.F),
-                         split ? p->at<uint16_t>(L.Fhi) : nullptr,
-                         split ? p->at<uint16_t>(L.Flo) : nullptr, s));
+  st = enqueue_fields(p, vis, ngrid, s);
+  if (st != BS_OK) return st;
   st = delta_reset(p, s);
   if (st != BS_OK) return st;
   p->loaded = true;
@@ -676,7 +841,7 @@ bs_status bs_mabs(bs_plan p, const int32_t *block, double *out_full, int accumul
   const WsLayout &L = p->L;
   const long long full_bstride = (long long)p->ntrip * nc * nc * nc;
   if (out_full) BS_CUDA(launch_full_fill(out_full, full_bstride, p->batch, p->ntrip, nc, blk, 0.0, s));
-  if (p->d.precision == BS_PREC_SPLIT_BF16) {
+  if (p->d.precision == BS_PREC_SPLIT_BF16 || p->multires) {
     st = mabs_tc(p, blk, out_full, accumulate, s);
     if (st != BS_OK) return st;
   } else {

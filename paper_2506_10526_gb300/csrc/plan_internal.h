@@ -21,6 +21,17 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 
+// Fields at one image side M: the rings that need it (slots), where they live
+// in the workspace, and their tensor maps.
+struct Level {
+  int M = 0, UC = 1, nslot = 0;
+  Radices rad;
+  std::vector<int> slot_of;  // [nb], -1: no field at this level
+  std::vector<int> ring_of;  // [nslot]
+  size_t offF = 0, offFhi = 0, offFlo = 0, offTw = 0, offSlot = 0, offRing = 0;
+  CUtensorMap maps[2]{};     // BF16 hi, lo (host copies; device copies at L.maps)
+};
+
 }  // namespace bsi
 
 using namespace bsi;  // internal header: plan state uses the library types unqualified
@@ -36,6 +47,10 @@ struct bs_plan_s {
   std::vector<int> cells;        // packed (u + 32768) | (v + 32768) << 16 of binned cells
   std::vector<int> uext;         // [nb]
   std::vector<double> umean;     // [nb] mean |U| of each ring's cells
+  std::vector<int> cring;        // [nb] largest |u| or |v| of a ring's cells
+  std::vector<Level> levels;     // image sides; one level holding every ring unless multires
+  std::vector<int> lev_of_trip;  // [ntrip] level of each ring triple (-1: cannot close)
+  bool multires = false;
   std::vector<int> trips;        // [ntrip][3]
   std::vector<int> trip_of;      // [nb^3] -> trip index of sorted (i<=j<=l), else -1
   std::vector<long long> T;      // [ntrip] closed-triangle counts
@@ -53,9 +68,9 @@ struct bs_plan_s {
   std::vector<ColEntry> h_cols;
   std::vector<PairTile> h_ptiles;
   std::vector<TcTile> h_tctiles;
-  CUtensorMap maps[2]{};  // hi, lo (host copies; device copies at L.maps)
+
   bool maps_ready = false;
-  TcGroup h_group{};
+  std::vector<TcGroup> h_groups;
   int nsm = 152;
 
   template <class T_>
@@ -75,11 +90,14 @@ bs_status ensure_tensor_maps(bs_plan p, cudaStream_t s);
 bs_status check_device_error(bs_plan p, cudaStream_t s);
 void accumulate_block_nnu(bs_plan p, const int *blk);
 bs_status upload_nnu(bs_plan p, cudaStream_t s);
-// Append the tensor-core work of one channel block of plan p (all realisations)
-// as shape group `group`; column entries are appended to cols, tiles to tiles.
-// Returns the group descriptor (device pointers of p, column list offset
-// relative to the concatenated list on the device at cols_dev).
-TcGroup build_tc_work(bs_plan p, const int *blk, int group, std::vector<ColEntry> &cols,
-                      const ColEntry *cols_dev, std::vector<TcTile> &tiles, double *out_full,
-                      int accumulate, int min_tiles);
+// Append the tensor-core work of one channel block of plan p (all
+// realisations): one shape group per image level, numbered from group_base.
+// Column entries are appended to cols, tiles to tiles (col_off relative to
+// the concatenated list at cols_dev).  Returns the group descriptors.
+std::vector<TcGroup> build_tc_work(bs_plan p, const int *blk, int group_base,
+                                   std::vector<ColEntry> &cols, const ColEntry *cols_dev,
+                                   std::vector<TcTile> &tiles, double *out_full, int accumulate,
+                                   int min_tiles);
+// Enqueue shell masks + field FFTs of every level (kernel launches only).
+bs_status enqueue_fields(bs_plan p, const void *vis, const float *ngrid, cudaStream_t s);
 }  // namespace bsi

@@ -33,20 +33,20 @@ def test_header_declarations_exported(lib):
 
 
 def test_abi_version(lib):
-    assert lib.bs_abi_version() == 1
+    assert lib.bs_abi_version() == 2
 
 
 def test_desc_validation_and_no_device(lib):
     import torch
     edges = (ctypes.c_double * 3)(0.0, 2.0, 4.0)
     h = ctypes.c_void_p()
-    bad = bs.PlanDesc(7, 4, 2, edges, 0, 0, 1, 1, 1, 1, 1)  # odd nt
+    bad = bs.PlanDesc(7, 4, 2, edges, 0, 0, 1, 1, 1, 1, 1, 0)  # odd nt
     assert lib.bs_plan_create(ctypes.byref(bad), ctypes.byref(h)) == 1
     assert b"nt" in lib.bs_last_error(None)
     desc_edges = (ctypes.c_double * 3)(0.0, 4.0, 2.0)  # not ascending
-    bad = bs.PlanDesc(16, 4, 2, desc_edges, 0, 0, 1, 1, 1, 1, 1)
+    bad = bs.PlanDesc(16, 4, 2, desc_edges, 0, 0, 1, 1, 1, 1, 1, 0)
     assert lib.bs_plan_create(ctypes.byref(bad), ctypes.byref(h)) == 1
-    good = bs.PlanDesc(16, 4, 2, edges, 0, 0, 1, 1, 1, 1, 1)
+    good = bs.PlanDesc(16, 4, 2, edges, 0, 0, 1, 1, 1, 1, 1, 0)
     st = lib.bs_plan_create(ctypes.byref(good), ctypes.byref(h))
     if not torch.cuda.is_available():
         assert st == 2  # BS_ERR_NO_DEVICE: no CPU fallback

@@ -34,14 +34,15 @@ def _points(T, trips):
     return pts, chosen
 
 
-@pytest.mark.parametrize("precision,tol", [(1, 1e-3), (0, 1e-5)])
-def test_mwa_block_sampled_parity(precision, tol):
+@pytest.mark.parametrize("precision,multires,tol", [(1, True, 1e-3), (1, False, 1e-3),
+                                                    (0, False, 1e-5)])
+def test_mwa_block_sampled_parity(precision, multires, tol):
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     import paper_2506_10526_gb300 as bs
     vis = synth.sky_visibilities(NT, NC, 2000, f_ng=0.5, sigma=0.5)
-    plan = bs.Plan(NT, NC, EDGES, precision=precision)
+    plan = bs.Plan(NT, NC, EDGES, precision=precision, multires=multires)
     assert plan.M == 384
     plan.grid_load(torch.from_numpy(vis[None]).cuda())
     blk = (0, BLOCK, 0, BLOCK, 0, BLOCK)
@@ -63,5 +64,6 @@ def test_mwa_block_sampled_parity(precision, tol):
     plan.close()
     assert np.all(cnt > 0)
     err = np.abs(got - want.real) / babs.real
-    print(f"precision {precision}: sampled kappa-normalised error max {err.max():.3e}")
+    print(f"precision {precision} multires {multires}: sampled kappa-normalised error max "
+          f"{err.max():.3e}")
     assert err.max() < tol, err

@@ -11,7 +11,7 @@ import synth
 pytestmark = pytest.mark.gpu
 
 GROUPS = [dict(nt=32, nchan=8, edges=list(synth.edges_linear(4, 16)), batch=3),
-          dict(nt=40, nchan=6, edges=list(synth.edges_log(5, 1.5, 19.0)), batch=2)]
+          dict(nt=40, nchan=6, edges=list(synth.edges_log(5, 1.5, 19.0)), batch=2, multires=True)]
 
 
 def _realisation(g, k):

@@ -31,7 +31,7 @@ def _torch():
 
 
 def _run(vis, edges, flags=None, ngrid=None, precision=0, block=None, full=True, batch_vis=None,
-         norm_A=1.0, r=1.0, rprime=1.0, dnu_c=1.0):
+         norm_A=1.0, r=1.0, rprime=1.0, dnu_c=1.0, multires=False):
     torch = _torch()
     import paper_2506_10526_gb300 as bs
     v = vis if batch_vis is None else batch_vis
@@ -39,7 +39,7 @@ def _run(vis, edges, flags=None, ngrid=None, precision=0, block=None, full=True,
         v = v[None]
     batch, nc, nt, _ = v.shape
     plan = bs.Plan(nt, nc, edges, precision=precision, batch=batch, norm_A=norm_A, r=r,
-                   rprime=rprime, dnu_c=dnu_c)
+                   rprime=rprime, dnu_c=dnu_c, multires=multires)
     vd = torch.from_numpy(np.ascontiguousarray(v.astype(np.complex64))).cuda()
     gd = None if ngrid is None else torch.from_numpy(ngrid.astype(np.float32)).cuda()
     plan.grid_load(vd, ngrid=gd, chan_flags=flags)
@@ -91,9 +91,9 @@ def test_three_mode_golden_gpu(precision):
     assert abs(out["full"][0, 0, 0, 0, 0]) < 1e-6
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision,multires", [(0, False), (1, False), (1, True)])
 @pytest.mark.parametrize("flagged", [False, True])
-def test_tiny_config_full_cube(flagged, precision):
+def test_tiny_config_full_cube(flagged, precision, multires):
     """64^2 grid, 16 channels, 8 linear rings (and the coarse-band flags):
     every ring triple x channel triple against the oracle, FP32 SIMT and
     split-BF16 tensor-core contraction."""
@@ -101,11 +101,12 @@ def test_tiny_config_full_cube(flagged, precision):
     edges = synth.edges_linear(8, 32)
     vis = synth.sky_visibilities(nt, nc, seed=1001)
     flags = synth.flag_mask_coarse_band(nc) if flagged else None
-    out = _run(vis, edges, flags=flags, precision=precision)
+    out = _run(vis, edges, flags=flags, precision=precision, multires=multires)
     ref, babs = _oracle(vis, edges, flags)
     np.testing.assert_array_equal(out["T"], ref["T"])
     e = _kappa_err(out["full"][0], ref["B"].real, babs)
-    print(f"precision {precision} flagged {flagged}: max kappa-normalised error {e:.3e}")
+    print(f"precision {precision} multires {multires} flagged {flagged}: "
+          f"max kappa-normalised error {e:.3e}")
     tol = TOL[precision]
     assert e < tol, e
     bbar, cnt = oracle.collapse_fold(ref["B"].real)
@@ -121,8 +122,8 @@ def test_tiny_config_full_cube(flagged, precision):
     assert err3.max() < tol, err3.max()
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_ragged_sizes_occupancy_and_blocks(precision):
+@pytest.mark.parametrize("precision,multires", [(0, False), (1, False), (1, True)])
+def test_ragged_sizes_occupancy_and_blocks(precision, multires):
     """Non-tile-multiple sizes: nt = 40, 11 channels (non-smooth: direct DFT in
     the delay transform), log rings, empty cells with N_g in {0, 1, 2, 3},
     one flagged channel, and three channel blocks that tile the cube."""
@@ -139,7 +140,7 @@ def test_ragged_sizes_occupancy_and_blocks(precision):
     occ = oracle.ring_labels(nt, edges, occupancy=ngrid > 0)
     torch = _torch()
     import paper_2506_10526_gb300 as bs
-    plan = bs.Plan(nt, nc, edges, precision=precision)
+    plan = bs.Plan(nt, nc, edges, precision=precision, multires=multires)
     plan.grid_load(torch.from_numpy(vis[None]).cuda(), ngrid=torch.from_numpy(ngrid).cuda(),
                    chan_flags=flags)
     full = torch.full((1, plan.ntrip, nc, nc, nc), np.nan, dtype=torch.float64, device="cuda")
@@ -191,26 +192,26 @@ def test_batch_and_scales(precision):
         assert np.abs(out["bs3d"][b][keep] - b3[keep]).max() / b3_scale < tol
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_degenerate_cases(precision):
+@pytest.mark.parametrize("precision,multires", [(0, False), (1, False), (1, True)])
+def test_degenerate_cases(precision, multires):
     """One channel (the single-frequency ABS special case), a single ring,
     an empty ring, every channel flagged, and the constant field (B = 1/A)."""
     nt = 16
     tol = TOL[precision]
     vis = synth.sky_visibilities(nt, 1, seed=9)
     edges = [1.0, 3.0, 3.1, 7.0]  # ring 1 holds no cell
-    out = _run(vis, edges, precision=precision)
+    out = _run(vis, edges, precision=precision, multires=multires)
     ref, babs = _oracle(vis, edges)
     assert _kappa_err(out["full"][0], ref["B"].real, babs) < tol
-    out = _run(vis, [1.0, 7.0], precision=precision)
+    out = _run(vis, [1.0, 7.0], precision=precision, multires=multires)
     ref, babs = _oracle(vis, [1.0, 7.0])
     assert _kappa_err(out["full"][0], ref["B"].real, babs) < tol
     vis4 = synth.sky_visibilities(nt, 4, seed=10)
-    out = _run(vis4, [1.0, 4.0, 7.0], flags=np.ones(4, np.uint8), precision=precision)
+    out = _run(vis4, [1.0, 4.0, 7.0], flags=np.ones(4, np.uint8), precision=precision, multires=multires)
     assert np.all(np.isnan(out["full"])) and np.all(np.isnan(out["delta"]))
     assert np.all(out["bs3d"] == 0)
     ones = np.ones((3, nt, nt), np.complex64)
-    out = _run(ones, [1.0, 4.0, 7.0], norm_A=4.0, precision=precision)
+    out = _run(ones, [1.0, 4.0, 7.0], norm_A=4.0, precision=precision, multires=multires)
     f = out["full"][0]
     ok = ~np.isnan(f)
     np.testing.assert_allclose(f[ok], 0.25, rtol=1e-5 if precision == 0 else 1e-3)
