@@ -45,11 +45,37 @@ __global__ void k_delta_norm(const double *__restrict__ dsum, const long long *_
   const double *ds = dsum + ((long long)b * ntrip + trip) * plane;
   double *o = out + ((long long)b * ntrip + trip) * plane;
   const double tn = tnorm[trip];
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < plane;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int i1 = (int)(t / n2), i2 = (int)(t - (long long)i1 * n2);
-    o[t] = folded_bbar(ds, nnu, tn, nc, i1, i2);
+  const double nan = __longlong_as_double(0x7ff8000000000000LL);
+  if (tn == 0.0) {  // no closed triangle: undefined everywhere, nothing to read
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < plane;
+         t += (long long)gridDim.x * blockDim.x)
+      o[t] = nan;
+    return;
   }
+  // element t pairs with its point reflection plane-1-t; each pair is read once
+  const long long half = (plane + 1) / 2;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < half;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long j = plane - 1 - t;
+    double s = ds[t];
+    long long c = nnu[t];
+    if (j != t) {
+      s += ds[j];
+      c += nnu[j];
+    }
+    const double v = c > 0 ? s * tn / (double)c : nan;
+    o[t] = v;
+    o[j] = v;
+  }
+}
+
+__global__ void k_zero_planes(double *__restrict__ dsum, const int *__restrict__ trips, int ntr,
+                              int ntrip, long long plane) {
+  const int k = blockIdx.y, b = blockIdx.z;
+  double *o = dsum + ((long long)b * ntrip + trips[k]) * plane;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < plane;
+       t += (long long)gridDim.x * blockDim.x)
+    o[t] = 0.0;
 }
 
 __device__ void dft_direct(const float2 *x, float2 *y, int N, const float2 *tw, float sign) {
@@ -79,6 +105,7 @@ __global__ void k_bs3d_rows(const double *__restrict__ dsum, const long long *__
   const int n2 = 2 * nc - 1, h = nc / 2;
   const double *ds = dsum + ((long long)b * ntrip + trip) * (long long)n2 * n2;
   const double tn = tnorm[trip];
+  if (tn == 0.0) return;  // no closed triangle: the column pass writes zeros
   for (int t = threadIdx.x; t < nc; t += blockDim.x) tw[t] = twN[t];
   for (int m = threadIdx.x; m < nc; m += blockDim.x) {
     double acc = 0.0;
@@ -107,13 +134,20 @@ __global__ void k_bs3d_rows(const double *__restrict__ dsum, const long long *__
 }
 
 __global__ void k_bs3d_cols(const float2 *__restrict__ tmp, double *__restrict__ out, int ntrip,
-                            int nc, const float2 *__restrict__ twN, Radices radN, double scale) {
+                            int nc, const float2 *__restrict__ twN, Radices radN, double scale,
+                            const double *__restrict__ tnorm) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2 *tw = reinterpret_cast<float2 *>(smem_raw);
   float2 *bufA = tw + nc;
   float2 *bufB = bufA + nc;
   const int bb = blockIdx.x, trip = blockIdx.y, b = blockIdx.z;
   const int h = nc / 2;
+  if (tnorm[trip] == 0.0) {
+    double *ob = out + ((long long)b * ntrip + trip) * (long long)nc * nc;
+    const int bidx = (bb < nc - h) ? bb + h : bb - nc + h;
+    for (int k = threadIdx.x; k < nc; k += blockDim.x) ob[(long long)k * nc + bidx] = 0.0;
+    return;
+  }
   const float2 *tb = tmp + ((long long)b * ntrip + trip) * (long long)nc * nc + (long long)bb * nc;
   for (int t = threadIdx.x; t < nc; t += blockDim.x) {
     tw[t] = twN[t];
@@ -180,6 +214,14 @@ cudaError_t launch_delta_norm(const double *dsum, const long long *nnu, const do
   return cudaGetLastError();
 }
 
+cudaError_t launch_zero_planes(double *dsum, const int *trips, int ntr, int batch, int ntrip,
+                               long long plane, cudaStream_t s) {
+  if (ntr == 0) return cudaSuccess;
+  dim3 grid((unsigned)std::min<long long>((plane + 255) / 256, 256), ntr, batch);
+  k_zero_planes<<<grid, 256, 0, s>>>(dsum, trips, ntr, ntrip, plane);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_bs3d(const double *dsum, const long long *nnu, const double *tnorm, float2 *tmp,
                         double *out, int batch, int ntrip, int nc, const float2 *twN,
                         const Radices &radN, double scale, cudaStream_t s) {
@@ -193,7 +235,7 @@ cudaError_t launch_bs3d(const double *dsum, const long long *nnu, const double *
   k_bs3d_rows<<<grid, threads, smem, s>>>(dsum, nnu, tnorm, tmp, ntrip, nc, twN, radN);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_bs3d_cols<<<grid, threads, smem, s>>>(tmp, out, ntrip, nc, twN, radN, scale);
+  k_bs3d_cols<<<grid, threads, smem, s>>>(tmp, out, ntrip, nc, twN, radN, scale, tnorm);
   return cudaGetLastError();
 }
 

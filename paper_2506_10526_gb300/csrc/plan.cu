@@ -132,6 +132,7 @@ void compute_layout(bs_plan p) {
   L.maps = take(2 * p->levels.size() * sizeof(CUtensorMap));
   L.tcgroup = take(p->levels.size() * sizeof(TcGroup));
   L.mlptab = take(((size_t)p->ntrip * 4 + 33) * sizeof(float));
+  L.ztrips = take((size_t)p->ntrip * sizeof(int));
   L.total = o;
 }
 
@@ -285,6 +286,7 @@ bs_status run_counts(bs_plan p, const int8_t *lab_dev, cudaStream_t s) {
                           cudaMemcpyHostToDevice, s));
   BS_CUDA(cudaStreamSynchronize(s));
   p->counts_ready = true;
+  p->dsum_clean = false;
   return BS_OK;
 }
 
@@ -354,8 +356,21 @@ bs_status delta_reset(bs_plan p, cudaStream_t s) {
   std::fill(p->nnu.begin(), p->nnu.end(), 0LL);
   p->nnu_dirty = true;
   const size_t n2 = (size_t)(2 * p->nc - 1);
-  BS_CUDA(cudaMemsetAsync(p->at<double>(p->L.dsum), 0,
-                          (size_t)p->batch * p->ntrip * n2 * n2 * sizeof(double), s));
+  if (!p->dsum_clean || !p->counts_ready) {
+    BS_CUDA(cudaMemsetAsync(p->at<double>(p->L.dsum), 0,
+                            (size_t)p->batch * p->ntrip * n2 * n2 * sizeof(double), s));
+    p->dsum_clean = p->counts_ready;
+    p->zero_trips.clear();
+    for (int t = 0; t < p->ntrip; ++t)
+      if (p->counts_ready && p->T[t] > 0) p->zero_trips.push_back(t);
+    if (!p->zero_trips.empty())
+      BS_CUDA(cudaMemcpyAsync(p->at<int>(p->L.ztrips), p->zero_trips.data(),
+                              p->zero_trips.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    return BS_OK;
+  }
+  // only ring triples with closed triangles are ever accumulated into
+  BS_CUDA(launch_zero_planes(p->at<double>(p->L.dsum), p->at<int>(p->L.ztrips),
+                             (int)p->zero_trips.size(), p->batch, p->ntrip, (long long)(n2 * n2), s));
   return BS_OK;
 }
 
