@@ -94,17 +94,6 @@ def make_vis(w, seed):
     return synth.sky_visibilities(w["nt"], w["nc"], seed, f_ng=0.5, sigma=0.5).astype(np.complex64)
 
 
-def blocks_of(nc, bsz):
-    nb_ = (nc + bsz - 1) // bsz
-    out = []
-    for a in range(nb_):
-        for b in range(nb_):
-            for c in range(nb_):
-                out.append((a * bsz, min(nc, (a + 1) * bsz), b * bsz, min(nc, (b + 1) * bsz),
-                            c * bsz, min(nc, (c + 1) * bsz)))
-    return out
-
-
 class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -252,6 +241,7 @@ def main():
     import torch.distributed as dist
 
     import paper_2506_10526_gb300 as bs
+    from paper_2506_10526_gb300.sharding import blocks_of, rank_block, reduce_step_stats
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -287,7 +277,7 @@ def main():
         return nclos * (b[1] - b[0]) * (b[3] - b[2]) * (b[5] - b[4])
 
     def step(i, e2e=False, ev=None):
-        b = jobs[(i * world + rank) % len(jobs)]
+        b = rank_block(jobs, i, world, rank)
         if e2e:
             vis_d.copy_(vis_h, non_blocking=True)
         plan.grid_load(vis_d)
@@ -324,13 +314,7 @@ def main():
     clk = clocks.stop()
     ms = t0.elapsed_time(t1)
     kms = [a.elapsed_time(b) for a, b in kev]
-    if world > 1:
-        tt = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-        ev_t = torch.tensor([float(evals)], dtype=torch.float64, device=dev)
-        dist.all_reduce(ev_t)
-        evals = float(ev_t.item())
+    ms, evals = reduce_step_stats(ms, evals, world, dev)
     value = evals / (ms / 1e3)
 
     e2e = None

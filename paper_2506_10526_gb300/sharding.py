@@ -1,0 +1,45 @@
+"""Host-side sharding of the channel cube across ranks (one process per GPU).
+
+The job of a plan is the full channel cube nc^3 of every closable ring
+triple.  It splits into B^3 blocks of side B (the last ones ragged); rank r of
+W takes blocks r, r + W, r + 2W, ... in step order, so ranks never share a
+block and need no data-path collective: each rank's collapse sums hold its
+own blocks (the sum over ranks is the job's).  Timing is the maximum over
+ranks; throughput counts every rank's evaluations.
+"""
+from __future__ import annotations
+
+
+def blocks_of(nc: int, bsz: int):
+    """Half-open channel blocks (nu1_lo, nu1_hi, nu2_lo, nu2_hi, nu3_lo, nu3_hi)."""
+    n = (nc + bsz - 1) // bsz
+    out = []
+    for a in range(n):
+        for b in range(n):
+            for c in range(n):
+                out.append((a * bsz, min(nc, (a + 1) * bsz), b * bsz, min(nc, (b + 1) * bsz),
+                            c * bsz, min(nc, (c + 1) * bsz)))
+    return out
+
+
+def rank_block(jobs, step: int, world: int, rank: int):
+    """Block of `rank` at `step` (steps cycle through the job)."""
+    return jobs[(step * world + rank) % len(jobs)]
+
+
+def block_evals(block, closable_triples: int) -> int:
+    b = block
+    return closable_triples * (b[1] - b[0]) * (b[3] - b[2]) * (b[5] - b[4])
+
+
+def reduce_step_stats(ms: float, evals: float, world: int, device=None):
+    """(max over ranks of the elapsed ms, sum over ranks of evaluations)."""
+    if world <= 1:
+        return ms, evals
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e = torch.tensor([float(evals)], dtype=torch.float64, device=device)
+    dist.all_reduce(e)
+    return float(t.item()), float(e.item())
