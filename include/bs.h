@@ -305,6 +305,47 @@ bs_status bs_mlp_grad(bs_mlp mlp, const float *x_dev, const float *t_dev, int n,
 bs_status bs_mlp_train(bs_mlp mlp, const float *x_dev, const float *t_dev, int n, int steps,
                        int batch, float lr, uint64_t seed, float *loss_host, void *cuda_stream);
 
+/* ---- Monte Carlo sky generator (the validation sky of Section 4) ---------
+ * Draws realisations of the non-Gaussian sky of Eq. (mb1) on the GPU and
+ * writes their gridded visibilities in the layout bs_grid_load reads, so a
+ * Monte Carlo ensemble (bs_mc_*) runs with no host traffic per realisation.
+ * Realisation r of a generator (nt, nchan, slope, sigma, f_ng) and a seed:
+ *   w[z][y][x]  unit normals: cell c = (z nt + y) nt + x is normal c mod 4 of
+ *               Philox4x32-10 (Salmon et al. 2011) call q = c div 4 with
+ *               counter words (q lo, q hi, r lo, r hi) and key (seed lo,
+ *               seed hi); the call's outputs (o0, o1) give cells 4q, 4q+1 by
+ *               Box-Muller, sqrt(-2 ln a) (cos 2 pi b, sin 2 pi b) with
+ *               a = (o0 + 1/2) 2^-32, b = (o1 + 1/2) 2^-32, and (o2, o3) give
+ *               cells 4q+2, 4q+3 the same way;
+ *   g           IDFT3( sqrt(P) DFT3(w) ), P(k) = A |k|^slope on the periodic
+ *               box (k = 2 pi (fftfreq), unit cells), P(0) = 0, A such that
+ *               the mean of P over the box is sigma^2;
+ *   delta       g + f_ng (g^2 - sigma^2)                        (Eq. mb1)
+ *   V[z][v + nt/2][u + nt/2] = sum_{x,y} delta[z][y][x] e^{-2 pi i (ux + vy)/nt}.
+ * FP32 arithmetic (FFTs, Box-Muller); a double-precision restatement of the
+ * same definition agrees to ~1e-6 of max |V|.
+ *  nt         even, 8..4096;  nchan 1..4096;  both of the form 2^a 3^b 5^c
+ *             (otherwise BS_ERR_UNSUPPORTED)
+ *  max_batch  1..131070 realisations per bs_sky_generate call; the generator
+ *             holds ceil(max_batch/2) nchan nt^2 complex64 of scratch plus a
+ *             float sqrt(P) table of nchan nt^2
+ * Errors: BS_ERR_ARG, BS_ERR_UNSUPPORTED, BS_ERR_NO_DEVICE, BS_ERR_OOM,
+ * BS_ERR_CUDA.  bs_sky_last_error(NULL) returns the last creation error of
+ * the calling thread. */
+typedef struct bs_sky_s *bs_sky;
+bs_status bs_sky_create(int nt, int nchan, double slope, double sigma, double f_ng, int max_batch,
+                        bs_sky *out);
+bs_status bs_sky_destroy(bs_sky sky);
+const char *bs_sky_last_error(bs_sky sky);
+/* Realisations realisation0 .. realisation0 + batch - 1 into vis_dev,
+ * complex64 [batch][nchan][nt][nt] (device, caller-owned, 8-byte aligned),
+ * asynchronously on cuda_stream.  Calls on one generator must not overlap on
+ * the GPU (they share its scratch): use one stream per generator.
+ * Errors: BS_ERR_ARG (batch outside 1..max_batch, NULL buffer), BS_ERR_STATE
+ * (an earlier CUDA error), BS_ERR_CUDA. */
+bs_status bs_sky_generate(bs_sky sky, uint64_t seed, uint64_t realisation0, int batch,
+                          void *vis_dev, void *cuda_stream);
+
 /* Closed-triangle counts T(i,j,l) without any device allocation.
  * The paper has no counterpart: this entry point exists for callers that
  * cannot call cudaMalloc (a pipeline bound to its own pre-allocated memory

@@ -36,6 +36,7 @@ EXPORTS = ("bs_abi_version", "bs_plan_create", "bs_plan_destroy", "bs_last_error
            "bs_mc_stats",
            "bs_mlp_features", "bs_mlp_create", "bs_mlp_destroy", "bs_mlp_last_error",
            "bs_mlp_params", "bs_mlp_fit_norm", "bs_mlp_forward", "bs_mlp_grad", "bs_mlp_train",
+           "bs_sky_create", "bs_sky_destroy", "bs_sky_last_error", "bs_sky_generate",
            "bs_counts_noalloc")
 
 _lib = None
@@ -83,6 +84,11 @@ def lib() -> ctypes.CDLL:
             L.bs_bs3d.argtypes = [P, P, P]
             L.bs_check_hermitian.argtypes = [P, P, D, P]
             L.bs_counts_noalloc.argtypes = [I, I, P, P, P, P]
+            L.bs_sky_create.argtypes = [I, I, D, D, D, I, ctypes.POINTER(P)]
+            L.bs_sky_destroy.argtypes = [P]
+            L.bs_sky_last_error.argtypes = [P]
+            L.bs_sky_last_error.restype = ctypes.c_char_p
+            L.bs_sky_generate.argtypes = [P, ctypes.c_uint64, ctypes.c_uint64, I, P, P]
             L.bs_mc_create.argtypes = [P, I, ctypes.POINTER(P)]
             L.bs_mc_destroy.argtypes = [P]
             L.bs_mc_last_error.argtypes = [P]
@@ -107,7 +113,7 @@ def lib() -> ctypes.CDLL:
             L.bs_mlp_train.argtypes = [P, P, P, I, I, I, ctypes.c_float, ctypes.c_uint64, P, P]
             for name in EXPORTS:
                 if name not in ("bs_abi_version", "bs_last_error", "bs_mc_last_error",
-                                "bs_mlp_last_error"):
+                                "bs_mlp_last_error", "bs_sky_last_error"):
                     getattr(L, name).restype = I
             _lib = L
     return _lib
@@ -265,6 +271,51 @@ def counts_noalloc(nt: int, edges, tri_out, ngrid=None, stream=None):
         raise BsError(st, "bs_counts_noalloc failed (sizes beyond nt <= 1024, nbins <= 32 are "
                           "rejected)")
 
+
+
+class SkyGenerator:
+    """bs_sky_*: realisations of the non-Gaussian validation sky (Eq. mb1)
+    drawn on the GPU, written as centred visibilities [batch][nchan][nt][nt]."""
+
+    def __init__(self, nt, nchan, slope=-2.0, sigma=0.5, f_ng=0.5, max_batch=1):
+        L = lib()
+        self._L = L
+        h = ctypes.c_void_p()
+        st = L.bs_sky_create(int(nt), int(nchan), float(slope), float(sigma), float(f_ng),
+                             int(max_batch), ctypes.byref(h))
+        if st != BS_OK:
+            raise BsError(st, L.bs_sky_last_error(None).decode())
+        self._h = h
+        self.nt, self.nchan, self.max_batch = int(nt), int(nchan), int(max_batch)
+
+    def generate(self, seed, realisation0, out=None, batch=None, stream=None):
+        """Realisations realisation0 .. + batch - 1 into `out` (a complex64 CUDA
+        tensor of shape (batch, nchan, nt, nt); allocated when None)."""
+        import torch
+        if out is None:
+            b = self.max_batch if batch is None else int(batch)
+            out = torch.empty((b, self.nchan, self.nt, self.nt), dtype=torch.complex64,
+                              device="cuda")
+        if out.dtype != torch.complex64 or not out.is_cuda or not out.is_contiguous() or \
+                tuple(out.shape[1:]) != (self.nchan, self.nt, self.nt):
+            raise ValueError("out must be a contiguous complex64 CUDA tensor (batch, nchan, nt, nt)")
+        st = self._L.bs_sky_generate(self._h, ctypes.c_uint64(int(seed)),
+                                     ctypes.c_uint64(int(realisation0)), int(out.shape[0]),
+                                     _dptr(out), _stream_ptr(stream))
+        if st != BS_OK:
+            raise BsError(st, self._L.bs_sky_last_error(self._h).decode())
+        return out
+
+    def close(self):
+        if self._h:
+            self._L.bs_sky_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 class Ensemble:
     """bs_mc_*: batched Monte Carlo over shape groups.

@@ -17,6 +17,12 @@ struct Radices {
   int r[24] = {0};
 };
 
+// n = 4^a 2^b 3^c 5^d: the Stockham stage radices (4s first, then 2, 3, 5);
+// false when n has another prime factor.
+bool factor_radices(int n, Radices &r);
+// exp(+2 pi i t / n), t in [0, n), computed in FP64 and rounded to FP32.
+std::vector<float2> twiddles(int n);
+
 // One column of the triple contraction: field (l, nu3) and its ring triple.
 struct ColEntry {
   int field;  // l * nchan + nu3

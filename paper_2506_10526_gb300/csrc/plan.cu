@@ -20,6 +20,15 @@ thread_local std::string g_create_error = "no error";
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+bool is_smooth(int n) {
+  Radices r;
+  return n == 1 || factor_radices(n, r);
+}
+
+}  // namespace
+
+namespace bsi {
+
 bool factor_radices(int n, Radices &r) {
   r.n = 0;
   if (n <= 0) return false;
@@ -47,11 +56,6 @@ bool factor_radices(int n, Radices &r) {
   return true;
 }
 
-bool is_smooth(int n) {
-  Radices r;
-  return n == 1 || factor_radices(n, r);
-}
-
 // exp(+2 pi i t / n), t in [0, n), FP64 then rounded to FP32
 std::vector<float2> twiddles(int n) {
   std::vector<float2> tw(n);
@@ -61,10 +65,6 @@ std::vector<float2> twiddles(int n) {
   }
   return tw;
 }
-
-}  // namespace
-
-namespace bsi {
 
 bs_status fail(bs_plan p, bs_status s, const std::string &msg) {
   if (p)

@@ -102,3 +102,68 @@ def edges_linear(nbins: int, u_max: float) -> np.ndarray:
 def edges_log(nbins: int, u_min: float, u_max: float) -> np.ndarray:
     """nbins log-spaced rings covering u_min <= |U| < u_max."""
     return np.geomspace(float(u_min), float(u_max), nbins + 1)
+
+
+# ---------------------------------------------------------------------------
+# Counter-based generator shared (by definition, not by code) with the GPU
+# sky generator: Philox4x32 with 10 rounds (Salmon, Moraes, Dror & Shaw 2011,
+# "Parallel random numbers: as easy as 1, 2, 3"), and Box-Muller normals.
+# ---------------------------------------------------------------------------
+
+_PH_M0, _PH_M1 = np.uint64(0xD2511F53), np.uint64(0xCD9E8D57)
+_PH_W0, _PH_W1 = np.uint64(0x9E3779B9), np.uint64(0xBB67AE85)
+_MASK32 = np.uint64(0xFFFFFFFF)
+
+
+def philox4x32(counter, key, rounds: int = 10):
+    """Philox4x32: counter uint64 array [..., 4] of 32-bit words, key [2].
+    Each round: (hi0, lo0) = M0 * c0, (hi1, lo1) = M1 * c2,
+    c = (hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0); then k += (W0, W1)."""
+    c = np.asarray(counter, dtype=np.uint64) & _MASK32
+    c0, c1, c2, c3 = c[..., 0], c[..., 1], c[..., 2], c[..., 3]
+    k0, k1 = np.uint64(int(key[0]) & 0xFFFFFFFF), np.uint64(int(key[1]) & 0xFFFFFFFF)
+    for _ in range(rounds):
+        p0 = _PH_M0 * c0
+        p1 = _PH_M1 * c2
+        hi0, lo0 = p0 >> np.uint64(32), p0 & _MASK32
+        hi1, lo1 = p1 >> np.uint64(32), p1 & _MASK32
+        c0, c1, c2, c3 = hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0
+        k0 = (k0 + _PH_W0) & _MASK32
+        k1 = (k1 + _PH_W1) & _MASK32
+    return np.stack([c0, c1, c2, c3], axis=-1)
+
+
+def philox_normals(ncell: int, seed: int, realisation: int) -> np.ndarray:
+    """Unit normals for cells 0..ncell-1: Philox call q (counter words
+    q_lo, q_hi, r_lo, r_hi; key = seed lo, hi) gives four uint32 u; with
+    u' = (u + 1/2) 2^-32, cells 4q, 4q+1 get Box-Muller of (u'0, u'1) and
+    cells 4q+2, 4q+3 of (u'2, u'3):  sqrt(-2 ln a) (cos 2 pi b, sin 2 pi b)."""
+    nq = (ncell + 3) // 4
+    q = np.arange(nq, dtype=np.uint64)
+    r = np.uint64(realisation)
+    ctr = np.stack([q & _MASK32, q >> np.uint64(32), np.full(nq, r & _MASK32, np.uint64),
+                    np.full(nq, r >> np.uint64(32), np.uint64)], axis=-1)
+    out = philox4x32(ctr, (seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF))
+    u = (out.astype(np.float64) + 0.5) * 2.0**-32
+    rad0 = np.sqrt(-2.0 * np.log(u[:, 0]))
+    rad1 = np.sqrt(-2.0 * np.log(u[:, 2]))
+    n = np.empty((nq, 4))
+    n[:, 0] = rad0 * np.cos(2 * np.pi * u[:, 1])
+    n[:, 1] = rad0 * np.sin(2 * np.pi * u[:, 1])
+    n[:, 2] = rad1 * np.cos(2 * np.pi * u[:, 3])
+    n[:, 3] = rad1 * np.sin(2 * np.pi * u[:, 3])
+    return n.reshape(-1)[:ncell]
+
+
+def philox_sky_visibilities(nt: int, nc: int, seed: int, realisation: int, f_ng: float = 0.5,
+                            sigma: float = 0.5, slope: float = -2.0) -> np.ndarray:
+    """The validation sky of Eq. (mb1) drawn with the Philox normals above
+    (same recipe as sky_visibilities, other random numbers): white noise
+    w[z, y, x] = normals of cell (z nt + y) nt + x, g = IDFT(sqrt(P) DFT(w)),
+    delta = g + f (g^2 - sigma^2), V[nu] = fftshift(DFT2(delta[nu])).
+    complex128 (nc, nt, nt)."""
+    w = philox_normals(nc * nt * nt, seed, realisation).reshape(nc, nt, nt)
+    p = grf_power(nt, nc, slope, sigma)
+    g = np.fft.ifftn(np.sqrt(p) * np.fft.fftn(w)).real
+    d = g + f_ng * (g * g - sigma**2)
+    return visibilities(d)
