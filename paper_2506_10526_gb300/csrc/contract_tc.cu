@@ -13,10 +13,12 @@
 //   B = 512 channel pairs: nu1 in 32 x nu2 in 16        -> 2 x 256 TMEM columns
 //   K = image pixels in chunks of 32 (64-byte rows, 64B swizzle, K-major)
 // A hi/lo come from the field arrays the row pass writes, by TMA in boxes of
-// 8 fields x 32 pixels.  B hi/lo are made on the fly: 8 producer warps load
-// the FP32 rows of F_i and F_j, multiply, split and store them in the same
-// swizzled layout.  One thread issues 12 MMAs (M128 N256 K16) per stage.
-// Two pipeline stages; mbarriers hand stages between TMA, producers and MMA.
+// 8 fields x 32 pixels.  B hi/lo are made on the fly: a second TMA thread
+// streams the FP32 rows of F_i (32 channels) and F_j (16 channels) into a
+// four-deep ring (128-byte swizzle), and 8 producer warps multiply, split and
+// store the pairs in the operand layout.  One thread issues 12 MMAs
+// (M128 N256 K16) per stage.  Two operand stages; mbarriers hand stages
+// between the TMA threads, the producers and the MMA thread.
 //
 // Epilogue (the producer warps): tcgen05.ld of the 128 x 512 FP32 tile,
 // shared-memory pre-reduction keyed by (ring triple segment, nu1-nu2,
@@ -41,25 +43,32 @@ constexpr int KC = 32;                    // BF16 elements per K chunk = 64 byte
 constexpr int MROWS = 128;                // fields per tile
 constexpr int P1 = 32, P2 = 16;           // pair rectangle
 constexpr int NPAIR = P1 * P2;            // 512
-constexpr int STAGES = 2;
+constexpr int ASTAGES = 4;               // field-operand ring depth
+constexpr int STAGES = 2;                 // pair-operand ring depth
 constexpr int NPROD = 8;                  // producer / epilogue warps
-constexpr int NTHREADS = 32 * (2 + NPROD);
+constexpr int NTHREADS = 32 * (3 + NPROD);  // TMA (A), MMA, producers, TMA (rows)
 constexpr int GROUP = 8;                  // fields per TMA box
 constexpr int NGROUP = MROWS / GROUP;
 constexpr int A_BYTES = MROWS * KC * 2;   // 8 KB (hi or lo)
 constexpr int B_BYTES = NPAIR * KC * 2;   // 32 KB (hi or lo)
-constexpr int RAW_ROWS = 4 + P2;          // per warp: 4 nu1 rows + 16 nu2 rows
-constexpr int RAW_STRIDE = KC + 4;        // floats (padding against bank conflicts)
+constexpr int RSTAGES = 4;                // FP32 row ring depth
+constexpr int RAW_ROWS = P1 + P2;         // 32 rows of F_i, 16 of F_j
+constexpr int RAW_BYTES = RAW_ROWS * KC * 4;  // 6 KB: 128-byte rows, 128B swizzle
+constexpr int RAW_BOX_BYTES = 16 * KC * 4;    // one TMA box: 16 rows
 constexpr int RED_CAP = STAGES * 2 * B_BYTES / 4;  // floats in the B buffers
 
 constexpr int OFF_A = 0;
-constexpr int OFF_B = OFF_A + STAGES * 2 * A_BYTES;
+constexpr int OFF_B = OFF_A + ASTAGES * 2 * A_BYTES;
 constexpr int OFF_RAW = OFF_B + STAGES * 2 * B_BYTES;
-constexpr int OFF_ROW = OFF_RAW + NPROD * RAW_ROWS * RAW_STRIDE * 4;
+constexpr int OFF_ROW = OFF_RAW + RSTAGES * RAW_BYTES;
 constexpr int OFF_SEG = OFF_ROW + MROWS * 16;
 constexpr int MAX_SEG = 16;
+// tensor maps per level: BF16 hi/lo with boxes of 8, 32 and 128 field rows, FP32 rows
+constexpr int NMAPS = 7;
 constexpr int OFF_BAR = OFF_SEG + MAX_SEG * 16;
-constexpr int NBAR = 3 * STAGES + 3;      // a_full, b_full, empty per stage; acc_full, acc_empty, stall
+// a_full, a_empty per field stage; b_full, b_empty per pair stage; raw_full, raw_empty per
+// row stage; acc_full, acc_empty, stall
+constexpr int NBAR = 2 * ASTAGES + 2 * STAGES + 2 * RSTAGES + 3;
 constexpr int OFF_MISC = OFF_BAR + NBAR * 8;
 constexpr int SMEM_BYTES = OFF_MISC + 64 + 1024;  // + alignment slack
 
@@ -151,6 +160,11 @@ __device__ __forceinline__ uint64_t sw64_desc(uint32_t addr) {
 __device__ __forceinline__ uint32_t sw64_off(int r, int c) {
   return (uint32_t)(r * 64 + ((c ^ ((r >> 1) & 3)) << 4));
 }
+// Byte offset of 16-byte chunk c (0..7) of row r in a 128B-swizzled tile of
+// 128-byte rows (TMA SWIZZLE_128B on a 1024-byte aligned buffer).
+__device__ __forceinline__ uint32_t sw128_off(int r, int c) {
+  return (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4));
+}
 // BF16 hi/lo split of two FP32 values, packed (element 0 in the low half).
 __device__ __forceinline__ void split2(float v0, float v1, uint32_t &hi, uint32_t &lo) {
   __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
@@ -168,17 +182,29 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_contract_tc(const __grid_consta
   const uint32_t sA = smem_u32(sm + OFF_A), sB = smem_u32(sm + OFF_B);
   const uint32_t sBar = smem_u32(sm + OFF_BAR);
   auto a_full = [&](int s) { return sBar + 8 * s; };
-  auto b_full = [&](int s) { return sBar + 8 * (STAGES + s); };
-  auto empty = [&](int s) { return sBar + 8 * (2 * STAGES + s); };
-  const uint32_t acc_full = sBar + 8 * (3 * STAGES), acc_empty = acc_full + 8, stall_bar = acc_full + 16;
+  auto a_empty = [&](int s) { return sBar + 8 * (ASTAGES + s); };
+  auto b_full = [&](int s) { return sBar + 8 * (2 * ASTAGES + s); };
+  auto empty = [&](int s) { return sBar + 8 * (2 * ASTAGES + STAGES + s); };  // pair stage free
+  auto raw_full = [&](int r) { return sBar + 8 * (2 * ASTAGES + 2 * STAGES + r); };
+  auto raw_empty = [&](int r) { return sBar + 8 * (2 * ASTAGES + 2 * STAGES + RSTAGES + r); };
+  const uint32_t acc_full = sBar + 8 * (2 * ASTAGES + 2 * STAGES + 2 * RSTAGES),
+                 acc_empty = acc_full + 8, stall_bar = acc_full + 16;
+  const uint32_t sRaw = smem_u32(sm + OFF_RAW);
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + OFF_MISC);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(sm + OFF_MISC + 4);
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
+    for (int s = 0; s < ASTAGES; ++s) {
       mbar_init(a_full(s), 1);
+      mbar_init(a_empty(s), 1);
+    }
+    for (int s = 0; s < STAGES; ++s) {
       mbar_init(b_full(s), NPROD);
       mbar_init(empty(s), 1);
+    }
+    for (int r = 0; r < RSTAGES; ++r) {
+      mbar_init(raw_full(r), 1);
+      mbar_init(raw_empty(r), NPROD);
     }
     mbar_init(acc_full, 1);
     mbar_init(acc_empty, NPROD);
@@ -210,38 +236,65 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_contract_tc(const __grid_consta
     // ------------------------------------------------------------ TMA producer (A)
     if (lane == 0) {
       uint32_t it = 0;
-      int armed[STAGES] = {0, 0};
+      int armed[ASTAGES] = {0, 0, 0, 0};
       for (int gt = blockIdx.x; gt < ntot; gt += gridDim.x) {
         const TcTile t = a.tiles[gt];
         const TcGroup &G = a.groups[t.group];
-        const CUtensorMap *map_hi = maps + 2 * t.group, *map_lo = map_hi + 1;
+        const CUtensorMap *mg = maps + NMAPS * t.group;
         int rowc[NGROUP];
+#pragma unroll
         for (int g = 0; g < NGROUP; ++g) {
           const int e = t.col0 + g * GROUP;
           int f = -1;
           if (e < t.ncol) f = G.cols[t.col_off + e].field;
           rowc[g] = f >= 0 ? t.b * G.nf + f : G.batch * G.nf;  // out of range: TMA fills zeros
         }
+        // runs of consecutive field rows go in one box of 128 or 32 rows (the same
+        // bytes land at the same places as with 8-row boxes)
+        int boxk[NGROUP];  // 3: 128 rows, 2: 32 rows, 1: 8 rows, 0: covered
+#pragma unroll
+        for (int g = 0; g < NGROUP; ++g) boxk[g] = 1;
+        bool run128 = true;
+#pragma unroll
+        for (int g = 1; g < NGROUP; ++g) run128 = run128 && rowc[g] == rowc[0] + 8 * g;
+        if (run128) {
+          boxk[0] = 3;
+#pragma unroll
+          for (int g = 1; g < NGROUP; ++g) boxk[g] = 0;
+        } else {
+#pragma unroll
+          for (int g = 0; g < NGROUP; g += 4) {
+            const bool r32 = rowc[g + 1] == rowc[g] + 8 && rowc[g + 2] == rowc[g] + 16 &&
+                             rowc[g + 3] == rowc[g] + 24;
+            if (r32) {
+              boxk[g] = 2;
+              boxk[g + 1] = boxk[g + 2] = boxk[g + 3] = 0;
+            }
+          }
+        }
         const int k0 = t.kseg * G.kseg_len, k1 = min(G.Kpad, k0 + G.kseg_len);
         for (int kc = k0; kc < k1; kc += KC, ++it) {
-          const int s = it & 1;
-          const uint32_t ph = (it >> 1) & 1;
+          const int s = it % ASTAGES;
+          const uint32_t ph = (it / ASTAGES) & 1;
           if (*abort_flag) continue;
-          if (!mbar_wait(empty(s), ph ^ 1, limit, abort_flag)) {
+          if (!mbar_wait(a_empty(s), ph ^ 1, limit, abort_flag)) {
             fail();
             continue;
           }
           mbar_expect_tx(a_full(s), 2 * A_BYTES);
           ++armed[s];
           const uint32_t dh = sA + s * 2 * A_BYTES, dl = dh + A_BYTES;
+#pragma unroll
           for (int g = 0; g < NGROUP; ++g) {
-            tma_load_2d(dh + g * GROUP * 64, map_hi, kc, rowc[g], a_full(s));
-            tma_load_2d(dl + g * GROUP * 64, map_lo, kc, rowc[g], a_full(s));
+            if (boxk[g] == 0) continue;
+            const CUtensorMap *mh = mg + 2 * (boxk[g] - 1);
+            tma_load_2d(dh + g * GROUP * 64, mh, kc, rowc[g], a_full(s));
+            tma_load_2d(dl + g * GROUP * 64, mh + 1, kc, rowc[g], a_full(s));
           }
         }
       }
       // copies in flight land before the CTA can exit
-      for (int s = 0; s < STAGES; ++s)
+      for (int s = 0; s < ASTAGES; ++s)
         if (armed[s]) {
           volatile int never = 0;
           if (!mbar_wait(a_full(s), (armed[s] - 1) & 1, limit, &never)) atomicExch(a.err, 1);
@@ -270,18 +323,20 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_contract_tc(const __grid_consta
         for (int st = 0; st < nst; ++st, ++it) {
           const int s = it & 1;
           const uint32_t ph = (it >> 1) & 1;
+          const int sa = it % ASTAGES;
+          const uint32_t pha = (it / ASTAGES) & 1;
           if (!ok || *abort_flag) {
             ok = false;
             continue;
           }
-          if (!mbar_wait(a_full(s), ph, limit, abort_flag) ||
+          if (!mbar_wait(a_full(sa), pha, limit, abort_flag) ||
               !mbar_wait(b_full(s), ph, limit, abort_flag)) {
             fail();
             ok = false;
             continue;
           }
           tc_fence_after();
-          const uint32_t ah = sA + s * 2 * A_BYTES, al = ah + A_BYTES;
+          const uint32_t ah = sA + sa * 2 * A_BYTES, al = ah + A_BYTES;
           const uint32_t bh = sB + s * 2 * B_BYTES, bl = bh + B_BYTES;
 #pragma unroll
           for (int kk = 0; kk < KC / 16; ++kk) {
@@ -296,6 +351,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_contract_tc(const __grid_consta
               tc_mma(d, dal, dbh, 1u);
             }
           }
+          tc_commit(a_empty(sa));
           tc_commit(empty(s));
           last_bar = empty(s);
           last_par = ph;
@@ -313,85 +369,102 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_contract_tc(const __grid_consta
         if (!mbar_wait(last_bar, last_par, limit, &never)) atomicExch(a.err, 1);
       }
     }
+  } else if (warp == 2 + NPROD) {
+    // ------------------------------------------------------------ TMA producer (FP32 rows)
+    if (lane == 0) {
+      uint32_t rit = 0;
+      int armed[RSTAGES] = {0, 0, 0, 0};
+      for (int gt = blockIdx.x; gt < ntot; gt += gridDim.x) {
+        const TcTile t = a.tiles[gt];
+        const TcGroup &G = a.groups[t.group];
+        const CUtensorMap *map_f = maps + NMAPS * t.group + 6;
+        // rows past the channel block hold other fields (or zeros past the array):
+        // their pair columns are dropped in the epilogue
+        const int rowi = t.b * G.nf + t.ri * G.nc + t.nu1_0;
+        const int rowj = t.b * G.nf + t.rj * G.nc + t.nu2_0;
+        const int k0 = t.kseg * G.kseg_len, k1 = min(G.Kpad, k0 + G.kseg_len);
+        for (int kc = k0; kc < k1; kc += KC, ++rit) {
+          const int r = rit % RSTAGES;
+          const uint32_t ph = (rit / RSTAGES) & 1;
+          if (*abort_flag) continue;
+          if (!mbar_wait(raw_empty(r), ph ^ 1, limit, abort_flag)) {
+            fail();
+            continue;
+          }
+          mbar_expect_tx(raw_full(r), RAW_BYTES);
+          ++armed[r];
+          const uint32_t d = sRaw + r * RAW_BYTES;
+          tma_load_2d(d, map_f, kc, rowi, raw_full(r));
+          tma_load_2d(d + RAW_BOX_BYTES, map_f, kc, rowi + 16, raw_full(r));
+          tma_load_2d(d + 2 * RAW_BOX_BYTES, map_f, kc, rowj, raw_full(r));
+        }
+      }
+      for (int r = 0; r < RSTAGES; ++r)
+        if (armed[r]) {
+          volatile int never = 0;
+          if (!mbar_wait(raw_full(r), (armed[r] - 1) & 1, limit, &never)) atomicExch(a.err, 1);
+        }
+    }
   } else {
     // ------------------------------------------------------------ producers + epilogue
     const int pw = warp - 2;  // 0..7
     const int ptid = threadIdx.x - 64;
-    float *raw = reinterpret_cast<float *>(sm + OFF_RAW) + pw * RAW_ROWS * RAW_STRIDE;
+    const unsigned char *rawb = sm + OFF_RAW;
     int4 *rowinfo = reinterpret_cast<int4 *>(sm + OFF_ROW);  // (C_m, E_m, trip, nu3 | -1)
     int4 *seginfo = reinterpret_cast<int4 *>(sm + OFF_SEG);  // (base, E, trip, hi)
     int *nseg_s = reinterpret_cast<int *>(sm + OFF_MISC + 8);
     int *total_s = reinterpret_cast<int *>(sm + OFF_MISC + 12);
     float *red = reinterpret_cast<float *>(sm + OFF_B);
-    // compute mapping: lane -> (a-pair ap, b-offset bq, k-chunk kcq); warp covers nu1 rows
-    // 4pw..4pw+3; a lane takes nu2 = bq + 4y (y = 0..3).  Within each quarter-warp the raw
-    // rows read differ by one row (4 banks apart with the 36-float stride) and the pair
-    // rows stored alternate in parity, so loads and swizzled stores are conflict-free.
+    // lane -> (a-pair ap, b-offset bq, k-chunk kcq); the warp covers nu1 rows
+    // 4pw..4pw+3 and a lane takes nu2 = bq + 4y (y = 0..3).  With the 128-byte
+    // swizzle the 16 distinct F_j chunks of a load fall on 8 distinct bank
+    // groups (two wavefronts, the minimum for 256 bytes); pair rows stored
+    // alternate in parity, so the swizzled operand stores are conflict-free.
     const int kcq = lane & 3, bq = (lane >> 2) & 3, ap = lane >> 4;
-    uint32_t it = 0, tc = 0;
+    uint32_t it = 0, rit = 0, tc = 0;
     for (int gt = blockIdx.x; gt < ntot; gt += gridDim.x, ++tc) {
       const TcTile t = a.tiles[gt];
       const TcGroup &G = a.groups[t.group];
       const int b = t.b;
-      const float *Fb = G.F + (long long)b * G.bstride;
       const int k0 = t.kseg * G.kseg_len, k1 = min(G.Kpad, k0 + G.kseg_len);
-      // raw rows of this warp: r < 4 -> F_i[nu1_0 + 4pw + r], r >= 4 -> F_j[nu2_0 + r - 4]
-      auto row_ptr = [&](int r) -> const float * {
-        if (r < 4) {
-          const int nu1 = t.nu1_0 + 4 * pw + r;
-          return nu1 < G.nu1_hi ? Fb + ((long long)t.ri * G.nc + nu1) * G.fstride : nullptr;
-        }
-        const int nu2 = t.nu2_0 + r - 4;
-        return nu2 < G.nu2_hi ? Fb + ((long long)t.rj * G.nc + nu2) * G.fstride : nullptr;
-      };
-      // 20 rows x 8 float4 = 160 float4 per warp per stage: 5 per lane
-      float4 pre[5];
-      auto load_raw = [&](int kc) {
-#pragma unroll
-        for (int q = 0; q < 5; ++q) {
-          const int idx = lane + 32 * q;
-          const int r = idx >> 3, c4 = idx & 7;
-          const float *p = row_ptr(r);
-          const int k = kc + 4 * c4;
-          pre[q] = (p && k < G.M2) ? __ldg(reinterpret_cast<const float4 *>(p + k))
-                                   : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-      };
-      load_raw(k0);
-      for (int kc = k0; kc < k1; kc += KC, ++it) {
+      for (int kc = k0; kc < k1; kc += KC, ++it, ++rit) {
         const int s = it & 1;
         const uint32_t ph = (it >> 1) & 1;
-#pragma unroll
-        for (int q = 0; q < 5; ++q) {
-          const int idx = lane + 32 * q;
-          const int r = idx >> 3, c4 = idx & 7;
-          *reinterpret_cast<float4 *>(raw + r * RAW_STRIDE + 4 * c4) = pre[q];
-        }
-        __syncwarp();
-        if (kc + KC < k1) load_raw(kc + KC);
+        const int r = rit % RSTAGES;
+        const uint32_t rph = (rit / RSTAGES) & 1;
         bool ok = !*abort_flag;
-        if (ok && !mbar_wait(empty(s), ph ^ 1, limit, abort_flag)) {
+        if (ok && !mbar_wait(raw_full(r), rph, limit, abort_flag)) {
           fail();
           ok = false;
         }
+        // 2 nu1 x 4 nu2 pairs x 8 pixels per lane
+        float fi[2][8], fj[4][8];
         if (ok) {
-          // 2 nu1 x 4 nu2 pairs x 8 pixels per lane
-          float fi[2][8], fj[4][8];
+          const unsigned char *rb = rawb + r * RAW_BYTES;
 #pragma unroll
           for (int x = 0; x < 2; ++x) {
-            const float4 u = *reinterpret_cast<const float4 *>(raw + (2 * ap + x) * RAW_STRIDE + 8 * kcq);
-            const float4 v = *reinterpret_cast<const float4 *>(raw + (2 * ap + x) * RAW_STRIDE + 8 * kcq + 4);
+            const int row = 4 * pw + 2 * ap + x;
+            const float4 u = *reinterpret_cast<const float4 *>(rb + sw128_off(row, 2 * kcq));
+            const float4 v = *reinterpret_cast<const float4 *>(rb + sw128_off(row, 2 * kcq + 1));
             fi[x][0] = u.x; fi[x][1] = u.y; fi[x][2] = u.z; fi[x][3] = u.w;
             fi[x][4] = v.x; fi[x][5] = v.y; fi[x][6] = v.z; fi[x][7] = v.w;
           }
 #pragma unroll
           for (int y = 0; y < 4; ++y) {
-            const float *rp = raw + (4 + bq + 4 * y) * RAW_STRIDE + 8 * kcq;
-            const float4 u = *reinterpret_cast<const float4 *>(rp);
-            const float4 v = *reinterpret_cast<const float4 *>(rp + 4);
+            const int row = P1 + bq + 4 * y;
+            const float4 u = *reinterpret_cast<const float4 *>(rb + sw128_off(row, 2 * kcq));
+            const float4 v = *reinterpret_cast<const float4 *>(rb + sw128_off(row, 2 * kcq + 1));
             fj[y][0] = u.x; fj[y][1] = u.y; fj[y][2] = u.z; fj[y][3] = u.w;
             fj[y][4] = v.x; fj[y][5] = v.y; fj[y][6] = v.z; fj[y][7] = v.w;
           }
+        }
+        __syncwarp();
+        if (lane == 0 && ok) mbar_arrive(raw_empty(r));
+        if (ok && !mbar_wait(empty(s), ph ^ 1, limit, abort_flag)) {
+          fail();
+          ok = false;
+        }
+        if (ok) {
           unsigned char *bh = sm + OFF_B + s * 2 * B_BYTES;
           unsigned char *bl = bh + B_BYTES;
 #pragma unroll

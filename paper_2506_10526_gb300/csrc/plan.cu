@@ -129,7 +129,7 @@ void compute_layout(bs_plan p) {
   L.tmp3d = take((size_t)p->batch * p->ntrip * (size_t)p->nc * p->nc * sizeof(float2));
   L.herm = take(2 * sizeof(float));
   L.err = take(sizeof(int));
-  L.maps = take(2 * p->levels.size() * sizeof(CUtensorMap));
+  L.maps = take(7 * p->levels.size() * sizeof(CUtensorMap));
   L.tcgroup = take(p->levels.size() * sizeof(TcGroup));
   L.mlptab = take(((size_t)p->ntrip * 4 + 33) * sizeof(float));
   L.ztrips = take((size_t)p->ntrip * sizeof(int));
@@ -196,8 +196,11 @@ bs_status check_device_error(bs_plan p, cudaStream_t s) {
   return BS_OK;
 }
 
-// Tensor maps over the BF16 hi / lo field arrays: rows = batch * nf fields,
-// inner dimension = M^2 pixels; boxes of 32 pixels x 8 fields, 64-byte swizzle.
+// Tensor maps over the field arrays of each level: rows = batch * nf fields,
+// inner dimension = M^2 pixels.  BF16 hi / lo: boxes of 32 pixels x 8, 32 or
+// 128 fields, 64-byte swizzle (the MMA operand layout; the contraction loads
+// runs of consecutive fields with the larger boxes).  FP32 F: boxes of 32
+// pixels x 16 fields, 128-byte swizzle (the pair producers' input rows).
 bs_status ensure_tensor_maps(bs_plan p, cudaStream_t s) {
   if (p->maps_ready) return BS_OK;
   void *fn = nullptr;
@@ -213,13 +216,18 @@ bs_status ensure_tensor_maps(bs_plan p, cudaStream_t s) {
   for (Level &lv : p->levels) {
     const cuuint64_t M2 = (cuuint64_t)lv.M * lv.M;
     cuuint64_t dims[2] = {M2, (cuuint64_t)p->batch * std::max(1, lv.nslot) * p->nc};
-    cuuint64_t strides[1] = {M2 * 2};
-    cuuint32_t box[2] = {32, 8};
     cuuint32_t estr[2] = {1, 1};
-    for (int w = 0; w < 2; ++w) {
-      void *base = p->at<uint16_t>(w == 0 ? lv.offFhi : lv.offFlo);
-      CUresult r = enc(&lv.maps[w], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box,
-                       estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+    for (int w = 0; w < 7; ++w) {
+      const bool f32 = (w == 6);
+      static const cuuint32_t rows[7] = {8, 8, 32, 32, 128, 128, 16};
+      cuuint64_t strides[1] = {M2 * (f32 ? 4 : 2)};
+      cuuint32_t box[2] = {32, rows[w]};
+      void *base = f32 ? (void *)p->at<float>(lv.offF)
+                       : (void *)p->at<uint16_t>(w % 2 == 0 ? lv.offFhi : lv.offFlo);
+      CUresult r = enc(&lv.maps[w],
+                       f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                       base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                       f32 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
       if (r != CUDA_SUCCESS)
         return fail(p, BS_ERR_CUDA,
