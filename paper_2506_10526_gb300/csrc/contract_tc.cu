@@ -8,30 +8,43 @@
 // lo = round(v - hi)); three products hi.hi + hi.lo + lo.hi accumulate in
 // FP32 in tensor memory (the lo.lo term is below the BF16 split's own error).
 //
-// Tile (one CTA per SM, persistent over a static tile list):
-//   A = 128 fields (l, nu3) of the third ring          -> TMEM lanes
-//   B = 512 channel pairs: nu1 in 32 x nu2 in 16        -> 2 x 256 TMEM columns
+// Work unit: a CTA pair (thread-block cluster of 2 on neighbouring SMs) runs
+// the two-SM MMA (tcgen05.mma.cta_group::2, M256 N256 K16) on one tile,
+// persistent over a static tile list:
+//   A = 256 fields (l, nu3) of the third ring: 128 per CTA  -> TMEM lanes
+//   B = 512 channel pairs: nu1 in 32 x nu2 in 16, as two N = 256 halves;
+//       each CTA makes and holds 128 pairs of each half      -> 2 x 256 TMEM columns
 //   K = image pixels in chunks of 32 (64-byte rows, 64B swizzle, K-major)
-// A hi/lo come from the field arrays the row pass writes, by TMA in boxes of
-// 8 fields x 32 pixels.  B hi/lo are made on the fly: a second TMA thread
-// streams the FP32 rows of F_i (32 channels) and F_j (16 channels) into a
-// four-deep ring (128-byte swizzle), and 8 producer warps multiply, split and
-// store the pairs in the operand layout.  One thread issues 12 MMAs
-// (M128 N256 K16) per stage.  Two operand stages; mbarriers hand stages
-// between the TMA threads, the producers and the MMA thread.
+// Each CTA's tensor memory receives its own 128 fields x all 512 pairs.  Per
+// stage a CTA supplies half of the A and half of the B operand, so it reads
+// 8 KB of shared memory per MMA (12 KB in the one-SM form) and makes half as
+// many pair operands for the same tensor work.
 //
-// Epilogue (the producer warps): tcgen05.ld of the 128 x 512 FP32 tile,
+// Roles per CTA (352 threads):
+//   warp 0      TMA of the A hi/lo fields (boxes of 8, 32 or 128 rows; runs of
+//               consecutive field rows take the larger boxes), 4-stage ring
+//   warp 1      leader CTA: TMEM allocation and the MMA thread;
+//               peer CTA: TMEM allocation and a relay that tells the leader
+//               when the peer's stage is loaded (remote mbarrier arrive)
+//   warps 2-9   pair producers (FP32 product, hi/lo split, swizzled stores;
+//               4-stage ring) and, after the last stage of a tile, epilogue
+//   warp 10     TMA of the producers' FP32 rows of F_i and F_j, 4-stage ring
+// MMA completions are committed to the mbarriers of both CTAs (multicast).
+//
+// Epilogue (the producer warps): tcgen05.ld of the CTA's 128 x 512 FP32 tile,
 // shared-memory pre-reduction keyed by (ring triple segment, nu1-nu2,
 // nu2-nu3) into the idle B buffers, then FP64 global atomics into the
 // collapse sums (and, when asked, FP64 atomics into the FULL cube).
 //
 // Every mbarrier wait is bounded by %globaltimer.  A wait that gives up sets
-// the CTA's abort flag and the plan's error word; all roles then run their
-// loops to the end without waiting or issuing work, the TMA thread waits
-// (bounded) for its own copies in flight, the MMA thread for its last
-// commit, and TMEM is freed before the CTA exits.
+// the abort flag of both CTAs of the pair and the plan's error word; all roles
+// then run their loops to the end without waiting or issuing work, the TMA
+// threads wait (bounded) for their own copies in flight, the MMA thread for
+// its last commit, and the pair frees TMEM after a cluster barrier.
 #include <cuda.h>
 #include <cuda_bf16.h>
+
+#include <algorithm>
 
 #include "bs_internal.h"
 
@@ -40,21 +53,21 @@ namespace bsi {
 namespace {
 
 constexpr int KC = 32;                    // BF16 elements per K chunk = 64 bytes
-constexpr int MROWS = 128;                // fields per tile
-constexpr int P1 = 32, P2 = 16;           // pair rectangle
-constexpr int NPAIR = P1 * P2;            // 512
-constexpr int ASTAGES = 4;               // field-operand ring depth
-constexpr int STAGES = 2;                 // pair-operand ring depth
+constexpr int MROWS = 128;                // fields per CTA (256 per pair)
+constexpr int P1 = 32, P2 = 16;           // pair rectangle of a tile
+constexpr int PHALF = 128;                // pairs per CTA per N-half
+constexpr int ASTAGES = 4;                // field-operand ring depth
+constexpr int STAGES = 4;                 // pair-operand ring depth
+constexpr int RSTAGES = 4;                // FP32 row ring depth
 constexpr int NPROD = 8;                  // producer / epilogue warps
-constexpr int NTHREADS = 32 * (3 + NPROD);  // TMA (A), MMA, producers, TMA (rows)
-constexpr int GROUP = 8;                  // fields per TMA box
+constexpr int NTHREADS = 32 * (3 + NPROD);  // TMA (A), MMA/relay, producers, TMA (rows)
+constexpr int GROUP = 8;                  // fields per 8-row box
 constexpr int NGROUP = MROWS / GROUP;
 constexpr int A_BYTES = MROWS * KC * 2;   // 8 KB (hi or lo)
-constexpr int B_BYTES = NPAIR * KC * 2;   // 32 KB (hi or lo)
-constexpr int RSTAGES = 4;                // FP32 row ring depth
-constexpr int RAW_ROWS = P1 + P2;         // 32 rows of F_i, 16 of F_j
-constexpr int RAW_BYTES = RAW_ROWS * KC * 4;  // 6 KB: 128-byte rows, 128B swizzle
-constexpr int RAW_BOX_BYTES = 16 * KC * 4;    // one TMA box: 16 rows
+constexpr int B_BYTES = 2 * PHALF * KC * 2;  // 16 KB (hi or lo): both halves
+constexpr int RAW_ROWS = 16 + P2;         // 16 rows of F_i (8 per half), 16 of F_j
+constexpr int RAW_BYTES = RAW_ROWS * KC * 4;  // 4 KB: 128-byte rows, 128B swizzle
+constexpr int RAW_BOX_BYTES = 8 * KC * 4;     // one TMA box: 8 rows
 constexpr int RED_CAP = STAGES * 2 * B_BYTES / 4;  // floats in the B buffers
 
 constexpr int OFF_A = 0;
@@ -66,14 +79,15 @@ constexpr int MAX_SEG = 16;
 // tensor maps per level: BF16 hi/lo with boxes of 8, 32 and 128 field rows, FP32 rows
 constexpr int NMAPS = 7;
 constexpr int OFF_BAR = OFF_SEG + MAX_SEG * 16;
-// a_full, a_empty per field stage; b_full, b_empty per pair stage; raw_full, raw_empty per
-// row stage; acc_full, acc_empty, stall
-constexpr int NBAR = 2 * ASTAGES + 2 * STAGES + 2 * RSTAGES + 3;
+// a_full, a_empty, pfull per field stage; b_full, b_empty per pair stage; raw_full,
+// raw_empty per row stage; acc_full, acc_empty, stall
+constexpr int NBAR = 3 * ASTAGES + 2 * STAGES + 2 * RSTAGES + 3;
 constexpr int OFF_MISC = OFF_BAR + NBAR * 8;
 constexpr int SMEM_BYTES = OFF_MISC + 64 + 1024;  // + alignment slack
+static_assert(OFF_RAW % 1024 == 0 && RAW_BYTES % 1024 == 0, "128B-swizzled TMA needs 1 KB alignment");
 
-// instruction descriptor, kind::f16: D f32, A bf16, B bf16, both K-major, N = 256, M = 128
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((256u >> 3) << 17) | ((128u >> 4) << 24);
+// instruction descriptor, kind::f16: D f32, A bf16, B bf16, both K-major, N = 256, M = 256
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((256u >> 3) << 17) | ((256u >> 4) << 24);
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -83,33 +97,73 @@ __device__ __forceinline__ uint64_t gtime() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_id() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_count() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+  return r;
+}
+// Shared-memory address of the same variable in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t map_rank(uint32_t addr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                   : "memory");
+}
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
 }
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
+// Arrive on an mbarrier of any CTA of the cluster (address from map_rank).
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar) : "memory");
+}
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
                : "memory");
 }
+template <bool CLUSTER>
 __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
+  if (CLUSTER)
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+  else
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
   return ok != 0;
 }
-// Bounded wait; false on timeout or when the CTA is aborting.
+// Bounded wait; false on timeout or when the CTA is aborting.  CLUSTER: the
+// phase was completed by arrivals from the other CTA of the pair.
+template <bool CLUSTER = false>
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit_ns,
                                           volatile int *abort_flag) {
-  if (mbar_try(bar, parity)) return true;
+  if (mbar_try<CLUSTER>(bar, parity)) return true;
   const uint64_t t0 = gtime();
   while (true) {
-    if (mbar_try(bar, parity)) return true;
+    if (mbar_try<CLUSTER>(bar, parity)) return true;
     if (*abort_flag) return false;
     if ((long long)(gtime() - t0) > limit_ns) return false;
   }
@@ -131,13 +185,18 @@ __device__ __forceinline__ void tc_fence_after() {
 __device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
       "l"(a), "l"(b), "r"(IDESC), "r"(acc));
 }
-__device__ __forceinline__ void tc_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                   bar)
-               : "memory");
+// Arrive (once) on the mbarrier at this shared offset in both CTAs of the pair
+// when every MMA issued so far has completed.
+__device__ __forceinline__ void tc_commit_pair(uint32_t bar) {
+  const uint16_t mask = 3;
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+      " [%0], %1;" ::"r"(bar),
+      "h"(mask)
+      : "memory");
 }
 __device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile(
@@ -174,29 +233,35 @@ __device__ __forceinline__ void split2(float v0, float v1, uint32_t &hi, uint32_
   lo = *reinterpret_cast<uint32_t *>(&l);
 }
 
-__global__ void __launch_bounds__(NTHREADS, 1) k_contract_tc(const __grid_constant__ TcArgs a) {
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
+    k_contract_tc(const __grid_constant__ TcArgs a) {
   extern __shared__ unsigned char smem_dyn[];
   unsigned char *sm = reinterpret_cast<unsigned char *>(
       (reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_rank();  // 0: leader (issues the MMAs), 1: peer
   const uint32_t sA = smem_u32(sm + OFF_A), sB = smem_u32(sm + OFF_B);
   const uint32_t sBar = smem_u32(sm + OFF_BAR);
   auto a_full = [&](int s) { return sBar + 8 * s; };
   auto a_empty = [&](int s) { return sBar + 8 * (ASTAGES + s); };
-  auto b_full = [&](int s) { return sBar + 8 * (2 * ASTAGES + s); };
-  auto empty = [&](int s) { return sBar + 8 * (2 * ASTAGES + STAGES + s); };  // pair stage free
-  auto raw_full = [&](int r) { return sBar + 8 * (2 * ASTAGES + 2 * STAGES + r); };
-  auto raw_empty = [&](int r) { return sBar + 8 * (2 * ASTAGES + 2 * STAGES + RSTAGES + r); };
-  const uint32_t acc_full = sBar + 8 * (2 * ASTAGES + 2 * STAGES + 2 * RSTAGES),
+  auto pfull = [&](int s) { return sBar + 8 * (2 * ASTAGES + s); };  // peer stage loaded
+  auto b_full = [&](int s) { return sBar + 8 * (3 * ASTAGES + s); };
+  auto empty = [&](int s) { return sBar + 8 * (3 * ASTAGES + STAGES + s); };  // pair stage free
+  auto raw_full = [&](int r) { return sBar + 8 * (3 * ASTAGES + 2 * STAGES + r); };
+  auto raw_empty = [&](int r) { return sBar + 8 * (3 * ASTAGES + 2 * STAGES + RSTAGES + r); };
+  const uint32_t acc_full = sBar + 8 * (3 * ASTAGES + 2 * STAGES + 2 * RSTAGES),
                  acc_empty = acc_full + 8, stall_bar = acc_full + 16;
   const uint32_t sRaw = smem_u32(sm + OFF_RAW);
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + OFF_MISC);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(sm + OFF_MISC + 4);
+  const uint32_t peer_abort = map_rank(smem_u32(sm + OFF_MISC + 4), rank ^ 1u);
+  const uint32_t acc_empty_lead = map_rank(acc_empty, 0);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < ASTAGES; ++s) {
       mbar_init(a_full(s), 1);
       mbar_init(a_empty(s), 1);
+      mbar_init(pfull(s), 1);
     }
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(b_full(s), NPROD);
@@ -207,28 +272,30 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_contract_tc(const __grid_consta
       mbar_init(raw_empty(r), NPROD);
     }
     mbar_init(acc_full, 1);
-    mbar_init(acc_empty, NPROD);
+    mbar_init(acc_empty, 2 * NPROD);  // the producer warps of both CTAs (leader's copy is used)
     mbar_init(stall_bar, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_slot)),
                  "r"(512));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
   }
   tc_fence_before();
-  __syncthreads();
+  cluster_sync_all();  // barriers of both CTAs initialised, TMEM allocated
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const long long limit = a.wait_limit_ns;
   const int ntot = a.ntiles;
+  const int cid = (int)cluster_id(), ncl = (int)cluster_count();
   const CUtensorMap *maps = reinterpret_cast<const CUtensorMap *>(a.maps);
 
   auto fail = [&]() {
     *abort_flag = 1;
+    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(peer_abort), "r"(1) : "memory");
     atomicExch(a.err, 1);
   };
 
@@ -237,14 +304,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_contract_tc(const __grid_consta
     if (lane == 0) {
       uint32_t it = 0;
       int armed[ASTAGES] = {0, 0, 0, 0};
-      for (int gt = blockIdx.x; gt < ntot; gt += gridDim.x) {
+      for (int gt = cid; gt < ntot; gt += ncl) {
         const TcTile t = a.tiles[gt];
         const TcGroup &G = a.groups[t.group];
         const CUtensorMap *mg = maps + NMAPS * t.group;
+        const int cbase = t.col0 + MROWS * (int)rank;
         int rowc[NGROUP];
 #pragma unroll
         for (int g = 0; g < NGROUP; ++g) {
-          const int e = t.col0 + g * GROUP;
+          const int e = cbase + g * GROUP;
           int f = -1;
           if (e < t.ncol) f = G.cols[t.col_off + e].field;
           rowc[g] = f >= 0 ? t.b * G.nf + f : G.batch * G.nf;  // out of range: TMA fills zeros
@@ -301,28 +369,28 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_contract_tc(const __grid_consta
         }
     }
   } else if (warp == 1) {
-    // ------------------------------------------------------------ MMA issuer
-    if (lane == 0) {
+    if (rank == 0 && lane == 0) {
+      // ---------------------------------------------------------- MMA issuer (leader)
       uint32_t it = 0, tc = 0;
       uint32_t last_bar = 0, last_par = 0;
       bool committed = false;
       if (a.stall_test) {  // failure-injection test: a barrier nothing arrives at
         if (!mbar_wait(stall_bar, 0, limit, abort_flag)) fail();
       }
-      for (int gt = blockIdx.x; gt < ntot; gt += gridDim.x, ++tc) {
+      for (int gt = cid; gt < ntot; gt += ncl, ++tc) {
         const TcTile t = a.tiles[gt];
         const TcGroup &G = a.groups[t.group];
         const int k0 = t.kseg * G.kseg_len, k1 = min(G.Kpad, k0 + G.kseg_len);
         const int nst = (k1 - k0) / KC;
         bool ok = !*abort_flag;
-        if (ok && !mbar_wait(acc_empty, (tc & 1) ^ 1, limit, abort_flag)) {
+        if (ok && !mbar_wait<true>(acc_empty, (tc & 1) ^ 1, limit, abort_flag)) {
           fail();
           ok = false;
         }
         tc_fence_after();
         for (int st = 0; st < nst; ++st, ++it) {
-          const int s = it & 1;
-          const uint32_t ph = (it >> 1) & 1;
+          const int s = it % STAGES;
+          const uint32_t ph = (it / STAGES) & 1;
           const int sa = it % ASTAGES;
           const uint32_t pha = (it / ASTAGES) & 1;
           if (!ok || *abort_flag) {
@@ -330,7 +398,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_contract_tc(const __grid_consta
             continue;
           }
           if (!mbar_wait(a_full(sa), pha, limit, abort_flag) ||
-              !mbar_wait(b_full(s), ph, limit, abort_flag)) {
+              !mbar_wait(b_full(s), ph, limit, abort_flag) ||
+              !mbar_wait<true>(pfull(sa), pha, limit, abort_flag)) {
             fail();
             ok = false;
             continue;
@@ -343,22 +412,22 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_contract_tc(const __grid_consta
             const uint64_t dah = sw64_desc(ah + kk * 32), dal = sw64_desc(al + kk * 32);
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-              const uint64_t dbh = sw64_desc(bh + h * 256 * 64 + kk * 32);
-              const uint64_t dbl = sw64_desc(bl + h * 256 * 64 + kk * 32);
+              const uint64_t dbh = sw64_desc(bh + h * PHALF * 64 + kk * 32);
+              const uint64_t dbl = sw64_desc(bl + h * PHALF * 64 + kk * 32);
               const uint32_t d = tmem + h * 256;
               tc_mma(d, dah, dbh, (st == 0 && kk == 0) ? 0u : 1u);
               tc_mma(d, dah, dbl, 1u);
               tc_mma(d, dal, dbh, 1u);
             }
           }
-          tc_commit(a_empty(sa));
-          tc_commit(empty(s));
+          tc_commit_pair(a_empty(sa));
+          tc_commit_pair(empty(s));
           last_bar = empty(s);
           last_par = ph;
           committed = true;
         }
         if (ok && !*abort_flag) {
-          tc_commit(acc_full);
+          tc_commit_pair(acc_full);
           last_bar = acc_full;
           last_par = tc & 1;
           committed = true;
@@ -368,19 +437,44 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_contract_tc(const __grid_consta
         volatile int never = 0;
         if (!mbar_wait(last_bar, last_par, limit, &never)) atomicExch(a.err, 1);
       }
+    } else if (rank == 1 && lane == 0) {
+      // ---------------------------------------------------------- relay (peer)
+      // Stage `it` of this CTA is in shared memory (fields by TMA, pairs by the
+      // producers): tell the leader's MMA thread.
+      const uint32_t pfull_lead0 = map_rank(pfull(0), 0);
+      uint32_t it = 0;
+      for (int gt = cid; gt < ntot; gt += ncl) {
+        const TcTile t = a.tiles[gt];
+        const TcGroup &G = a.groups[t.group];
+        const int k0 = t.kseg * G.kseg_len, k1 = min(G.Kpad, k0 + G.kseg_len);
+        for (int kc = k0; kc < k1; kc += KC, ++it) {
+          const int s = it % STAGES;
+          const uint32_t ph = (it / STAGES) & 1;
+          const int sa = it % ASTAGES;
+          const uint32_t pha = (it / ASTAGES) & 1;
+          if (*abort_flag) continue;
+          if (!mbar_wait(a_full(sa), pha, limit, abort_flag) ||
+              !mbar_wait(b_full(s), ph, limit, abort_flag)) {
+            fail();
+            continue;
+          }
+          mbar_arrive_cluster(pfull_lead0 + 8 * sa);
+        }
+      }
     }
   } else if (warp == 2 + NPROD) {
     // ------------------------------------------------------------ TMA producer (FP32 rows)
     if (lane == 0) {
       uint32_t rit = 0;
       int armed[RSTAGES] = {0, 0, 0, 0};
-      for (int gt = blockIdx.x; gt < ntot; gt += gridDim.x) {
+      for (int gt = cid; gt < ntot; gt += ncl) {
         const TcTile t = a.tiles[gt];
         const TcGroup &G = a.groups[t.group];
         const CUtensorMap *map_f = maps + NMAPS * t.group + 6;
+        // this CTA's nu1 rows: nu1_0 + 8 rank + [0, 8) and nu1_0 + 16 + 8 rank + [0, 8);
         // rows past the channel block hold other fields (or zeros past the array):
         // their pair columns are dropped in the epilogue
-        const int rowi = t.b * G.nf + t.ri * G.nc + t.nu1_0;
+        const int rowi = t.b * G.nf + t.ri * G.nc + t.nu1_0 + 8 * (int)rank;
         const int rowj = t.b * G.nf + t.rj * G.nc + t.nu2_0;
         const int k0 = t.kseg * G.kseg_len, k1 = min(G.Kpad, k0 + G.kseg_len);
         for (int kc = k0; kc < k1; kc += KC, ++rit) {
@@ -397,6 +491,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_contract_tc(const __grid_consta
           tma_load_2d(d, map_f, kc, rowi, raw_full(r));
           tma_load_2d(d + RAW_BOX_BYTES, map_f, kc, rowi + 16, raw_full(r));
           tma_load_2d(d + 2 * RAW_BOX_BYTES, map_f, kc, rowj, raw_full(r));
+          tma_load_2d(d + 3 * RAW_BOX_BYTES, map_f, kc, rowj + 8, raw_full(r));
         }
       }
       for (int r = 0; r < RSTAGES; ++r)
@@ -415,21 +510,26 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_contract_tc(const __grid_consta
     int *nseg_s = reinterpret_cast<int *>(sm + OFF_MISC + 8);
     int *total_s = reinterpret_cast<int *>(sm + OFF_MISC + 12);
     float *red = reinterpret_cast<float *>(sm + OFF_B);
-    // lane -> (a-pair ap, b-offset bq, k-chunk kcq); the warp covers nu1 rows
-    // 4pw..4pw+3 and a lane takes nu2 = bq + 4y (y = 0..3).  With the 128-byte
-    // swizzle the 16 distinct F_j chunks of a load fall on 8 distinct bank
-    // groups (two wavefronts, the minimum for 256 bytes); pair rows stored
-    // alternate in parity, so the swizzled operand stores are conflict-free.
+    // lane -> (row ap, b-offset bq, k-chunk kcq).  Warp pw makes the pairs of this
+    // CTA's nu1 rows q = 2pw + ap (q < 8: half 0, nu1 = nu1_0 + 8 rank + q; q >= 8:
+    // half 1, nu1 = nu1_0 + 16 + 8 rank + q - 8) with nu2 = bq + 4y (y = 0..3): pair
+    // row (q >> 3) 128 + (q & 7) 16 + nu2 of the B operand.  With the 128-byte
+    // swizzle the 16 distinct F_j chunks of a load fall on 8 distinct bank groups
+    // (two wavefronts, the minimum for 256 bytes); the swizzled operand stores of
+    // a warp spread evenly over the banks.
     const int kcq = lane & 3, bq = (lane >> 2) & 3, ap = lane >> 4;
+    const int qrow = 2 * pw + ap;
+    const int prow0 = (qrow >> 3) * PHALF + (qrow & 7) * P2;
     uint32_t it = 0, rit = 0, tc = 0;
-    for (int gt = blockIdx.x; gt < ntot; gt += gridDim.x, ++tc) {
+    for (int gt = cid; gt < ntot; gt += ncl, ++tc) {
       const TcTile t = a.tiles[gt];
       const TcGroup &G = a.groups[t.group];
       const int b = t.b;
+      const int cbase = t.col0 + MROWS * (int)rank;
       const int k0 = t.kseg * G.kseg_len, k1 = min(G.Kpad, k0 + G.kseg_len);
       for (int kc = k0; kc < k1; kc += KC, ++it, ++rit) {
-        const int s = it & 1;
-        const uint32_t ph = (it >> 1) & 1;
+        const int s = it % STAGES;
+        const uint32_t ph = (it / STAGES) & 1;
         const int r = rit % RSTAGES;
         const uint32_t rph = (rit / RSTAGES) & 1;
         bool ok = !*abort_flag;
@@ -437,21 +537,19 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_contract_tc(const __grid_consta
           fail();
           ok = false;
         }
-        // 2 nu1 x 4 nu2 pairs x 8 pixels per lane
-        float fi[2][8], fj[4][8];
+        // 1 nu1 x 4 nu2 pairs x 8 pixels per lane
+        float fi[8], fj[4][8];
         if (ok) {
           const unsigned char *rb = rawb + r * RAW_BYTES;
-#pragma unroll
-          for (int x = 0; x < 2; ++x) {
-            const int row = 4 * pw + 2 * ap + x;
-            const float4 u = *reinterpret_cast<const float4 *>(rb + sw128_off(row, 2 * kcq));
-            const float4 v = *reinterpret_cast<const float4 *>(rb + sw128_off(row, 2 * kcq + 1));
-            fi[x][0] = u.x; fi[x][1] = u.y; fi[x][2] = u.z; fi[x][3] = u.w;
-            fi[x][4] = v.x; fi[x][5] = v.y; fi[x][6] = v.z; fi[x][7] = v.w;
+          {
+            const float4 u = *reinterpret_cast<const float4 *>(rb + sw128_off(qrow, 2 * kcq));
+            const float4 v = *reinterpret_cast<const float4 *>(rb + sw128_off(qrow, 2 * kcq + 1));
+            fi[0] = u.x; fi[1] = u.y; fi[2] = u.z; fi[3] = u.w;
+            fi[4] = v.x; fi[5] = v.y; fi[6] = v.z; fi[7] = v.w;
           }
 #pragma unroll
           for (int y = 0; y < 4; ++y) {
-            const int row = P1 + bq + 4 * y;
+            const int row = 16 + bq + 4 * y;
             const float4 u = *reinterpret_cast<const float4 *>(rb + sw128_off(row, 2 * kcq));
             const float4 v = *reinterpret_cast<const float4 *>(rb + sw128_off(row, 2 * kcq + 1));
             fj[y][0] = u.x; fj[y][1] = u.y; fj[y][2] = u.z; fj[y][3] = u.w;
@@ -468,19 +566,17 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_contract_tc(const __grid_consta
           unsigned char *bh = sm + OFF_B + s * 2 * B_BYTES;
           unsigned char *bl = bh + B_BYTES;
 #pragma unroll
-          for (int x = 0; x < 2; ++x)
-#pragma unroll
-            for (int y = 0; y < 4; ++y) {
-              const int p = (4 * pw + 2 * ap + x) * P2 + bq + 4 * y;  // pair row
-              uint4 H, L;
-              split2(fi[x][0] * fj[y][0], fi[x][1] * fj[y][1], H.x, L.x);
-              split2(fi[x][2] * fj[y][2], fi[x][3] * fj[y][3], H.y, L.y);
-              split2(fi[x][4] * fj[y][4], fi[x][5] * fj[y][5], H.z, L.z);
-              split2(fi[x][6] * fj[y][6], fi[x][7] * fj[y][7], H.w, L.w);
-              const uint32_t o = sw64_off(p, kcq);
-              *reinterpret_cast<uint4 *>(bh + o) = H;
-              *reinterpret_cast<uint4 *>(bl + o) = L;
-            }
+          for (int y = 0; y < 4; ++y) {
+            const int p = prow0 + bq + 4 * y;  // pair row
+            uint4 H, L;
+            split2(fi[0] * fj[y][0], fi[1] * fj[y][1], H.x, L.x);
+            split2(fi[2] * fj[y][2], fi[3] * fj[y][3], H.y, L.y);
+            split2(fi[4] * fj[y][4], fi[5] * fj[y][5], H.z, L.z);
+            split2(fi[6] * fj[y][6], fi[7] * fj[y][7], H.w, L.w);
+            const uint32_t o = sw64_off(p, kcq);
+            *reinterpret_cast<uint4 *>(bh + o) = H;
+            *reinterpret_cast<uint4 *>(bl + o) = L;
+          }
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         }
         __syncwarp();
@@ -500,7 +596,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_contract_tc(const __grid_consta
         // segments of consecutive rows with one ring triple
         int ns = 0, base = 0, m = 0;
         while (m < MROWS) {
-          const int e = t.col0 + m;
+          const int e = cbase + m;
           if (e >= t.ncol) break;
           const ColEntry c0 = G.cols[t.col_off + e];
           if (c0.field < 0) {
@@ -508,8 +604,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_contract_tc(const __grid_consta
             continue;
           }
           int lo = c0.nu3, hi = c0.nu3, q = m;
-          while (q + 1 < MROWS && t.col0 + q + 1 < t.ncol) {
-            const ColEntry cn = G.cols[t.col_off + t.col0 + q + 1];
+          while (q + 1 < MROWS && cbase + q + 1 < t.ncol) {
+            const ColEntry cn = G.cols[t.col_off + cbase + q + 1];
             if (cn.field >= 0 && cn.trip != c0.trip) break;
             ++q;
             if (cn.field >= 0) {
@@ -520,7 +616,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_contract_tc(const __grid_consta
           const int E = (P2 - 1) + (hi - lo) + 1;
           if (ns < MAX_SEG) seginfo[ns] = make_int4(base, E, c0.trip, hi);
           for (int r = m; r <= q; ++r) {
-            const int ee = t.col0 + r;
+            const int ee = cbase + r;
             const ColEntry cr = G.cols[t.col_off + ee];
             if (cr.field < 0)
               rowinfo[r] = make_int4(0, 0, cr.trip, -1);
@@ -580,7 +676,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_contract_tc(const __grid_consta
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0 && ok) mbar_arrive(acc_empty);
+      if (lane == 0 && ok) mbar_arrive_cluster(acc_empty_lead);
       asm volatile("bar.sync 1, 256;" ::: "memory");
       if (use_red && ok) {
         const int ns = *nseg_s;
@@ -604,10 +700,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_contract_tc(const __grid_consta
     }
   }
   tc_fence_before();
-  __syncthreads();
+  cluster_sync_all();  // all MMAs of the pair have completed (the leader waited for them)
   tc_fence_after();
   if (warp == 1)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }
 
 }  // namespace
@@ -616,11 +712,22 @@ int tc_smem_bytes() { return SMEM_BYTES; }
 
 cudaError_t launch_contract_tc(const TcArgs &a, int nsm, cudaStream_t s) {
   if (a.ntiles == 0) return cudaSuccess;
-  cudaError_t e =
-      smem_optin_once(k_contract_tc);
+  cudaError_t e = smem_optin_once(k_contract_tc);
   if (e != cudaSuccess) return e;
-  const int grid = std::min(a.ntiles, nsm);
-  k_contract_tc<<<grid, NTHREADS, SMEM_BYTES, s>>>(a);
+  // one CTA pair per two SMs, as many pairs as can be resident at once
+  static int max_pairs = 0;
+  if (max_pairs == 0) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * (nsm / 2), 1, 1);
+    cfg.blockDim = dim3(NTHREADS, 1, 1);
+    cfg.dynamicSmemBytes = SMEM_BYTES;
+    int n = 0;
+    e = cudaOccupancyMaxActiveClusters(&n, k_contract_tc, &cfg);
+    if (e != cudaSuccess) return e;
+    max_pairs = n > 0 ? n : 1;
+  }
+  const int pairs = std::max(1, std::min({a.ntiles, max_pairs, nsm / 2}));
+  k_contract_tc<<<2 * pairs, NTHREADS, SMEM_BYTES, s>>>(a);
   return cudaGetLastError();
 }
 

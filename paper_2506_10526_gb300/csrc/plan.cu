@@ -200,7 +200,7 @@ bs_status check_device_error(bs_plan p, cudaStream_t s) {
 // inner dimension = M^2 pixels.  BF16 hi / lo: boxes of 32 pixels x 8, 32 or
 // 128 fields, 64-byte swizzle (the MMA operand layout; the contraction loads
 // runs of consecutive fields with the larger boxes).  FP32 F: boxes of 32
-// pixels x 16 fields, 128-byte swizzle (the pair producers' input rows).
+// pixels x 8 fields, 128-byte swizzle (the pair producers' input rows).
 bs_status ensure_tensor_maps(bs_plan p, cudaStream_t s) {
   if (p->maps_ready) return BS_OK;
   void *fn = nullptr;
@@ -219,7 +219,7 @@ bs_status ensure_tensor_maps(bs_plan p, cudaStream_t s) {
     cuuint32_t estr[2] = {1, 1};
     for (int w = 0; w < 7; ++w) {
       const bool f32 = (w == 6);
-      static const cuuint32_t rows[7] = {8, 8, 32, 32, 128, 128, 16};
+      static const cuuint32_t rows[7] = {8, 8, 32, 32, 128, 128, 8};
       cuuint64_t strides[1] = {M2 * (f32 ? 4 : 2)};
       cuuint32_t box[2] = {32, rows[w]};
       void *base = f32 ? (void *)p->at<float>(lv.offF)
@@ -440,7 +440,8 @@ std::vector<TcGroup> build_tc_work(bs_plan p, const int *blk, int group_base,
   }
   const int n1b = (blk[1] - blk[0] + 31) / 32, n2b = (blk[3] - blk[2] + 15) / 16;
   long long base_tiles = 0;
-  for (const PairList &q : pl) base_tiles += (long long)n1b * n2b * ((q.n + 127) / 128);
+  // a tile is one CTA pair's work: 256 column entries (128 per CTA) x 32 x 16 pairs
+  for (const PairList &q : pl) base_tiles += (long long)n1b * n2b * ((q.n + 255) / 256);
   base_tiles *= p->batch;
   // split K (the same factor on every level) until the launch has min_tiles tiles
   int nk = 1;
@@ -456,7 +457,7 @@ std::vector<TcGroup> build_tc_work(bs_plan p, const int *blk, int group_base,
   const size_t t0 = tiles.size();
   for (int b = 0; b < p->batch; ++b)
     for (const PairList &q : pl)
-      for (int c0 = 0; c0 < q.n; c0 += 128)
+      for (int c0 = 0; c0 < q.n; c0 += 256)
         for (int a1 = 0; a1 < n1b; ++a1)
           for (int a2 = 0; a2 < n2b; ++a2)
             for (int k = 0; k < nks[q.lv]; ++k)
@@ -477,7 +478,7 @@ bs_status mabs_tc(bs_plan p, const int *blk, double *out_full, int accumulate, c
   p->h_cols.clear();
   p->h_tctiles.clear();
   p->h_groups = build_tc_work(p, blk, 0, p->h_cols, p->at<ColEntry>(L.cols), p->h_tctiles,
-                              out_full, accumulate, 2 * p->nsm);
+                              out_full, accumulate, p->nsm);
   if (p->h_tctiles.empty()) return BS_OK;
   if (p->h_tctiles.size() > p->max_tctiles || p->h_cols.size() > p->max_cols)
     return fail(p, BS_ERR_UNSUPPORTED, "tensor-core tile list exceeds the plan's capacity");
@@ -729,7 +730,7 @@ bs_status bs_plan_create(const bs_plan_desc *desc, bs_plan *out) {
   const int npairs = p->nb * (p->nb + 1) / 2;
   p->max_cols = (size_t)npairs * p->nb * p->nc;
   p->max_ptiles = (size_t)npairs * ((size_t)p->nb * p->nc / 128 + 1);
-  // tensor-core tiles: pair rectangles (32 x 16) x 128-entry column windows (runs padded to 8)
+  // tensor-core tiles: pair rectangles (32 x 16) x 256-entry column windows (runs padded to 8)
   cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, dev);
   if (p->d.precision == BS_PREC_SPLIT_BF16) {
     // largest block: the full cube; K splitting only happens while tiles < 2 per SM

@@ -1,7 +1,8 @@
 """Host-side sharding of the channel cube across ranks (one process per GPU).
 
 The job of a plan is the full channel cube nc^3 of every closable ring
-triple.  It splits into B^3 blocks of side B (the last ones ragged); rank r of
+triple.  It splits into blocks of B x B x B3 channels (nu1 x nu2 x nu3, the
+last ones ragged; B3 = B unless given); rank r of
 W takes blocks r, r + W, r + 2W, ... in step order, so ranks never share a
 block and need no data-path collective: each rank's collapse sums hold its
 own blocks (the sum over ranks is the job's).  Timing is the maximum over
@@ -10,15 +11,18 @@ ranks; throughput counts every rank's evaluations.
 from __future__ import annotations
 
 
-def blocks_of(nc: int, bsz: int):
-    """Half-open channel blocks (nu1_lo, nu1_hi, nu2_lo, nu2_hi, nu3_lo, nu3_hi)."""
+def blocks_of(nc: int, bsz: int, bsz3: int | None = None):
+    """Half-open channel blocks (nu1_lo, nu1_hi, nu2_lo, nu2_hi, nu3_lo, nu3_hi):
+    sides bsz along nu1 and nu2, bsz3 (default bsz) along nu3."""
+    b3 = bsz if not bsz3 else bsz3
     n = (nc + bsz - 1) // bsz
+    n3 = (nc + b3 - 1) // b3
     out = []
     for a in range(n):
         for b in range(n):
-            for c in range(n):
+            for c in range(n3):
                 out.append((a * bsz, min(nc, (a + 1) * bsz), b * bsz, min(nc, (b + 1) * bsz),
-                            c * bsz, min(nc, (c + 1) * bsz)))
+                            c * b3, min(nc, (c + 1) * b3)))
     return out
 
 
