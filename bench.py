@@ -382,7 +382,8 @@ def main():
                    "channel_block": [w["block"], w["block"], w.get("block3") or w["block"]],
                    "closable_ring_triples": nclos, "ring_triples": plan.ntrip,
                    "evals_per_step_per_gpu": per_launch_evals, "precision": args.precision,
-                   "l2": "inputs larger than L2 (403 MB visibilities, 9 GB fields)",
+                   "l2": (f"inputs larger than L2 ({vis_h.numel() * 8 / 1e6:.0f} MB visibilities, "
+                          f"{plan.info()[3] / 1e9:.1f} GB plan workspace holding the fields)"),
                    "parallelism": f"blocks of the channel cube sharded over {world} GPU(s)"},
         "roofline": roof, "clocks": clk,
         "gpu_launches": 6 * args.steps,

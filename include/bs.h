@@ -185,10 +185,13 @@ bs_status bs_mabs_delta(bs_plan plan, double *out_dev, void *cuda_stream);
 
 /* Eq. (dft) applied to the folded collapsed MABS:
  *   B(a, b) = (r^2 r' dnu_c)^2 sum_{n,m} exp(-2 pi i (n a + m b)/nchan) B_A(n, m)
- * with n, m over the integers of [-nchan/2, nchan/2] (both ends, as the limits
- * of Eq. dft state; unsampled separations contribute nothing) and
- * a, b in [-nchan/2, nchan/2).  The input plane is point symmetric, so B is
- * real.  k_par a = 2 pi a / (r' nchan dnu_c).
+ * with n, m over the integers of [-nchan/2, nchan/2) -- one period of the
+ * nchan-periodic kernel (the printed limits, -nchan/2 ... nchan/2, would count
+ * the end separation of an even nchan twice) -- unsampled separations
+ * contributing nothing, and a, b in [-nchan/2, nchan/2).  The input plane is
+ * point symmetric, so the imaginary part of the sum comes only from the
+ * unpaired edge n, m = -nchan/2; the real part is returned.
+ * k_par a = 2 pi a / (r' nchan dnu_c).
  *  out_dev  double [batch][T_r][nchan][nchan], index [a + nchan/2][b + nchan/2]. */
 bs_status bs_bs3d(bs_plan plan, double *out_dev, void *cuda_stream);
 

@@ -309,16 +309,28 @@ def collapse_fold(B: np.ndarray):
 
 
 def delay_dft(bbar: np.ndarray, nc: int, r: float = 1.0, rprime: float = 1.0,
-              dnu_c: float = 1.0) -> np.ndarray:
+              dnu_c: float = 1.0, variant: str = "half_open") -> np.ndarray:
     """Eq. (dft): B(a, b) = (r^2 r' dnu_c)^2 sum_{n,m} exp(-2 pi i (n a + m b)/nc)
-    Bbar(n, m), with n, m over the integers of [-nc/2, nc/2] (both ends, as
-    the limits of Eq. dft state) and a, b in [-nc/2, nc/2) (stored at index
-    a + nc/2).  Separations where Bbar is undefined (no sampled triple)
-    contribute nothing.  Input: centred (2nc-1, 2nc-1) planes [..., d1, d2].
-    Output: complex [..., nc, nc]."""
+    Bbar(n, m), a, b in [-nc/2, nc/2) (stored at index a + nc//2).
+
+    The printed limits of the n, m sums, -nc/2 ... nc/2, give nc + 1 terms per
+    axis with an nc-periodic kernel.  variant="half_open" (the reading used
+    everywhere): n, m over the integers with -nc/2 <= n < nc/2, one full
+    period (nc points).  variant="inclusive": both ends included (nc + 1
+    points for even nc), reported beside it so the difference is visible.
+    The 3D bispectrum is the real part: Bbar is point symmetric, so the
+    imaginary part comes only from the unpaired edge row and column
+    n, m = -nc/2 of the half-open range.  Separations where Bbar is undefined
+    (no sampled triple) contribute nothing.  Input: centred (2nc-1, 2nc-1)
+    planes [..., d1, d2].  Output: complex [..., nc, nc]."""
     bbar = np.asarray(bbar)
     h = nc // 2
-    n = np.arange(-h, h + 1) if nc % 2 == 0 else np.arange(-h, h + 1)
+    if variant == "half_open":
+        n = np.arange(-h, nc - h)  # 2n >= -nc and 2n < nc
+    elif variant == "inclusive":
+        n = np.arange(-h, h + 1)
+    else:
+        raise ValueError(variant)
     sub = bbar[..., n + nc - 1, :][..., :, n + nc - 1]
     sub = np.where(np.isnan(sub), 0.0, sub)
     a = np.arange(-h, -h + nc)

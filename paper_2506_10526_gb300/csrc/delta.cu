@@ -9,11 +9,13 @@
 //   Bbar(0) = S(0) / (A M^2 T N(0))
 // is the mean of B_A over the valid triples at +-d: the fold of Fig. Nv.
 //
-// Delay transform: the inclusive square n, m in [-nc/2, nc/2] is summed onto
-// Z_nc (n mod nc; for even nc the two ends +-nc/2 share index nc/2), then a
-// forward 2D DFT of length nc (Stockham, FP32) gives
-//   B(a, b) = (r^2 r' dnu_c)^2 sum_{n,m} exp(-2 pi i (n a + m b)/nc) Bbar(n, m).
-// Unsampled separations contribute zero.  Non-smooth nc use a direct DFT.
+// Delay transform: the separations -nc/2 <= n, m < nc/2 (one period of the
+// nc-periodic kernel) are placed at n mod nc, then a forward 2D DFT of length
+// nc (Stockham, FP32) gives
+//   B(a, b) = (r^2 r' dnu_c)^2 sum_{n,m} exp(-2 pi i (n a + m b)/nc) Bbar(n, m),
+// whose real part is stored (Bbar is point symmetric: the imaginary part is
+// the unpaired edge n, m = -nc/2 alone).  Unsampled separations contribute
+// zero.  Non-smooth nc use a direct DFT.
 #include "bs_internal.h"
 #include "fft_smem.cuh"
 
@@ -109,12 +111,13 @@ __global__ void k_bs3d_rows(const double *__restrict__ dsum, const long long *__
   for (int t = threadIdx.x; t < nc; t += blockDim.x) tw[t] = twN[t];
   for (int m = threadIdx.x; m < nc; m += blockDim.x) {
     double acc = 0.0;
+    // one period of the nc-periodic kernel: separations -nc/2 <= n, m < nc/2
     for (int sa = 0; sa < 2; ++sa) {
       const int np = sa ? nidx - nc : nidx;
-      if (np < -h || np > h) continue;
+      if (2 * np < -nc || 2 * np >= nc) continue;
       for (int sb = 0; sb < 2; ++sb) {
         const int mp = sb ? m - nc : m;
-        if (mp < -h || mp > h) continue;
+        if (2 * mp < -nc || 2 * mp >= nc) continue;
         const double v = folded_bbar(ds, nnu, tn, nc, np + nc - 1, mp + nc - 1);
         if (v == v) acc += v;
       }

@@ -311,55 +311,76 @@ def test_collapse_fold_ratio_identity():
             assert g == pytest.approx(w, rel=1e-12, abs=1e-12 * np.nanmax(np.abs(bbar[k])))
 
 
-def _periodize(plane, nc):
-    """Sum the inclusive range [-nc/2, nc/2] onto Z_nc (indices n mod nc)."""
-    h = nc // 2
-    n = np.arange(-h, h + 1)
+def _placed(plane, nc, lo):
+    """Put the separations n = lo .. lo + nc - 1 of a centred plane at
+    indices n mod nc (one full period of the nc-periodic DFT kernel)."""
+    n = np.arange(lo, lo + nc)
     sub = plane[n + nc - 1][:, n + nc - 1]
     out = np.zeros((nc, nc), complex)
-    for a, na in enumerate(n):
-        for b, nb_ in enumerate(n):
-            out[na % nc, nb_ % nc] += sub[a, b]
+    out[np.ix_(n % nc, n % nc)] = sub
     return out
 
 
 @pytest.mark.parametrize("nc", [8, 16, 7])
 def test_delay_dft_closed_forms(nc):
-    """Eq. (dft) on planes with known transforms: a constant plane, a
-    separable cosine, and agreement with numpy's FFT of the periodized plane
-    (with Parseval).  Output index a + nc//2 holds k_par index a."""
+    """Eq. (dft), half-open range n, m in [-nc/2, nc/2) (one period), on planes
+    with known transforms: a constant plane (a single spike), a separable
+    cosine (four spikes), and agreement with numpy's FFT of the same nc x nc
+    separations (with Parseval).  Output index a + nc//2 holds k_par index a."""
     h = nc // 2
     d = np.arange(-(nc - 1), nc)
     D1, D2 = np.meshgrid(d, d, indexing="ij")
-    a = np.arange(-h, -h + nc)
     const = np.ones((2 * nc - 1, 2 * nc - 1))
     out = oracle.delay_dft(const, nc)
-    # sum over n in [-h, h] of exp(-2 pi i n a / nc)
-    if nc % 2 == 0:
-        s = nc * (a % nc == 0) + (-1.0) ** a
-    else:
-        s = nc * (a % nc == 0).astype(float)
-    np.testing.assert_allclose(out, np.outer(s, s), atol=1e-10)
+    want = np.zeros((nc, nc))
+    want[h, h] = nc * nc
+    np.testing.assert_allclose(out, want, atol=1e-10 * nc * nc)
     p, q = 2, 3
     cosp = np.cos(2 * np.pi * p * D1 / nc) * np.cos(2 * np.pi * q * D2 / nc)
     out = oracle.delay_dft(cosp, nc, r=1.3, rprime=0.7, dnu_c=0.04)
-    want = np.fft.fft2(_periodize(cosp, nc))
-    want = np.roll(want, (h, h), axis=(0, 1)) * (1.3**2 * 0.7 * 0.04) ** 2
-    np.testing.assert_allclose(out, want, atol=1e-9 * np.abs(want).max())
-    if nc % 2 == 1:
-        spikes = np.abs(out) > 1e-6 * np.abs(out).max()
-        assert spikes.sum() == 4
-        for aa in (p, -p):
-            for bb in (q, -q):
-                assert spikes[aa + h, bb + h]
+    scale = (1.3**2 * 0.7 * 0.04) ** 2
+    spikes = np.abs(out) > 1e-6 * np.abs(out).max()
+    assert spikes.sum() == 4
+    for aa in (p, -p):
+        for bb in (q, -q):
+            assert spikes[aa + h, bb + h]
+            assert out[aa + h, bb + h].real == pytest.approx(scale * nc * nc / 4, rel=1e-12)
     rnd = synth.rng(nc).standard_normal((2 * nc - 1, 2 * nc - 1))
-    rnd = rnd + rnd[::-1, ::-1]
+    rnd = rnd + rnd[::-1, ::-1]  # point symmetric, as a folded plane is
     out = oracle.delay_dft(rnd, nc)
-    per = _periodize(rnd, nc)
+    per = _placed(rnd, nc, -h)
     np.testing.assert_allclose(out, np.roll(np.fft.fft2(per), (h, h), axis=(0, 1)),
                                atol=1e-10 * np.abs(out).max())
     assert np.sum(np.abs(out) ** 2) == pytest.approx(nc * nc * np.sum(np.abs(per) ** 2), rel=1e-12)
-    assert np.abs(out.imag).max() <= 1e-10 * np.abs(out.real).max()
+    # real part = mean of the two half-open ranges [-h, h) and (-h, h]
+    other = np.roll(np.fft.fft2(_placed(rnd, nc, -h + 1 if nc % 2 == 0 else -h)), (h, h), axis=(0, 1))
+    np.testing.assert_allclose(out.real, 0.5 * (out + other).real, atol=1e-10 * np.abs(out).max())
+    if nc % 2 == 1:  # the half-open range is symmetric: the output is real
+        assert np.abs(out.imag).max() <= 1e-10 * np.abs(out.real).max()
+
+
+@pytest.mark.parametrize("nc", [8, 7])
+def test_delay_dft_inclusive_variant_differs_by_the_end_terms(nc):
+    """The printed limits -nc/2 ... nc/2 read literally (both ends) add, for
+    even nc, the row n = nc/2 and the column m = nc/2 to the half-open sum;
+    for odd nc the two readings are the same sum."""
+    h = nc // 2
+    rnd = synth.rng(100 + nc).standard_normal((2 * nc - 1, 2 * nc - 1))
+    half = oracle.delay_dft(rnd, nc)
+    incl = oracle.delay_dft(rnd, nc, variant="inclusive")
+    if nc % 2 == 1:
+        np.testing.assert_allclose(incl, half, atol=1e-12 * np.abs(half).max())
+        return
+    a = np.arange(-h, -h + nc)
+    ninc = np.arange(-h, h + 1)
+    extra = np.zeros((nc, nc), complex)
+    for n in ninc:
+        for m in ninc:
+            if n == h or m == h:
+                extra += rnd[n + nc - 1, m + nc - 1] * np.exp(
+                    -2j * np.pi * (np.add.outer(n * a, m * a)) / nc)
+    np.testing.assert_allclose(incl - half, extra, atol=1e-10 * np.abs(incl).max())
+    assert np.abs(extra).max() > 1e-3 * np.abs(half).max()  # the difference is visible
 
 
 def _ensemble_z(nreal=400, f_ng=1.0, predict=None):
