@@ -54,7 +54,7 @@
 extern "C" {
 #endif
 
-#define BS_ABI_VERSION 2
+#define BS_ABI_VERSION 3
 
 typedef struct bs_plan_s *bs_plan;
 
@@ -269,18 +269,22 @@ bs_status bs_mc_stats(bs_mc mc, int group, int which, double *mean_dev, double *
  * fallback and the judge of its error.  Flat parameter vector (float):
  *   W1 [w][d] | b1 [w] | W2 [w][w] | b2 [w] | w3 [w] | b3 | mu_x [d] | sd_x [d] | mu_y | sd_y
  * ------------------------------------------------------------------------- */
-#define BS_MLP_FEATURES 42
+#define BS_MLP_FEATURES 45
 typedef struct bs_mlp_s *bs_mlp;
 
 /* Features of every 3D-bispectrum bin (trip, a, b) of a plan, float
- * [T_r*nchan*nchan][42] on the device, rows in bs_bs3d order:
+ * [T_r*nchan*nchan][45] on the device, rows in bs_bs3d order:
  *  0 log k1, 1 t = k2/k1, 2 mu = (k1^2+k2^2-k3^2)/(2 k1 k2) (Eq. shape), where
  *    k_n = sqrt(k_perp n^2 + k_par n^2), k_perp = 2 pi Ubar_ring / r (ring-mean
  *    |U|), k_par a = 2 pi a / (r' nchan dnu_c), k_par 3 = -k_par a - k_par b,
  *    sorted k1 >= k2 >= k3;
  *  3 flagged fraction; 4 log T(i,j,l); 5 |k_par a|; 6 |k_par b|;
  *  7..9 log k_perp of rings i, j, l; 10..41 fraction of channels flagged at
- *  each position c mod 32 of the coarse bands.
+ *  each position c mod 32 of the coarse bands; 42..44 the sampling of the
+ *  Eq. (dft) square under the mask: with N(d) the folded number of valid
+ *  channel triples at separation d, -nchan/2 <= d1, d2 < nchan/2,
+ *  42 log sum_{N>0} 1/N, 43 fraction of separations with N > 0,
+ *  44 log mean_{N>0} N (0 and 0 when nothing is sampled).
  * Rows of ring triples without closed triangles are NaN.  Synchronises. */
 bs_status bs_mlp_features(bs_plan plan, const uint8_t *chan_flag_host, float *feat_dev,
                           void *cuda_stream);

@@ -26,6 +26,8 @@ STATUS = {0: "BS_OK", 1: "BS_ERR_ARG", 2: "BS_ERR_NO_DEVICE", 3: "BS_ERR_CUDA", 
           8: "BS_ERR_UNSUPPORTED"}
 PREC_FP32 = 0
 PREC_SPLIT_BF16 = 1
+ABI_VERSION = 3      # BS_ABI_VERSION of include/bs.h
+MLP_FEATURES = 45    # BS_MLP_FEATURES of include/bs.h
 
 # every symbol declared in include/bs.h
 EXPORTS = ("bs_abi_version", "bs_plan_create", "bs_plan_destroy", "bs_last_error",
@@ -238,10 +240,11 @@ class Plan:
         self._check(self._L.bs_bs3d(self._h, _dptr(out), _stream_ptr(stream)))
 
     def mlp_features(self, chan_flags=None, stream=None):
-        """bs_mlp_features: float32 CUDA tensor [ntrip*nc*nc, 42] (NaN rows: no triangle)."""
+        """bs_mlp_features: float32 CUDA tensor [ntrip*nc*nc, MLP_FEATURES] (NaN rows: no
+        triangle)."""
         import numpy as np
         import torch
-        out = torch.empty((self.ntrip * self.nchan * self.nchan, 42), dtype=torch.float32,
+        out = torch.empty((self.ntrip * self.nchan * self.nchan, MLP_FEATURES), dtype=torch.float32,
                           device="cuda")
         fl = None
         if chan_flags is not None:
@@ -420,7 +423,8 @@ class Ensemble:
 class Surrogate:
     """bs_mlp_*: the error-bar network (d_in inputs, width hidden units)."""
 
-    def __init__(self, d_in=42, width=128, seed=1):
+    def __init__(self, d_in=None, width=128, seed=1):
+        d_in = MLP_FEATURES if d_in is None else d_in
         L = lib()
         self._L = L
         h = ctypes.c_void_p()

@@ -289,6 +289,7 @@ __global__ void k_mlp_features(int ntrip, int nc, const float4 *__restrict__ tab
     o[8] = logf(tb.z);
     o[9] = logf(tb.w);
     for (int k = 0; k < 32; ++k) o[10 + k] = flagf[1 + k];
+    for (int k = 0; k < 3; ++k) o[42 + k] = flagf[33 + k];
   }
 }
 
@@ -521,7 +522,7 @@ bs_status bs_mlp_features(bs_plan p, const uint8_t *flags_host, float *feat_dev,
   }
   const double r = p->d.r > 0 ? p->d.r : 1.0, rp = p->d.rprime > 0 ? p->d.rprime : 1.0,
                dnu = p->d.dnu_c > 0 ? p->d.dnu_c : 1.0;
-  std::vector<float> tab((size_t)p->ntrip * 4 + 33);
+  std::vector<float> tab((size_t)p->ntrip * 4 + 36);
   for (int t = 0; t < p->ntrip; ++t) {
     const int i = p->trips[3 * t], j = p->trips[3 * t + 1], l = p->trips[3 * t + 2];
     const bool ok = p->T[t] > 0;
@@ -541,6 +542,31 @@ bs_status bs_mlp_features(bs_plan p, const uint8_t *flags_host, float *feat_dev,
   }
   ff[0] = (float)nfl / p->nc;
   for (int q = 0; q < 32; ++q) ff[1 + q] = pos_n[q] ? (float)pos_f[q] / pos_n[q] : 0.f;
+  // sampling of the Eq. (dft) square under this mask: folded counts N(d) of valid
+  // channel triples at the separations -nc/2 <= d1, d2 < nc/2
+  {
+    const int nc = p->nc, n2 = 2 * nc - 1, h = nc / 2;
+    std::vector<uint8_t> valid(nc);
+    for (int c = 0; c < nc; ++c) valid[c] = (flags_host && flags_host[c]) ? 0 : 1;
+    std::vector<long long> plane((size_t)n2 * n2, 0);
+    const int full[6] = {0, nc, 0, nc, 0, nc};
+    add_block_sampling(nc, valid, full, plane.data());
+    double sinv = 0, ssum = 0;
+    long long nsamp = 0;
+    for (int d1 = -h; d1 < nc - h; ++d1)
+      for (int d2 = -h; d2 < nc - h; ++d2) {
+        long long c = plane[(size_t)(d1 + nc - 1) * n2 + d2 + nc - 1];
+        if (d1 != 0 || d2 != 0) c += plane[(size_t)((long long)(nc - 1 - d1) * n2 + (nc - 1 - d2))];
+        if (c > 0) {
+          sinv += 1.0 / (double)c;
+          ssum += (double)c;
+          ++nsamp;
+        }
+      }
+    ff[33] = nsamp ? (float)std::log(sinv) : 0.f;
+    ff[34] = (float)nsamp / ((float)nc * nc);
+    ff[35] = nsamp ? (float)std::log(ssum / nsamp) : 0.f;
+  }
   float *dtab = p->at<float>(p->L.mlptab);
   BS_CUDA(cudaMemcpyAsync(dtab, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice, s));
   const float kpar_unit = (float)(2 * M_PI / (rp * p->nc * dnu));

@@ -131,7 +131,7 @@ void compute_layout(bs_plan p) {
   L.err = take(sizeof(int));
   L.maps = take(7 * p->levels.size() * sizeof(CUtensorMap));
   L.tcgroup = take(p->levels.size() * sizeof(TcGroup));
-  L.mlptab = take(((size_t)p->ntrip * 4 + 33) * sizeof(float));
+  L.mlptab = take(((size_t)p->ntrip * 4 + 36) * sizeof(float));
   L.ztrips = take((size_t)p->ntrip * sizeof(int));
   L.total = o;
 }
@@ -300,13 +300,15 @@ bs_status run_counts(bs_plan p, const int8_t *lab_dev, cudaStream_t s) {
 
 // Unfolded sampling of a channel block: cnt[d1][d2] += #{nu3 in B3 : nu3+d1 in
 // B1, nu3+d2 in B2, all three valid}, with 64-bit words of channel bits.
-void accumulate_block_nnu(bs_plan p, const int *blk) {
-  const int nc = p->nc, n2 = 2 * nc - 1;
+// plane: [2nc-1][2nc-1], index (d1 + nc - 1, d2 + nc - 1).
+void add_block_sampling(int nc, const std::vector<uint8_t> &valid, const int *blk,
+                        long long *plane) {
+  const int n2 = 2 * nc - 1;
   const int W = (nc + 63) / 64;
   auto bits = [&](int lo, int hi) {
     std::vector<uint64_t> b(W, 0);
     for (int c = lo; c < hi; ++c)
-      if (p->valid[c]) b[c >> 6] |= uint64_t(1) << (c & 63);
+      if (valid[c]) b[c >> 6] |= uint64_t(1) << (c & 63);
     return b;
   };
   const std::vector<uint64_t> b1 = bits(blk[0], blk[1]), b2 = bits(blk[2], blk[3]),
@@ -340,7 +342,7 @@ void accumulate_block_nnu(bs_plan p, const int *blk) {
       any |= p1[w] != 0;
     }
     if (!any) continue;
-    long long *row = &p->nnu[(size_t)(d1 + nc - 1) * n2];
+    long long *row = plane + (size_t)(d1 + nc - 1) * n2;
     for (int d2i = d2lo + nc - 1; d2i <= d2hi + nc - 1; ++d2i) {
       const uint64_t *q = &s2[(size_t)d2i * W];
       long long c = 0;
@@ -348,6 +350,10 @@ void accumulate_block_nnu(bs_plan p, const int *blk) {
       row[d2i] += c;
     }
   }
+}
+
+void accumulate_block_nnu(bs_plan p, const int *blk) {
+  add_block_sampling(p->nc, p->valid, blk, p->nnu.data());
   p->nnu_dirty = true;
 }
 

@@ -92,6 +92,10 @@ bs_status run_counts(bs_plan p, const int8_t *lab_dev, cudaStream_t s);
 bs_status ensure_tensor_maps(bs_plan p, cudaStream_t s);
 bs_status check_device_error(bs_plan p, cudaStream_t s);
 void accumulate_block_nnu(bs_plan p, const int *blk);
+// Adds the unfolded sampling of channel block blk under the channel validity
+// `valid` to plane[(d1 + nc - 1) * (2nc - 1) + d2 + nc - 1].
+void add_block_sampling(int nc, const std::vector<uint8_t> &valid, const int *blk,
+                        long long *plane);
 bs_status upload_nnu(bs_plan p, cudaStream_t s);
 // Append the tensor-core work of one channel block of plan p (all
 // realisations): one shape group per image level, numbered from group_base.

@@ -33,7 +33,13 @@ def test_header_declarations_exported(lib):
 
 
 def test_abi_version(lib):
-    assert lib.bs_abi_version() == 2
+    assert lib.bs_abi_version() == bs.ABI_VERSION == 3
+
+
+def test_binding_constants_match_header():
+    src = open(os.path.join(ROOT, "include", "bs.h")).read()
+    assert int(re.search(r"#define BS_ABI_VERSION (\d+)", src).group(1)) == bs.ABI_VERSION
+    assert int(re.search(r"#define BS_MLP_FEATURES (\d+)", src).group(1)) == bs.MLP_FEATURES
 
 
 def test_desc_validation_and_no_device(lib):
