@@ -74,7 +74,8 @@ constexpr int OFF_A = 0;
 constexpr int OFF_B = OFF_A + ASTAGES * 2 * A_BYTES;
 constexpr int OFF_RAW = OFF_B + STAGES * 2 * B_BYTES;
 constexpr int OFF_ROW = OFF_RAW + RSTAGES * RAW_BYTES;
-constexpr int OFF_SEG = OFF_ROW + MROWS * 16;
+constexpr int OFF_COL = OFF_ROW + MROWS * 16;  // the tile's column entries (epilogue)
+constexpr int OFF_SEG = OFF_COL + MROWS * 16;
 constexpr int MAX_SEG = 16;
 // tensor maps per level: BF16 hi/lo with boxes of 8, 32 and 128 field rows, FP32 rows
 constexpr int NMAPS = 7;
@@ -214,6 +215,10 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 __device__ __forceinline__ uint64_t sw64_desc(uint32_t addr) {
   return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) |
          ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
+}
+// Shared-memory float reduction (no return value) at a shared-space address.
+__device__ __forceinline__ void red_add_shared(uint32_t addr, float v) {
+  asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
 }
 // Byte offset of 16-byte chunk c (0..3) of row r in a 64B-swizzled K-major tile.
 __device__ __forceinline__ uint32_t sw64_off(int r, int c) {
@@ -507,6 +512,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
     const unsigned char *rawb = sm + OFF_RAW;
     int4 *rowinfo = reinterpret_cast<int4 *>(sm + OFF_ROW);  // (C_m, E_m, trip, nu3 | -1)
     int4 *seginfo = reinterpret_cast<int4 *>(sm + OFF_SEG);  // (base, E, trip, hi)
+    ColEntry *colbuf = reinterpret_cast<ColEntry *>(sm + OFF_COL);
     int *nseg_s = reinterpret_cast<int *>(sm + OFF_MISC + 8);
     int *total_s = reinterpret_cast<int *>(sm + OFF_MISC + 12);
     float *red = reinterpret_cast<float *>(sm + OFF_B);
@@ -527,6 +533,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
       const int b = t.b;
       const int cbase = t.col0 + MROWS * (int)rank;
       const int k0 = t.kseg * G.kseg_len, k1 = min(G.Kpad, k0 + G.kseg_len);
+
       for (int kc = k0; kc < k1; kc += KC, ++it, ++rit) {
         const int s = it % STAGES;
         const uint32_t ph = (it / STAGES) & 1;
@@ -591,21 +598,25 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
       }
       ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
       tc_fence_after();
+      if (ptid < MROWS) {  // the tile's column entries (field -2: past the end of the list)
+        ColEntry ce{-2, 0, 0, 0};
+        if (cbase + ptid < t.ncol) ce = G.cols[t.col_off + cbase + ptid];
+        colbuf[ptid] = ce;
+      }
       asm volatile("bar.sync 1, 256;" ::: "memory");
       if (ptid == 0) {
         // segments of consecutive rows with one ring triple
         int ns = 0, base = 0, m = 0;
         while (m < MROWS) {
-          const int e = cbase + m;
-          if (e >= t.ncol) break;
-          const ColEntry c0 = G.cols[t.col_off + e];
+          const ColEntry c0 = colbuf[m];
+          if (c0.field == -2) break;
           if (c0.field < 0) {
             ++m;
             continue;
           }
           int lo = c0.nu3, hi = c0.nu3, q = m;
-          while (q + 1 < MROWS && cbase + q + 1 < t.ncol) {
-            const ColEntry cn = G.cols[t.col_off + cbase + q + 1];
+          while (q + 1 < MROWS && colbuf[q + 1].field != -2) {
+            const ColEntry cn = colbuf[q + 1];
             if (cn.field >= 0 && cn.trip != c0.trip) break;
             ++q;
             if (cn.field >= 0) {
@@ -616,8 +627,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
           const int E = (P2 - 1) + (hi - lo) + 1;
           if (ns < MAX_SEG) seginfo[ns] = make_int4(base, E, c0.trip, hi);
           for (int r = m; r <= q; ++r) {
-            const int ee = cbase + r;
-            const ColEntry cr = G.cols[t.col_off + ee];
+            const ColEntry cr = colbuf[r];
             if (cr.field < 0)
               rowinfo[r] = make_int4(0, 0, cr.trip, -1);
             else if (ns >= MAX_SEG)  // no reduction slot: direct atomics (total > RED_CAP)
@@ -644,33 +654,47 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
       const int m = 32 * quad + lane;
       const int4 ri = rowinfo[m];
       const bool row_ok = ri.w >= 0;
+      // the group's fields in registers: the loop below writes memory through
+      // atomics, which would otherwise make every field a reload
+      const int nu1_hi = G.nu1_hi, nu2_hi = G.nu2_hi;
+      const bool fast = use_red && G.out_full == nullptr;  // collapse only: shared reduction
       const double tn = (G.out_full && row_ok) ? G.tnorm[ri.z] : 0.0;
       const int n2 = 2 * G.nc - 1;
+      const int nu1_0 = t.nu1_0, nu2_0 = t.nu2_0;
+      const uint32_t red_row = smem_u32(red) + 4u * (uint32_t)ri.x;
       for (int ch = 0; ch < 256 / 32; ++ch) {
         uint32_t v[32];
         if (ok) tc_ld32(tmem + ((uint32_t)(32 * quad) << 16) + half * 256 + ch * 32, v);
         if (!ok || !row_ok) continue;
+        if (fast) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int p = half * 256 + ch * 32 + j;
+            const int pa = p >> 4, pb = p & 15;
+            if (nu1_0 + pa >= nu1_hi || nu2_0 + pb >= nu2_hi) continue;
+            red_add_shared(red_row + 4u * (uint32_t)((pa - pb) * ri.y + pb), __uint_as_float(v[j]));
+          }
+          continue;
+        }
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const int p = half * 256 + ch * 32 + j;
           const int pa = p >> 4, pb = p & 15;
           const int nu1 = t.nu1_0 + pa, nu2 = t.nu2_0 + pb;
           if (nu1 >= G.nu1_hi || nu2 >= G.nu2_hi) continue;
-          const float s = __uint_as_float(v[j]);
-          if (G.dsum) {
-            if (use_red) {
-              atomicAdd(red + ri.x + (pa - pb) * ri.y + pb, s);
-            } else {
-              const long long o = (long long)b * G.dsum_bstride +
-                                  ((long long)ri.z * n2 + (nu1 - ri.w + G.nc - 1)) * n2 +
-                                  (nu2 - ri.w + G.nc - 1);
-              atomicAdd(G.dsum + o, (double)s);
-            }
+          const float sv = __uint_as_float(v[j]);
+          if (use_red) {
+            red_add_shared(red_row + 4u * (uint32_t)((pa - pb) * ri.y + pb), sv);
+          } else if (G.dsum) {
+            const long long o = (long long)b * G.dsum_bstride +
+                                ((long long)ri.z * n2 + (nu1 - ri.w + G.nc - 1)) * n2 +
+                                (nu2 - ri.w + G.nc - 1);
+            atomicAdd(G.dsum + o, (double)sv);
           }
           if (G.out_full) {
             const long long o = (long long)b * G.full_bstride +
                                 (((long long)ri.z * G.nc + nu1) * G.nc + nu2) * G.nc + ri.w;
-            atomicAdd(G.out_full + o, (double)s * tn);
+            atomicAdd(G.out_full + o, (double)sv * tn);
           }
         }
       }
