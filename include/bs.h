@@ -180,7 +180,10 @@ bs_status bs_delta_reset(bs_plan plan, void *cuda_stream);
  * nchan-1]^2, the mean of B_A over the accumulated valid channel triples with
  * (nu1-nu3, nu2-nu3) = (d1, d2) or (-d1, -d2).
  *  out_dev  double [batch][T_r][2nchan-1][2nchan-1], index [d1+nchan-1][d2+nchan-1];
- *           the plane is point symmetric; NaN where no triple was sampled. */
+ *           the plane is point symmetric; NaN where no triple was sampled.
+ * If a tensor-core contraction ran since the last check, synchronises on
+ * cuda_stream to read its error word and returns BS_ERR_TIMEOUT when one of
+ * its bounded waits gave up (the accumulated sums are then invalid). */
 bs_status bs_mabs_delta(bs_plan plan, double *out_dev, void *cuda_stream);
 
 /* Eq. (dft) applied to the folded collapsed MABS:
@@ -192,7 +195,8 @@ bs_status bs_mabs_delta(bs_plan plan, double *out_dev, void *cuda_stream);
  * point symmetric, so the imaginary part of the sum comes only from the
  * unpaired edge n, m = -nchan/2; the real part is returned.
  * k_par a = 2 pi a / (r' nchan dnu_c).
- *  out_dev  double [batch][T_r][nchan][nchan], index [a + nchan/2][b + nchan/2]. */
+ *  out_dev  double [batch][T_r][nchan][nchan], index [a + nchan/2][b + nchan/2].
+ * Checks the contraction's error word like bs_mabs_delta. */
 bs_status bs_bs3d(bs_plan plan, double *out_dev, void *cuda_stream);
 
 /* Check V(-U) = conj V(U) on every binned cell of every channel and

@@ -184,12 +184,12 @@ bs_status init_tables(bs_plan p, cudaStream_t s) {
 // Read and clear the device error word (synchronises): a bounded wait in a
 // kernel gave up since the last check.
 bs_status check_device_error(bs_plan p, cudaStream_t s) {
-  int h = 0;
-  BS_CUDA(cudaMemcpyAsync(&h, p->at<int>(p->L.err), sizeof(int), cudaMemcpyDeviceToHost, s));
+  if (!p->err_pending) return BS_OK;
   BS_CUDA(cudaStreamSynchronize(s));
-  if (h != 0) {
-    BS_CUDA(cudaMemsetAsync(p->at<int>(p->L.err), 0, sizeof(int), s));
-    BS_CUDA(cudaStreamSynchronize(s));
+  p->err_pending = false;
+  volatile int *e = p->err_host;
+  if (*e != 0) {
+    *e = 0;
     return fail(p, BS_ERR_TIMEOUT,
                 "a bounded wait in the tensor-core contraction gave up; its results are invalid");
   }
@@ -499,7 +499,8 @@ bs_status mabs_tc(bs_plan p, const int *blk, double *out_full, int accumulate, c
   a.maps = p->at<unsigned char>(L.maps);
   a.tiles = p->at<TcTile>(L.tctiles);
   a.ntiles = (int)p->h_tctiles.size();
-  a.err = p->at<int>(L.err);
+  a.err = p->err_dev;
+  p->err_pending = true;
   a.wait_limit_ns = 2000000000LL;
   const char *inj = std::getenv("BS_INJECT_MMA_STALL");
   a.stall_test = (inj && inj[0] == '1') ? 1 : 0;
@@ -558,6 +559,13 @@ bs_status bs_plan_create(const bs_plan_desc *desc, bs_plan *out) {
   p->nc = d.nchan;
   p->nb = d.nbins;
   p->batch = d.batch;
+  if (cudaHostAlloc(&p->err_host, sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
+      cudaHostGetDevicePointer(&p->err_dev, p->err_host, 0) != cudaSuccess) {
+    cudaGetLastError();
+    delete p;
+    return fail(nullptr, BS_ERR_OOM, "cannot allocate the mapped error word");
+  }
+  *p->err_host = 0;
   p->edges.assign(d.bin_edges, d.bin_edges + d.nbins + 1);
   p->d.bin_edges = nullptr;
   p->normA = d.norm_A > 0 ? d.norm_A : 1.0;

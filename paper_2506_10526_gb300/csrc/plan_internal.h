@@ -62,6 +62,13 @@ struct bs_plan_s {
   std::vector<long long> nnu;    // [(2nc-1)^2] accumulated unfolded sampling
   bool counts_ready = false, counts_default = false, nnu_dirty = true, loaded = false;
   bool sticky = false;
+  // error word of the tensor-core contraction in mapped pinned host memory
+  // (read after a stream sync, with no copy engine involved)
+  int *err_host = nullptr, *err_dev = nullptr;
+  bool err_pending = false;  // a contraction ran since the last check
+  ~bs_plan_s() {
+    if (err_host) cudaFreeHost(err_host);
+  }
   std::string err = "no error";
   // workspace
   WsLayout L{};
