@@ -96,20 +96,31 @@ __device__ void dft_direct(const float2 *x, float2 *y, int N, const float2 *tw, 
   __syncthreads();
 }
 
+// Rows (columns) of the 2D delay transform per CTA: the transposed stores of
+// the row pass and the scattered stores of the column pass go out as runs of
+// kBsRows consecutive elements.
+constexpr int kBsRows = 8;
+
+// First pass: for kBsRows consecutive n, the folded plane Bbar(n, m) over one
+// period of m, transformed along m; written transposed, tmp[k][n].
 __global__ void k_bs3d_rows(const double *__restrict__ dsum, const long long *__restrict__ nnu,
                             const double *__restrict__ tnorm, float2 *__restrict__ tmp, int ntrip,
                             int nc, const float2 *__restrict__ twN, Radices radN) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int LD = nc + 1;  // padded rows: the transposed reads spread over the banks
   float2 *tw = reinterpret_cast<float2 *>(smem_raw);
   float2 *bufA = tw + nc;
-  float2 *bufB = bufA + nc;
-  const int nidx = blockIdx.x, trip = blockIdx.y, b = blockIdx.z;
-  const int n2 = 2 * nc - 1, h = nc / 2;
+  float2 *bufB = bufA + kBsRows * LD;
+  const int n0 = blockIdx.x * kBsRows, trip = blockIdx.y, b = blockIdx.z;
+  const int nr = min(kBsRows, nc - n0);
+  const int n2 = 2 * nc - 1;
   const double *ds = dsum + ((long long)b * ntrip + trip) * (long long)n2 * n2;
   const double tn = tnorm[trip];
   if (tn == 0.0) return;  // no closed triangle: the column pass writes zeros
   for (int t = threadIdx.x; t < nc; t += blockDim.x) tw[t] = twN[t];
-  for (int m = threadIdx.x; m < nc; m += blockDim.x) {
+  for (int e = threadIdx.x; e < nr * nc; e += blockDim.x) {
+    const int r = e / nc, m = e - r * nc;
+    const int nidx = n0 + r;
     double acc = 0.0;
     // one period of the nc-periodic kernel: separations -nc/2 <= n, m < nc/2
     for (int sa = 0; sa < 2; ++sa) {
@@ -122,53 +133,62 @@ __global__ void k_bs3d_rows(const double *__restrict__ dsum, const long long *__
         if (v == v) acc += v;
       }
     }
-    bufA[m] = make_float2((float)acc, 0.f);
+    bufA[r * LD + m] = make_float2((float)acc, 0.f);
   }
   __syncthreads();
   float2 *res;
   if (radN.n > 0) {
-    res = stockham(bufA, bufB, 1, nc, radN, tw, -1.0f);
+    res = stockham(bufA, bufB, nr, nc, LD, radN, tw, -1.0f);
   } else {
-    dft_direct(bufA, bufB, nc, tw, -1.0f);
+    for (int r = 0; r < nr; ++r) dft_direct(bufA + r * LD, bufB + r * LD, nc, tw, -1.0f);
     res = bufB;
   }
   float2 *tb = tmp + ((long long)b * ntrip + trip) * (long long)nc * nc;
-  for (int k = threadIdx.x; k < nc; k += blockDim.x) tb[(long long)k * nc + nidx] = res[k];
+  for (int e = threadIdx.x; e < nr * nc; e += blockDim.x) {
+    const int k = e / nr, r = e - k * nr;
+    tb[(long long)k * nc + n0 + r] = res[r * LD + k];
+  }
 }
 
+// Second pass: for kBsRows consecutive first-pass frequencies, transform along
+// n; out[a + nc/2][b + nc/2] = scale * Re.
 __global__ void k_bs3d_cols(const float2 *__restrict__ tmp, double *__restrict__ out, int ntrip,
                             int nc, const float2 *__restrict__ twN, Radices radN, double scale,
                             const double *__restrict__ tnorm) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int LD = nc + 1;
   float2 *tw = reinterpret_cast<float2 *>(smem_raw);
   float2 *bufA = tw + nc;
-  float2 *bufB = bufA + nc;
-  const int bb = blockIdx.x, trip = blockIdx.y, b = blockIdx.z;
+  float2 *bufB = bufA + kBsRows * LD;
+  const int bb0 = blockIdx.x * kBsRows, trip = blockIdx.y, b = blockIdx.z;
+  const int nr = min(kBsRows, nc - bb0);
   const int h = nc / 2;
+  double *ob = out + ((long long)b * ntrip + trip) * (long long)nc * nc;
+  auto centred = [&](int k) { return (k < nc - h) ? k + h : k - nc + h; };
   if (tnorm[trip] == 0.0) {
-    double *ob = out + ((long long)b * ntrip + trip) * (long long)nc * nc;
-    const int bidx = (bb < nc - h) ? bb + h : bb - nc + h;
-    for (int k = threadIdx.x; k < nc; k += blockDim.x) ob[(long long)k * nc + bidx] = 0.0;
+    for (int e = threadIdx.x; e < nr * nc; e += blockDim.x) {
+      const int k = e / nr, r = e - k * nr;
+      ob[(long long)k * nc + centred(bb0 + r)] = 0.0;
+    }
     return;
   }
-  const float2 *tb = tmp + ((long long)b * ntrip + trip) * (long long)nc * nc + (long long)bb * nc;
-  for (int t = threadIdx.x; t < nc; t += blockDim.x) {
-    tw[t] = twN[t];
-    bufA[t] = tb[t];
+  const float2 *tb = tmp + ((long long)b * ntrip + trip) * (long long)nc * nc + (long long)bb0 * nc;
+  for (int t = threadIdx.x; t < nc; t += blockDim.x) tw[t] = twN[t];
+  for (int e = threadIdx.x; e < nr * nc; e += blockDim.x) {
+    const int r = e / nc, t = e - r * nc;
+    bufA[r * LD + t] = tb[(long long)r * nc + t];
   }
   __syncthreads();
   float2 *res;
   if (radN.n > 0) {
-    res = stockham(bufA, bufB, 1, nc, radN, tw, -1.0f);
+    res = stockham(bufA, bufB, nr, nc, LD, radN, tw, -1.0f);
   } else {
-    dft_direct(bufA, bufB, nc, tw, -1.0f);
+    for (int r = 0; r < nr; ++r) dft_direct(bufA + r * LD, bufB + r * LD, nc, tw, -1.0f);
     res = bufB;
   }
-  double *ob = out + ((long long)b * ntrip + trip) * (long long)nc * nc;
-  const int bidx = (bb < nc - h) ? bb + h : bb - nc + h;
-  for (int k = threadIdx.x; k < nc; k += blockDim.x) {
-    const int aidx = (k < nc - h) ? k + h : k - nc + h;
-    ob[(long long)aidx * nc + bidx] = scale * (double)res[k].x;
+  for (int e = threadIdx.x; e < nr * nc; e += blockDim.x) {
+    const int k = e / nr, r = e - k * nr;
+    ob[(long long)centred(k) * nc + centred(bb0 + r)] = scale * (double)res[r * LD + k].x;
   }
 }
 
@@ -228,13 +248,13 @@ cudaError_t launch_zero_planes(double *dsum, const int *trips, int ntr, int batc
 cudaError_t launch_bs3d(const double *dsum, const long long *nnu, const double *tnorm, float2 *tmp,
                         double *out, int batch, int ntrip, int nc, const float2 *twN,
                         const Radices &radN, double scale, cudaStream_t s) {
-  const size_t smem = (size_t)3 * nc * sizeof(float2);
+  const size_t smem = (size_t)(nc + 2 * kBsRows * (nc + 1)) * sizeof(float2);
   cudaError_t e = smem_optin_once(k_bs3d_rows);
   if (e != cudaSuccess) return e;
   e = smem_optin_once(k_bs3d_cols);
   if (e != cudaSuccess) return e;
-  const int threads = nc >= 256 ? 256 : (nc >= 64 ? 64 : 32);
-  dim3 grid(nc, ntrip, batch);
+  const int threads = nc >= 64 ? 256 : 64;
+  dim3 grid((nc + kBsRows - 1) / kBsRows, ntrip, batch);
   k_bs3d_rows<<<grid, threads, smem, s>>>(dsum, nnu, tnorm, tmp, ntrip, nc, twN, radN);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;

@@ -82,7 +82,7 @@ __device__ __forceinline__ void butterfly<5>(float2 *u, float sign) {
 
 template <int R>
 __device__ __forceinline__ void stockham_stage(const float2 *__restrict__ x, float2 *__restrict__ y,
-                                               int nrows, int N, int p, const float2 *tw,
+                                               int nrows, int N, int ld, int p, const float2 *tw,
                                                float sign) {
   const int NR = N / R;
   const int tstride = N / (p * R);
@@ -90,8 +90,8 @@ __device__ __forceinline__ void stockham_stage(const float2 *__restrict__ x, flo
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
     const int row = idx / NR;
     const int i = idx - row * NR;
-    const float2 *xr = x + row * N;
-    float2 *yr = y + row * N;
+    const float2 *xr = x + row * ld;
+    float2 *yr = y + row * ld;
     const int k = i % p;
     float2 u[R];
 #pragma unroll
@@ -111,19 +111,20 @@ __device__ __forceinline__ void stockham_stage(const float2 *__restrict__ x, flo
   }
 }
 
-// In-place (ping-pong) transform of nrows rows of length N stored
-// contiguously in x; y is scratch of the same size.  All threads of the block
-// must call it.  Returns the buffer that holds the result.
-__device__ __forceinline__ float2 *stockham(float2 *x, float2 *y, int nrows, int N,
+// In-place (ping-pong) transform of nrows rows of length N, row r at x + r ld
+// (ld >= N; ld = N + 1 keeps column-wise accesses of power-of-two rows off a
+// single bank); y is scratch of the same size.  All threads of the block must
+// call it.  Returns the buffer that holds the result.
+__device__ __forceinline__ float2 *stockham(float2 *x, float2 *y, int nrows, int N, int ld,
                                             const Radices &rad, const float2 *tw, float sign) {
   int p = 1;
   for (int s = 0; s < rad.n; ++s) {
     const int R = rad.r[s];
     switch (R) {
-      case 4: stockham_stage<4>(x, y, nrows, N, p, tw, sign); break;
-      case 2: stockham_stage<2>(x, y, nrows, N, p, tw, sign); break;
-      case 3: stockham_stage<3>(x, y, nrows, N, p, tw, sign); break;
-      default: stockham_stage<5>(x, y, nrows, N, p, tw, sign); break;
+      case 4: stockham_stage<4>(x, y, nrows, N, ld, p, tw, sign); break;
+      case 2: stockham_stage<2>(x, y, nrows, N, ld, p, tw, sign); break;
+      case 3: stockham_stage<3>(x, y, nrows, N, ld, p, tw, sign); break;
+      default: stockham_stage<5>(x, y, nrows, N, ld, p, tw, sign); break;
     }
     __syncthreads();
     float2 *t = x;
@@ -132,6 +133,10 @@ __device__ __forceinline__ float2 *stockham(float2 *x, float2 *y, int nrows, int
     p *= R;
   }
   return x;
+}
+__device__ __forceinline__ float2 *stockham(float2 *x, float2 *y, int nrows, int N,
+                                            const Radices &rad, const float2 *tw, float sign) {
+  return stockham(x, y, nrows, N, N, rad, tw, sign);
 }
 
 }  // namespace bsi

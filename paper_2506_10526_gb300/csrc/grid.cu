@@ -39,10 +39,11 @@ __global__ void __launch_bounds__(256) k_colpass(GridGeom g, int UB, const float
   const int nu = blockIdx.y;
   const int b = blockIdx.z;
   if (!valid[nu]) return;  // fields of a flagged channel are written as zeros by rowpass
+  const int LD = M + 1;  // padded column rows: column-wise accesses spread over the banks
   float2 *tw = reinterpret_cast<float2 *>(smem_raw);
   float2 *bufA = tw + M;
-  float2 *bufB = bufA + UB * M;
-  float2 *xt = bufB + UB * M;                                   // [nt][UB] weighted visibilities
+  float2 *bufB = bufA + UB * LD;
+  float2 *xt = bufB + UB * LD;                                  // [nt][UB] weighted visibilities
   int8_t *lt = reinterpret_cast<int8_t *>(xt + nt * UB);        // [nt][UB] ring labels
   for (int t = threadIdx.x; t < M; t += blockDim.x) tw[t] = twM[t];
   const float2 *vb = vis + ((long long)b * g.nc + nu) * (long long)nt * nt;
@@ -73,23 +74,23 @@ __global__ void __launch_bounds__(256) k_colpass(GridGeom g, int UB, const float
     const int ue = uext[m];
     const int slot = g.slot_of[m];
     if (slot < 0 || u0 >= ue) continue;  // block-uniform
-    for (int t = threadIdx.x; t < UB * M; t += blockDim.x) bufA[t] = make_float2(0.f, 0.f);
+    for (int t = threadIdx.x; t < UB * LD; t += blockDim.x) bufA[t] = make_float2(0.f, 0.f);
     __syncthreads();
     for (int t = threadIdx.x; t < nt * UB; t += blockDim.x) {
       if (lt[t] == m) {
         const int iv = t / UB, c = t - iv * UB;
         int y = iv - h;
         if (y < 0) y += M;
-        bufA[c * M + y] = xt[t];
+        bufA[c * LD + y] = xt[t];
       }
     }
     __syncthreads();
-    float2 *res = stockham(bufA, bufB, UB, M, radM, tw, +1.0f);
+    float2 *res = stockham(bufA, bufB, UB, M, LD, radM, tw, +1.0f);
     float2 *Gm = G + (((long long)b * g.nslot + slot) * g.nc + nu) * (long long)M * g.UC;
     const int ncols = min(UB, g.UC - u0);
     for (int t = threadIdx.x; t < M * UB; t += blockDim.x) {
       const int y = t / UB, c = t - y * UB;
-      if (c < ncols) Gm[(long long)y * g.UC + u0 + c] = res[c * M + y];
+      if (c < ncols) Gm[(long long)y * g.UC + u0 + c] = res[c * LD + y];
     }
     __syncthreads();
   }
@@ -279,11 +280,13 @@ __global__ void k_hermitian(const float2 *__restrict__ vis, int nc, int nt,
 cudaError_t launch_colpass(const GridGeom &g, const float2 *vis, const float *ngrid,
                            const uint8_t *valid, const int8_t *label, const int *uext,
                            const float2 *twM, const Radices &radM, float2 *G, cudaStream_t s) {
+  // at least two CTAs per SM (shared memory below ~110 KB)
   int UB = 16;
-  while (UB > 1 && (size_t)(2 * UB * g.M + g.M + UB * g.nt) * sizeof(float2) + UB * g.nt >
-                       (size_t)200 * 1024)
-    UB /= 2;
-  const size_t smem = (size_t)(g.M + 2 * UB * g.M + g.nt * UB) * sizeof(float2) + (size_t)g.nt * UB;
+  auto bytes = [&](int ub) {
+    return (size_t)(g.M + 2 * ub * (g.M + 1) + g.nt * ub) * sizeof(float2) + (size_t)g.nt * ub;
+  };
+  while (UB > 1 && bytes(UB) > (size_t)110 * 1024) UB /= 2;
+  const size_t smem = bytes(UB);
   cudaError_t e = smem_optin_once(k_colpass);
   if (e != cudaSuccess) return e;
   dim3 grid((g.UC + UB - 1) / UB, g.nc, g.batch);

@@ -98,9 +98,10 @@ __global__ void __launch_bounds__(kSkyThreads) k_sky_lines(LineGeom g, SkyParams
                                                           Radices rad, float sign1) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = g.n, UB = g.UB;
+  const int LD = n + 1;  // padded lines: strided (line-major) accesses spread over the banks
   float2 *tw = reinterpret_cast<float2 *>(smem_raw);
   float2 *bufA = tw + n;
-  float2 *bufB = bufA + UB * n;
+  float2 *bufB = bufA + UB * LD;
   for (int t = threadIdx.x; t < n; t += blockDim.x) tw[t] = twg[t];
   const int i0 = blockIdx.x * UB;
   const int nl = min(UB, g.ni - i0);
@@ -120,7 +121,10 @@ __global__ void __launch_bounds__(kSkyThreads) k_sky_lines(LineGeom g, SkyParams
 #pragma unroll
       for (int s = 0; s < 4; ++s) {
         const unsigned long long c = 4 * q + s;
-        if (c >= c0 && c < c1) bufA[c - c0] = make_float2(av[s], bv[s]);
+        if (c >= c0 && c < c1) {
+          const int l = (int)((c - c0) / n), t = (int)(c - c0) - l * n;
+          bufA[l * LD + t] = make_float2(av[s], bv[s]);
+        }
       }
     }
   } else {
@@ -134,17 +138,17 @@ __global__ void __launch_bounds__(kSkyThreads) k_sky_lines(LineGeom g, SkyParams
         t = e / nl;
         l = e - t * nl;
       }
-      bufA[l * n + t] = data[base + (long long)l * g.istride + (long long)t * g.tstride];
+      bufA[l * LD + t] = data[base + (long long)l * g.istride + (long long)t * g.tstride];
     }
   }
   __syncthreads();
-  float2 *res = stockham(bufA, bufB, nl, n, rad, tw, sign1);
+  float2 *res = stockham(bufA, bufB, nl, n, LD, rad, tw, sign1);
   if (MID != MID_NONE) {
     float2 *oth = (res == bufA) ? bufB : bufA;
     const int tot = nl * n;
     for (int e = threadIdx.x; e < tot; e += blockDim.x) {
       const int l = e / n, t = e - l * n;
-      float2 v = res[e];
+      float2 v = res[l * LD + t];
       if (MID == MID_FILTER) {
         // offset of the element inside its pair = its box cell (kz, ky, kx)
         const long long cell =
@@ -154,10 +158,10 @@ __global__ void __launch_bounds__(kSkyThreads) k_sky_lines(LineGeom g, SkyParams
       } else {
         v = make_float2(v.x + sp.f_ng * (v.x * v.x - sp.sigma2), v.y + sp.f_ng * (v.y * v.y - sp.sigma2));
       }
-      res[e] = v;
+      res[l * LD + t] = v;
     }
     __syncthreads();
-    res = stockham(res, oth, nl, n, rad, tw, -sign1);
+    res = stockham(res, oth, nl, n, LD, rad, tw, -sign1);
   }
   const int tot = nl * n;
   for (int e = threadIdx.x; e < tot; e += blockDim.x) {
@@ -169,7 +173,7 @@ __global__ void __launch_bounds__(kSkyThreads) k_sky_lines(LineGeom g, SkyParams
       t = e / nl;
       l = e - t * nl;
     }
-    data[base + (long long)l * g.istride + (long long)t * g.tstride] = res[l * n + t];
+    data[base + (long long)l * g.istride + (long long)t * g.tstride] = res[l * LD + t];
   }
 }
 
@@ -198,9 +202,11 @@ __global__ void k_sky_separate(const float2 *__restrict__ Z, int nt, int nc, lon
   }
 }
 
+size_t sky_smem(int n, int ub) { return (size_t)8 * (n + 2 * (size_t)ub * (n + 1)); }
+
 int pick_ub(int n) {
   for (int ub = 16; ub > 1; ub >>= 1)
-    if ((size_t)8 * n * (1 + 2 * ub) <= (size_t)kSkySmemBudget) return ub;
+    if (sky_smem(n, ub) <= (size_t)kSkySmemBudget) return ub;
   return 1;
 }
 
@@ -237,7 +243,7 @@ bs_status sky_fail(bs_sky s, bs_status st, const std::string &msg) {
 template <int PRE, int MID>
 cudaError_t launch_lines(const bs_sky_s *s, const LineGeom &g, const SkyParams &sp, int npair,
                          const float2 *tw, const Radices &rad, float sign1, cudaStream_t st) {
-  const size_t smem = (size_t)8 * g.n * (1 + 2 * g.UB);
+  const size_t smem = sky_smem(g.n, g.UB);
   cudaError_t e = cudaFuncSetAttribute(k_sky_lines<PRE, MID>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
