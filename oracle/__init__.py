@@ -335,7 +335,7 @@ def delay_dft(bbar: np.ndarray, nc: int, r: float = 1.0, rprime: float = 1.0,
     sub = np.where(np.isnan(sub), 0.0, sub)
     a = np.arange(-h, -h + nc)
     ker = np.exp(-2j * np.pi * np.outer(a, n) / nc)  # [a, n]
-    out = np.einsum("an,...nm,bm->...ab", ker, sub, ker)
+    out = ker @ sub @ ker.T  # sum over n then m: [..., a, b]
     return (r * r * rprime * dnu_c) ** 2 * out
 
 
