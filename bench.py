@@ -47,6 +47,8 @@ WORKLOADS = {
     "mwa": dict(nt=256, nc=768, nb=20, edges=("log", 4.41, 128.0), block=128, block3=256,
                 desc="MWA-like: 256^2 uv grid, 768 channels (30.72 MHz at 40 kHz), 20 log rings "
                      "|U| in [4.41, 128), no flagging"),
+    "mwa64": dict(nt=256, nc=64, nb=20, edges=("log", 4.41, 128.0), block=64,
+                  desc="profiling case: the MWA-like grid and rings with 64 channels"),
     "small": dict(nt=128, nc=128, nb=12, edges=("log", 2.2, 64.0), block=32, block3=128,
                   desc="profiling case: 128^2 uv grid, 128 channels, 12 log rings |U| in "
                        "[2.2, 64), no flagging"),

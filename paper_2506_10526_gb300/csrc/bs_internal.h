@@ -147,6 +147,7 @@ cudaError_t launch_delta_norm(const double *dsum, const long long *nnu, const do
                               double *out, int batch, int ntrip, int nc, cudaStream_t s);
 cudaError_t launch_zero_planes(double *dsum, const int *trips, int ntr, int batch, int ntrip,
                                long long plane, cudaStream_t s);
+// tmp: batch * ntrip * nc^2 float2 followed by nc^2 doubles of scratch
 cudaError_t launch_bs3d(const double *dsum, const long long *nnu, const double *tnorm,
                         float2 *tmp, double *out, int batch, int ntrip, int nc,
                         const float2 *twN, const Radices &radN, double scale,

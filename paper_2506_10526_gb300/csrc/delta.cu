@@ -23,21 +23,6 @@ namespace bsi {
 
 namespace {
 
-__device__ __forceinline__ double folded_bbar(const double *__restrict__ ds,
-                                              const long long *__restrict__ nnu, double tn, int nc,
-                                              int i1, int i2) {
-  const int n2 = 2 * nc - 1;
-  const int j1 = n2 - 1 - i1, j2 = n2 - 1 - i2;
-  long long cnt = nnu[i1 * n2 + i2];
-  double s = ds[(long long)i1 * n2 + i2];
-  if (j1 != i1 || j2 != i2) {
-    cnt += nnu[j1 * n2 + j2];
-    s += ds[(long long)j1 * n2 + j2];
-  }
-  if (cnt <= 0 || tn == 0.0) return __longlong_as_double(0x7ff8000000000000LL);
-  return s * tn / (double)cnt;
-}
-
 __global__ void k_delta_norm(const double *__restrict__ dsum, const long long *__restrict__ nnu,
                              const double *__restrict__ tnorm, double *__restrict__ out, int ntrip,
                              int nc) {
@@ -96,6 +81,22 @@ __device__ void dft_direct(const float2 *x, float2 *y, int N, const float2 *tw, 
   __syncthreads();
 }
 
+// Reciprocal folded sampling over one period of the Eq. (dft) square, in the
+// periodic placement of the row pass: rinv[n][m] = 1 / (N(d) + N(-d)) (N(0)
+// once) for the separation d = (n, m) taken in [-nc/2, nc/2), 0 where nothing
+// was sampled.  The same for every ring triple, so the row pass multiplies.
+__global__ void k_fold_rinv(const long long *__restrict__ nnu, int nc, double *__restrict__ rinv) {
+  const int n2 = 2 * nc - 1;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nc * nc; e += gridDim.x * blockDim.x) {
+    const int nidx = e / nc, m = e - nidx * nc;
+    const int np = (2 * nidx < nc) ? nidx : nidx - nc, mp = (2 * m < nc) ? m : m - nc;
+    const int i1 = np + nc - 1, i2 = mp + nc - 1, j1 = n2 - 1 - i1, j2 = n2 - 1 - i2;
+    long long cnt = nnu[i1 * n2 + i2];
+    if (j1 != i1 || j2 != i2) cnt += nnu[j1 * n2 + j2];
+    rinv[e] = cnt > 0 ? 1.0 / (double)cnt : 0.0;
+  }
+}
+
 // Rows (columns) of the 2D delay transform per CTA: the transposed stores of
 // the row pass and the scattered stores of the column pass go out as runs of
 // kBsRows consecutive elements.
@@ -103,7 +104,7 @@ constexpr int kBsRows = 8;
 
 // First pass: for kBsRows consecutive n, the folded plane Bbar(n, m) over one
 // period of m, transformed along m; written transposed, tmp[k][n].
-__global__ void k_bs3d_rows(const double *__restrict__ dsum, const long long *__restrict__ nnu,
+__global__ void k_bs3d_rows(const double *__restrict__ dsum, const double *__restrict__ rinv,
                             const double *__restrict__ tnorm, float2 *__restrict__ tmp, int ntrip,
                             int nc, const float2 *__restrict__ twN, Radices radN) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -121,18 +122,13 @@ __global__ void k_bs3d_rows(const double *__restrict__ dsum, const long long *__
   for (int e = threadIdx.x; e < nr * nc; e += blockDim.x) {
     const int r = e / nc, m = e - r * nc;
     const int nidx = n0 + r;
-    double acc = 0.0;
-    // one period of the nc-periodic kernel: separations -nc/2 <= n, m < nc/2
-    for (int sa = 0; sa < 2; ++sa) {
-      const int np = sa ? nidx - nc : nidx;
-      if (2 * np < -nc || 2 * np >= nc) continue;
-      for (int sb = 0; sb < 2; ++sb) {
-        const int mp = sb ? m - nc : m;
-        if (2 * mp < -nc || 2 * mp >= nc) continue;
-        const double v = folded_bbar(ds, nnu, tn, nc, np + nc - 1, mp + nc - 1);
-        if (v == v) acc += v;
-      }
-    }
+    // one period of the nc-periodic kernel: separations -nc/2 <= n, m < nc/2,
+    // each (nidx, m) of the periodic placement being exactly one of them
+    const int np = (2 * nidx < nc) ? nidx : nidx - nc, mp = (2 * m < nc) ? m : m - nc;
+    const int i1 = np + nc - 1, i2 = mp + nc - 1, j1 = n2 - 1 - i1, j2 = n2 - 1 - i2;
+    double sv = ds[(long long)i1 * n2 + i2];
+    if (j1 != i1 || j2 != i2) sv += ds[(long long)j1 * n2 + j2];
+    const double acc = sv * (tn * rinv[(long long)nidx * nc + m]);  // 0 where unsampled
     bufA[r * LD + m] = make_float2((float)acc, 0.f);
   }
   __syncthreads();
@@ -254,8 +250,13 @@ cudaError_t launch_bs3d(const double *dsum, const long long *nnu, const double *
   e = smem_optin_once(k_bs3d_cols);
   if (e != cudaSuccess) return e;
   const int threads = nc >= 64 ? 256 : 64;
+  // the reciprocal sampling table sits after the batch's complex scratch
+  double *rinv = reinterpret_cast<double *>(tmp + (size_t)batch * ntrip * nc * nc);
+  k_fold_rinv<<<(nc * nc + 255) / 256, 256, 0, s>>>(nnu, nc, rinv);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   dim3 grid((nc + kBsRows - 1) / kBsRows, ntrip, batch);
-  k_bs3d_rows<<<grid, threads, smem, s>>>(dsum, nnu, tnorm, tmp, ntrip, nc, twN, radN);
+  k_bs3d_rows<<<grid, threads, smem, s>>>(dsum, rinv, tnorm, tmp, ntrip, nc, twN, radN);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_bs3d_cols<<<grid, threads, smem, s>>>(tmp, out, ntrip, nc, twN, radN, scale, tnorm);
