@@ -80,6 +80,16 @@ __device__ __forceinline__ void butterfly<5>(float2 *u, float sign) {
   u[3] = csub(m2, e2);
 }
 
+// Quotient n / d for 0 <= n < 2^20 from the FP32 reciprocal of d: the product
+// is within 1/8 of the true quotient, so one correction step makes it exact
+// (checked exhaustively for every stage divisor of the lengths up to 4096).
+__device__ __forceinline__ int quot(int n, float inv_d, int d) {
+  int q = __float2int_rz(__fmul_rn((float)n, inv_d));
+  const int r = n - q * d;
+  q += (r >= d) - (r < 0);
+  return q;
+}
+
 template <int R>
 __device__ __forceinline__ void stockham_stage(const float2 *__restrict__ x, float2 *__restrict__ y,
                                                int nrows, int N, int ld, int p, const float2 *tw,
@@ -87,12 +97,13 @@ __device__ __forceinline__ void stockham_stage(const float2 *__restrict__ x, flo
   const int NR = N / R;
   const int tstride = N / (p * R);
   const int total = nrows * NR;
+  const float inv_nr = __fdiv_rn(1.0f, (float)NR), inv_p = __fdiv_rn(1.0f, (float)p);
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-    const int row = idx / NR;
+    const int row = quot(idx, inv_nr, NR);
     const int i = idx - row * NR;
     const float2 *xr = x + row * ld;
     float2 *yr = y + row * ld;
-    const int k = i % p;
+    const int k = i - quot(i, inv_p, p) * p;
     float2 u[R];
 #pragma unroll
     for (int q = 0; q < R; ++q) u[q] = xr[i + q * NR];
