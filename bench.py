@@ -60,11 +60,17 @@ FP32_LANES_PER_SM = 128
 PROFILES = {"fp32": (os.path.join(ROOT, "profiles", "contract_simt_mwa.txt"),
                      os.path.join(ROOT, "paper_2506_10526_gb300", "csrc", "contract_simt.cu")),
             "split_bf16": (os.path.join(ROOT, "profiles", "contract_tc_mwa.txt"),
+                           os.path.join(ROOT, "paper_2506_10526_gb300", "csrc", "contract_tc.cu")),
+            "split_fp16": (os.path.join(ROOT, "profiles", "contract_tc_fp16_mwa.txt"),
                            os.path.join(ROOT, "paper_2506_10526_gb300", "csrc", "contract_tc.cu"))}
+# tensor-core products per algorithmic product, and the operand dtype label
+SPLIT_PRODUCTS = {"split_bf16": 3, "split_fp16": 3}
+DTYPE = {"fp32": "f32", "split_bf16": "bf16x3", "split_fp16": "fp16x3"}
 # maximum kappa-normalised error against the FP64 oracle measured by the GPU
 # parity tests (tests/test_gpu_parity.py, tests/test_gpu_fullsize.py)
 STATED_ERROR = {"fp32": "kappa-normalised error <= 1e-5 (measured 3.1e-7)",
-                "split_bf16": "kappa-normalised error <= 1e-3 (measured 1.3e-6)"}
+                "split_bf16": "kappa-normalised error <= 1e-3 (measured 1.3e-6)",
+                "split_fp16": "kappa-normalised error <= 1e-4 (measured 6.2e-7)"}
 
 
 def parse():
@@ -74,7 +80,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="mwa", choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default="split_bf16", choices=["fp32", "split_bf16"])
+    ap.add_argument("--precision", default="split_bf16",
+                    choices=["fp32", "split_bf16", "split_fp16"])
     ap.add_argument("--no-multires", action="store_true",
                     help="one image side for every ring triple (split-BF16 path)")
     ap.add_argument("--no-fp32-compare", action="store_true",
@@ -311,12 +318,12 @@ MC_GROUPS = [dict(nt=128, nchan=384, nb=12, edges=("log", 2.2, 64.0), batch=1),
              dict(nt=64, nchan=192, nb=8, edges=("linear", 0.0, 32.0), batch=2)]
 
 
-def run_mc(dev, iters=3):
+def run_mc(dev, precision, iters=3):
     import numpy as np
     import torch
     import paper_2506_10526_gb300 as bs
     specs = [dict(nt=g["nt"], nchan=g["nchan"], edges=list(edges_of(g)), batch=g["batch"],
-                  multires=True) for g in MC_GROUPS]
+                  multires=True, precision=precision) for g in MC_GROUPS]
     ens = bs.Ensemble(specs)
     gens, bufs = [], []
     for k, sp in enumerate(specs):
@@ -328,7 +335,7 @@ def run_mc(dev, iters=3):
     # channel triple, from a plan of the same shape
     flops, evals = 0.0, 0
     for sp in specs:
-        pl = bs.Plan(sp["nt"], sp["nchan"], sp["edges"], precision=bs.PREC_SPLIT_BF16, multires=True)
+        pl = bs.Plan(sp["nt"], sp["nchan"], sp["edges"], precision=precision, multires=True)
         pl.grid_load(torch.zeros((1, sp["nchan"], sp["nt"], sp["nt"]), dtype=torch.complex64,
                                  device=dev))
         tri, _ = pl.counts()
@@ -359,7 +366,8 @@ def run_mc(dev, iters=3):
     for gg in gens:
         gg.close()
     ens.close()
-    peak = float(measured_peaks().get("bf16_tflops", 1900.0)) / 3.0
+    npr = 3  # tensor products per algorithmic one (split BF16 and split FP16 alike)
+    peak = float(measured_peaks().get("bf16_tflops", 1900.0)) / npr
     nr = sum(sp["batch"] for sp in specs)
     return {"groups": [f'{g["nt"]}^2 x {g["nchan"]} ch x {g["nb"]} rings x {g["batch"]}'
                        for g in MC_GROUPS],
@@ -370,7 +378,7 @@ def run_mc(dev, iters=3):
             "note": "one graph replay per run: GPU sky generation, fields, one persistent "
                     "tensor-core launch over all groups, collapse, delay transform, Welford "
                     "statistics; frac = algorithmic contraction FLOP/s over the whole run "
-                    "against the measured BF16 burst peak / 3"}
+                    f"against the measured BF16 burst peak / {npr} ({npr} split products)"}
 
 
 def run_surrogate(dev, steps=200, rows=1 << 17):
@@ -417,7 +425,9 @@ def main():
         return
     if args.only_mc:
         import torch
-        print(json.dumps({"mc": run_mc(torch.device("cuda", 0))}), flush=True)
+        import paper_2506_10526_gb300 as bs
+        prec = bs.PREC_SPLIT_FP16 if args.precision == "split_fp16" else bs.PREC_SPLIT_BF16
+        print(json.dumps({"mc": run_mc(torch.device("cuda", 0), prec)}), flush=True)
         return
     import numpy as np
     import torch
@@ -440,9 +450,10 @@ def main():
 
     edges = edges_of(w)
     nt, nc = w["nt"], w["nc"]
-    prec = bs.PREC_FP32 if args.precision == "fp32" else bs.PREC_SPLIT_BF16
+    prec = {"fp32": bs.PREC_FP32, "split_bf16": bs.PREC_SPLIT_BF16,
+            "split_fp16": bs.PREC_SPLIT_FP16}[args.precision]
     vis = make_vis(w, seed=1000 * 2 + rank)
-    multires = args.precision == "split_bf16" and not args.no_multires
+    multires = args.precision != "fp32" and not args.no_multires
     plan = bs.Plan(nt, nc, edges, precision=prec, multires=multires)
     stream = torch.cuda.current_stream()
     vis_h = torch.from_numpy(vis[None]).pin_memory()
@@ -513,8 +524,13 @@ def main():
         roof = {"bound": "alu", "peak_source": f"FP32 FMA: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 "
                 f"flop x {sm_max:.0f} MHz"}
     else:
-        peak = float(peaks.get("bf16_tflops", 1900.0)) / 3.0
-        roof = {"bound": "tensor", "peak_source": "measured bf16 burst / 3 (three split products)"}
+        # FP16 and BF16 share the dense tensor rate (kind::f16, nominal ratio 1)
+        npr = SPLIT_PRODUCTS[args.precision]
+        peak = float(peaks.get("bf16_tflops", 1900.0)) / npr
+        roof = {"bound": "tensor",
+                "peak_source": (f"measured bf16 burst / {npr} ({npr} split products"
+                                + ("; FP16 has the BF16 dense rate)"
+                                   if args.precision == "split_fp16" else ")"))}
     b0 = jobs[0]
     achieved = flops_per_chan_triple * (b0[1] - b0[0]) * (b0[3] - b0[2]) * (b0[5] - b0[4]) / (
         avg_ms / 1e3) / 1e12
@@ -526,14 +542,14 @@ def main():
     if args.precision != "fp32" and "bf16_tflops_sustained" in peaks:
         # the contraction runs back to back for the whole timed region: the measured
         # sustained (power-capped) GEMM rate is the other fair denominator
-        sus = float(peaks["bf16_tflops_sustained"]) / 3.0
+        sus = float(peaks["bf16_tflops_sustained"]) / SPLIT_PRODUCTS[args.precision]
         roof.update({"peak_sustained": sus, "frac_sustained": achieved / sus})
 
     line = {
         "metric": "mabs_bin_triple_x_channel_evals_per_s",
         "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "bf16x3",
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision],
         "data": "synthetic",
         "config": {"workload": w["desc"], "M": M, "multires": multires,
                    "image_sides": sorted(set(int(x) for x in sides[tri > 0])),
@@ -553,10 +569,10 @@ def main():
     plan.close()
     del out_delta, out3d
     torch.cuda.empty_cache()
-    if not args.no_mc and world == 1 and args.precision == "split_bf16":
-        line["mc"] = run_mc(dev)
+    if not args.no_mc and world == 1 and args.precision != "fp32":
+        line["mc"] = run_mc(dev, prec)
         line["surrogate"] = run_surrogate(dev)
-    if args.precision == "split_bf16" and not args.no_fp32_compare and world == 1:
+    if args.precision != "fp32" and not args.no_fp32_compare and world == 1:
         # the plain FP32 GPU path on the same input, timed the same way, on 64^3 blocks
         fb = min(64, w["block"])
         fp = bs.Plan(nt, nc, edges, precision=bs.PREC_FP32)

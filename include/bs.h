@@ -54,7 +54,7 @@
 extern "C" {
 #endif
 
-#define BS_ABI_VERSION 3
+#define BS_ABI_VERSION 4
 
 typedef struct bs_plan_s *bs_plan;
 
@@ -73,9 +73,19 @@ typedef enum {
 /* Arithmetic of the triple contraction (bs_mabs). */
 enum {
     BS_PREC_FP32 = 0,       /* FP32 SIMT FMA, FP32 partial sums, FP64 across tiles */
-    BS_PREC_SPLIT_BF16 = 1  /* tcgen05 tensor cores: pair and field operands split
+    BS_PREC_SPLIT_BF16 = 1, /* tcgen05 tensor cores: pair and field operands split
                                into BF16 hi + lo, three products (hi.hi + hi.lo +
                                lo.hi) accumulated in FP32 TMEM, FP64 across tiles */
+    BS_PREC_SPLIT_FP16 = 2  /* tcgen05 tensor cores, same three products as
+                               split BF16 on FP16 hi + lo parts: each field is
+                               scaled by a power of two 2^k (k per image side, ring
+                               and realisation, from the field's largest |value|, so
+                               that |scaled field| < 2^7) and the pair product of two
+                               scaled fields stays below 2^14; the FP64 sums undo the
+                               scales exactly.  Per term the rounding error is about
+                               3 x 2^-22 of its magnitude (split BF16: 3 x 2^-17) at
+                               the same tensor-core cost; field magnitudes within
+                               2^-93 .. 2^107 keep the full precision */
 };
 
 typedef struct {
@@ -98,7 +108,8 @@ typedef struct {
                                 M > 2 max(c) (c = largest |u| or |v| in a ring): closure
                                 stays exact, the pixel sums shrink with the rings;
                                 fields are kept at each side that some triple needs.
-                                Split-BF16 only.  0: one M for all (fft_m rule). */
+                                Split-BF16 or split-FP16 only.  0: one M for all
+                                (fft_m rule). */
 } bs_plan_desc;
 
 /* ABI version this library was built with (BS_ABI_VERSION). */
@@ -210,16 +221,17 @@ bs_status bs_check_hermitian(bs_plan plan, const void *vis_dev, double tol, void
  * (uneven grid sides, channel counts and ring sets); group g processes
  * desc[g].batch realisations per run.  A run loads every group's fields,
  * contracts the full channel cube of every realisation of every group in ONE
- * persistent tensor-core launch (split BF16 only), forms the folded collapsed
+ * persistent tensor-core launch (split BF16 or split FP16), forms the folded collapsed
  * plane and Eq. (dft), and adds each realisation to per-bin Welford
  * statistics (FP64 mean and M2).  The first run executes eagerly; later runs
  * with use_graph replay a captured CUDA graph of the same launches.
  * ------------------------------------------------------------------------- */
 typedef struct bs_mc_s *bs_mc;
 
-/* Create the ensemble: one plan per group (each desc must use
- * BS_PREC_SPLIT_BF16), device input buffers, statistics.  Allocates device
- * memory.  Errors: as bs_plan_create, BS_ERR_OOM. */
+/* Create the ensemble: one plan per group (every desc must use the same
+ * tensor-core precision, BS_PREC_SPLIT_BF16 or BS_PREC_SPLIT_FP16), device
+ * input buffers, statistics.  Allocates device memory.  Errors: as
+ * bs_plan_create, BS_ERR_OOM. */
 bs_status bs_mc_create(const bs_plan_desc *group_descs, int ngroups, bs_mc *out);
 bs_status bs_mc_destroy(bs_mc mc);
 /* Message of the last failure on this ensemble; never NULL. */

@@ -26,7 +26,8 @@ STATUS = {0: "BS_OK", 1: "BS_ERR_ARG", 2: "BS_ERR_NO_DEVICE", 3: "BS_ERR_CUDA", 
           8: "BS_ERR_UNSUPPORTED"}
 PREC_FP32 = 0
 PREC_SPLIT_BF16 = 1
-ABI_VERSION = 3      # BS_ABI_VERSION of include/bs.h
+PREC_SPLIT_FP16 = 2
+ABI_VERSION = 4      # BS_ABI_VERSION of include/bs.h
 MLP_FEATURES = 45    # BS_MLP_FEATURES of include/bs.h
 
 # every symbol declared in include/bs.h
@@ -324,7 +325,8 @@ class Ensemble:
     """bs_mc_*: batched Monte Carlo over shape groups.
 
     groups: list of dicts with keys nt, nchan, edges, batch (and optionally
-    fft_m, norm_A, r, rprime, dnu_c).  All groups use the split-BF16 path."""
+    fft_m, norm_A, r, rprime, dnu_c, precision).  All groups use one tensor-core
+    precision: PREC_SPLIT_BF16 (default) or PREC_SPLIT_FP16."""
 
     def __init__(self, groups, tiles_per_sm=None):
         import torch
@@ -338,7 +340,8 @@ class Ensemble:
             arr = (ctypes.c_double * len(e))(*e)
             self._edges.append(arr)
             descs[g] = PlanDesc(spec["nt"], spec["nchan"], len(e) - 1, arr, spec.get("fft_m", 0),
-                                PREC_SPLIT_BF16, spec["batch"], spec.get("norm_A", 1.0),
+                                spec.get("precision", PREC_SPLIT_BF16), spec["batch"],
+                                spec.get("norm_A", 1.0),
                                 spec.get("r", 1.0), spec.get("rprime", 1.0), spec.get("dnu_c", 1.0),
                                 1 if spec.get("multires", False) else 0)
         h = ctypes.c_void_p()

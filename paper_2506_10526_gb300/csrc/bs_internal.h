@@ -94,6 +94,10 @@ struct TcGroup {
   long long full_bstride;
   double *dsum;
   long long dsum_bstride;
+  // split-FP16 only (null otherwise): per (realisation, slot) exponent k of the
+  // power-of-two field scale 2^k, index b * nslot + slot
+  const int *kexp;
+  int nslot;
 };
 
 struct TcArgs {
@@ -104,12 +108,14 @@ struct TcArgs {
   int *err;                // device error word: 1 = a bounded wait gave up
   long long wait_limit_ns;
   int stall_test;          // failure injection: the MMA thread waits on a barrier nobody arrives at
+  int f16;                 // 1: split-FP16 operands (two products), 0: split BF16 (three)
 };
 
 // Set a kernel's dynamic shared-memory limit to the device's opt-in maximum,
-// once per process (so that launches can be captured in CUDA graphs).
-template <class K>
-inline cudaError_t smem_optin_once(K kernel) {
+// once per process (so that launches can be captured in CUDA graphs).  The
+// kernel is a template argument: one flag per kernel, not per signature.
+template <auto kernel>
+inline cudaError_t smem_optin_once() {
   static cudaError_t done = cudaErrorNotReady;
   if (done == cudaErrorNotReady) {
     int dev = 0, mx = 0;
@@ -129,9 +135,16 @@ cudaError_t launch_colpass(const GridGeom &g, const float2 *vis, const float *ng
                            const uint8_t *valid, const int8_t *label, const int *uext,
                            const float2 *twM, const Radices &radM, float2 *G,
                            cudaStream_t s);
+// fmax (split FP16, else null): per (realisation, slot) largest |F| as float
+// bits, combined with atomicMax (zeroed by the caller)
 cudaError_t launch_rowpass(const GridGeom &g, const float2 *G, const uint8_t *valid,
                            const int *uext, const float2 *twM, const Radices &radM,
-                           float *F, uint16_t *Fhi, uint16_t *Flo, cudaStream_t s);
+                           float *F, uint16_t *Fhi, uint16_t *Flo, unsigned *fmax,
+                           cudaStream_t s);
+// Split FP16: kexp[b][slot] = power-of-two scale exponent from fmax, and the
+// FP16 hi / lo parts of every scaled field of one level.
+cudaError_t launch_split_f16(const GridGeom &g, const float *F, const unsigned *fmax, int *kexp,
+                             uint16_t *Fhi, uint16_t *Flo, cudaStream_t s);
 cudaError_t launch_effective_label(int ncell, const int8_t *label, const float *ngrid,
                                   int8_t *out, cudaStream_t s);
 cudaError_t launch_counts(int nt, int nb, const int8_t *label, const int *cells, int ncells,
@@ -152,7 +165,7 @@ cudaError_t launch_bs3d(const double *dsum, const long long *nnu, const double *
                         float2 *tmp, double *out, int batch, int ntrip, int nc,
                         const float2 *twN, const Radices &radN, double scale,
                         cudaStream_t s);
-int tc_smem_bytes();
+int tc_smem_bytes(int f16);
 cudaError_t launch_contract_tc(const TcArgs &a, int nsm, cudaStream_t s);
 cudaError_t launch_hermitian_check(const float2 *vis, int batch, int nc, int nt,
                                    const int8_t *label, float *maxdiff, float *maxabs,

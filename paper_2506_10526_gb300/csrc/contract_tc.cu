@@ -1,12 +1,19 @@
 // Triple contraction of Eq. (estimator_t) on the 5th-generation tensor cores
-// (tcgen05, sm_103a), split-BF16 precision:
+// (tcgen05, sm_103a):
 //
 //   S(l nu3; i nu1, j nu2) = sum_x F_{l,nu3}(x) * P_{nu1 nu2}(x),
 //   P(x) = F_{i,nu1}(x) F_{j,nu2}(x)      (pair product, FP32)
 //
-// Each FP32 operand is split into BF16 hi + lo (hi = round(v),
-// lo = round(v - hi)); three products hi.hi + hi.lo + lo.hi accumulate in
-// FP32 in tensor memory (the lo.lo term is below the BF16 split's own error).
+// Each FP32 operand is split into hi + lo (hi = round(v), lo = round(v - hi));
+// three products hi.hi + hi.lo + lo.hi accumulate in FP32 in tensor memory
+// (the lo.lo term is below the split's own error).  Two operand formats
+// (template parameter F16):
+//  * split BF16: 2 x 8 significant bits, FP32 range;
+//  * split FP16: 2 x 11 significant bits.  The fields arrive scaled by 2^k_l
+//    (|.| < 2^7) as FP16 hi + lo; the producers scale the pair product by
+//    2^(k_i + k_j) (|.| < 2^14) before the split.  The FP64 sums multiply by
+//    2^-(k_i + k_j + k_l), which is exact.  Per term the error is about
+//    3 x 2^-22 of its magnitude, against 3 x 2^-17 for split BF16.
 //
 // Work unit: a CTA pair (thread-block cluster of 2 on neighbouring SMs) runs
 // the two-SM MMA (tcgen05.mma.cta_group::2, M256 N256 K16) on one tile,
@@ -43,6 +50,7 @@
 // its last commit, and the pair frees TMEM after a cluster barrier.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 
@@ -70,27 +78,37 @@ constexpr int B_BYTES = 2 * PHALF * KC * 2;  // 16 KB (hi or lo): both halves
 constexpr int RAW_ROWS = 16 + P2;         // 16 rows of F_i (8 per half), 16 of F_j
 constexpr int RAW_BYTES = RAW_ROWS * KC * 4;  // 4 KB: 128-byte rows, 128B swizzle
 constexpr int RAW_BOX_BYTES = 8 * KC * 4;     // one TMA box: 8 rows
-constexpr int RED_CAP = STAGES * 2 * B_BYTES / 4;  // floats in the B buffers
-
-constexpr int OFF_A = 0;
-constexpr int OFF_B = OFF_A + ASTAGES * 2 * A_BYTES;
-constexpr int OFF_RAW = OFF_B + STAGES * 2 * B_BYTES;
-constexpr int OFF_ROW = OFF_RAW + RSTAGES * RAW_BYTES;
-constexpr int OFF_COL = OFF_ROW + MROWS * 16;  // the tile's column entries (epilogue)
-constexpr int OFF_SEG = OFF_COL + MROWS * 16;
 constexpr int MAX_SEG = 16;
-// tensor maps per level: BF16 hi/lo with boxes of 8, 32 and 128 field rows, FP32 rows
+// tensor maps per level: hi/lo with boxes of 8, 32 and 128 field rows, FP32 rows
 constexpr int NMAPS = 7;
-constexpr int OFF_BAR = OFF_SEG + MAX_SEG * 16;
 // a_full, a_empty, pfull per field stage; b_full, b_empty per pair stage; raw_full,
 // raw_empty per row stage; acc_full, acc_empty, stall
 constexpr int NBAR = 3 * ASTAGES + 2 * STAGES + 2 * RSTAGES + 3;
-constexpr int OFF_MISC = OFF_BAR + NBAR * 8;
-constexpr int SMEM_BYTES = OFF_MISC + 64 + 1024;  // + alignment slack
-static_assert(OFF_RAW % 1024 == 0 && RAW_BYTES % 1024 == 0, "128B-swizzled TMA needs 1 KB alignment");
 
-// instruction descriptor, kind::f16: D f32, A bf16, B bf16, both K-major, N = 256, M = 256
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((256u >> 3) << 17) | ((256u >> 4) << 24);
+// Shared-memory layout (the same for both operand formats) and the MMA
+// instruction descriptor.
+template <bool F16>
+struct Lay {
+  static constexpr int BP = 2;  // pair operand parts: hi, lo
+  static constexpr int RED_CAP = STAGES * BP * B_BYTES / 4;  // floats in the B buffers
+  static constexpr int OFF_A = 0;
+  static constexpr int OFF_B = OFF_A + ASTAGES * 2 * A_BYTES;
+  static constexpr int OFF_RAW = OFF_B + STAGES * BP * B_BYTES;
+  static constexpr int OFF_ROW = OFF_RAW + RSTAGES * RAW_BYTES;
+  static constexpr int OFF_COL = OFF_ROW + MROWS * 16;  // the tile's column entries (epilogue)
+  static constexpr int OFF_SEG = OFF_COL + MROWS * 16;
+  static constexpr int OFF_SSC = OFF_SEG + MAX_SEG * 16;  // per-segment FP64 unscale (FP16)
+  static constexpr int OFF_RSC = OFF_SSC + MAX_SEG * 8;   // per-row FP64 unscale (FP16)
+  static constexpr int OFF_BAR = OFF_RSC + MROWS * 8;
+  static constexpr int OFF_MISC = OFF_BAR + NBAR * 8;
+  static constexpr int SMEM_BYTES = OFF_MISC + 64 + 1024;  // + alignment slack
+  static_assert(OFF_RAW % 1024 == 0 && RAW_BYTES % 1024 == 0,
+                "128B-swizzled TMA needs 1 KB alignment");
+  // instruction descriptor, kind::f16: D f32, A and B bf16 (1) or f16 (0), both
+  // K-major, N = 256, M = 256
+  static constexpr uint32_t IDESC = (1u << 4) | ((F16 ? 0u : 1u) << 7) | ((F16 ? 0u : 1u) << 10) |
+                                    ((256u >> 3) << 17) | ((256u >> 4) << 24);
+};
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -185,11 +203,12 @@ __device__ __forceinline__ void tc_fence_before() {
 __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
+template <bool F16>
 __device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-      "l"(a), "l"(b), "r"(IDESC), "r"(acc));
+      "l"(a), "l"(b), "r"(Lay<F16>::IDESC), "r"(acc));
 }
 // Arrive (once) on the mbarrier at this shared offset in both CTAs of the pair
 // when every MMA issued so far has completed.
@@ -239,9 +258,27 @@ __device__ __forceinline__ void split2(float v0, float v1, uint32_t &hi, uint32_
   __nv_bfloat162 l = __floats2bfloat162_rn(v0 - h0, v1 - h1);
   lo = *reinterpret_cast<uint32_t *>(&l);
 }
+// FP16 hi/lo split of two FP32 values, packed (element 0 in the low half).
+__device__ __forceinline__ void split2_f16(float v0, float v1, uint32_t &hi, uint32_t &lo) {
+  const __half2 h = __floats2half2_rn(v0, v1);
+  hi = *reinterpret_cast<const uint32_t *>(&h);
+  const float2 hf = __half22float2(h);
+  const __half2 l = __floats2half2_rn(v0 - hf.x, v1 - hf.y);
+  lo = *reinterpret_cast<const uint32_t *>(&l);
+}
+// 2^k as FP32 (|k| <= 126) and as FP64 (|k| <= 1022), built from the exponent field.
+__device__ __forceinline__ float exp2i_f32(int k) { return __uint_as_float((uint32_t)(k + 127) << 23); }
+__device__ __forceinline__ double exp2i_f64(int k) {
+  return __longlong_as_double((long long)(k + 1023) << 52);
+}
 
+template <bool F16>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
     k_contract_tc(const __grid_constant__ TcArgs a) {
+  using Ly = Lay<F16>;
+  constexpr int OFF_A = Ly::OFF_A, OFF_B = Ly::OFF_B, OFF_RAW = Ly::OFF_RAW, OFF_ROW = Ly::OFF_ROW,
+                OFF_COL = Ly::OFF_COL, OFF_SEG = Ly::OFF_SEG, OFF_BAR = Ly::OFF_BAR,
+                OFF_MISC = Ly::OFF_MISC, RED_CAP = Ly::RED_CAP, BP = Ly::BP;
   extern __shared__ unsigned char smem_dyn[];
   unsigned char *sm = reinterpret_cast<unsigned char *>(
       (reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
@@ -413,18 +450,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
           }
           tc_fence_after();
           const uint32_t ah = sA + sa * 2 * A_BYTES, al = ah + A_BYTES;
-          const uint32_t bh = sB + s * 2 * B_BYTES, bl = bh + B_BYTES;
+          const uint32_t bh = sB + s * BP * B_BYTES, bl = bh + B_BYTES;
 #pragma unroll
           for (int kk = 0; kk < KC / 16; ++kk) {
             const uint64_t dah = sw64_desc(ah + kk * 32), dal = sw64_desc(al + kk * 32);
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
               const uint64_t dbh = sw64_desc(bh + h * PHALF * 64 + kk * 32);
-              const uint64_t dbl = sw64_desc(bl + h * PHALF * 64 + kk * 32);
               const uint32_t d = tmem + h * 256;
-              tc_mma(d, dah, dbh, (st == 0 && kk == 0) ? 0u : 1u);
-              tc_mma(d, dah, dbl, 1u);
-              tc_mma(d, dal, dbh, 1u);
+              tc_mma<F16>(d, dah, dbh, (st == 0 && kk == 0) ? 0u : 1u);
+              tc_mma<F16>(d, dah, sw64_desc(bl + h * PHALF * 64 + kk * 32), 1u);
+              tc_mma<F16>(d, dal, dbh, 1u);
             }
           }
           tc_commit_pair(a_empty(sa));
@@ -514,6 +550,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
     const unsigned char *rawb = sm + OFF_RAW;
     int4 *rowinfo = reinterpret_cast<int4 *>(sm + OFF_ROW);  // (C_m, E_m, trip, nu3 | -1)
     int4 *seginfo = reinterpret_cast<int4 *>(sm + OFF_SEG);  // (base, E, trip, hi)
+    double *segscale = reinterpret_cast<double *>(sm + Ly::OFF_SSC);  // 2^-(k_i+k_j+k_l)
+    double *rowscale = reinterpret_cast<double *>(sm + Ly::OFF_RSC);
     ColEntry *colbuf = reinterpret_cast<ColEntry *>(sm + OFF_COL);
     int *nseg_s = reinterpret_cast<int *>(sm + OFF_MISC + 8);
     int *total_s = reinterpret_cast<int *>(sm + OFF_MISC + 12);
@@ -535,6 +573,20 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
       const int b = t.b;
       const int cbase = t.col0 + MROWS * (int)rank;
       const int k0 = t.kseg * G.kseg_len, k1 = min(G.Kpad, k0 + G.kseg_len);
+      // split FP16: the pair product is scaled by 2^(k_i + k_j) — one factor on
+      // F_i when it is a finite FP32 power of two, else 2^k_i on F_i and 2^k_j
+      // on the product (|k| <= 100 each)
+      float sc_i = 1.f, sc_p = 1.f;
+      if constexpr (F16) {
+        const int ki = G.kexp[b * G.nslot + t.ri], kj = G.kexp[b * G.nslot + t.rj];
+        const int kij = ki + kj;
+        if (kij >= -120 && kij <= 120) {
+          sc_i = exp2i_f32(kij);
+        } else {
+          sc_i = exp2i_f32(ki);
+          sc_p = exp2i_f32(kj);
+        }
+      }
 
       for (int kc = k0; kc < k1; kc += KC, ++it, ++rit) {
         const int s = it % STAGES;
@@ -572,16 +624,33 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
           ok = false;
         }
         if (ok) {
-          unsigned char *bh = sm + OFF_B + s * 2 * B_BYTES;
+          unsigned char *bh = sm + OFF_B + s * BP * B_BYTES;
           unsigned char *bl = bh + B_BYTES;
+          if constexpr (F16) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) fi[k] *= sc_i;
+            if (sc_p != 1.f) {  // tile-uniform: only for extreme field scales
+#pragma unroll
+              for (int y = 0; y < 4; ++y)
+#pragma unroll
+                for (int k = 0; k < 8; ++k) fj[y][k] *= sc_p;
+            }
+          }
 #pragma unroll
           for (int y = 0; y < 4; ++y) {
             const int p = prow0 + bq + 4 * y;  // pair row
             uint4 H, L;
-            split2(fi[0] * fj[y][0], fi[1] * fj[y][1], H.x, L.x);
-            split2(fi[2] * fj[y][2], fi[3] * fj[y][3], H.y, L.y);
-            split2(fi[4] * fj[y][4], fi[5] * fj[y][5], H.z, L.z);
-            split2(fi[6] * fj[y][6], fi[7] * fj[y][7], H.w, L.w);
+            if constexpr (F16) {
+              split2_f16(fi[0] * fj[y][0], fi[1] * fj[y][1], H.x, L.x);
+              split2_f16(fi[2] * fj[y][2], fi[3] * fj[y][3], H.y, L.y);
+              split2_f16(fi[4] * fj[y][4], fi[5] * fj[y][5], H.z, L.z);
+              split2_f16(fi[6] * fj[y][6], fi[7] * fj[y][7], H.w, L.w);
+            } else {
+              split2(fi[0] * fj[y][0], fi[1] * fj[y][1], H.x, L.x);
+              split2(fi[2] * fj[y][2], fi[3] * fj[y][3], H.y, L.y);
+              split2(fi[4] * fj[y][4], fi[5] * fj[y][5], H.z, L.z);
+              split2(fi[6] * fj[y][6], fi[7] * fj[y][7], H.w, L.w);
+            }
             const uint32_t o = sw64_off(p, kcq);
             *reinterpret_cast<uint4 *>(bh + o) = H;
             *reinterpret_cast<uint4 *>(bl + o) = L;
@@ -627,9 +696,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
             }
           }
           const int E = (P2 - 1) + (hi - lo) + 1;
-          if (ns < MAX_SEG) seginfo[ns] = make_int4(base, E, c0.trip, hi);
+          double usc = 1.0;  // undoes the split-FP16 operand scales of this ring triple
+          if constexpr (F16)
+            usc = exp2i_f64(-(G.kexp[b * G.nslot + t.ri] + G.kexp[b * G.nslot + t.rj] +
+                              G.kexp[b * G.nslot + c0.field / G.nc]));
+          if (ns < MAX_SEG) {
+            seginfo[ns] = make_int4(base, E, c0.trip, hi);
+            segscale[ns] = usc;
+          }
           for (int r = m; r <= q; ++r) {
             const ColEntry cr = colbuf[r];
+            rowscale[r] = usc;
             if (cr.field < 0)
               rowinfo[r] = make_int4(0, 0, cr.trip, -1);
             else if (ns >= MAX_SEG)  // no reduction slot: direct atomics (total > RED_CAP)
@@ -656,11 +733,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
       const int m = 32 * quad + lane;
       const int4 ri = rowinfo[m];
       const bool row_ok = ri.w >= 0;
+      const double rsc = F16 && row_ok ? rowscale[m] : 1.0;
       // the group's fields in registers: the loop below writes memory through
       // atomics, which would otherwise make every field a reload
       const int nu1_hi = G.nu1_hi, nu2_hi = G.nu2_hi;
       const bool fast = use_red && G.out_full == nullptr;  // collapse only: shared reduction
-      const double tn = (G.out_full && row_ok) ? G.tnorm[ri.z] : 0.0;
+      const double tn = (G.out_full && row_ok) ? G.tnorm[ri.z] * rsc : 0.0;
       const int n2 = 2 * G.nc - 1;
       const int nu1_0 = t.nu1_0, nu2_0 = t.nu2_0;
       const uint32_t red_row = smem_u32(red) + 4u * (uint32_t)ri.x;
@@ -691,7 +769,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
             const long long o = (long long)b * G.dsum_bstride +
                                 ((long long)ri.z * n2 + (nu1 - ri.w + G.nc - 1)) * n2 +
                                 (nu2 - ri.w + G.nc - 1);
-            atomicAdd(G.dsum + o, (double)sv);
+            atomicAdd(G.dsum + o, (double)sv * rsc);
           }
           if (G.out_full) {
             const long long o = (long long)b * G.full_bstride +
@@ -719,7 +797,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
           const int d1 = d + d2;
           const long long o = (long long)b * G.dsum_bstride +
                               ((long long)si.z * n2 + (d1 + G.nc - 1)) * n2 + (d2 + G.nc - 1);
-          atomicAdd(G.dsum + o, (double)v);
+          atomicAdd(G.dsum + o, F16 ? (double)v * segscale[sg] : (double)v);
         }
       }
       asm volatile("bar.sync 1, 256;" ::: "memory");
@@ -732,13 +810,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
     asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }
 
-}  // namespace
-
-int tc_smem_bytes() { return SMEM_BYTES; }
-
-cudaError_t launch_contract_tc(const TcArgs &a, int nsm, cudaStream_t s) {
-  if (a.ntiles == 0) return cudaSuccess;
-  cudaError_t e = smem_optin_once(k_contract_tc);
+template <bool F16>
+cudaError_t launch_tc(const TcArgs &a, int nsm, cudaStream_t s) {
+  constexpr int SMEM = Lay<F16>::SMEM_BYTES;
+  cudaError_t e = smem_optin_once<k_contract_tc<F16>>();
   if (e != cudaSuccess) return e;
   // one CTA pair per two SMs, as many pairs as can be resident at once
   static int max_pairs = 0;
@@ -746,15 +821,24 @@ cudaError_t launch_contract_tc(const TcArgs &a, int nsm, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(2 * (nsm / 2), 1, 1);
     cfg.blockDim = dim3(NTHREADS, 1, 1);
-    cfg.dynamicSmemBytes = SMEM_BYTES;
+    cfg.dynamicSmemBytes = SMEM;
     int n = 0;
-    e = cudaOccupancyMaxActiveClusters(&n, k_contract_tc, &cfg);
+    e = cudaOccupancyMaxActiveClusters(&n, k_contract_tc<F16>, &cfg);
     if (e != cudaSuccess) return e;
     max_pairs = n > 0 ? n : 1;
   }
   const int pairs = std::max(1, std::min({a.ntiles, max_pairs, nsm / 2}));
-  k_contract_tc<<<2 * pairs, NTHREADS, SMEM_BYTES, s>>>(a);
+  k_contract_tc<F16><<<2 * pairs, NTHREADS, SMEM, s>>>(a);
   return cudaGetLastError();
+}
+
+}  // namespace
+
+int tc_smem_bytes(int f16) { return f16 ? Lay<true>::SMEM_BYTES : Lay<false>::SMEM_BYTES; }
+
+cudaError_t launch_contract_tc(const TcArgs &a, int nsm, cudaStream_t s) {
+  if (a.ntiles == 0) return cudaSuccess;
+  return a.f16 ? launch_tc<true>(a, nsm, s) : launch_tc<false>(a, nsm, s);
 }
 
 }  // namespace bsi

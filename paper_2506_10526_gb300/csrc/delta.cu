@@ -245,9 +245,9 @@ cudaError_t launch_bs3d(const double *dsum, const long long *nnu, const double *
                         double *out, int batch, int ntrip, int nc, const float2 *twN,
                         const Radices &radN, double scale, cudaStream_t s) {
   const size_t smem = (size_t)(nc + 2 * kBsRows * (nc + 1)) * sizeof(float2);
-  cudaError_t e = smem_optin_once(k_bs3d_rows);
+  cudaError_t e = smem_optin_once<k_bs3d_rows>();
   if (e != cudaSuccess) return e;
-  e = smem_optin_once(k_bs3d_cols);
+  e = smem_optin_once<k_bs3d_cols>();
   if (e != cudaSuccess) return e;
   const int threads = nc >= 64 ? 256 : 64;
   // the reciprocal sampling table sits after the batch's complex scratch

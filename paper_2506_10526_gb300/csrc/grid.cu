@@ -13,11 +13,18 @@
 //           F(x, y) = sum_{|u| < uext(m)} G(u, y) exp(+2 pi i u x / M) with
 //           G(-u, y) = conj G(u, y); two rows y, y+1 share one complex FFT
 //           (z = A + i B, F(., y) = Re z, F(., y+1) = Im z).  Output
-//           F[b][m*nc+nu][y*M + x]; in split-precision plans also the BF16
-//           hi / lo parts (hi = round(F), lo = round(F - hi)).
+//           F[b][m*nc+nu][y*M + x]; in split-BF16 plans also the BF16
+//           hi / lo parts (hi = round(F), lo = round(F - hi)); in split-FP16
+//           plans the largest |F| of each (realisation, slot) instead.
+//  split16  (split-FP16 plans) F * 2^k in FP16 hi / lo, with k per
+//           (realisation, slot) chosen from that largest |F| so that the
+//           scaled field stays below 2^7 in magnitude.
 //
 // Also: exact closed-triangle counts and the Hermitian check.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
 
 #include "bs_internal.h"
 #include "fft_smem.cuh"
@@ -109,7 +116,8 @@ __global__ void __launch_bounds__(256) k_rowpass(GridGeom g, int RPB, const floa
                                                  const int *__restrict__ uext,
                                                  const float2 *__restrict__ twM, Radices radM,
                                                  float *__restrict__ F, uint16_t *__restrict__ Fhi,
-                                                 uint16_t *__restrict__ Flo) {
+                                                 uint16_t *__restrict__ Flo,
+                                                 unsigned *__restrict__ fmax) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int M = g.M;
   const int f = blockIdx.y;  // slot * nc + nu
@@ -155,6 +163,7 @@ __global__ void __launch_bounds__(256) k_rowpass(GridGeom g, int RPB, const floa
   float2 *res = stockham(bufA, bufB, RPB, M, radM, tw, +1.0f);
   // four pixels per thread: 16-byte FP32 stores, 8-byte BF16 hi / lo stores (M % 4 == 0)
   const int M4 = M / 4;
+  unsigned amax = 0;  // largest |F| written by this thread, as float bits (order-preserving)
   for (int t = threadIdx.x; t < npair * 2 * M4; t += blockDim.x) {
     const int p = t / (2 * M4), r = t - p * 2 * M4;
     const int which = r / M4, x = 4 * (r - which * M4);
@@ -164,6 +173,7 @@ __global__ void __launch_bounds__(256) k_rowpass(GridGeom g, int RPB, const floa
                            : make_float4(z01.x, z01.z, z23.x, z23.z);
     const long long o = fbase + (long long)(y0 + 2 * p + which) * M + x;
     *reinterpret_cast<float4 *>(F + o) = v;
+    amax = max(amax, __float_as_uint(fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w)))));
     if (Fhi) {
       const uint16_t h0 = bf16_bits(v.x), h1 = bf16_bits(v.y), h2 = bf16_bits(v.z),
                      h3 = bf16_bits(v.w);
@@ -173,6 +183,66 @@ __global__ void __launch_bounds__(256) k_rowpass(GridGeom g, int RPB, const floa
           make_uint2((uint32_t)h0 | ((uint32_t)h1 << 16), (uint32_t)h2 | ((uint32_t)h3 << 16));
       *reinterpret_cast<uint2 *>(Flo + o) =
           make_uint2((uint32_t)l0 | ((uint32_t)l1 << 16), (uint32_t)l2 | ((uint32_t)l3 << 16));
+    }
+  }
+  if (fmax) {  // one atomic per CTA: warp maxima, then the block's
+    __shared__ unsigned wmax[8];
+    amax = __reduce_max_sync(0xffffffffu, amax);
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = amax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned m = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = max(m, wmax[w]);
+      if (m) atomicMax(fmax + (size_t)b * g.nslot + slot, m);
+    }
+  }
+}
+
+// Exponent k of the power-of-two scale of a field whose largest |value| has
+// float bits mb: with 2^(E-1) <= max < 2^E, k = 7 - E, so |F| 2^k < 2^7 and a
+// pair product of two scaled fields stays below 2^14 (FP16 holds 65504).  An
+// all-zero field takes k = 0; k is clamped to [-100, 100] so that 2^k and the
+// pair scale 2^(k_i + k_j) of the contraction stay finite FP32 factors.
+__device__ __forceinline__ int f16_scale_exp(unsigned mb) {
+  if (mb == 0) return 0;
+  const int be = (int)((mb >> 23) & 0xffu);
+  const int E = be == 0 ? -126 : be - 126;
+  return min(100, max(-100, 7 - E));
+}
+// 2^k as FP32, |k| <= 126
+__device__ __forceinline__ float exp2i_f32(int k) { return __uint_as_float((uint32_t)(k + 127) << 23); }
+
+__device__ __forceinline__ uint32_t f16x2_bits(float a, float b) {
+  __half2 h = __floats2half2_rn(a, b);
+  return *reinterpret_cast<uint32_t *>(&h);
+}
+
+// One CTA: 1024 float4 of one field row (F[b][slot*nc + nu][0, M^2)).
+__global__ void __launch_bounds__(256) k_split16(int nslot, int nc, int M2, int nrows,
+                                                 const float *__restrict__ F,
+                                                 const unsigned *__restrict__ fmax,
+                                                 int *__restrict__ kexp,
+                                                 uint16_t *__restrict__ Fhi,
+                                                 uint16_t *__restrict__ Flo) {
+  const int nf = nslot * nc;
+  for (int row = blockIdx.y; row < nrows; row += gridDim.y) {
+    const int b = row / nf, f = row - b * nf;
+    const int slot = f / nc;
+    const int k = f16_scale_exp(fmax[b * nslot + slot]);
+    if (blockIdx.x == 0 && f == slot * nc && threadIdx.x == 0) kexp[b * nslot + slot] = k;
+    const float sc = exp2i_f32(k);
+    const long long base = (long long)row * M2;
+    const int n4 = M2 / 4;
+    for (int q = blockIdx.x * 1024 + threadIdx.x; q < min(n4, (int)(blockIdx.x + 1) * 1024); q += 256) {
+      const float4 v = *reinterpret_cast<const float4 *>(F + base + 4 * (long long)q);
+      const float x0 = v.x * sc, x1 = v.y * sc, x2 = v.z * sc, x3 = v.w * sc;
+      const uint32_t h01 = f16x2_bits(x0, x1), h23 = f16x2_bits(x2, x3);
+      const __half2 a01 = *reinterpret_cast<const __half2 *>(&h01);
+      const __half2 a23 = *reinterpret_cast<const __half2 *>(&h23);
+      const float2 r01 = __half22float2(a01), r23 = __half22float2(a23);
+      const uint32_t l01 = f16x2_bits(x0 - r01.x, x1 - r01.y), l23 = f16x2_bits(x2 - r23.x, x3 - r23.y);
+      *reinterpret_cast<uint2 *>(Fhi + base + 4 * (long long)q) = make_uint2(h01, h23);
+      *reinterpret_cast<uint2 *>(Flo + base + 4 * (long long)q) = make_uint2(l01, l23);
     }
   }
 }
@@ -287,7 +357,7 @@ cudaError_t launch_colpass(const GridGeom &g, const float2 *vis, const float *ng
   };
   while (UB > 1 && bytes(UB) > (size_t)110 * 1024) UB /= 2;
   const size_t smem = bytes(UB);
-  cudaError_t e = smem_optin_once(k_colpass);
+  cudaError_t e = smem_optin_once<k_colpass>();
   if (e != cudaSuccess) return e;
   dim3 grid((g.UC + UB - 1) / UB, g.nc, g.batch);
   k_colpass<<<grid, 256, smem, s>>>(g, UB, vis, ngrid, valid, label, uext, twM, radM, G);
@@ -296,14 +366,24 @@ cudaError_t launch_colpass(const GridGeom &g, const float2 *vis, const float *ng
 
 cudaError_t launch_rowpass(const GridGeom &g, const float2 *G, const uint8_t *valid,
                            const int *uext, const float2 *twM, const Radices &radM, float *F,
-                           uint16_t *Fhi, uint16_t *Flo, cudaStream_t s) {
+                           uint16_t *Fhi, uint16_t *Flo, unsigned *fmax, cudaStream_t s) {
   int RPB = 8;
   while (RPB > 1 && (size_t)(2 * RPB * g.M + g.M) * sizeof(float2) > (size_t)96 * 1024) RPB /= 2;
   const size_t smem = (size_t)(2 * RPB * g.M + g.M) * sizeof(float2);
-  cudaError_t e = smem_optin_once(k_rowpass);
+  cudaError_t e = smem_optin_once<k_rowpass>();
   if (e != cudaSuccess) return e;
   dim3 grid((g.M / 2 + RPB - 1) / RPB, g.nslot * g.nc, g.batch);
-  k_rowpass<<<grid, 256, smem, s>>>(g, RPB, G, valid, uext, twM, radM, F, Fhi, Flo);
+  k_rowpass<<<grid, 256, smem, s>>>(g, RPB, G, valid, uext, twM, radM, F, Fhi, Flo, fmax);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_f16(const GridGeom &g, const float *F, const unsigned *fmax, int *kexp,
+                             uint16_t *Fhi, uint16_t *Flo, cudaStream_t s) {
+  const int M2 = g.M * g.M;  // a multiple of 4: M % 4 == 0
+  const int nrows = g.batch * g.nslot * g.nc;
+  if (nrows == 0) return cudaSuccess;
+  dim3 grid((M2 / 4 + 1023) / 1024, std::min(nrows, 65535));
+  k_split16<<<grid, 256, 0, s>>>(g.nslot, g.nc, M2, nrows, F, fmax, kexp, Fhi, Flo);
   return cudaGetLastError();
 }
 
@@ -320,7 +400,7 @@ cudaError_t launch_counts(int nt, int nb, const int8_t *label, const int *cells,
   const size_t base = (size_t)ntrip * sizeof(unsigned int) + (size_t)nb * nb * nb * sizeof(int);
   const int in_smem = base + (size_t)nt * nt <= (size_t)160 * 1024;
   const size_t smem = base + (in_smem ? (size_t)nt * nt : 0);
-  cudaError_t e = smem_optin_once(k_counts);
+  cudaError_t e = smem_optin_once<k_counts>();
   if (e != cudaSuccess) return e;
   dim3 grid((ncells + kCountP1 - 1) / kCountP1);
   k_counts<<<grid, 256, smem, s>>>(nt, nb, label, cells, ncells, trip_of, T, ntrip, in_smem);

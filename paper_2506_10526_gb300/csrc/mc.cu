@@ -83,6 +83,7 @@ struct bs_mc_s {
   unsigned char *maps = nullptr;
   int *errw = nullptr;
   int ntiles = 0, nsm = 152;
+  int f16 = 0;                  // 1: split-FP16 groups (two-product contraction)
   int min_tiles_factor = 2;     // autotuner knob: K splitting target (tiles per SM)
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -201,6 +202,7 @@ bs_status mc_enqueue(bs_mc m, cudaStream_t s) {
   a.err = m->errw;
   a.wait_limit_ns = 2000000000LL;
   a.stall_test = 0;
+  a.f16 = m->f16;
   MC_CUDA(launch_contract_tc(a, m->nsm, s));
   for (Group &gr : m->groups) {
     bs_plan p = gr.plan;
@@ -353,10 +355,13 @@ bs_status bs_mc_create(const bs_plan_desc *descs, int ngroups, bs_mc *out) {
   *out = nullptr;
   bs_mc m = new bs_mc_s();
   for (int g = 0; g < ngroups; ++g) {
-    if (descs[g].precision != BS_PREC_SPLIT_BF16) {
+    if ((descs[g].precision != BS_PREC_SPLIT_BF16 && descs[g].precision != BS_PREC_SPLIT_FP16) ||
+        descs[g].precision != descs[0].precision) {
       delete m;
-      return fail(nullptr, BS_ERR_ARG, "Monte Carlo groups use the split-BF16 tensor-core path");
+      return fail(nullptr, BS_ERR_ARG,
+                  "Monte Carlo groups share one tensor-core precision (split BF16 or split FP16)");
     }
+    m->f16 = descs[0].precision == BS_PREC_SPLIT_FP16 ? 1 : 0;
     Group gr;
     bs_status st = bs_plan_create(&descs[g], &gr.plan);
     if (st != BS_OK) {

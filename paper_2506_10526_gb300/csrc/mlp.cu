@@ -400,8 +400,8 @@ bs_status bs_mlp_create(int d_in, int width, uint64_t seed, bs_mlp *out) {
   cudaMemset(m->dev.m, 0, np * 4);
   cudaMemset(m->dev.v, 0, np * 4);
   cudaMemcpy(m->dev.norm, norm.data(), norm.size() * 4, cudaMemcpyHostToDevice);
-  if (smem_optin_once(k_mlp_forward) != cudaSuccess ||
-      smem_optin_once(k_mlp_backward_rows) != cudaSuccess) {
+  if (smem_optin_once<k_mlp_forward>() != cudaSuccess ||
+      smem_optin_once<k_mlp_backward_rows>() != cudaSuccess) {
     cudaGetLastError();
     bs_mlp_destroy(m);
     return BS_ERR_CUDA;

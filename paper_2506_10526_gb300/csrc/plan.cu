@@ -108,7 +108,8 @@ void compute_layout(bs_plan p) {
   L.ptiles = take(p->max_ptiles * sizeof(PairTile));
   L.tctiles = take(p->max_tctiles * sizeof(TcTile));
   size_t gmax = 0;
-  const bool split = p->d.precision == BS_PREC_SPLIT_BF16;
+  const bool split = p->d.precision != BS_PREC_FP32;
+  const bool f16 = p->d.precision == BS_PREC_SPLIT_FP16;
   for (Level &lv : p->levels) {
     const size_t nfl = (size_t)lv.nslot * p->nc, m2 = (size_t)lv.M * lv.M;
     gmax = std::max(gmax, (size_t)p->batch * nfl * lv.M * lv.UC * sizeof(float2));
@@ -118,6 +119,8 @@ void compute_layout(bs_plan p) {
     lv.offTw = take((size_t)lv.M * sizeof(float2));
     lv.offSlot = take((size_t)p->nb * sizeof(int));
     lv.offRing = take((size_t)std::max(1, lv.nslot) * sizeof(int));
+    lv.offFmax = take(f16 ? (size_t)p->batch * std::max(1, lv.nslot) * sizeof(unsigned) : 0);
+    lv.offKexp = take(f16 ? (size_t)p->batch * std::max(1, lv.nslot) * sizeof(int) : 0);
   }
   L.G = take(gmax);
   // level 0 doubles as the single-level layout of the FP32 path
@@ -199,8 +202,8 @@ bs_status check_device_error(bs_plan p, cudaStream_t s) {
 }
 
 // Tensor maps over the field arrays of each level: rows = batch * nf fields,
-// inner dimension = M^2 pixels.  BF16 hi / lo: boxes of 32 pixels x 8, 32 or
-// 128 fields, 64-byte swizzle (the MMA operand layout; the contraction loads
+// inner dimension = M^2 pixels.  hi / lo (BF16, or FP16 in split-FP16
+// plans): boxes of 32 pixels x 8, 32 or 128 fields, 64-byte swizzle (the MMA operand layout; the contraction loads
 // runs of consecutive fields with the larger boxes).  FP32 F: boxes of 32
 // pixels x 8 fields, 128-byte swizzle (the pair producers' input rows).
 bs_status ensure_tensor_maps(bs_plan p, cudaStream_t s) {
@@ -226,8 +229,10 @@ bs_status ensure_tensor_maps(bs_plan p, cudaStream_t s) {
       cuuint32_t box[2] = {32, rows[w]};
       void *base = f32 ? (void *)p->at<float>(lv.offF)
                        : (void *)p->at<uint16_t>(w % 2 == 0 ? lv.offFhi : lv.offFlo);
-      CUresult r = enc(&lv.maps[w],
-                       f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+      const CUtensorMapDataType half_t = p->d.precision == BS_PREC_SPLIT_FP16
+                                             ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                             : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+      CUresult r = enc(&lv.maps[w], f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : half_t, 2,
                        base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                        f32 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -246,7 +251,8 @@ bs_status ensure_tensor_maps(bs_plan p, cudaStream_t s) {
 
 bs_status enqueue_fields(bs_plan p, const void *vis, const float *ngrid, cudaStream_t s) {
   const WsLayout &L = p->L;
-  const bool split = p->d.precision == BS_PREC_SPLIT_BF16;
+  const bool bf16 = p->d.precision == BS_PREC_SPLIT_BF16;
+  const bool f16 = p->d.precision == BS_PREC_SPLIT_FP16;
   for (const Level &lv : p->levels) {
     if (lv.nslot == 0) continue;
     GridGeom g{p->nt, p->nc, p->nb, lv.M, lv.UC, p->batch, lv.nslot, p->at<int>(lv.offSlot),
@@ -254,10 +260,18 @@ bs_status enqueue_fields(bs_plan p, const void *vis, const float *ngrid, cudaStr
     BS_CUDA(launch_colpass(g, static_cast<const float2 *>(vis), ngrid, p->at<uint8_t>(L.valid),
                            p->at<int8_t>(L.label), p->at<int>(L.uext), p->at<float2>(lv.offTw),
                            lv.rad, p->at<float2>(L.G), s));
+    if (f16)
+      BS_CUDA(cudaMemsetAsync(p->at<unsigned>(lv.offFmax), 0,
+                              (size_t)p->batch * lv.nslot * sizeof(unsigned), s));
     BS_CUDA(launch_rowpass(g, p->at<float2>(L.G), p->at<uint8_t>(L.valid), p->at<int>(L.uext),
                            p->at<float2>(lv.offTw), lv.rad, p->at<float>(lv.offF),
-                           split ? p->at<uint16_t>(lv.offFhi) : nullptr,
-                           split ? p->at<uint16_t>(lv.offFlo) : nullptr, s));
+                           bf16 ? p->at<uint16_t>(lv.offFhi) : nullptr,
+                           bf16 ? p->at<uint16_t>(lv.offFlo) : nullptr,
+                           f16 ? p->at<unsigned>(lv.offFmax) : nullptr, s));
+    if (f16)
+      BS_CUDA(launch_split_f16(g, p->at<float>(lv.offF), p->at<unsigned>(lv.offFmax),
+                               p->at<int>(lv.offKexp), p->at<uint16_t>(lv.offFhi),
+                               p->at<uint16_t>(lv.offFlo), s));
   }
   return BS_OK;
 }
@@ -420,6 +434,8 @@ std::vector<TcGroup> build_tc_work(bs_plan p, const int *blk, int group_base,
     G.dsum = accumulate ? p->at<double>(p->L.dsum) : nullptr;
     G.dsum_bstride = (long long)p->ntrip * (2 * nc - 1) * (2 * nc - 1);
     G.kseg_len = G.Kpad;
+    G.kexp = p->d.precision == BS_PREC_SPLIT_FP16 ? p->at<int>(L.offKexp) : nullptr;
+    G.nslot = std::max(1, L.nslot);
   }
   if (w3 == 0 || blk[1] <= blk[0] || blk[3] <= blk[2]) return groups;
   // column lists per (level, ring pair): fields (l, nu3) of the level's slots,
@@ -506,6 +522,7 @@ bs_status mabs_tc(bs_plan p, const int *blk, double *out_full, int accumulate, c
   a.wait_limit_ns = 2000000000LL;
   const char *inj = std::getenv("BS_INJECT_MMA_STALL");
   a.stall_test = (inj && inj[0] == '1') ? 1 : 0;
+  a.f16 = p->d.precision == BS_PREC_SPLIT_FP16 ? 1 : 0;
   if (a.stall_test) a.wait_limit_ns = 50000000LL;
   BS_CUDA(launch_contract_tc(a, p->nsm, s));
   return BS_OK;
@@ -531,7 +548,8 @@ bs_status bs_plan_create(const bs_plan_desc *desc, bs_plan *out) {
   if (d.nbins < 1 || d.nbins > 32) return fail(nullptr, BS_ERR_ARG, "nbins must be in [1, 32]");
   if (!d.bin_edges) return fail(nullptr, BS_ERR_ARG, "bin_edges must not be NULL");
   if (d.batch < 1) return fail(nullptr, BS_ERR_ARG, "batch must be >= 1");
-  if (d.precision != BS_PREC_FP32 && d.precision != BS_PREC_SPLIT_BF16)
+  if (d.precision != BS_PREC_FP32 && d.precision != BS_PREC_SPLIT_BF16 &&
+      d.precision != BS_PREC_SPLIT_FP16)
     return fail(nullptr, BS_ERR_ARG, "unknown precision");
   for (int m = 0; m <= d.nbins; ++m)
     if (!std::isfinite(d.bin_edges[m]) || d.bin_edges[m] < 0 ||
@@ -659,9 +677,9 @@ bs_status bs_plan_create(const bs_plan_desc *desc, bs_plan *out) {
     rmax[m] = std::max(rmax[m], r);
   }
   p->multires = d.multires != 0;
-  if (p->multires && d.precision != BS_PREC_SPLIT_BF16) {
+  if (p->multires && d.precision == BS_PREC_FP32) {
     delete p;
-    return fail(nullptr, BS_ERR_UNSUPPORTED, "multires needs the split-BF16 tensor-core path");
+    return fail(nullptr, BS_ERR_UNSUPPORTED, "multires needs a tensor-core (split BF16 or split FP16) path");
   }
   p->lev_of_trip.assign(p->ntrip, -1);
   if (!p->multires) {
@@ -748,7 +766,7 @@ bs_status bs_plan_create(const bs_plan_desc *desc, bs_plan *out) {
   p->max_ptiles = (size_t)npairs * ((size_t)p->nb * p->nc / 128 + 1);
   // tensor-core tiles: pair rectangles (32 x 16) x 256-entry column windows (runs padded to 8)
   cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, dev);
-  if (p->d.precision == BS_PREC_SPLIT_BF16) {
+  if (p->d.precision != BS_PREC_FP32) {
     // largest block: the full cube; K splitting only happens while tiles < 2 per SM
     const size_t runs = (size_t)p->nb * (((p->nc + 7) / 8) * 8);
     const size_t full = (size_t)npairs * ((p->nc + 31) / 32) * ((p->nc + 15) / 16) * ((runs + 127) / 128);
@@ -875,13 +893,14 @@ bs_status bs_mabs(bs_plan p, const int32_t *block, double *out_full, int accumul
   for (int k = 0; k < 6; k += 2)
     if (blk[k] < 0 || blk[k + 1] > nc || blk[k] > blk[k + 1])
       return fail(p, BS_ERR_ARG, "channel block out of range");
-  if (p->d.precision != BS_PREC_FP32 && p->d.precision != BS_PREC_SPLIT_BF16)
+  if (p->d.precision != BS_PREC_FP32 && p->d.precision != BS_PREC_SPLIT_BF16 &&
+      p->d.precision != BS_PREC_SPLIT_FP16)
     return fail(p, BS_ERR_UNSUPPORTED, "precision");
   if (!out_full && !accumulate) return BS_OK;
   const WsLayout &L = p->L;
   const long long full_bstride = (long long)p->ntrip * nc * nc * nc;
   if (out_full) BS_CUDA(launch_full_fill(out_full, full_bstride, p->batch, p->ntrip, nc, blk, 0.0, s));
-  if (p->d.precision == BS_PREC_SPLIT_BF16 || p->multires) {
+  if (p->d.precision != BS_PREC_FP32 || p->multires) {
     st = mabs_tc(p, blk, out_full, accumulate, s);
     if (st != BS_OK) return st;
   } else {

@@ -29,7 +29,9 @@ struct Level {
   std::vector<int> slot_of;  // [nb], -1: no field at this level
   std::vector<int> ring_of;  // [nslot]
   size_t offF = 0, offFhi = 0, offFlo = 0, offTw = 0, offSlot = 0, offRing = 0;
-  // BF16 hi, lo with boxes of 8, 32, 128 rows, then FP32 F (host copies; device at L.maps)
+  // split FP16: per (realisation, slot) largest |F| (float bits) and scale exponent
+  size_t offFmax = 0, offKexp = 0;
+  // hi, lo (BF16 or FP16) with boxes of 8, 32, 128 rows, then FP32 F (host copies; device at L.maps)
   CUtensorMap maps[7]{};
 };
 

@@ -33,7 +33,7 @@ def test_header_declarations_exported(lib):
 
 
 def test_abi_version(lib):
-    assert lib.bs_abi_version() == bs.ABI_VERSION == 3
+    assert lib.bs_abi_version() == bs.ABI_VERSION == 4
 
 
 def test_binding_constants_match_header():
@@ -52,6 +52,10 @@ def test_desc_validation_and_no_device(lib):
     desc_edges = (ctypes.c_double * 3)(0.0, 4.0, 2.0)  # not ascending
     bad = bs.PlanDesc(16, 4, 2, desc_edges, 0, 0, 1, 1, 1, 1, 1, 0)
     assert lib.bs_plan_create(ctypes.byref(bad), ctypes.byref(h)) == 1
+    bad = bs.PlanDesc(16, 4, 2, edges, 0, 3, 1, 1, 1, 1, 1, 0)  # no precision 3
+    assert lib.bs_plan_create(ctypes.byref(bad), ctypes.byref(h)) == 1
+    assert b"precision" in lib.bs_last_error(None)
+    assert (bs.PREC_FP32, bs.PREC_SPLIT_BF16, bs.PREC_SPLIT_FP16) == (0, 1, 2)
     good = bs.PlanDesc(16, 4, 2, edges, 0, 0, 1, 1, 1, 1, 1, 0)
     st = lib.bs_plan_create(ctypes.byref(good), ctypes.byref(h))
     if not torch.cuda.is_available():

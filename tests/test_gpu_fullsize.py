@@ -35,7 +35,7 @@ def _points(T, trips):
 
 
 @pytest.mark.parametrize("precision,multires,tol", [(1, True, 1e-3), (1, False, 1e-3),
-                                                    (0, False, 1e-5)])
+                                                    (2, True, 1e-4), (0, False, 1e-5)])
 def test_mwa_block_sampled_parity(precision, multires, tol):
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():

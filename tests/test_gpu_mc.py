@@ -19,10 +19,10 @@ def _realisation(g, k):
     return synth.sky_visibilities(spec["nt"], spec["nchan"], 7000 + 100 * g + k)
 
 
-def _run_ensemble(runs, use_graph):
+def _run_ensemble(runs, use_graph, precision=1):
     import torch
     import paper_2506_10526_gb300 as bs
-    ens = bs.Ensemble(GROUPS)
+    ens = bs.Ensemble([dict(g, precision=precision) for g in GROUPS])
     bufs = [torch.empty((s["batch"], s["nchan"], s["nt"], s["nt"]), dtype=torch.complex64,
                         device="cuda") for s in GROUPS]
     for g in range(len(GROUPS)):
@@ -37,13 +37,14 @@ def _run_ensemble(runs, use_graph):
     return out
 
 
-def test_mc_statistics_match_oracle_and_graph_replay():
+@pytest.mark.parametrize("precision", [1, 2])  # split BF16, split FP16
+def test_mc_statistics_match_oracle_and_graph_replay(precision):
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     runs = 3
-    eager = _run_ensemble(runs, use_graph=False)
-    graph = _run_ensemble(runs, use_graph=True)
+    eager = _run_ensemble(runs, use_graph=False, precision=precision)
+    graph = _run_ensemble(runs, use_graph=True, precision=precision)
     for g, spec in enumerate(GROUPS):
         n = runs * spec["batch"]
         planes, b3s, abs_planes = [], [], []

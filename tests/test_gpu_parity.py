@@ -20,7 +20,11 @@ TOL_FP32 = 1e-5
 # split-BF16 tensor-core path: operands carry 16 significant bits (hi + lo),
 # products lose ~2^-16 relative; target 1e-3 kappa-normalised
 TOL_SPLIT = 1e-3
-TOL = {0: TOL_FP32, 1: TOL_SPLIT}
+# split-FP16 path (precision 2): the same three products on FP16 hi + lo parts
+# of power-of-two-scaled operands, 22 significant bits (~3 x 2^-22 per term):
+# held to 1e-4, ten times tighter than split BF16
+TOL = {0: TOL_FP32, 1: TOL_SPLIT, 2: 1e-4}
+SPLIT_CASES = [(1, False), (1, True), (2, False), (2, True)]
 
 
 def _torch():
@@ -78,7 +82,7 @@ def _oracle(vis, edges, flags=None, ngrid=None, norm_A=1.0):
     return ref, babs
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_three_mode_golden_gpu(precision):
     nt = 8
     vis = np.zeros((1, nt, nt), np.complex64)
@@ -91,7 +95,7 @@ def test_three_mode_golden_gpu(precision):
     assert abs(out["full"][0, 0, 0, 0, 0]) < 1e-6
 
 
-@pytest.mark.parametrize("precision,multires", [(0, False), (1, False), (1, True)])
+@pytest.mark.parametrize("precision,multires", [(0, False)] + SPLIT_CASES)
 @pytest.mark.parametrize("flagged", [False, True])
 def test_tiny_config_full_cube(flagged, precision, multires):
     """64^2 grid, 16 channels, 8 linear rings (and the coarse-band flags):
@@ -122,7 +126,7 @@ def test_tiny_config_full_cube(flagged, precision, multires):
     assert err3.max() < tol, err3.max()
 
 
-@pytest.mark.parametrize("precision,multires", [(0, False), (1, False), (1, True)])
+@pytest.mark.parametrize("precision,multires", [(0, False)] + SPLIT_CASES)
 def test_ragged_sizes_occupancy_and_blocks(precision, multires):
     """Non-tile-multiple sizes: nt = 40, 11 channels (non-smooth: direct DFT in
     the delay transform), log rings, empty cells with N_g in {0, 1, 2, 3},
@@ -172,7 +176,7 @@ def test_ragged_sizes_occupancy_and_blocks(precision, multires):
     plan.close()
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_batch_and_scales(precision):
     """Two realisations in one plan; A, r, r', dnu_c scale factors."""
     nt, nc = 32, 8
@@ -192,7 +196,7 @@ def test_batch_and_scales(precision):
         assert np.abs(out["bs3d"][b][keep] - b3[keep]).max() / b3_scale < tol
 
 
-@pytest.mark.parametrize("precision,multires", [(0, False), (1, False), (1, True)])
+@pytest.mark.parametrize("precision,multires", [(0, False)] + SPLIT_CASES)
 def test_degenerate_cases(precision, multires):
     """One channel (the single-frequency ABS special case), a single ring,
     an empty ring, every channel flagged, and the constant field (B = 1/A)."""
@@ -215,6 +219,26 @@ def test_degenerate_cases(precision, multires):
     f = out["full"][0]
     ok = ~np.isnan(f)
     np.testing.assert_allclose(f[ok], 0.25, rtol=1e-5 if precision == 0 else 1e-3)
+
+
+@pytest.mark.parametrize("amp", [1e-15, 1e15])
+def test_split_fp16_amplitude_range(amp):
+    """Split FP16 keeps FP16 operands in range by power-of-two field scales
+    chosen from each field's largest value: visibilities scaled by 1e-15 or
+    1e15 give B scaled by amp^3 at the same kappa-normalised error (two
+    realisations 3e3 apart in amplitude share one plan).  Log rings on a 48^2
+    grid with few closed triangles per bin: split BF16 measures 1e-4 to 2.4e-4
+    here and overflows FP32 at 1e15."""
+    nt, nc = 48, 12
+    edges = synth.edges_log(6, 1.5, 23.0)
+    v = np.stack([synth.sky_visibilities(nt, nc, seed=s) for s in (21, 22)])
+    v[1] *= 3.0e3
+    ref = [_oracle(v[b], edges) for b in range(2)]
+    out = _run(None, edges, batch_vis=(v * amp).astype(np.complex64), precision=2, multires=True)
+    for b in range(2):
+        e = _kappa_err(out["full"][b] / amp ** 3, ref[b][0]["B"].real, ref[b][1])
+        print(f"amp {amp:g} realisation {b}: max kappa-normalised error {e:.3e}")
+        assert e < TOL[2], (b, e)
 
 
 def test_hermitian_check():
