@@ -458,11 +458,18 @@ def main():
     stream = torch.cuda.current_stream()
     vis_h = torch.from_numpy(vis[None]).pin_memory()
     vis_d = vis_h.to(dev)
-    out_delta = torch.empty((1, plan.ntrip, 2 * nc - 1, 2 * nc - 1), dtype=torch.float64, device=dev)
-    out3d = torch.empty((1, plan.ntrip, nc, nc), dtype=torch.float64, device=dev)
     plan.grid_load(vis_d)
     tri, _ = plan.counts()
     nclos = int((tri > 0).sum())
+    # results of the closable ring triples only: the other planes are undefined (NaN) or
+    # zero by construction and carry no information
+    out_delta = torch.empty((1, nclos, 2 * nc - 1, 2 * nc - 1), dtype=torch.float64, device=dev)
+    out3d = torch.empty((1, nclos, nc, nc), dtype=torch.float64, device=dev)
+    nlev = plan.info()[6]  # image sides the plan keeps fields at
+    # kernels per step: column + row pass per image side (+ the FP16 split), the
+    # accumulator reset, the contraction, normalisation, the sampling table, two
+    # delay-transform passes
+    launches_per_step = (3 if args.precision == "split_fp16" else 2) * nlev + 6
     sides = plan.trip_sides()
     flops_per_chan_triple = float(np.sum(2.0 * sides[tri > 0].astype(np.float64) ** 2))
     jobs = blocks_of(nc, w["block"], w.get("block3"))
@@ -478,8 +485,8 @@ def main():
         plan.mabs(block=b, accumulate=True)
         if ev is not None:
             ev[1].record(stream)
-        plan.mabs_delta(out_delta)
-        plan.bs3d(out3d if out is None else out)
+        plan.mabs_delta_closable(out_delta)
+        plan.bs3d_closable(out3d if out is None else out)
         return block_evals(b)
 
     for i in range(args.warmup):
@@ -555,12 +562,14 @@ def main():
                    "image_sides": sorted(set(int(x) for x in sides[tri > 0])),
                    "channel_block": [w["block"], w["block"], w.get("block3") or w["block"]],
                    "closable_ring_triples": nclos, "ring_triples": plan.ntrip,
+                   "outputs": (f"folded MABS and 3D bispectrum planes of the {nclos} closable "
+                               f"ring triples (bs_mabs_delta_closable, bs_bs3d_closable)"),
                    "evals_per_step_per_gpu": per_launch_evals, "precision": args.precision,
                    "l2": (f"inputs larger than L2 ({vis_h.numel() * 8 / 1e6:.0f} MB visibilities, "
                           f"{plan.info()[3] / 1e9:.1f} GB plan workspace holding the fields)"),
                    "parallelism": f"blocks of the channel cube sharded over {world} GPU(s)"},
         "roofline": roof, "clocks": clk,
-        "gpu_launches": 6 * args.steps,
+        "gpu_launches": launches_per_step * args.steps,
         "e2e": e2e,
     }
     line["config"]["stated_error"] = STATED_ERROR[args.precision]

@@ -54,7 +54,7 @@
 extern "C" {
 #endif
 
-#define BS_ABI_VERSION 4
+#define BS_ABI_VERSION 5
 
 typedef struct bs_plan_s *bs_plan;
 
@@ -209,6 +209,18 @@ bs_status bs_mabs_delta(bs_plan plan, double *out_dev, void *cuda_stream);
  *  out_dev  double [batch][T_r][nchan][nchan], index [a + nchan/2][b + nchan/2].
  * Checks the contraction's error word like bs_mabs_delta. */
 bs_status bs_bs3d(bs_plan plan, double *out_dev, void *cuda_stream);
+
+/* The same two results for the closable ring triples only (T > 0), in
+ * ascending ring-triple index: n_c = bs_plan_info()[5] planes per realisation
+ * instead of T_r.  The other planes of bs_mabs_delta / bs_bs3d carry no
+ * information (NaN / 0), so these layouts write (and a caller copies) only
+ * the planes with data.
+ *  bs_mabs_delta_closable  out_dev double [batch][n_c][2nchan-1][2nchan-1]
+ *  bs_bs3d_closable        out_dev double [batch][n_c][nchan][nchan]
+ * Values are bit-identical to the matching planes of the full layouts.
+ * Errors: as bs_mabs_delta / bs_bs3d. */
+bs_status bs_mabs_delta_closable(bs_plan plan, double *out_dev, void *cuda_stream);
+bs_status bs_bs3d_closable(bs_plan plan, double *out_dev, void *cuda_stream);
 
 /* Check V(-U) = conj V(U) on every binned cell of every channel and
  * realisation: |V(-U) - conj V(U)| <= tol * max|V| (synchronises).

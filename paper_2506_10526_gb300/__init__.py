@@ -27,13 +27,14 @@ STATUS = {0: "BS_OK", 1: "BS_ERR_ARG", 2: "BS_ERR_NO_DEVICE", 3: "BS_ERR_CUDA", 
 PREC_FP32 = 0
 PREC_SPLIT_BF16 = 1
 PREC_SPLIT_FP16 = 2
-ABI_VERSION = 4      # BS_ABI_VERSION of include/bs.h
+ABI_VERSION = 5      # BS_ABI_VERSION of include/bs.h
 MLP_FEATURES = 45    # BS_MLP_FEATURES of include/bs.h
 
 # every symbol declared in include/bs.h
 EXPORTS = ("bs_abi_version", "bs_plan_create", "bs_plan_destroy", "bs_last_error",
            "bs_plan_info", "bs_plan_trip_sides", "bs_plan_set_workspace", "bs_grid_load", "bs_counts", "bs_mabs",
-           "bs_delta_reset", "bs_mabs_delta", "bs_bs3d", "bs_check_hermitian",
+           "bs_delta_reset", "bs_mabs_delta", "bs_bs3d", "bs_mabs_delta_closable",
+           "bs_bs3d_closable", "bs_check_hermitian",
            "bs_mc_create", "bs_mc_destroy", "bs_mc_last_error", "bs_mc_info", "bs_mc_set_input",
            "bs_mc_set_flags", "bs_mc_set_tuning", "bs_mc_autotune", "bs_mc_run", "bs_mc_reset",
            "bs_mc_stats",
@@ -239,6 +240,22 @@ class Plan:
     def bs3d(self, out, stream=None):
         """bs_bs3d: out float64 CUDA [batch, ntrip, nc, nc]."""
         self._check(self._L.bs_bs3d(self._h, _dptr(out), _stream_ptr(stream)))
+
+    @property
+    def n_closable(self):
+        """Ring triples with at least one closed triangle (bs_plan_info [5]; -1 before
+        the first grid load or count)."""
+        return self.info()[5]
+
+    def mabs_delta_closable(self, out, stream=None):
+        """bs_mabs_delta_closable: out float64 CUDA [batch, n_closable, 2nc-1, 2nc-1], the
+        closable ring triples in ascending index."""
+        self._check(self._L.bs_mabs_delta_closable(self._h, _dptr(out), _stream_ptr(stream)))
+
+    def bs3d_closable(self, out, stream=None):
+        """bs_bs3d_closable: out float64 CUDA [batch, n_closable, nc, nc], the closable ring
+        triples in ascending index."""
+        self._check(self._L.bs_bs3d_closable(self._h, _dptr(out), _stream_ptr(stream)))
 
     def mlp_features(self, chan_flags=None, stream=None):
         """bs_mlp_features: float32 CUDA tensor [ntrip*nc*nc, MLP_FEATURES] (NaN rows: no

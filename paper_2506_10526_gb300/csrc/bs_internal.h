@@ -156,15 +156,18 @@ cudaError_t launch_full_fill(double *out, long long bstride, int batch, int ntri
 cudaError_t launch_full_finalize(double *out, long long bstride, int batch, int ntrip,
                                  int nc, const int *blk, const uint8_t *valid,
                                  const double *tnorm, cudaStream_t s);
+// list (nlist entries, or null for every ring triple): ring triples to process;
+// output plane y holds list[y] (compact layout), else plane t holds triple t
 cudaError_t launch_delta_norm(const double *dsum, const long long *nnu, const double *tnorm,
-                              double *out, int batch, int ntrip, int nc, cudaStream_t s);
+                              double *out, int batch, int ntrip, int nc, const int *list,
+                              int nlist, cudaStream_t s);
 cudaError_t launch_zero_planes(double *dsum, const int *trips, int ntr, int batch, int ntrip,
                                long long plane, cudaStream_t s);
 // tmp: batch * ntrip * nc^2 float2 followed by nc^2 doubles of scratch
 cudaError_t launch_bs3d(const double *dsum, const long long *nnu, const double *tnorm,
                         float2 *tmp, double *out, int batch, int ntrip, int nc,
-                        const float2 *twN, const Radices &radN, double scale,
-                        cudaStream_t s);
+                        const float2 *twN, const Radices &radN, double scale, const int *list,
+                        int nlist, cudaStream_t s);
 int tc_smem_bytes(int f16);
 cudaError_t launch_contract_tc(const TcArgs &a, int nsm, cudaStream_t s);
 cudaError_t launch_hermitian_check(const float2 *vis, int batch, int nc, int nt,

@@ -9,6 +9,9 @@
 //   Bbar(0) = S(0) / (A M^2 T N(0))
 // is the mean of B_A over the valid triples at +-d: the fold of Fig. Nv.
 //
+// With a ring-triple list (the closable triples), grid row y handles ring
+// triple list[y] and writes output plane y: the compact layouts.
+//
 // Delay transform: the separations -nc/2 <= n, m < nc/2 (one period of the
 // nc-periodic kernel) are placed at n mod nc, then a forward 2D DFT of length
 // nc (Stockham, FP32) gives
@@ -25,12 +28,13 @@ namespace {
 
 __global__ void k_delta_norm(const double *__restrict__ dsum, const long long *__restrict__ nnu,
                              const double *__restrict__ tnorm, double *__restrict__ out, int ntrip,
-                             int nc) {
+                             int nc, const int *__restrict__ list) {
   const int n2 = 2 * nc - 1;
   const long long plane = (long long)n2 * n2;
-  const int trip = blockIdx.y, b = blockIdx.z;
+  const int trip = list ? list[blockIdx.y] : blockIdx.y, b = blockIdx.z;
+  const int nout = list ? gridDim.y : ntrip;
   const double *ds = dsum + ((long long)b * ntrip + trip) * plane;
-  double *o = out + ((long long)b * ntrip + trip) * plane;
+  double *o = out + ((long long)b * nout + blockIdx.y) * plane;
   const double tn = tnorm[trip];
   const double nan = __longlong_as_double(0x7ff8000000000000LL);
   if (tn == 0.0) {  // no closed triangle: undefined everywhere, nothing to read
@@ -106,13 +110,14 @@ constexpr int kBsRows = 8;
 // period of m, transformed along m; written transposed, tmp[k][n].
 __global__ void k_bs3d_rows(const double *__restrict__ dsum, const double *__restrict__ rinv,
                             const double *__restrict__ tnorm, float2 *__restrict__ tmp, int ntrip,
-                            int nc, const float2 *__restrict__ twN, Radices radN) {
+                            int nc, const float2 *__restrict__ twN, Radices radN,
+                            const int *__restrict__ list) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int LD = nc + 1;  // padded rows: the transposed reads spread over the banks
   float2 *tw = reinterpret_cast<float2 *>(smem_raw);
   float2 *bufA = tw + nc;
   float2 *bufB = bufA + kBsRows * LD;
-  const int n0 = blockIdx.x * kBsRows, trip = blockIdx.y, b = blockIdx.z;
+  const int n0 = blockIdx.x * kBsRows, trip = list ? list[blockIdx.y] : blockIdx.y, b = blockIdx.z;
   const int nr = min(kBsRows, nc - n0);
   const int n2 = 2 * nc - 1;
   const double *ds = dsum + ((long long)b * ntrip + trip) * (long long)n2 * n2;
@@ -150,16 +155,17 @@ __global__ void k_bs3d_rows(const double *__restrict__ dsum, const double *__res
 // n; out[a + nc/2][b + nc/2] = scale * Re.
 __global__ void k_bs3d_cols(const float2 *__restrict__ tmp, double *__restrict__ out, int ntrip,
                             int nc, const float2 *__restrict__ twN, Radices radN, double scale,
-                            const double *__restrict__ tnorm) {
+                            const double *__restrict__ tnorm, const int *__restrict__ list) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int LD = nc + 1;
   float2 *tw = reinterpret_cast<float2 *>(smem_raw);
   float2 *bufA = tw + nc;
   float2 *bufB = bufA + kBsRows * LD;
-  const int bb0 = blockIdx.x * kBsRows, trip = blockIdx.y, b = blockIdx.z;
+  const int bb0 = blockIdx.x * kBsRows, trip = list ? list[blockIdx.y] : blockIdx.y, b = blockIdx.z;
   const int nr = min(kBsRows, nc - bb0);
   const int h = nc / 2;
-  double *ob = out + ((long long)b * ntrip + trip) * (long long)nc * nc;
+  const int nout = list ? gridDim.y : ntrip;
+  double *ob = out + ((long long)b * nout + blockIdx.y) * (long long)nc * nc;
   auto centred = [&](int k) { return (k < nc - h) ? k + h : k - nc + h; };
   if (tnorm[trip] == 0.0) {
     for (int e = threadIdx.x; e < nr * nc; e += blockDim.x) {
@@ -226,10 +232,13 @@ __global__ void k_full_finalize(double *__restrict__ out, long long bstride, int
 }  // namespace
 
 cudaError_t launch_delta_norm(const double *dsum, const long long *nnu, const double *tnorm,
-                              double *out, int batch, int ntrip, int nc, cudaStream_t s) {
+                              double *out, int batch, int ntrip, int nc, const int *list,
+                              int nlist, cudaStream_t s) {
   const long long plane = (long long)(2 * nc - 1) * (2 * nc - 1);
-  dim3 grid((unsigned)std::min<long long>((plane + 255) / 256, 1024), ntrip, batch);
-  k_delta_norm<<<grid, 256, 0, s>>>(dsum, nnu, tnorm, out, ntrip, nc);
+  const int ny = list ? nlist : ntrip;
+  if (ny == 0) return cudaSuccess;
+  dim3 grid((unsigned)std::min<long long>((plane + 255) / 256, 1024), ny, batch);
+  k_delta_norm<<<grid, 256, 0, s>>>(dsum, nnu, tnorm, out, ntrip, nc, list);
   return cudaGetLastError();
 }
 
@@ -243,7 +252,8 @@ cudaError_t launch_zero_planes(double *dsum, const int *trips, int ntr, int batc
 
 cudaError_t launch_bs3d(const double *dsum, const long long *nnu, const double *tnorm, float2 *tmp,
                         double *out, int batch, int ntrip, int nc, const float2 *twN,
-                        const Radices &radN, double scale, cudaStream_t s) {
+                        const Radices &radN, double scale, const int *list, int nlist,
+                        cudaStream_t s) {
   const size_t smem = (size_t)(nc + 2 * kBsRows * (nc + 1)) * sizeof(float2);
   cudaError_t e = smem_optin_once<k_bs3d_rows>();
   if (e != cudaSuccess) return e;
@@ -255,11 +265,13 @@ cudaError_t launch_bs3d(const double *dsum, const long long *nnu, const double *
   k_fold_rinv<<<(nc * nc + 255) / 256, 256, 0, s>>>(nnu, nc, rinv);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  dim3 grid((nc + kBsRows - 1) / kBsRows, ntrip, batch);
-  k_bs3d_rows<<<grid, threads, smem, s>>>(dsum, rinv, tnorm, tmp, ntrip, nc, twN, radN);
+  const int ny = list ? nlist : ntrip;
+  if (ny == 0) return cudaSuccess;
+  dim3 grid((nc + kBsRows - 1) / kBsRows, ny, batch);
+  k_bs3d_rows<<<grid, threads, smem, s>>>(dsum, rinv, tnorm, tmp, ntrip, nc, twN, radN, list);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_bs3d_cols<<<grid, threads, smem, s>>>(tmp, out, ntrip, nc, twN, radN, scale, tnorm);
+  k_bs3d_cols<<<grid, threads, smem, s>>>(tmp, out, ntrip, nc, twN, radN, scale, tnorm, list);
   return cudaGetLastError();
 }
 

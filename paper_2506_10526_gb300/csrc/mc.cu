@@ -208,10 +208,11 @@ bs_status mc_enqueue(bs_mc m, cudaStream_t s) {
     bs_plan p = gr.plan;
     const WsLayout &L = p->L;
     MC_CUDA(launch_delta_norm(p->at<double>(L.dsum), p->at<long long>(L.nnu),
-                              p->at<double>(L.tnorm), gr.dout, p->batch, p->ntrip, p->nc, s));
+                              p->at<double>(L.tnorm), gr.dout, p->batch, p->ntrip, p->nc,
+                              nullptr, 0, s));
     MC_CUDA(launch_bs3d(p->at<double>(L.dsum), p->at<long long>(L.nnu), p->at<double>(L.tnorm),
                         p->at<float2>(L.tmp3d), gr.bout, p->batch, p->ntrip, p->nc,
-                        p->at<float2>(L.twN), p->radN, p->scale3d, s));
+                        p->at<float2>(L.twN), p->radN, p->scale3d, nullptr, 0, s));
     const int blocks = (int)std::min<long long>((gr.nd + 255) / 256, 4096);
     k_welford<<<blocks, 256, 0, s>>>(gr.dout, p->batch, gr.nd, gr.stats, gr.stats + gr.nd,
                                      gr.stats + 2 * gr.nd);

@@ -138,6 +138,7 @@ void compute_layout(bs_plan p) {
   L.tcgroup = take(p->levels.size() * sizeof(TcGroup));
   L.mlptab = take(((size_t)p->ntrip * 4 + 36) * sizeof(float));
   L.ztrips = take((size_t)p->ntrip * sizeof(int));
+  L.clos = take((size_t)p->ntrip * sizeof(int));
   L.total = o;
 }
 
@@ -308,6 +309,12 @@ bs_status run_counts(bs_plan p, const int8_t *lab_dev, cudaStream_t s) {
   }
   BS_CUDA(cudaMemcpyAsync(p->at<double>(p->L.tnorm), p->tnorm.data(), p->ntrip * sizeof(double),
                           cudaMemcpyHostToDevice, s));
+  p->clos.clear();
+  for (int t = 0; t < p->ntrip; ++t)
+    if (p->T[t] > 0) p->clos.push_back(t);
+  if (!p->clos.empty())
+    BS_CUDA(cudaMemcpyAsync(p->at<int>(p->L.clos), p->clos.data(), p->clos.size() * sizeof(int),
+                            cudaMemcpyHostToDevice, s));
   BS_CUDA(cudaStreamSynchronize(s));
   p->counts_ready = true;
   p->dsum_clean = false;
@@ -983,7 +990,24 @@ bs_status bs_mabs_delta(bs_plan p, double *out, void *stream) {
   st = upload_nnu(p, s);
   if (st != BS_OK) return st;
   BS_CUDA(launch_delta_norm(p->at<double>(p->L.dsum), p->at<long long>(p->L.nnu),
-                            p->at<double>(p->L.tnorm), out, p->batch, p->ntrip, p->nc, s));
+                            p->at<double>(p->L.tnorm), out, p->batch, p->ntrip, p->nc, nullptr, 0,
+                            s));
+  return BS_OK;
+}
+
+bs_status bs_mabs_delta_closable(bs_plan p, double *out, void *stream) {
+  if (!p || !out) return fail(p, BS_ERR_ARG, "out_dev must not be NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!p->loaded) return fail(p, BS_ERR_STATE, "bs_mabs_delta_closable before bs_grid_load");
+  bs_status st = prepare(p, s);
+  if (st != BS_OK) return st;
+  st = check_device_error(p, s);
+  if (st != BS_OK) return st;
+  st = upload_nnu(p, s);
+  if (st != BS_OK) return st;
+  BS_CUDA(launch_delta_norm(p->at<double>(p->L.dsum), p->at<long long>(p->L.nnu),
+                            p->at<double>(p->L.tnorm), out, p->batch, p->ntrip, p->nc,
+                            p->at<int>(p->L.clos), (int)p->clos.size(), s));
   return BS_OK;
 }
 
@@ -999,7 +1023,25 @@ bs_status bs_bs3d(bs_plan p, double *out, void *stream) {
   if (st != BS_OK) return st;
   BS_CUDA(launch_bs3d(p->at<double>(p->L.dsum), p->at<long long>(p->L.nnu),
                       p->at<double>(p->L.tnorm), p->at<float2>(p->L.tmp3d), out, p->batch,
-                      p->ntrip, p->nc, p->at<float2>(p->L.twN), p->radN, p->scale3d, s));
+                      p->ntrip, p->nc, p->at<float2>(p->L.twN), p->radN, p->scale3d, nullptr, 0,
+                      s));
+  return BS_OK;
+}
+
+bs_status bs_bs3d_closable(bs_plan p, double *out, void *stream) {
+  if (!p || !out) return fail(p, BS_ERR_ARG, "out_dev must not be NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!p->loaded) return fail(p, BS_ERR_STATE, "bs_bs3d_closable before bs_grid_load");
+  bs_status st = prepare(p, s);
+  if (st != BS_OK) return st;
+  st = check_device_error(p, s);
+  if (st != BS_OK) return st;
+  st = upload_nnu(p, s);
+  if (st != BS_OK) return st;
+  BS_CUDA(launch_bs3d(p->at<double>(p->L.dsum), p->at<long long>(p->L.nnu),
+                      p->at<double>(p->L.tnorm), p->at<float2>(p->L.tmp3d), out, p->batch,
+                      p->ntrip, p->nc, p->at<float2>(p->L.twN), p->radN, p->scale3d,
+                      p->at<int>(p->L.clos), (int)p->clos.size(), s));
   return BS_OK;
 }
 

@@ -241,6 +241,40 @@ def test_split_fp16_amplitude_range(amp):
         assert e < TOL[2], (b, e)
 
 
+@pytest.mark.parametrize("precision,multires", [(1, True), (0, False)])
+def test_closable_layouts_match_full(precision, multires):
+    """bs_mabs_delta_closable / bs_bs3d_closable hold exactly the planes of the
+    full layouts whose ring triple has closed triangles, in ascending order,
+    bit for bit; two realisations, one flagged channel."""
+    torch = _torch()
+    import paper_2506_10526_gb300 as bs
+    nt, nc = 40, 11
+    edges = synth.edges_log(5, 1.5, 19.0)
+    v = np.stack([synth.sky_visibilities(nt, nc, seed=s) for s in (61, 62)])
+    flags = np.zeros(nc, np.uint8)
+    flags[3] = 1
+    plan = bs.Plan(nt, nc, edges, precision=precision, batch=2, multires=multires)
+    plan.grid_load(torch.from_numpy(v).cuda(), chan_flags=flags)
+    plan.mabs(accumulate=True)
+    tri, _ = plan.counts()
+    clos = np.flatnonzero(tri > 0)
+    assert plan.n_closable == clos.size and 0 < clos.size < plan.ntrip
+    n2 = 2 * nc - 1
+    dd = torch.empty((2, plan.ntrip, n2, n2), dtype=torch.float64, device="cuda")
+    dc = torch.full((2, clos.size, n2, n2), 7.0, dtype=torch.float64, device="cuda")
+    bd = torch.empty((2, plan.ntrip, nc, nc), dtype=torch.float64, device="cuda")
+    bc = torch.full((2, clos.size, nc, nc), 7.0, dtype=torch.float64, device="cuda")
+    plan.mabs_delta(dd)
+    plan.mabs_delta_closable(dc)
+    plan.bs3d(bd)
+    plan.bs3d_closable(bc)
+    torch.cuda.synchronize()
+    idx = torch.from_numpy(clos).cuda()
+    np.testing.assert_array_equal(dc.cpu().numpy(), dd.index_select(1, idx).cpu().numpy())
+    np.testing.assert_array_equal(bc.cpu().numpy(), bd.index_select(1, idx).cpu().numpy())
+    plan.close()
+
+
 def test_hermitian_check():
     torch = _torch()
     import paper_2506_10526_gb300 as bs
