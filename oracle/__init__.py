@@ -30,6 +30,10 @@ reordering beyond what the definition states:
 * ``analytic_mabs``    exact ensemble mean of the estimator for the Eq. (mb1)
                        test field on a periodic box (first-order term of
                        Eq. bsana plus the f_NG^3 loop term).
+* ``monopole``         (module) the 3D bispectrum monopole binned in triangle
+                       size and shape: Eq. (shape), Eq. (bs_lm) at l = m = 0
+                       and the (k1, mu, t) binning of Section 5, for
+                       estimated values or for Eq. (bsana).
 
 Pins (tests/test_oracle_pins.py) tie every function to something other than
 itself: brute force, hand-worked cases, closed forms, invariants and the

@@ -1,0 +1,137 @@
+"""Pins of the monopole binning oracle (oracle/monopole.py) to the paper's
+statements and to independent routes: the corners and edges of the (mu, t)
+plane named in Section 5, explicit 3D vectors for Eq. (shape), a pure-Python
+binning by linear search, the closed form of Eq. (bsana) for equilateral
+triangles, and ring centres of hand-counted rings."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import monopole as mo
+
+
+def _shape(k1, k2, k3):
+    K1, mu, t = mo.triangle_shape(k1 * k1, k2 * k2, k3 * k3)
+    return float(K1), float(mu), float(t)
+
+
+def test_shape_corners_named_in_the_paper():
+    # equilateral: upper-left corner of the (mu, t) plane
+    assert _shape(1.0, 1.0, 1.0) == pytest.approx((1.0, 0.5, 1.0), abs=1e-15)
+    # squeezed (k1 = k2, k3 -> 0): upper-right corner
+    K1, mu, t = _shape(1.0, 1.0, 1e-7)
+    assert (mu, t) == pytest.approx((1.0, 1.0), abs=1e-12)
+    # stretched (k1 / 2 = k2 = k3): lower-right corner
+    assert _shape(2.0, 1.0, 1.0)[1:] == pytest.approx((1.0, 0.5), abs=1e-15)
+    # linear (collinear, k1 = k2 + k3): right boundary mu = 1
+    assert _shape(1.0, 0.7, 0.3)[1] == pytest.approx(1.0, abs=1e-15)
+    # L-isosceles (two larger sides equal): upper boundary t = 1
+    assert _shape(1.0, 1.0, 0.6)[2] == 1.0
+    # S-isosceles (two smaller sides equal): lower boundary 2 mu t = 1
+    _, mu, t = _shape(1.0, 0.8, 0.8)
+    assert 2 * mu * t == pytest.approx(1.0, abs=1e-15)
+    # argument order does not matter
+    assert _shape(0.6, 1.0, 0.9) == _shape(1.0, 0.9, 0.6)
+
+
+def test_shape_against_explicit_vectors():
+    """mu = -k1.k2 / (k1 k2) from explicit 3D vectors (two random vectors, the
+    third closing the triangle) against the squared-length form."""
+    r = np.random.default_rng(5)
+    for _ in range(2000):
+        a, b = r.normal(size=3), r.normal(size=3) * r.uniform(0.1, 3.0)
+        vecs = sorted([a, b, -(a + b)], key=lambda v: -np.dot(v, v))
+        k1, k2 = vecs[0], vecs[1]
+        mu_v = -np.dot(k1, k2) / (np.linalg.norm(k1) * np.linalg.norm(k2))
+        t_v = np.linalg.norm(k2) / np.linalg.norm(k1)
+        K1, mu, t = mo.triangle_shape(*(np.dot(v, v) for v in (a, b, -(a + b))))
+        assert mu == pytest.approx(mu_v, abs=1e-12)
+        assert t == pytest.approx(t_v, abs=1e-13)
+        assert K1 == pytest.approx(np.linalg.norm(k1), rel=1e-15)
+        # the parameter range stated after Eq. (shape)
+        assert 0.5 - 1e-12 <= mu <= 1 + 1e-12 and 0.5 - 1e-12 <= t <= 1
+        assert 2 * mu * t >= 1 - 1e-12
+
+
+def _brute_monopole(b3d, trips, kperp, kpar, k1_edges, n_mu, n_t):
+    """Per-sample loops, bins found by linear search over their edges."""
+    n_k1 = len(k1_edges) - 1
+    batch, _, nc, _ = b3d.shape
+    sums = np.zeros((batch, n_k1, n_mu, n_t))
+    cnt = np.zeros((n_k1, n_mu, n_t), np.int64)
+    mu_e = [0.5 + 0.5 * q / n_mu for q in range(n_mu + 1)]
+    t_e = [0.5 + 0.5 * q / n_t for q in range(n_t + 1)]
+    for p, (i, j, l) in enumerate(trips):
+        for ia in range(nc):
+            for ib in range(nc):
+                za, zb = kpar[ia], kpar[ib]
+                sides = [math.sqrt(kperp[i] ** 2 + za ** 2), math.sqrt(kperp[j] ** 2 + zb ** 2),
+                         math.sqrt(kperp[l] ** 2 + (za + zb) ** 2)]
+                sides.sort(reverse=True)
+                k1, k2, k3 = sides
+                mu = (k1 * k1 + k2 * k2 - k3 * k3) / (2 * k1 * k2)
+                t = k2 / k1
+                if not (0.5 - 1e-9 <= mu <= 1 + 1e-9 and 0.5 - 1e-9 <= t <= 1 + 1e-9):
+                    continue
+                mu, t = min(max(mu, 0.5), 1.0), min(max(t, 0.5), 1.0)
+                qk = next((q for q in range(n_k1) if k1_edges[q] <= k1 < k1_edges[q + 1]), None)
+                if qk is None:
+                    continue
+                qm = next(q for q in range(n_mu) if mu < mu_e[q + 1] or q == n_mu - 1)
+                qt = next(q for q in range(n_t) if t < t_e[q + 1] or q == n_t - 1)
+                cnt[qk, qm, qt] += 1
+                sums[:, qk, qm, qt] += b3d[:, p, ia, ib]
+    return sums, cnt
+
+
+def test_monopole_binning_against_brute_force():
+    r = np.random.default_rng(11)
+    nb, nc = 4, 10
+    kperp = np.sort(r.uniform(0.05, 0.3, nb))
+    trips = [(0, 0, 0), (0, 1, 1), (0, 1, 2), (1, 2, 3), (2, 3, 3), (3, 3, 3)]
+    kpar = mo.kpar_axis(nc, rprime=30.0, dnu_c=0.05)
+    b3d = r.normal(size=(2, len(trips), nc, nc))
+    edges = np.geomspace(0.04, 2.5, 7)
+    s, c = mo.bs_monopole(b3d, trips, kperp, kpar, edges, 5, 5)
+    s_b, c_b = _brute_monopole(b3d, trips, kperp, kpar, edges, 5, 5)
+    np.testing.assert_array_equal(c, c_b)
+    np.testing.assert_allclose(s, s_b, rtol=1e-12, atol=1e-12)
+    assert 0 < c.sum() <= len(trips) * nc * nc
+
+
+def test_bsana_closed_form_and_equilateral_bin():
+    """Eq. (bsana) with P = k^-2 on an equilateral triangle is 6 f k^-4; a
+    single equilateral sample (nc = 1: a = b = 0) lands in the first mu bin
+    and the last t bin of the k1 bin holding k."""
+    kap, f = 0.2, 0.7
+    assert mo.bsana(kap ** 2, kap ** 2, kap ** 2, f, 1.0, -2.0) == pytest.approx(6 * f * kap ** -4,
+                                                                              rel=1e-14)
+    v = mo.bsana(0.3, 0.5, 0.7, f, 2.0, -2.0)
+    assert v == pytest.approx(mo.bsana(0.7, 0.3, 0.5, f, 2.0, -2.0), rel=1e-15)
+    edges = np.array([0.1, 0.15, 0.25, 0.4])
+    s, c = mo.bs_monopole(None, [(0, 0, 0)], np.array([kap]), np.array([0.0]), edges, 5, 5,
+                          model=(f, 1.0, -2.0))
+    assert c.sum() == 1 and c[1, 0, 4] == 1
+    assert s[0, 1, 0, 4] == pytest.approx(6 * f * kap ** -4, rel=1e-14)
+
+
+def test_ring_mean_u_hand_counted_rings():
+    nt = 16
+    # [1, 1.2): the four cells at |U| = 1;  [1.4, 1.5): four at sqrt 2;
+    # [1.9, 2.1): four at 2;  [2.2, 2.3): the eight at sqrt 5
+    u = mo.ring_mean_u(nt, [1.0, 1.2, 1.4, 1.5, 1.9, 2.1, 2.2, 2.3])
+    assert u[0] == 1.0
+    assert u[2] == pytest.approx(math.sqrt(2), rel=1e-15)
+    assert u[4] == 2.0
+    assert u[6] == pytest.approx(math.sqrt(5), rel=1e-15)
+    # empty ring: the mid point of its edges
+    assert u[1] == pytest.approx(1.3) and u[3] == pytest.approx(1.7)
+    # a ring with both |U| = 1 and sqrt 2 cells
+    assert mo.ring_mean_u(nt, [1.0, 1.5])[0] == pytest.approx((1 + math.sqrt(2)) / 2, rel=1e-15)
+
+
+def test_kpar_axis():
+    k = mo.kpar_axis(8, rprime=2.0, dnu_c=0.5)
+    assert k[4] == 0.0 and k[0] == pytest.approx(-4 * 2 * np.pi / (2.0 * 8 * 0.5))
+    np.testing.assert_allclose(np.diff(k), 2 * np.pi / 8.0)
