@@ -31,31 +31,38 @@ Readings (the paper leaves them open):
   the Eq. (dft) output, a -> ring i (nu1), b -> ring j (nu2), the third
   component -a-b -> ring l.  The bin value is the unweighted mean.
 * U_m of a ring is the mean |U| over its grid cells (grid units).
-* Binning arithmetic (the same operations on the GPU, so that bin indices
-  agree bit for bit): S_n = kperp_n^2 + kpar_n^2 in FP64, sorted
+* Binning arithmetic: the bin of a sample is decided in FP32, every
+  operation rounded once (IEEE), in this order, which the GPU repeats so
+  that bin indices agree bit for bit.  kperp and kpar are rounded to FP32;
+  kpar_3 = -(kpar_1 + kpar_2); S_n = kperp_n^2 + kpar_n^2, sorted
   S1 >= S2 >= S3; K_n = sqrt(S_n); t = K2 / K1;
-  mu = ((S1 + S2) - S3) / (2 (K1 K2)).  mu and t within 1e-9 of [0.5, 1]
+  mu = ((S1 + S2) - S3) / (2 (K1 K2)).  mu and t within 1e-6 of [0.5, 1]
   are clamped into it, samples further out (side lengths from ring means
-  need not close) are dropped.  k1 bin q: e_q <= K1 < e_{q+1}.  mu bin:
-  floor((mu - 0.5) * (2 n_mu)), the value 1 in the last bin; t alike.
+  need not close) are dropped.  k1 bin q: e_q <= K1 < e_{q+1} (K1 widened
+  to FP64, edges in FP64).  mu bin: floor((mu - 0.5) * (2 n_mu)) in FP32,
+  the value 1 in the last bin; t alike.  Values and sums are FP64; the
+  model of Eq. (bsana) takes the FP32 squared lengths widened to FP64.
 """
 from __future__ import annotations
 
 import numpy as np
 
-SHAPE_TOL = 1e-9
+SHAPE_TOL = 1e-6
+F32 = np.float32
 
 
 def triangle_shape(s1, s2, s3):
     """(k1, mu, t) of Eq. (shape) from the squared side lengths of a closed
-    triangle (any order; arrays broadcast)."""
-    s = np.sort(np.stack(np.broadcast_arrays(np.asarray(s1, np.float64),
-                                             np.asarray(s2, np.float64),
-                                             np.asarray(s3, np.float64))), axis=0)[::-1]
+    triangle (any order; arrays broadcast), computed in the inputs' floating
+    type (FP64 for Python floats)."""
+    arrs = np.broadcast_arrays(*(np.asarray(x) if isinstance(x, np.ndarray) and x.dtype == F32
+                                 else np.asarray(x, np.float64) for x in (s1, s2, s3)))
+    s = np.sort(np.stack(arrs), axis=0)[::-1]
     S1, S2, S3 = s[0], s[1], s[2]
     K1, K2 = np.sqrt(S1), np.sqrt(S2)
     t = K2 / K1
-    mu = ((S1 + S2) - S3) / (2.0 * (K1 * K2))
+    two = S1.dtype.type(2.0)
+    mu = ((S1 + S2) - S3) / (two * (K1 * K2))
     return K1, mu, t
 
 
@@ -88,16 +95,17 @@ def bsana(S1, S2, S3, f_ng: float, p_amp: float, p_index: float):
 
 
 def _bins(K1, mu, t, k1_edges, n_mu, n_t):
-    """Flat bin index (k1, mu, t) of each sample, -1 where it falls outside."""
+    """Flat bin index (k1, mu, t) of each FP32 sample, -1 where it falls outside."""
     e = np.asarray(k1_edges, np.float64)
-    qk = np.searchsorted(e, K1, side="right") - 1
+    qk = np.searchsorted(e, K1.astype(np.float64), side="right") - 1
     ok = (qk >= 0) & (qk < e.size - 1)
-    ok &= (mu >= 0.5 - SHAPE_TOL) & (mu <= 1.0 + SHAPE_TOL)
-    ok &= (t >= 0.5 - SHAPE_TOL) & (t <= 1.0 + SHAPE_TOL)
-    muc = np.clip(mu, 0.5, 1.0)
-    tc = np.clip(t, 0.5, 1.0)
-    qm = np.minimum(np.floor((muc - 0.5) * (2.0 * n_mu)).astype(np.int64), n_mu - 1)
-    qt = np.minimum(np.floor((tc - 0.5) * (2.0 * n_t)).astype(np.int64), n_t - 1)
+    lo, hi = F32(0.5 - SHAPE_TOL), F32(1.0 + SHAPE_TOL)
+    ok &= (mu >= lo) & (mu <= hi) & (t >= lo) & (t <= hi)
+    half, one = F32(0.5), F32(1.0)
+    muc = np.minimum(np.maximum(mu, half), one)
+    tc = np.minimum(np.maximum(t, half), one)
+    qm = np.minimum(np.floor((muc - half) * F32(2 * n_mu)).astype(np.int64), n_mu - 1)
+    qt = np.minimum(np.floor((tc - half) * F32(2 * n_t)).astype(np.int64), n_t - 1)
     return np.where(ok, (qk * n_mu + qm) * n_t + qt, -1)
 
 
@@ -112,18 +120,18 @@ def bs_monopole(b3d, trips, kperp, kpar, k1_edges, n_mu: int, n_t: int, model=No
     model   None, or (f_ng, p_amp, p_index): bin Eq. (bsana) instead of b3d
     returns sums [batch][n_k1][n_mu][n_t], counts [n_k1][n_mu][n_t] (int64)
     """
-    kpar = np.asarray(kpar, np.float64)
+    kpar = np.asarray(kpar, np.float64).astype(F32)
+    kp = np.asarray(kperp, np.float64).astype(F32)
     nc = kpar.size
     n_k1 = len(k1_edges) - 1
     nbin = n_k1 * n_mu * n_t
     batch = 1 if b3d is None else b3d.shape[0]
     sums = np.zeros((batch, nbin))
     cnt = np.zeros(nbin, np.int64)
-    ka = kpar[:, None] * np.ones((1, nc))
-    kb = np.ones((nc, 1)) * kpar[None, :]
+    ka = np.repeat(kpar[:, None], nc, axis=1)
+    kb = np.repeat(kpar[None, :], nc, axis=0)
     kc = -(ka + kb)
     for p, (i, j, l) in enumerate(trips):
-        kp = np.asarray(kperp, np.float64)
         S1 = kp[i] * kp[i] + ka * ka
         S2 = kp[j] * kp[j] + kb * kb
         S3 = kp[l] * kp[l] + kc * kc
@@ -135,6 +143,7 @@ def bs_monopole(b3d, trips, kperp, kpar, k1_edges, n_mu: int, n_t: int, model=No
             if model is None:
                 v = np.asarray(b3d[b, p], np.float64).ravel()
             else:
-                v = bsana(S1, S2, S3, *model).ravel()
+                v = bsana(S1.astype(np.float64), S2.astype(np.float64), S3.astype(np.float64),
+                          *model).ravel()
             sums[b] += np.bincount(q[sel], weights=v[sel], minlength=nbin)
     return sums.reshape(batch, n_k1, n_mu, n_t), cnt.reshape(n_k1, n_mu, n_t)
