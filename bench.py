@@ -245,6 +245,42 @@ def run_reference(args, w):
     print(json.dumps(line), flush=True)
 
 
+def run_monopole(plan, b3, stream, nc, reps=5):
+    """The binned 3D-bispectrum monopole (bs_bs_monopole) of the step's own
+    closable-plane output: 12 log k1 bins x 5 mu x 5 t, CUDA events on the
+    launching stream; the algorithmic bytes are one read of the planes."""
+    import numpy as np
+    import torch
+    kperp = 2 * np.pi * plan.ring_umean()  # r = 1 in the bench plans
+    kpar = (np.arange(nc) - nc // 2) * (2 * np.pi / nc)
+    kmax = float(np.sqrt(kperp.max() ** 2 + 4 * np.abs(kpar).max() ** 2))
+    edges = np.geomspace(0.9 * kperp.min(), 1.01 * kmax, 13)
+    for _ in range(3):
+        sums, cnt = plan.bs_monopole(b3, kperp, kpar, edges, 5, 5)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for _ in range(reps):
+        sums, cnt = plan.bs_monopole(b3, kperp, kpar, edges, 5, 5)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    ms = ev[0].elapsed_time(ev[1]) / reps
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    plan.bs_monopole(None, kperp, kpar, edges, 5, 5, model=(1.0, 1.0, -2.0))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    samples = b3.numel()
+    gbs = samples * 8 / (ms / 1e3) / 1e9
+    peak = float(measured_peaks().get("hbm_gbs", 6800.0))
+    return {"bins": "12 log k1 x 5 mu x 5 t", "samples": samples, "ms": ms,
+            "samples_per_s": samples / (ms / 1e3), "binned": int(cnt.sum().item()),
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                         "frac": gbs / peak, "bytes": samples * 8},
+            "model_ms": e0.elapsed_time(e1),
+            "note": "kernel k_bs_monopole<1>; model_ms bins Eq. (bsana) (FP64 pow per sample)"}
+
+
 def run_e2e(args, step_e2e, vis_h, vis_d, out3d, stream, world, dev, barrier):
     """End-to-end throughput through the C ABI from host memory.  Every step
     copies its visibilities host->device (pinned) and reads its 3D bispectrum
@@ -522,6 +558,7 @@ def main():
                       vis_d=vis_d, out3d=out3d, stream=stream, world=world, dev=dev,
                       barrier=barrier)
         e2e["clocks"] = eclk.stop()  # runs after the timed region, GPU already warm
+    mono = run_monopole(plan, out3d, stream, nc) if world == 1 else None
 
     # roofline of the contraction (dominant kernel): algorithmic FLOPs = 2 M^2 per evaluation
     M = plan.M
@@ -575,6 +612,8 @@ def main():
         "gpu_launches": launches_per_step * args.steps,
         "e2e": e2e,
     }
+    if mono is not None:
+        line["monopole"] = mono
     line["config"]["stated_error"] = STATED_ERROR[args.precision]
     contraction_rate = per_launch_evals / (avg_ms / 1e3)
     line["contraction_evals_per_s"] = contraction_rate

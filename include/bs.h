@@ -54,7 +54,7 @@
 extern "C" {
 #endif
 
-#define BS_ABI_VERSION 5
+#define BS_ABI_VERSION 6
 
 typedef struct bs_plan_s *bs_plan;
 
@@ -221,6 +221,45 @@ bs_status bs_bs3d(bs_plan plan, double *out_dev, void *cuda_stream);
  * Errors: as bs_mabs_delta / bs_bs3d. */
 bs_status bs_mabs_delta_closable(bs_plan plan, double *out_dev, void *cuda_stream);
 bs_status bs_bs3d_closable(bs_plan plan, double *out_dev, void *cuda_stream);
+
+/* Mean |U| of each ring's binned grid cells, in grid units (the mid point of
+ * the ring's edges when it holds no cell): U_m in k_perp = 2 pi U_m / r.
+ *  umean_host  double [nbins], written. */
+bs_status bs_plan_ring_umean(bs_plan plan, double *umean_host);
+
+/* Monopole of the 3D bispectrum binned in triangle size and shape (Section
+ * 2, Eq. shape and Eq. bs_lm with l = m = 0; the (k1, mu, t) binning of
+ * Section 5).  Samples: every closable ring triple (i, j, l) x every delay
+ * pair (a, b); sides k_n = sqrt(kperp_n^2 + kpar_n^2) with kpar(a) for ring
+ * i, kpar(b) for ring j and -kpar(a) - kpar(b) for ring l; k1 >= k2 >= k3,
+ * t = k2 / k1, mu = -k1.k2 / (k1 k2) = (k1^2 + k2^2 - k3^2) / (2 k1 k2).
+ *  b3d_dev        double [batch][n_c][nchan][nchan] as bs_bs3d_closable writes
+ *                 it, or NULL: bin the model of Eq. (bsana),
+ *                 2 f_ng [P(k1)P(k2) + P(k2)P(k3) + P(k3)P(k1)] with
+ *                 P(k) = p_amp k^p_index, at the same discrete modes (the
+ *                 binned analytic prediction [B]_d of Section 5)
+ *  kperp_host     double [nbins]: k_perp of each ring (e.g. 2 pi U_m / r)
+ *  kpar_host      double [nchan]: k_par of Eq. (dft) row a + nchan/2
+ *                 (2 pi a / (r' nchan dnu_c))
+ *  k1_edges_host  double [n_k1 + 1], finite and ascending (n_k1 <= 1024);
+ *                 bin q holds e_q <= k1 < e_{q+1}
+ *  n_mu, n_t      linear bins of mu and t over [0.5, 1] (<= 1024 each); the
+ *                 value 1 falls in the last bin
+ *  sum_dev        double [batch (1 for the model)][n_k1][n_mu][n_t]: sum of
+ *                 the values in each bin (overwritten)
+ *  count_dev      int64 [n_k1][n_mu][n_t]: samples in each bin (overwritten);
+ *                 the monopole is sum / count
+ * The bin of a sample is decided in FP32, every operation rounded once in the
+ * order above (no fused multiply-add); samples whose mu or t falls outside
+ * [0.5 - 1e-6, 1 + 1e-6] are dropped (side lengths from ring centres need
+ * not close), the rest clamped to [0.5, 1].  Values and sums are FP64.
+ * Errors: BS_ERR_ARG (NULL, counts out of range, edges not ascending),
+ * BS_ERR_STATE (no counts yet), BS_ERR_UNSUPPORTED (bins x realisations
+ * beyond one CTA's shared memory). */
+bs_status bs_bs_monopole(bs_plan plan, const double *b3d_dev, const double *kperp_host,
+                         const double *kpar_host, const double *k1_edges_host, int n_k1,
+                         int n_mu, int n_t, double f_ng, double p_amp, double p_index,
+                         double *sum_dev, int64_t *count_dev, void *cuda_stream);
 
 /* Check V(-U) = conj V(U) on every binned cell of every channel and
  * realisation: |V(-U) - conj V(U)| <= tol * max|V| (synchronises).

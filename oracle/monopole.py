@@ -147,3 +147,21 @@ def bs_monopole(b3d, trips, kperp, kpar, k1_edges, n_mu: int, n_t: int, model=No
                           *model).ravel()
             sums[b] += np.bincount(q[sel], weights=v[sel], minlength=nbin)
     return sums.reshape(batch, n_k1, n_mu, n_t), cnt.reshape(n_k1, n_mu, n_t)
+
+
+def _chunk(args):
+    b3d, trips, kperp, kpar, k1_edges, n_mu, n_t, model = args
+    return bs_monopole(b3d, trips, kperp, kpar, k1_edges, n_mu, n_t, model=model)
+
+
+def bs_monopole_pool(trips, kperp, kpar, k1_edges, n_mu: int, n_t: int, model, workers: int = 16):
+    """``bs_monopole`` of the model (no values) over many planes, the planes
+    split across a spawn-started process pool: sums and counts of disjoint
+    plane sets add."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    chunks = [trips[k::workers] for k in range(workers) if trips[k::workers]]
+    args = [(None, c, kperp, kpar, k1_edges, n_mu, n_t, model) for c in chunks]
+    with ProcessPoolExecutor(len(chunks), mp_context=mp.get_context("spawn")) as ex:
+        parts = list(ex.map(_chunk, args))
+    return sum(p[0] for p in parts), sum(p[1] for p in parts)

@@ -27,14 +27,14 @@ STATUS = {0: "BS_OK", 1: "BS_ERR_ARG", 2: "BS_ERR_NO_DEVICE", 3: "BS_ERR_CUDA", 
 PREC_FP32 = 0
 PREC_SPLIT_BF16 = 1
 PREC_SPLIT_FP16 = 2
-ABI_VERSION = 5      # BS_ABI_VERSION of include/bs.h
+ABI_VERSION = 6      # BS_ABI_VERSION of include/bs.h
 MLP_FEATURES = 45    # BS_MLP_FEATURES of include/bs.h
 
 # every symbol declared in include/bs.h
 EXPORTS = ("bs_abi_version", "bs_plan_create", "bs_plan_destroy", "bs_last_error",
            "bs_plan_info", "bs_plan_trip_sides", "bs_plan_set_workspace", "bs_grid_load", "bs_counts", "bs_mabs",
            "bs_delta_reset", "bs_mabs_delta", "bs_bs3d", "bs_mabs_delta_closable",
-           "bs_bs3d_closable", "bs_check_hermitian",
+           "bs_bs3d_closable", "bs_plan_ring_umean", "bs_bs_monopole", "bs_check_hermitian",
            "bs_mc_create", "bs_mc_destroy", "bs_mc_last_error", "bs_mc_info", "bs_mc_set_input",
            "bs_mc_set_flags", "bs_mc_set_tuning", "bs_mc_autotune", "bs_mc_run", "bs_mc_reset",
            "bs_mc_stats",
@@ -251,6 +251,40 @@ class Plan:
         """bs_mabs_delta_closable: out float64 CUDA [batch, n_closable, 2nc-1, 2nc-1], the
         closable ring triples in ascending index."""
         self._check(self._L.bs_mabs_delta_closable(self._h, _dptr(out), _stream_ptr(stream)))
+
+    def ring_umean(self):
+        """bs_plan_ring_umean: mean |U| of each ring's cells (numpy float64 [nbins])."""
+        import numpy as np
+        out = np.zeros(self.nbins, np.float64)
+        self._check(self._L.bs_plan_ring_umean(self._h, out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def bs_monopole(self, b3d, kperp, kpar, k1_edges, n_mu=5, n_t=5, model=None, stream=None):
+        """bs_bs_monopole: binned 3D-bispectrum monopole.  b3d: float64 CUDA tensor as
+        bs3d_closable writes it, or None with model = (f_ng, p_amp, p_index) for the binned
+        Eq. (bsana).  Returns (sums [batch, n_k1, n_mu, n_t] float64 CUDA,
+        counts [n_k1, n_mu, n_t] int64 CUDA)."""
+        import numpy as np
+        import torch
+        kp = np.ascontiguousarray(np.asarray(kperp, np.float64))
+        kz = np.ascontiguousarray(np.asarray(kpar, np.float64))
+        ed = np.ascontiguousarray(np.asarray(k1_edges, np.float64))
+        if kp.size != self.nbins or kz.size != self.nchan:
+            raise ValueError("kperp needs nbins entries and kpar nchan entries")
+        n_k1 = ed.size - 1
+        batch = 1 if b3d is None else self.batch
+        if b3d is not None and (b3d.dtype != torch.float64 or
+                                b3d.numel() != batch * self.n_closable * self.nchan ** 2):
+            raise ValueError("b3d must be float64 [batch, n_closable, nchan, nchan]")
+        sums = torch.empty((batch, n_k1, n_mu, n_t), dtype=torch.float64, device="cuda")
+        cnt = torch.empty((n_k1, n_mu, n_t), dtype=torch.int64, device="cuda")
+        f, a, pi = model if model is not None else (0.0, 0.0, 0.0)
+        self._check(self._L.bs_bs_monopole(
+            self._h, _dptr(b3d), kp.ctypes.data_as(ctypes.c_void_p),
+            kz.ctypes.data_as(ctypes.c_void_p), ed.ctypes.data_as(ctypes.c_void_p), n_k1, n_mu, n_t,
+            ctypes.c_double(f), ctypes.c_double(a), ctypes.c_double(pi), _dptr(sums), _dptr(cnt),
+            _stream_ptr(stream)))
+        return sums, cnt
 
     def bs3d_closable(self, out, stream=None):
         """bs_bs3d_closable: out float64 CUDA [batch, n_closable, nc, nc], the closable ring

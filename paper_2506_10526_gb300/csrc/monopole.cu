@@ -1,0 +1,254 @@
+// Monopole of the 3D bispectrum binned in triangle size and shape
+// (Section 2: Eq. shape and Eq. bs_lm at l = m = 0; the (k1, mu, t) binning
+// of Section 5; Eq. bsana for the binned analytic prediction).
+//
+// Samples: every closable ring triple (i, j, l) x every delay pair (a, b) of
+// the Eq. (dft) output.  The three sides are k_n = sqrt(kperp_n^2 + kpar_n^2)
+// with kpar_1 = kpar(a) (ring i), kpar_2 = kpar(b) (ring j) and
+// kpar_3 = -(kpar_1 + kpar_2) (ring l).  With S1 >= S2 >= S3 the squared
+// sides, the size is K1 = sqrt(S1) and the shape t = K2 / K1,
+// mu = ((S1 + S2) - S3) / (2 K1 K2) (the closure k1 + k2 + k3 = 0 turns
+// -k1.k2 into squared lengths).  A bin holds the sum of the values and the
+// number of samples; the caller divides.
+//
+// The bin is decided in FP32 with every operation rounded once, in a fixed
+// order and without fused multiply-adds, so that bin indices are a
+// deterministic function of the inputs; values and sums are FP64.
+//
+// Kernel: grid (chunks of one plane, planes).  Each thread walks runs of kRun
+// consecutive samples and keeps a running (bin, sums, count) in registers,
+// flushing to the CTA's shared-memory histogram only when the bin changes
+// (neighbouring delay modes mostly share a bin).  The CTA then adds its
+// non-empty bins to the global sums with FP64 atomics.
+#include <cmath>
+#include <vector>
+
+#include "plan_internal.h"
+
+namespace bsi {
+
+namespace {
+
+constexpr int kRun = 16;      // consecutive samples per thread and pass
+constexpr int kThreads = 256;
+constexpr int kMaxBatch = 8;  // realisations per launch (the host loops over more)
+constexpr int kMonoMaxK1 = 1024;
+
+struct MonoArgs {
+  const double *b3d;     // [batch_total][n_planes][nc][nc] or null (model)
+  long long bstride;     // n_planes * nc * nc
+  int b0, nbatch;        // realisations [b0, b0 + nbatch) of this launch
+  const int *rings;      // [n_planes][3]
+  const double *kperp;   // [nb]
+  const double *kpar;    // [nc]
+  const double *edges;   // [n_k1 + 1]
+  int nc, n_k1, n_mu, n_t, nbin;
+  long long chunk;       // samples per CTA
+  float lo, hi;          // accepted mu, t range before clamping
+  int model;
+  double f2, p_amp, p_half;  // 2 f_NG, amplitude, p_index / 2
+  double *sums;          // [batch_total][nbin]
+  unsigned long long *cnt;  // [nbin], or null (counted by an earlier launch)
+};
+
+__device__ __forceinline__ int bin_of(const MonoArgs &a, const double *edges, float kpi, float kpj,
+                                      float kpl, float ka, float kb, float (&S)[3]) {
+  const float kc = -__fadd_rn(ka, kb);
+  S[0] = __fadd_rn(__fmul_rn(kpi, kpi), __fmul_rn(ka, ka));
+  S[1] = __fadd_rn(__fmul_rn(kpj, kpj), __fmul_rn(kb, kb));
+  S[2] = __fadd_rn(__fmul_rn(kpl, kpl), __fmul_rn(kc, kc));
+  float s1 = S[0], s2 = S[1], s3 = S[2], tmp;
+  if (s1 < s2) { tmp = s1; s1 = s2; s2 = tmp; }
+  if (s2 < s3) { tmp = s2; s2 = s3; s3 = tmp; }
+  if (s1 < s2) { tmp = s1; s1 = s2; s2 = tmp; }
+  const float K1 = __fsqrt_rn(s1), K2 = __fsqrt_rn(s2);
+  const float t = __fdiv_rn(K2, K1);
+  const float mu = __fdiv_rn(__fsub_rn(__fadd_rn(s1, s2), s3), __fmul_rn(2.0f, __fmul_rn(K1, K2)));
+  if (!(mu >= a.lo && mu <= a.hi && t >= a.lo && t <= a.hi)) return -1;
+  const double k1 = (double)K1;
+  if (!(k1 >= edges[0] && k1 < edges[a.n_k1])) return -1;
+  int lo = 0, hi = a.n_k1;  // edges[lo] <= k1 < edges[hi]
+  while (hi - lo > 1) {
+    const int m = (lo + hi) >> 1;
+    if (edges[m] <= k1) lo = m; else hi = m;
+  }
+  const float muc = fminf(fmaxf(mu, 0.5f), 1.0f), tc = fminf(fmaxf(t, 0.5f), 1.0f);
+  const int qm = min((int)floorf(__fmul_rn(__fsub_rn(muc, 0.5f), (float)(2 * a.n_mu))), a.n_mu - 1);
+  const int qt = min((int)floorf(__fmul_rn(__fsub_rn(tc, 0.5f), (float)(2 * a.n_t))), a.n_t - 1);
+  return (lo * a.n_mu + qm) * a.n_t + qt;
+}
+
+template <int NB>  // realisations held in registers (a.nbatch <= NB)
+__global__ void __launch_bounds__(kThreads) k_bs_monopole(const MonoArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double *hs = reinterpret_cast<double *>(smem_raw);                  // [nbatch][nbin]
+  unsigned *hc = reinterpret_cast<unsigned *>(hs + (size_t)a.nbatch * a.nbin);  // [nbin]
+  double *edges = reinterpret_cast<double *>(hc + a.nbin + (a.nbin & 1));  // [n_k1 + 1]
+  const int p = blockIdx.y;
+  for (int q = threadIdx.x; q < a.nbatch * a.nbin; q += blockDim.x) hs[q] = 0.0;
+  for (int q = threadIdx.x; q < a.nbin; q += blockDim.x) hc[q] = 0u;
+  for (int q = threadIdx.x; q <= a.n_k1; q += blockDim.x) edges[q] = a.edges[q];
+  __syncthreads();
+  const int i = a.rings[3 * p], j = a.rings[3 * p + 1], l = a.rings[3 * p + 2];
+  const float kpi = __double2float_rn(a.kperp[i]), kpj = __double2float_rn(a.kperp[j]),
+              kpl = __double2float_rn(a.kperp[l]);
+  const long long n = (long long)a.nc * a.nc;
+  const long long e0 = (long long)blockIdx.x * a.chunk, e1 = min(n, e0 + a.chunk);
+  const double *vb = a.b3d ? a.b3d + (long long)a.b0 * a.bstride + (long long)p * n : nullptr;
+
+  int cur = -1;
+  unsigned run_n = 0;
+  double run_s[NB];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) run_s[b] = 0.0;
+  auto flush = [&]() {
+    if (cur >= 0 && run_n) {
+      atomicAdd(hc + cur, run_n);
+#pragma unroll
+      for (int b = 0; b < NB; ++b)
+        if (b < a.nbatch) atomicAdd(hs + (size_t)b * a.nbin + cur, run_s[b]);
+    }
+    run_n = 0;
+#pragma unroll
+    for (int b = 0; b < NB; ++b) run_s[b] = 0.0;
+  };
+  for (long long base = e0 + (long long)threadIdx.x * kRun; base < e1;
+       base += (long long)blockDim.x * kRun) {
+    const long long stop = min(e1, base + kRun);
+    for (long long e = base; e < stop; ++e) {
+      const int ia = (int)(e / a.nc), ib = (int)(e - (long long)ia * a.nc);
+      float S[3];
+      const int q = bin_of(a, edges, kpi, kpj, kpl, __double2float_rn(a.kpar[ia]),
+                           __double2float_rn(a.kpar[ib]), S);
+      if (q < 0) continue;
+      if (q != cur) {
+        flush();
+        cur = q;
+      }
+      ++run_n;
+      if (a.model) {
+        const double P1 = a.p_amp * pow((double)S[0], a.p_half),
+                     P2 = a.p_amp * pow((double)S[1], a.p_half),
+                     P3 = a.p_amp * pow((double)S[2], a.p_half);
+        run_s[0] += a.f2 * (P1 * P2 + P2 * P3 + P3 * P1);
+      } else {
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+          if (b < a.nbatch) run_s[b] += vb[(long long)b * a.bstride + e];
+      }
+    }
+  }
+  flush();
+  __syncthreads();
+  for (int q = threadIdx.x; q < a.nbin; q += blockDim.x) {
+    const unsigned c = hc[q];
+    if (!c) continue;
+    if (a.cnt) atomicAdd(a.cnt + q, (unsigned long long)c);
+    for (int b = 0; b < a.nbatch; ++b)
+      atomicAdd(a.sums + (size_t)(a.b0 + b) * a.nbin + q, hs[(size_t)b * a.nbin + q]);
+  }
+}
+
+}  // namespace
+
+// Bytes of shared memory the kernel needs for nbatch realisations.
+static size_t mono_smem(int nbin, int nbatch, int n_k1) {
+  return (size_t)nbatch * nbin * 8 + (size_t)(nbin + (nbin & 1)) * 4 + (size_t)(n_k1 + 1) * 8;
+}
+
+}  // namespace bsi
+
+#define MONO_CUDA(call)                                          \
+  do {                                                           \
+    cudaError_t e__ = (call);                                    \
+    if (e__ != cudaSuccess) return cuda_fail(p, e__, #call);     \
+  } while (0)
+
+extern "C" {
+
+bs_status bs_plan_ring_umean(bs_plan p, double *umean_host) {
+  if (!p || !umean_host) return fail(p, BS_ERR_ARG, "umean_host must not be NULL");
+  for (int m = 0; m < p->nb; ++m) umean_host[m] = p->umean[m];
+  return BS_OK;
+}
+
+bs_status bs_bs_monopole(bs_plan p, const double *b3d, const double *kperp_host,
+                         const double *kpar_host, const double *k1_edges_host, int n_k1, int n_mu,
+                         int n_t, double f_ng, double p_amp, double p_index, double *sum_dev,
+                         int64_t *count_dev, void *stream) {
+  using namespace bsi;
+  if (!p || !kperp_host || !kpar_host || !k1_edges_host || !sum_dev || !count_dev)
+    return fail(p, BS_ERR_ARG, "bs_bs_monopole: NULL argument");
+  if (n_k1 < 1 || n_k1 > kMonoMaxK1 || n_mu < 1 || n_t < 1 || n_mu > 1024 || n_t > 1024)
+    return fail(p, BS_ERR_ARG, "bs_bs_monopole: bin counts out of range");
+  for (int q = 0; q < n_k1; ++q)
+    if (!(k1_edges_host[q + 1] > k1_edges_host[q]) || !std::isfinite(k1_edges_host[q + 1]))
+      return fail(p, BS_ERR_ARG, "bs_bs_monopole: k1 edges must be finite and ascending");
+  if (!p->counts_ready) return fail(p, BS_ERR_STATE, "bs_bs_monopole before the ring-triple counts");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  bs_status st = prepare(p, s);
+  if (st != BS_OK) return st;
+  const int nbin = n_k1 * n_mu * n_t;
+  const int batch = b3d ? p->batch : 1;
+  const int per = std::min(batch, kMaxBatch);
+  if (mono_smem(nbin, per, n_k1) > (size_t)160 * 1024)
+    return fail(p, BS_ERR_UNSUPPORTED, "bs_bs_monopole: too many bins for one CTA's histogram");
+  MONO_CUDA(cudaMemsetAsync(sum_dev, 0, (size_t)batch * nbin * sizeof(double), s));
+  MONO_CUDA(cudaMemsetAsync(count_dev, 0, (size_t)nbin * sizeof(int64_t), s));
+  const int npl = (int)p->clos.size();
+  if (npl == 0) return BS_OK;
+  // constants: kperp [nb], kpar [nc], edges [n_k1 + 1]
+  double *tab = p->at<double>(p->L.mono);
+  MONO_CUDA(cudaMemcpyAsync(tab, kperp_host, p->nb * sizeof(double), cudaMemcpyHostToDevice, s));
+  MONO_CUDA(cudaMemcpyAsync(tab + p->nb, kpar_host, p->nc * sizeof(double), cudaMemcpyHostToDevice, s));
+  MONO_CUDA(cudaMemcpyAsync(tab + p->nb + p->nc, k1_edges_host, (n_k1 + 1) * sizeof(double),
+                            cudaMemcpyHostToDevice, s));
+  MONO_CUDA(smem_optin_once<k_bs_monopole<1>>());
+  MONO_CUDA(smem_optin_once<k_bs_monopole<2>>());
+  MONO_CUDA(smem_optin_once<k_bs_monopole<4>>());
+  MONO_CUDA(smem_optin_once<k_bs_monopole<kMaxBatch>>());
+  MonoArgs a{};
+  a.b3d = b3d;
+  a.bstride = (long long)npl * p->nc * p->nc;
+  a.rings = p->at<int>(p->L.closrings);
+  a.kperp = tab;
+  a.kpar = tab + p->nb;
+  a.edges = tab + p->nb + p->nc;
+  a.nc = p->nc;
+  a.n_k1 = n_k1;
+  a.n_mu = n_mu;
+  a.n_t = n_t;
+  a.nbin = nbin;
+  a.lo = (float)(0.5 - 1e-6);
+  a.hi = (float)(1.0 + 1e-6);
+  a.model = b3d ? 0 : 1;
+  a.f2 = 2.0 * f_ng;
+  a.p_amp = p_amp;
+  a.p_half = 0.5 * p_index;
+  a.sums = sum_dev;
+  a.cnt = reinterpret_cast<unsigned long long *>(count_dev);
+  // about 64 Ki samples per CTA: few global flushes, several CTAs per plane
+  const long long n = (long long)p->nc * p->nc;
+  const long long per_cta = (long long)kThreads * kRun * 16;
+  const int nx = (int)std::max<long long>(1, (n + per_cta - 1) / per_cta);
+  a.chunk = ((n + nx - 1) / nx + kRun - 1) / kRun * kRun;
+  for (int b0 = 0; b0 < batch; b0 += per) {
+    a.b0 = b0;
+    a.nbatch = std::min(per, batch - b0);
+    if (b0 > 0) a.cnt = nullptr;  // the same samples: counted by the first launch
+    const dim3 grid(nx, npl);
+    const size_t sm = mono_smem(nbin, a.nbatch, n_k1);
+    if (a.nbatch == 1)
+      k_bs_monopole<1><<<grid, kThreads, sm, s>>>(a);
+    else if (a.nbatch == 2)
+      k_bs_monopole<2><<<grid, kThreads, sm, s>>>(a);
+    else if (a.nbatch <= 4)
+      k_bs_monopole<4><<<grid, kThreads, sm, s>>>(a);
+    else
+      k_bs_monopole<kMaxBatch><<<grid, kThreads, sm, s>>>(a);
+    MONO_CUDA(cudaGetLastError());
+  }
+  return BS_OK;
+}
+
+}  // extern "C"

@@ -139,6 +139,9 @@ void compute_layout(bs_plan p) {
   L.mlptab = take(((size_t)p->ntrip * 4 + 36) * sizeof(float));
   L.ztrips = take((size_t)p->ntrip * sizeof(int));
   L.clos = take((size_t)p->ntrip * sizeof(int));
+  L.closrings = take((size_t)p->ntrip * 3 * sizeof(int));
+  // monopole binning constants: kperp [nb], kpar [nc], k1 edges [<= 1025]
+  L.mono = take(((size_t)p->nb + p->nc + 1025) * sizeof(double));
   L.total = o;
 }
 
@@ -310,11 +313,18 @@ bs_status run_counts(bs_plan p, const int8_t *lab_dev, cudaStream_t s) {
   BS_CUDA(cudaMemcpyAsync(p->at<double>(p->L.tnorm), p->tnorm.data(), p->ntrip * sizeof(double),
                           cudaMemcpyHostToDevice, s));
   p->clos.clear();
+  p->closrings.clear();
   for (int t = 0; t < p->ntrip; ++t)
-    if (p->T[t] > 0) p->clos.push_back(t);
-  if (!p->clos.empty())
+    if (p->T[t] > 0) {
+      p->clos.push_back(t);
+      for (int k = 0; k < 3; ++k) p->closrings.push_back(p->trips[3 * t + k]);
+    }
+  if (!p->clos.empty()) {
     BS_CUDA(cudaMemcpyAsync(p->at<int>(p->L.clos), p->clos.data(), p->clos.size() * sizeof(int),
                             cudaMemcpyHostToDevice, s));
+    BS_CUDA(cudaMemcpyAsync(p->at<int>(p->L.closrings), p->closrings.data(),
+                            p->closrings.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  }
   BS_CUDA(cudaStreamSynchronize(s));
   p->counts_ready = true;
   p->dsum_clean = false;

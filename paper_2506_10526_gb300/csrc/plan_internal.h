@@ -12,7 +12,7 @@ namespace bsi {
 
 struct WsLayout {
   size_t label, efflabel, cells, uext, tripof, valid, twM, twN, tnorm, T, nnu, cols, ptiles, tctiles,
-      G, F, Fhi, Flo, dsum, tmp3d, herm, err, maps, tcgroup, mlptab, ztrips, clos, total;
+      G, F, Fhi, Flo, dsum, tmp3d, herm, err, maps, tcgroup, mlptab, ztrips, clos, closrings, mono, total;
 };
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
@@ -57,6 +57,7 @@ struct bs_plan_s {
   bool dsum_clean = false;        // every plane of a non-closable triple is zero
   std::vector<int> zero_trips;    // closable ring triples (the only planes ever accumulated)
   std::vector<int> clos;          // ring triples with T > 0, ascending (device copy at L.clos)
+  std::vector<int> closrings;     // [clos.size()][3] rings (i, j, l) of those triples
   std::vector<int> trips;        // [ntrip][3]
   std::vector<int> trip_of;      // [nb^3] -> trip index of sorted (i<=j<=l), else -1
   std::vector<long long> T;      // [ntrip] closed-triangle counts
