@@ -13,7 +13,11 @@
 //
 // The bin is decided in FP32 with every operation rounded once, in a fixed
 // order and without fused multiply-adds, so that bin indices are a
-// deterministic function of the inputs; values and sums are FP64.
+// deterministic function of the inputs; values and sums are FP64.  The k1
+// edges are compared in FP32 too: for a float x and a double e, x >= e
+// exactly when x >= the smallest float not below e, so the host rounds each
+// edge up to FP32 once and the comparisons stay on the FP32 pipe (the GB300
+// FP64 rate is a small fraction of its FP32 rate).
 //
 // Kernel: grid (chunks of one plane, planes).  Each thread walks runs of kRun
 // consecutive samples and keeps a running (bin, sums, count) in registers,
@@ -21,6 +25,7 @@
 // (neighbouring delay modes mostly share a bin).  The CTA then adds its
 // non-empty bins to the global sums with FP64 atomics.
 #include <cmath>
+#include <limits>
 #include <vector>
 
 #include "plan_internal.h"
@@ -39,11 +44,11 @@ struct MonoArgs {
   long long bstride;     // n_planes * nc * nc
   int b0, nbatch;        // realisations [b0, b0 + nbatch) of this launch
   const int *rings;      // [n_planes][3]
-  const double *kperp;   // [nb]
-  const double *kpar;    // [nc]
-  const double *edges;   // [n_k1 + 1]
+  const float *kperp;    // [nb], rounded to FP32
+  const float *kpar;     // [nc], rounded to FP32
+  const float *edges;    // [n_k1 + 1], each rounded up to FP32
   int nc, n_k1, n_mu, n_t, nbin;
-  long long chunk;       // samples per CTA
+  int chunk;             // samples per CTA (nc^2 < 2^31)
   float lo, hi;          // accepted mu, t range before clamping
   int model;
   double f2, p_amp, p_half;  // 2 f_NG, amplitude, p_index / 2
@@ -51,7 +56,7 @@ struct MonoArgs {
   unsigned long long *cnt;  // [nbin], or null (counted by an earlier launch)
 };
 
-__device__ __forceinline__ int bin_of(const MonoArgs &a, const double *edges, float kpi, float kpj,
+__device__ __forceinline__ int bin_of(const MonoArgs &a, const float *edges, float kpi, float kpj,
                                       float kpl, float ka, float kb, float (&S)[3]) {
   const float kc = -__fadd_rn(ka, kb);
   S[0] = __fadd_rn(__fmul_rn(kpi, kpi), __fmul_rn(ka, ka));
@@ -65,12 +70,11 @@ __device__ __forceinline__ int bin_of(const MonoArgs &a, const double *edges, fl
   const float t = __fdiv_rn(K2, K1);
   const float mu = __fdiv_rn(__fsub_rn(__fadd_rn(s1, s2), s3), __fmul_rn(2.0f, __fmul_rn(K1, K2)));
   if (!(mu >= a.lo && mu <= a.hi && t >= a.lo && t <= a.hi)) return -1;
-  const double k1 = (double)K1;
-  if (!(k1 >= edges[0] && k1 < edges[a.n_k1])) return -1;
-  int lo = 0, hi = a.n_k1;  // edges[lo] <= k1 < edges[hi]
+  if (!(K1 >= edges[0] && K1 < edges[a.n_k1])) return -1;
+  int lo = 0, hi = a.n_k1;  // edges[lo] <= K1 < edges[hi]
   while (hi - lo > 1) {
     const int m = (lo + hi) >> 1;
-    if (edges[m] <= k1) lo = m; else hi = m;
+    if (edges[m] <= K1) lo = m; else hi = m;
   }
   const float muc = fminf(fmaxf(mu, 0.5f), 1.0f), tc = fminf(fmaxf(t, 0.5f), 1.0f);
   const int qm = min((int)floorf(__fmul_rn(__fsub_rn(muc, 0.5f), (float)(2 * a.n_mu))), a.n_mu - 1);
@@ -83,17 +87,16 @@ __global__ void __launch_bounds__(kThreads) k_bs_monopole(const MonoArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double *hs = reinterpret_cast<double *>(smem_raw);                  // [nbatch][nbin]
   unsigned *hc = reinterpret_cast<unsigned *>(hs + (size_t)a.nbatch * a.nbin);  // [nbin]
-  double *edges = reinterpret_cast<double *>(hc + a.nbin + (a.nbin & 1));  // [n_k1 + 1]
+  float *edges = reinterpret_cast<float *>(hc + a.nbin);                          // [n_k1 + 1]
   const int p = blockIdx.y;
   for (int q = threadIdx.x; q < a.nbatch * a.nbin; q += blockDim.x) hs[q] = 0.0;
   for (int q = threadIdx.x; q < a.nbin; q += blockDim.x) hc[q] = 0u;
   for (int q = threadIdx.x; q <= a.n_k1; q += blockDim.x) edges[q] = a.edges[q];
   __syncthreads();
   const int i = a.rings[3 * p], j = a.rings[3 * p + 1], l = a.rings[3 * p + 2];
-  const float kpi = __double2float_rn(a.kperp[i]), kpj = __double2float_rn(a.kperp[j]),
-              kpl = __double2float_rn(a.kperp[l]);
-  const long long n = (long long)a.nc * a.nc;
-  const long long e0 = (long long)blockIdx.x * a.chunk, e1 = min(n, e0 + a.chunk);
+  const float kpi = a.kperp[i], kpj = a.kperp[j], kpl = a.kperp[l];
+  const int n = a.nc * a.nc;
+  const int e0 = blockIdx.x * a.chunk, e1 = min(n, e0 + a.chunk);
   const double *vb = a.b3d ? a.b3d + (long long)a.b0 * a.bstride + (long long)p * n : nullptr;
 
   int cur = -1;
@@ -112,14 +115,17 @@ __global__ void __launch_bounds__(kThreads) k_bs_monopole(const MonoArgs a) {
 #pragma unroll
     for (int b = 0; b < NB; ++b) run_s[b] = 0.0;
   };
-  for (long long base = e0 + (long long)threadIdx.x * kRun; base < e1;
-       base += (long long)blockDim.x * kRun) {
-    const long long stop = min(e1, base + kRun);
-    for (long long e = base; e < stop; ++e) {
-      const int ia = (int)(e / a.nc), ib = (int)(e - (long long)ia * a.nc);
+  for (int base = e0 + threadIdx.x * kRun; base < e1; base += blockDim.x * kRun) {
+    const int stop = min(e1, base + kRun);
+    int ia = base / a.nc, ib = base - ia * a.nc;  // row a + nc/2, column b + nc/2
+    float ka = a.kpar[ia];
+    for (int e = base; e < stop; ++e, ++ib) {
+      if (ib == a.nc) {
+        ib = 0;
+        ka = a.kpar[++ia];
+      }
       float S[3];
-      const int q = bin_of(a, edges, kpi, kpj, kpl, __double2float_rn(a.kpar[ia]),
-                           __double2float_rn(a.kpar[ib]), S);
+      const int q = bin_of(a, edges, kpi, kpj, kpl, ka, a.kpar[ib], S);
       if (q < 0) continue;
       if (q != cur) {
         flush();
@@ -153,7 +159,14 @@ __global__ void __launch_bounds__(kThreads) k_bs_monopole(const MonoArgs a) {
 
 // Bytes of shared memory the kernel needs for nbatch realisations.
 static size_t mono_smem(int nbin, int nbatch, int n_k1) {
-  return (size_t)nbatch * nbin * 8 + (size_t)(nbin + (nbin & 1)) * 4 + (size_t)(n_k1 + 1) * 8;
+  return (size_t)nbatch * nbin * 8 + (size_t)nbin * 4 + (size_t)(n_k1 + 1) * 4;
+}
+
+// The smallest float not below e (x >= e  <=>  x >= up_f32(e) for floats x).
+static float up_f32(double e) {
+  float f = (float)e;
+  if ((double)f < e) f = std::nextafter(f, std::numeric_limits<float>::infinity());
+  return f;
 }
 
 }  // namespace bsi
@@ -197,12 +210,15 @@ bs_status bs_bs_monopole(bs_plan p, const double *b3d, const double *kperp_host,
   MONO_CUDA(cudaMemsetAsync(count_dev, 0, (size_t)nbin * sizeof(int64_t), s));
   const int npl = (int)p->clos.size();
   if (npl == 0) return BS_OK;
-  // constants: kperp [nb], kpar [nc], edges [n_k1 + 1]
-  double *tab = p->at<double>(p->L.mono);
-  MONO_CUDA(cudaMemcpyAsync(tab, kperp_host, p->nb * sizeof(double), cudaMemcpyHostToDevice, s));
-  MONO_CUDA(cudaMemcpyAsync(tab + p->nb, kpar_host, p->nc * sizeof(double), cudaMemcpyHostToDevice, s));
-  MONO_CUDA(cudaMemcpyAsync(tab + p->nb + p->nc, k1_edges_host, (n_k1 + 1) * sizeof(double),
-                            cudaMemcpyHostToDevice, s));
+  // FP32 constants: kperp [nb] and kpar [nc] rounded to nearest, the k1 edges
+  // [n_k1 + 1] rounded up (a pageable source is staged before the copy call returns)
+  std::vector<float> &ftab = p->mono_tab;
+  ftab.assign((size_t)p->nb + p->nc + n_k1 + 1, 0.f);
+  for (int m = 0; m < p->nb; ++m) ftab[m] = (float)kperp_host[m];
+  for (int c = 0; c < p->nc; ++c) ftab[p->nb + c] = (float)kpar_host[c];
+  for (int q = 0; q <= n_k1; ++q) ftab[p->nb + p->nc + q] = up_f32(k1_edges_host[q]);
+  float *tab = p->at<float>(p->L.mono);
+  MONO_CUDA(cudaMemcpyAsync(tab, ftab.data(), ftab.size() * sizeof(float), cudaMemcpyHostToDevice, s));
   MONO_CUDA(smem_optin_once<k_bs_monopole<1>>());
   MONO_CUDA(smem_optin_once<k_bs_monopole<2>>());
   MONO_CUDA(smem_optin_once<k_bs_monopole<4>>());
@@ -228,9 +244,9 @@ bs_status bs_bs_monopole(bs_plan p, const double *b3d, const double *kperp_host,
   a.sums = sum_dev;
   a.cnt = reinterpret_cast<unsigned long long *>(count_dev);
   // about 64 Ki samples per CTA: few global flushes, several CTAs per plane
-  const long long n = (long long)p->nc * p->nc;
-  const long long per_cta = (long long)kThreads * kRun * 16;
-  const int nx = (int)std::max<long long>(1, (n + per_cta - 1) / per_cta);
+  const int n = p->nc * p->nc;
+  const int per_cta = kThreads * kRun * 16;
+  const int nx = std::max(1, (n + per_cta - 1) / per_cta);
   a.chunk = ((n + nx - 1) / nx + kRun - 1) / kRun * kRun;
   for (int b0 = 0; b0 < batch; b0 += per) {
     a.b0 = b0;

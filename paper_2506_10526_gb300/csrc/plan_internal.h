@@ -58,6 +58,7 @@ struct bs_plan_s {
   std::vector<int> zero_trips;    // closable ring triples (the only planes ever accumulated)
   std::vector<int> clos;          // ring triples with T > 0, ascending (device copy at L.clos)
   std::vector<int> closrings;     // [clos.size()][3] rings (i, j, l) of those triples
+  std::vector<float> mono_tab;    // FP32 k tables of the last monopole call
   std::vector<int> trips;        // [ntrip][3]
   std::vector<int> trip_of;      // [nb^3] -> trip index of sorted (i<=j<=l), else -1
   std::vector<long long> T;      // [ntrip] closed-triangle counts

@@ -94,7 +94,7 @@ def test_monopole_geometry_full_mwa_size():
     tri, _ = plan.counts()
     kperp = 2 * np.pi * plan.ring_umean() / r
     kpar = mo.kpar_axis(nc, rp, dnu)
-    k1e = np.geomspace(2e-3, 0.8, 13)
+    k1e = np.geomspace(2e-3, 10.0, 13)
     model = (1.0, 1.0, -2.0)
     sums, cnt = plan.bs_monopole(None, kperp, kpar, k1e, 5, 5, model=model)
     torch.cuda.synchronize()
@@ -104,5 +104,6 @@ def test_monopole_geometry_full_mwa_size():
     c = cnt.cpu().numpy()
     np.testing.assert_array_equal(c, c_o)
     print(f"samples binned: {c.sum()} of {len(trips) * nc * nc}; occupied bins {(c > 0).sum()}")
+    assert c.sum() > 0.5 * len(trips) * nc * nc
     np.testing.assert_allclose(sums.cpu().numpy(), s_o, rtol=1e-10)
     plan.close()
