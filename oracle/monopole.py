@@ -165,3 +165,33 @@ def bs_monopole_pool(trips, kperp, kpar, k1_edges, n_mu: int, n_t: int, model, w
     with ProcessPoolExecutor(len(chunks), mp_context=mp.get_context("spawn")) as ex:
         parts = list(ex.map(_chunk, args))
     return sum(p[0] for p in parts), sum(p[1] for p in parts)
+
+
+def axis_bins(kpar, edges) -> np.ndarray:
+    """Bin of each delay index along one k_par axis: q with e_q <= k_par < e_{q+1},
+    -1 outside (FP64 comparisons)."""
+    e = np.asarray(edges, np.float64)
+    q = np.searchsorted(e, np.asarray(kpar, np.float64), side="right") - 1
+    return np.where((q >= 0) & (q < e.size - 1), q, -1)
+
+
+def bs_cylindrical(b3d, kpar, edges):
+    """The 3D bispectrum of each plane binned on a grid in the (k_par1,
+    k_par2) plane (Section 5, the binning behind Fig. cylbs): sums
+    [batch][n_planes][n][n] over the delay pairs (a, b) whose k_par(a),
+    k_par(b) fall in bins (q, r), and counts [n][n] of those pairs (the same
+    for every plane).  The bin value is sum / count."""
+    q = axis_bins(kpar, edges)
+    n = len(edges) - 1
+    batch, npl, nc, _ = b3d.shape
+    sums = np.zeros((batch, npl, n, n))
+    cnt = np.zeros((n, n), np.int64)
+    for a in range(nc):
+        if q[a] < 0:
+            continue
+        for b in range(nc):
+            if q[b] < 0:
+                continue
+            cnt[q[a], q[b]] += 1
+            sums[:, :, q[a], q[b]] += b3d[:, :, a, b]
+    return sums, cnt

@@ -140,3 +140,33 @@ def test_kpar_axis():
     k = mo.kpar_axis(8, rprime=2.0, dnu_c=0.5)
     assert k[4] == 0.0 and k[0] == pytest.approx(-4 * 2 * np.pi / (2.0 * 8 * 0.5))
     np.testing.assert_allclose(np.diff(k), 2 * np.pi / 8.0)
+
+
+def test_cylindrical_binning_pins():
+    """Constant planes give sum = value x count; the counts factor into the
+    per-axis counts; the total over bins equals the sum over the covered
+    delay pairs; a point-symmetric plane B(a, b) = B(-a, -b) gives a
+    point-symmetric binned plane on symmetric edges."""
+    nc = 12
+    kpar = mo.kpar_axis(nc, 1.0, 1.0)
+    edges = np.linspace(-2.0, 2.0, 5)  # k_par = a pi / 6: a = -3 .. 3 fall in [-2, 2)
+    q = mo.axis_bins(kpar, edges)
+    # a = -3, -2 -> [-2, -1); a = -1 -> [-1, 0); a = 0, 1 -> [0, 1); a = 2, 3 -> [1, 2)
+    assert list(q) == [-1, -1, -1, 0, 0, 1, 2, 2, 3, 3, -1, -1]
+    b3 = np.full((1, 2, nc, nc), 3.0)
+    s, c = mo.bs_cylindrical(b3, kpar, edges)
+    na = np.bincount(q[q >= 0], minlength=4)
+    np.testing.assert_array_equal(c, np.outer(na, na))
+    np.testing.assert_allclose(s, 3.0 * c[None, None])
+    r = np.random.default_rng(3)
+    x = r.normal(size=(2, 3, nc, nc))
+    s, c = mo.bs_cylindrical(x, kpar, edges)
+    inside = q >= 0
+    np.testing.assert_allclose(s.sum(axis=(-1, -2)), x[:, :, inside][:, :, :, inside].sum(axis=(-1, -2)))
+    # point symmetry about a = b = 0 (index nc/2): reflect the indices 1 .. nc-1
+    y = r.normal(size=(1, 1, nc, nc))
+    ys = y.copy()
+    ys[..., 1:, 1:] = 0.5 * (y[..., 1:, 1:] + y[..., 1:, 1:][..., ::-1, ::-1])
+    e_sym = np.array([-1.6, -0.5, 0.5, 1.6])  # symmetric, kpar a = -1, 0, 1 and +-1.047
+    s, c = mo.bs_cylindrical(ys, kpar, e_sym)
+    np.testing.assert_allclose(s[0, 0], s[0, 0][::-1, ::-1], rtol=1e-13)
