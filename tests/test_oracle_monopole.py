@@ -157,7 +157,7 @@ def test_cylindrical_binning_pins():
     s, c = mo.bs_cylindrical(b3, kpar, edges)
     na = np.bincount(q[q >= 0], minlength=4)
     np.testing.assert_array_equal(c, np.outer(na, na))
-    np.testing.assert_allclose(s, 3.0 * c[None, None])
+    np.testing.assert_allclose(s, np.broadcast_to(3.0 * c, s.shape))
     r = np.random.default_rng(3)
     x = r.normal(size=(2, 3, nc, nc))
     s, c = mo.bs_cylindrical(x, kpar, edges)
