@@ -54,7 +54,7 @@
 extern "C" {
 #endif
 
-#define BS_ABI_VERSION 6
+#define BS_ABI_VERSION 7
 
 typedef struct bs_plan_s *bs_plan;
 
@@ -260,6 +260,22 @@ bs_status bs_bs_monopole(bs_plan plan, const double *b3d_dev, const double *kper
                          const double *kpar_host, const double *k1_edges_host, int n_k1,
                          int n_mu, int n_t, double f_ng, double p_amp, double p_index,
                          double *sum_dev, int64_t *count_dev, void *cuda_stream);
+
+/* The 3D bispectrum of every closable ring triple binned on an n x n grid in
+ * the (k_par1, k_par2) plane (Section 5: the binning behind Fig. cylbs).
+ *  b3d_dev     double [batch][n_c][nchan][nchan] as bs_bs3d_closable writes it
+ *  kpar_host   double [nchan], strictly increasing: k_par of Eq. (dft) row
+ *              a + nchan/2
+ *  edges_host  double [n + 1] ascending, n <= 64; delay index a falls in bin
+ *              q when e_q <= kpar[a] < e_{q+1} (decided on the host in FP64)
+ *  sum_dev     double [batch][n_c][n][n]: sum over the (a, b) in bins (q, r)
+ *  count_dev   int64 [n][n]: number of those (a, b), the same for every plane
+ * Both outputs are overwritten; the binned value is sum / count.
+ * Errors: BS_ERR_ARG, BS_ERR_STATE (no counts yet), BS_ERR_UNSUPPORTED
+ * (nchan beyond the kernel's shared-memory row buffers, about 3000). */
+bs_status bs_bs_cylindrical(bs_plan plan, const double *b3d_dev, const double *kpar_host,
+                            const double *edges_host, int n, double *sum_dev,
+                            int64_t *count_dev, void *cuda_stream);
 
 /* Check V(-U) = conj V(U) on every binned cell of every channel and
  * realisation: |V(-U) - conj V(U)| <= tol * max|V| (synchronises).

@@ -27,14 +27,15 @@ STATUS = {0: "BS_OK", 1: "BS_ERR_ARG", 2: "BS_ERR_NO_DEVICE", 3: "BS_ERR_CUDA", 
 PREC_FP32 = 0
 PREC_SPLIT_BF16 = 1
 PREC_SPLIT_FP16 = 2
-ABI_VERSION = 6      # BS_ABI_VERSION of include/bs.h
+ABI_VERSION = 7      # BS_ABI_VERSION of include/bs.h
 MLP_FEATURES = 45    # BS_MLP_FEATURES of include/bs.h
 
 # every symbol declared in include/bs.h
 EXPORTS = ("bs_abi_version", "bs_plan_create", "bs_plan_destroy", "bs_last_error",
            "bs_plan_info", "bs_plan_trip_sides", "bs_plan_set_workspace", "bs_grid_load", "bs_counts", "bs_mabs",
            "bs_delta_reset", "bs_mabs_delta", "bs_bs3d", "bs_mabs_delta_closable",
-           "bs_bs3d_closable", "bs_plan_ring_umean", "bs_bs_monopole", "bs_check_hermitian",
+           "bs_bs3d_closable", "bs_plan_ring_umean", "bs_bs_monopole",
+           "bs_bs_cylindrical", "bs_check_hermitian",
            "bs_mc_create", "bs_mc_destroy", "bs_mc_last_error", "bs_mc_info", "bs_mc_set_input",
            "bs_mc_set_flags", "bs_mc_set_tuning", "bs_mc_autotune", "bs_mc_run", "bs_mc_reset",
            "bs_mc_stats",
@@ -284,6 +285,26 @@ class Plan:
             kz.ctypes.data_as(ctypes.c_void_p), ed.ctypes.data_as(ctypes.c_void_p), n_k1, n_mu, n_t,
             ctypes.c_double(f), ctypes.c_double(a), ctypes.c_double(pi), _dptr(sums), _dptr(cnt),
             _stream_ptr(stream)))
+        return sums, cnt
+
+    def bs_cylindrical(self, b3d, kpar, edges, stream=None):
+        """bs_bs_cylindrical: the closable 3D bispectrum binned on the (k_par1, k_par2)
+        grid of the given edges.  Returns (sums [batch, n_closable, n, n] float64 CUDA,
+        counts [n, n] int64 CUDA)."""
+        import numpy as np
+        import torch
+        kz = np.ascontiguousarray(np.asarray(kpar, np.float64))
+        ed = np.ascontiguousarray(np.asarray(edges, np.float64))
+        n = ed.size - 1
+        if kz.size != self.nchan:
+            raise ValueError("kpar needs nchan entries")
+        if b3d.dtype != torch.float64 or b3d.numel() != self.batch * self.n_closable * self.nchan ** 2:
+            raise ValueError("b3d must be float64 [batch, n_closable, nchan, nchan]")
+        sums = torch.empty((self.batch, self.n_closable, n, n), dtype=torch.float64, device="cuda")
+        cnt = torch.empty((n, n), dtype=torch.int64, device="cuda")
+        self._check(self._L.bs_bs_cylindrical(
+            self._h, _dptr(b3d), kz.ctypes.data_as(ctypes.c_void_p),
+            ed.ctypes.data_as(ctypes.c_void_p), n, _dptr(sums), _dptr(cnt), _stream_ptr(stream)))
         return sums, cnt
 
     def bs3d_closable(self, out, stream=None):

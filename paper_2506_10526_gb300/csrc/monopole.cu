@@ -24,6 +24,7 @@
 // flushing to the CTA's shared-memory histogram only when the bin changes
 // (neighbouring delay modes mostly share a bin).  The CTA then adds its
 // non-empty bins to the global sums with FP64 atomics.
+#include <algorithm>
 #include <cmath>
 #include <limits>
 #include <vector>
@@ -155,6 +156,44 @@ __global__ void __launch_bounds__(kThreads) k_bs_monopole(const MonoArgs a) {
   }
 }
 
+// The 3D bispectrum of each plane binned on an n x n grid in the (k_par1,
+// k_par2) plane (Section 5, the binning behind Fig. cylbs).  k_par grows with
+// the delay index, so every bin is a contiguous index range [seg[r].x,
+// seg[r].y); qa[a] is the bin of row a (-1 outside).  One CTA owns one
+// (plane, realisation): each warp stages a row in shared memory (coalesced),
+// lane r adds the row's range of column bin r into acc[qa[a]][r], and the
+// CTA writes its n x n sums with plain stores.
+constexpr int kCylWarps = 8;
+__global__ void __launch_bounds__(32 * kCylWarps) k_bs_cylindrical(
+    const double *__restrict__ b3d, long long bstride, int nc, int n, const int *__restrict__ qa,
+    const int2 *__restrict__ seg, double *__restrict__ sums) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double *acc = reinterpret_cast<double *>(smem_raw);  // [n][n]
+  double *rows = acc + n * n;                           // [kCylWarps][nc]
+  const int p = blockIdx.x, b = blockIdx.y, npl = gridDim.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int q = threadIdx.x; q < n * n; q += blockDim.x) acc[q] = 0.0;
+  __syncthreads();
+  const double *pl = b3d + (long long)b * bstride + (long long)p * nc * nc;
+  double *row = rows + (size_t)warp * nc;
+  for (int a = warp; a < nc; a += kCylWarps) {
+    const int q = qa[a];
+    if (q < 0) continue;  // warp-uniform
+    for (int c = lane; c < nc; c += 32) row[c] = pl[(long long)a * nc + c];
+    __syncwarp();
+    for (int r = lane; r < n; r += 32) {
+      const int2 sg = seg[r];
+      double v = 0.0;
+      for (int c = sg.x; c < sg.y; ++c) v += row[c];
+      atomicAdd(acc + q * n + r, v);
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  double *out = sums + ((long long)b * npl + p) * n * n;
+  for (int q = threadIdx.x; q < n * n; q += blockDim.x) out[q] = acc[q];
+}
+
 }  // namespace
 
 // Bytes of shared memory the kernel needs for nbatch realisations.
@@ -264,6 +303,60 @@ bs_status bs_bs_monopole(bs_plan p, const double *b3d, const double *kperp_host,
       k_bs_monopole<kMaxBatch><<<grid, kThreads, sm, s>>>(a);
     MONO_CUDA(cudaGetLastError());
   }
+  return BS_OK;
+}
+
+bs_status bs_bs_cylindrical(bs_plan p, const double *b3d, const double *kpar_host,
+                            const double *edges_host, int n, double *sum_dev, int64_t *count_dev,
+                            void *stream) {
+  using namespace bsi;
+  if (!p || !b3d || !kpar_host || !edges_host || !sum_dev || !count_dev)
+    return fail(p, BS_ERR_ARG, "bs_bs_cylindrical: NULL argument");
+  if (n < 1 || n > 64) return fail(p, BS_ERR_ARG, "bs_bs_cylindrical: n must be in [1, 64]");
+  for (int q = 0; q < n; ++q)
+    if (!(edges_host[q + 1] > edges_host[q]))
+      return fail(p, BS_ERR_ARG, "bs_bs_cylindrical: edges must be ascending");
+  for (int c = 1; c < p->nc; ++c)
+    if (!(kpar_host[c] > kpar_host[c - 1]))
+      return fail(p, BS_ERR_ARG, "bs_bs_cylindrical: k_par must grow with the delay index");
+  if (!p->counts_ready) return fail(p, BS_ERR_STATE, "bs_bs_cylindrical before the ring-triple counts");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  bs_status st = prepare(p, s);
+  if (st != BS_OK) return st;
+  const int nc = p->nc, npl = (int)p->clos.size();
+  // bins along one axis: q = (number of edges <= k_par) - 1, decided on the host
+  std::vector<int> &tab = p->cyl_tab;  // qa [nc], then seg [n] as (start, end)
+  tab.assign((size_t)nc + 2 * n, 0);
+  std::vector<long long> na(n, 0);
+  for (int r = 0; r < n; ++r) {
+    tab[nc + 2 * r] = nc;
+    tab[nc + 2 * r + 1] = nc;
+  }
+  for (int c = 0; c < nc; ++c) {
+    int q = (int)(std::upper_bound(edges_host, edges_host + n + 1, kpar_host[c]) - edges_host) - 1;
+    if (q >= n) q = -1;
+    tab[c] = q;
+    if (q >= 0) {
+      if (na[q]++ == 0) tab[nc + 2 * q] = c;
+      tab[nc + 2 * q + 1] = c + 1;
+    }
+  }
+  std::vector<long long> &cnt = p->cyl_cnt;
+  cnt.assign((size_t)n * n, 0);
+  for (int q = 0; q < n; ++q)
+    for (int r = 0; r < n; ++r) cnt[(size_t)q * n + r] = na[q] * na[r];
+  MONO_CUDA(cudaMemcpyAsync(count_dev, cnt.data(), cnt.size() * sizeof(long long),
+                            cudaMemcpyHostToDevice, s));
+  if (npl == 0) return BS_OK;
+  int *dtab = p->at<int>(p->L.cyl);
+  MONO_CUDA(cudaMemcpyAsync(dtab, tab.data(), tab.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  const size_t sm = ((size_t)n * n + (size_t)kCylWarps * nc) * sizeof(double);
+  if (sm > (size_t)200 * 1024)
+    return fail(p, BS_ERR_UNSUPPORTED, "bs_bs_cylindrical: nchan too large for the row buffers");
+  MONO_CUDA(smem_optin_once<k_bs_cylindrical>());
+  k_bs_cylindrical<<<dim3(npl, p->batch), 32 * kCylWarps, sm, s>>>(
+      b3d, (long long)npl * nc * nc, nc, n, dtab, reinterpret_cast<const int2 *>(dtab + nc), sum_dev);
+  MONO_CUDA(cudaGetLastError());
   return BS_OK;
 }
 

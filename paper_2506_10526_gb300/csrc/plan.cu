@@ -142,6 +142,7 @@ void compute_layout(bs_plan p) {
   L.closrings = take((size_t)p->ntrip * 3 * sizeof(int));
   // monopole binning constants: kperp [nb], kpar [nc], k1 edges [<= 1025]
   L.mono = take(((size_t)p->nb + p->nc + 1025) * sizeof(double));
+  L.cyl = take(((size_t)p->nc + 2 * 64) * sizeof(int));  // cylindrical bins (n <= 64)
   L.total = o;
 }
 

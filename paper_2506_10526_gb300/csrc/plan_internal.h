@@ -12,7 +12,7 @@ namespace bsi {
 
 struct WsLayout {
   size_t label, efflabel, cells, uext, tripof, valid, twM, twN, tnorm, T, nnu, cols, ptiles, tctiles,
-      G, F, Fhi, Flo, dsum, tmp3d, herm, err, maps, tcgroup, mlptab, ztrips, clos, closrings, mono, total;
+      G, F, Fhi, Flo, dsum, tmp3d, herm, err, maps, tcgroup, mlptab, ztrips, clos, closrings, mono, cyl, total;
 };
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
@@ -59,6 +59,8 @@ struct bs_plan_s {
   std::vector<int> clos;          // ring triples with T > 0, ascending (device copy at L.clos)
   std::vector<int> closrings;     // [clos.size()][3] rings (i, j, l) of those triples
   std::vector<float> mono_tab;    // FP32 k tables of the last monopole call
+  std::vector<int> cyl_tab;       // row bins and column ranges of the last cylindrical call
+  std::vector<long long> cyl_cnt; // its per-bin counts
   std::vector<int> trips;        // [ntrip][3]
   std::vector<int> trip_of;      // [nb^3] -> trip index of sorted (i<=j<=l), else -1
   std::vector<long long> T;      // [ntrip] closed-triangle counts
