@@ -271,8 +271,7 @@ bs_status bs_bs_monopole(bs_plan plan, const double *b3d_dev, const double *kper
  *  sum_dev     double [batch][n_c][n][n]: sum over the (a, b) in bins (q, r)
  *  count_dev   int64 [n][n]: number of those (a, b), the same for every plane
  * Both outputs are overwritten; the binned value is sum / count.
- * Errors: BS_ERR_ARG, BS_ERR_STATE (no counts yet), BS_ERR_UNSUPPORTED
- * (nchan beyond the kernel's shared-memory row buffers, about 3000). */
+ * Errors: BS_ERR_ARG, BS_ERR_STATE (no counts yet). */
 bs_status bs_bs_cylindrical(bs_plan plan, const double *b3d_dev, const double *kpar_host,
                             const double *edges_host, int n, double *sum_dev,
                             int64_t *count_dev, void *cuda_stream);

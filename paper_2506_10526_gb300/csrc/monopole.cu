@@ -158,40 +158,86 @@ __global__ void __launch_bounds__(kThreads) k_bs_monopole(const MonoArgs a) {
 
 // The 3D bispectrum of each plane binned on an n x n grid in the (k_par1,
 // k_par2) plane (Section 5, the binning behind Fig. cylbs).  k_par grows with
-// the delay index, so every bin is a contiguous index range [seg[r].x,
-// seg[r].y); qa[a] is the bin of row a (-1 outside).  One CTA owns one
-// (plane, realisation): each warp stages a row in shared memory (coalesced),
-// lane r adds the row's range of column bin r into acc[qa[a]][r], and the
-// CTA writes its n x n sums with plain stores.
-constexpr int kCylWarps = 8;
-__global__ void __launch_bounds__(32 * kCylWarps) k_bs_cylindrical(
+// the delay index, so the bins of rows (and of columns) are contiguous index
+// ranges; qa[a] is the bin of index a (-1 outside), seg[r] the index range
+// of bin r.  One CTA owns one (plane, realisation) and each thread CPT
+// columns: walking the rows in order, a thread keeps running column sums in
+// registers while the row bin stays the same.  When it changes (the same
+// row for the whole CTA), the threads write their column sums to a shared
+// row buffer and thread r adds bin r's range of it to acc[q][r]: no atomics.
+// Loads are coalesced row segments.  The rows of a plane are split over
+// gridDim.z CTAs, which add their n x n partial sums into the (zeroed)
+// output.
+constexpr int kCylThreads = 256;
+template <int CPT>
+__global__ void __launch_bounds__(kCylThreads) k_bs_cylindrical(
     const double *__restrict__ b3d, long long bstride, int nc, int n, const int *__restrict__ qa,
     const int2 *__restrict__ seg, double *__restrict__ sums) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double *acc = reinterpret_cast<double *>(smem_raw);  // [n][n]
-  double *rows = acc + n * n;                           // [kCylWarps][nc]
+  double *colsum = acc + n * n;                         // [nc]
   const int p = blockIdx.x, b = blockIdx.y, npl = gridDim.x;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rows = (nc + gridDim.z - 1) / gridDim.z;
+  const int ra = blockIdx.z * rows, rb = min(nc, ra + rows);
   for (int q = threadIdx.x; q < n * n; q += blockDim.x) acc[q] = 0.0;
   __syncthreads();
   const double *pl = b3d + (long long)b * bstride + (long long)p * nc * nc;
-  double *row = rows + (size_t)warp * nc;
-  for (int a = warp; a < nc; a += kCylWarps) {
-    const int q = qa[a];
-    if (q < 0) continue;  // warp-uniform
-    for (int c = lane; c < nc; c += 32) row[c] = pl[(long long)a * nc + c];
-    __syncwarp();
-    for (int r = lane; r < n; r += 32) {
-      const int2 sg = seg[r];
-      double v = 0.0;
-      for (int c = sg.x; c < sg.y; ++c) v += row[c];
-      atomicAdd(acc + q * n + r, v);
-    }
-    __syncwarp();
+  int qc[CPT];
+  double run[CPT];
+#pragma unroll
+  for (int k = 0; k < CPT; ++k) {
+    const int c = threadIdx.x + k * kCylThreads;
+    qc[k] = c < nc ? qa[c] : -1;
+    run[k] = 0.0;
   }
+  int qcur = -1;
+  auto flush = [&]() {  // CTA-uniform: every thread sees the same row bins
+    if (qcur >= 0) {
+#pragma unroll
+      for (int k = 0; k < CPT; ++k)
+        if (qc[k] >= 0) colsum[threadIdx.x + k * kCylThreads] = run[k];
+      __syncthreads();
+      for (int r = threadIdx.x; r < n; r += blockDim.x) {
+        const int2 sg = seg[r];
+        double v = 0.0;
+        for (int c = sg.x; c < sg.y; ++c) v += colsum[c];
+        acc[qcur * n + r] += v;
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int k = 0; k < CPT; ++k) run[k] = 0.0;
+  };
+  constexpr int U = 8;  // rows loaded ahead
+  for (int a0 = ra; a0 < rb; a0 += U) {
+    double v[U][CPT];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int a = a0 + u;
+      const bool rowok = a < rb && qa[a] >= 0;
+#pragma unroll
+      for (int k = 0; k < CPT; ++k)
+        v[u][k] = (rowok && qc[k] >= 0) ? pl[(long long)a * nc + threadIdx.x + k * kCylThreads] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int a = a0 + u;
+      if (a >= rb) break;
+      const int q = qa[a];
+      if (q != qcur) {
+        flush();
+        qcur = q;
+      }
+      if (q < 0) continue;
+#pragma unroll
+      for (int k = 0; k < CPT; ++k) run[k] += v[u][k];
+    }
+  }
+  flush();
   __syncthreads();
   double *out = sums + ((long long)b * npl + p) * n * n;
-  for (int q = threadIdx.x; q < n * n; q += blockDim.x) out[q] = acc[q];
+  for (int q = threadIdx.x; q < n * n; q += blockDim.x)
+    if (acc[q] != 0.0) atomicAdd(out + q, acc[q]);
 }
 
 }  // namespace
@@ -328,10 +374,6 @@ bs_status bs_bs_cylindrical(bs_plan p, const double *b3d, const double *kpar_hos
   std::vector<int> &tab = p->cyl_tab;  // qa [nc], then seg [n] as (start, end)
   tab.assign((size_t)nc + 2 * n, 0);
   std::vector<long long> na(n, 0);
-  for (int r = 0; r < n; ++r) {
-    tab[nc + 2 * r] = nc;
-    tab[nc + 2 * r + 1] = nc;
-  }
   for (int c = 0; c < nc; ++c) {
     int q = (int)(std::upper_bound(edges_host, edges_host + n + 1, kpar_host[c]) - edges_host) - 1;
     if (q >= n) q = -1;
@@ -350,12 +392,22 @@ bs_status bs_bs_cylindrical(bs_plan p, const double *b3d, const double *kpar_hos
   if (npl == 0) return BS_OK;
   int *dtab = p->at<int>(p->L.cyl);
   MONO_CUDA(cudaMemcpyAsync(dtab, tab.data(), tab.size() * sizeof(int), cudaMemcpyHostToDevice, s));
-  const size_t sm = ((size_t)n * n + (size_t)kCylWarps * nc) * sizeof(double);
-  if (sm > (size_t)200 * 1024)
-    return fail(p, BS_ERR_UNSUPPORTED, "bs_bs_cylindrical: nchan too large for the row buffers");
-  MONO_CUDA(smem_optin_once<k_bs_cylindrical>());
-  k_bs_cylindrical<<<dim3(npl, p->batch), 32 * kCylWarps, sm, s>>>(
-      b3d, (long long)npl * nc * nc, nc, n, dtab, reinterpret_cast<const int2 *>(dtab + nc), sum_dev);
+  const size_t sm = ((size_t)n * n + nc) * sizeof(double);
+  MONO_CUDA(smem_optin_once<k_bs_cylindrical<16>>());
+  MONO_CUDA(cudaMemsetAsync(sum_dev, 0, (size_t)p->batch * npl * n * n * sizeof(double), s));
+  const dim3 grid(npl, p->batch, 2);  // two row ranges per plane
+  const int2 *seg = reinterpret_cast<const int2 *>(dtab + nc);
+  const long long bst = (long long)npl * nc * nc;
+  if (nc <= kCylThreads)
+    k_bs_cylindrical<1><<<grid, kCylThreads, sm, s>>>(b3d, bst, nc, n, dtab, seg, sum_dev);
+  else if (nc <= 2 * kCylThreads)
+    k_bs_cylindrical<2><<<grid, kCylThreads, sm, s>>>(b3d, bst, nc, n, dtab, seg, sum_dev);
+  else if (nc <= 3 * kCylThreads)
+    k_bs_cylindrical<3><<<grid, kCylThreads, sm, s>>>(b3d, bst, nc, n, dtab, seg, sum_dev);
+  else if (nc <= 8 * kCylThreads)
+    k_bs_cylindrical<8><<<grid, kCylThreads, sm, s>>>(b3d, bst, nc, n, dtab, seg, sum_dev);
+  else
+    k_bs_cylindrical<16><<<grid, kCylThreads, sm, s>>>(b3d, bst, nc, n, dtab, seg, sum_dev);
   MONO_CUDA(cudaGetLastError());
   return BS_OK;
 }
