@@ -30,6 +30,9 @@ reordering beyond what the definition states:
 * ``analytic_mabs``    exact ensemble mean of the estimator for the Eq. (mb1)
                        test field on a periodic box (first-order term of
                        Eq. bsana plus the f_NG^3 loop term).
+* ``gridding``         (module) nearest-grid-point gridding of raw
+                       visibilities (Eq. vg) with the Hermitian mirror, and
+                       the channel pre-averaging of Section 4.
 * ``monopole``         (module) the 3D bispectrum monopole binned in triangle
                        size and shape: Eq. (shape), Eq. (bs_lm) at l = m = 0
                        and the (k1, mu, t) binning of Section 5, for
