@@ -54,7 +54,7 @@
 extern "C" {
 #endif
 
-#define BS_ABI_VERSION 7
+#define BS_ABI_VERSION 8
 
 typedef struct bs_plan_s *bs_plan;
 
@@ -221,6 +221,29 @@ bs_status bs_bs3d(bs_plan plan, double *out_dev, void *cuda_stream);
  * Errors: as bs_mabs_delta / bs_bs3d. */
 bs_status bs_mabs_delta_closable(bs_plan plan, double *out_dev, void *cuda_stream);
 bs_status bs_bs3d_closable(bs_plan plan, double *out_dev, void *cuda_stream);
+
+/* Eq. (vg): nearest-grid-point gridding of raw visibilities onto the plan's
+ * N_t x N_t grid, with channel pre-averaging (Section 4).  Visibility
+ * (baseline i, input channel c) goes to the cell g = (floor(u_i + 1/2),
+ * floor(v_i + 1/2)) (FP64) and, the sky being real, its conjugate to -g;
+ * cells with |u| or |v| >= N_t/2 are dropped; input channel c feeds output
+ * channel c / avg; flagged data (F = 0) are skipped.
+ *  uv_dev       double [nbl][2]: baseline (u, v) in grid units
+ *  vis_dev      complex64 [nbl][nchan_in]
+ *  flag_dev     uint8 [nbl][nchan_in], 1 = flagged, or NULL
+ *  nchan_in     avg * nchan of the plan
+ *  mode 0       out_vis = V_g (sum), out_ng = N_g (count), as Eq. (vg)
+ *  mode 1       out_vis = V_g / N_g, out_ng = 1 where N_g > 0 (else both 0):
+ *               the input of bs_grid_load that applies the per-channel
+ *               weight 1 / N_g(nu) of Eq. (vg)
+ *  out_vis_dev  complex64 [nchan][N_t][N_t], centred, row index v (the
+ *               layout bs_grid_load reads), overwritten
+ *  out_ng_dev   float [nchan][N_t][N_t], overwritten
+ * FP32 atomic sums (their order varies between runs).
+ * Errors: BS_ERR_ARG (NULL, nchan_in != avg * nchan, mode). */
+bs_status bs_grid_visibilities(bs_plan plan, const double *uv_dev, const void *vis_dev,
+                               const uint8_t *flag_dev, int64_t nbl, int nchan_in, int avg,
+                               int mode, void *out_vis_dev, float *out_ng_dev, void *cuda_stream);
 
 /* Mean |U| of each ring's binned grid cells, in grid units (the mid point of
  * the ring's edges when it holds no cell): U_m in k_perp = 2 pi U_m / r.

@@ -27,14 +27,14 @@ STATUS = {0: "BS_OK", 1: "BS_ERR_ARG", 2: "BS_ERR_NO_DEVICE", 3: "BS_ERR_CUDA", 
 PREC_FP32 = 0
 PREC_SPLIT_BF16 = 1
 PREC_SPLIT_FP16 = 2
-ABI_VERSION = 7      # BS_ABI_VERSION of include/bs.h
+ABI_VERSION = 8      # BS_ABI_VERSION of include/bs.h
 MLP_FEATURES = 45    # BS_MLP_FEATURES of include/bs.h
 
 # every symbol declared in include/bs.h
 EXPORTS = ("bs_abi_version", "bs_plan_create", "bs_plan_destroy", "bs_last_error",
            "bs_plan_info", "bs_plan_trip_sides", "bs_plan_set_workspace", "bs_grid_load", "bs_counts", "bs_mabs",
            "bs_delta_reset", "bs_mabs_delta", "bs_bs3d", "bs_mabs_delta_closable",
-           "bs_bs3d_closable", "bs_plan_ring_umean", "bs_bs_monopole",
+           "bs_bs3d_closable", "bs_grid_visibilities", "bs_plan_ring_umean", "bs_bs_monopole",
            "bs_bs_cylindrical", "bs_check_hermitian",
            "bs_mc_create", "bs_mc_destroy", "bs_mc_last_error", "bs_mc_info", "bs_mc_set_input",
            "bs_mc_set_flags", "bs_mc_set_tuning", "bs_mc_autotune", "bs_mc_run", "bs_mc_reset",
@@ -252,6 +252,24 @@ class Plan:
         """bs_mabs_delta_closable: out float64 CUDA [batch, n_closable, 2nc-1, 2nc-1], the
         closable ring triples in ascending index."""
         self._check(self._L.bs_mabs_delta_closable(self._h, _dptr(out), _stream_ptr(stream)))
+
+    def grid_visibilities(self, uv, vis, flags=None, avg=1, mode=0, stream=None):
+        """bs_grid_visibilities (Eq. vg): uv float64 CUDA [nbl, 2] in grid units, vis
+        complex64 CUDA [nbl, avg * nchan], flags uint8 CUDA or None.  Returns
+        (vis_g complex64 [nchan, nt, nt], n_g float32 [nchan, nt, nt]); mode 1 gives the
+        per-channel mean and a 0/1 occupancy for grid_load."""
+        import torch
+        nbl = int(vis.shape[0])
+        if (uv.dtype != torch.float64 or tuple(uv.shape) != (nbl, 2) or vis.dtype != torch.complex64
+                or vis.dim() != 2 or (flags is not None and (flags.dtype != torch.uint8
+                                                             or flags.shape != vis.shape))):
+            raise ValueError("uv float64 [nbl, 2], vis complex64 [nbl, nchan_in], flags uint8")
+        out = torch.empty((self.nchan, self.nt, self.nt), dtype=torch.complex64, device="cuda")
+        ng = torch.empty((self.nchan, self.nt, self.nt), dtype=torch.float32, device="cuda")
+        self._check(self._L.bs_grid_visibilities(
+            self._h, _dptr(uv), _dptr(vis), _dptr(flags), ctypes.c_int64(nbl), int(vis.shape[1]),
+            int(avg), int(mode), _dptr(out), _dptr(ng), _stream_ptr(stream)))
+        return out, ng
 
     def ring_umean(self):
         """bs_plan_ring_umean: mean |U| of each ring's cells (numpy float64 [nbins])."""
