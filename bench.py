@@ -298,6 +298,41 @@ def run_monopole(plan, b3, stream, nc, reps=5):
                     "(FP64 pow per sample)"}
 
 
+def run_gridding(plan, nt, nc, stream, reps=5):
+    """Eq. (vg) gridding (bs_grid_visibilities) of 8128 baselines (a 128-antenna
+    array) x nc channels onto the plan's grid, 15% of the data flagged, CUDA
+    events on the launching stream.  Algorithmic bytes: the visibilities,
+    flags and coordinates read once, the output grid written once."""
+    import numpy as np
+    import torch
+    nbl = 8128
+    r = np.random.default_rng(5)
+    uv = torch.from_numpy(r.uniform(-0.5 * nt + 1, 0.5 * nt - 1, size=(nbl, 2))).cuda()
+    g = torch.Generator(device="cuda").manual_seed(6)
+    vis = torch.complex(torch.randn((nbl, nc), device="cuda", generator=g),
+                        torch.randn((nbl, nc), device="cuda", generator=g))
+    flags = (torch.rand((nbl, nc), device="cuda", generator=g) < 0.15).to(torch.uint8)
+    for _ in range(3):
+        out = plan.grid_visibilities(uv, vis, flags)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for _ in range(reps):
+        out = plan.grid_visibilities(uv, vis, flags)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    ms = ev[0].elapsed_time(ev[1]) / reps
+    nv = nbl * nc
+    nbytes = nv * (8 + 1) + nbl * 16 + nc * nt * nt * (8 + 4)
+    gbs = nbytes / (ms / 1e3) / 1e9
+    peak = float(measured_peaks().get("hbm_gbs", 6800.0))
+    del out
+    return {"baselines": nbl, "channels": nc, "visibilities_per_s": nv / (ms / 1e3), "ms": ms,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                         "frac": gbs / peak, "bytes": nbytes},
+            "note": "memsets of the output grid + k_grid_vis (6 FP32 atomics per visibility)"}
+
+
 def run_e2e(args, step_e2e, vis_h, vis_d, out3d, stream, world, dev, barrier):
     """End-to-end throughput through the C ABI from host memory.  Every step
     copies its visibilities host->device (pinned) and reads its 3D bispectrum
@@ -631,6 +666,7 @@ def main():
     }
     if mono is not None:
         line["monopole"] = mono
+        line["gridding"] = run_gridding(plan, nt, nc, stream)
     line["config"]["stated_error"] = STATED_ERROR[args.precision]
     contraction_rate = per_launch_evals / (avg_ms / 1e3)
     line["contraction_evals_per_s"] = contraction_rate
