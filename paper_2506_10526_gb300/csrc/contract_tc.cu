@@ -783,21 +783,30 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
       if (lane == 0 && ok) mbar_arrive_cluster(acc_empty_lead);
       asm volatile("bar.sync 1, 256;" ::: "memory");
       if (use_red && ok) {
+        // in the order of the (d1, d2) plane: entry (dd, e2) of a segment sits at
+        // d1 = dd + e2 + const, d2 = e2 + const, so plane row r = dd + e2 holds the
+        // contiguous run e2 in [max(0, r - (P1 + P2 - 2)), min(E - 1, r)].  One warp
+        // per row: coalesced FP64 atomics, a few sectors per row instead of one per
+        // entry (walking the buffer linearly would step along a diagonal of the plane)
         const int ns = *nseg_s;
-        for (int q = ptid; q < total; q += 256) {
-          const float v = red[q];
-          if (v == 0.f) continue;
-          int sg = 0;
-          while (sg + 1 < ns && seginfo[sg + 1].x <= q) ++sg;
-          const int4 si = seginfo[sg];
-          const int off = q - si.x;
-          const int dd = off / si.y, e2 = off - dd * si.y;
-          const int d = dd - (P2 - 1) + t.nu1_0 - t.nu2_0;  // nu1 - nu2
-          const int d2 = e2 + t.nu2_0 - si.w;                // nu2 - nu3
-          const int d1 = d + d2;
-          const long long o = (long long)b * G.dsum_bstride +
-                              ((long long)si.z * n2 + (d1 + G.nc - 1)) * n2 + (d2 + G.nc - 1);
-          atomicAdd(G.dsum + o, F16 ? (double)v * segscale[sg] : (double)v);
+        for (int sg = 0; sg < ns; ++sg) {
+          const int4 si = seginfo[sg];  // (base, E, trip, hi)
+          const int E = si.y;
+          const double sc = F16 ? segscale[sg] : 1.0;
+          const int d1base = t.nu1_0 - (P2 - 1) - si.w + G.nc - 1;  // d1 index = dd + e2 + d1base
+          const int d2base = t.nu2_0 - si.w + G.nc - 1;             // d2 index = e2 + d2base
+          double *plane = G.dsum + (long long)b * G.dsum_bstride + (long long)si.z * n2 * n2;
+          const float *rs = red + si.x;
+          const int nrow = (P1 + P2 - 1) + E - 1;
+          for (int r = pw; r < nrow; r += NPROD) {
+            const int e2lo = max(0, r - (P1 + P2 - 2)), e2hi = min(E - 1, r);
+            const long long row = (long long)(r + d1base) * n2;
+            for (int e2 = e2lo + lane; e2 <= e2hi; e2 += 32) {
+              const float v = rs[(r - e2) * E + e2];
+              if (v == 0.f) continue;
+              atomicAdd(plane + row + (e2 + d2base), F16 ? (double)v * sc : (double)v);
+            }
+          }
         }
       }
       asm volatile("bar.sync 1, 256;" ::: "memory");
