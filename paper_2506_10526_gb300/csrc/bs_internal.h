@@ -17,7 +17,7 @@ struct Radices {
   int r[24] = {0};
 };
 
-// n = 4^a 2^b 3^c 5^d: the Stockham stage radices (4s first, then 2, 3, 5);
+// n = 8^a 4^b 2^c 3^d 5^e: the Stockham stage radices (8s first, then 4, 2, 3, 5);
 // false when n has another prime factor.
 bool factor_radices(int n, Radices &r);
 // exp(+2 pi i t / n), t in [0, n), computed in FP64 and rounded to FP32.

@@ -1,4 +1,4 @@
-// Shared-memory Stockham autosort FFT (radix 4, 2, 3, 5), FP32, used by the
+// Shared-memory Stockham autosort FFT (radix 8, 4, 2, 3, 5), FP32, used by the
 // image-plane field kernels (Eq. iFT) and by the delay transform (Eq. dft).
 //
 // Formulation: for a length-N transform with radices R_1 ... R_s and
@@ -43,6 +43,28 @@ __device__ __forceinline__ void butterfly<4>(float2 *u, float sign) {
   u[2] = csub(s02, s13);
   u[1] = cadd(d02, d13);
   u[3] = csub(d02, d13);
+}
+
+// Radix 8 as two radix-4 DFTs of the even and odd inputs, combined with
+// w^k, w = exp(sign 2 pi i / 8): w = sqrt(1/2) (1 + sign i), w^2 = sign i,
+// w^3 = sqrt(1/2) (-1 + sign i).
+template <>
+__device__ __forceinline__ void butterfly<8>(float2 *u, float sign) {
+  float2 e[4] = {u[0], u[2], u[4], u[6]}, o[4] = {u[1], u[3], u[5], u[7]};
+  butterfly<4>(e, sign);
+  butterfly<4>(o, sign);
+  const float h = 0.70710678118654752440f;
+  const float2 o1 = make_float2(h * (o[1].x - sign * o[1].y), h * (o[1].y + sign * o[1].x));
+  const float2 o2 = cmuli(o[2], sign);
+  const float2 o3 = make_float2(h * (-o[3].x - sign * o[3].y), h * (sign * o[3].x - o[3].y));
+  u[0] = cadd(e[0], o[0]);
+  u[4] = csub(e[0], o[0]);
+  u[1] = cadd(e[1], o1);
+  u[5] = csub(e[1], o1);
+  u[2] = cadd(e[2], o2);
+  u[6] = csub(e[2], o2);
+  u[3] = cadd(e[3], o3);
+  u[7] = csub(e[3], o3);
 }
 
 template <>
@@ -132,6 +154,7 @@ __device__ __forceinline__ float2 *stockham(float2 *x, float2 *y, int nrows, int
   for (int s = 0; s < rad.n; ++s) {
     const int R = rad.r[s];
     switch (R) {
+      case 8: stockham_stage<8>(x, y, nrows, N, ld, p, tw, sign); break;
       case 4: stockham_stage<4>(x, y, nrows, N, ld, p, tw, sign); break;
       case 2: stockham_stage<2>(x, y, nrows, N, ld, p, tw, sign); break;
       case 3: stockham_stage<3>(x, y, nrows, N, ld, p, tw, sign); break;

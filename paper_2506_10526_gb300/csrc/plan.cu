@@ -33,6 +33,10 @@ bool factor_radices(int n, Radices &r) {
   r.n = 0;
   if (n <= 0) return false;
   int m = n;
+  while (m % 8 == 0 && r.n < 24) {
+    r.r[r.n++] = 8;
+    m /= 8;
+  }
   while (m % 4 == 0 && r.n < 24) {
     r.r[r.n++] = 4;
     m /= 4;
