@@ -71,3 +71,17 @@ def test_null_handles(lib):
     assert lib.bs_plan_destroy(None) == 0
     assert lib.bs_grid_load(None, None, None, None, None) == 1
     assert lib.bs_mabs(None, None, None, 0, None) == 1
+
+
+def test_null_handles_of_the_output_and_analysis_entry_points(lib):
+    """Every entry point added for the closable layouts, the binning and the
+    gridding refuses a NULL plan with BS_ERR_ARG before touching a device."""
+    d = ctypes.c_double(0.0)
+    assert lib.bs_mabs_delta_closable(None, None, None) == 1
+    assert lib.bs_bs3d_closable(None, None, None) == 1
+    assert lib.bs_plan_ring_umean(None, None) == 1
+    assert lib.bs_bs_monopole(None, None, None, None, None, 12, 5, 5, d, d, d, None, None,
+                              None) == 1
+    assert lib.bs_bs_cylindrical(None, None, None, None, 20, None, None, None) == 1
+    assert lib.bs_grid_visibilities(None, None, None, None, ctypes.c_int64(0), 4, 4, 0, None,
+                                    None, None) == 1
