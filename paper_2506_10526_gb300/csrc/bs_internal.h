@@ -161,8 +161,9 @@ cudaError_t launch_full_finalize(double *out, long long bstride, int batch, int 
 cudaError_t launch_delta_norm(const double *dsum, const long long *nnu, const double *tnorm,
                               double *out, int batch, int ntrip, int nc, const int *list,
                               int nlist, cudaStream_t s);
+// box = {row_lo, row_hi, col_lo, col_hi} (inclusive plane indices) to zero
 cudaError_t launch_zero_planes(double *dsum, const int *trips, int ntr, int batch, int ntrip,
-                               long long plane, cudaStream_t s);
+                               int n2, const int *box, cudaStream_t s);
 // tmp: batch * ntrip * nc^2 float2 followed by nc^2 doubles of scratch
 cudaError_t launch_bs3d(const double *dsum, const long long *nnu, const double *tnorm,
                         float2 *tmp, double *out, int batch, int ntrip, int nc,

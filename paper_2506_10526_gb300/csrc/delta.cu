@@ -48,25 +48,31 @@ __global__ void k_delta_norm(const double *__restrict__ dsum, const long long *_
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < half;
        t += (long long)gridDim.x * blockDim.x) {
     const long long j = plane - 1 - t;
-    double s = ds[t];
     long long c = nnu[t];
-    if (j != t) {
-      s += ds[j];
-      c += nnu[j];
+    if (j != t) c += nnu[j];
+    double v = nan;
+    if (c > 0) {  // unsampled separations hold no sums: their reads are skipped
+      double s = ds[t];
+      if (j != t) s += ds[j];
+      v = s * tn / (double)c;
     }
-    const double v = c > 0 ? s * tn / (double)c : nan;
     o[t] = v;
     o[j] = v;
   }
 }
 
+// Zero rows [r0, r0 + nr) x columns [c0, c0 + ncol) of the (2nc-1)^2 plane of each
+// listed ring triple: the separations accumulated since the last reset.
 __global__ void k_zero_planes(double *__restrict__ dsum, const int *__restrict__ trips, int ntr,
-                              int ntrip, long long plane) {
+                              int ntrip, int n2, int r0, int nr, int c0, int ncol) {
   const int k = blockIdx.y, b = blockIdx.z;
-  double *o = dsum + ((long long)b * ntrip + trips[k]) * plane;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < plane;
-       t += (long long)gridDim.x * blockDim.x)
-    o[t] = 0.0;
+  double *o = dsum + ((long long)b * ntrip + trips[k]) * (long long)n2 * n2;
+  const long long n = (long long)nr * ncol;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(t / ncol), c = (int)(t - (long long)r * ncol);
+    o[(long long)(r0 + r) * n2 + c0 + c] = 0.0;
+  }
 }
 
 __device__ void dft_direct(const float2 *x, float2 *y, int N, const float2 *tw, float sign) {
@@ -131,9 +137,13 @@ __global__ void k_bs3d_rows(const double *__restrict__ dsum, const double *__res
     // each (nidx, m) of the periodic placement being exactly one of them
     const int np = (2 * nidx < nc) ? nidx : nidx - nc, mp = (2 * m < nc) ? m : m - nc;
     const int i1 = np + nc - 1, i2 = mp + nc - 1, j1 = n2 - 1 - i1, j2 = n2 - 1 - i2;
-    double sv = ds[(long long)i1 * n2 + i2];
-    if (j1 != i1 || j2 != i2) sv += ds[(long long)j1 * n2 + j2];
-    const double acc = sv * (tn * rinv[(long long)nidx * nc + m]);  // 0 where unsampled
+    const double ri = rinv[(long long)nidx * nc + m];
+    double acc = 0.0;  // unsampled separations contribute nothing and are not read
+    if (ri != 0.0) {
+      double sv = ds[(long long)i1 * n2 + i2];
+      if (j1 != i1 || j2 != i2) sv += ds[(long long)j1 * n2 + j2];
+      acc = sv * (tn * ri);
+    }
     bufA[r * LD + m] = make_float2((float)acc, 0.f);
   }
   __syncthreads();
@@ -243,10 +253,12 @@ cudaError_t launch_delta_norm(const double *dsum, const long long *nnu, const do
 }
 
 cudaError_t launch_zero_planes(double *dsum, const int *trips, int ntr, int batch, int ntrip,
-                               long long plane, cudaStream_t s) {
-  if (ntr == 0) return cudaSuccess;
-  dim3 grid((unsigned)std::min<long long>((plane + 255) / 256, 256), ntr, batch);
-  k_zero_planes<<<grid, 256, 0, s>>>(dsum, trips, ntr, ntrip, plane);
+                               int n2, const int *box, cudaStream_t s) {
+  const int nr = box[1] - box[0] + 1, ncol = box[3] - box[2] + 1;
+  if (ntr == 0 || nr <= 0 || ncol <= 0) return cudaSuccess;
+  const long long n = (long long)nr * ncol;
+  dim3 grid((unsigned)std::min<long long>((n + 255) / 256, 256), ntr, batch);
+  k_zero_planes<<<grid, 256, 0, s>>>(dsum, trips, ntr, ntrip, n2, box[0], nr, box[2], ncol);
   return cudaGetLastError();
 }
 

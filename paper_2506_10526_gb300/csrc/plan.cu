@@ -393,6 +393,19 @@ void add_block_sampling(int nc, const std::vector<uint8_t> &valid, const int *bl
 void accumulate_block_nnu(bs_plan p, const int *blk) {
   add_block_sampling(p->nc, p->valid, blk, p->nnu.data());
   p->nnu_dirty = true;
+  // the separations this block can write: d = nu - nu3, nu in the block's
+  // nu1 (nu2) range, nu3 in its nu3 range
+  const int nc = p->nc;
+  const int r0 = std::max(0, blk[0] - blk[5] + 1 + nc - 1), r1 = std::min(2 * nc - 2, blk[1] - 1 - blk[4] + nc - 1);
+  const int c0 = std::max(0, blk[2] - blk[5] + 1 + nc - 1), c1 = std::min(2 * nc - 2, blk[3] - 1 - blk[4] + nc - 1);
+  if (r0 > r1 || c0 > c1) return;
+  int *b = p->dbox;
+  if (b[1] < b[0] || b[3] < b[2]) {
+    b[0] = r0; b[1] = r1; b[2] = c0; b[3] = c1;
+  } else {
+    b[0] = std::min(b[0], r0); b[1] = std::max(b[1], r1);
+    b[2] = std::min(b[2], c0); b[3] = std::max(b[3], c1);
+  }
 }
 
 bs_status upload_nnu(bs_plan p, cudaStream_t s) {
@@ -412,6 +425,7 @@ bs_status delta_reset(bs_plan p, cudaStream_t s) {
     BS_CUDA(cudaMemsetAsync(p->at<double>(p->L.dsum), 0,
                             (size_t)p->batch * p->ntrip * n2 * n2 * sizeof(double), s));
     p->dsum_clean = p->counts_ready;
+    p->dbox[0] = 0; p->dbox[1] = -1; p->dbox[2] = 0; p->dbox[3] = -1;
     p->zero_trips.clear();
     for (int t = 0; t < p->ntrip; ++t)
       if (p->counts_ready && p->T[t] > 0) p->zero_trips.push_back(t);
@@ -420,9 +434,11 @@ bs_status delta_reset(bs_plan p, cudaStream_t s) {
                               p->zero_trips.size() * sizeof(int), cudaMemcpyHostToDevice, s));
     return BS_OK;
   }
-  // only ring triples with closed triangles are ever accumulated into
+  // only ring triples with closed triangles are ever accumulated into, and only
+  // at the separations of the blocks accumulated since the last reset
   BS_CUDA(launch_zero_planes(p->at<double>(p->L.dsum), p->at<int>(p->L.ztrips),
-                             (int)p->zero_trips.size(), p->batch, p->ntrip, (long long)(n2 * n2), s));
+                             (int)p->zero_trips.size(), p->batch, p->ntrip, (int)n2, p->dbox, s));
+  p->dbox[0] = 0; p->dbox[1] = -1; p->dbox[2] = 0; p->dbox[3] = -1;
   return BS_OK;
 }
 

@@ -55,6 +55,9 @@ struct bs_plan_s {
   std::vector<int> lev_of_trip;  // [ntrip] level of each ring triple (-1: cannot close)
   bool multires = false;
   bool dsum_clean = false;        // every plane of a non-closable triple is zero
+  // plane indices (d + nc - 1) of the separations accumulated since the last
+  // reset: rows [0] .. [1], columns [2] .. [3] (empty when [1] < [0])
+  int dbox[4] = {0, -1, 0, -1};
   std::vector<int> zero_trips;    // closable ring triples (the only planes ever accumulated)
   std::vector<int> clos;          // ring triples with T > 0, ascending (device copy at L.clos)
   std::vector<int> closrings;     // [clos.size()][3] rings (i, j, l) of those triples
