@@ -130,6 +130,7 @@ __global__ void k_bs3d_rows(const double *__restrict__ dsum, const double *__res
   const double tn = tnorm[trip];
   if (tn == 0.0) return;  // no closed triangle: the column pass writes zeros
   for (int t = threadIdx.x; t < nc; t += blockDim.x) tw[t] = twN[t];
+  int nonzero = 0;
   for (int e = threadIdx.x; e < nr * nc; e += blockDim.x) {
     const int r = e / nc, m = e - r * nc;
     const int nidx = n0 + r;
@@ -145,8 +146,16 @@ __global__ void k_bs3d_rows(const double *__restrict__ dsum, const double *__res
       acc = sv * (tn * ri);
     }
     bufA[r * LD + m] = make_float2((float)acc, 0.f);
+    nonzero |= acc != 0.0;
   }
-  __syncthreads();
+  float2 *tb = tmp + ((long long)b * ntrip + trip) * (long long)nc * nc;
+  if (!__syncthreads_or(nonzero)) {  // rows with nothing sampled: their transform is zero
+    for (int e = threadIdx.x; e < nr * nc; e += blockDim.x) {
+      const int k = e / nr, r = e - k * nr;
+      tb[(long long)k * nc + n0 + r] = make_float2(0.f, 0.f);
+    }
+    return;
+  }
   float2 *res;
   if (radN.n > 0) {
     res = stockham(bufA, bufB, nr, nc, LD, radN, tw, -1.0f);
@@ -154,7 +163,6 @@ __global__ void k_bs3d_rows(const double *__restrict__ dsum, const double *__res
     for (int r = 0; r < nr; ++r) dft_direct(bufA + r * LD, bufB + r * LD, nc, tw, -1.0f);
     res = bufB;
   }
-  float2 *tb = tmp + ((long long)b * ntrip + trip) * (long long)nc * nc;
   for (int e = threadIdx.x; e < nr * nc; e += blockDim.x) {
     const int k = e / nr, r = e - k * nr;
     tb[(long long)k * nc + n0 + r] = res[r * LD + k];
