@@ -67,7 +67,7 @@ typedef enum {
     BS_ERR_NOT_HERMITIAN = 5, /* bs_check_hermitian found V(-U) != conj V(U) */
     BS_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up */
     BS_ERR_STATE = 7,         /* call out of order (e.g. no grid loaded) or sticky error */
-    BS_ERR_UNSUPPORTED = 8    /* valid request this build does not implement */
+    BS_ERR_UNSUPPORTED = 8    /* valid request this library does not implement */
 } bs_status;
 
 /* Arithmetic of the triple contraction (bs_mabs). */
@@ -371,7 +371,8 @@ bs_status bs_mc_stats(bs_mc mc, int group, int which, double *mean_dev, double *
  * with BF16 weights (rounded from FP32 masters) and FP32 accumulation,
  * trained by the library's own forward, backward and Adam kernels on the
  * per-bin log variances that bs_mc_stats produces.  Monte Carlo remains the
- * fallback and the judge of its error.  Flat parameter vector (float):
+ * fallback and the reference its error is measured against.  Flat parameter
+ * vector (float):
  *   W1 [w][d] | b1 [w] | W2 [w][w] | b2 [w] | w3 [w] | b3 | mu_x [d] | sd_x [d] | mu_y | sd_y
  * ------------------------------------------------------------------------- */
 #define BS_MLP_FEATURES 45

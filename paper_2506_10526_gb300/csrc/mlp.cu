@@ -2,7 +2,8 @@
 // bispectrum bin from triangle and flag features, trained on the per-bin
 // variances the batched Monte Carlo path produces.  Not in the paper (which
 // estimates error bars by brute Monte Carlo over 250 realisations); the
-// Monte Carlo stays the fallback and the judge of the surrogate's error.
+// Monte Carlo stays the fallback and the reference the surrogate's error is
+// measured against.
 //
 //   xn = (x - mu_x)/sd_x;  h1 = tanh(W1 xn + b1);  h2 = tanh(W2 h1 + b2)
 //   yn = w3 . h2 + b3;     y = mu_y + sd_y yn

@@ -223,7 +223,7 @@ bs_status ensure_tensor_maps(bs_plan p, cudaStream_t s) {
                                                    cudaEnableDefault, &q);
   if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
     cudaGetLastError();
-    return fail(p, BS_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    return fail(p, BS_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the CUDA driver");
   }
   EncodeTiledFn enc = reinterpret_cast<EncodeTiledFn>(fn);
   std::vector<CUtensorMap> all;
