@@ -85,3 +85,20 @@ def test_null_handles_of_the_output_and_analysis_entry_points(lib):
     assert lib.bs_bs_cylindrical(None, None, None, None, 20, None, None, None) == 1
     assert lib.bs_grid_visibilities(None, None, None, None, ctypes.c_int64(0), 4, 4, 0, None,
                                     None, None) == 1
+
+
+def test_every_declaration_is_documented():
+    """Each entry point of include/bs.h follows a comment block (its arguments,
+    layout, ownership, errors and the passage it implements); declarations
+    that share one block (create / destroy / last_error) may follow each other
+    or a typedef."""
+    lines = open(os.path.join(ROOT, "include", "bs.h")).read().split("\n")
+    decl = re.compile(r"^(bs_status|int|const char \*)\s*\*?\s*bs_\w+\s*\(")
+    for i, line in enumerate(lines):
+        if not decl.match(line):
+            continue
+        j = i - 1
+        while j >= 0 and lines[j].strip() and not lines[j].rstrip().endswith("*/"):
+            assert (decl.match(lines[j]) or lines[j].startswith((" ", "typedef"))), (line, lines[j])
+            j -= 1
+        assert j >= 0 and lines[j].rstrip().endswith("*/"), line
