@@ -275,6 +275,48 @@ def test_closable_layouts_match_full(precision, multires):
     plan.close()
 
 
+@pytest.mark.parametrize("precision,multires", [(1, True), (0, False)])
+def test_reload_resets_the_accumulators(precision, multires):
+    """A grid load resets the collapse sums by zeroing only the separations
+    the previous blocks touched: load, accumulate block A, reload with other
+    visibilities, accumulate block B; the collapse and the delay transform
+    equal those of a fresh plan that only saw the second load and block B."""
+    torch = _torch()
+    import paper_2506_10526_gb300 as bs
+    nt, nc = 40, 12
+    edges = synth.edges_log(5, 1.5, 19.0)
+    v1 = torch.from_numpy(synth.sky_visibilities(nt, nc, seed=91)[None]).cuda()
+    v2 = torch.from_numpy(synth.sky_visibilities(nt, nc, seed=92)[None]).cuda()
+    blk_a, blk_b = (0, 6, 0, 12, 0, 12), (6, 12, 0, 5, 4, 12)
+
+    def outputs(plan):
+        n2 = 2 * nc - 1
+        dd = torch.empty((1, plan.ntrip, n2, n2), dtype=torch.float64, device="cuda")
+        bd = torch.empty((1, plan.ntrip, nc, nc), dtype=torch.float64, device="cuda")
+        plan.mabs_delta(dd)
+        plan.bs3d(bd)
+        torch.cuda.synchronize()
+        return dd.cpu().numpy(), bd.cpu().numpy()
+
+    p = bs.Plan(nt, nc, edges, precision=precision, multires=multires)
+    p.grid_load(v1)
+    p.mabs(block=blk_a, accumulate=True)
+    outputs(p)
+    p.grid_load(v2)
+    p.mabs(block=blk_b, accumulate=True)
+    got = outputs(p)
+    q = bs.Plan(nt, nc, edges, precision=precision, multires=multires)
+    q.grid_load(v2)
+    q.mabs(block=blk_b, accumulate=True)
+    want = outputs(q)
+    for g, w in zip(got, want):
+        assert np.array_equal(np.isnan(g), np.isnan(w))
+        ok = ~np.isnan(w)
+        assert np.abs(g[ok] - w[ok]).max() <= 1e-9 * max(np.abs(w[ok]).max(), 1e-300)
+    p.close()
+    q.close()
+
+
 def test_hermitian_check():
     torch = _torch()
     import paper_2506_10526_gb300 as bs
