@@ -107,24 +107,25 @@ __global__ void k_fold_rinv(const long long *__restrict__ nnu, int nc, double *_
   }
 }
 
-// Rows (columns) of the 2D delay transform per CTA: the transposed stores of
-// the row pass and the scattered stores of the column pass go out as runs of
-// kBsRows consecutive elements.
+// Rows (columns) of the 2D delay transform per CTA, `rows`: the transposed
+// stores of the row pass and the scattered stores of the column pass go out as
+// runs of that many consecutive elements.  8, or fewer where 8 padded rows
+// (and their ping-pong copies) would not fit one CTA's shared memory.
 constexpr int kBsRows = 8;
 
-// First pass: for kBsRows consecutive n, the folded plane Bbar(n, m) over one
+// First pass: for `rows` consecutive n, the folded plane Bbar(n, m) over one
 // period of m, transformed along m; written transposed, tmp[k][n].
 __global__ void k_bs3d_rows(const double *__restrict__ dsum, const double *__restrict__ rinv,
                             const double *__restrict__ tnorm, float2 *__restrict__ tmp, int ntrip,
                             int nc, const float2 *__restrict__ twN, Radices radN,
-                            const int *__restrict__ list) {
+                            const int *__restrict__ list, int rows) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int LD = nc + 1;  // padded rows: the transposed reads spread over the banks
   float2 *tw = reinterpret_cast<float2 *>(smem_raw);
   float2 *bufA = tw + nc;
-  float2 *bufB = bufA + kBsRows * LD;
-  const int n0 = blockIdx.x * kBsRows, trip = list ? list[blockIdx.y] : blockIdx.y, b = blockIdx.z;
-  const int nr = min(kBsRows, nc - n0);
+  float2 *bufB = bufA + rows * LD;
+  const int n0 = blockIdx.x * rows, trip = list ? list[blockIdx.y] : blockIdx.y, b = blockIdx.z;
+  const int nr = min(rows, nc - n0);
   const int n2 = 2 * nc - 1;
   const double *ds = dsum + ((long long)b * ntrip + trip) * (long long)n2 * n2;
   const double tn = tnorm[trip];
@@ -169,18 +170,19 @@ __global__ void k_bs3d_rows(const double *__restrict__ dsum, const double *__res
   }
 }
 
-// Second pass: for kBsRows consecutive first-pass frequencies, transform along
+// Second pass: for `rows` consecutive first-pass frequencies, transform along
 // n; out[a + nc/2][b + nc/2] = scale * Re.
 __global__ void k_bs3d_cols(const float2 *__restrict__ tmp, double *__restrict__ out, int ntrip,
                             int nc, const float2 *__restrict__ twN, Radices radN, double scale,
-                            const double *__restrict__ tnorm, const int *__restrict__ list) {
+                            const double *__restrict__ tnorm, const int *__restrict__ list,
+                            int rows) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int LD = nc + 1;
   float2 *tw = reinterpret_cast<float2 *>(smem_raw);
   float2 *bufA = tw + nc;
-  float2 *bufB = bufA + kBsRows * LD;
-  const int bb0 = blockIdx.x * kBsRows, trip = list ? list[blockIdx.y] : blockIdx.y, b = blockIdx.z;
-  const int nr = min(kBsRows, nc - bb0);
+  float2 *bufB = bufA + rows * LD;
+  const int bb0 = blockIdx.x * rows, trip = list ? list[blockIdx.y] : blockIdx.y, b = blockIdx.z;
+  const int nr = min(rows, nc - bb0);
   const int h = nc / 2;
   const int nout = list ? gridDim.y : ntrip;
   double *ob = out + ((long long)b * nout + blockIdx.y) * (long long)nc * nc;
@@ -274,7 +276,14 @@ cudaError_t launch_bs3d(const double *dsum, const long long *nnu, const double *
                         double *out, int batch, int ntrip, int nc, const float2 *twN,
                         const Radices &radN, double scale, const int *list, int nlist,
                         cudaStream_t s) {
-  const size_t smem = (size_t)(nc + 2 * kBsRows * (nc + 1)) * sizeof(float2);
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  int rows = kBsRows;
+  auto smem_of = [&](int r) { return (size_t)(nc + 2 * r * (nc + 1)) * sizeof(float2); };
+  while (rows > 1 && smem_of(rows) > (size_t)optin) rows /= 2;
+  const size_t smem = smem_of(rows);
+  if (smem > (size_t)optin) return cudaErrorInvalidValue;  // nc beyond one row per CTA
   cudaError_t e = smem_optin_once<k_bs3d_rows>();
   if (e != cudaSuccess) return e;
   e = smem_optin_once<k_bs3d_cols>();
@@ -287,11 +296,11 @@ cudaError_t launch_bs3d(const double *dsum, const long long *nnu, const double *
   if (e != cudaSuccess) return e;
   const int ny = list ? nlist : ntrip;
   if (ny == 0) return cudaSuccess;
-  dim3 grid((nc + kBsRows - 1) / kBsRows, ny, batch);
-  k_bs3d_rows<<<grid, threads, smem, s>>>(dsum, rinv, tnorm, tmp, ntrip, nc, twN, radN, list);
+  dim3 grid((nc + rows - 1) / rows, ny, batch);
+  k_bs3d_rows<<<grid, threads, smem, s>>>(dsum, rinv, tnorm, tmp, ntrip, nc, twN, radN, list, rows);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_bs3d_cols<<<grid, threads, smem, s>>>(tmp, out, ntrip, nc, twN, radN, scale, tnorm, list);
+  k_bs3d_cols<<<grid, threads, smem, s>>>(tmp, out, ntrip, nc, twN, radN, scale, tnorm, list, rows);
   return cudaGetLastError();
 }
 

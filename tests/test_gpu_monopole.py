@@ -133,3 +133,60 @@ def test_cylindrical_binning_matches_oracle():
     scale = np.abs(b3h).max() * np.maximum(c_o, 1)
     assert np.all(np.abs(sums.cpu().numpy() - s_o) <= 1e-12 * scale)
     plan.close()
+
+
+def test_monopole_more_realisations_than_one_launch_holds():
+    """Ten realisations: the host splits them into launches of at most eight
+    (counts taken by the first); every realisation's sums against the oracle."""
+    torch = _torch()
+    import paper_2506_10526_gb300 as bs
+    nt, nc, batch = 24, 8, 10
+    edges = synth.edges_linear(4, 11)
+    v = np.stack([synth.sky_visibilities(nt, nc, seed=300 + k) for k in range(batch)])
+    plan = bs.Plan(nt, nc, edges, precision=1, batch=batch)
+    plan.grid_load(torch.from_numpy(v).cuda())
+    plan.mabs(accumulate=True)
+    tri, _ = plan.counts()
+    b3 = torch.empty((batch, plan.n_closable, nc, nc), dtype=torch.float64, device="cuda")
+    plan.bs3d_closable(b3)
+    kperp = 2 * np.pi * plan.ring_umean()
+    kpar = mo.kpar_axis(nc)
+    k1e = np.geomspace(0.5 * kperp.min(), 2 * np.sqrt(kperp.max() ** 2 + 4 * kpar.max() ** 2), 7)
+    sums, cnt = plan.bs_monopole(b3, kperp, kpar, k1e, 5, 5)
+    torch.cuda.synchronize()
+    b3h = b3.cpu().numpy()
+    s_o, c_o = mo.bs_monopole(b3h, _planes_trips(tri, len(edges) - 1), kperp, kpar, k1e, 5, 5)
+    np.testing.assert_array_equal(cnt.cpu().numpy(), c_o)
+    scale = np.abs(b3h).max() * np.maximum(c_o, 1)
+    assert np.all(np.abs(sums.cpu().numpy() - s_o) <= 1e-12 * scale)
+    plan.close()
+
+
+@pytest.mark.parametrize("nc", [1000, 2160])  # 8 and 16 columns per thread; 2160: 4 delay rows per CTA
+def test_cylindrical_binning_wide_rows(nc):
+    torch = _torch()
+    import paper_2506_10526_gb300 as bs
+    nt = 16
+    edges = [1.0, 3.0, 5.0]
+    v = synth.sky_visibilities(nt, nc, seed=17)
+    plan = bs.Plan(nt, nc, edges, precision=1)
+    plan.grid_load(torch.from_numpy(v[None]).cuda())
+    plan.mabs(accumulate=True)
+    b3 = torch.empty((1, plan.n_closable, nc, nc), dtype=torch.float64, device="cuda")
+    plan.bs3d_closable(b3)
+    kpar = mo.kpar_axis(nc)
+    ke = np.linspace(-0.7 * kpar.max(), 0.95 * kpar.max(), 17)
+    sums, cnt = plan.bs_cylindrical(b3, kpar, ke)
+    torch.cuda.synchronize()
+    b3h = b3.cpu().numpy()
+    q = mo.axis_bins(kpar, ke)
+    n = len(ke) - 1
+    na = np.bincount(q[q >= 0], minlength=n)
+    np.testing.assert_array_equal(cnt.cpu().numpy(), np.outer(na, na))
+    # sums by separable bin sums (row-bin x column-bin indicator matrices)
+    ind = np.zeros((n, nc))
+    ind[q[q >= 0], np.flatnonzero(q >= 0)] = 1.0
+    want = np.einsum("qa,pab,rb->pqr", ind, b3h[0], ind)
+    scale = np.abs(b3h).max() * np.maximum(cnt.cpu().numpy(), 1)
+    assert np.all(np.abs(sums.cpu().numpy()[0] - want) <= 1e-12 * scale)
+    plan.close()
