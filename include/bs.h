@@ -272,11 +272,18 @@ bs_status bs_plan_ring_umean(bs_plan plan, double *umean_host);
  *                 the values in each bin (overwritten)
  *  count_dev      int64 [n_k1][n_mu][n_t]: samples in each bin (overwritten);
  *                 the monopole is sum / count
- * The bin of a sample is decided in FP32, every operation rounded once in the
- * order above (no fused multiply-add); samples whose mu or t falls outside
- * [0.5 - 1e-6, 1 + 1e-6] are dropped (side lengths from ring centres need
- * not close), the rest clamped to [0.5, 1].  Values and sums are FP64.
- * Errors: BS_ERR_ARG (NULL, counts out of range, edges not ascending),
+ * Side lengths from ring centres close only approximately: samples whose mu
+ * or t falls outside [0.5 - 1e-2, 1 + 1e-2] are dropped, the rest clamped to
+ * [0.5, 1].  The bin is decided in FP32 on squared lengths (k1 >= e_q as
+ * S1 >= e_q^2, t >= tau as S2 >= tau^2 S1, mu >= m as
+ * (S1 + S2 - S3)^2 >= 4 m^2 S1 S2): it equals the FP64 decision except for
+ * samples whose k1 lies within a relative 1e-6 of a k1 edge, or whose t lies
+ * within 1e-6 or mu within 4e-6 of a shape edge or an acceptance limit.
+ * Values, sums and the model (from FP64 squared lengths) are FP64.
+ * kperp_host must lie in [1e-8, 1e8] and |kpar_host| <= 1e8 (FP32 range of
+ * the squared comparisons).
+ * Errors: BS_ERR_ARG (NULL, counts out of range, edges not ascending, k out
+ * of range),
  * BS_ERR_STATE (no counts yet), BS_ERR_UNSUPPORTED (bins x realisations
  * beyond one CTA's shared memory). */
 bs_status bs_bs_monopole(bs_plan plan, const double *b3d_dev, const double *kperp_host,
@@ -475,8 +482,12 @@ bs_status bs_sky_generate(bs_sky sky, uint64_t seed, uint64_t realisation0, int 
  *  tri_dev         int64 [nbins(nbins+1)(nbins+2)/6] device output, ring
  *                  triples i <= j <= l in lexicographic order; overwritten
  * Runs on the current device, asynchronously on cuda_stream.  The first call
- * on a device looks up the array's device address (cudaGetSymbolAddress);
- * make that first call before any stream capture.  The array is shared by
+ * on a device looks up the array's device address (cudaGetSymbolAddress) and,
+ * under CUDA's lazy module loading, is also the call that reserves the array
+ * on that device: make it (a warm-up call) before any stream capture and
+ * before relying on device memory staying unchanged.  A reset of the device's
+ * context frees the array; the next call notices the new context and looks
+ * the address up again (reserving the array anew).  The array is shared by
  * all calls and keeps the last call's contents (the call clears what must
  * start at zero): calls that overlap on the GPU, from any stream or thread,
  * race and must be serialised by the caller.

@@ -31,39 +31,43 @@ Readings (the paper leaves them open):
   the Eq. (dft) output, a -> ring i (nu1), b -> ring j (nu2), the third
   component -a-b -> ring l.  The bin value is the unweighted mean.
 * U_m of a ring is the mean |U| over its grid cells (grid units).
-* Binning arithmetic: the bin of a sample is decided in FP32, every
-  operation rounded once (IEEE), in this order, which the GPU repeats so
-  that bin indices agree bit for bit.  kperp and kpar are rounded to FP32;
-  kpar_3 = -(kpar_1 + kpar_2); S_n = kperp_n^2 + kpar_n^2, sorted
-  S1 >= S2 >= S3; K_n = sqrt(S_n); t = K2 / K1;
-  mu = ((S1 + S2) - S3) / (2 (K1 K2)).  mu and t within 1e-6 of [0.5, 1]
-  are clamped into it, samples further out (side lengths from ring means
-  need not close) are dropped.  k1 bin q: e_q <= K1 < e_{q+1} (K1 widened
-  to FP64, edges in FP64).  mu bin: floor((mu - 0.5) * (2 n_mu)) in FP32,
-  the value 1 in the last bin; t alike.  Values and sums are FP64; the
-  model of Eq. (bsana) takes the FP32 squared lengths widened to FP64.
+* Binning, as the definitions read, in FP64: k_n = sqrt(kperp_n^2 +
+  kpar_n^2) with kpar_3 = -(kpar_1 + kpar_2); sides sorted k1 >= k2 >= k3;
+  t = k2 / k1; mu = (k1^2 + k2^2 - k3^2) / (2 k1 k2).  The range
+  0.5 <= mu, t <= 1 of Eq. (shape) holds for closed triangles; sides built
+  from ring-mean k_perp close only approximately, and on the MWA-like grid
+  (k_par >> k_perp) a large share of the samples are near-collinear with mu
+  within 1e-4 above 1.  Samples within SHAPE_TOL = 1e-2 outside [0.5, 1] are
+  therefore clamped into it and only those further out (sides that clearly
+  cannot close) are dropped; few samples lie near that limit.  k1 bin
+  q: e_q <= k1 < e_{q+1}; mu bin q: 0.5 + q / (2 n_mu) <= mu, the value 1
+  in the last bin; t alike.  Values, sums and the model of Eq. (bsana) are
+  FP64.
+* ``bin_candidates`` lists, for each sample, every bin (or the drop, -1)
+  reachable by moving k1 by a relative ``rel_k`` and mu, t by ``rel_s``
+  about their FP64 values.  A kernel that decides bins in lower precision
+  may disagree with ``bs_monopole`` only on samples with more than one
+  candidate; the tests check GPU counts and sums against that interval.
 """
 from __future__ import annotations
 
 import numpy as np
 
-SHAPE_TOL = 1e-6
-F32 = np.float32
+SHAPE_TOL = 1e-2
 
 
 def triangle_shape(s1, s2, s3):
-    """(k1, mu, t) of Eq. (shape) from the squared side lengths of a closed
-    triangle (any order; arrays broadcast), computed in the inputs' floating
-    type (FP64 for Python floats)."""
-    arrs = np.broadcast_arrays(*(np.asarray(x) if isinstance(x, np.ndarray) and x.dtype == F32
-                                 else np.asarray(x, np.float64) for x in (s1, s2, s3)))
+    """(k1, mu, t) of Eq. (shape) in FP64 from the squared side lengths of a
+    closed triangle (any order; arrays broadcast): sides k_n = sqrt(S_n)
+    sorted k1 >= k2 >= k3, t = k2 / k1, mu = (k1^2 + k2^2 - k3^2) / (2 k1 k2)."""
+    arrs = np.broadcast_arrays(*(np.asarray(x, np.float64) for x in (s1, s2, s3)))
     s = np.sort(np.stack(arrs), axis=0)[::-1]
     S1, S2, S3 = s[0], s[1], s[2]
-    K1, K2 = np.sqrt(S1), np.sqrt(S2)
-    t = K2 / K1
-    two = S1.dtype.type(2.0)
-    mu = ((S1 + S2) - S3) / (two * (K1 * K2))
-    return K1, mu, t
+    k1, k2 = np.sqrt(S1), np.sqrt(S2)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        t = k2 / k1
+        mu = (S1 + S2 - S3) / (2.0 * k1 * k2)
+    return k1, mu, t
 
 
 def ring_mean_u(nt: int, edges, labels=None) -> np.ndarray:
@@ -94,23 +98,36 @@ def bsana(S1, S2, S3, f_ng: float, p_amp: float, p_index: float):
     return 2.0 * f_ng * (P[0] * P[1] + P[1] * P[2] + P[2] * P[0])
 
 
-def _bins(K1, mu, t, k1_edges, n_mu, n_t):
-    """Flat bin index (k1, mu, t) of each FP32 sample, -1 where it falls outside."""
+def _bins(k1, mu, t, k1_edges, n_mu, n_t):
+    """Flat bin index (k1, mu, t) of each sample (FP64), -1 where it is
+    dropped or falls outside the k1 edges."""
     e = np.asarray(k1_edges, np.float64)
-    qk = np.searchsorted(e, K1.astype(np.float64), side="right") - 1
+    qk = np.searchsorted(e, k1, side="right") - 1
     ok = (qk >= 0) & (qk < e.size - 1)
-    lo, hi = F32(0.5 - SHAPE_TOL), F32(1.0 + SHAPE_TOL)
-    ok &= (mu >= lo) & (mu <= hi) & (t >= lo) & (t <= hi)
-    half, one = F32(0.5), F32(1.0)
-    muc = np.minimum(np.maximum(mu, half), one)
-    tc = np.minimum(np.maximum(t, half), one)
-    qm = np.minimum(np.floor((muc - half) * F32(2 * n_mu)).astype(np.int64), n_mu - 1)
-    qt = np.minimum(np.floor((tc - half) * F32(2 * n_t)).astype(np.int64), n_t - 1)
+    lo, hi = 0.5 - SHAPE_TOL, 1.0 + SHAPE_TOL
+    with np.errstate(invalid="ignore"):
+        ok &= (mu >= lo) & (mu <= hi) & (t >= lo) & (t <= hi)
+        muc = np.nan_to_num(np.clip(mu, 0.5, 1.0), nan=0.5)
+        tc = np.nan_to_num(np.clip(t, 0.5, 1.0), nan=0.5)
+    qm = np.minimum(np.floor((muc - 0.5) * (2 * n_mu)).astype(np.int64), n_mu - 1)
+    qt = np.minimum(np.floor((tc - 0.5) * (2 * n_t)).astype(np.int64), n_t - 1)
     return np.where(ok, (qk * n_mu + qm) * n_t + qt, -1)
 
 
+def _plane_squares(kp, kpar, i, j, l):
+    """Squared sides S1, S2, S3 [nc][nc] of ring triple (i, j, l) at every
+    delay pair (a, b): kpar_1 = kpar[a], kpar_2 = kpar[b], kpar_3 = -(sum)."""
+    ka = kpar[:, None]
+    kb = kpar[None, :]
+    kc = -(ka + kb)
+    S1 = np.broadcast_to(kp[i] ** 2 + ka ** 2, kc.shape)
+    S2 = np.broadcast_to(kp[j] ** 2 + kb ** 2, kc.shape)
+    S3 = kp[l] ** 2 + kc ** 2
+    return S1, S2, S3
+
+
 def bs_monopole(b3d, trips, kperp, kpar, k1_edges, n_mu: int, n_t: int, model=None):
-    """Binned monopole sums and counts.
+    """Binned monopole sums and counts (FP64 throughout).
 
     b3d     [batch][n_planes][nc][nc] delay-space bispectrum, rows a + nc/2,
             columns b + nc/2 (or None with ``model``)
@@ -120,51 +137,135 @@ def bs_monopole(b3d, trips, kperp, kpar, k1_edges, n_mu: int, n_t: int, model=No
     model   None, or (f_ng, p_amp, p_index): bin Eq. (bsana) instead of b3d
     returns sums [batch][n_k1][n_mu][n_t], counts [n_k1][n_mu][n_t] (int64)
     """
-    kpar = np.asarray(kpar, np.float64).astype(F32)
-    kp = np.asarray(kperp, np.float64).astype(F32)
-    nc = kpar.size
+    kpar = np.asarray(kpar, np.float64)
+    kp = np.asarray(kperp, np.float64)
     n_k1 = len(k1_edges) - 1
     nbin = n_k1 * n_mu * n_t
     batch = 1 if b3d is None else b3d.shape[0]
     sums = np.zeros((batch, nbin))
     cnt = np.zeros(nbin, np.int64)
-    ka = np.repeat(kpar[:, None], nc, axis=1)
-    kb = np.repeat(kpar[None, :], nc, axis=0)
-    kc = -(ka + kb)
     for p, (i, j, l) in enumerate(trips):
-        S1 = kp[i] * kp[i] + ka * ka
-        S2 = kp[j] * kp[j] + kb * kb
-        S3 = kp[l] * kp[l] + kc * kc
-        K1, mu, t = triangle_shape(S1, S2, S3)
-        q = _bins(K1, mu, t, k1_edges, n_mu, n_t).ravel()
+        S1, S2, S3 = _plane_squares(kp, kpar, i, j, l)
+        k1, mu, t = triangle_shape(S1, S2, S3)
+        q = _bins(k1, mu, t, k1_edges, n_mu, n_t).ravel()
         sel = q >= 0
         cnt += np.bincount(q[sel], minlength=nbin)
         for b in range(batch):
             if model is None:
                 v = np.asarray(b3d[b, p], np.float64).ravel()
             else:
-                v = bsana(S1.astype(np.float64), S2.astype(np.float64), S3.astype(np.float64),
-                          *model).ravel()
+                v = bsana(S1, S2, S3, *model).ravel()
             sums[b] += np.bincount(q[sel], weights=v[sel], minlength=nbin)
     return sums.reshape(batch, n_k1, n_mu, n_t), cnt.reshape(n_k1, n_mu, n_t)
 
 
+def bin_candidates(k1, mu, t, k1_edges, n_mu: int, n_t: int, rel_k: float, rel_s: float):
+    """Bins a sample can take when k1 moves by a relative ``rel_k`` and mu, t
+    by ``rel_s`` (absolute; both lie near [0.5, 1]) about their FP64 values
+    (t never above 1: the sides are sorted).
+
+    Returns (q, amb, cand): q the FP64 bin (-1 dropped), amb a mask of the
+    samples with more than one candidate, cand [27][n_amb] the candidate bins
+    of those samples (with repeats; -1 = dropped)."""
+    k1, mu, t = (np.asarray(x, np.float64).ravel() for x in (k1, mu, t))
+    q = _bins(k1, mu, t, k1_edges, n_mu, n_t)
+    amb = np.zeros(q.shape, bool)
+
+    def tmove(tt, dt):  # t = k2 / k1 <= 1 holds for sorted sides in any precision
+        return np.minimum(tt + dt, 1.0) if dt > 0 else tt + dt
+
+    for fk in (1 - rel_k, 1 + rel_k):
+        amb |= _bins(k1 * fk, mu, t, k1_edges, n_mu, n_t) != q
+    for dm in (-rel_s, rel_s):
+        amb |= _bins(k1, mu + dm, t, k1_edges, n_mu, n_t) != q
+        amb |= _bins(k1, mu, tmove(t, dm), k1_edges, n_mu, n_t) != q
+    ka, ma, ta = k1[amb], mu[amb], t[amb]
+    cand = np.stack([_bins(ka * fk, ma + dm, tmove(ta, dt), k1_edges, n_mu, n_t)
+                     for fk in (1 - rel_k, 1.0, 1 + rel_k) for dm in (-rel_s, 0.0, rel_s)
+                     for dt in (-rel_s, 0.0, rel_s)])
+    return q, amb, cand
+
+
+def monopole_interval(b3d, trips, kperp, kpar, k1_edges, n_mu: int, n_t: int, rel_k: float,
+                      rel_s: float, model=None):
+    """What a kernel whose bin decision may differ from the FP64 one within
+    ``rel_k`` and ``rel_s`` (see ``bin_candidates``) can return.
+
+    returns dict with, per bin, ``c_lo`` (samples whose only candidate is the
+    bin), ``c_hi`` (samples having the bin among their candidates), ``s_sure``
+    [batch][bin] (sums over the first set), ``s_amb`` [batch][bin] (sums of
+    |value| over ambiguous samples that can reach the bin), and the numbers
+    of samples ``n_amb`` and ``n`` (all samples)."""
+    kpar = np.asarray(kpar, np.float64)
+    kp = np.asarray(kperp, np.float64)
+    n_k1 = len(k1_edges) - 1
+    nbin = n_k1 * n_mu * n_t
+    batch = 1 if b3d is None else b3d.shape[0]
+    c_lo = np.zeros(nbin, np.int64)
+    c_hi = np.zeros(nbin, np.int64)
+    s_sure = np.zeros((batch, nbin))
+    s_amb = np.zeros((batch, nbin))
+    n_amb = 0
+    n_all = 0
+    for p, (i, j, l) in enumerate(trips):
+        S1, S2, S3 = _plane_squares(kp, kpar, i, j, l)
+        k1, mu, t = triangle_shape(S1, S2, S3)
+        q, amb, cand = bin_candidates(k1, mu, t, k1_edges, n_mu, n_t, rel_k, rel_s)
+        n_all += q.size
+        n_amb += int(amb.sum())
+        sure = (q >= 0) & ~amb
+        c_lo += np.bincount(q[sure], minlength=nbin)
+        # distinct candidate bins per ambiguous sample
+        idx = np.broadcast_to(np.arange(cand.shape[1])[None, :], cand.shape).ravel()
+        cb = cand.ravel()
+        keep = cb >= 0
+        pairs = np.unique(np.stack([idx[keep], cb[keep]]), axis=1)
+        c_hi += np.bincount(pairs[1], minlength=nbin)
+        for b in range(batch):
+            if model is None:
+                v = np.asarray(b3d[b, p], np.float64).ravel()
+            else:
+                v = bsana(S1, S2, S3, *model).ravel()
+            s_sure[b] += np.bincount(q[sure], weights=v[sure], minlength=nbin)
+            s_amb[b] += np.bincount(pairs[1], weights=np.abs(v[amb])[pairs[0]], minlength=nbin)
+    c_hi += c_lo
+    shape = (n_k1, n_mu, n_t)
+    return {"c_lo": c_lo.reshape(shape), "c_hi": c_hi.reshape(shape),
+            "s_sure": s_sure.reshape((batch,) + shape), "s_amb": s_amb.reshape((batch,) + shape),
+            "n_amb": n_amb, "n": n_all}
+
+
 def _chunk(args):
-    b3d, trips, kperp, kpar, k1_edges, n_mu, n_t, model = args
+    fn, b3d, trips, kperp, kpar, k1_edges, n_mu, n_t, model, rel = args
+    if fn == "interval":
+        return monopole_interval(b3d, trips, kperp, kpar, k1_edges, n_mu, n_t, *rel, model=model)
     return bs_monopole(b3d, trips, kperp, kpar, k1_edges, n_mu, n_t, model=model)
+
+
+def _pool(fn, trips, kperp, kpar, k1_edges, n_mu, n_t, model, rel, workers):
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    chunks = [trips[k::workers] for k in range(workers) if trips[k::workers]]
+    args = [(fn, None, c, kperp, kpar, k1_edges, n_mu, n_t, model, rel) for c in chunks]
+    with ProcessPoolExecutor(len(chunks), mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_chunk, args))
 
 
 def bs_monopole_pool(trips, kperp, kpar, k1_edges, n_mu: int, n_t: int, model, workers: int = 16):
     """``bs_monopole`` of the model (no values) over many planes, the planes
     split across a spawn-started process pool: sums and counts of disjoint
     plane sets add."""
-    import multiprocessing as mp
-    from concurrent.futures import ProcessPoolExecutor
-    chunks = [trips[k::workers] for k in range(workers) if trips[k::workers]]
-    args = [(None, c, kperp, kpar, k1_edges, n_mu, n_t, model) for c in chunks]
-    with ProcessPoolExecutor(len(chunks), mp_context=mp.get_context("spawn")) as ex:
-        parts = list(ex.map(_chunk, args))
+    parts = _pool("plain", trips, kperp, kpar, k1_edges, n_mu, n_t, model, None, workers)
     return sum(p[0] for p in parts), sum(p[1] for p in parts)
+
+
+def monopole_interval_pool(trips, kperp, kpar, k1_edges, n_mu: int, n_t: int, model,
+                           rel_k: float, rel_s: float, workers: int = 16):
+    """``monopole_interval`` of the model over many planes in a spawn-started
+    process pool (every field adds over disjoint plane sets)."""
+    parts = _pool("interval", trips, kperp, kpar, k1_edges, n_mu, n_t, model, (rel_k, rel_s),
+                  workers)
+    return {k: sum(p[k] for p in parts) for k in parts[0]}
 
 
 def axis_bins(kpar, edges) -> np.ndarray:

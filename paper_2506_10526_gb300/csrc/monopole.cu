@@ -6,26 +6,37 @@
 // the Eq. (dft) output.  The three sides are k_n = sqrt(kperp_n^2 + kpar_n^2)
 // with kpar_1 = kpar(a) (ring i), kpar_2 = kpar(b) (ring j) and
 // kpar_3 = -(kpar_1 + kpar_2) (ring l).  With S1 >= S2 >= S3 the squared
-// sides, the size is K1 = sqrt(S1) and the shape t = K2 / K1,
-// mu = ((S1 + S2) - S3) / (2 K1 K2) (the closure k1 + k2 + k3 = 0 turns
+// sides, the size is k1 = sqrt(S1) and the shape t = k2 / k1,
+// mu = (S1 + S2 - S3) / (2 k1 k2) (the closure k1 + k2 + k3 = 0 turns
 // -k1.k2 into squared lengths).  A bin holds the sum of the values and the
 // number of samples; the caller divides.
 //
-// The bin is decided in FP32 with every operation rounded once, in a fixed
-// order and without fused multiply-adds, so that bin indices are a
-// deterministic function of the inputs; values and sums are FP64.  The k1
-// edges are compared in FP32 too: for a float x and a double e, x >= e
-// exactly when x >= the smallest float not below e, so the host rounds each
-// edge up to FP32 once and the comparisons stay on the FP32 pipe (the GB300
-// FP64 rate is a small fraction of its FP32 rate).
+// The bin is decided in FP32 on squared quantities, with no square root and
+// no division on the exact path:
+//   k1 in bin q          <=>  E_q <= S1 < E_{q+1},  E_q = fl32(e_q^2)
+//   t >= tau             <=>  S2 >= tau^2 S1
+//   mu >= m              <=>  N^2 >= 4 m^2 P,  N = S1 + S2 - S3 >= S1 > 0,
+//                                              P = S1 S2
+// A fast approximate t and mu (reciprocal square root, fast divide) picks a
+// first bin, and the exact comparisons above move it to the right one.  The
+// squared sides carry at most 16 units u = 2^-24 of relative error
+// (including the rounding of the FP64 inputs and of k_par3 = -(k_par1 +
+// k_par2)), so the decisions equal the FP64 ones except for samples whose k1
+// lies within about 9u relative of a k1 edge, t within 17u or mu within 68u
+// of a shape edge or an acceptance limit.  Values and sums are FP64; the
+// model of Eq. (bsana) takes FP64 squared lengths from FP64 tables.
 //
-// Kernel: grid (chunks of one plane, planes).  Each thread walks runs of kRun
-// consecutive samples and keeps a running (bin, sums, count) in registers,
-// flushing to the CTA's shared-memory histogram only when the bin changes
-// (neighbouring delay modes mostly share a bin).  The CTA then adds its
+// Kernel: grid (chunks of one plane, planes).  A CTA walks its chunk in
+// passes of kThreads x kRun consecutive samples.  Each thread decides the
+// bins of kRun consecutive samples, then, per realisation, the CTA stages the
+// pass's values in shared memory with coalesced loads (rows padded by one
+// element against bank conflicts) and each thread sums its samples in runs
+// of equal bin (neighbouring delay modes mostly share a bin), flushing a run
+// to the CTA's shared-memory histogram when the bin changes.  The CTA adds its
 // non-empty bins to the global sums with FP64 atomics.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <limits>
 #include <vector>
 
@@ -37,8 +48,13 @@ namespace {
 
 constexpr int kRun = 16;      // consecutive samples per thread and pass
 constexpr int kThreads = 256;
+constexpr int kPass = kThreads * kRun;
 constexpr int kMaxBatch = 8;  // realisations per launch (the host loops over more)
 constexpr int kMonoMaxK1 = 1024;
+constexpr int kMonoMaxShape = 1024;
+// Sides from ring-mean k_perp close only approximately: mu and t within
+// kShapeTol outside [0.5, 1] are clamped into it, samples further out dropped.
+constexpr double kShapeTol = 1e-2;
 
 struct MonoArgs {
   const double *b3d;     // [batch_total][n_planes][nc][nc] or null (model)
@@ -47,105 +63,154 @@ struct MonoArgs {
   const int *rings;      // [n_planes][3]
   const float *kperp;    // [nb], rounded to FP32
   const float *kpar;     // [nc], rounded to FP32
-  const float *edges;    // [n_k1 + 1], each rounded up to FP32
+  const double *kperp64; // [nb] (model values)
+  const double *kpar64;  // [nc]
+  const float *thr;      // E [n_k1 + 1] | cmu [n_mu + 1] | ct [n_t + 1]
   int nc, n_k1, n_mu, n_t, nbin;
-  int chunk;             // samples per CTA (nc^2 < 2^31)
-  float lo, hi;          // accepted mu, t range before clamping
+  int chunk;             // samples per CTA, a multiple of kPass (nc^2 < 2^31)
   int model;
   double f2, p_amp, p_half;  // 2 f_NG, amplitude, p_index / 2
   double *sums;          // [batch_total][nbin]
   unsigned long long *cnt;  // [nbin], or null (counted by an earlier launch)
 };
 
-__device__ __forceinline__ int bin_of(const MonoArgs &a, const float *edges, float kpi, float kpj,
-                                      float kpl, float ka, float kb, float (&S)[3]) {
-  const float kc = -__fadd_rn(ka, kb);
-  S[0] = __fadd_rn(__fmul_rn(kpi, kpi), __fmul_rn(ka, ka));
-  S[1] = __fadd_rn(__fmul_rn(kpj, kpj), __fmul_rn(kb, kb));
-  S[2] = __fadd_rn(__fmul_rn(kpl, kpl), __fmul_rn(kc, kc));
-  float s1 = S[0], s2 = S[1], s3 = S[2], tmp;
+// Bin of one sample, -1 when it is dropped.  E, cmu, ct: squared thresholds
+// (cmu[0] and cmu[n_mu], ct[0]: the acceptance limits of mu and t).
+__device__ __forceinline__ int bin_of(const MonoArgs &a, const float *E, const float *cmu,
+                                      const float *ct, float kpi, float kpj, float kpl, float ka,
+                                      float kb) {
+  const float kc = -(ka + kb);
+  float s1 = kpi * kpi + ka * ka, s2 = kpj * kpj + kb * kb, s3 = kpl * kpl + kc * kc, tmp;
   if (s1 < s2) { tmp = s1; s1 = s2; s2 = tmp; }
   if (s2 < s3) { tmp = s2; s2 = s3; s3 = tmp; }
   if (s1 < s2) { tmp = s1; s1 = s2; s2 = tmp; }
-  const float K1 = __fsqrt_rn(s1), K2 = __fsqrt_rn(s2);
-  const float t = __fdiv_rn(K2, K1);
-  const float mu = __fdiv_rn(__fsub_rn(__fadd_rn(s1, s2), s3), __fmul_rn(2.0f, __fmul_rn(K1, K2)));
-  if (!(mu >= a.lo && mu <= a.hi && t >= a.lo && t <= a.hi)) return -1;
-  if (!(K1 >= edges[0] && K1 < edges[a.n_k1])) return -1;
-  int lo = 0, hi = a.n_k1;  // edges[lo] <= K1 < edges[hi]
+  if (!(s1 >= E[0] && s1 < E[a.n_k1] && s1 > 0.0f)) return -1;
+  if (!(s2 >= ct[0] * s1)) return -1;  // t below its acceptance limit
+  const float N = (s1 + s2) - s3, P = s1 * s2, N2 = N * N;
+  if (!(N2 >= cmu[0] * P && N2 <= cmu[a.n_mu] * P)) return -1;  // mu outside its limits
+  int lo = 0, hi = a.n_k1;  // E[lo] <= S1 < E[hi]
   while (hi - lo > 1) {
     const int m = (lo + hi) >> 1;
-    if (edges[m] <= K1) lo = m; else hi = m;
+    if (E[m] <= s1) lo = m; else hi = m;
   }
-  const float muc = fminf(fmaxf(mu, 0.5f), 1.0f), tc = fminf(fmaxf(t, 0.5f), 1.0f);
-  const int qm = min((int)floorf(__fmul_rn(__fsub_rn(muc, 0.5f), (float)(2 * a.n_mu))), a.n_mu - 1);
-  const int qt = min((int)floorf(__fmul_rn(__fsub_rn(tc, 0.5f), (float)(2 * a.n_t))), a.n_t - 1);
+  const float r = __fdividef(s2, s1);
+  const float ta = r * rsqrtf(r);              // ~ t
+  const float ma = 0.5f * N * rsqrtf(P);       // ~ mu
+  int qt = min(max((int)((ta - 0.5f) * (float)(2 * a.n_t)), 0), a.n_t - 1);
+  while (qt > 0 && s2 < ct[qt] * s1) --qt;
+  while (qt < a.n_t - 1 && s2 >= ct[qt + 1] * s1) ++qt;
+  int qm = min(max((int)((ma - 0.5f) * (float)(2 * a.n_mu)), 0), a.n_mu - 1);
+  while (qm > 0 && N2 < cmu[qm] * P) --qm;
+  while (qm < a.n_mu - 1 && N2 >= cmu[qm + 1] * P) ++qm;
   return (lo * a.n_mu + qm) * a.n_t + qt;
 }
 
-template <int NB>  // realisations held in registers (a.nbatch <= NB)
+// Eq. (bsana) at one sample from FP64 squared lengths.
+__device__ __forceinline__ double model_value(const MonoArgs &a, int i, int j, int l, int ia,
+                                              int ib) {
+  const double za = a.kpar64[ia], zb = a.kpar64[ib], zc = -(za + zb);
+  const double pi_ = a.kperp64[i], pj = a.kperp64[j], pl = a.kperp64[l];
+  const double P1 = a.p_amp * pow(pi_ * pi_ + za * za, a.p_half),
+               P2 = a.p_amp * pow(pj * pj + zb * zb, a.p_half),
+               P3 = a.p_amp * pow(pl * pl + zc * zc, a.p_half);
+  return a.f2 * (P1 * P2 + P2 * P3 + P3 * P1);
+}
+
 __global__ void __launch_bounds__(kThreads) k_bs_monopole(const MonoArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double *hs = reinterpret_cast<double *>(smem_raw);                  // [nbatch][nbin]
+  double *stage = reinterpret_cast<double *>(smem_raw);                   // [kThreads][kRun + 1]
+  double *hs = stage + kThreads * (kRun + 1);                              // [nbatch][nbin]
   unsigned *hc = reinterpret_cast<unsigned *>(hs + (size_t)a.nbatch * a.nbin);  // [nbin]
-  float *edges = reinterpret_cast<float *>(hc + a.nbin);                          // [n_k1 + 1]
+  float *thr = reinterpret_cast<float *>(hc + a.nbin);
+  const int nthr = a.n_k1 + a.n_mu + a.n_t + 3;
+  float *E = thr, *cmu = thr + a.n_k1 + 1, *ct = cmu + a.n_mu + 1;
   const int p = blockIdx.y;
   for (int q = threadIdx.x; q < a.nbatch * a.nbin; q += blockDim.x) hs[q] = 0.0;
   for (int q = threadIdx.x; q < a.nbin; q += blockDim.x) hc[q] = 0u;
-  for (int q = threadIdx.x; q <= a.n_k1; q += blockDim.x) edges[q] = a.edges[q];
+  for (int q = threadIdx.x; q < nthr; q += blockDim.x) thr[q] = a.thr[q];
   __syncthreads();
   const int i = a.rings[3 * p], j = a.rings[3 * p + 1], l = a.rings[3 * p + 2];
   const float kpi = a.kperp[i], kpj = a.kperp[j], kpl = a.kperp[l];
   const int n = a.nc * a.nc;
   const int e0 = blockIdx.x * a.chunk, e1 = min(n, e0 + a.chunk);
   const double *vb = a.b3d ? a.b3d + (long long)a.b0 * a.bstride + (long long)p * n : nullptr;
+  double *my = stage + threadIdx.x * (kRun + 1);
 
-  int cur = -1;
-  unsigned run_n = 0;
-  double run_s[NB];
+  for (int pass = e0; pass < e1; pass += kPass) {
+    const int base = pass + threadIdx.x * kRun;  // this thread's first sample
+    int q[kRun];
+    {
+      int ia = base / a.nc, ib = base - ia * a.nc;  // row a + nc/2, column b + nc/2
+      float ka = ia < a.nc ? a.kpar[ia] : 0.0f;
 #pragma unroll
-  for (int b = 0; b < NB; ++b) run_s[b] = 0.0;
-  auto flush = [&]() {
-    if (cur >= 0 && run_n) {
-      atomicAdd(hc + cur, run_n);
-#pragma unroll
-      for (int b = 0; b < NB; ++b)
-        if (b < a.nbatch) atomicAdd(hs + (size_t)b * a.nbin + cur, run_s[b]);
+      for (int k = 0; k < kRun; ++k) {
+        q[k] = -1;
+        if (base + k < e1) q[k] = bin_of(a, E, cmu, ct, kpi, kpj, kpl, ka, a.kpar[ib]);
+        if (++ib == a.nc) {
+          ib = 0;
+          ++ia;
+          ka = ia < a.nc ? a.kpar[ia] : 0.0f;
+        }
+      }
     }
-    run_n = 0;
+    // counts: runs of equal bin, one shared atomic per run
+    {
+      int cur = -1;
+      unsigned run = 0;
 #pragma unroll
-    for (int b = 0; b < NB; ++b) run_s[b] = 0.0;
-  };
-  for (int base = e0 + threadIdx.x * kRun; base < e1; base += blockDim.x * kRun) {
-    const int stop = min(e1, base + kRun);
-    int ia = base / a.nc, ib = base - ia * a.nc;  // row a + nc/2, column b + nc/2
-    float ka = a.kpar[ia];
-    for (int e = base; e < stop; ++e, ++ib) {
-      if (ib == a.nc) {
-        ib = 0;
-        ka = a.kpar[++ia];
+      for (int k = 0; k < kRun; ++k) {
+        if (q[k] != cur) {
+          if (cur >= 0 && run) atomicAdd(hc + cur, run);
+          cur = q[k];
+          run = 0;
+        }
+        ++run;
       }
-      float S[3];
-      const int q = bin_of(a, edges, kpi, kpj, kpl, ka, a.kpar[ib], S);
-      if (q < 0) continue;
-      if (q != cur) {
-        flush();
-        cur = q;
-      }
-      ++run_n;
+      if (cur >= 0 && run) atomicAdd(hc + cur, run);
+    }
+    for (int b = 0; b < (a.model ? 1 : a.nbatch); ++b) {
+      double v[kRun];
       if (a.model) {
-        const double P1 = a.p_amp * pow((double)S[0], a.p_half),
-                     P2 = a.p_amp * pow((double)S[1], a.p_half),
-                     P3 = a.p_amp * pow((double)S[2], a.p_half);
-        run_s[0] += a.f2 * (P1 * P2 + P2 * P3 + P3 * P1);
-      } else {
+        int ia = base / a.nc, ib = base - ia * a.nc;
 #pragma unroll
-        for (int b = 0; b < NB; ++b)
-          if (b < a.nbatch) run_s[b] += vb[(long long)b * a.bstride + e];
+        for (int k = 0; k < kRun; ++k) {
+          v[k] = q[k] >= 0 ? model_value(a, i, j, l, ia, ib) : 0.0;
+          if (++ib == a.nc) { ib = 0; ++ia; }
+        }
+      } else {
+        // coalesced staging of this pass's values: element e -> stage[e / kRun][e % kRun]
+        const double *src = vb + (long long)b * a.bstride + pass;
+        const int m = min(kPass, e1 - pass);
+        double ld[kRun];
+#pragma unroll
+        for (int k = 0; k < kRun; ++k) {
+          const int e = threadIdx.x + k * kThreads;
+          ld[k] = e < m ? __ldg(src + e) : 0.0;
+        }
+        __syncthreads();  // the previous realisation's reads are done
+#pragma unroll
+        for (int k = 0; k < kRun; ++k) {
+          const int e = threadIdx.x + k * kThreads;
+          stage[(e / kRun) * (kRun + 1) + (e % kRun)] = ld[k];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kRun; ++k) v[k] = my[k];
       }
+      int cur = -1;
+      double run = 0.0;
+#pragma unroll
+      for (int k = 0; k < kRun; ++k) {
+        if (q[k] != cur) {
+          if (cur >= 0) atomicAdd(hs + (size_t)b * a.nbin + cur, run);
+          cur = q[k];
+          run = 0.0;
+        }
+        if (cur >= 0) run += v[k];
+      }
+      if (cur >= 0) atomicAdd(hs + (size_t)b * a.nbin + cur, run);
     }
   }
-  flush();
   __syncthreads();
   for (int q = threadIdx.x; q < a.nbin; q += blockDim.x) {
     const unsigned c = hc[q];
@@ -243,15 +308,9 @@ __global__ void __launch_bounds__(kCylThreads) k_bs_cylindrical(
 }  // namespace
 
 // Bytes of shared memory the kernel needs for nbatch realisations.
-static size_t mono_smem(int nbin, int nbatch, int n_k1) {
-  return (size_t)nbatch * nbin * 8 + (size_t)nbin * 4 + (size_t)(n_k1 + 1) * 4;
-}
-
-// The smallest float not below e (x >= e  <=>  x >= up_f32(e) for floats x).
-static float up_f32(double e) {
-  float f = (float)e;
-  if ((double)f < e) f = std::nextafter(f, std::numeric_limits<float>::infinity());
-  return f;
+static size_t mono_smem(int nbin, int nbatch, int n_k1, int n_mu, int n_t) {
+  return (size_t)kThreads * (kRun + 1) * 8 + (size_t)nbatch * nbin * 8 + (size_t)nbin * 4 +
+         (size_t)(n_k1 + n_mu + n_t + 3) * 4;
 }
 
 }  // namespace bsi
@@ -277,7 +336,8 @@ bs_status bs_bs_monopole(bs_plan p, const double *b3d, const double *kperp_host,
   using namespace bsi;
   if (!p || !kperp_host || !kpar_host || !k1_edges_host || !sum_dev || !count_dev)
     return fail(p, BS_ERR_ARG, "bs_bs_monopole: NULL argument");
-  if (n_k1 < 1 || n_k1 > kMonoMaxK1 || n_mu < 1 || n_t < 1 || n_mu > 1024 || n_t > 1024)
+  if (n_k1 < 1 || n_k1 > kMonoMaxK1 || n_mu < 1 || n_t < 1 || n_mu > kMonoMaxShape ||
+      n_t > kMonoMaxShape)
     return fail(p, BS_ERR_ARG, "bs_bs_monopole: bin counts out of range");
   for (int q = 0; q < n_k1; ++q)
     if (!(k1_edges_host[q + 1] > k1_edges_host[q]) || !std::isfinite(k1_edges_host[q + 1]))
@@ -286,67 +346,84 @@ bs_status bs_bs_monopole(bs_plan p, const double *b3d, const double *kperp_host,
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   bs_status st = prepare(p, s);
   if (st != BS_OK) return st;
+  for (int m = 0; m < p->nb; ++m)
+    if (!(kperp_host[m] >= 1e-8 && kperp_host[m] <= 1e8))
+      return fail(p, BS_ERR_ARG, "bs_bs_monopole: k_perp must lie in [1e-8, 1e8]");
+  for (int c = 0; c < p->nc; ++c)
+    if (!(std::fabs(kpar_host[c]) <= 1e8))
+      return fail(p, BS_ERR_ARG, "bs_bs_monopole: |k_par| must not exceed 1e8");
   const int nbin = n_k1 * n_mu * n_t;
   const int batch = b3d ? p->batch : 1;
   const int per = std::min(batch, kMaxBatch);
-  if (mono_smem(nbin, per, n_k1) > (size_t)160 * 1024)
+  if (mono_smem(nbin, per, n_k1, n_mu, n_t) > (size_t)200 * 1024)
     return fail(p, BS_ERR_UNSUPPORTED, "bs_bs_monopole: too many bins for one CTA's histogram");
   MONO_CUDA(cudaMemsetAsync(sum_dev, 0, (size_t)batch * nbin * sizeof(double), s));
   MONO_CUDA(cudaMemsetAsync(count_dev, 0, (size_t)nbin * sizeof(int64_t), s));
   const int npl = (int)p->clos.size();
   if (npl == 0) return BS_OK;
-  // FP32 constants: kperp [nb] and kpar [nc] rounded to nearest, the k1 edges
-  // [n_k1 + 1] rounded up (a pageable source is staged before the copy call returns)
-  std::vector<float> &ftab = p->mono_tab;
-  ftab.assign((size_t)p->nb + p->nc + n_k1 + 1, 0.f);
-  for (int m = 0; m < p->nb; ++m) ftab[m] = (float)kperp_host[m];
-  for (int c = 0; c < p->nc; ++c) ftab[p->nb + c] = (float)kpar_host[c];
-  for (int q = 0; q <= n_k1; ++q) ftab[p->nb + p->nc + q] = up_f32(k1_edges_host[q]);
-  float *tab = p->at<float>(p->L.mono);
-  MONO_CUDA(cudaMemcpyAsync(tab, ftab.data(), ftab.size() * sizeof(float), cudaMemcpyHostToDevice, s));
-  MONO_CUDA(smem_optin_once<k_bs_monopole<1>>());
-  MONO_CUDA(smem_optin_once<k_bs_monopole<2>>());
-  MONO_CUDA(smem_optin_once<k_bs_monopole<4>>());
-  MONO_CUDA(smem_optin_once<k_bs_monopole<kMaxBatch>>());
+  // constants: FP64 kperp [nb], kpar [nc]; FP32 kperp, kpar (rounded to nearest);
+  // squared thresholds E_q = e_q^2 [n_k1 + 1], cmu_q = 4 m_q^2 [n_mu + 1],
+  // ct_q = tau_q^2 [n_t + 1], with the acceptance limits at both ends of the
+  // shape tables (a pageable source is staged before the copy call returns)
+  const int nb = p->nb, nc = p->nc, nthr = n_k1 + n_mu + n_t + 3;
+  std::vector<unsigned char> &tab = p->mono_tab;
+  const size_t off32 = (size_t)(nb + nc) * 8;
+  tab.assign(off32 + (size_t)(nb + nc + nthr) * 4, 0);
+  std::vector<float> f32((size_t)nb + nc + nthr);
+  for (int m = 0; m < nb; ++m) f32[m] = (float)kperp_host[m];
+  for (int c = 0; c < nc; ++c) f32[nb + c] = (float)kpar_host[c];
+  float *thr = f32.data() + nb + nc;
+  const double lo = 0.5 - kShapeTol, hi = 1.0 + kShapeTol;
+  for (int q = 0; q <= n_k1; ++q) thr[q] = (float)(k1_edges_host[q] * k1_edges_host[q]);
+  thr[0] = k1_edges_host[0] > 0.0 ? thr[0] : 0.0f;  // k1 >= e_0 for every k1 > 0
+  float *cmu = thr + n_k1 + 1, *ct = cmu + n_mu + 1;
+  for (int q = 0; q <= n_mu; ++q) {
+    const double m = q == 0 ? lo : q == n_mu ? hi : 0.5 + 0.5 * q / n_mu;
+    cmu[q] = (float)(4.0 * m * m);
+  }
+  for (int q = 0; q <= n_t; ++q) {
+    const double t = q == 0 ? lo : q == n_t ? hi : 0.5 + 0.5 * q / n_t;
+    ct[q] = (float)(t * t);
+  }
+  std::memcpy(tab.data(), kperp_host, (size_t)nb * 8);
+  std::memcpy(tab.data() + (size_t)nb * 8, kpar_host, (size_t)nc * 8);
+  std::memcpy(tab.data() + off32, f32.data(), f32.size() * 4);
+  unsigned char *dtab = p->at<unsigned char>(p->L.mono);
+  MONO_CUDA(cudaMemcpyAsync(dtab, tab.data(), tab.size(), cudaMemcpyHostToDevice, s));
+  MONO_CUDA(smem_optin_once<k_bs_monopole>());
   MonoArgs a{};
   a.b3d = b3d;
-  a.bstride = (long long)npl * p->nc * p->nc;
+  a.bstride = (long long)npl * nc * nc;
   a.rings = p->at<int>(p->L.closrings);
-  a.kperp = tab;
-  a.kpar = tab + p->nb;
-  a.edges = tab + p->nb + p->nc;
-  a.nc = p->nc;
+  a.kperp64 = reinterpret_cast<const double *>(dtab);
+  a.kpar64 = a.kperp64 + nb;
+  a.kperp = reinterpret_cast<const float *>(dtab + off32);
+  a.kpar = a.kperp + nb;
+  a.thr = a.kpar + nc;
+  a.nc = nc;
   a.n_k1 = n_k1;
   a.n_mu = n_mu;
   a.n_t = n_t;
   a.nbin = nbin;
-  a.lo = (float)(0.5 - 1e-6);
-  a.hi = (float)(1.0 + 1e-6);
   a.model = b3d ? 0 : 1;
   a.f2 = 2.0 * f_ng;
   a.p_amp = p_amp;
   a.p_half = 0.5 * p_index;
   a.sums = sum_dev;
   a.cnt = reinterpret_cast<unsigned long long *>(count_dev);
-  // about 64 Ki samples per CTA: few global flushes, several CTAs per plane
-  const int n = p->nc * p->nc;
-  const int per_cta = kThreads * kRun * 16;
+  // CTAs of about 16 passes (64 Ki samples): few global flushes, several CTAs per plane
+  const int n = nc * nc;
+  const int per_cta = kPass * 16;
   const int nx = std::max(1, (n + per_cta - 1) / per_cta);
-  a.chunk = ((n + nx - 1) / nx + kRun - 1) / kRun * kRun;
+  a.chunk = ((n + nx - 1) / nx + kPass - 1) / kPass * kPass;
+  const int gx = (n + a.chunk - 1) / a.chunk;
   for (int b0 = 0; b0 < batch; b0 += per) {
     a.b0 = b0;
     a.nbatch = std::min(per, batch - b0);
     if (b0 > 0) a.cnt = nullptr;  // the same samples: counted by the first launch
-    const dim3 grid(nx, npl);
-    const size_t sm = mono_smem(nbin, a.nbatch, n_k1);
-    if (a.nbatch == 1)
-      k_bs_monopole<1><<<grid, kThreads, sm, s>>>(a);
-    else if (a.nbatch == 2)
-      k_bs_monopole<2><<<grid, kThreads, sm, s>>>(a);
-    else if (a.nbatch <= 4)
-      k_bs_monopole<4><<<grid, kThreads, sm, s>>>(a);
-    else
-      k_bs_monopole<kMaxBatch><<<grid, kThreads, sm, s>>>(a);
+    const dim3 grid(gx, npl);
+    const size_t sm = mono_smem(nbin, a.nbatch, n_k1, n_mu, n_t);
+    k_bs_monopole<<<grid, kThreads, sm, s>>>(a);
     MONO_CUDA(cudaGetLastError());
   }
   return BS_OK;

@@ -144,8 +144,9 @@ void compute_layout(bs_plan p) {
   L.ztrips = take((size_t)p->ntrip * sizeof(int));
   L.clos = take((size_t)p->ntrip * sizeof(int));
   L.closrings = take((size_t)p->ntrip * 3 * sizeof(int));
-  // monopole binning constants: kperp [nb], kpar [nc], k1 edges [<= 1025]
-  L.mono = take(((size_t)p->nb + p->nc + 1025) * sizeof(double));
+  // monopole binning constants: FP64 kperp [nb], kpar [nc]; FP32 kperp, kpar,
+  // squared k1 edges [<= 1025], mu and t thresholds [<= 1025 each]
+  L.mono = take(((size_t)p->nb + p->nc) * 12 + (size_t)3 * 1025 * 4 + 64);
   L.cyl = take(((size_t)p->nc + 2 * 64) * sizeof(int));  // cylindrical bins (n <= 64)
   L.total = o;
 }
@@ -651,7 +652,7 @@ bs_status bs_plan_create(const bs_plan_desc *desc, bs_plan *out) {
         }
       if (ring < 0) continue;
       p->label[(size_t)iv * nt + iu] = (int8_t)ring;
-      p->cells.push_back((u + 32768) | ((v + 32768) << 16));
+      p->cells.push_back(pack_cell(u, v));
       p->uext[ring] = std::max(p->uext[ring], std::abs(u) + 1);
       cmax = std::max(cmax, std::max(std::abs(u), std::abs(v)));
     }

@@ -61,7 +61,7 @@ struct bs_plan_s {
   std::vector<int> zero_trips;    // closable ring triples (the only planes ever accumulated)
   std::vector<int> clos;          // ring triples with T > 0, ascending (device copy at L.clos)
   std::vector<int> closrings;     // [clos.size()][3] rings (i, j, l) of those triples
-  std::vector<float> mono_tab;    // FP32 k tables of the last monopole call
+  std::vector<unsigned char> mono_tab;  // k tables and thresholds of the last monopole call
   std::vector<int> cyl_tab;       // row bins and column ranges of the last cylindrical call
   std::vector<long long> cyl_cnt; // its per-bin counts
   std::vector<int> trips;        // [ntrip][3]

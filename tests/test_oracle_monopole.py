@@ -60,6 +60,7 @@ def _brute_monopole(b3d, trips, kperp, kpar, k1_edges, n_mu, n_t):
     batch, _, nc, _ = b3d.shape
     sums = np.zeros((batch, n_k1, n_mu, n_t))
     cnt = np.zeros((n_k1, n_mu, n_t), np.int64)
+    tol = mo.SHAPE_TOL
     mu_e = [0.5 + 0.5 * q / n_mu for q in range(n_mu + 1)]
     t_e = [0.5 + 0.5 * q / n_t for q in range(n_t + 1)]
     for p, (i, j, l) in enumerate(trips):
@@ -72,7 +73,7 @@ def _brute_monopole(b3d, trips, kperp, kpar, k1_edges, n_mu, n_t):
                 k1, k2, k3 = sides
                 mu = (k1 * k1 + k2 * k2 - k3 * k3) / (2 * k1 * k2)
                 t = k2 / k1
-                if not (0.5 - 1e-6 <= mu <= 1 + 1e-6 and 0.5 - 1e-6 <= t <= 1 + 1e-6):
+                if not (0.5 - tol <= mu <= 1 + tol and 0.5 - tol <= t <= 1 + tol):
                     continue
                 mu, t = min(max(mu, 0.5), 1.0), min(max(t, 0.5), 1.0)
                 qk = next((q for q in range(n_k1) if k1_edges[q] <= k1 < k1_edges[q + 1]), None)
@@ -95,8 +96,7 @@ def test_monopole_binning_against_brute_force():
     edges = np.geomspace(0.04, 2.5, 7)
     s, c = mo.bs_monopole(b3d, trips, kperp, kpar, edges, 5, 5)
     s_b, c_b = _brute_monopole(b3d, trips, kperp, kpar, edges, 5, 5)
-    # the oracle decides bins in FP32, the brute force in FP64: random
-    # samples sit far from bin edges compared with FP32 rounding
+    # both decide bins in FP64 from the definition, by different routes
     np.testing.assert_array_equal(c, c_b)
     np.testing.assert_allclose(s, s_b, rtol=1e-12, atol=1e-12)
     assert 0 < c.sum() <= len(trips) * nc * nc
@@ -115,10 +115,7 @@ def test_bsana_closed_form_and_equilateral_bin():
     s, c = mo.bs_monopole(None, [(0, 0, 0)], np.array([kap]), np.array([0.0]), edges, 5, 5,
                           model=(f, 1.0, -2.0))
     assert c.sum() == 1 and c[1, 0, 4] == 1
-    # the binning reads the squared length in FP32: S = fl32(fl32(k)^2)
-    s32 = float(np.float32(kap) * np.float32(kap))
-    assert s[0, 1, 0, 4] == pytest.approx(6 * f / s32 ** 2, rel=1e-14)
-    assert s32 == pytest.approx(kap ** 2, rel=1e-7)
+    assert s[0, 1, 0, 4] == pytest.approx(6 * f * kap ** -4, rel=1e-14)
 
 
 def test_ring_mean_u_hand_counted_rings():
@@ -170,3 +167,78 @@ def test_cylindrical_binning_pins():
     e_sym = np.array([-1.6, -0.5, 0.5, 1.6])  # symmetric, kpar a = -1, 0, 1 and +-1.047
     s, c = mo.bs_cylindrical(ys, kpar, e_sym)
     np.testing.assert_allclose(s[0, 0], s[0, 0][::-1, ::-1], rtol=1e-13)
+
+
+def _fp32_squared_decision(trips, kperp, kpar, k1_edges, n_mu, n_t, mistake=None):
+    """A numpy FP32 emulation of a bin decision on squared quantities (the
+    route a fast kernel takes): S_n in FP32, k1 by E_q = fl32(e_q^2) <= S1,
+    t by S2 >= tau^2 S1, mu by N^2 >= 4 m^2 S1 S2 with N = S1 + S2 - S3.
+    ``mistake`` plants an error to show the interval check catches it."""
+    f = np.float32
+    kp = np.asarray(kperp, np.float64).astype(f)
+    kz = np.asarray(kpar, np.float64).astype(f)
+    E = (np.asarray(k1_edges, np.float64) ** 2).astype(f)
+    lo, hi = 0.5 - mo.SHAPE_TOL, 1.0 + mo.SHAPE_TOL
+    tq = np.array([lo] + [0.5 + 0.5 * q / n_t for q in range(1, n_t)]) ** 2
+    mq = 4 * np.array([lo] + [0.5 + 0.5 * q / n_mu for q in range(1, n_mu)] + [hi]) ** 2
+    tq, mq = tq.astype(f), mq.astype(f)
+    n_k1 = len(k1_edges) - 1
+    cnt = np.zeros(n_k1 * n_mu * n_t, np.int64)
+    ka, kb = kz[:, None], kz[None, :]
+    kc = -(ka + kb)
+    for (i, j, l) in trips:
+        S = np.stack(np.broadcast_arrays(kp[i] * kp[i] + ka * ka, kp[j] * kp[j] + kb * kb,
+                                         kp[l] * kp[l] + kc * kc))
+        if mistake == "third_side_wrong_ring":
+            S[2] = kp[j] * kp[j] + kc * kc
+        S = np.sort(S, axis=0)[::-1]
+        s1, s2, s3 = S
+        N = (s1 + s2) - s3
+        if mistake == "mu_sign":
+            N = (s1 - s2) + s3
+        P, N2 = s1 * s2, N * N
+        ok = (s1 >= E[0]) & (s1 < E[-1]) & (s2 >= tq[0] * s1) & (N2 >= mq[0] * P) & (N2 <= mq[-1] * P)
+        qk = np.searchsorted(E, s1, side="right") - 1
+        qt = sum((s2 >= tq[q] * s1).astype(np.int64) for q in range(1, n_t))
+        qm = sum((N2 >= mq[q] * P).astype(np.int64) for q in range(1, n_mu))
+        q = np.where(ok, (qk * n_mu + qm) * n_t + qt, -1).ravel()
+        cnt += np.bincount(q[q >= 0], minlength=cnt.size)
+    return cnt.reshape(n_k1, n_mu, n_t)
+
+
+def _interval_setup():
+    r = np.random.default_rng(23)
+    nb, nc = 6, 64
+    kperp = np.sort(r.uniform(0.02, 0.4, nb))
+    trips = [(i, j, l) for i in range(nb) for j in range(i, nb) for l in range(j, nb)][::3]
+    kpar = mo.kpar_axis(nc, rprime=10.0, dnu_c=0.1)
+    edges = np.geomspace(0.03, 3.0, 13)
+    return trips, kperp, kpar, edges
+
+
+def test_interval_holds_an_fp32_squared_decision():
+    """The FP32 squared-length decision lands inside the interval of
+    samples within 1e-5 of an edge, and the interval is narrow."""
+    trips, kperp, kpar, edges = _interval_setup()
+    iv = mo.monopole_interval(None, trips, kperp, kpar, edges, 5, 5, 2e-6, 1e-5,
+                              model=(1.0, 1.0, -2.0))
+    _, c = mo.bs_monopole(None, trips, kperp, kpar, edges, 5, 5, model=(1.0, 1.0, -2.0))
+    assert np.all(iv["c_lo"] <= c) and np.all(c <= iv["c_hi"])
+    c32 = _fp32_squared_decision(trips, kperp, kpar, edges, 5, 5)
+    assert np.all(iv["c_lo"] <= c32) and np.all(c32 <= iv["c_hi"])
+    assert iv["n_amb"] < 1e-3 * iv["n"]
+    # samples on an edge in exact arithmetic are flagged: mu = 0.6 (the edge
+    # of the first two mu bins) and k1 on a k1 edge
+    q, amb, cand = mo.bin_candidates(np.array([1.0, edges[4]]), np.array([0.6, 0.75]),
+                                     np.array([1.0, 0.75]), edges, 5, 5, 2e-6, 1e-5)
+    assert amb.all() and q[0] >= 0 and q[1] >= 0
+    assert len(set(cand[:, 0])) == 2 and len(set(cand[:, 1])) == 2
+
+
+@pytest.mark.parametrize("mistake", ["mu_sign", "third_side_wrong_ring"])
+def test_interval_rejects_planted_mistakes(mistake):
+    trips, kperp, kpar, edges = _interval_setup()
+    iv = mo.monopole_interval(None, trips, kperp, kpar, edges, 5, 5, 2e-6, 1e-5,
+                              model=(1.0, 1.0, -2.0))
+    c32 = _fp32_squared_decision(trips, kperp, kpar, edges, 5, 5, mistake=mistake)
+    assert not (np.all(iv["c_lo"] <= c32) and np.all(c32 <= iv["c_hi"]))
