@@ -358,7 +358,15 @@ def counts_noalloc(nt: int, edges, tri_out, ngrid=None, stream=None):
     """bs_counts_noalloc: closed-triangle counts into a caller-owned int64 CUDA
     tensor of nbins(nbins+1)(nbins+2)/6 entries; allocates no device memory."""
     import numpy as np
+    import torch
     e = np.ascontiguousarray(np.asarray(edges, dtype=np.float64))
+    nb = e.size - 1
+    # the kernels write nb(nb+1)(nb+2)/6 int64 counts and read nt x nt floats:
+    # refuse anything else before it reaches the device
+    if tri_out.dtype != torch.int64 or tri_out.numel() != nb * (nb + 1) * (nb + 2) // 6:
+        raise ValueError(f"tri_out must be int64 with {nb * (nb + 1) * (nb + 2) // 6} elements")
+    if ngrid is not None and (ngrid.dtype != torch.float32 or tuple(ngrid.shape) != (nt, nt)):
+        raise ValueError(f"ngrid must be float32 of shape ({nt}, {nt})")
     st = lib().bs_counts_noalloc(int(nt), int(e.size - 1), e.ctypes.data_as(ctypes.c_void_p),
                                  _dptr(ngrid), _dptr(tri_out), _stream_ptr(stream))
     if st != BS_OK:

@@ -1,6 +1,8 @@
 // Internal declarations shared by the libbs translation units.
 #pragma once
 
+#include <cstring>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -110,6 +112,16 @@ struct TcArgs {
   int stall_test;          // failure injection: the MMA thread waits on a barrier nobody arrives at
   int f16;                 // 1: split-FP16 operands (two products), 0: split BF16 (three)
 };
+
+// Grid cell (u, v) with |u|, |v| < 32768 packed as (u + 32768) | (v + 32768) << 16,
+// computed in unsigned arithmetic and stored bit for bit in an int; the
+// counting kernel decodes it with c & 0xffff and (c >> 16) & 0xffff.
+__host__ __device__ inline int pack_cell(int u, int v) {
+  const unsigned w = (unsigned)(u + 32768) | ((unsigned)(v + 32768) << 16);
+  int c;
+  memcpy(&c, &w, sizeof c);
+  return c;
+}
 
 // Set a kernel's dynamic shared-memory limit to the device's opt-in maximum,
 // once per process (so that launches can be captured in CUDA graphs).  The

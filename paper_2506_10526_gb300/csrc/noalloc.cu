@@ -7,8 +7,11 @@
 // the same triangle-count kernel as bs_counts, but its scratch (the ring
 // label table, the list of binned cells and the ring-triple index table)
 // lives in one file-scope __device__ array of fixed size instead of a plan
-// workspace.  The array exists on every device that loads the library, for
-// the life of the process.
+// workspace.  Under CUDA's lazy module loading the array is reserved on a
+// device by the first call there (which loads this file's module); it then
+// stays for the life of the process, or until the device's context is reset.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "bs_internal.h"
@@ -53,7 +56,7 @@ __global__ void k_noalloc_labels(int nt, Edges E, const float *__restrict__ ngri
           break;
         }
     }
-    if (ring >= 0) cells[atomicAdd(ncells, 1)] = (u + 32768) | ((v + 32768) << 16);
+    if (ring >= 0) cells[atomicAdd(ncells, 1)] = pack_cell(u, v);
     if (ring >= 0 && ngrid && !(ngrid[t] > 0.f)) ring = -1;
     label[t] = (int8_t)ring;
   }
@@ -77,8 +80,44 @@ __global__ void k_noalloc_tripof(int nb, int *__restrict__ trip_of) {
   }
 }
 
+// Device address of the array per device, with the id of the context it was
+// looked up in: a context reset (cudaDeviceReset) unloads the module and frees
+// the array, so an address is reused only while the context id is the same.
+struct SymbolCache {
+  void *ptr = nullptr;
+  unsigned long long ctx = 0;
+};
 std::mutex g_symbol_mutex;
-void *g_symbol_addr[64] = {nullptr};
+SymbolCache g_symbol[64];
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+
+// Unique id of the calling thread's current context (0 if none or unknown).
+unsigned long long current_context_id() {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    looked_up = true;
+    void *f1 = nullptr, *f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) ==
+            cudaSuccess && q1 == cudaDriverEntryPointSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) ==
+            cudaSuccess && q2 == cudaDriverEntryPointSuccess) {
+      get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+      get_id = reinterpret_cast<CtxGetIdFn>(f2);
+    }
+    cudaGetLastError();
+  }
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx ||
+      get_id(ctx, &id) != CUDA_SUCCESS)
+    return 0;
+  return id;
+}
 
 }  // namespace
 
@@ -101,17 +140,22 @@ extern "C" bs_status bs_counts_noalloc(int nt, int nbins, const double *bin_edge
   }
   unsigned char *scratch = nullptr;
   {
-    // once per device, with that device current: the device address of the array
+    // once per device (and again after a reset of its context), with that
+    // device current: the device address of the array
     std::lock_guard<std::mutex> lock(g_symbol_mutex);
-    if (!g_symbol_addr[dev]) {
+    SymbolCache &c = g_symbol[dev];
+    const unsigned long long ctx = c.ptr ? current_context_id() : 0;
+    if (!c.ptr || ctx == 0 || ctx != c.ctx) {
       void *ptr = nullptr;
       if (cudaGetSymbolAddress(&ptr, g_counts_scratch) != cudaSuccess || !ptr) {
         cudaGetLastError();
+        c.ptr = nullptr;
         return BS_ERR_CUDA;
       }
-      g_symbol_addr[dev] = ptr;
+      c.ptr = ptr;
+      c.ctx = current_context_id();
     }
-    scratch = static_cast<unsigned char *>(g_symbol_addr[dev]);
+    scratch = static_cast<unsigned char *>(c.ptr);
   }
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   int8_t *label = reinterpret_cast<int8_t *>(scratch);

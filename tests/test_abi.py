@@ -102,3 +102,21 @@ def test_every_declaration_is_documented():
             assert (decl.match(lines[j]) or lines[j].startswith((" ", "typedef"))), (line, lines[j])
             j -= 1
         assert j >= 0 and lines[j].rstrip().endswith("*/"), line
+
+
+def test_counts_noalloc_binding_refuses_wrong_tensors():
+    """The allocation-free counts write nb(nb+1)(nb+2)/6 int64 entries and read
+    an nt x nt float grid: the binding refuses other dtypes and sizes before
+    any pointer reaches the library."""
+    import torch
+    edges = [1.0, 3.0, 5.0, 7.0, 9.0]  # 4 rings: 20 ring triples
+    with pytest.raises(ValueError):
+        bs.counts_noalloc(32, edges, torch.zeros(20, dtype=torch.int32))
+    with pytest.raises(ValueError):
+        bs.counts_noalloc(32, edges, torch.zeros(21, dtype=torch.int64))
+    with pytest.raises(ValueError):
+        bs.counts_noalloc(32, edges, torch.zeros(20, dtype=torch.int64),
+                          ngrid=torch.ones((32, 16), dtype=torch.float32))
+    with pytest.raises(ValueError):
+        bs.counts_noalloc(32, edges, torch.zeros(20, dtype=torch.int64),
+                          ngrid=torch.ones((32, 32), dtype=torch.float64))
