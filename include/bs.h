@@ -54,7 +54,7 @@
 extern "C" {
 #endif
 
-#define BS_ABI_VERSION 8
+#define BS_ABI_VERSION 9
 
 typedef struct bs_plan_s *bs_plan;
 
@@ -83,7 +83,7 @@ enum {
                                that |scaled field| < 2^7) and the pair product of two
                                scaled fields stays below 2^14; the FP64 sums undo the
                                scales exactly.  Per term the rounding error is about
-                               3 x 2^-22 of its magnitude (split BF16: 3 x 2^-17) at
+                               3 x 2^-22 of its magnitude (split BF16: 3 x 2^-16) at
                                the same tensor-core cost; field magnitudes within
                                2^-93 .. 2^107 keep the full precision */
 };
@@ -221,6 +221,37 @@ bs_status bs_bs3d(bs_plan plan, double *out_dev, void *cuda_stream);
  * Errors: as bs_mabs_delta / bs_bs3d. */
 bs_status bs_mabs_delta_closable(bs_plan plan, double *out_dev, void *cuda_stream);
 bs_status bs_bs3d_closable(bs_plan plan, double *out_dev, void *cuda_stream);
+
+/* Upper bound on the rounding error of the estimates of Eq. (estimator_t)
+ * computed from the last bs_grid_load, for the plan's precision.  For every
+ * ring triple, beta bounds |B_A(computed) - B_A(exact)| of each of its
+ * estimates: every entry of the full cube that bs_mabs writes, and (the
+ * collapse being a mean) every entry of the folded plane of bs_mabs_delta.
+ * The bound is worst-case and first-order: with S = sum_x F_i F_j F_l,
+ *   |dS| <= (c_term + c_acc) ||F_i||_3 ||F_j||_3 ||F_l||_3
+ *           + eps_fft sum over the three fields of
+ *             ||F_a||_2 min(||F_b||_inf ||F_c||_2, ||F_b||_2 ||F_c||_inf)
+ *   (Hoelder and Cauchy-Schwarz on the pixel sum, the normwise error of the
+ *   FP32 transforms), beta = 1.01 |dS| / (A M^2 T), norms the largest over
+ *   the channels of each ring's fields; u = 2^-24:
+ *   c_term  FP32 u; split BF16 3 x 2^-16 + u; split FP16 3 x 2^-22 + u (plus
+ *           the FP16 subnormal floor 2^-25 (2^14 + 2^7) M^2 2^-(k_i+k_j+k_l))
+ *   c_acc   FP32 (1024 + ceil(M^2/1024) + 1) u; split modes
+ *           2 u (3 ceil(M^2/16) + 1) (FP32 accumulation of the K16 MMAs)
+ *   eps_fft (16 (ceil(log2 M) + 2) + 2) u
+ *  bound_dev   double [batch][T_r], written; NaN for ring triples without a
+ *              closed triangle
+ *  delta_dev   NULL, or a folded plane as bs_mabs_delta (closable = 0:
+ *              [batch][T_r][2nchan-1][2nchan-1]) or bs_mabs_delta_closable
+ *              (closable = 1: [batch][n_c][2nchan-1][2nchan-1]) wrote it
+ *  relerr_dev  NULL (with delta_dev NULL), or the same shape as delta_dev:
+ *              per bin, the relative error bound beta / |B_A| (NaN where the
+ *              estimate is undefined)
+ * Reads the plan's fields, so call it before the next bs_grid_load.
+ * Errors: BS_ERR_ARG (NULL bound_dev, only one of delta_dev / relerr_dev),
+ * BS_ERR_STATE (no grid loaded), BS_ERR_CUDA. */
+bs_status bs_mabs_error_bound(bs_plan plan, double *bound_dev, const double *delta_dev,
+                              int closable, double *relerr_dev, void *cuda_stream);
 
 /* Eq. (vg): nearest-grid-point gridding of raw visibilities onto the plan's
  * N_t x N_t grid, with channel pre-averaging (Section 4).  Visibility

@@ -27,14 +27,14 @@ STATUS = {0: "BS_OK", 1: "BS_ERR_ARG", 2: "BS_ERR_NO_DEVICE", 3: "BS_ERR_CUDA", 
 PREC_FP32 = 0
 PREC_SPLIT_BF16 = 1
 PREC_SPLIT_FP16 = 2
-ABI_VERSION = 8      # BS_ABI_VERSION of include/bs.h
+ABI_VERSION = 9      # BS_ABI_VERSION of include/bs.h
 MLP_FEATURES = 45    # BS_MLP_FEATURES of include/bs.h
 
 # every symbol declared in include/bs.h
 EXPORTS = ("bs_abi_version", "bs_plan_create", "bs_plan_destroy", "bs_last_error",
            "bs_plan_info", "bs_plan_trip_sides", "bs_plan_set_workspace", "bs_grid_load", "bs_counts", "bs_mabs",
            "bs_delta_reset", "bs_mabs_delta", "bs_bs3d", "bs_mabs_delta_closable",
-           "bs_bs3d_closable", "bs_grid_visibilities", "bs_plan_ring_umean", "bs_bs_monopole",
+           "bs_bs3d_closable", "bs_mabs_error_bound", "bs_grid_visibilities", "bs_plan_ring_umean", "bs_bs_monopole",
            "bs_bs_cylindrical", "bs_check_hermitian",
            "bs_mc_create", "bs_mc_destroy", "bs_mc_last_error", "bs_mc_info", "bs_mc_set_input",
            "bs_mc_set_flags", "bs_mc_set_tuning", "bs_mc_autotune", "bs_mc_run", "bs_mc_reset",
@@ -88,6 +88,7 @@ def lib() -> ctypes.CDLL:
             L.bs_mabs_delta.argtypes = [P, P, P]
             L.bs_bs3d.argtypes = [P, P, P]
             L.bs_check_hermitian.argtypes = [P, P, D, P]
+            L.bs_mabs_error_bound.argtypes = [P, P, P, I, P, P]
             L.bs_counts_noalloc.argtypes = [I, I, P, P, P, P]
             L.bs_sky_create.argtypes = [I, I, D, D, D, I, ctypes.POINTER(P)]
             L.bs_sky_destroy.argtypes = [P]
@@ -329,6 +330,24 @@ class Plan:
         """bs_bs3d_closable: out float64 CUDA [batch, n_closable, nc, nc], the closable ring
         triples in ascending index."""
         self._check(self._L.bs_bs3d_closable(self._h, _dptr(out), _stream_ptr(stream)))
+
+    def error_bound(self, delta=None, closable=False, stream=None):
+        """bs_mabs_error_bound: float64 CUDA [batch, ntrip] bounds on |B_A error| per ring
+        triple; with ``delta`` (a folded plane from mabs_delta, or from
+        mabs_delta_closable with closable=True) also the per-bin relative bound of the
+        same shape.  Returns (bound, relerr or None)."""
+        import torch
+        bound = torch.empty((self.batch, self.ntrip), dtype=torch.float64, device="cuda")
+        rel = None
+        if delta is not None:
+            npl = self.n_closable if closable else self.ntrip
+            if delta.dtype != torch.float64 or delta.numel() != self.batch * npl * (2 * self.nchan - 1) ** 2:
+                raise ValueError("delta must be float64 [batch, planes, 2nc-1, 2nc-1]")
+            rel = torch.empty_like(delta)
+        self._check(self._L.bs_mabs_error_bound(self._h, _dptr(bound), _dptr(delta),
+                                                int(bool(closable)), _dptr(rel),
+                                                _stream_ptr(stream)))
+        return bound, rel
 
     def mlp_features(self, chan_flags=None, stream=None):
         """bs_mlp_features: float32 CUDA tensor [ntrip*nc*nc, MLP_FEATURES] (NaN rows: no

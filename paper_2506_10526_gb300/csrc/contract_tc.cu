@@ -13,7 +13,7 @@
 //    (|.| < 2^7) as FP16 hi + lo; the producers scale the pair product by
 //    2^(k_i + k_j) (|.| < 2^14) before the split.  The FP64 sums multiply by
 //    2^-(k_i + k_j + k_l), which is exact.  Per term the error is about
-//    3 x 2^-22 of its magnitude, against 3 x 2^-17 for split BF16.
+//    3 x 2^-22 of its magnitude, against 3 x 2^-16 for split BF16.
 //
 // Work unit: a CTA pair (thread-block cluster of 2 on neighbouring SMs) runs
 // the two-SM MMA (tcgen05.mma.cta_group::2, M256 N256 K16) on one tile,

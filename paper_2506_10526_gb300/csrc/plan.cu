@@ -148,6 +148,12 @@ void compute_layout(bs_plan p) {
   // squared k1 edges [<= 1025], mu and t thresholds [<= 1025 each]
   L.mono = take(((size_t)p->nb + p->nc) * 12 + (size_t)3 * 1025 * 4 + 64);
   L.cyl = take(((size_t)p->nc + 2 * 64) * sizeof(int));  // cylindrical bins (n <= 64)
+  // error bound: per-field norms (max |F|, ||F||_2, ||F||_3) of every level, and
+  // the ring-triple table (i, j, l, level)
+  size_t nfield_all = 0;
+  for (const Level &lv : p->levels) nfield_all += (size_t)p->batch * lv.nslot * p->nc;
+  L.errn = take(std::max<size_t>(1, nfield_all) * 3 * sizeof(double));
+  L.errtab = take((size_t)p->ntrip * 4 * sizeof(int));
   L.total = o;
 }
 

@@ -12,7 +12,8 @@ namespace bsi {
 
 struct WsLayout {
   size_t label, efflabel, cells, uext, tripof, valid, twM, twN, tnorm, T, nnu, cols, ptiles, tctiles,
-      G, F, Fhi, Flo, dsum, tmp3d, herm, err, maps, tcgroup, mlptab, ztrips, clos, closrings, mono, cyl, total;
+      G, F, Fhi, Flo, dsum, tmp3d, herm, err, maps, tcgroup, mlptab, ztrips, clos, closrings, mono, cyl,
+      errn, errtab, total;
 };
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
@@ -64,6 +65,7 @@ struct bs_plan_s {
   std::vector<unsigned char> mono_tab;  // k tables and thresholds of the last monopole call
   std::vector<int> cyl_tab;       // row bins and column ranges of the last cylindrical call
   std::vector<long long> cyl_cnt; // its per-bin counts
+  std::vector<int> err_tab;       // [ntrip][4] rings (i, j, l) and level, for the error bound
   std::vector<int> trips;        // [ntrip][3]
   std::vector<int> trip_of;      // [nb^3] -> trip index of sorted (i<=j<=l), else -1
   std::vector<long long> T;      // [ntrip] closed-triangle counts
