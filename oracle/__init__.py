@@ -84,7 +84,9 @@ def _load():
             lib.orc_counts.argtypes = [I, I, P, P, I]
             lib.orc_points.argtypes = [I, I, I, P, P, P, P, I, P, P, P, P, P, I]
             lib.orc_delta_points.argtypes = [I, I, I, P, P, P, P, I, I, I, P, P, P, P, I]
-            for f in (lib.orc_enumerate, lib.orc_counts, lib.orc_points, lib.orc_delta_points):
+            lib.orc_delta_points_block.argtypes = [I, I, I, P, P, P, P, P, I, P, P, P, P, I]
+            for f in (lib.orc_enumerate, lib.orc_counts, lib.orc_points, lib.orc_delta_points,
+                      lib.orc_delta_points_block):
                 f.restype = I
             _lib = lib
     return _lib
@@ -230,13 +232,16 @@ def mabs_points(vis, edges, pts, ngrid=None, chan_flags=None, norm_A: float = 1.
 
 
 def delta_points(vis, edges, pts, nu_lo: int = 0, nu_hi=None, ngrid=None, chan_flags=None,
-                 norm_A: float = 1.0, nthreads: int = 0):
+                 norm_A: float = 1.0, nthreads: int = 0, block=None):
     """Folded collapsed MABS at points (i, j, l, d1, d2) for the channel window
-    [nu_lo, nu_hi): the mean of Eq. (estimator_t) over the valid channel
-    triples with (nu1-nu3, nu2-nu3) = (d1, d2) or (-d1, -d2).
-    Returns (Bbar complex [npts], folded N_nu [npts])."""
+    [nu_lo, nu_hi) of all three channels, or ``block`` = (nu1_lo, nu1_hi,
+    nu2_lo, nu2_hi, nu3_lo, nu3_hi): the mean of Eq. (estimator_t) over the
+    valid channel triples of the window with (nu1-nu3, nu2-nu3) = (d1, d2) or
+    (-d1, -d2).  Returns (Bbar complex [npts], folded N_nu [npts])."""
     nc, nt, nb, lab, xre, xim, y = _prepare(vis, edges, ngrid, chan_flags)
     nu_hi = nc if nu_hi is None else int(nu_hi)
+    blk = np.ascontiguousarray(np.asarray(
+        block if block is not None else (nu_lo, nu_hi) * 3, dtype=np.int32))
     p = np.asarray(pts, dtype=np.int64).reshape(-1, 5)
     both = [p]
     neg = p.copy()
@@ -246,9 +251,9 @@ def delta_points(vis, edges, pts, nu_lo: int = 0, nu_hi=None, ngrid=None, chan_f
     n = q.shape[0]
     rr, ri = np.empty(n), np.empty(n)
     nv = np.empty(n, dtype=np.int64)
-    rc = _load().orc_delta_points(nt, nc, nb, _ptr(lab), _ptr(xre), _ptr(xim), _ptr(y),
-                                  int(nu_lo), nu_hi, n, _ptr(q), _ptr(rr), _ptr(ri), _ptr(nv),
-                                  int(nthreads))
+    rc = _load().orc_delta_points_block(nt, nc, nb, _ptr(lab), _ptr(xre), _ptr(xim), _ptr(y),
+                                        _ptr(blk), n, _ptr(q), _ptr(rr), _ptr(ri), _ptr(nv),
+                                        int(nthreads))
     if rc != 0:
         raise ValueError("orc_delta_points failed")
     m = p.shape[0]

@@ -317,12 +317,14 @@ int orc_points(int nt, int nc, int nb, const int *label, const double *xre,
  *   nvalid[s]    = number of such nu3.
  * The Section 3.2 collapse takes the mean ratio_sum / nvalid.
  */
-int orc_delta_points(int nt, int nc, int nb, const int *label, const double *xre,
-                     const double *xim, const double *y, int nu_lo, int nu_hi, int npts,
-                     const int *pts, double *ratio_re, double *ratio_im, long long *nvalid,
-                     int nthreads) {
+int orc_delta_points_block(int nt, int nc, int nb, const int *label, const double *xre,
+                           const double *xim, const double *y, const int *blk, int npts,
+                           const int *pts, double *ratio_re, double *ratio_im,
+                           long long *nvalid, int nthreads) {
     int ncell = nt * nt;
-    if (nu_lo < 0 || nu_hi > nc || nu_lo >= nu_hi) return -2;
+    for (int k = 0; k < 3; ++k)
+        if (blk[2 * k] < 0 || blk[2 * k + 1] > nc || blk[2 * k] >= blk[2 * k + 1]) return -2;
+    int nu_lo = blk[4], nu_hi = blk[5];
     ring_cells *rc = build_rings(nt, nb, label);
     double *tr = transpose_cc(xre, nc, ncell);
     double *ti = transpose_cc(xim, nc, ncell);
@@ -343,12 +345,12 @@ int orc_delta_points(int nt, int nc, int nb, const int *label, const double *xre
         int ri = pts[5 * s], rj = pts[5 * s + 1], rl = pts[5 * s + 2];
         int d1 = pts[5 * s + 3], d2 = pts[5 * s + 4];
         memset(acc, 0, (size_t)nth * 3 * nw * sizeof(double));
-        /* window channels nu3 such that all three channels stay inside */
+        /* window channels nu3 such that all three channels stay inside their ranges */
         int lo = nu_lo, hi = nu_hi;
-        if (nu_lo - d1 > lo) lo = nu_lo - d1;
-        if (nu_lo - d2 > lo) lo = nu_lo - d2;
-        if (nu_hi - d1 < hi) hi = nu_hi - d1;
-        if (nu_hi - d2 < hi) hi = nu_hi - d2;
+        if (blk[0] - d1 > lo) lo = blk[0] - d1;
+        if (blk[2] - d2 > lo) lo = blk[2] - d2;
+        if (blk[1] - d1 < hi) hi = blk[1] - d1;
+        if (blk[3] - d2 < hi) hi = blk[3] - d2;
         if (ri >= 0 && ri < nb && rj >= 0 && rj < nb && rl >= 0 && rl < nb && lo < hi) {
             const ring_cells *a = &rc[ri], *b = &rc[rj];
 #pragma omp parallel num_threads(nth)
@@ -406,4 +408,14 @@ int orc_delta_points(int nt, int nc, int nb, const int *label, const double *xre
     free(ti);
     free(ty);
     return err ? -1 : 0;
+}
+
+/* Cube window [nu_lo, nu_hi) for all three channels. */
+int orc_delta_points(int nt, int nc, int nb, const int *label, const double *xre,
+                     const double *xim, const double *y, int nu_lo, int nu_hi, int npts,
+                     const int *pts, double *ratio_re, double *ratio_im, long long *nvalid,
+                     int nthreads) {
+    const int blk[6] = {nu_lo, nu_hi, nu_lo, nu_hi, nu_lo, nu_hi};
+    return orc_delta_points_block(nt, nc, nb, label, xre, xim, y, blk, npts, pts, ratio_re,
+                                  ratio_im, nvalid, nthreads);
 }

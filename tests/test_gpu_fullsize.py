@@ -1,11 +1,15 @@
-"""Parity at the full MWA-like size, in the launch configuration bench.py
-times: 256^2 grid, 768 channels, 20 log rings (M = 384), one 64^3 channel
-block per bs_mabs call.  The full channel cube cannot be stored, so the
-check samples the folded collapsed plane: for chosen ring triples and
-separations the oracle evaluates the mean of Eq. (estimator_t) over the
-block's channel triples directly (closed-triangle enumeration), and the
-kappa-normalised error is formed with the oracle's value on |V|.  Counts of
-all 1540 ring triples are compared exactly."""
+"""Parity at the full MWA-like size: 256^2 grid, 768 channels, 20 log rings
+(M = 384), one 64^3 channel block per bs_mabs call, and the exact
+128 x 128 x 256 block the benchmark times.  The full channel cube cannot be
+stored, so the check samples the folded collapsed plane: for chosen ring
+triples and separations the oracle evaluates the mean of Eq. (estimator_t)
+over the block's channel triples directly (closed-triangle enumeration), and
+the kappa-normalised error is formed with the oracle's value on |V|.  At
+every sampled point the error bound of bs_mabs_error_bound must cover the
+error, and well-conditioned points (kappa u <= tol / 10) must meet the
+tolerance in relative error.  Counts of all 1540 ring triples are compared
+exactly.  A 512^2 grid with 24 log rings (image side 768) is sampled the
+same way on a small channel block."""
 import numpy as np
 import pytest
 
@@ -17,6 +21,22 @@ pytestmark = pytest.mark.gpu
 NT, NC, NB = 256, 768, 20
 EDGES = synth.edges_log(NB, 4.41, 128.0)
 BLOCK = 64
+UNIT = {0: 2.0 ** -24, 1: 2.0 ** -17, 2: 2.0 ** -22}
+
+
+def _check_points(got, want, babs, beta, precision, tol, label):
+    """kappa-normalised error, bound coverage and the relative error of
+    well-conditioned points at sampled points."""
+    err = np.abs(got - want.real)
+    ek = err / babs.real
+    kappa = babs.real / np.abs(want.real)
+    good = kappa * UNIT[precision] <= tol / 10
+    print(f"{label}: kappa-normalised error max {ek.max():.3e}; error/bound max "
+          f"{(err / beta).max():.2e}; kappa range {kappa.min():.3g}..{kappa.max():.3g}, "
+          f"{good.sum()} of {good.size} well-conditioned")
+    assert ek.max() < tol, ek
+    assert np.all(err <= beta + 1e-13 * babs.real), err / beta
+    assert np.all(err[good] / np.abs(want.real[good]) <= tol)
 
 
 def _points(T, trips):
@@ -50,6 +70,7 @@ def test_mwa_block_sampled_parity(precision, multires, tol):
     n2 = 2 * NC - 1
     out = torch.empty((1, plan.ntrip, n2, n2), dtype=torch.float64, device="cuda")
     plan.mabs_delta(out)
+    bound, _ = plan.error_bound()
     tri, _ = plan.counts()
     torch.cuda.synchronize()
     Tor = oracle.counts(NT, EDGES)
@@ -61,12 +82,88 @@ def test_mwa_block_sampled_parity(precision, multires, tol):
     babs, _ = oracle.delta_points(np.abs(sub), EDGES, pts)
     got = np.array([out[0, trips.index(tuple(p[:3])), p[3] + NC - 1, p[4] + NC - 1].item()
                     for p in pts])
+    beta = np.array([bound[0, trips.index(tuple(p[:3]))].item() for p in pts])
     plan.close()
     assert np.all(cnt > 0)
-    err = np.abs(got - want.real) / babs.real
-    print(f"precision {precision} multires {multires}: sampled kappa-normalised error max "
-          f"{err.max():.3e}")
-    assert err.max() < tol, err
+    _check_points(got, want, babs, beta, precision, tol,
+                  f"precision {precision} multires {multires}")
+
+
+def test_bench_block_sampled_parity():
+    """The benchmark's exact launch: split BF16, per-triple image sides, the
+    128 x 128 x 256 channel block (nu3 over 256 channels)."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2506_10526_gb300 as bs
+    vis = synth.sky_visibilities(NT, NC, 2000, f_ng=0.5, sigma=0.5)
+    plan = bs.Plan(NT, NC, EDGES, precision=1, multires=True)
+    plan.grid_load(torch.from_numpy(vis[None]).cuda())
+    blk = (0, 128, 0, 128, 0, 256)
+    plan.mabs(block=blk, accumulate=True)
+    n2 = 2 * NC - 1
+    out = torch.empty((1, plan.ntrip, n2, n2), dtype=torch.float64, device="cuda")
+    plan.mabs_delta(out)
+    bound, _ = plan.error_bound()
+    tri, _ = plan.counts()
+    torch.cuda.synchronize()
+    trips = oracle.ring_triples(NB)
+    idx = [k for k in range(len(trips)) if tri[k] > 0]
+    chosen = idx[:4] + [idx[len(idx) // 4], idx[len(idx) // 3]]
+    ds = [(0, 0), (100, -3), (-17, 90), (127, 127), (-200, -90), (-250, -130)]  # all sampled
+    pts = [(*trips[k], *ds[n % len(ds)]) for n, k in enumerate(chosen)]
+    pts += [(*trips[k], 1, 0) for k in chosen[:3]]
+    sub = vis[:256].astype(np.complex128)
+    want, cnt = oracle.delta_points(sub, EDGES, pts, block=blk)
+    babs, _ = oracle.delta_points(np.abs(sub), EDGES, pts, block=blk)
+    got = np.array([out[0, trips.index(tuple(p[:3])), p[3] + NC - 1, p[4] + NC - 1].item()
+                    for p in pts])
+    beta = np.array([bound[0, trips.index(tuple(p[:3]))].item() for p in pts])
+    plan.close()
+    assert np.all(cnt > 0)
+    _check_points(got, want, babs, beta, 1, 1e-3, "bench block 128 x 128 x 256")
+
+
+@pytest.mark.parametrize("precision,multires", [(1, True), (0, False)])
+def test_grid_512_with_24_log_rings(precision, multires):
+    """512^2 grid, 24 log rings |U| in [4.41, 256): a single image side of 768
+    (FP32), or per-triple sides up to 768 (split BF16); 8 channels.  Points
+    on ring triples at the largest side and at small ones."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2506_10526_gb300 as bs
+    nt, nc, nb = 512, 8, 24
+    edges = synth.edges_log(nb, 4.41, 256.0)
+    vis = synth.sky_visibilities(nt, nc, 4000, f_ng=0.5, sigma=0.5)
+    plan = bs.Plan(nt, nc, edges, precision=precision, multires=multires)
+    plan.grid_load(torch.from_numpy(vis[None]).cuda())
+    plan.mabs(accumulate=True)
+    n2 = 2 * nc - 1
+    out = torch.empty((1, plan.ntrip, n2, n2), dtype=torch.float64, device="cuda")
+    plan.mabs_delta(out)
+    bound, _ = plan.error_bound()
+    tri, _ = plan.counts()
+    sides = plan.trip_sides()
+    torch.cuda.synchronize()
+    assert plan.M == 768 and sides.max() == 768
+    trips = oracle.ring_triples(nb)
+    Tor = oracle.counts(nt, edges)
+    np.testing.assert_array_equal(tri, [Tor[t] for t in trips])
+    big = [k for k in range(len(trips)) if tri[k] > 0 and sides[k] == 768 and trips[k][0] <= 12]
+    small = [k for k in range(len(trips)) if tri[k] > 0 and trips[k][2] <= 6]
+    chosen = big[:3] + small[:3]
+    assert len(chosen) == 6
+    pts = [(*trips[k], d1, d2) for k in chosen for d1, d2 in ((0, 0), (3, -2))]
+    want, cnt = oracle.delta_points(vis.astype(np.complex128), edges, pts)
+    babs, _ = oracle.delta_points(np.abs(vis).astype(np.complex128), edges, pts)
+    got = np.array([out[0, trips.index(tuple(p[:3])), p[3] + nc - 1, p[4] + nc - 1].item()
+                    for p in pts])
+    beta = np.array([bound[0, trips.index(tuple(p[:3]))].item() for p in pts])
+    plan.close()
+    assert np.all(cnt > 0)
+    tol = {0: 1e-5, 1: 1e-3}[precision]
+    _check_points(got, want, babs, beta, precision, tol, f"512^2 precision {precision}")
 
 
 def test_mwa_delay_transform_full_size():

@@ -311,6 +311,33 @@ def test_collapse_fold_ratio_identity():
             assert g == pytest.approx(w, rel=1e-12, abs=1e-12 * np.nanmax(np.abs(bbar[k])))
 
 
+def test_delta_points_rectangular_block():
+    """The collapsed-plane points of a rectangular channel block (nu1, nu2 in
+    one range, nu3 in another) against a brute-force mean over the full
+    cube's channel triples inside the block."""
+    vis, edges = _cfg_small(nc=7)
+    res = oracle.mabs_full(vis, edges)
+    nc = 7
+    blk = (1, 4, 0, 3, 2, 7)
+    k = int(np.nonzero(res["T"] > 0)[0][-1])
+    i, j, l = res["triples"][k]
+    pts = [(i, j, l, d1, d2) for d1, d2 in [(0, 0), (1, -1), (-2, -3), (-1, 0), (3, 3)]]
+    got, cnt = oracle.delta_points(vis, edges, pts, block=blk)
+    for p, g, c in zip(pts, got, cnt):
+        vals = []
+        for sgn in ((1,) if p[3] == p[4] == 0 else (1, -1)):
+            d1, d2 = sgn * p[3], sgn * p[4]
+            for n3 in range(blk[4], blk[5]):
+                n1, n2 = n3 + d1, n3 + d2
+                if blk[0] <= n1 < blk[1] and blk[2] <= n2 < blk[3]:
+                    vals.append(res["B"][k, n1, n2, n3])
+        assert c == len(vals)
+        if vals:
+            assert g == pytest.approx(np.mean(vals), rel=1e-12, abs=1e-12 * np.abs(vals).max())
+        else:
+            assert np.isnan(g)
+
+
 def _placed(plane, nc, lo):
     """Put the separations n = lo .. lo + nc - 1 of a centred plane at
     indices n mod nc (one full period of the nc-periodic DFT kernel)."""
