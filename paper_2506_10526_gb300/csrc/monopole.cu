@@ -26,14 +26,19 @@
 // of a shape edge or an acceptance limit.  Values and sums are FP64; the
 // model of Eq. (bsana) takes FP64 squared lengths from FP64 tables.
 //
-// Kernel: grid (chunks of one plane, planes).  A CTA walks its chunk in
-// passes of kThreads x kRun consecutive samples.  Each thread decides the
-// bins of kRun consecutive samples, then, per realisation, the CTA stages the
-// pass's values in shared memory with coalesced loads (rows padded by one
-// element against bank conflicts) and each thread sums its samples in runs
-// of equal bin (neighbouring delay modes mostly share a bin), flushing a run
-// to the CTA's shared-memory histogram when the bin changes.  The CTA adds its
-// non-empty bins to the global sums with FP64 atomics.
+// The bin of a sample depends only on the geometry (k tables, edges, bin
+// counts, closable ring triples), not on the values, so the plan keeps an
+// int16 table of the bins of every sample and rebuilds it only when the
+// geometry changes (k_mono_bins: one thread per sample).  The summing kernel
+// (k_mono_sum) then streams the table and the values with coalesced loads:
+// each warp walks a contiguous range 32 samples at a time; when all 32 share
+// the warp's running bin each lane adds its value to its own per-realisation
+// running sums, which are reduced across the warp and flushed to the CTA's
+// shared-memory histogram only when the bin changes (neighbouring delay modes
+// mostly share a bin); mixed groups add per lane.  One FP64 add per sample
+// and realisation remains: the GB300 FP64 rate (about 0.5e12 adds/s
+// measured), not HBM, is what bounds the kernel.  The CTA adds its non-empty
+// bins to the global sums with FP64 atomics.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -46,9 +51,7 @@ namespace bsi {
 
 namespace {
 
-constexpr int kRun = 16;      // consecutive samples per thread and pass
 constexpr int kThreads = 256;
-constexpr int kPass = kThreads * kRun;
 constexpr int kMaxBatch = 8;  // realisations per launch (the host loops over more)
 constexpr int kMonoMaxK1 = 1024;
 constexpr int kMonoMaxShape = 1024;
@@ -67,7 +70,7 @@ struct MonoArgs {
   const double *kpar64;  // [nc]
   const float *thr;      // E [n_k1 + 1] | cmu [n_mu + 1] | ct [n_t + 1]
   int nc, n_k1, n_mu, n_t, nbin;
-  int chunk;             // samples per CTA, a multiple of kPass (nc^2 < 2^31)
+  int chunk;             // samples per CTA, a multiple of 256 (nc^2 < 2^31)
   int model;
   double f2, p_amp, p_half;  // 2 f_NG, amplitude, p_index / 2
   double *sums;          // [batch_total][nbin]
@@ -116,101 +119,121 @@ __device__ __forceinline__ double model_value(const MonoArgs &a, int i, int j, i
   return a.f2 * (P1 * P2 + P2 * P3 + P3 * P1);
 }
 
-__global__ void __launch_bounds__(kThreads) k_bs_monopole(const MonoArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  double *stage = reinterpret_cast<double *>(smem_raw);                   // [kThreads][kRun + 1]
-  double *hs = stage + kThreads * (kRun + 1);                              // [nbatch][nbin]
-  unsigned *hc = reinterpret_cast<unsigned *>(hs + (size_t)a.nbatch * a.nbin);  // [nbin]
-  float *thr = reinterpret_cast<float *>(hc + a.nbin);
+// Bin of every sample of every closable plane: bins[p][e], e = (a + nc/2) nc + b + nc/2.
+__global__ void __launch_bounds__(kThreads) k_mono_bins(const MonoArgs a, long long total,
+                                                        int16_t *__restrict__ bins) {
+  __shared__ float thr_s[3 * (kMonoMaxShape + 1) + kMonoMaxK1 + 1];
   const int nthr = a.n_k1 + a.n_mu + a.n_t + 3;
-  float *E = thr, *cmu = thr + a.n_k1 + 1, *ct = cmu + a.n_mu + 1;
+  for (int q = threadIdx.x; q < nthr; q += blockDim.x) thr_s[q] = a.thr[q];
+  __syncthreads();
+  const float *E = thr_s, *cmu = thr_s + a.n_k1 + 1, *ct = cmu + a.n_mu + 1;
+  const long long n = (long long)a.nc * a.nc;
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < total;
+       x += (long long)gridDim.x * blockDim.x) {
+    const int p = (int)(x / n);
+    const int e = (int)(x - (long long)p * n);
+    const int ia = e / a.nc, ib = e - ia * a.nc;
+    const int i = a.rings[3 * p], j = a.rings[3 * p + 1], l = a.rings[3 * p + 2];
+    bins[x] = (int16_t)bin_of(a, E, cmu, ct, a.kperp[i], a.kperp[j], a.kperp[l], a.kpar[ia],
+                              a.kpar[ib]);
+  }
+}
+
+constexpr int kSumUnroll = 8;  // groups of 32 samples loaded ahead per warp
+
+template <int NB>  // realisations per launch held in registers (a.nbatch <= NB)
+__global__ void __launch_bounds__(kThreads) k_mono_sum(const MonoArgs a,
+                                                       const int16_t *__restrict__ bins) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double *hs = reinterpret_cast<double *>(smem_raw);                             // [nbatch][nbin]
+  unsigned *hc = reinterpret_cast<unsigned *>(hs + (size_t)a.nbatch * a.nbin);  // [nbin]
   const int p = blockIdx.y;
   for (int q = threadIdx.x; q < a.nbatch * a.nbin; q += blockDim.x) hs[q] = 0.0;
   for (int q = threadIdx.x; q < a.nbin; q += blockDim.x) hc[q] = 0u;
-  for (int q = threadIdx.x; q < nthr; q += blockDim.x) thr[q] = a.thr[q];
   __syncthreads();
+  const int nb = a.model ? 1 : a.nbatch;
   const int i = a.rings[3 * p], j = a.rings[3 * p + 1], l = a.rings[3 * p + 2];
-  const float kpi = a.kperp[i], kpj = a.kperp[j], kpl = a.kperp[l];
   const int n = a.nc * a.nc;
-  const int e0 = blockIdx.x * a.chunk, e1 = min(n, e0 + a.chunk);
+  const int c0 = blockIdx.x * a.chunk, c1 = min(n, c0 + a.chunk);
+  // this warp's contiguous range
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = kThreads / 32;
+  const int per = ((c1 - c0 + nw - 1) / nw + 31) / 32 * 32;
+  const int w0 = min(c1, c0 + warp * per), w1 = min(c1, w0 + per);
+  const int16_t *bp = bins + (long long)p * n;
   const double *vb = a.b3d ? a.b3d + (long long)a.b0 * a.bstride + (long long)p * n : nullptr;
-  double *my = stage + threadIdx.x * (kRun + 1);
 
-  for (int pass = e0; pass < e1; pass += kPass) {
-    const int base = pass + threadIdx.x * kRun;  // this thread's first sample
-    int q[kRun];
-    {
-      int ia = base / a.nc, ib = base - ia * a.nc;  // row a + nc/2, column b + nc/2
-      float ka = ia < a.nc ? a.kpar[ia] : 0.0f;
+  // The warp's running bin (uniform across the warp) and count; each lane keeps
+  // its own per-realisation running sums (one FP64 add per sample: the FP64 rate
+  // of the part bounds this kernel), reduced across the warp only when flushed.
+  int cur = -1;
+  unsigned cnt = 0;
+  double run[NB];
 #pragma unroll
-      for (int k = 0; k < kRun; ++k) {
-        q[k] = -1;
-        if (base + k < e1) q[k] = bin_of(a, E, cmu, ct, kpi, kpj, kpl, ka, a.kpar[ib]);
-        if (++ib == a.nc) {
-          ib = 0;
-          ++ia;
-          ka = ia < a.nc ? a.kpar[ia] : 0.0f;
+  for (int b = 0; b < NB; ++b) run[b] = 0.0;
+  auto flush = [&]() {
+    if (cur >= 0) {
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        if (b >= nb) break;
+        double x = run[b];
+        for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) atomicAdd(hs + (size_t)b * a.nbin + cur, x);
+      }
+      if (lane == 0) atomicAdd(hc + cur, cnt);
+    }
+    cnt = 0;
+#pragma unroll
+    for (int b = 0; b < NB; ++b) run[b] = 0.0;
+  };
+  for (int g0 = w0; g0 < w1; g0 += 32 * kSumUnroll) {
+    int q[kSumUnroll];
+    double v[kSumUnroll][NB];
+    // bins and values are loaded together (no load waits on another)
+#pragma unroll
+    for (int u = 0; u < kSumUnroll; ++u) {
+      const int e = g0 + 32 * u + lane;
+      q[u] = e < w1 ? (int)bp[e] : -1;
+#pragma unroll
+      for (int b = 0; b < NB; ++b)
+        v[u][b] = (!a.model && b < nb && e < w1) ? __ldg(vb + (long long)b * a.bstride + e) : 0.0;
+    }
+    if (a.model) {
+#pragma unroll
+      for (int u = 0; u < kSumUnroll; ++u) {
+        const int e = g0 + 32 * u + lane;
+        if (q[u] >= 0) {
+          const int ia = e / a.nc;
+          v[u][0] = model_value(a, i, j, l, ia, e - ia * a.nc);
         }
       }
     }
-    // counts: runs of equal bin, one shared atomic per run
-    {
-      int cur = -1;
-      unsigned run = 0;
 #pragma unroll
-      for (int k = 0; k < kRun; ++k) {
-        if (q[k] != cur) {
-          if (cur >= 0 && run) atomicAdd(hc + cur, run);
-          cur = q[k];
-          run = 0;
+    for (int u = 0; u < kSumUnroll; ++u) {
+      const int q0 = __shfl_sync(0xffffffffu, q[u], 0);
+      if (__all_sync(0xffffffffu, q[u] == q0)) {
+        if (q0 != cur) {
+          flush();
+          cur = q0;
         }
-        ++run;
+        if (cur >= 0) {
+          cnt += 32;
+#pragma unroll
+          for (int b = 0; b < NB; ++b)
+            if (b < nb) run[b] += v[u][b];
+        }
+      } else {  // mixed bins: close the run, then every lane adds its own sample
+        flush();
+        cur = -1;
+        if (q[u] >= 0) {
+          atomicAdd(hc + q[u], 1u);
+#pragma unroll
+          for (int b = 0; b < NB; ++b)
+            if (b < nb) atomicAdd(hs + (size_t)b * a.nbin + q[u], v[u][b]);
+        }
       }
-      if (cur >= 0 && run) atomicAdd(hc + cur, run);
-    }
-    for (int b = 0; b < (a.model ? 1 : a.nbatch); ++b) {
-      double v[kRun];
-      if (a.model) {
-        int ia = base / a.nc, ib = base - ia * a.nc;
-#pragma unroll
-        for (int k = 0; k < kRun; ++k) {
-          v[k] = q[k] >= 0 ? model_value(a, i, j, l, ia, ib) : 0.0;
-          if (++ib == a.nc) { ib = 0; ++ia; }
-        }
-      } else {
-        // coalesced staging of this pass's values: element e -> stage[e / kRun][e % kRun]
-        const double *src = vb + (long long)b * a.bstride + pass;
-        const int m = min(kPass, e1 - pass);
-        double ld[kRun];
-#pragma unroll
-        for (int k = 0; k < kRun; ++k) {
-          const int e = threadIdx.x + k * kThreads;
-          ld[k] = e < m ? __ldg(src + e) : 0.0;
-        }
-        __syncthreads();  // the previous realisation's reads are done
-#pragma unroll
-        for (int k = 0; k < kRun; ++k) {
-          const int e = threadIdx.x + k * kThreads;
-          stage[(e / kRun) * (kRun + 1) + (e % kRun)] = ld[k];
-        }
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < kRun; ++k) v[k] = my[k];
-      }
-      int cur = -1;
-      double run = 0.0;
-#pragma unroll
-      for (int k = 0; k < kRun; ++k) {
-        if (q[k] != cur) {
-          if (cur >= 0) atomicAdd(hs + (size_t)b * a.nbin + cur, run);
-          cur = q[k];
-          run = 0.0;
-        }
-        if (cur >= 0) run += v[k];
-      }
-      if (cur >= 0) atomicAdd(hs + (size_t)b * a.nbin + cur, run);
     }
   }
+  flush();
   __syncthreads();
   for (int q = threadIdx.x; q < a.nbin; q += blockDim.x) {
     const unsigned c = hc[q];
@@ -307,10 +330,9 @@ __global__ void __launch_bounds__(kCylThreads) k_bs_cylindrical(
 
 }  // namespace
 
-// Bytes of shared memory the kernel needs for nbatch realisations.
-static size_t mono_smem(int nbin, int nbatch, int n_k1, int n_mu, int n_t) {
-  return (size_t)kThreads * (kRun + 1) * 8 + (size_t)nbatch * nbin * 8 + (size_t)nbin * 4 +
-         (size_t)(n_k1 + n_mu + n_t + 3) * 4;
+// Bytes of shared memory the summing kernel needs for nbatch realisations.
+static size_t mono_smem(int nbin, int nbatch) {
+  return (size_t)nbatch * nbin * 8 + (size_t)nbin * 4;
 }
 
 }  // namespace bsi
@@ -355,7 +377,7 @@ bs_status bs_bs_monopole(bs_plan p, const double *b3d, const double *kperp_host,
   const int nbin = n_k1 * n_mu * n_t;
   const int batch = b3d ? p->batch : 1;
   const int per = std::min(batch, kMaxBatch);
-  if (mono_smem(nbin, per, n_k1, n_mu, n_t) > (size_t)200 * 1024)
+  if (mono_smem(nbin, per) > (size_t)200 * 1024)
     return fail(p, BS_ERR_UNSUPPORTED, "bs_bs_monopole: too many bins for one CTA's histogram");
   MONO_CUDA(cudaMemsetAsync(sum_dev, 0, (size_t)batch * nbin * sizeof(double), s));
   MONO_CUDA(cudaMemsetAsync(count_dev, 0, (size_t)nbin * sizeof(int64_t), s));
@@ -390,7 +412,10 @@ bs_status bs_bs_monopole(bs_plan p, const double *b3d, const double *kperp_host,
   std::memcpy(tab.data() + off32, f32.data(), f32.size() * 4);
   unsigned char *dtab = p->at<unsigned char>(p->L.mono);
   MONO_CUDA(cudaMemcpyAsync(dtab, tab.data(), tab.size(), cudaMemcpyHostToDevice, s));
-  MONO_CUDA(smem_optin_once<k_bs_monopole>());
+  MONO_CUDA(smem_optin_once<k_mono_sum<1>>());
+  MONO_CUDA(smem_optin_once<k_mono_sum<2>>());
+  MONO_CUDA(smem_optin_once<k_mono_sum<4>>());
+  MONO_CUDA(smem_optin_once<k_mono_sum<kMaxBatch>>());
   MonoArgs a{};
   a.b3d = b3d;
   a.bstride = (long long)npl * nc * nc;
@@ -411,19 +436,53 @@ bs_status bs_bs_monopole(bs_plan p, const double *b3d, const double *kperp_host,
   a.p_half = 0.5 * p_index;
   a.sums = sum_dev;
   a.cnt = reinterpret_cast<unsigned long long *>(count_dev);
-  // CTAs of about 16 passes (64 Ki samples): few global flushes, several CTAs per plane
+  // the bin table: rebuilt only when the geometry (tables, bin counts, planes) changed
+  std::vector<unsigned char> key(tab);
+  const int dims[3] = {n_k1, n_mu, n_t};
+  key.insert(key.end(), reinterpret_cast<const unsigned char *>(dims),
+             reinterpret_cast<const unsigned char *>(dims) + sizeof(dims));
+  key.insert(key.end(), reinterpret_cast<const unsigned char *>(p->clos.data()),
+             reinterpret_cast<const unsigned char *>(p->clos.data() + p->clos.size()));
+  const long long total = (long long)npl * nc * nc;
+  if (!p->mono_bins || key != p->mono_key) {
+    if ((size_t)total > p->mono_bins_cap) {
+      if (p->mono_bins) MONO_CUDA(cudaFree(p->mono_bins));
+      p->mono_bins = nullptr;
+      p->mono_bins_cap = 0;
+      void *m = nullptr;
+      const cudaError_t e = cudaMalloc(&m, (size_t)total * sizeof(int16_t));
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(p, BS_ERR_OOM, "bs_bs_monopole: bin table allocation failed");
+      }
+      p->mono_bins = static_cast<int16_t *>(m);
+      p->mono_bins_cap = (size_t)total;
+    }
+    const int grid = (int)std::min<long long>((total + kThreads - 1) / kThreads, 152LL * 64);
+    k_mono_bins<<<grid, kThreads, 0, s>>>(a, total, p->mono_bins);
+    MONO_CUDA(cudaGetLastError());
+    p->mono_key.swap(key);
+  }
+  // CTAs of 64 Ki samples (8 Ki per warp): few flushes, several CTAs per plane
   const int n = nc * nc;
-  const int per_cta = kPass * 16;
+  const int per_cta = 65536;
   const int nx = std::max(1, (n + per_cta - 1) / per_cta);
-  a.chunk = ((n + nx - 1) / nx + kPass - 1) / kPass * kPass;
+  a.chunk = ((n + nx - 1) / nx + 255) / 256 * 256;
   const int gx = (n + a.chunk - 1) / a.chunk;
   for (int b0 = 0; b0 < batch; b0 += per) {
     a.b0 = b0;
     a.nbatch = std::min(per, batch - b0);
     if (b0 > 0) a.cnt = nullptr;  // the same samples: counted by the first launch
     const dim3 grid(gx, npl);
-    const size_t sm = mono_smem(nbin, a.nbatch, n_k1, n_mu, n_t);
-    k_bs_monopole<<<grid, kThreads, sm, s>>>(a);
+    const size_t sm = mono_smem(nbin, a.nbatch);
+    if (a.nbatch == 1)
+      k_mono_sum<1><<<grid, kThreads, sm, s>>>(a, p->mono_bins);
+    else if (a.nbatch == 2)
+      k_mono_sum<2><<<grid, kThreads, sm, s>>>(a, p->mono_bins);
+    else if (a.nbatch <= 4)
+      k_mono_sum<4><<<grid, kThreads, sm, s>>>(a, p->mono_bins);
+    else
+      k_mono_sum<kMaxBatch><<<grid, kThreads, sm, s>>>(a, p->mono_bins);
     MONO_CUDA(cudaGetLastError());
   }
   return BS_OK;

@@ -722,10 +722,6 @@ bs_status bs_plan_create(const bs_plan_desc *desc, bs_plan *out) {
     rmax[m] = std::max(rmax[m], r);
   }
   p->multires = d.multires != 0;
-  if (p->multires && d.precision == BS_PREC_FP32) {
-    delete p;
-    return fail(nullptr, BS_ERR_UNSUPPORTED, "multires needs a tensor-core (split BF16 or split FP16) path");
-  }
   p->lev_of_trip.assign(p->ntrip, -1);
   if (!p->multires) {
     Level lv;
@@ -828,6 +824,10 @@ bs_status bs_plan_destroy(bs_plan p) {
   if (p->ws && p->ws_owned) {
     cudaSetDevice(p->device);
     cudaFree(p->ws);
+  }
+  if (p->mono_bins) {
+    cudaSetDevice(p->device);
+    cudaFree(p->mono_bins);
   }
   delete p;
   return BS_OK;
@@ -945,39 +945,44 @@ bs_status bs_mabs(bs_plan p, const int32_t *block, double *out_full, int accumul
   const WsLayout &L = p->L;
   const long long full_bstride = (long long)p->ntrip * nc * nc * nc;
   if (out_full) BS_CUDA(launch_full_fill(out_full, full_bstride, p->batch, p->ntrip, nc, blk, 0.0, s));
-  if (p->d.precision != BS_PREC_FP32 || p->multires) {
+  if (p->d.precision != BS_PREC_FP32) {
     st = mabs_tc(p, blk, out_full, accumulate, s);
     if (st != BS_OK) return st;
   } else {
-    // work list: ring pairs (i <= j) x column tiles over (l, nu3), T(i,j,l) > 0, nu3 valid
-    p->h_cols.clear();
-    p->h_ptiles.clear();
+    // one launch per image side: work list of ring pairs (i <= j) x column tiles over
+    // (l, nu3) with T(i,j,l) > 0 at this side and nu3 valid; rings are this level's slots
     const int nb = p->nb;
-    for (int i = 0; i < nb; ++i)
-      for (int j = i; j < nb; ++j) {
-        const int off = (int)p->h_cols.size();
-        for (int l = j; l < nb; ++l) {
-          const int t = p->trip_of[((size_t)i * nb + j) * nb + l];
-          if (p->T[t] <= 0) continue;
-          for (int n3 = blk[4]; n3 < blk[5]; ++n3)
-            if (p->valid[n3]) p->h_cols.push_back(ColEntry{l * nc + n3, t, n3, 0});
+    for (int li = 0; li < (int)p->levels.size(); ++li) {
+      const Level &lv = p->levels[li];
+      if (lv.nslot == 0) continue;
+      p->h_cols.clear();
+      p->h_ptiles.clear();
+      for (int i = 0; i < nb; ++i)
+        for (int j = i; j < nb; ++j) {
+          const int off = (int)p->h_cols.size();
+          for (int l = j; l < nb; ++l) {
+            const int t = p->trip_of[((size_t)i * nb + j) * nb + l];
+            if (p->T[t] <= 0 || p->lev_of_trip[t] != li) continue;
+            for (int n3 = blk[4]; n3 < blk[5]; ++n3)
+              if (p->valid[n3]) p->h_cols.push_back(ColEntry{lv.slot_of[l] * nc + n3, t, n3, 0});
+          }
+          const int ncol = (int)p->h_cols.size() - off;
+          for (int c0 = 0; c0 < ncol; c0 += 128)
+            p->h_ptiles.push_back(PairTile{lv.slot_of[i], lv.slot_of[j], off, ncol, c0, {0, 0, 0}});
         }
-        const int ncol = (int)p->h_cols.size() - off;
-        for (int c0 = 0; c0 < ncol; c0 += 128) p->h_ptiles.push_back(PairTile{i, j, off, ncol, c0, {0, 0, 0}});
-      }
-    const int n_r1 = (blk[1] - blk[0] + 15) / 16, n_r2 = (blk[3] - blk[2] + 7) / 8;
-    const int npt = (int)p->h_ptiles.size();
-    if (npt > 0 && n_r1 > 0 && n_r2 > 0) {
+      const int n_r1 = (blk[1] - blk[0] + 15) / 16, n_r2 = (blk[3] - blk[2] + 7) / 8;
+      const int npt = (int)p->h_ptiles.size();
+      if (npt == 0 || n_r1 == 0 || n_r2 == 0) continue;
       if (npt > 65535) return fail(p, BS_ERR_UNSUPPORTED, "too many column tiles in one block");
       BS_CUDA(cudaMemcpyAsync(p->at<ColEntry>(L.cols), p->h_cols.data(),
                               p->h_cols.size() * sizeof(ColEntry), cudaMemcpyHostToDevice, s));
       BS_CUDA(cudaMemcpyAsync(p->at<PairTile>(L.ptiles), p->h_ptiles.data(),
                               p->h_ptiles.size() * sizeof(PairTile), cudaMemcpyHostToDevice, s));
       ContractArgs a{};
-      a.F = p->at<float>(L.F);
-      a.fstride = (long long)p->M * p->M;
-      a.bstride = (long long)p->nf * p->M * p->M;
-      a.M2 = p->M * p->M;
+      a.F = p->at<float>(lv.offF);
+      a.fstride = (long long)lv.M * lv.M;
+      a.bstride = (long long)lv.nslot * nc * lv.M * lv.M;
+      a.M2 = lv.M * lv.M;
       a.nc = nc;
       a.cols = p->at<ColEntry>(L.cols);
       a.ptiles = p->at<PairTile>(L.ptiles);

@@ -63,6 +63,12 @@ struct bs_plan_s {
   std::vector<int> clos;          // ring triples with T > 0, ascending (device copy at L.clos)
   std::vector<int> closrings;     // [clos.size()][3] rings (i, j, l) of those triples
   std::vector<unsigned char> mono_tab;  // k tables and thresholds of the last monopole call
+  // bin of every monopole sample [n_c][nchan][nchan] (int16, -1 dropped) for the
+  // geometry in mono_key (k tables, edges, bin counts, closable triples); device,
+  // allocated at the first monopole call, freed with the plan
+  int16_t *mono_bins = nullptr;
+  size_t mono_bins_cap = 0;
+  std::vector<unsigned char> mono_key;
   std::vector<int> cyl_tab;       // row bins and column ranges of the last cylindrical call
   std::vector<long long> cyl_cnt; // its per-bin counts
   std::vector<int> err_tab;       // [ntrip][4] rings (i, j, l) and level, for the error bound
