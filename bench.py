@@ -66,11 +66,11 @@ PROFILES = {"fp32": (os.path.join(ROOT, "profiles", "contract_simt_mwa.txt"),
 # tensor-core products per algorithmic product, and the operand dtype label
 SPLIT_PRODUCTS = {"split_bf16": 3, "split_fp16": 3}
 DTYPE = {"fp32": "f32", "split_bf16": "bf16x3", "split_fp16": "fp16x3"}
-# maximum kappa-normalised error against the FP64 oracle measured by the GPU
-# parity tests (tests/test_gpu_parity.py, tests/test_gpu_fullsize.py)
-STATED_ERROR = {"fp32": "kappa-normalised error <= 1e-5 (measured 3.1e-7)",
-                "split_bf16": "kappa-normalised error <= 1e-3 (measured 1.3e-6)",
-                "split_fp16": "kappa-normalised error <= 1e-4 (measured 6.2e-7)"}
+# error targets against the FP64 oracle (kappa-normalised, and relative on
+# well-conditioned bins) and the unit u of each arithmetic for the
+# well-conditioned test kappa u <= tol / 10
+TOL = {"fp32": 1e-5, "split_bf16": 1e-3, "split_fp16": 1e-4}
+UNIT = {"fp32": 2.0 ** -24, "split_bf16": 2.0 ** -17, "split_fp16": 2.0 ** -22}
 
 
 def parse():
@@ -221,6 +221,63 @@ def cpu_baseline(w, seconds, vis=None):
                       f"{w['nt']}^2 grid, {dt:.1f} s"}
 
 
+def measure_error(plan, vis, edges, blk, out_delta, tri, precision, closable=True):
+    """Error of a step's folded plane against the FP64 oracle, measured in this
+    run: the oracle evaluates the collapsed mean over the block's channel
+    triples at sampled points (the cheapest closable ring triples, and one of
+    medium size; separations from channel triples inside the block), on V and
+    on |V| (B_abs).  Reported: the kappa-normalised error |B - B64| / B_abs,
+    the relative error, and the relative error of the well-conditioned points
+    (kappa u <= tol / 10); and whether the library's own error bound
+    (bs_mabs_error_bound) covers the measured error at every point."""
+    import numpy as np
+    import oracle
+    import torch
+    bound, _ = plan.error_bound()
+    torch.cuda.synchronize()
+    nc = vis.shape[0]
+    trips = oracle.ring_triples(len(edges) - 1)
+    clos = np.flatnonzero(tri > 0)
+    pos = {int(t): k for k, t in enumerate(clos)}
+    chosen = [int(t) for t in clos[:4]] + [int(clos[len(clos) // 5])]
+    b = blk
+    mid3 = (b[4] + b[5]) // 2
+    picks = [(b[0], b[2]), (b[1] - 1, b[3] - 1), ((b[0] + b[1]) // 2, b[2] + 1),
+             (b[0] + 1, (b[2] + b[3]) // 2)]
+    pts = []
+    for n, t in enumerate(chosen):
+        for n1, n2 in (picks[n % len(picks)], picks[(n + 1) % len(picks)]):
+            pts.append((*trips[t], n1 - mid3, n2 - mid3))
+    nmax = max(b[1], b[3], b[5])
+    sub = np.ascontiguousarray(vis[:nmax]).astype(np.complex128)
+    t0 = time.perf_counter()
+    want, cnt = oracle.delta_points(sub, edges, pts, block=b)
+    babs, _ = oracle.delta_points(np.abs(sub), edges, pts, block=b)
+    dt = time.perf_counter() - t0
+    got = np.array([out_delta[0, pos[trips.index(tuple(p[:3]))] if closable else
+                              trips.index(tuple(p[:3])), p[3] + nc - 1, p[4] + nc - 1].item()
+                    for p in pts])
+    beta = np.array([bound[0, trips.index(tuple(p[:3]))].item() for p in pts])
+    want, babs = want.real, babs.real
+    err = np.abs(got - want)
+    kappa = babs / np.abs(want)
+    good = kappa * UNIT[precision] <= TOL[precision] / 10
+    erel = err / np.abs(want)
+    return {"points": len(pts), "kappa_err_max": float((err / babs).max()),
+            "rel_err_max": float(erel.max()),
+            "kappa_min_max": [float(kappa.min()), float(kappa.max())],
+            "well_conditioned": {"points": int(good.sum()), "u": UNIT[precision],
+                                 "tol": TOL[precision],
+                                 "rel_err_max": float(erel[good].max()) if good.any() else None},
+            "bound_covers_every_point": bool(np.all(err <= beta)),
+            "bound_over_error_min": float(np.min(beta / np.maximum(err, 1e-300))),
+            "rel_bound_median": float(np.median(beta / np.abs(want))),
+            "min_triples_per_point": int(cnt.min()),
+            "sample": (f"FP64 oracle collapsed means at {len(pts)} points (ring triples "
+                       f"{sorted(set(tuple(trips[t]) for t in chosen))}) over the channel block "
+                       f"{list(b)}, {dt:.1f} s of CPU")}
+
+
 def run_reference(args, w):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -255,9 +312,15 @@ def run_monopole(plan, b3, stream, nc, reps=5):
     kpar = (np.arange(nc) - nc // 2) * (2 * np.pi / nc)
     kmax = float(np.sqrt(kperp.max() ** 2 + 4 * np.abs(kpar).max() ** 2))
     edges = np.geomspace(0.9 * kperp.min(), 1.01 * kmax, 13)
-    for _ in range(3):
-        sums, cnt = plan.bs_monopole(b3, kperp, kpar, edges, 5, 5)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)  # the first call with this geometry also builds the bin table
+    sums, cnt = plan.bs_monopole(b3, kperp, kpar, edges, 5, 5)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    first_ms = ev[0].elapsed_time(ev[1])
+    for _ in range(2):
+        sums, cnt = plan.bs_monopole(b3, kperp, kpar, edges, 5, 5)
     torch.cuda.synchronize()
     ev[0].record(stream)
     for _ in range(reps):
@@ -286,6 +349,7 @@ def run_monopole(plan, b3, stream, nc, reps=5):
     cms = ev[0].elapsed_time(ev[1]) / reps
     cgbs = samples * 8 / (cms / 1e3) / 1e9
     return {"bins": "12 log k1 x 5 mu x 5 t", "samples": samples, "ms": ms,
+            "first_call_ms": first_ms,
             "samples_per_s": samples / (ms / 1e3), "binned": int(cnt.sum().item()),
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
                          "frac": gbs / peak, "bytes": samples * 8},
@@ -294,8 +358,11 @@ def run_monopole(plan, b3, stream, nc, reps=5):
                             "roofline": {"bound": "hbm", "achieved": cgbs, "peak": peak,
                                          "unit": "GB/s", "frac": cgbs / peak,
                                          "bytes": samples * 8}},
-            "note": "kernels k_bs_monopole<1>, k_bs_cylindrical; model_ms bins Eq. (bsana) "
-                    "(FP64 pow per sample)"}
+            "note": "kernels k_mono_sum<1> (bins from the plan's cached int16 table: 8 B of "
+                    "values + 2 B of bins per sample, one FP64 add per binned sample), "
+                    "k_bs_cylindrical; first_call_ms includes k_mono_bins (the bin decision "
+                    "of every sample, once per geometry); model_ms bins Eq. (bsana) (FP64 pow "
+                    "per sample)"}
 
 
 def run_gridding(plan, nt, nc, stream, reps=5):
@@ -451,9 +518,46 @@ def run_mc(dev, precision, iters=3):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / iters
     _, _, nreal = ens.stats(0, 1)
+    ens.close()
+    # the same realisations one at a time: a plan per shape with batch 1, each
+    # realisation through grid load, full-cube contraction, collapse and Eq. (dft)
+    # as separate calls (sky generation included, as in the batched run)
+    loop = []
+    for k, sp in enumerate(specs):
+        pl = bs.Plan(sp["nt"], sp["nchan"], sp["edges"], precision=precision, multires=True)
+        one_buf = torch.empty((1, sp["nchan"], sp["nt"], sp["nt"]), dtype=torch.complex64,
+                              device=dev)
+        gen1 = bs.SkyGenerator(sp["nt"], sp["nchan"], max_batch=1)
+        gen1.generate(77, 0, out=one_buf)
+        pl.grid_load(one_buf)  # the first load counts the closed triangles
+        ncl = pl.n_closable
+        n2 = 2 * sp["nchan"] - 1
+        dd = torch.empty((1, ncl, n2, n2), dtype=torch.float64, device=dev)
+        b3 = torch.empty((1, ncl, sp["nchan"], sp["nchan"]), dtype=torch.float64, device=dev)
+        loop.append((sp, pl, one_buf, gen1, dd, b3))
+
+    def one_at_a_time(i):
+        for sp, pl, one_buf, gen1, dd, b3 in loop:
+            for r in range(sp["batch"]):
+                gen1.generate(77, i * sp["batch"] + r, out=one_buf)
+                pl.grid_load(one_buf)
+                pl.mabs(accumulate=True)
+                pl.mabs_delta_closable(dd)
+                pl.bs3d_closable(b3)
+
+    one_at_a_time(0)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for i in range(iters):
+        one_at_a_time(2 + i)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    loop_ms = e0.elapsed_time(e1) / iters
+    for sp, pl, one_buf, gen1, dd, b3 in loop:
+        pl.close()
+        gen1.close()
     for gg in gens:
         gg.close()
-    ens.close()
     npr = 3  # tensor products per algorithmic one (split BF16 and split FP16 alike)
     peak = float(measured_peaks().get("bf16_tflops", 1900.0)) / npr
     nr = sum(sp["batch"] for sp in specs)
@@ -463,10 +567,87 @@ def run_mc(dev, precision, iters=3):
             "realisations_per_s": nr / (ms / 1e3), "evals_per_s": evals / (ms / 1e3),
             "tiles_per_sm": tiles, "realisations_accumulated": int(nreal),
             "contraction_flops_frac_of_run": (flops / (ms / 1e3) / 1e12) / peak,
+            "one_at_a_time_ms_per_run": loop_ms, "batched_speedup": loop_ms / ms,
             "note": "one graph replay per run: GPU sky generation, fields, one persistent "
                     "tensor-core launch over all groups, collapse, delay transform, Welford "
                     "statistics; frac = algorithmic contraction FLOP/s over the whole run "
                     f"against the measured BF16 burst peak / {npr} ({npr} split products)"}
+
+
+def run_mc_small(dev, precision, batch=256, loop_real=32, iters=3):
+    """The flagged tiny configuration (64^2 grid, 16 channels, 8 linear rings,
+    coarse-band flags) as a Monte Carlo ensemble: `batch` realisations per run in
+    one graph-replayed persistent launch, against the same realisations one at a
+    time through a batch-1 plan (grid load, contraction, collapse, Eq. (dft) as
+    separate calls; `loop_real` of them timed).  Sky generation is inside both."""
+    import numpy as np
+    import torch
+    import paper_2506_10526_gb300 as bs
+    import synth
+    nt, nc = 64, 16
+    edges = list(synth.edges_linear(8, 32))
+    flags = synth.flag_mask_coarse_band(nc)
+    ens = bs.Ensemble([dict(nt=nt, nchan=nc, edges=edges, batch=batch, multires=True,
+                            precision=precision)])
+    ens.set_flags(0, flags)
+    gen = bs.SkyGenerator(nt, nc, max_batch=batch)
+    buf = torch.empty((batch, nc, nt, nt), dtype=torch.complex64, device=dev)
+    ens.set_input(0, buf)
+    stream = torch.cuda.current_stream()
+
+    def run(i):
+        gen.generate(91, i * batch, out=buf)
+        ens.run(use_graph=True)
+
+    for i in range(2):
+        run(i)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for i in range(iters):
+        run(2 + i)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / iters
+    ens.close()
+    gen.close()
+    pl = bs.Plan(nt, nc, edges, precision=precision, multires=True)
+    g1 = bs.SkyGenerator(nt, nc, max_batch=1)
+    one = torch.empty((1, nc, nt, nt), dtype=torch.complex64, device=dev)
+    g1.generate(91, 0, out=one)
+    pl.grid_load(one, chan_flags=flags)
+    n2 = 2 * nc - 1
+    dd = torch.empty((1, pl.n_closable, n2, n2), dtype=torch.float64, device=dev)
+    b3 = torch.empty((1, pl.n_closable, nc, nc), dtype=torch.float64, device=dev)
+
+    def loop(r0, n):
+        for r in range(r0, r0 + n):
+            g1.generate(91, r, out=one)
+            pl.grid_load(one, chan_flags=flags)
+            pl.mabs(accumulate=True)
+            pl.mabs_delta_closable(dd)
+            pl.bs3d_closable(b3)
+
+    loop(0, 4)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e0.record(stream)
+    loop(4, loop_real)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    wall = (time.perf_counter() - t0) * 1e3
+    loop_ms = max(e0.elapsed_time(e1), wall) / loop_real
+    pl.close()
+    g1.close()
+    return {"shape": "64^2 x 16 ch x 8 linear rings, coarse-band flags", "batch": batch,
+            "ms_per_run": ms, "realisations_per_s": batch / (ms / 1e3),
+            "one_at_a_time_ms_per_realisation": loop_ms,
+            "batched_speedup": loop_ms / (ms / batch),
+            "note": "batched: one graph replay (sky generation, fields, one persistent "
+                    "tensor-core launch, collapse, Eq. (dft), Welford statistics) per run of "
+                    f"{batch} realisations; one at a time: {loop_real} realisations through a "
+                    "batch-1 plan, per-realisation time from the larger of CUDA-event and "
+                    "host wall time (the loop is launch-bound)"}
 
 
 def run_surrogate(dev, steps=200, rows=1 << 17):
@@ -611,6 +792,15 @@ def main():
                       barrier=barrier)
         e2e["clocks"] = eclk.stop()  # runs after the timed region, GPU already warm
     mono = run_monopole(plan, out3d, stream, nc) if world == 1 else None
+    # error of the timed path against the FP64 oracle, measured in this run on the
+    # first block of the job (after the timed region)
+    err_info = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        step(0)
+        err_info = measure_error(plan, vis, edges, jobs[0], out_delta, tri, args.precision)
+    # measured arithmetic ceilings (FP32 / FP64 FMA) for the FP32 path's roofline
+    peak_fp32 = bs.measure_peak("fp32", 1 << 22)
+    peak_fp64 = bs.measure_peak("fp64", 1 << 16)
 
     # roofline of the contraction (dominant kernel): algorithmic FLOPs = 2 M^2 per evaluation
     M = plan.M
@@ -619,9 +809,10 @@ def main():
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     if args.precision == "fp32":
-        peak = SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-        roof = {"bound": "alu", "peak_source": f"FP32 FMA: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 "
-                f"flop x {sm_max:.0f} MHz"}
+        peak = peak_fp32 / 1e12
+        roof = {"bound": "alu", "peak_source": "measured FP32 FMA rate (bs_measure_peak), "
+                f"nominal {SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12:.1f} TFLOP/s at "
+                f"{sm_max:.0f} MHz"}
     else:
         # FP16 and BF16 share the dense tensor rate (kind::f16, nominal ratio 1)
         npr = SPLIT_PRODUCTS[args.precision]
@@ -667,37 +858,69 @@ def main():
     if mono is not None:
         line["monopole"] = mono
         line["gridding"] = run_gridding(plan, nt, nc, stream)
-    line["config"]["stated_error"] = STATED_ERROR[args.precision]
+    line["error"] = err_info
+    line["peaks_measured"] = {"fp32_fma_tflops": peak_fp32 / 1e12,
+                              "fp64_fma_tflops": peak_fp64 / 1e12,
+                              "source": "bs_measure_peak: 8 independent FMA chains per thread, "
+                                        "4 x 256 threads per SM, CUDA events"}
     contraction_rate = per_launch_evals / (avg_ms / 1e3)
     line["contraction_evals_per_s"] = contraction_rate
     plan.close()
-    del out_delta, out3d
+    del out3d
     torch.cuda.empty_cache()
     if not args.no_mc and world == 1 and args.precision != "fp32":
         line["mc"] = run_mc(dev, prec)
+        line["mc_small"] = run_mc_small(dev, prec)
         line["surrogate"] = run_surrogate(dev)
     if args.precision != "fp32" and not args.no_fp32_compare and world == 1:
-        # the plain FP32 GPU path on the same input, timed the same way, on 64^3 blocks
+        # the plain FP32 GPU path (FP32 FFTs, FP32 SIMT contraction) on the same input,
+        # timed the same way on 64^3 blocks: with the same per-triple image sides as the
+        # split path (equal work), and with one image side for every triple
         fb = min(64, w["block"])
-        fp = bs.Plan(nt, nc, edges, precision=bs.PREC_FP32)
-        fp.grid_load(vis_d)
         fjobs = blocks_of(nc, fb)
-        fev = []
-        for i in range(3):
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            fp.mabs(block=fjobs[i % len(fjobs)], accumulate=True)
-            e1.record(stream)
-            fev.append((e0, e1))
-        torch.cuda.synchronize()
-        fms = statistics.mean(a.elapsed_time(b) for a, b in fev[1:])
         fb_evals = nclos * fb ** 3
-        fp32_rate = fb_evals / (fms / 1e3)
-        fp.close()
-        line["fp32_plain"] = {"channel_block": fb, "contraction_evals_per_s": fp32_rate,
-                              "avg_launch_ms": fms, "stated_error": STATED_ERROR["fp32"]}
-        line["speedup_vs_fp32"] = contraction_rate / fp32_rate
+
+        def fp32_rate(mr):
+            fp = bs.Plan(nt, nc, edges, precision=bs.PREC_FP32, multires=mr)
+            fp.grid_load(vis_d)
+            fev = []
+            for i in range(3):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fp.mabs(block=fjobs[i % len(fjobs)], accumulate=True)
+                e1.record(stream)
+                fev.append((e0, e1))
+            torch.cuda.synchronize()
+            fms = statistics.mean(a.elapsed_time(b) for a, b in fev[1:])
+            ferr = None
+            if mr and not args.no_cpu:
+                fp.grid_load(vis_d)
+                fp.mabs(block=fjobs[0], accumulate=True)
+                fp.mabs_delta_closable(out_delta)
+                ferr = measure_error(fp, vis, edges, fjobs[0], out_delta, tri, "fp32")
+            fs = fp.trip_sides()
+            fflops = float(np.sum(2.0 * fs[tri > 0].astype(np.float64) ** 2)) * fb ** 3
+            fp.close()
+            return fb_evals / (fms / 1e3), fms, fflops / (fms / 1e3) / 1e12, ferr
+
+        r_eq, ms_eq, tf_eq, err_eq = fp32_rate(True)
+        r_one, ms_one, tf_one, _ = fp32_rate(False)
+        p32 = peak_fp32 / 1e12
+        line["fp32_plain"] = {
+            "channel_block": fb, "contraction_evals_per_s": r_eq, "avg_launch_ms": ms_eq,
+            "image_sides": "per ring triple, as the split path",
+            "roofline": {"bound": "alu", "achieved": tf_eq, "peak": p32, "unit": "TFLOP/s",
+                         "frac": tf_eq / p32, "peak_source": "measured FP32 FMA rate"},
+            "error": err_eq,
+            "single_side": {"contraction_evals_per_s": r_one, "avg_launch_ms": ms_one,
+                            "achieved_tflops": tf_one, "frac": tf_one / p32}}
+        # precision gain at equal work; the single-side ratio adds the work saved by
+        # per-triple image sides
+        line["speedup_vs_fp32"] = contraction_rate / r_eq
+        line["speedup_vs_fp32_single_side"] = contraction_rate / r_one
+    del out_delta
+    torch.cuda.empty_cache()
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds, vis)
     if rank == 0:

@@ -107,9 +107,9 @@ typedef struct {
                                 smallest M = 2^a x {8, 12} with M > c_i + c_j + c_l and
                                 M > 2 max(c) (c = largest |u| or |v| in a ring): closure
                                 stays exact, the pixel sums shrink with the rings;
-                                fields are kept at each side that some triple needs.
-                                Split-BF16 or split-FP16 only.  0: one M for all
-                                (fft_m rule). */
+                                fields are kept at each side that some triple needs
+                                (every precision; the FP32 path launches once per
+                                side).  0: one M for all (fft_m rule). */
 } bs_plan_desc;
 
 /* ABI version this library was built with (BS_ABI_VERSION). */
@@ -496,6 +496,14 @@ const char *bs_sky_last_error(bs_sky sky);
  * (an earlier CUDA error), BS_ERR_CUDA. */
 bs_status bs_sky_generate(bs_sky sky, uint64_t seed, uint64_t realisation0, int batch,
                           void *vis_dev, void *cuda_stream);
+
+/* Arithmetic ceiling of the current device for roofline fractions (the paper
+ * has no counterpart): kind 0 FP32 FMA, kind 1 FP64 FMA.  Every thread of
+ * 4 x 256-thread blocks per SM runs 8 independent FMA chains for `iters`
+ * steps on registers; *flops_per_s = 2 x FMAs / the launch's CUDA-event time
+ * on cuda_stream (after one short warm-up launch).  Synchronises.
+ * Errors: BS_ERR_ARG (kind, iters < 1, NULL), BS_ERR_NO_DEVICE, BS_ERR_CUDA. */
+bs_status bs_measure_peak(int kind, int iters, double *flops_per_s, void *cuda_stream);
 
 /* Closed-triangle counts T(i,j,l) without any device allocation.
  * The paper has no counterpart: this entry point exists for callers that

@@ -42,7 +42,7 @@ EXPORTS = ("bs_abi_version", "bs_plan_create", "bs_plan_destroy", "bs_last_error
            "bs_mlp_features", "bs_mlp_create", "bs_mlp_destroy", "bs_mlp_last_error",
            "bs_mlp_params", "bs_mlp_fit_norm", "bs_mlp_forward", "bs_mlp_grad", "bs_mlp_train",
            "bs_sky_create", "bs_sky_destroy", "bs_sky_last_error", "bs_sky_generate",
-           "bs_counts_noalloc")
+           "bs_counts_noalloc", "bs_measure_peak")
 
 _lib = None
 _lock = threading.Lock()
@@ -90,6 +90,7 @@ def lib() -> ctypes.CDLL:
             L.bs_check_hermitian.argtypes = [P, P, D, P]
             L.bs_mabs_error_bound.argtypes = [P, P, P, I, P, P]
             L.bs_counts_noalloc.argtypes = [I, I, P, P, P, P]
+            L.bs_measure_peak.argtypes = [I, I, P, P]
             L.bs_sky_create.argtypes = [I, I, D, D, D, I, ctypes.POINTER(P)]
             L.bs_sky_destroy.argtypes = [P]
             L.bs_sky_last_error.argtypes = [P]
@@ -392,6 +393,17 @@ def counts_noalloc(nt: int, edges, tri_out, ngrid=None, stream=None):
         raise BsError(st, "bs_counts_noalloc failed (sizes beyond nt <= 1024, nbins <= 32 are "
                           "rejected)")
 
+
+
+def measure_peak(kind: str = "fp32", iters: int = 1 << 16, stream=None) -> float:
+    """bs_measure_peak: measured FMA rate of the current device in FLOP/s
+    (kind "fp32" or "fp64")."""
+    out = ctypes.c_double(0.0)
+    st = lib().bs_measure_peak({"fp32": 0, "fp64": 1}[kind], int(iters), ctypes.byref(out),
+                               _stream_ptr(stream))
+    if st != BS_OK:
+        raise BsError(st, "bs_measure_peak failed")
+    return out.value
 
 
 class SkyGenerator:

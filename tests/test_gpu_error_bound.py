@@ -103,7 +103,7 @@ def _check(out, b, ref, babs, precision, label):
     assert np.all(err[ok] / babs[ok] <= tol)
 
 
-@pytest.mark.parametrize("precision,multires", [(0, False), (1, True), (1, False), (2, True)])
+@pytest.mark.parametrize("precision,multires", [(0, False), (0, True), (1, True), (1, False), (2, True)])
 @pytest.mark.parametrize("flagged", [False, True])
 def test_bound_covers_the_error_tiny_config(precision, multires, flagged):
     """64^2 grid, 16 channels, 8 linear rings (with and without the

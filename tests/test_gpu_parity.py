@@ -95,7 +95,7 @@ def test_three_mode_golden_gpu(precision):
     assert abs(out["full"][0, 0, 0, 0, 0]) < 1e-6
 
 
-@pytest.mark.parametrize("precision,multires", [(0, False)] + SPLIT_CASES)
+@pytest.mark.parametrize("precision,multires", [(0, False), (0, True)] + SPLIT_CASES)
 @pytest.mark.parametrize("flagged", [False, True])
 def test_tiny_config_full_cube(flagged, precision, multires):
     """64^2 grid, 16 channels, 8 linear rings (and the coarse-band flags):
@@ -126,7 +126,7 @@ def test_tiny_config_full_cube(flagged, precision, multires):
     assert err3.max() < tol, err3.max()
 
 
-@pytest.mark.parametrize("precision,multires", [(0, False)] + SPLIT_CASES)
+@pytest.mark.parametrize("precision,multires", [(0, False), (0, True)] + SPLIT_CASES)
 def test_ragged_sizes_occupancy_and_blocks(precision, multires):
     """Non-tile-multiple sizes: nt = 40, 11 channels (non-smooth: direct DFT in
     the delay transform), log rings, empty cells with N_g in {0, 1, 2, 3},
@@ -196,7 +196,7 @@ def test_batch_and_scales(precision):
         assert np.abs(out["bs3d"][b][keep] - b3[keep]).max() / b3_scale < tol
 
 
-@pytest.mark.parametrize("precision,multires", [(0, False)] + SPLIT_CASES)
+@pytest.mark.parametrize("precision,multires", [(0, False), (0, True)] + SPLIT_CASES)
 def test_degenerate_cases(precision, multires):
     """One channel (the single-frequency ABS special case), a single ring,
     an empty ring, every channel flagged, and the constant field (B = 1/A)."""
