@@ -54,7 +54,7 @@
 extern "C" {
 #endif
 
-#define BS_ABI_VERSION 9
+#define BS_ABI_VERSION 10
 
 typedef struct bs_plan_s *bs_plan;
 
@@ -110,6 +110,22 @@ typedef struct {
                                 fields are kept at each side that some triple needs
                                 (every precision; the FP32 path launches once per
                                 side).  0: one M for all (fft_m rule). */
+    int general;             /* 0: Hermitian visibilities and sampling (the sky is real):
+                                real fields and real estimates.  1: general input -- the
+                                visibilities V and the sampling N_g need not satisfy
+                                V(-U) = V(U)*, N_g(-U) = N_g(U) (Eqs. iFT, iFT_I with
+                                complex fields): the weighted grid X = W V is split
+                                into Hermitian parts X = X_H + i Y, the real path runs on
+                                X_H + t Y for t = 0, 1, -1, 2 (four internal
+                                realisations per realisation), and the cubic in t gives
+                                the complex S = sum_x F_i F_j F_l exactly:
+                                Re S = 2 S(0) - (S(1) + S(-1)) / 2,
+                                Im S = (9 S(1) - S(-1) - 2 S(2) - 6 S(0)) / 6.
+                                Outputs are complex128 (interleaved re, im) with the
+                                layouts of the Hermitian case; counts use the occupied
+                                cells as given.  The error bound, the monopole and
+                                cylindrical binnings and Monte Carlo ensembles take
+                                general = 0 only (BS_ERR_UNSUPPORTED). */
 } bs_plan_desc;
 
 /* ABI version this library was built with (BS_ABI_VERSION). */
@@ -176,7 +192,8 @@ bs_status bs_counts(bs_plan plan, int64_t *tri_host, int64_t *nnu_host);
  *              half-open channel ranges; NULL = every channel for all three.
  *  out_full_dev  double [batch][T_r][nchan][nchan][nchan] or NULL: entries of the
  *              block are overwritten with B_A (NaN where undefined); entries
- *              outside the block are left untouched.
+ *              outside the block are left untouched.  General plans: complex128
+ *              (double pairs) of the same shape.
  *  accumulate  nonzero: add the block's pixel sums and sampling to the
  *              collapse accumulators used by bs_mabs_delta / bs_bs3d.
  * Errors: BS_ERR_STATE (no grid loaded), BS_ERR_ARG (block out of range). */
@@ -186,12 +203,36 @@ bs_status bs_mabs(bs_plan plan, const int32_t *block_host, double *out_full_dev,
 /* Zero the collapse accumulators and the accumulated sampling. */
 bs_status bs_delta_reset(bs_plan plan, void *cuda_stream);
 
+/* Raw collapse accumulators, for merging the work of several plans or ranks
+ * (Section 3.2: the collapse to (dnu1, dnu2) averages over channel triples, so
+ * the sums over disjoint channel blocks add, and the mean is formed once, from
+ * the merged sums and sampling).
+ *  sums_dev  double [batch][T_r][2nchan-1][2nchan-1]: sum over the accumulated
+ *            channel triples of S = sum_x F_i F_j F_l at (nu1-nu3, nu2-nu3)
+ *            (unfolded, not normalised), index [d1+nchan-1][d2+nchan-1]
+ *  nnu_host  int64 [(2nchan-1)^2]: the unfolded count of accumulated valid
+ *            channel triples at each separation, same index
+ * bs_delta_export copies them out (either pointer may be NULL).  In a general
+ * plan the batch dimension holds the four Hermitian components of each
+ * realisation (4 x batch entries, component fastest).
+ * bs_delta_import replaces (add = 0) or adds to (add = 1) the plan's
+ * accumulators; bs_mabs_delta and bs_bs3d then normalise the merged sums.
+ * Plans merged this way must share the shape (grid, channels, rings, image
+ * sides, precision, batch, flags and sampling), so that a ring triple's
+ * normalisation A M^2 T is the same in each.
+ * Errors: BS_ERR_ARG, BS_ERR_STATE (no grid loaded), BS_ERR_TIMEOUT (as
+ * bs_mabs_delta, on export), BS_ERR_CUDA. */
+bs_status bs_delta_export(bs_plan plan, double *sums_dev, int64_t *nnu_host, void *cuda_stream);
+bs_status bs_delta_import(bs_plan plan, const double *sums_dev, const int64_t *nnu_host, int add,
+                          void *cuda_stream);
+
 /* Folded collapsed MABS (Section 3.2; fold of Fig. Nv) from the accumulated
  * blocks: for every ring triple and separation (d1, d2) in [-(nchan-1),
  * nchan-1]^2, the mean of B_A over the accumulated valid channel triples with
  * (nu1-nu3, nu2-nu3) = (d1, d2) or (-d1, -d2).
  *  out_dev  double [batch][T_r][2nchan-1][2nchan-1], index [d1+nchan-1][d2+nchan-1];
  *           the plane is point symmetric; NaN where no triple was sampled.
+ *           General plans: complex128 of the same shape.
  * If a tensor-core contraction ran since the last check, synchronises on
  * cuda_stream to read its error word and returns BS_ERR_TIMEOUT when one of
  * its bounded waits gave up (the accumulated sums are then invalid). */
@@ -207,6 +248,8 @@ bs_status bs_mabs_delta(bs_plan plan, double *out_dev, void *cuda_stream);
  * unpaired edge n, m = -nchan/2; the real part is returned.
  * k_par a = 2 pi a / (r' nchan dnu_c).
  *  out_dev  double [batch][T_r][nchan][nchan], index [a + nchan/2][b + nchan/2].
+ *           General plans: complex128 of the same shape (each of the real and
+ *           imaginary parts of the folded plane transformed as above).
  * Checks the contraction's error word like bs_mabs_delta. */
 bs_status bs_bs3d(bs_plan plan, double *out_dev, void *cuda_stream);
 
@@ -217,7 +260,8 @@ bs_status bs_bs3d(bs_plan plan, double *out_dev, void *cuda_stream);
  * the planes with data.
  *  bs_mabs_delta_closable  out_dev double [batch][n_c][2nchan-1][2nchan-1]
  *  bs_bs3d_closable        out_dev double [batch][n_c][nchan][nchan]
- * Values are bit-identical to the matching planes of the full layouts.
+ * Values are bit-identical to the matching planes of the full layouts
+ * (complex128 for general plans).
  * Errors: as bs_mabs_delta / bs_bs3d. */
 bs_status bs_mabs_delta_closable(bs_plan plan, double *out_dev, void *cuda_stream);
 bs_status bs_bs3d_closable(bs_plan plan, double *out_dev, void *cuda_stream);

@@ -27,14 +27,14 @@ STATUS = {0: "BS_OK", 1: "BS_ERR_ARG", 2: "BS_ERR_NO_DEVICE", 3: "BS_ERR_CUDA", 
 PREC_FP32 = 0
 PREC_SPLIT_BF16 = 1
 PREC_SPLIT_FP16 = 2
-ABI_VERSION = 9      # BS_ABI_VERSION of include/bs.h
+ABI_VERSION = 10     # BS_ABI_VERSION of include/bs.h
 MLP_FEATURES = 45    # BS_MLP_FEATURES of include/bs.h
 
 # every symbol declared in include/bs.h
 EXPORTS = ("bs_abi_version", "bs_plan_create", "bs_plan_destroy", "bs_last_error",
            "bs_plan_info", "bs_plan_trip_sides", "bs_plan_set_workspace", "bs_grid_load", "bs_counts", "bs_mabs",
            "bs_delta_reset", "bs_mabs_delta", "bs_bs3d", "bs_mabs_delta_closable",
-           "bs_bs3d_closable", "bs_mabs_error_bound", "bs_grid_visibilities", "bs_plan_ring_umean", "bs_bs_monopole",
+           "bs_bs3d_closable", "bs_mabs_error_bound", "bs_delta_export", "bs_delta_import", "bs_grid_visibilities", "bs_plan_ring_umean", "bs_bs_monopole",
            "bs_bs_cylindrical", "bs_check_hermitian",
            "bs_mc_create", "bs_mc_destroy", "bs_mc_last_error", "bs_mc_info", "bs_mc_set_input",
            "bs_mc_set_flags", "bs_mc_set_tuning", "bs_mc_autotune", "bs_mc_run", "bs_mc_reset",
@@ -60,7 +60,7 @@ class PlanDesc(ctypes.Structure):
                 ("precision", ctypes.c_int), ("batch", ctypes.c_int),
                 ("norm_A", ctypes.c_double), ("r", ctypes.c_double),
                 ("rprime", ctypes.c_double), ("dnu_c", ctypes.c_double),
-                ("multires", ctypes.c_int)]
+                ("multires", ctypes.c_int), ("general", ctypes.c_int)]
 
 
 def lib() -> ctypes.CDLL:
@@ -89,6 +89,8 @@ def lib() -> ctypes.CDLL:
             L.bs_bs3d.argtypes = [P, P, P]
             L.bs_check_hermitian.argtypes = [P, P, D, P]
             L.bs_mabs_error_bound.argtypes = [P, P, P, I, P, P]
+            L.bs_delta_export.argtypes = [P, P, P, P]
+            L.bs_delta_import.argtypes = [P, P, P, I, P]
             L.bs_counts_noalloc.argtypes = [I, I, P, P, P, P]
             L.bs_measure_peak.argtypes = [I, I, P, P]
             L.bs_sky_create.argtypes = [I, I, D, D, D, I, ctypes.POINTER(P)]
@@ -149,14 +151,16 @@ class Plan:
 
     def __init__(self, nt: int, nchan: int, edges, precision: int = PREC_FP32, batch: int = 1,
                  fft_m: int = 0, norm_A: float = 1.0, r: float = 1.0, rprime: float = 1.0,
-                 dnu_c: float = 1.0, torch_workspace: bool = True, multires: bool = False):
+                 dnu_c: float = 1.0, torch_workspace: bool = True, multires: bool = False,
+                 general: bool = False):
         import torch
         L = lib()
         self._L = L
         e = [float(x) for x in edges]
         self._edges = (ctypes.c_double * len(e))(*e)
         d = PlanDesc(nt, nchan, len(e) - 1, self._edges, fft_m, precision, batch, norm_A, r,
-                     rprime, dnu_c, 1 if multires else 0)
+                     rprime, dnu_c, 1 if multires else 0, 1 if general else 0)
+        self.general = bool(general)
         h = ctypes.c_void_p()
         st = L.bs_plan_create(ctypes.byref(d), ctypes.byref(h))
         if st != BS_OK:
@@ -224,13 +228,26 @@ class Plan:
                                       nnu.ctypes.data_as(ctypes.c_void_p)))
         return tri, nnu.reshape(2 * self.nchan - 1, 2 * self.nchan - 1)
 
+    def _out(self, t, planes, side):
+        """Pointer of an output tensor of [batch, planes, side, side] float64 values
+        (complex128 for general plans), refused when the type or size differs."""
+        import torch
+        want = torch.complex128 if self.general else torch.float64
+        if t.dtype != want or t.numel() != self.batch * planes * side * side:
+            raise ValueError(f"output must be {want} with {self.batch * planes * side * side} "
+                             "elements")
+        return _dptr(t)
+
     def mabs(self, block=None, out_full=None, accumulate=True, stream=None):
         """bs_mabs over channel block (nu1_lo, nu1_hi, nu2_lo, nu2_hi, nu3_lo, nu3_hi)."""
+        full = None
+        if out_full is not None:
+            full = self._out(out_full, self.ntrip * self.nchan, self.nchan)
         blk = None
         if block is not None:
             self._blk = (ctypes.c_int32 * 6)(*[int(x) for x in block])
             blk = self._blk
-        self._check(self._L.bs_mabs(self._h, blk, _dptr(out_full), 1 if accumulate else 0,
+        self._check(self._L.bs_mabs(self._h, blk, full, 1 if accumulate else 0,
                                     _stream_ptr(stream)))
 
     def delta_reset(self, stream=None):
@@ -238,11 +255,13 @@ class Plan:
 
     def mabs_delta(self, out, stream=None):
         """bs_mabs_delta: out float64 CUDA [batch, ntrip, 2nc-1, 2nc-1]."""
-        self._check(self._L.bs_mabs_delta(self._h, _dptr(out), _stream_ptr(stream)))
+        self._check(self._L.bs_mabs_delta(self._h, self._out(out, self.ntrip, 2 * self.nchan - 1),
+                                          _stream_ptr(stream)))
 
     def bs3d(self, out, stream=None):
         """bs_bs3d: out float64 CUDA [batch, ntrip, nc, nc]."""
-        self._check(self._L.bs_bs3d(self._h, _dptr(out), _stream_ptr(stream)))
+        self._check(self._L.bs_bs3d(self._h, self._out(out, self.ntrip, self.nchan),
+                                    _stream_ptr(stream)))
 
     @property
     def n_closable(self):
@@ -253,7 +272,8 @@ class Plan:
     def mabs_delta_closable(self, out, stream=None):
         """bs_mabs_delta_closable: out float64 CUDA [batch, n_closable, 2nc-1, 2nc-1], the
         closable ring triples in ascending index."""
-        self._check(self._L.bs_mabs_delta_closable(self._h, _dptr(out), _stream_ptr(stream)))
+        self._check(self._L.bs_mabs_delta_closable(
+            self._h, self._out(out, self.n_closable, 2 * self.nchan - 1), _stream_ptr(stream)))
 
     def grid_visibilities(self, uv, vis, flags=None, avg=1, mode=0, stream=None):
         """bs_grid_visibilities (Eq. vg): uv float64 CUDA [nbl, 2] in grid units, vis
@@ -330,7 +350,34 @@ class Plan:
     def bs3d_closable(self, out, stream=None):
         """bs_bs3d_closable: out float64 CUDA [batch, n_closable, nc, nc], the closable ring
         triples in ascending index."""
-        self._check(self._L.bs_bs3d_closable(self._h, _dptr(out), _stream_ptr(stream)))
+        self._check(self._L.bs_bs3d_closable(self._h, self._out(out, self.n_closable, self.nchan),
+                                             _stream_ptr(stream)))
+
+    def delta_export(self, stream=None):
+        """bs_delta_export: (sums float64 CUDA [batch, ntrip, 2nc-1, 2nc-1], nnu int64 numpy
+        [2nc-1, 2nc-1]): the raw collapse sums and unfolded sampling."""
+        import numpy as np
+        import torch
+        n2 = 2 * self.nchan - 1
+        sums = torch.empty((self.batch, self.ntrip, n2, n2), dtype=torch.float64, device="cuda")
+        nnu = np.zeros((n2, n2), np.int64)
+        self._check(self._L.bs_delta_export(self._h, _dptr(sums),
+                                            nnu.ctypes.data_as(ctypes.c_void_p),
+                                            _stream_ptr(stream)))
+        return sums, nnu
+
+    def delta_import(self, sums, nnu, add=False, stream=None):
+        """bs_delta_import: replace (or add to) the collapse accumulators."""
+        import numpy as np
+        import torch
+        n2 = 2 * self.nchan - 1
+        if sums.dtype != torch.float64 or sums.numel() != self.batch * self.ntrip * n2 * n2:
+            raise ValueError("sums must be float64 [batch, ntrip, 2nc-1, 2nc-1]")
+        nn = np.ascontiguousarray(np.asarray(nnu, dtype=np.int64))
+        if nn.size != n2 * n2:
+            raise ValueError("nnu must hold (2nc-1)^2 entries")
+        self._check(self._L.bs_delta_import(self._h, _dptr(sums), nn.ctypes.data_as(ctypes.c_void_p),
+                                            int(bool(add)), _stream_ptr(stream)))
 
     def error_bound(self, delta=None, closable=False, stream=None):
         """bs_mabs_error_bound: float64 CUDA [batch, ntrip] bounds on |B_A error| per ring

@@ -173,6 +173,8 @@ cudaError_t launch_full_finalize(double *out, long long bstride, int batch, int 
 cudaError_t launch_delta_norm(const double *dsum, const long long *nnu, const double *tnorm,
                               double *out, int batch, int ntrip, int nc, const int *list,
                               int nlist, cudaStream_t s);
+// y[k] += x[k], k < n
+cudaError_t launch_add_f64(double *y, const double *x, long long n, cudaStream_t s);
 // box = {row_lo, row_hi, col_lo, col_hi} (inclusive plane indices) to zero
 cudaError_t launch_zero_planes(double *dsum, const int *trips, int ntr, int batch, int ntrip,
                                int n2, const int *box, cudaStream_t s);
@@ -181,6 +183,15 @@ cudaError_t launch_bs3d(const double *dsum, const long long *nnu, const double *
                         float2 *tmp, double *out, int batch, int ntrip, int nc,
                         const float2 *twN, const Radices &radN, double scale, const int *list,
                         int nlist, cudaStream_t s);
+// General (non-Hermitian) input: the four Hermitian components X_H + t Y,
+// t = 0, 1, -1, 2, of X = W V (out [4 ub][nc][nt][nt]), and the combination of
+// four real results into complex ones (in [4 ub][n] -> out [ub][n][2]; the
+// _full form only touches the channel block blk of [.][ntrip][nc^3]).
+cudaError_t launch_general_prep(int nt, int nc, int ub, const float2 *vis, const float *ngrid,
+                                const int8_t *label, float2 *out, cudaStream_t s);
+cudaError_t launch_combine4(const double *in, long long n, int ub, double *out, cudaStream_t s);
+cudaError_t launch_combine4_full(const double *in, int ub, int ntrip, int nc, const int *blk,
+                                 double *out, cudaStream_t s);
 int tc_smem_bytes(int f16);
 cudaError_t launch_contract_tc(const TcArgs &a, int nsm, cudaStream_t s);
 cudaError_t launch_hermitian_check(const float2 *vis, int batch, int nc, int nt,

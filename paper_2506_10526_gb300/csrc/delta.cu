@@ -272,6 +272,22 @@ cudaError_t launch_zero_planes(double *dsum, const int *trips, int ntr, int batc
   return cudaGetLastError();
 }
 
+namespace {
+// y[k] += x[k] (merging collapse sums of disjoint channel blocks)
+__global__ void k_add_f64(double *__restrict__ y, const double *__restrict__ x, long long n) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x)
+    y[k] += x[k];
+}
+}  // namespace
+
+cudaError_t launch_add_f64(double *y, const double *x, long long n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int grid = (int)std::min<long long>((n + 255) / 256, 152LL * 16);
+  k_add_f64<<<grid, 256, 0, s>>>(y, x, n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_bs3d(const double *dsum, const long long *nnu, const double *tnorm, float2 *tmp,
                         double *out, int batch, int ntrip, int nc, const float2 *twN,
                         const Radices &radN, double scale, const int *list, int nlist,

@@ -154,6 +154,8 @@ void compute_layout(bs_plan p) {
   for (const Level &lv : p->levels) nfield_all += (size_t)p->batch * lv.nslot * p->nc;
   L.errn = take(std::max<size_t>(1, nfield_all) * 3 * sizeof(double));
   L.errtab = take((size_t)p->ntrip * 4 * sizeof(int));
+  // general plans: the four Hermitian components of the weighted input
+  L.gvis = take(p->general ? (size_t)p->batch * p->nc * p->nt * p->nt * sizeof(float2) : 0);
   L.total = o;
 }
 
@@ -593,6 +595,9 @@ bs_status bs_plan_create(const bs_plan_desc *desc, bs_plan *out) {
   if (d.nbins < 1 || d.nbins > 32) return fail(nullptr, BS_ERR_ARG, "nbins must be in [1, 32]");
   if (!d.bin_edges) return fail(nullptr, BS_ERR_ARG, "bin_edges must not be NULL");
   if (d.batch < 1) return fail(nullptr, BS_ERR_ARG, "batch must be >= 1");
+  if (d.general != 0 && d.general != 1) return fail(nullptr, BS_ERR_ARG, "general must be 0 or 1");
+  if (d.general && (long long)d.batch * 4 > 65535)
+    return fail(nullptr, BS_ERR_ARG, "batch too large for a general plan");
   if (d.precision != BS_PREC_FP32 && d.precision != BS_PREC_SPLIT_BF16 &&
       d.precision != BS_PREC_SPLIT_FP16)
     return fail(nullptr, BS_ERR_ARG, "unknown precision");
@@ -623,7 +628,11 @@ bs_status bs_plan_create(const bs_plan_desc *desc, bs_plan *out) {
   p->nt = d.nt;
   p->nc = d.nchan;
   p->nb = d.nbins;
-  p->batch = d.batch;
+  // general input: four Hermitian components per realisation, processed as
+  // realisations of their own and combined into complex results
+  p->general = d.general != 0;
+  p->ubatch = d.batch;
+  p->batch = p->general ? 4 * d.batch : d.batch;
   if (cudaHostAlloc(&p->err_host, sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
       cudaHostGetDevicePointer(&p->err_dev, p->err_host, 0) != cudaSuccess) {
     cudaGetLastError();
@@ -829,6 +838,11 @@ bs_status bs_plan_destroy(bs_plan p) {
     cudaSetDevice(p->device);
     cudaFree(p->mono_bins);
   }
+  for (double *g : {p->gfull, p->gdelta, p->g3d})
+    if (g) {
+      cudaSetDevice(p->device);
+      cudaFree(g);
+    }
   delete p;
   return BS_OK;
 }
@@ -891,7 +905,15 @@ bs_status bs_grid_load(bs_plan p, const void *vis, const float *ngrid, const uin
     if (st != BS_OK) return st;
     p->counts_default = true;
   }
-  st = enqueue_fields(p, vis, ngrid, s);
+  if (p->general) {
+    // weights and the Hermitian split applied here; the fields see unit weights
+    float2 *gv = p->at<float2>(L.gvis);
+    BS_CUDA(launch_general_prep(p->nt, p->nc, p->ubatch, static_cast<const float2 *>(vis), ngrid,
+                                lab, gv, s));
+    st = enqueue_fields(p, gv, nullptr, s);
+  } else {
+    st = enqueue_fields(p, vis, ngrid, s);
+  }
   if (st != BS_OK) return st;
   st = delta_reset(p, s);
   if (st != BS_OK) return st;
@@ -925,6 +947,25 @@ bs_status bs_counts(bs_plan p, int64_t *tri, int64_t *nnu_host) {
   return BS_OK;
 }
 
+// Scratch of a general plan for the four real components of an output (grown on
+// demand with cudaMalloc, freed with the plan).
+static bs_status general_scratch(bs_plan p, double **buf, size_t *cap, size_t n) {
+  if (*buf && *cap >= n) return BS_OK;
+  if (*buf) cudaFree(*buf);
+  *buf = nullptr;
+  *cap = 0;
+  void *m = nullptr;
+  const cudaError_t e = cudaMalloc(&m, std::max<size_t>(1, n) * sizeof(double));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(p, BS_ERR_OOM, "scratch of " + std::to_string(n * sizeof(double)) +
+                                   " bytes for the general-input components failed");
+  }
+  *buf = static_cast<double *>(m);
+  *cap = n;
+  return BS_OK;
+}
+
 bs_status bs_mabs(bs_plan p, const int32_t *block, double *out_full, int accumulate, void *stream) {
   if (!p) return BS_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -944,6 +985,12 @@ bs_status bs_mabs(bs_plan p, const int32_t *block, double *out_full, int accumul
   if (!out_full && !accumulate) return BS_OK;
   const WsLayout &L = p->L;
   const long long full_bstride = (long long)p->ntrip * nc * nc * nc;
+  double *const user_full = out_full;
+  if (out_full && p->general) {  // the four real components go to the plan's scratch
+    st = general_scratch(p, &p->gfull, &p->gfull_cap, (size_t)p->batch * full_bstride);
+    if (st != BS_OK) return st;
+    out_full = p->gfull;
+  }
   if (out_full) BS_CUDA(launch_full_fill(out_full, full_bstride, p->batch, p->ntrip, nc, blk, 0.0, s));
   if (p->d.precision != BS_PREC_FP32) {
     st = mabs_tc(p, blk, out_full, accumulate, s);
@@ -1010,6 +1057,8 @@ bs_status bs_mabs(bs_plan p, const int32_t *block, double *out_full, int accumul
   if (out_full)
     BS_CUDA(launch_full_finalize(out_full, full_bstride, p->batch, p->ntrip, nc, blk,
                                  p->at<uint8_t>(L.valid), p->at<double>(L.tnorm), s));
+  if (user_full && p->general)
+    BS_CUDA(launch_combine4_full(out_full, p->ubatch, p->ntrip, nc, blk, user_full, s));
   if (accumulate) accumulate_block_nnu(p, blk);
   return BS_OK;
 }
@@ -1022,6 +1071,84 @@ bs_status bs_delta_reset(bs_plan p, void *stream) {
   return delta_reset(p, s);
 }
 
+bs_status bs_delta_export(bs_plan p, double *sums_dev, int64_t *nnu_host, void *stream) {
+  if (!p || (!sums_dev && !nnu_host)) return fail(p, BS_ERR_ARG, "bs_delta_export: nothing to export");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!p->loaded) return fail(p, BS_ERR_STATE, "bs_delta_export before bs_grid_load");
+  bs_status st = prepare(p, s);
+  if (st != BS_OK) return st;
+  st = check_device_error(p, s);
+  if (st != BS_OK) return st;
+  const size_t n2 = (size_t)(2 * p->nc - 1);
+  if (sums_dev)
+    BS_CUDA(cudaMemcpyAsync(sums_dev, p->at<double>(p->L.dsum),
+                            (size_t)p->batch * p->ntrip * n2 * n2 * sizeof(double),
+                            cudaMemcpyDeviceToDevice, s));
+  if (nnu_host)
+    for (size_t k = 0; k < p->nnu.size(); ++k) nnu_host[k] = p->nnu[k];
+  return BS_OK;
+}
+
+bs_status bs_delta_import(bs_plan p, const double *sums_dev, const int64_t *nnu_host, int add,
+                          void *stream) {
+  if (!p || !sums_dev || !nnu_host || (add != 0 && add != 1))
+    return fail(p, BS_ERR_ARG, "bs_delta_import: sums_dev and nnu_host are required, add is 0 or 1");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!p->loaded) return fail(p, BS_ERR_STATE, "bs_delta_import before bs_grid_load");
+  bs_status st = prepare(p, s);
+  if (st != BS_OK) return st;
+  const size_t n2 = (size_t)(2 * p->nc - 1);
+  const long long n = (long long)p->batch * p->ntrip * n2 * n2;
+  double *d = p->at<double>(p->L.dsum);
+  if (add)
+    BS_CUDA(launch_add_f64(d, sums_dev, n, s));
+  else
+    BS_CUDA(cudaMemcpyAsync(d, sums_dev, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  for (size_t k = 0; k < p->nnu.size(); ++k) p->nnu[k] = (add ? p->nnu[k] : 0) + nnu_host[k];
+  p->nnu_dirty = true;
+  // the imported sums may touch any separation and any plane: the next reset zeroes all
+  p->dsum_clean = false;
+  return BS_OK;
+}
+
+// Folded collapsed plane of every (or every closable) ring triple into out; a
+// general plan normalises its four real components into scratch and combines
+// them into complex planes.
+static bs_status delta_out(bs_plan p, double *out, bool closable, cudaStream_t s) {
+  const int npl = closable ? (int)p->clos.size() : p->ntrip;
+  const long long n2 = 2LL * p->nc - 1, per = (long long)npl * n2 * n2;
+  double *dst = out;
+  if (p->general) {
+    bs_status st = general_scratch(p, &p->gdelta, &p->gdelta_cap, (size_t)p->batch * per);
+    if (st != BS_OK) return st;
+    dst = p->gdelta;
+  }
+  BS_CUDA(launch_delta_norm(p->at<double>(p->L.dsum), p->at<long long>(p->L.nnu),
+                            p->at<double>(p->L.tnorm), dst, p->batch, p->ntrip, p->nc,
+                            closable ? p->at<int>(p->L.clos) : nullptr,
+                            closable ? npl : 0, s));
+  if (p->general) BS_CUDA(launch_combine4(dst, per, p->ubatch, out, s));
+  return BS_OK;
+}
+
+// Eq. (dft) of every (or every closable) ring triple into out; general plans as above.
+static bs_status bs3d_out(bs_plan p, double *out, bool closable, cudaStream_t s) {
+  const int npl = closable ? (int)p->clos.size() : p->ntrip;
+  const long long per = (long long)npl * p->nc * p->nc;
+  double *dst = out;
+  if (p->general) {
+    bs_status st = general_scratch(p, &p->g3d, &p->g3d_cap, (size_t)p->batch * per);
+    if (st != BS_OK) return st;
+    dst = p->g3d;
+  }
+  BS_CUDA(launch_bs3d(p->at<double>(p->L.dsum), p->at<long long>(p->L.nnu),
+                      p->at<double>(p->L.tnorm), p->at<float2>(p->L.tmp3d), dst, p->batch,
+                      p->ntrip, p->nc, p->at<float2>(p->L.twN), p->radN, p->scale3d,
+                      closable ? p->at<int>(p->L.clos) : nullptr, closable ? npl : 0, s));
+  if (p->general) BS_CUDA(launch_combine4(dst, per, p->ubatch, out, s));
+  return BS_OK;
+}
+
 bs_status bs_mabs_delta(bs_plan p, double *out, void *stream) {
   if (!p || !out) return fail(p, BS_ERR_ARG, "out_dev must not be NULL");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1032,10 +1159,7 @@ bs_status bs_mabs_delta(bs_plan p, double *out, void *stream) {
   if (st != BS_OK) return st;
   st = upload_nnu(p, s);
   if (st != BS_OK) return st;
-  BS_CUDA(launch_delta_norm(p->at<double>(p->L.dsum), p->at<long long>(p->L.nnu),
-                            p->at<double>(p->L.tnorm), out, p->batch, p->ntrip, p->nc, nullptr, 0,
-                            s));
-  return BS_OK;
+  return delta_out(p, out, false, s);
 }
 
 bs_status bs_mabs_delta_closable(bs_plan p, double *out, void *stream) {
@@ -1048,10 +1172,7 @@ bs_status bs_mabs_delta_closable(bs_plan p, double *out, void *stream) {
   if (st != BS_OK) return st;
   st = upload_nnu(p, s);
   if (st != BS_OK) return st;
-  BS_CUDA(launch_delta_norm(p->at<double>(p->L.dsum), p->at<long long>(p->L.nnu),
-                            p->at<double>(p->L.tnorm), out, p->batch, p->ntrip, p->nc,
-                            p->at<int>(p->L.clos), (int)p->clos.size(), s));
-  return BS_OK;
+  return delta_out(p, out, true, s);
 }
 
 bs_status bs_bs3d(bs_plan p, double *out, void *stream) {
@@ -1064,11 +1185,7 @@ bs_status bs_bs3d(bs_plan p, double *out, void *stream) {
   if (st != BS_OK) return st;
   st = upload_nnu(p, s);
   if (st != BS_OK) return st;
-  BS_CUDA(launch_bs3d(p->at<double>(p->L.dsum), p->at<long long>(p->L.nnu),
-                      p->at<double>(p->L.tnorm), p->at<float2>(p->L.tmp3d), out, p->batch,
-                      p->ntrip, p->nc, p->at<float2>(p->L.twN), p->radN, p->scale3d, nullptr, 0,
-                      s));
-  return BS_OK;
+  return bs3d_out(p, out, false, s);
 }
 
 bs_status bs_bs3d_closable(bs_plan p, double *out, void *stream) {
@@ -1081,11 +1198,7 @@ bs_status bs_bs3d_closable(bs_plan p, double *out, void *stream) {
   if (st != BS_OK) return st;
   st = upload_nnu(p, s);
   if (st != BS_OK) return st;
-  BS_CUDA(launch_bs3d(p->at<double>(p->L.dsum), p->at<long long>(p->L.nnu),
-                      p->at<double>(p->L.tnorm), p->at<float2>(p->L.tmp3d), out, p->batch,
-                      p->ntrip, p->nc, p->at<float2>(p->L.twN), p->radN, p->scale3d,
-                      p->at<int>(p->L.clos), (int)p->clos.size(), s));
-  return BS_OK;
+  return bs3d_out(p, out, true, s);
 }
 
 bs_status bs_check_hermitian(bs_plan p, const void *vis, double tol, void *stream) {
@@ -1095,7 +1208,7 @@ bs_status bs_check_hermitian(bs_plan p, const void *vis, double tol, void *strea
   if (st != BS_OK) return st;
   float *hm = p->at<float>(p->L.herm);
   BS_CUDA(cudaMemsetAsync(hm, 0, 2 * sizeof(float), s));
-  BS_CUDA(launch_hermitian_check(static_cast<const float2 *>(vis), p->batch, p->nc, p->nt,
+  BS_CUDA(launch_hermitian_check(static_cast<const float2 *>(vis), p->ubatch, p->nc, p->nt,
                                  p->at<int8_t>(p->L.label), hm, hm + 1, s));
   float h[2];
   BS_CUDA(cudaMemcpyAsync(h, hm, sizeof(h), cudaMemcpyDeviceToHost, s));

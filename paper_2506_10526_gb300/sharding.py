@@ -7,6 +7,12 @@ W takes blocks r, r + W, r + 2W, ... in step order, so ranks never share a
 block and need no data-path collective: each rank's collapse sums hold its
 own blocks (the sum over ranks is the job's).  Timing is the maximum over
 ranks; throughput counts every rank's evaluations.
+
+When ranks split nu3, one plane of the collapse (Section 3.2: the mean over
+channel triples sharing (dnu1, dnu2)) gathers triples from several ranks:
+``merge_collapse`` sums every rank's raw accumulators (bs_delta_export) and
+unfolded sampling before any rank normalises (bs_delta_import, then
+bs_mabs_delta / bs_bs3d).  That sum is the path's one exchange step.
 """
 from __future__ import annotations
 
@@ -47,3 +53,15 @@ def reduce_step_stats(ms: float, evals: float, world: int, device=None):
     e = torch.tensor([float(evals)], dtype=torch.float64, device=device)
     dist.all_reduce(e)
     return float(t.item()), float(e.item())
+
+
+def merge_collapse(sums, nnu, world: int):
+    """Sum the partial collapse accumulators of every rank in place: ``sums``
+    the raw pixel sums [batch, ntrip, 2nc-1, 2nc-1] (float64) and ``nnu`` the
+    unfolded sampling [2nc-1, 2nc-1] (int64), both torch tensors on the rank's
+    communication device.  Returns them; a no-op for one rank."""
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(sums)
+        dist.all_reduce(nnu)
+    return sums, nnu

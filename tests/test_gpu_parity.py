@@ -329,3 +329,57 @@ def test_hermitian_check():
     bad[0, nt // 2 + 2, nt // 2 + 1] += 5.0
     assert not plan.check_hermitian(torch.from_numpy(bad[None]).cuda(), 1e-5)
     plan.close()
+
+
+@pytest.mark.parametrize("precision,multires", [(1, True), (0, False)])
+def test_merged_plans_equal_one_plan(precision, multires):
+    """The exchange step of a channel cube split over ranks, on one GPU: two
+    plans accumulate disjoint channel blocks (nu3 split between them), plan A
+    imports A's + B's raw collapse sums and sampling (bs_delta_export /
+    bs_delta_import, as merge_collapse would after an all-reduce); its folded
+    plane and Eq. (dft) equal those of one plan that accumulated every block,
+    to FP64 rounding (the atomics add in another order)."""
+    torch = _torch()
+    import paper_2506_10526_gb300 as bs
+    from paper_2506_10526_gb300.sharding import blocks_of
+    nt, nc = 40, 12
+    edges = synth.edges_log(5, 1.5, 19.0)
+    vis = torch.from_numpy(synth.sky_visibilities(nt, nc, seed=93)[None]).cuda()
+    flags = np.zeros(nc, np.uint8)
+    flags[5] = 1
+    jobs = blocks_of(nc, 8, 4)
+    plans = [bs.Plan(nt, nc, edges, precision=precision, multires=multires) for _ in range(3)]
+    for pl in plans:
+        pl.grid_load(vis, chan_flags=flags)
+    for k, blk in enumerate(jobs):
+        plans[k % 2].mabs(block=blk, accumulate=True)
+        plans[2].mabs(block=blk, accumulate=True)
+    sa, na = plans[0].delta_export()
+    sb, nb_ = plans[1].delta_export()
+    assert np.any(na != 0) and np.any(nb_ != 0)
+    plans[0].delta_import(sa + sb, na + nb_)
+    n2 = 2 * nc - 1
+    out = []
+    for pl in (plans[0], plans[2]):
+        dd = torch.empty((1, pl.ntrip, n2, n2), dtype=torch.float64, device="cuda")
+        b3 = torch.empty((1, pl.ntrip, nc, nc), dtype=torch.float64, device="cuda")
+        pl.mabs_delta(dd)
+        pl.bs3d(b3)
+        torch.cuda.synchronize()
+        out.append((dd.cpu().numpy(), b3.cpu().numpy(), pl.counts()[1]))
+    (d0, b0, c0), (d1, b1, c1) = out
+    np.testing.assert_array_equal(c0, c1)
+    assert np.array_equal(np.isnan(d0), np.isnan(d1))
+    ok = ~np.isnan(d1)
+    assert np.abs(d0[ok] - d1[ok]).max() <= 1e-11 * np.abs(d1[ok]).max()
+    assert np.abs(b0 - b1).max() <= 1e-5 * max(np.abs(b1).max(), 1e-300)  # FP32 transforms
+    # add mode: import B's sums on top of A's own
+    plans[1].delta_import(sa, na, add=True)
+    dd = torch.empty((1, plans[1].ntrip, n2, n2), dtype=torch.float64, device="cuda")
+    plans[1].mabs_delta(dd)
+    torch.cuda.synchronize()
+    d2 = dd.cpu().numpy()
+    assert np.array_equal(np.isnan(d2), np.isnan(d1))
+    assert np.abs(d2[ok] - d1[ok]).max() <= 1e-11 * np.abs(d1[ok]).max()
+    for pl in plans:
+        pl.close()
