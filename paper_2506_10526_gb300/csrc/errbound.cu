@@ -8,7 +8,7 @@
 // FP32 accumulation of the terms before the FP64 sums.  To first order:
 //
 //   |dS| <= (c_term + c_acc) sum_x |F_i F_j F_l|
-//           + eps_fft (|dF_i . F_j F_l| + two permutations) / eps_fft
+//           + sum_x |dF_i F_j F_l| + the two permutations (dF: field error)
 //
 // and, by Hoelder's and Cauchy-Schwarz's inequalities,
 //   sum_x |F_i F_j F_l| <= ||F_i||_3 ||F_j||_3 ||F_l||_3,
@@ -188,6 +188,7 @@ extern "C" bs_status bs_mabs_error_bound(bs_plan p, double *bound_dev, const dou
     return fail(p, BS_ERR_ARG, "bs_mabs_error_bound: give both delta_dev and relerr_dev, or neither");
   if (closable != 0 && closable != 1)
     return fail(p, BS_ERR_ARG, "bs_mabs_error_bound: closable must be 0 or 1");
+  if (p->general) return fail(p, BS_ERR_UNSUPPORTED, "bs_mabs_error_bound: general plans");
   if (!p->loaded || !p->counts_ready)
     return fail(p, BS_ERR_STATE, "bs_mabs_error_bound before bs_grid_load");
   cudaStream_t s = static_cast<cudaStream_t>(stream);

@@ -362,6 +362,10 @@ bs_status bs_mc_create(const bs_plan_desc *descs, int ngroups, bs_mc *out) {
       return fail(nullptr, BS_ERR_ARG,
                   "Monte Carlo groups share one tensor-core precision (split BF16 or split FP16)");
     }
+    if (descs[g].general) {
+      delete m;
+      return fail(nullptr, BS_ERR_UNSUPPORTED, "Monte Carlo groups take Hermitian input (general = 0)");
+    }
     m->f16 = descs[0].precision == BS_PREC_SPLIT_FP16 ? 1 : 0;
     Group gr;
     bs_status st = bs_plan_create(&descs[g], &gr.plan);

@@ -364,6 +364,7 @@ bs_status bs_bs_monopole(bs_plan p, const double *b3d, const double *kperp_host,
   for (int q = 0; q < n_k1; ++q)
     if (!(k1_edges_host[q + 1] > k1_edges_host[q]) || !std::isfinite(k1_edges_host[q + 1]))
       return fail(p, BS_ERR_ARG, "bs_bs_monopole: k1 edges must be finite and ascending");
+  if (p->general) return fail(p, BS_ERR_UNSUPPORTED, "bs_bs_monopole: general plans");
   if (!p->counts_ready) return fail(p, BS_ERR_STATE, "bs_bs_monopole before the ring-triple counts");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   bs_status st = prepare(p, s);
@@ -501,6 +502,7 @@ bs_status bs_bs_cylindrical(bs_plan p, const double *b3d, const double *kpar_hos
   for (int c = 1; c < p->nc; ++c)
     if (!(kpar_host[c] > kpar_host[c - 1]))
       return fail(p, BS_ERR_ARG, "bs_bs_cylindrical: k_par must grow with the delay index");
+  if (p->general) return fail(p, BS_ERR_UNSUPPORTED, "bs_bs_cylindrical: general plans");
   if (!p->counts_ready) return fail(p, BS_ERR_STATE, "bs_bs_cylindrical before the ring-triple counts");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   bs_status st = prepare(p, s);

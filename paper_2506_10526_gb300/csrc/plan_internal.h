@@ -13,7 +13,7 @@ namespace bsi {
 struct WsLayout {
   size_t label, efflabel, cells, uext, tripof, valid, twM, twN, tnorm, T, nnu, cols, ptiles, tctiles,
       G, F, Fhi, Flo, dsum, tmp3d, herm, err, maps, tcgroup, mlptab, ztrips, clos, closrings, mono, cyl,
-      errn, errtab, total;
+      errn, errtab, gvis, total;
 };
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
@@ -69,6 +69,13 @@ struct bs_plan_s {
   int16_t *mono_bins = nullptr;
   size_t mono_bins_cap = 0;
   std::vector<unsigned char> mono_key;
+  // general (non-Hermitian) input: batch = 4 x ubatch internal realisations (the
+  // Hermitian components X_H + t Y, t = 0, 1, -1, 2, of each user realisation) and
+  // scratch for their real outputs before they are combined (device, on demand)
+  bool general = false;
+  int ubatch = 1;
+  double *gfull = nullptr, *gdelta = nullptr, *g3d = nullptr;
+  size_t gfull_cap = 0, gdelta_cap = 0, g3d_cap = 0;
   std::vector<int> cyl_tab;       // row bins and column ranges of the last cylindrical call
   std::vector<long long> cyl_cnt; // its per-bin counts
   std::vector<int> err_tab;       // [ntrip][4] rings (i, j, l) and level, for the error bound

@@ -107,6 +107,23 @@ def test_enumeration_matches_brute_force(nt, nc, edges, seed):
     np.testing.assert_array_equal(res["T"], cnt)
 
 
+def test_enumeration_matches_brute_force_general_input():
+    """Visibilities with no symmetry at all (V(-U) unrelated to V(U)*) and an
+    asymmetric sampling grid: complex numerators, pair enumeration against the
+    O(N^3) closure test; Hermitian input gives real numerators (the imaginary
+    parts here are not small)."""
+    nt, nc, edges = 12, 3, [1.0, 2.5, 4.0, 5.5]
+    r = synth.rng(31)
+    vis = r.standard_normal((nc, nt, nt)) + 1j * r.standard_normal((nc, nt, nt))
+    ngrid = r.integers(0, 3, size=(nt, nt)).astype(float)
+    res = oracle.mabs_full(vis, edges, ngrid=ngrid)
+    num, den, _ = _brute_force(vis, edges, ngrid=ngrid)
+    scale = np.abs(num).max()
+    np.testing.assert_allclose(res["num"], num, atol=1e-12 * scale, rtol=0)
+    np.testing.assert_allclose(res["den"], den, atol=1e-12 * np.abs(den).max(), rtol=0)
+    assert np.abs(res["num"].imag).max() > 0.1 * scale
+
+
 def test_counts_invariants():
     """T(i,j,l) is invariant under permutations of (i, j, l); summing over l
     gives the number of ordered pairs (g1 in a_i, g2 in a_j) whose closing
