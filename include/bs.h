@@ -54,7 +54,7 @@
 extern "C" {
 #endif
 
-#define BS_ABI_VERSION 10
+#define BS_ABI_VERSION 11
 
 typedef struct bs_plan_s *bs_plan;
 
@@ -126,6 +126,20 @@ typedef struct {
                                 cells as given.  The error bound, the monopole and
                                 cylindrical binnings and Monte Carlo ensembles take
                                 general = 0 only (BS_ERR_UNSUPPORTED). */
+    int chan_sampling;       /* 0: one sampling grid N_g for every channel (ngrid_dev
+                                [nt][nt]).  1: per-channel sampling N_g(nu) (Eq. vg with
+                                per-baseline flags; ngrid_dev [nchan][nt][nt] required,
+                                symmetric in U for each channel): the denominator of
+                                Eq. (estimator_t), sum_theta I1 I2 I3, depends on the
+                                channel triple and is computed like the numerator from
+                                the occupancy masks [N_g(nu) > 0] (two internal
+                                realisations per realisation), to the precision of the
+                                contraction; estimates are S_D / (A S_I) per channel
+                                triple, and the collapse takes the ratio of the summed
+                                numerators and denominators over the triples at +-d.
+                                Exact integer counts (bs_counts) are geometric then.
+                                Not with general = 1; the error bound and Monte Carlo
+                                ensembles take chan_sampling = 0. */
 } bs_plan_desc;
 
 /* ABI version this library was built with (BS_ABI_VERSION). */
@@ -171,7 +185,8 @@ bs_status bs_plan_set_workspace(bs_plan plan, void *workspace_dev, size_t bytes)
  *  ngrid_dev      float [nt][nt]: visibilities per grid cell N_g (same in every
  *                 channel); W = 1/N_g where N_g > 0, else the cell is empty
  *                 (W = 0 and it takes no part in the counts).  NULL = every
- *                 cell holds one visibility.
+ *                 cell holds one visibility.  Plans with chan_sampling = 1:
+ *                 float [nchan][nt][nt], N_g(nu) per channel (required).
  *  chan_flag_host uint8 [nchan], nonzero = channel flagged (W = 0 for the whole
  *                 channel: its triples are undefined).  NULL = none flagged.
  * Image-plane fields of side M are kept in the plan workspace.  Triangle
@@ -214,7 +229,8 @@ bs_status bs_delta_reset(bs_plan plan, void *cuda_stream);
  *            channel triples at each separation, same index
  * bs_delta_export copies them out (either pointer may be NULL).  In a general
  * plan the batch dimension holds the four Hermitian components of each
- * realisation (4 x batch entries, component fastest).
+ * realisation (4 x batch entries, component fastest), in a per-channel
+ * sampling plan the numerator and occupancy components (2 x batch).
  * bs_delta_import replaces (add = 0) or adds to (add = 1) the plan's
  * accumulators; bs_mabs_delta and bs_bs3d then normalise the merged sums.
  * Plans merged this way must share the shape (grid, channels, rings, image

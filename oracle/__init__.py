@@ -320,6 +320,32 @@ def collapse_fold(B: np.ndarray):
     return bbar, cf
 
 
+def collapse_fold_ratio(num: np.ndarray, den: np.ndarray, norm_A: float = 1.0):
+    """Folded collapse for per-channel sampling (reading: ratio of sums).
+
+    With sampling that differs between channels the denominators of
+    Eq. (estimator_t) differ between channel triples, and the collapse to
+    (dnu1, dnu2) is read as the ratio of the summed numerators and the summed
+    denominators over the channel triples at +-(d1, d2): with one sampling
+    grid it equals the mean of the estimates (``collapse_fold``).
+    num, den: [ntrip, nc, nc, nc] (nu1, nu2, nu3), as ``mabs_full`` returns
+    them (zero where a channel is flagged or a cell empty).
+    Returns the plane [ntrip, 2nc-1, 2nc-1], NaN where the summed
+    denominator is zero."""
+    ntrip, nc = num.shape[0], num.shape[1]
+    n2 = 2 * nc - 1
+    S = np.zeros((ntrip, n2, n2), dtype=num.dtype)
+    D = np.zeros((ntrip, n2, n2))
+    for n1 in range(nc):
+        for n2_ in range(nc):
+            for n3 in range(nc):
+                S[:, n1 - n3 + nc - 1, n2_ - n3 + nc - 1] += num[:, n1, n2_, n3]
+                D[:, n1 - n3 + nc - 1, n2_ - n3 + nc - 1] += den[:, n1, n2_, n3]
+    Sf, Df = fold_plane(S), fold_plane(D)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        return np.where(Df > 0, Sf / np.where(Df > 0, Df, 1.0), np.nan) / norm_A
+
+
 def delay_dft(bbar: np.ndarray, nc: int, r: float = 1.0, rprime: float = 1.0,
               dnu_c: float = 1.0, variant: str = "half_open") -> np.ndarray:
     """Eq. (dft): B(a, b) = (r^2 r' dnu_c)^2 sum_{n,m} exp(-2 pi i (n a + m b)/nc)

@@ -27,7 +27,7 @@ STATUS = {0: "BS_OK", 1: "BS_ERR_ARG", 2: "BS_ERR_NO_DEVICE", 3: "BS_ERR_CUDA", 
 PREC_FP32 = 0
 PREC_SPLIT_BF16 = 1
 PREC_SPLIT_FP16 = 2
-ABI_VERSION = 10     # BS_ABI_VERSION of include/bs.h
+ABI_VERSION = 11     # BS_ABI_VERSION of include/bs.h
 MLP_FEATURES = 45    # BS_MLP_FEATURES of include/bs.h
 
 # every symbol declared in include/bs.h
@@ -60,7 +60,8 @@ class PlanDesc(ctypes.Structure):
                 ("precision", ctypes.c_int), ("batch", ctypes.c_int),
                 ("norm_A", ctypes.c_double), ("r", ctypes.c_double),
                 ("rprime", ctypes.c_double), ("dnu_c", ctypes.c_double),
-                ("multires", ctypes.c_int), ("general", ctypes.c_int)]
+                ("multires", ctypes.c_int), ("general", ctypes.c_int),
+                ("chan_sampling", ctypes.c_int)]
 
 
 def lib() -> ctypes.CDLL:
@@ -152,15 +153,17 @@ class Plan:
     def __init__(self, nt: int, nchan: int, edges, precision: int = PREC_FP32, batch: int = 1,
                  fft_m: int = 0, norm_A: float = 1.0, r: float = 1.0, rprime: float = 1.0,
                  dnu_c: float = 1.0, torch_workspace: bool = True, multires: bool = False,
-                 general: bool = False):
+                 general: bool = False, chan_sampling: bool = False):
         import torch
         L = lib()
         self._L = L
         e = [float(x) for x in edges]
         self._edges = (ctypes.c_double * len(e))(*e)
         d = PlanDesc(nt, nchan, len(e) - 1, self._edges, fft_m, precision, batch, norm_A, r,
-                     rprime, dnu_c, 1 if multires else 0, 1 if general else 0)
+                     rprime, dnu_c, 1 if multires else 0, 1 if general else 0,
+                     1 if chan_sampling else 0)
         self.general = bool(general)
+        self.chan_sampling = bool(chan_sampling)
         h = ctypes.c_void_p()
         st = L.bs_plan_create(ctypes.byref(d), ctypes.byref(h))
         if st != BS_OK:
@@ -207,8 +210,16 @@ class Plan:
         return out
 
     def grid_load(self, vis, ngrid=None, chan_flags=None, stream=None):
-        """bs_grid_load: vis complex64 CUDA tensor [batch, nchan, nt, nt]."""
+        """bs_grid_load: vis complex64 CUDA tensor [batch, nchan, nt, nt]; ngrid float32
+        [nt, nt] (or [nchan, nt, nt] in a per-channel sampling plan) or None."""
         import numpy as np
+        import torch
+        if vis.dtype != torch.complex64 or vis.numel() != self.batch * self.nchan * self.nt ** 2:
+            raise ValueError("vis must be complex64 [batch, nchan, nt, nt]")
+        if ngrid is not None:
+            want = (self.nchan if self.chan_sampling else 1) * self.nt ** 2
+            if ngrid.dtype != torch.float32 or ngrid.numel() != want:
+                raise ValueError(f"ngrid must be float32 with {want} elements")
         flags = None
         if chan_flags is not None:
             f = np.ascontiguousarray(np.asarray(chan_flags, dtype=np.uint8))

@@ -192,6 +192,18 @@ cudaError_t launch_general_prep(int nt, int nc, int ub, const float2 *vis, const
 cudaError_t launch_combine4(const double *in, long long n, int ub, double *out, cudaStream_t s);
 cudaError_t launch_combine4_full(const double *in, int ub, int ntrip, int nc, const int *blk,
                                  double *out, cudaStream_t s);
+// Per-channel sampling: components W V and [N_g(nu) > 0] (out [2 ub][nc][nt][nt]),
+// ratios of the two components (x [2b] / x [2b+1] / A; the _full form only in the
+// channel block), and ratio planes rewritten as collapse sums for the delay
+// transform (see general.cu).
+cudaError_t launch_chans_prep(int nt, int nc, int ub, const float2 *vis, const float *ngrid,
+                              const int8_t *label, float2 *out, cudaStream_t s);
+cudaError_t launch_ratio2(const double *in, long long n, int ub, double inv_a, double *out,
+                          cudaStream_t s);
+cudaError_t launch_ratio2_full(const double *in, int ub, int ntrip, int nc, const int *blk,
+                               double inv_a, double *out, cudaStream_t s);
+cudaError_t launch_ratio_to_sums(const double *R, const long long *nnu, const double *tnorm,
+                                 int ub, int ntrip, int nc, double *sums, cudaStream_t s);
 int tc_smem_bytes(int f16);
 cudaError_t launch_contract_tc(const TcArgs &a, int nsm, cudaStream_t s);
 cudaError_t launch_hermitian_check(const float2 *vis, int batch, int nc, int nt,

@@ -188,7 +188,8 @@ extern "C" bs_status bs_mabs_error_bound(bs_plan p, double *bound_dev, const dou
     return fail(p, BS_ERR_ARG, "bs_mabs_error_bound: give both delta_dev and relerr_dev, or neither");
   if (closable != 0 && closable != 1)
     return fail(p, BS_ERR_ARG, "bs_mabs_error_bound: closable must be 0 or 1");
-  if (p->general) return fail(p, BS_ERR_UNSUPPORTED, "bs_mabs_error_bound: general plans");
+  if (p->general || p->chans)
+    return fail(p, BS_ERR_UNSUPPORTED, "bs_mabs_error_bound: general or per-channel sampling plans");
   if (!p->loaded || !p->counts_ready)
     return fail(p, BS_ERR_STATE, "bs_mabs_error_bound before bs_grid_load");
   cudaStream_t s = static_cast<cudaStream_t>(stream);

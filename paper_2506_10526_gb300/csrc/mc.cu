@@ -362,9 +362,9 @@ bs_status bs_mc_create(const bs_plan_desc *descs, int ngroups, bs_mc *out) {
       return fail(nullptr, BS_ERR_ARG,
                   "Monte Carlo groups share one tensor-core precision (split BF16 or split FP16)");
     }
-    if (descs[g].general) {
+    if (descs[g].general || descs[g].chan_sampling) {
       delete m;
-      return fail(nullptr, BS_ERR_UNSUPPORTED, "Monte Carlo groups take Hermitian input (general = 0)");
+      return fail(nullptr, BS_ERR_UNSUPPORTED, "Monte Carlo groups take Hermitian input with one sampling grid");
     }
     m->f16 = descs[0].precision == BS_PREC_SPLIT_FP16 ? 1 : 0;
     Group gr;

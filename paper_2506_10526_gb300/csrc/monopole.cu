@@ -376,7 +376,7 @@ bs_status bs_bs_monopole(bs_plan p, const double *b3d, const double *kperp_host,
     if (!(std::fabs(kpar_host[c]) <= 1e8))
       return fail(p, BS_ERR_ARG, "bs_bs_monopole: |k_par| must not exceed 1e8");
   const int nbin = n_k1 * n_mu * n_t;
-  const int batch = b3d ? p->batch : 1;
+  const int batch = b3d ? p->ubatch : 1;
   const int per = std::min(batch, kMaxBatch);
   if (mono_smem(nbin, per) > (size_t)200 * 1024)
     return fail(p, BS_ERR_UNSUPPORTED, "bs_bs_monopole: too many bins for one CTA's histogram");
@@ -532,8 +532,8 @@ bs_status bs_bs_cylindrical(bs_plan p, const double *b3d, const double *kpar_hos
   MONO_CUDA(cudaMemcpyAsync(dtab, tab.data(), tab.size() * sizeof(int), cudaMemcpyHostToDevice, s));
   const size_t sm = ((size_t)n * n + nc) * sizeof(double);
   MONO_CUDA(smem_optin_once<k_bs_cylindrical<16>>());
-  MONO_CUDA(cudaMemsetAsync(sum_dev, 0, (size_t)p->batch * npl * n * n * sizeof(double), s));
-  const dim3 grid(npl, p->batch, 2);  // two row ranges per plane
+  MONO_CUDA(cudaMemsetAsync(sum_dev, 0, (size_t)p->ubatch * npl * n * n * sizeof(double), s));
+  const dim3 grid(npl, p->ubatch, 2);  // two row ranges per plane
   const int2 *seg = reinterpret_cast<const int2 *>(dtab + nc);
   const long long bst = (long long)npl * nc * nc;
   if (nc <= kCylThreads)

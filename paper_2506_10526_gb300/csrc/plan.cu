@@ -155,7 +155,8 @@ void compute_layout(bs_plan p) {
   L.errn = take(std::max<size_t>(1, nfield_all) * 3 * sizeof(double));
   L.errtab = take((size_t)p->ntrip * 4 * sizeof(int));
   // general plans: the four Hermitian components of the weighted input
-  L.gvis = take(p->general ? (size_t)p->batch * p->nc * p->nt * p->nt * sizeof(float2) : 0);
+  L.gvis = take(p->general || p->chans ? (size_t)p->batch * p->nc * p->nt * p->nt * sizeof(float2)
+                                        : 0);
   L.total = o;
 }
 
@@ -598,6 +599,12 @@ bs_status bs_plan_create(const bs_plan_desc *desc, bs_plan *out) {
   if (d.general != 0 && d.general != 1) return fail(nullptr, BS_ERR_ARG, "general must be 0 or 1");
   if (d.general && (long long)d.batch * 4 > 65535)
     return fail(nullptr, BS_ERR_ARG, "batch too large for a general plan");
+  if (d.chan_sampling != 0 && d.chan_sampling != 1)
+    return fail(nullptr, BS_ERR_ARG, "chan_sampling must be 0 or 1");
+  if (d.chan_sampling && d.general)
+    return fail(nullptr, BS_ERR_UNSUPPORTED, "chan_sampling with general input");
+  if (d.chan_sampling && (long long)d.batch * 2 > 65535)
+    return fail(nullptr, BS_ERR_ARG, "batch too large for a per-channel sampling plan");
   if (d.precision != BS_PREC_FP32 && d.precision != BS_PREC_SPLIT_BF16 &&
       d.precision != BS_PREC_SPLIT_FP16)
     return fail(nullptr, BS_ERR_ARG, "unknown precision");
@@ -631,8 +638,9 @@ bs_status bs_plan_create(const bs_plan_desc *desc, bs_plan *out) {
   // general input: four Hermitian components per realisation, processed as
   // realisations of their own and combined into complex results
   p->general = d.general != 0;
+  p->chans = d.chan_sampling != 0;
   p->ubatch = d.batch;
-  p->batch = p->general ? 4 * d.batch : d.batch;
+  p->batch = p->general ? 4 * d.batch : p->chans ? 2 * d.batch : d.batch;
   if (cudaHostAlloc(&p->err_host, sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
       cudaHostGetDevicePointer(&p->err_dev, p->err_host, 0) != cudaSuccess) {
     cudaGetLastError();
@@ -895,12 +903,16 @@ bs_status bs_grid_load(bs_plan p, const void *vis, const float *ngrid, const uin
   BS_CUDA(cudaMemcpyAsync(p->at<uint8_t>(L.valid), p->valid.data(), p->nc,
                           cudaMemcpyHostToDevice, s));
   const int8_t *lab = p->at<int8_t>(L.label);
-  if (ngrid) {
+  if (p->chans && !ngrid)
+    return fail(p, BS_ERR_ARG, "a per-channel sampling plan needs ngrid_dev [nchan][nt][nt]");
+  if (ngrid && !p->chans) {
     BS_CUDA(launch_effective_label(p->nt * p->nt, lab, ngrid, p->at<int8_t>(L.efflabel), s));
     st = run_counts(p, p->at<int8_t>(L.efflabel), s);
     if (st != BS_OK) return st;
     p->counts_default = false;
   } else if (!p->counts_ready || !p->counts_default) {
+    // geometric counts: with per-channel sampling they decide only which ring
+    // triples can close; the denominators come from the occupancy component
     st = run_counts(p, lab, s);
     if (st != BS_OK) return st;
     p->counts_default = true;
@@ -910,6 +922,12 @@ bs_status bs_grid_load(bs_plan p, const void *vis, const float *ngrid, const uin
     float2 *gv = p->at<float2>(L.gvis);
     BS_CUDA(launch_general_prep(p->nt, p->nc, p->ubatch, static_cast<const float2 *>(vis), ngrid,
                                 lab, gv, s));
+    st = enqueue_fields(p, gv, nullptr, s);
+  } else if (p->chans) {
+    // per-channel weights W V and occupancy masks, as two realisations each
+    float2 *gv = p->at<float2>(L.gvis);
+    BS_CUDA(launch_chans_prep(p->nt, p->nc, p->ubatch, static_cast<const float2 *>(vis), ngrid,
+                              lab, gv, s));
     st = enqueue_fields(p, gv, nullptr, s);
   } else {
     st = enqueue_fields(p, vis, ngrid, s);
@@ -986,7 +1004,7 @@ bs_status bs_mabs(bs_plan p, const int32_t *block, double *out_full, int accumul
   const WsLayout &L = p->L;
   const long long full_bstride = (long long)p->ntrip * nc * nc * nc;
   double *const user_full = out_full;
-  if (out_full && p->general) {  // the four real components go to the plan's scratch
+  if (out_full && (p->general || p->chans)) {  // the real components go to the plan's scratch
     st = general_scratch(p, &p->gfull, &p->gfull_cap, (size_t)p->batch * full_bstride);
     if (st != BS_OK) return st;
     out_full = p->gfull;
@@ -1059,6 +1077,8 @@ bs_status bs_mabs(bs_plan p, const int32_t *block, double *out_full, int accumul
                                  p->at<uint8_t>(L.valid), p->at<double>(L.tnorm), s));
   if (user_full && p->general)
     BS_CUDA(launch_combine4_full(out_full, p->ubatch, p->ntrip, nc, blk, user_full, s));
+  if (user_full && p->chans)  // tnorm cancels in the ratio; 1/A stays
+    BS_CUDA(launch_ratio2_full(out_full, p->ubatch, p->ntrip, nc, blk, 1.0 / p->normA, user_full, s));
   if (accumulate) accumulate_block_nnu(p, blk);
   return BS_OK;
 }
@@ -1118,7 +1138,7 @@ static bs_status delta_out(bs_plan p, double *out, bool closable, cudaStream_t s
   const int npl = closable ? (int)p->clos.size() : p->ntrip;
   const long long n2 = 2LL * p->nc - 1, per = (long long)npl * n2 * n2;
   double *dst = out;
-  if (p->general) {
+  if (p->general || p->chans) {
     bs_status st = general_scratch(p, &p->gdelta, &p->gdelta_cap, (size_t)p->batch * per);
     if (st != BS_OK) return st;
     dst = p->gdelta;
@@ -1128,12 +1148,32 @@ static bs_status delta_out(bs_plan p, double *out, bool closable, cudaStream_t s
                             closable ? p->at<int>(p->L.clos) : nullptr,
                             closable ? npl : 0, s));
   if (p->general) BS_CUDA(launch_combine4(dst, per, p->ubatch, out, s));
+  // per-channel sampling: (summed numerators) / (A x summed denominators)
+  if (p->chans && out) BS_CUDA(launch_ratio2(dst, per, p->ubatch, 1.0 / p->normA, out, s));
   return BS_OK;
 }
 
 // Eq. (dft) of every (or every closable) ring triple into out; general plans as above.
 static bs_status bs3d_out(bs_plan p, double *out, bool closable, cudaStream_t s) {
   const int npl = closable ? (int)p->clos.size() : p->ntrip;
+  if (p->chans) {
+    // the ratio planes of every ring triple, rewritten as collapse sums that the
+    // delay transform normalises back, then transformed like ordinary planes
+    bs_status st = delta_out(p, nullptr, false, s);  // components into gdelta only
+    if (st != BS_OK) return st;
+    const long long n2 = 2LL * p->nc - 1, per = (long long)p->ntrip * n2 * n2;
+    st = general_scratch(p, &p->g3d, &p->g3d_cap, (size_t)2 * p->ubatch * per);
+    if (st != BS_OK) return st;
+    double *ratio = p->g3d, *sums = p->g3d + (size_t)p->ubatch * per;
+    BS_CUDA(launch_ratio2(p->gdelta, per, p->ubatch, 1.0 / p->normA, ratio, s));
+    BS_CUDA(launch_ratio_to_sums(ratio, p->at<long long>(p->L.nnu), p->at<double>(p->L.tnorm),
+                                 p->ubatch, p->ntrip, p->nc, sums, s));
+    BS_CUDA(launch_bs3d(sums, p->at<long long>(p->L.nnu), p->at<double>(p->L.tnorm),
+                        p->at<float2>(p->L.tmp3d), out, p->ubatch, p->ntrip, p->nc,
+                        p->at<float2>(p->L.twN), p->radN, p->scale3d,
+                        closable ? p->at<int>(p->L.clos) : nullptr, closable ? npl : 0, s));
+    return BS_OK;
+  }
   const long long per = (long long)npl * p->nc * p->nc;
   double *dst = out;
   if (p->general) {

@@ -73,6 +73,8 @@ struct bs_plan_s {
   // Hermitian components X_H + t Y, t = 0, 1, -1, 2, of each user realisation) and
   // scratch for their real outputs before they are combined (device, on demand)
   bool general = false;
+  // per-channel sampling: batch = 2 x ubatch (weighted visibilities, occupancy)
+  bool chans = false;
   int ubatch = 1;
   double *gfull = nullptr, *gdelta = nullptr, *g3d = nullptr;
   size_t gfull_cap = 0, gdelta_cap = 0, g3d_cap = 0;

@@ -328,6 +328,52 @@ def test_collapse_fold_ratio_identity():
             assert g == pytest.approx(w, rel=1e-12, abs=1e-12 * np.nanmax(np.abs(bbar[k])))
 
 
+def test_collapse_ratio_of_sums_for_per_channel_sampling():
+    """The ratio-of-sums collapse (per-channel sampling): equal to the mean of
+    the estimates with one sampling grid; a constant field c gives c^3 / A at
+    every sampled separation whatever the per-channel occupancy; a field c(nu)
+    gives the mean of c1 c2 c3 weighted by the closed-triangle counts of the
+    occupied cells (those counts from the O(N^3) brute force)."""
+    nt, nc = 16, 4
+    vis, edges = _cfg_small(nt=nt, nc=nc)
+    res = oracle.mabs_full(vis, edges)
+    r = oracle.collapse_fold_ratio(res["num"], res["den"])
+    bbar, _ = oracle.collapse_fold(res["B"])
+    keep = res["T"] > 0
+    ok = ~np.isnan(bbar[keep])
+    np.testing.assert_allclose(r[keep][ok], bbar[keep][ok], rtol=1e-12,
+                               atol=1e-12 * np.nanmax(np.abs(bbar[keep])))
+    # per-channel occupancy, symmetric in U for each channel
+    g = synth.rng(41)
+    occ = g.integers(0, 2, size=(nc, nt, nt)).astype(float)
+    occ[:, 1:, 1:] = np.maximum(occ[:, 1:, 1:], occ[:, 1:, 1:][:, ::-1, ::-1])
+    c = np.array([1.5, -0.5, 2.0, 0.75])
+    for field in (np.full(nc, 1.3), c):
+        v = field[:, None, None] * occ  # N_g visibilities of value c(nu) per cell
+        rr = oracle.mabs_full(v.astype(complex), edges, ngrid=occ, norm_A=2.0)
+        got = oracle.collapse_fold_ratio(rr["num"], rr["den"], norm_A=2.0)
+        _, den, _ = _brute_force(v.astype(complex), edges, ngrid=occ)
+        w = np.einsum("i,j,l->ijl", field, field, field)
+        for k in np.flatnonzero(rr["T"] > 0):
+            for d1 in range(-(nc - 1), nc):
+                for d2 in range(-(nc - 1), nc):
+                    num_w = den_w = 0.0
+                    for sgn in ((1,) if d1 == d2 == 0 else (1, -1)):
+                        for n3 in range(nc):
+                            n1, n2 = n3 + sgn * d1, n3 + sgn * d2
+                            if 0 <= n1 < nc and 0 <= n2 < nc:
+                                num_w += w[n1, n2, n3] * den[k, n1, n2, n3]
+                                den_w += den[k, n1, n2, n3]
+                    x = got[k, d1 + nc - 1, d2 + nc - 1]
+                    if den_w == 0:
+                        assert np.isnan(x)
+                    else:
+                        assert x.real == pytest.approx(num_w / den_w / 2.0, rel=1e-12)
+        if np.all(field == field[0]):
+            fin = np.isfinite(got.real)
+            np.testing.assert_allclose(got.real[fin], field[0] ** 3 / 2.0, rtol=1e-12)
+
+
 def test_delta_points_rectangular_block():
     """The collapsed-plane points of a rectangular channel block (nu1, nu2 in
     one range, nu3 in another) against a brute-force mean over the full
