@@ -439,13 +439,28 @@ bs_status bs_mc_set_flags(bs_mc mc, int group, const uint8_t *flags_host);
 /* Tuning knob chosen by the autotuner: split K until the contraction has at
  * least tiles_per_sm tiles per SM (1..64).  Only before the first run. */
 bs_status bs_mc_set_tuning(bs_mc mc, int tiles_per_sm);
-/* Autotuner: time each candidate K-split target (tiles per SM in
- * {1, 2, 4, 8, 16}) on the registered inputs (one warm-up and two timed runs
- * each), keep the fastest and store it in the JSON file cache_path under the
- * ensemble's shape signature (NULL: no cache); a cached signature is applied
- * without timing.  Resets the statistics; writes the choice to *chosen.
- * Synchronises. */
+/* Autotuner over the tile shapes of the persistent contraction.  A tile is
+ * 256 fields x 512 channel pairs (fixed by the two-SM MMA and the pair
+ * producers) x a K range; the tuner chooses the K extent (split K until the
+ * launch holds at least tiles_per_sm tiles per SM, tiles_per_sm in
+ * {1, 2, 4, 8, 16}) and then the tile order (0: longest K first across
+ * groups, 1: group and ring-pair order, which keeps neighbouring CTA pairs on
+ * the same field rows).  Each candidate: one warm-up and two timed runs on the
+ * registered inputs.  The choice is stored in the JSON file cache_path under
+ * the ensemble's shape signature (shapes, rings, channel blocks; NULL: no
+ * cache); a cached signature is applied without timing.  Resets the
+ * statistics; writes the chosen tiles_per_sm to *chosen (bs_mc_tuning gives
+ * both knobs).  Synchronises. */
 bs_status bs_mc_autotune(bs_mc mc, const char *cache_path, int *chosen, void *cuda_stream);
+/* The tuning in effect: K-split target and tile order (either pointer may be NULL). */
+bs_status bs_mc_tuning(bs_mc mc, int *tiles_per_sm, int *tile_order);
+/* The channel block each run of group g contracts, int32 [6] = {nu1_lo,
+ * nu1_hi, nu2_lo, nu2_hi, nu3_lo, nu3_hi} (default: the full cube): a
+ * declared subset of the tiles of every realisation, for ensembles whose
+ * full channel cubes are too large to run (the collapse and Eq. (dft) then
+ * hold the separations of that block).  Drops prepared work and the captured
+ * graph.  Errors: BS_ERR_ARG (group, NULL, block out of range or empty). */
+bs_status bs_mc_set_block(bs_mc mc, int group, const int32_t *block_host);
 /* One Monte Carlo step over all groups (asynchronous on cuda_stream). */
 bs_status bs_mc_run(bs_mc mc, int use_graph, void *cuda_stream);
 /* Zero the statistics. */

@@ -38,7 +38,7 @@ EXPORTS = ("bs_abi_version", "bs_plan_create", "bs_plan_destroy", "bs_last_error
            "bs_bs_cylindrical", "bs_check_hermitian",
            "bs_mc_create", "bs_mc_destroy", "bs_mc_last_error", "bs_mc_info", "bs_mc_set_input",
            "bs_mc_set_flags", "bs_mc_set_tuning", "bs_mc_autotune", "bs_mc_run", "bs_mc_reset",
-           "bs_mc_stats",
+           "bs_mc_stats", "bs_mc_tuning", "bs_mc_set_block",
            "bs_mlp_features", "bs_mlp_create", "bs_mlp_destroy", "bs_mlp_last_error",
            "bs_mlp_params", "bs_mlp_fit_norm", "bs_mlp_forward", "bs_mlp_grad", "bs_mlp_train",
            "bs_sky_create", "bs_sky_destroy", "bs_sky_last_error", "bs_sky_generate",
@@ -110,6 +110,8 @@ def lib() -> ctypes.CDLL:
             L.bs_mc_run.argtypes = [P, I, P]
             L.bs_mc_autotune.argtypes = [P, ctypes.c_char_p, ctypes.POINTER(I), P]
             L.bs_mc_reset.argtypes = [P, P]
+            L.bs_mc_tuning.argtypes = [P, P, P]
+            L.bs_mc_set_block.argtypes = [P, I, P]
             L.bs_mc_stats.argtypes = [P, I, I, P, P, P, P]
             L.bs_mlp_features.argtypes = [P, P, P, P]
             L.bs_mlp_create.argtypes = [I, I, ctypes.c_uint64, ctypes.POINTER(P)]
@@ -577,6 +579,18 @@ class Ensemble:
         path = None if cache_path is None else str(cache_path).encode()
         self._check(self._L.bs_mc_autotune(self._h, path, ctypes.byref(c), _stream_ptr(stream)))
         return c.value
+
+    def tuning(self):
+        """bs_mc_tuning: (tiles_per_sm, tile_order) in effect."""
+        t, o = ctypes.c_int(), ctypes.c_int()
+        self._check(self._L.bs_mc_tuning(self._h, ctypes.byref(t), ctypes.byref(o)))
+        return t.value, o.value
+
+    def set_block(self, g, block):
+        """bs_mc_set_block: channel block (nu1_lo, nu1_hi, nu2_lo, nu2_hi, nu3_lo, nu3_hi)
+        that every run of group g contracts."""
+        self._blk = (ctypes.c_int32 * 6)(*[int(x) for x in block])
+        self._check(self._L.bs_mc_set_block(self._h, int(g), self._blk))
 
     def run(self, use_graph=True, stream=None):
         self._check(self._L.bs_mc_run(self._h, 1 if use_graph else 0, _stream_ptr(stream)))

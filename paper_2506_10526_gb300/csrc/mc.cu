@@ -67,6 +67,7 @@ struct Group {
   double *bout = nullptr;       // [batch][ntrip][nc][nc]
   double *stats = nullptr;      // 3 x (delta bins) then 3 x (bs3d bins): cnt, mean, m2
   long long nd = 0, nb3 = 0;    // bins per realisation
+  int blk[6] = {0, 0, 0, 0, 0, 0};  // channel block each run contracts (set at create: full cube)
 };
 
 }  // namespace
@@ -85,6 +86,7 @@ struct bs_mc_s {
   int ntiles = 0, nsm = 152;
   int f16 = 0;                  // 1: split-FP16 groups (two-product contraction)
   int min_tiles_factor = 2;     // autotuner knob: K splitting target (tiles per SM)
+  int tile_order = 0;           // autotuner knob: 0 longest K first, 1 ring-pair order
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   // graphs are captured and replayed on a private stream (the legacy default
@@ -138,8 +140,7 @@ bs_status mc_prepare(bs_mc m, cudaStream_t s) {
     MC_CUDA(cudaMemcpyAsync(p->at<uint8_t>(p->L.valid), p->valid.data(), p->nc,
                             cudaMemcpyHostToDevice, s));
     std::fill(p->nnu.begin(), p->nnu.end(), 0LL);
-    const int blk[6] = {0, p->nc, 0, p->nc, 0, p->nc};
-    accumulate_block_nnu(p, blk);
+    accumulate_block_nnu(p, m->groups[g].blk);
     st = upload_nnu(p, s);
     if (st != BS_OK) return plan_status(m, p, st);
   }
@@ -148,7 +149,7 @@ bs_status mc_prepare(bs_mc m, cudaStream_t s) {
   for (size_t g = 0; g < m->groups.size(); ++g) {
     bs_plan p = m->groups[g].plan;
     const size_t c0 = cols.size();
-    const int blk[6] = {0, p->nc, 0, p->nc, 0, p->nc};
+    const int *blk = m->groups[g].blk;
     std::vector<ColEntry> gc;
     std::vector<TcTile> gt;
     std::vector<TcGroup> G = build_tc_work(p, blk, (int)tgs.size(), gc, nullptr, gt, nullptr, 1,
@@ -162,10 +163,17 @@ bs_status mc_prepare(bs_mc m, cudaStream_t s) {
       maps.insert(maps.end(), mp, mp + sizeof(lv.maps));
     }
   }
-  // heaviest tiles first across all groups (balance of the persistent launch)
-  std::stable_sort(tiles.begin(), tiles.end(), [&](const TcTile &x, const TcTile &y) {
-    return tgs[x.group].kseg_len > tgs[y.group].kseg_len;
-  });
+  // order 0: the longest K ranges first across all groups (balance of the
+  // persistent launch); order 1: group, level and ring pair order as built
+  // (neighbouring CTA pairs share field rows in L2)
+  if (m->tile_order == 0)
+    std::stable_sort(tiles.begin(), tiles.end(), [&](const TcTile &x, const TcTile &y) {
+      return tgs[x.group].kseg_len > tgs[y.group].kseg_len;
+    });
+  else
+    std::stable_sort(tiles.begin(), tiles.end(), [&](const TcTile &x, const TcTile &y) {
+      return x.group < y.group;
+    });
   MC_CUDA(cudaMalloc(&m->cols, std::max<size_t>(1, cols.size()) * sizeof(ColEntry)));
   MC_CUDA(cudaMalloc(&m->tiles, std::max<size_t>(1, tiles.size()) * sizeof(TcTile)));
   MC_CUDA(cudaMalloc(&m->tcgroups, tgs.size() * sizeof(TcGroup)));
@@ -253,35 +261,47 @@ std::string mc_signature(bs_mc m) {
     const bs_plan p = gr.plan;
     o << "|nt" << p->nt << "nc" << p->nc << "M" << p->M << "b" << p->batch << "e";
     for (double e : p->edges) o << ":" << e;
+    o << "blk";
+    for (int k = 0; k < 6; ++k) o << ":" << gr.blk[k];
   }
   return o.str();
 }
 
-std::map<std::string, std::pair<int, double>> read_cache(const char *path) {
-  std::map<std::string, std::pair<int, double>> out;
+struct Tuned {
+  int tiles_per_sm = 2, order = 0;
+  double ms = 0.0;
+};
+
+std::map<std::string, Tuned> read_cache(const char *path) {
+  std::map<std::string, Tuned> out;
   std::ifstream f(path);
   std::string line;
   while (std::getline(f, line)) {
     const size_t q0 = line.find('"');
     const size_t q1 = q0 == std::string::npos ? q0 : line.find('"', q0 + 1);
     const size_t t = line.find("\"tiles_per_sm\":");
+    const size_t o = line.find("\"order\":");
     const size_t ms = line.find("\"ms\":");
     if (q1 == std::string::npos || t == std::string::npos || ms == std::string::npos) continue;
-    out[line.substr(q0 + 1, q1 - q0 - 1)] = {std::atoi(line.c_str() + t + 15),
-                                             std::atof(line.c_str() + ms + 5)};
+    Tuned v;
+    v.tiles_per_sm = std::atoi(line.c_str() + t + 15);
+    v.order = o == std::string::npos ? 0 : std::atoi(line.c_str() + o + 8);
+    v.ms = std::atof(line.c_str() + ms + 5);
+    out[line.substr(q0 + 1, q1 - q0 - 1)] = v;
   }
   return out;
 }
 
-void write_cache(const char *path, const std::map<std::string, std::pair<int, double>> &c) {
+void write_cache(const char *path, const std::map<std::string, Tuned> &c) {
   const std::string tmp = std::string(path) + ".tmp";
   {
     std::ofstream f(tmp);
     f << "{\n";
     size_t k = 0;
     for (const auto &kv : c)
-      f << "\"" << kv.first << "\": {\"tiles_per_sm\": " << kv.second.first
-        << ", \"ms\": " << kv.second.second << "}" << (++k < c.size() ? "," : "") << "\n";
+      f << "\"" << kv.first << "\": {\"tiles_per_sm\": " << kv.second.tiles_per_sm
+        << ", \"order\": " << kv.second.order << ", \"ms\": " << kv.second.ms << "}"
+        << (++k < c.size() ? "," : "") << "\n";
     f << "}\n";
   }
   std::rename(tmp.c_str(), path);
@@ -297,55 +317,90 @@ bs_status bs_mc_autotune(bs_mc m, const char *cache_path, int *chosen, void *str
   for (size_t g = 0; g < m->groups.size(); ++g)
     if (!m->groups[g].vis) return mfail(m, BS_ERR_STATE, "autotune needs every group's input");
   const std::string key = mc_signature(m);
-  std::map<std::string, std::pair<int, double>> cache;
+  std::map<std::string, Tuned> cache;
   if (cache_path) cache = read_cache(cache_path);
   auto hit = cache.find(key);
-  int best = -1;
-  double best_ms = 0;
+  Tuned best;
+  best.ms = -1.0;
+  // one candidate: prepare its tiles, one warm-up run, two timed runs
+  auto trial = [&](int tps, int order, double *ms_out) -> bs_status {
+    mc_unprepare(m);
+    m->min_tiles_factor = tps;
+    m->tile_order = order;
+    bs_status st = mc_prepare(m, s);
+    if (st != BS_OK) return st;
+    st = mc_enqueue(m, s);
+    if (st != BS_OK) return st;
+    cudaEvent_t e0, e1;
+    MC_CUDA(cudaEventCreate(&e0));
+    MC_CUDA(cudaEventCreate(&e1));
+    MC_CUDA(cudaEventRecord(e0, s));
+    for (int r = 0; r < 2 && st == BS_OK; ++r) st = mc_enqueue(m, s);
+    MC_CUDA(cudaEventRecord(e1, s));
+    MC_CUDA(cudaEventSynchronize(e1));
+    float ms = 0;
+    MC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms_out = ms / 2;
+    return st;
+  };
   if (hit != cache.end()) {
-    best = hit->second.first;
-    best_ms = hit->second.second;
+    best = hit->second;
   } else {
-    const int cands[] = {1, 2, 4, 8, 16};
-    for (int c : cands) {
-      mc_unprepare(m);
-      m->min_tiles_factor = c;
-      bs_status st = mc_prepare(m, s);
+    // coordinate search: the K extent of the tiles (split target, tiles per SM),
+    // then the tile order at the best K extent
+    for (int c : {1, 2, 4, 8, 16}) {
+      double ms = 0;
+      bs_status st = trial(c, 0, &ms);
       if (st != BS_OK) return st;
-      st = mc_enqueue(m, s);  // warm-up
-      if (st != BS_OK) return st;
-      cudaEvent_t e0, e1;
-      MC_CUDA(cudaEventCreate(&e0));
-      MC_CUDA(cudaEventCreate(&e1));
-      MC_CUDA(cudaEventRecord(e0, s));
-      for (int r = 0; r < 2; ++r) {
-        st = mc_enqueue(m, s);
-        if (st != BS_OK) return st;
-      }
-      MC_CUDA(cudaEventRecord(e1, s));
-      MC_CUDA(cudaEventSynchronize(e1));
-      float ms = 0;
-      MC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-      cudaEventDestroy(e0);
-      cudaEventDestroy(e1);
-      if (best < 0 || ms / 2 < best_ms) {
-        best = c;
-        best_ms = ms / 2;
+      if (best.ms < 0 || ms < best.ms) {
+        best.tiles_per_sm = c;
+        best.order = 0;
+        best.ms = ms;
       }
     }
+    double ms = 0;
+    bs_status st = trial(best.tiles_per_sm, 1, &ms);
+    if (st != BS_OK) return st;
+    if (ms < best.ms) {
+      best.order = 1;
+      best.ms = ms;
+    }
     if (cache_path) {
-      cache[key] = {best, best_ms};
+      cache[key] = best;
       write_cache(cache_path, cache);
     }
   }
   mc_unprepare(m);
-  m->min_tiles_factor = best;
+  m->min_tiles_factor = best.tiles_per_sm;
+  m->tile_order = best.order;
   bs_status st = mc_prepare(m, s);
   if (st != BS_OK) return st;
   for (Group &gr : m->groups)  // tuning runs do not count as realisations
     MC_CUDA(cudaMemsetAsync(gr.stats, 0, (size_t)3 * (gr.nd + gr.nb3) * 8, s));
   m->runs = 0;
-  if (chosen) *chosen = best;
+  if (chosen) *chosen = best.tiles_per_sm;
+  return BS_OK;
+}
+
+bs_status bs_mc_tuning(bs_mc m, int *tiles_per_sm, int *tile_order) {
+  if (!m) return BS_ERR_ARG;
+  if (tiles_per_sm) *tiles_per_sm = m->min_tiles_factor;
+  if (tile_order) *tile_order = m->tile_order;
+  return BS_OK;
+}
+
+bs_status bs_mc_set_block(bs_mc m, int group, const int32_t *block_host) {
+  if (!m || group < 0 || group >= (int)m->groups.size() || !block_host)
+    return mfail(m, BS_ERR_ARG, "bs_mc_set_block: bad arguments");
+  Group &gr = m->groups[group];
+  const int nc = gr.plan->nc;
+  for (int k = 0; k < 6; k += 2)
+    if (block_host[k] < 0 || block_host[k + 1] > nc || block_host[k] >= block_host[k + 1])
+      return mfail(m, BS_ERR_ARG, "bs_mc_set_block: block out of range");
+  for (int k = 0; k < 6; ++k) gr.blk[k] = block_host[k];
+  mc_unprepare(m);  // tiles and sampling change: rebuilt (and recaptured) on the next run
   return BS_OK;
 }
 
@@ -375,6 +430,8 @@ bs_status bs_mc_create(const bs_plan_desc *descs, int ngroups, bs_mc *out) {
     }
     bs_plan p = gr.plan;
     m->nsm = p->nsm;
+    const int full[6] = {0, p->nc, 0, p->nc, 0, p->nc};
+    for (int k = 0; k < 6; ++k) gr.blk[k] = full[k];
     const size_t n2 = (size_t)(2 * p->nc - 1);
     gr.nd = (long long)p->ntrip * n2 * n2;
     gr.nb3 = (long long)p->ntrip * p->nc * p->nc;

@@ -105,4 +105,66 @@ def test_mc_autotuner_cache(tmp_path):
         ens.close()
     assert chosen[0] == chosen[1] and chosen[0] in (1, 2, 4, 8, 16)
     data = json.loads(cache.read_text())
-    assert len(data) == 1 and list(data.values())[0]["tiles_per_sm"] == chosen[0]
+    entry = list(data.values())[0]
+    assert len(data) == 1 and entry["tiles_per_sm"] == chosen[0] and entry["order"] in (0, 1)
+
+
+def _block_collapse(B, blk):
+    """Folded mean of the full cube B [ntrip, nc, nc, nc] over the valid channel
+    triples of a block (the collapse of Section 3.2 restricted to the block)."""
+    ntrip, nc = B.shape[0], B.shape[1]
+    n2 = 2 * nc - 1
+    s = np.zeros((ntrip, n2, n2))
+    c = np.zeros((ntrip, n2, n2))
+    for n1 in range(blk[0], blk[1]):
+        for n2_ in range(blk[2], blk[3]):
+            for n3 in range(blk[4], blk[5]):
+                v = B[:, n1, n2_, n3]
+                ok = ~np.isnan(v)
+                s[ok, n1 - n3 + nc - 1, n2_ - n3 + nc - 1] += v[ok]
+                c[ok, n1 - n3 + nc - 1, n2_ - n3 + nc - 1] += 1
+    sf, cf = oracle.fold_plane(s), oracle.fold_plane(c)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        return np.where(cf > 0, sf / np.where(cf > 0, cf, 1), np.nan)
+
+
+def test_mc_declared_block_subset_and_tile_order():
+    """A declared channel block per group (a subset of each realisation's
+    tiles): the ensemble mean of the collapsed plane equals the oracle's
+    collapse restricted to that block; the autotuner's choice of K extent and
+    tile order is reported, and a run with the other tile order gives the
+    same statistics."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2506_10526_gb300 as bs
+    blk = (1, 6, 0, 5, 2, 8)
+    means = []
+    for order in (0, 1):
+        ens = bs.Ensemble(GROUPS)
+        bufs = []
+        for g, spec in enumerate(GROUPS):
+            v = np.stack([_realisation(g, b) for b in range(spec["batch"])])
+            bufs.append(torch.from_numpy(v).cuda())
+            ens.set_input(g, bufs[-1])
+        ens.set_block(0, blk)
+        if order == 0:
+            ens.autotune()
+            tps, ordr = ens.tuning()
+            assert tps in (1, 2, 4, 8, 16) and ordr in (0, 1)
+        ens.run(use_graph=True)
+        means.append(ens.stats(0, 0))
+        ens.close()
+    spec = GROUPS[0]
+    planes = []
+    for k in range(spec["batch"]):
+        res = oracle.mabs_full(_realisation(0, k).astype(np.complex128), spec["edges"])
+        planes.append(_block_collapse(res["B"].real, blk))
+    want = np.mean(planes, axis=0)
+    mean, _, n = means[0]
+    assert n == spec["batch"]
+    assert np.array_equal(np.isnan(mean), np.isnan(want))
+    ok = ~np.isnan(want)
+    assert np.abs(mean[ok] - want[ok]).max() <= 1e-3 * np.abs(want[ok]).max()
+    np.testing.assert_allclose(means[1][0][ok], mean[ok], rtol=1e-9,
+                               atol=1e-12 * np.abs(mean[ok]).max())
