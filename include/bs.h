@@ -476,6 +476,20 @@ bs_status bs_mc_reset(bs_mc mc, void *cuda_stream);
 bs_status bs_mc_stats(bs_mc mc, int group, int which, double *mean_dev, double *var_dev,
                       int64_t *realisations_host, void *cuda_stream);
 
+/* Checkpoint and resume of a long Monte Carlo run (not in the paper).
+ * bs_mc_checkpoint synchronises on cuda_stream and writes to the file `path`
+ * (written to path.tmp, then renamed): the ensemble's shape signature, the
+ * per-bin Welford state (count, mean, M2) of every group, the runs so far, the
+ * tuning, and `counter`, a value of the caller's -- e.g. the realisation index
+ * that the next bs_sky_generate call starts at (the Philox counter), so that a
+ * resumed run draws the realisations that the interrupted one would have.
+ * bs_mc_restore reads such a file into an ensemble of the same shapes, returns
+ * the counter, and replaces the statistics, the run count and the tuning.
+ * Errors: BS_ERR_ARG (NULL path, unreadable or unwritable file, another
+ * ensemble's checkpoint), BS_ERR_CUDA. */
+bs_status bs_mc_checkpoint(bs_mc mc, const char *path, uint64_t counter, void *cuda_stream);
+bs_status bs_mc_restore(bs_mc mc, const char *path, uint64_t *counter, void *cuda_stream);
+
 /* ---------------------------------------------------------------------------
  * Error-bar surrogate (not in the paper, whose error bars are brute Monte
  * Carlo over 250 realisations, Section 4): a 3-layer MLP

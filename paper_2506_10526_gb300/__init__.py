@@ -38,7 +38,8 @@ EXPORTS = ("bs_abi_version", "bs_plan_create", "bs_plan_destroy", "bs_last_error
            "bs_bs_cylindrical", "bs_check_hermitian",
            "bs_mc_create", "bs_mc_destroy", "bs_mc_last_error", "bs_mc_info", "bs_mc_set_input",
            "bs_mc_set_flags", "bs_mc_set_tuning", "bs_mc_autotune", "bs_mc_run", "bs_mc_reset",
-           "bs_mc_stats", "bs_mc_tuning", "bs_mc_set_block",
+           "bs_mc_stats", "bs_mc_tuning", "bs_mc_set_block", "bs_mc_checkpoint",
+           "bs_mc_restore",
            "bs_mlp_features", "bs_mlp_create", "bs_mlp_destroy", "bs_mlp_last_error",
            "bs_mlp_params", "bs_mlp_fit_norm", "bs_mlp_forward", "bs_mlp_grad", "bs_mlp_train",
            "bs_sky_create", "bs_sky_destroy", "bs_sky_last_error", "bs_sky_generate",
@@ -112,6 +113,8 @@ def lib() -> ctypes.CDLL:
             L.bs_mc_reset.argtypes = [P, P]
             L.bs_mc_tuning.argtypes = [P, P, P]
             L.bs_mc_set_block.argtypes = [P, I, P]
+            L.bs_mc_checkpoint.argtypes = [P, ctypes.c_char_p, ctypes.c_uint64, P]
+            L.bs_mc_restore.argtypes = [P, ctypes.c_char_p, P, P]
             L.bs_mc_stats.argtypes = [P, I, I, P, P, P, P]
             L.bs_mlp_features.argtypes = [P, P, P, P]
             L.bs_mlp_create.argtypes = [I, I, ctypes.c_uint64, ctypes.POINTER(P)]
@@ -591,6 +594,18 @@ class Ensemble:
         that every run of group g contracts."""
         self._blk = (ctypes.c_int32 * 6)(*[int(x) for x in block])
         self._check(self._L.bs_mc_set_block(self._h, int(g), self._blk))
+
+    def checkpoint(self, path, counter=0, stream=None):
+        """bs_mc_checkpoint: statistics, runs, tuning and the caller's counter to `path`."""
+        self._check(self._L.bs_mc_checkpoint(self._h, str(path).encode(),
+                                             ctypes.c_uint64(int(counter)), _stream_ptr(stream)))
+
+    def restore(self, path, stream=None):
+        """bs_mc_restore: load a checkpoint of the same shapes; returns the counter."""
+        c = ctypes.c_uint64(0)
+        self._check(self._L.bs_mc_restore(self._h, str(path).encode(), ctypes.byref(c),
+                                          _stream_ptr(stream)))
+        return c.value
 
     def run(self, use_graph=True, stream=None):
         self._check(self._L.bs_mc_run(self._h, 1 if use_graph else 0, _stream_ptr(stream)))

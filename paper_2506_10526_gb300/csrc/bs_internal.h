@@ -11,6 +11,8 @@
 
 #include "bs.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace bsi {
 
 // Mixed-radix factorisation of a transform length (radices 4, 2, 3, 5).
@@ -112,6 +114,22 @@ struct TcArgs {
   int stall_test;          // failure injection: the MMA thread waits on a barrier nobody arrives at
   int f16;                 // 1: split-FP16 operands (two products), 0: split BF16 (three)
 };
+
+// NVTX range over an entry point, named after it (no cost unless a profiler
+// that records NVTX is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
+#define BS_NVTX(name) ::bsi::NvtxRange bs_nvtx_range_(name)
+
+// Host-side failure injection for tests: true when the environment variable
+// BS_INJECT_FAIL lists `point` (comma-separated: plan_create, workspace_alloc,
+// mc_alloc, sky_alloc, mlp_alloc, scratch_alloc).  The caller then fails as
+// the real failure would (BS_ERR_OOM), without touching the device.
+bool inject_fail(const char *point);
 
 // Grid cell (u, v) with |u|, |v| < 32768 packed as (u + 32768) | (v + 32768) << 16,
 // computed in unsigned arithmetic and stored bit for bit in an int; the

@@ -182,6 +182,7 @@ int ceil_log2(int m) {
 
 extern "C" bs_status bs_mabs_error_bound(bs_plan p, double *bound_dev, const double *delta_dev,
                                          int closable, double *relerr_dev, void *stream) {
+  BS_NVTX("bs_mabs_error_bound");
   using namespace bsi;
   if (!p || !bound_dev) return fail(p, BS_ERR_ARG, "bs_mabs_error_bound: bound_dev must not be NULL");
   if ((delta_dev == nullptr) != (relerr_dev == nullptr))

@@ -80,6 +80,7 @@ extern "C" {
 bs_status bs_grid_visibilities(bs_plan p, const double *uv_dev, const void *vis_dev,
                                const uint8_t *flag_dev, int64_t nbl, int nchan_in, int avg,
                                int mode, void *out_vis_dev, float *out_ng_dev, void *stream) {
+  BS_NVTX("bs_grid_visibilities");
   using namespace bsi;
   if (!p || !uv_dev || !vis_dev || !out_vis_dev || !out_ng_dev)
     return fail(p, BS_ERR_ARG, "bs_grid_visibilities: NULL argument");

@@ -312,6 +312,7 @@ void write_cache(const char *path, const std::map<std::string, Tuned> &c) {
 extern "C" {
 
 bs_status bs_mc_autotune(bs_mc m, const char *cache_path, int *chosen, void *stream) {
+  BS_NVTX("bs_mc_autotune");
   if (!m) return BS_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   for (size_t g = 0; g < m->groups.size(); ++g)
@@ -385,6 +386,7 @@ bs_status bs_mc_autotune(bs_mc m, const char *cache_path, int *chosen, void *str
 }
 
 bs_status bs_mc_tuning(bs_mc m, int *tiles_per_sm, int *tile_order) {
+  BS_NVTX("bs_mc_tuning");
   if (!m) return BS_ERR_ARG;
   if (tiles_per_sm) *tiles_per_sm = m->min_tiles_factor;
   if (tile_order) *tile_order = m->tile_order;
@@ -392,6 +394,7 @@ bs_status bs_mc_tuning(bs_mc m, int *tiles_per_sm, int *tile_order) {
 }
 
 bs_status bs_mc_set_block(bs_mc m, int group, const int32_t *block_host) {
+  BS_NVTX("bs_mc_set_block");
   if (!m || group < 0 || group >= (int)m->groups.size() || !block_host)
     return mfail(m, BS_ERR_ARG, "bs_mc_set_block: bad arguments");
   Group &gr = m->groups[group];
@@ -407,6 +410,7 @@ bs_status bs_mc_set_block(bs_mc m, int group, const int32_t *block_host) {
 const char *bs_mc_last_error(bs_mc m) { return m ? m->err.c_str() : bs_last_error(nullptr); }
 
 bs_status bs_mc_create(const bs_plan_desc *descs, int ngroups, bs_mc *out) {
+  BS_NVTX("bs_mc_create");
   if (!descs || !out || ngroups < 1 || ngroups > 64) return fail(nullptr, BS_ERR_ARG, "bad arguments");
   *out = nullptr;
   bs_mc m = new bs_mc_s();
@@ -435,7 +439,8 @@ bs_status bs_mc_create(const bs_plan_desc *descs, int ngroups, bs_mc *out) {
     const size_t n2 = (size_t)(2 * p->nc - 1);
     gr.nd = (long long)p->ntrip * n2 * n2;
     gr.nb3 = (long long)p->ntrip * p->nc * p->nc;
-    if (cudaMalloc(&gr.dout, (size_t)p->batch * gr.nd * 8) != cudaSuccess ||
+    if (inject_fail("mc_alloc") ||
+        cudaMalloc(&gr.dout, (size_t)p->batch * gr.nd * 8) != cudaSuccess ||
         cudaMalloc(&gr.bout, (size_t)p->batch * gr.nb3 * 8) != cudaSuccess ||
         cudaMalloc(&gr.stats, (size_t)3 * (gr.nd + gr.nb3) * 8) != cudaSuccess) {
       cudaGetLastError();
@@ -451,6 +456,7 @@ bs_status bs_mc_create(const bs_plan_desc *descs, int ngroups, bs_mc *out) {
 }
 
 bs_status bs_mc_destroy(bs_mc m) {
+  BS_NVTX("bs_mc_destroy");
   if (!m) return BS_OK;
   mc_unprepare(m);
   if (m->gstream) {
@@ -470,11 +476,13 @@ bs_status bs_mc_destroy(bs_mc m) {
 }
 
 bs_status bs_mc_info(bs_mc m, int group, int64_t *info_host, int n) {
+  BS_NVTX("bs_mc_info");
   if (!m || group < 0 || group >= (int)m->groups.size()) return BS_ERR_ARG;
   return bs_plan_info(m->groups[group].plan, info_host, n);
 }
 
 bs_status bs_mc_set_input(bs_mc m, int group, const void *vis_dev) {
+  BS_NVTX("bs_mc_set_input");
   if (!m || group < 0 || group >= (int)m->groups.size())
     return m ? mfail(m, BS_ERR_ARG, "bad group") : BS_ERR_ARG;
   if (!vis_dev || (reinterpret_cast<uintptr_t>(vis_dev) & 7))
@@ -490,6 +498,7 @@ bs_status bs_mc_set_input(bs_mc m, int group, const void *vis_dev) {
 }
 
 bs_status bs_mc_set_flags(bs_mc m, int group, const uint8_t *flags_host) {
+  BS_NVTX("bs_mc_set_flags");
   if (!m || group < 0 || group >= (int)m->groups.size())
     return m ? mfail(m, BS_ERR_ARG, "bad group") : BS_ERR_ARG;
   Group &gr = m->groups[group];
@@ -502,6 +511,7 @@ bs_status bs_mc_set_flags(bs_mc m, int group, const uint8_t *flags_host) {
 }
 
 bs_status bs_mc_set_tuning(bs_mc m, int tiles_per_sm) {
+  BS_NVTX("bs_mc_set_tuning");
   if (!m || tiles_per_sm < 1 || tiles_per_sm > 64) return BS_ERR_ARG;
   if (m->prepared) return mfail(m, BS_ERR_STATE, "tuning must be set before the first run");
   m->min_tiles_factor = tiles_per_sm;
@@ -509,6 +519,7 @@ bs_status bs_mc_set_tuning(bs_mc m, int tiles_per_sm) {
 }
 
 bs_status bs_mc_run(bs_mc m, int use_graph, void *stream) {
+  BS_NVTX("bs_mc_run");
   if (!m) return BS_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   for (size_t g = 0; g < m->groups.size(); ++g)
@@ -551,6 +562,7 @@ bs_status bs_mc_run(bs_mc m, int use_graph, void *stream) {
 }
 
 bs_status bs_mc_reset(bs_mc m, void *stream) {
+  BS_NVTX("bs_mc_reset");
   if (!m) return BS_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   for (Group &gr : m->groups)
@@ -559,8 +571,98 @@ bs_status bs_mc_reset(bs_mc m, void *stream) {
   return BS_OK;
 }
 
+// Checkpoint file: "BSMCCKP1", then (little-endian host integers) the signature
+// length and the ensemble's shape signature, the caller's counter, the runs,
+// the tuning (tiles per SM, order), the number of groups, and per group its bin
+// counts nd, nb3 followed by the 3 (nd + nb3) FP64 Welford values (count,
+// mean, M2 of the collapsed plane, then of the 3D bispectrum).
+static const char kCkptMagic[8] = {'B', 'S', 'M', 'C', 'C', 'K', 'P', '1'};
+
+bs_status bs_mc_checkpoint(bs_mc m, const char *path, uint64_t counter, void *stream) {
+  BS_NVTX("bs_mc_checkpoint");
+  if (!m || !path) return m ? mfail(m, BS_ERR_ARG, "bs_mc_checkpoint: NULL path") : BS_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  MC_CUDA(cudaStreamSynchronize(s));
+  const std::string sig = mc_signature(m);
+  const std::string tmp = std::string(path) + ".tmp";
+  std::ofstream f(tmp, std::ios::binary);
+  if (!f) return mfail(m, BS_ERR_ARG, std::string("bs_mc_checkpoint: cannot write ") + tmp);
+  const uint64_t siglen = sig.size();
+  const int64_t runs = m->runs;
+  const int32_t tune[2] = {m->min_tiles_factor, m->tile_order};
+  const int32_t ng = (int32_t)m->groups.size();
+  f.write(kCkptMagic, 8);
+  f.write(reinterpret_cast<const char *>(&siglen), 8);
+  f.write(sig.data(), (std::streamsize)siglen);
+  f.write(reinterpret_cast<const char *>(&counter), 8);
+  f.write(reinterpret_cast<const char *>(&runs), 8);
+  f.write(reinterpret_cast<const char *>(tune), 8);
+  f.write(reinterpret_cast<const char *>(&ng), 4);
+  std::vector<double> h;
+  for (const Group &gr : m->groups) {
+    const int64_t nd = gr.nd, nb3 = gr.nb3;
+    h.resize((size_t)3 * (nd + nb3));
+    MC_CUDA(cudaMemcpy(h.data(), gr.stats, h.size() * 8, cudaMemcpyDeviceToHost));
+    f.write(reinterpret_cast<const char *>(&nd), 8);
+    f.write(reinterpret_cast<const char *>(&nb3), 8);
+    f.write(reinterpret_cast<const char *>(h.data()), (std::streamsize)(h.size() * 8));
+  }
+  f.close();
+  if (!f) return mfail(m, BS_ERR_ARG, std::string("bs_mc_checkpoint: write failed: ") + tmp);
+  if (std::rename(tmp.c_str(), path) != 0)
+    return mfail(m, BS_ERR_ARG, std::string("bs_mc_checkpoint: cannot rename to ") + path);
+  return BS_OK;
+}
+
+bs_status bs_mc_restore(bs_mc m, const char *path, uint64_t *counter, void *stream) {
+  BS_NVTX("bs_mc_restore");
+  if (!m || !path) return m ? mfail(m, BS_ERR_ARG, "bs_mc_restore: NULL path") : BS_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::ifstream f(path, std::ios::binary);
+  if (!f) return mfail(m, BS_ERR_ARG, std::string("bs_mc_restore: cannot read ") + path);
+  char magic[8];
+  uint64_t siglen = 0, ctr = 0;
+  int64_t runs = 0;
+  int32_t tune[2] = {0, 0}, ng = 0;
+  f.read(magic, 8);
+  f.read(reinterpret_cast<char *>(&siglen), 8);
+  if (!f || std::memcmp(magic, kCkptMagic, 8) != 0 || siglen > (1u << 20))
+    return mfail(m, BS_ERR_ARG, "bs_mc_restore: not a Monte Carlo checkpoint");
+  std::string sig(siglen, '\0');
+  f.read(&sig[0], (std::streamsize)siglen);
+  f.read(reinterpret_cast<char *>(&ctr), 8);
+  f.read(reinterpret_cast<char *>(&runs), 8);
+  f.read(reinterpret_cast<char *>(tune), 8);
+  f.read(reinterpret_cast<char *>(&ng), 4);
+  if (!f || sig != mc_signature(m) || ng != (int32_t)m->groups.size())
+    return mfail(m, BS_ERR_ARG, "bs_mc_restore: the checkpoint belongs to other shapes");
+  std::vector<std::vector<double>> h(m->groups.size());
+  for (size_t g = 0; g < m->groups.size(); ++g) {
+    int64_t nd = 0, nb3 = 0;
+    f.read(reinterpret_cast<char *>(&nd), 8);
+    f.read(reinterpret_cast<char *>(&nb3), 8);
+    if (!f || nd != m->groups[g].nd || nb3 != m->groups[g].nb3)
+      return mfail(m, BS_ERR_ARG, "bs_mc_restore: bin counts differ");
+    h[g].resize((size_t)3 * (nd + nb3));
+    f.read(reinterpret_cast<char *>(h[g].data()), (std::streamsize)(h[g].size() * 8));
+    if (!f) return mfail(m, BS_ERR_ARG, "bs_mc_restore: truncated checkpoint");
+  }
+  if (tune[0] != m->min_tiles_factor || tune[1] != m->tile_order) {
+    mc_unprepare(m);
+    m->min_tiles_factor = tune[0];
+    m->tile_order = tune[1];
+  }
+  MC_CUDA(cudaStreamSynchronize(s));
+  for (size_t g = 0; g < m->groups.size(); ++g)
+    MC_CUDA(cudaMemcpy(m->groups[g].stats, h[g].data(), h[g].size() * 8, cudaMemcpyHostToDevice));
+  m->runs = runs;
+  if (counter) *counter = ctr;
+  return BS_OK;
+}
+
 bs_status bs_mc_stats(bs_mc m, int group, int which, double *mean_dev, double *var_dev,
                       int64_t *runs_host, void *stream) {
+  BS_NVTX("bs_mc_stats");
   if (!m || group < 0 || group >= (int)m->groups.size() || (which != 0 && which != 1))
     return m ? mfail(m, BS_ERR_ARG, "bad group or statistic") : BS_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);

@@ -359,6 +359,7 @@ extern "C" {
 const char *bs_mlp_last_error(bs_mlp m) { return m ? m->err.c_str() : "no surrogate"; }
 
 bs_status bs_mlp_create(int d_in, int width, uint64_t seed, bs_mlp *out) {
+  BS_NVTX("bs_mlp_create");
   if (!out || d_in < 1 || d_in > kMaxD || width < 1 || width > kMaxW) return BS_ERR_ARG;
   *out = nullptr;
   bs_mlp m = new bs_mlp_s();
@@ -388,7 +389,8 @@ bs_status bs_mlp_create(int d_in, int width, uint64_t seed, bs_mlp *out) {
   std::vector<float> norm(2 * d_in + 2, 0.f);
   for (int k = 0; k < d_in; ++k) norm[d_in + k] = 1.f;
   norm[2 * d_in + 1] = 1.f;
-  if (cudaMalloc(&m->dev.p, np * 4) != cudaSuccess || cudaMalloc(&m->dev.g, np * 4) != cudaSuccess ||
+  if (inject_fail("mlp_alloc") || cudaMalloc(&m->dev.p, np * 4) != cudaSuccess ||
+      cudaMalloc(&m->dev.g, np * 4) != cudaSuccess ||
       cudaMalloc(&m->dev.m, np * 4) != cudaSuccess || cudaMalloc(&m->dev.v, np * 4) != cudaSuccess ||
       cudaMalloc(&m->dev.norm, norm.size() * 4) != cudaSuccess ||
       cudaMalloc(&m->loss, sizeof(float)) != cudaSuccess) {
@@ -412,6 +414,7 @@ bs_status bs_mlp_create(int d_in, int width, uint64_t seed, bs_mlp *out) {
 }
 
 bs_status bs_mlp_destroy(bs_mlp m) {
+  BS_NVTX("bs_mlp_destroy");
   if (!m) return BS_OK;
   cudaFree(m->dev.p);
   cudaFree(m->dev.g);
@@ -427,6 +430,7 @@ bs_status bs_mlp_destroy(bs_mlp m) {
 }
 
 bs_status bs_mlp_params(bs_mlp m, float *params_host, int64_t n, int set) {
+  BS_NVTX("bs_mlp_params");
   if (!m || !params_host) return BS_ERR_ARG;
   const long long np = n_params(m->dev.d, m->dev.w);
   const long long nn = np + 2 * m->dev.d + 2;
@@ -445,6 +449,7 @@ bs_status bs_mlp_params(bs_mlp m, float *params_host, int64_t n, int set) {
 }
 
 bs_status bs_mlp_fit_norm(bs_mlp m, const float *x_dev, const float *t_dev, int n, void *stream) {
+  BS_NVTX("bs_mlp_fit_norm");
   if (!m || !x_dev || !t_dev || n < 2) return BS_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   k_mlp_colstats<<<m->dev.d + 1, 256, 0, s>>>(x_dev, t_dev, n, m->dev.d, m->dev.norm);
@@ -453,6 +458,7 @@ bs_status bs_mlp_fit_norm(bs_mlp m, const float *x_dev, const float *t_dev, int 
 }
 
 bs_status bs_mlp_forward(bs_mlp m, const float *x_dev, int n, float *y_dev, void *stream) {
+  BS_NVTX("bs_mlp_forward");
   if (!m || !x_dev || !y_dev || n < 0) return BS_ERR_ARG;
   if (n == 0) return BS_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -464,6 +470,7 @@ bs_status bs_mlp_forward(bs_mlp m, const float *x_dev, int n, float *y_dev, void
 
 bs_status bs_mlp_grad(bs_mlp m, const float *x_dev, const float *t_dev, int n, float *grad_host,
                       float *loss_host, void *stream) {
+  BS_NVTX("bs_mlp_grad");
   if (!m || !x_dev || !t_dev || n < 1) return BS_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   bs_status st = ensure_scratch(m, n);
@@ -482,6 +489,7 @@ bs_status bs_mlp_grad(bs_mlp m, const float *x_dev, const float *t_dev, int n, f
 
 bs_status bs_mlp_train(bs_mlp m, const float *x_dev, const float *t_dev, int n, int steps,
                        int batch, float lr, uint64_t seed, float *loss_host, void *stream) {
+  BS_NVTX("bs_mlp_train");
   if (!m || !x_dev || !t_dev || n < 1 || steps < 0 || batch < 1) return BS_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   bs_status st = ensure_scratch(m, batch);
@@ -512,6 +520,7 @@ bs_status bs_mlp_train(bs_mlp m, const float *x_dev, const float *t_dev, int n, 
   } while (0)
 
 bs_status bs_mlp_features(bs_plan p, const uint8_t *flags_host, float *feat_dev, void *stream) {
+  BS_NVTX("bs_mlp_features");
   if (!p || !feat_dev) return BS_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   bs_status st = prepare(p, s);

@@ -346,6 +346,7 @@ static size_t mono_smem(int nbin, int nbatch) {
 extern "C" {
 
 bs_status bs_plan_ring_umean(bs_plan p, double *umean_host) {
+  BS_NVTX("bs_plan_ring_umean");
   if (!p || !umean_host) return fail(p, BS_ERR_ARG, "umean_host must not be NULL");
   for (int m = 0; m < p->nb; ++m) umean_host[m] = p->umean[m];
   return BS_OK;
@@ -355,6 +356,7 @@ bs_status bs_bs_monopole(bs_plan p, const double *b3d, const double *kperp_host,
                          const double *kpar_host, const double *k1_edges_host, int n_k1, int n_mu,
                          int n_t, double f_ng, double p_amp, double p_index, double *sum_dev,
                          int64_t *count_dev, void *stream) {
+  BS_NVTX("bs_bs_monopole");
   using namespace bsi;
   if (!p || !kperp_host || !kpar_host || !k1_edges_host || !sum_dev || !count_dev)
     return fail(p, BS_ERR_ARG, "bs_bs_monopole: NULL argument");
@@ -492,6 +494,7 @@ bs_status bs_bs_monopole(bs_plan p, const double *b3d, const double *kperp_host,
 bs_status bs_bs_cylindrical(bs_plan p, const double *b3d, const double *kpar_host,
                             const double *edges_host, int n, double *sum_dev, int64_t *count_dev,
                             void *stream) {
+  BS_NVTX("bs_bs_cylindrical");
   using namespace bsi;
   if (!p || !b3d || !kpar_host || !edges_host || !sum_dev || !count_dev)
     return fail(p, BS_ERR_ARG, "bs_bs_cylindrical: NULL argument");

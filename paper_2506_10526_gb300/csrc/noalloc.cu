@@ -128,6 +128,7 @@ using namespace bsi;
 extern "C" bs_status bs_counts_noalloc(int nt, int nbins, const double *bin_edges,
                                        const float *ngrid_dev, int64_t *tri_dev,
                                        void *cuda_stream) {
+  BS_NVTX("bs_counts_noalloc");
   if (nt < 8 || nt > kNoallocMaxNt || (nt & 1) || nbins < 1 || nbins > kNoallocMaxBins ||
       !bin_edges || !tri_dev)
     return BS_ERR_ARG;  // sizes beyond the static scratch (nt <= 1024, nbins <= 32)

@@ -72,6 +72,7 @@ cudaError_t time_peak(int iters, cudaStream_t s, double *rate) {
 }  // namespace bsi
 
 extern "C" bs_status bs_measure_peak(int kind, int iters, double *flops_per_s, void *stream) {
+  BS_NVTX("bs_measure_peak");
   using namespace bsi;
   if (!flops_per_s || (kind != 0 && kind != 1) || iters < 1) return BS_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);

@@ -160,8 +160,17 @@ void compute_layout(bs_plan p) {
   L.total = o;
 }
 
+bool inject_fail(const char *point) {
+  const char *env = std::getenv("BS_INJECT_FAIL");
+  if (!env || !*env) return false;
+  const std::string list = std::string(",") + env + ",";
+  return list.find(std::string(",") + point + ",") != std::string::npos;
+}
+
 bs_status ensure_workspace(bs_plan p) {
   if (p->ws) return BS_OK;
+  if (inject_fail("workspace_alloc"))
+    return fail(p, BS_ERR_OOM, "injected failure: workspace allocation (BS_INJECT_FAIL)");
   void *w = nullptr;
   cudaError_t e = cudaMalloc(&w, p->L.total);
   if (e != cudaSuccess) {
@@ -587,8 +596,11 @@ const char *bs_last_error(bs_plan plan) {
 }
 
 bs_status bs_plan_create(const bs_plan_desc *desc, bs_plan *out) {
+  BS_NVTX("bs_plan_create");
   if (!desc || !out) return fail(nullptr, BS_ERR_ARG, "desc and out must not be NULL");
   *out = nullptr;
+  if (inject_fail("plan_create"))
+    return fail(nullptr, BS_ERR_OOM, "injected failure: plan creation (BS_INJECT_FAIL)");
   const bs_plan_desc &d = *desc;
   if (d.nt < 8 || d.nt > 1024 || (d.nt & 1))
     return fail(nullptr, BS_ERR_ARG, "nt must be even and in [8, 1024]");
@@ -837,6 +849,7 @@ bs_status bs_plan_create(const bs_plan_desc *desc, bs_plan *out) {
 }
 
 bs_status bs_plan_destroy(bs_plan p) {
+  BS_NVTX("bs_plan_destroy");
   if (!p) return BS_OK;
   if (p->ws && p->ws_owned) {
     cudaSetDevice(p->device);
@@ -856,6 +869,7 @@ bs_status bs_plan_destroy(bs_plan p) {
 }
 
 bs_status bs_plan_info(bs_plan p, int64_t *info, int n) {
+  BS_NVTX("bs_plan_info");
   if (!p || !info || n < 0) return fail(p, BS_ERR_ARG, "bad arguments");
   int64_t v[7] = {p->M, p->ntrip, p->nf, (int64_t)p->L.total, p->UC, -1,
                   (int64_t)p->levels.size()};
@@ -869,6 +883,7 @@ bs_status bs_plan_info(bs_plan p, int64_t *info, int n) {
 }
 
 bs_status bs_plan_trip_sides(bs_plan p, int64_t *side_host) {
+  BS_NVTX("bs_plan_trip_sides");
   if (!p || !side_host) return fail(p, BS_ERR_ARG, "side_host must not be NULL");
   for (int t = 0; t < p->ntrip; ++t) {
     const int lv = p->lev_of_trip[t];
@@ -878,6 +893,7 @@ bs_status bs_plan_trip_sides(bs_plan p, int64_t *side_host) {
 }
 
 bs_status bs_plan_set_workspace(bs_plan p, void *ws, size_t bytes) {
+  BS_NVTX("bs_plan_set_workspace");
   if (!p) return BS_ERR_ARG;
   if (p->ws) return fail(p, BS_ERR_STATE, "workspace already in place");
   if (!ws || bytes < p->L.total || (reinterpret_cast<uintptr_t>(ws) & 255))
@@ -892,6 +908,7 @@ bs_status bs_plan_set_workspace(bs_plan p, void *ws, size_t bytes) {
 
 bs_status bs_grid_load(bs_plan p, const void *vis, const float *ngrid, const uint8_t *flags,
                        void *stream) {
+  BS_NVTX("bs_grid_load");
   if (!p) return BS_ERR_ARG;
   if (!vis || (reinterpret_cast<uintptr_t>(vis) & 7))
     return fail(p, BS_ERR_ARG, "vis_dev must be a non-NULL 8-byte aligned device pointer");
@@ -940,6 +957,7 @@ bs_status bs_grid_load(bs_plan p, const void *vis, const float *ngrid, const uin
 }
 
 bs_status bs_counts(bs_plan p, int64_t *tri, int64_t *nnu_host) {
+  BS_NVTX("bs_counts");
   if (!p) return BS_ERR_ARG;
   if (p->sticky) return fail(p, BS_ERR_STATE, "plan has a sticky CUDA error: " + p->err);
   if (!p->counts_ready) {
@@ -969,6 +987,8 @@ bs_status bs_counts(bs_plan p, int64_t *tri, int64_t *nnu_host) {
 // demand with cudaMalloc, freed with the plan).
 static bs_status general_scratch(bs_plan p, double **buf, size_t *cap, size_t n) {
   if (*buf && *cap >= n) return BS_OK;
+  if (inject_fail("scratch_alloc"))
+    return fail(p, BS_ERR_OOM, "injected failure: scratch allocation (BS_INJECT_FAIL)");
   if (*buf) cudaFree(*buf);
   *buf = nullptr;
   *cap = 0;
@@ -985,6 +1005,7 @@ static bs_status general_scratch(bs_plan p, double **buf, size_t *cap, size_t n)
 }
 
 bs_status bs_mabs(bs_plan p, const int32_t *block, double *out_full, int accumulate, void *stream) {
+  BS_NVTX("bs_mabs");
   if (!p) return BS_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (!p->loaded) return fail(p, BS_ERR_STATE, "bs_mabs before bs_grid_load");
@@ -1084,6 +1105,7 @@ bs_status bs_mabs(bs_plan p, const int32_t *block, double *out_full, int accumul
 }
 
 bs_status bs_delta_reset(bs_plan p, void *stream) {
+  BS_NVTX("bs_delta_reset");
   if (!p) return BS_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   bs_status st = prepare(p, s);
@@ -1092,6 +1114,7 @@ bs_status bs_delta_reset(bs_plan p, void *stream) {
 }
 
 bs_status bs_delta_export(bs_plan p, double *sums_dev, int64_t *nnu_host, void *stream) {
+  BS_NVTX("bs_delta_export");
   if (!p || (!sums_dev && !nnu_host)) return fail(p, BS_ERR_ARG, "bs_delta_export: nothing to export");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (!p->loaded) return fail(p, BS_ERR_STATE, "bs_delta_export before bs_grid_load");
@@ -1111,6 +1134,7 @@ bs_status bs_delta_export(bs_plan p, double *sums_dev, int64_t *nnu_host, void *
 
 bs_status bs_delta_import(bs_plan p, const double *sums_dev, const int64_t *nnu_host, int add,
                           void *stream) {
+  BS_NVTX("bs_delta_import");
   if (!p || !sums_dev || !nnu_host || (add != 0 && add != 1))
     return fail(p, BS_ERR_ARG, "bs_delta_import: sums_dev and nnu_host are required, add is 0 or 1");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1190,6 +1214,7 @@ static bs_status bs3d_out(bs_plan p, double *out, bool closable, cudaStream_t s)
 }
 
 bs_status bs_mabs_delta(bs_plan p, double *out, void *stream) {
+  BS_NVTX("bs_mabs_delta");
   if (!p || !out) return fail(p, BS_ERR_ARG, "out_dev must not be NULL");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (!p->loaded) return fail(p, BS_ERR_STATE, "bs_mabs_delta before bs_grid_load");
@@ -1203,6 +1228,7 @@ bs_status bs_mabs_delta(bs_plan p, double *out, void *stream) {
 }
 
 bs_status bs_mabs_delta_closable(bs_plan p, double *out, void *stream) {
+  BS_NVTX("bs_mabs_delta_closable");
   if (!p || !out) return fail(p, BS_ERR_ARG, "out_dev must not be NULL");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (!p->loaded) return fail(p, BS_ERR_STATE, "bs_mabs_delta_closable before bs_grid_load");
@@ -1216,6 +1242,7 @@ bs_status bs_mabs_delta_closable(bs_plan p, double *out, void *stream) {
 }
 
 bs_status bs_bs3d(bs_plan p, double *out, void *stream) {
+  BS_NVTX("bs_bs3d");
   if (!p || !out) return fail(p, BS_ERR_ARG, "out_dev must not be NULL");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (!p->loaded) return fail(p, BS_ERR_STATE, "bs_bs3d before bs_grid_load");
@@ -1229,6 +1256,7 @@ bs_status bs_bs3d(bs_plan p, double *out, void *stream) {
 }
 
 bs_status bs_bs3d_closable(bs_plan p, double *out, void *stream) {
+  BS_NVTX("bs_bs3d_closable");
   if (!p || !out) return fail(p, BS_ERR_ARG, "out_dev must not be NULL");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (!p->loaded) return fail(p, BS_ERR_STATE, "bs_bs3d_closable before bs_grid_load");
@@ -1242,6 +1270,7 @@ bs_status bs_bs3d_closable(bs_plan p, double *out, void *stream) {
 }
 
 bs_status bs_check_hermitian(bs_plan p, const void *vis, double tol, void *stream) {
+  BS_NVTX("bs_check_hermitian");
   if (!p || !vis) return fail(p, BS_ERR_ARG, "vis_dev must not be NULL");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   bs_status st = prepare(p, s);

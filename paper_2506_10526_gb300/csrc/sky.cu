@@ -261,6 +261,7 @@ const char *bs_sky_last_error(bs_sky s) { return s ? s->err.c_str() : bsi::g_sky
 
 bs_status bs_sky_create(int nt, int nchan, double slope, double sigma, double f_ng, int max_batch,
                         bs_sky *out) {
+  BS_NVTX("bs_sky_create");
   if (!out) return sky_fail(nullptr, BS_ERR_ARG, "out is NULL");
   *out = nullptr;
   if (nt < 8 || nt > 4096 || nt % 2) return sky_fail(nullptr, BS_ERR_ARG, "nt must be even, 8..4096");
@@ -321,7 +322,7 @@ bs_status bs_sky_create(int nt, int nchan, double slope, double sigma, double f_
   const double scale = sum > 0 ? sigma * sigma * (double)s->N / sum : 0.0;
   for (long long c = 0; c < s->N; ++c) sp[c] = (float)(std::sqrt(P[c] * scale) / (double)s->N);
   const long long npair = (max_batch + 1) / 2;
-  if (cudaMalloc(&s->sqrtp, s->N * sizeof(float)) != cudaSuccess ||
+  if (inject_fail("sky_alloc") || cudaMalloc(&s->sqrtp, s->N * sizeof(float)) != cudaSuccess ||
       cudaMalloc(&s->work, npair * s->N * sizeof(float2)) != cudaSuccess ||
       cudaMalloc(&s->twT, nt * sizeof(float2)) != cudaSuccess ||
       cudaMalloc(&s->twC, nchan * sizeof(float2)) != cudaSuccess) {
@@ -342,6 +343,7 @@ bs_status bs_sky_create(int nt, int nchan, double slope, double sigma, double f_
 }
 
 bs_status bs_sky_destroy(bs_sky s) {
+  BS_NVTX("bs_sky_destroy");
   if (!s) return BS_OK;
   cudaFree(s->sqrtp);
   cudaFree(s->work);
@@ -353,6 +355,7 @@ bs_status bs_sky_destroy(bs_sky s) {
 
 bs_status bs_sky_generate(bs_sky s, uint64_t seed, uint64_t realisation0, int batch, void *vis_dev,
                           void *cuda_stream) {
+  BS_NVTX("bs_sky_generate");
   if (!s) return BS_ERR_ARG;
   if (s->broken) return sky_fail(s, BS_ERR_STATE, "generator is in an error state: " + s->err);
   if (batch < 1 || batch > s->max_batch) return sky_fail(s, BS_ERR_ARG, "batch must be 1..max_batch");

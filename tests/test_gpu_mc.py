@@ -168,3 +168,65 @@ def test_mc_declared_block_subset_and_tile_order():
     assert np.abs(mean[ok] - want[ok]).max() <= 1e-3 * np.abs(want[ok]).max()
     np.testing.assert_allclose(means[1][0][ok], mean[ok], rtol=1e-9,
                                atol=1e-12 * np.abs(mean[ok]).max())
+
+
+def test_mc_checkpoint_and_resume(tmp_path):
+    """A run interrupted after three Monte Carlo steps and resumed from its
+    checkpoint in a new ensemble (skies drawn on the GPU, the generator's
+    realisation counter carried in the checkpoint) ends with the statistics of
+    an uninterrupted five-step run."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2506_10526_gb300 as bs
+    groups = [dict(g, precision=1) for g in GROUPS]
+
+    def make():
+        ens = bs.Ensemble(groups)
+        gens = [bs.SkyGenerator(g["nt"], g["nchan"], max_batch=g["batch"]) for g in groups]
+        bufs = [torch.empty((g["batch"], g["nchan"], g["nt"], g["nt"]), dtype=torch.complex64,
+                            device="cuda") for g in groups]
+        for k, b in enumerate(bufs):
+            ens.set_input(k, b)
+        return ens, gens, bufs
+
+    def step(ens, gens, bufs, counter):
+        for k, g in enumerate(groups):
+            gens[k].generate(123, counter * g["batch"], out=bufs[k])
+        ens.run(use_graph=True)
+        return counter + 1
+
+    ens, gens, bufs = make()
+    c = 0
+    for _ in range(5):
+        c = step(ens, gens, bufs, c)
+    want = [(ens.stats(g, 0), ens.stats(g, 1)) for g in range(len(groups))]
+    ens.close()
+    ens, gens, bufs = make()
+    c = 0
+    for _ in range(3):
+        c = step(ens, gens, bufs, c)
+    path = tmp_path / "mc.ckpt"
+    ens.checkpoint(path, counter=c)
+    ens.close()
+    ens, gens2, bufs = make()
+    c = ens.restore(path)
+    assert c == 3
+    for _ in range(2):
+        c = step(ens, gens2, bufs, c)
+    got = [(ens.stats(g, 0), ens.stats(g, 1)) for g in range(len(groups))]
+    ens.close()
+    for (w0, w1), (g0, g1) in zip(want, got):
+        for (mw, vw, nw), (mg, vg, ng) in ((w0, g0), (w1, g1)):
+            assert nw == ng == 5 * (nw // 5)
+            ok = ~np.isnan(mw)
+            assert np.array_equal(ok, ~np.isnan(mg))
+            scale = np.abs(mw[ok]).max()
+            assert np.abs(mg[ok] - mw[ok]).max() <= 1e-9 * scale
+            okv = ~np.isnan(vw)
+            assert np.abs(vg[okv] - vw[okv]).max() <= 1e-8 * np.abs(vw[okv]).max()
+    # a checkpoint of other shapes is refused
+    other = bs.Ensemble([dict(GROUPS[0], precision=1)])
+    with pytest.raises(bs.BsError):
+        other.restore(path)
+    other.close()
