@@ -144,12 +144,77 @@ __device__ __forceinline__ void stockham_stage(const float2 *__restrict__ x, flo
   }
 }
 
-// In-place (ping-pong) transform of nrows rows of length N, row r at x + r ld
-// (ld >= N; ld = N + 1 keeps column-wise accesses of power-of-two rows off a
-// single bank); y is scratch of the same size.  All threads of the block must
-// call it.  Returns the buffer that holds the result.
-__device__ __forceinline__ float2 *stockham(float2 *x, float2 *y, int nrows, int N, int ld,
-                                            const Radices &rad, const float2 *tw, float sign) {
+// Compile-time stage sequence of a length N (the same radices, in the same
+// order, as factor_radices: 8s, then 4s, 2s, 3s, 5s).  With N, R and p known at
+// compile time the row / butterfly / twiddle index arithmetic of a stage
+// reduces to constant multiplies and shifts, and the stages unroll.
+__host__ __device__ constexpr int ct_radix(int N, int s) {
+  int m = N, k = 0;
+  const int rs[5] = {8, 4, 2, 3, 5};
+  for (int t = 0; t < 5; ++t)
+    while (m % rs[t] == 0) {
+      if (k == s) return rs[t];
+      m /= rs[t];
+      ++k;
+    }
+  return 0;
+}
+__host__ __device__ constexpr int ct_nstages(int N) {
+  int s = 0;
+  while (ct_radix(N, s)) ++s;
+  return s;
+}
+
+template <int N, int R, int P>
+__device__ __forceinline__ void stockham_stage_ct(const float2 *__restrict__ x,
+                                                  float2 *__restrict__ y, int nrows, int ld,
+                                                  const float2 *tw, float sign) {
+  constexpr int NR = N / R;
+  constexpr int tstride = N / (P * R);
+  const int total = nrows * NR;
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int row = idx / NR;
+    const int i = idx - row * NR;
+    const float2 *xr = x + row * ld;
+    float2 *yr = y + row * ld;
+    const int k = i % P;
+    float2 u[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) u[q] = xr[i + q * NR];
+    if constexpr (P > 1) {
+      if (k != 0) {
+        const int kt = k * tstride;
+#pragma unroll
+        for (int q = 1; q < R; ++q) {
+          float2 w = tw[q * kt];
+          w.y *= sign;
+          u[q] = cmul(u[q], w);
+        }
+      }
+    }
+    butterfly<R>(u, sign);
+    const int j = (i - k) * R + k;
+#pragma unroll
+    for (int q = 0; q < R; ++q) yr[j + q * P] = u[q];
+  }
+}
+
+template <int N, int S, int P>
+__device__ __forceinline__ float2 *stockham_ct(float2 *x, float2 *y, int nrows, int ld,
+                                               const float2 *tw, float sign) {
+  if constexpr (S < ct_nstages(N)) {
+    constexpr int R = ct_radix(N, S);
+    stockham_stage_ct<N, R, P>(x, y, nrows, ld, tw, sign);
+    __syncthreads();
+    return stockham_ct<N, S + 1, P * R>(y, x, nrows, ld, tw, sign);
+  } else {
+    return x;
+  }
+}
+
+// Runtime stage loop for the lengths without a compiled sequence.
+__device__ __forceinline__ float2 *stockham_rt(float2 *x, float2 *y, int nrows, int N, int ld,
+                                               const Radices &rad, const float2 *tw, float sign) {
   int p = 1;
   for (int s = 0; s < rad.n; ++s) {
     const int R = rad.r[s];
@@ -167,6 +232,31 @@ __device__ __forceinline__ float2 *stockham(float2 *x, float2 *y, int nrows, int
     p *= R;
   }
   return x;
+}
+
+// In-place (ping-pong) transform of nrows rows of length N, row r at x + r ld
+// (ld >= N; ld = N + 1 keeps column-wise accesses of power-of-two rows off a
+// single bank); y is scratch of the same size.  All threads of the block must
+// call it.  Returns the buffer that holds the result.  The image sides of
+// per-triple planes (2^a x {8, 12}) and the usual channel counts take the
+// compiled stage sequences.
+__device__ __forceinline__ float2 *stockham(float2 *x, float2 *y, int nrows, int N, int ld,
+                                            const Radices &rad, const float2 *tw, float sign) {
+  switch (N) {
+    case 16: return stockham_ct<16, 0, 1>(x, y, nrows, ld, tw, sign);
+    case 24: return stockham_ct<24, 0, 1>(x, y, nrows, ld, tw, sign);
+    case 32: return stockham_ct<32, 0, 1>(x, y, nrows, ld, tw, sign);
+    case 48: return stockham_ct<48, 0, 1>(x, y, nrows, ld, tw, sign);
+    case 64: return stockham_ct<64, 0, 1>(x, y, nrows, ld, tw, sign);
+    case 96: return stockham_ct<96, 0, 1>(x, y, nrows, ld, tw, sign);
+    case 128: return stockham_ct<128, 0, 1>(x, y, nrows, ld, tw, sign);
+    case 192: return stockham_ct<192, 0, 1>(x, y, nrows, ld, tw, sign);
+    case 256: return stockham_ct<256, 0, 1>(x, y, nrows, ld, tw, sign);
+    case 384: return stockham_ct<384, 0, 1>(x, y, nrows, ld, tw, sign);
+    case 512: return stockham_ct<512, 0, 1>(x, y, nrows, ld, tw, sign);
+    case 768: return stockham_ct<768, 0, 1>(x, y, nrows, ld, tw, sign);
+    default: return stockham_rt(x, y, nrows, N, ld, rad, tw, sign);
+  }
 }
 __device__ __forceinline__ float2 *stockham(float2 *x, float2 *y, int nrows, int N,
                                             const Radices &rad, const float2 *tw, float sign) {
