@@ -382,6 +382,32 @@ bs_status bs_bs_monopole(bs_plan plan, const double *b3d_dev, const double *kper
                          int n_mu, int n_t, double f_ng, double p_amp, double p_index,
                          double *sum_dev, int64_t *count_dev, void *cuda_stream);
 
+/* Multipole moments with m = 0 of the 3D bispectrum, binned like
+ * bs_bs_monopole (Section 2, Eq. bs_lm with the line-of-sight direction p of
+ * Eq. orient): in the triangle frame p_z = mu_1 = k_par(side 1) / k1, the
+ * largest side's line-of-sight cosine, and the discrete form of Eq. (bs_lm)
+ * (4 pi times the mean over a bin's samples) is
+ *   B_l^0(k1, mu, t) = sqrt(4 pi (2l+1)) < Y_l^0 B > = (2l+1) < P_l(mu_1) B >.
+ * m != 0 needs the azimuth of p about k1, which the triangle's handedness in
+ * the sky plane fixes; side lengths from ring centres do not (and it is
+ * undefined for collinear triangles).  Samples: as bs_bs_monopole but without
+ * the delay row and column a, b = -nc/2 of an even nchan (their point
+ * reflections lie off the grid), so that every sample's reflection
+ * (a, b) -> (-a, -b) is present: mu_1 changes sign and the bin does not, and
+ * the odd multipoles of a point-symmetric 3D bispectrum vanish identically.
+ * mu_1 and P_l (Bonnet's recursion) are FP64; the bin is the monopole's.
+ *  lmax       0..4
+ *  sum_dev    double [batch][lmax + 1][n_k1][n_mu][n_t]: sums of
+ *             (2l+1) P_l(mu_1) B over each bin's samples (overwritten)
+ *  count_dev  int64 [n_k1][n_mu][n_t]: samples per bin (overwritten);
+ *             B_l^0 = sum / count
+ * Other arguments as bs_bs_monopole (b3d_dev required).
+ * Errors: as bs_bs_monopole; BS_ERR_ARG for lmax out of range. */
+bs_status bs_bs_multipoles(bs_plan plan, const double *b3d_dev, const double *kperp_host,
+                           const double *kpar_host, const double *k1_edges_host, int n_k1,
+                           int n_mu, int n_t, int lmax, double *sum_dev, int64_t *count_dev,
+                           void *cuda_stream);
+
 /* The 3D bispectrum of every closable ring triple binned on an n x n grid in
  * the (k_par1, k_par2) plane (Section 5: the binning behind Fig. cylbs).
  *  b3d_dev     double [batch][n_c][nchan][nchan] as bs_bs3d_closable writes it

@@ -43,6 +43,18 @@ Readings (the paper leaves them open):
   q: e_q <= k1 < e_{q+1}; mu bin q: 0.5 + q / (2 n_mu) <= mu, the value 1
   in the last bin; t alike.  Values, sums and the model of Eq. (bsana) are
   FP64.
+* Multipoles (Eq. bs_lm) with m = 0: the line of sight has p_z = mu_1 =
+  k_par(side 1) / k1 in the triangle frame (Eq. orient), and the discrete
+  form of Eq. (bs_lm) -- the integral over orientations taken as 4 pi times
+  the mean over a bin's samples -- gives
+  B_l^0 = sqrt(4 pi (2l+1)) <Y_l^0 B> = (2l+1) <P_l(mu_1) B>.  The azimuth
+  that m != 0 needs depends on the triangle's handedness in the sky plane,
+  which side lengths from ring means cannot fix (and is undefined for the
+  collinear triangles).  Multipole samples leave out the delay row and
+  column a, b = -nc/2 of an even nc, whose point reflections lie outside the
+  grid, so the sample set is closed under (a, b) -> (-a, -b): mu_1 changes
+  sign and the bin does not, and odd l vanish for a point-symmetric 3D
+  bispectrum.
 * ``bin_candidates`` lists, for each sample, every bin (or the drop, -1)
   reachable by moving k1 by a relative ``rel_k`` and mu, t by ``rel_s``
   about their FP64 values.  A kernel that decides bins in lower precision
@@ -157,6 +169,120 @@ def bs_monopole(b3d, trips, kperp, kpar, k1_edges, n_mu: int, n_t: int, model=No
                 v = bsana(S1, S2, S3, *model).ravel()
             sums[b] += np.bincount(q[sel], weights=v[sel], minlength=nbin)
     return sums.reshape(batch, n_k1, n_mu, n_t), cnt.reshape(n_k1, n_mu, n_t)
+
+
+def legendre(lmax: int, x):
+    """P_0(x) .. P_lmax(x) by Bonnet's recursion (l+1) P_{l+1} = (2l+1) x P_l - l P_{l-1}."""
+    x = np.asarray(x, np.float64)
+    P = [np.ones_like(x), x.copy()]
+    for l in range(1, lmax):
+        P.append(((2 * l + 1) * x * P[l] - l * P[l - 1]) / (l + 1))
+    return np.stack(P[:lmax + 1])
+
+
+def _mu1(S1, S2, S3, kpar_a, kpar_b):
+    """mu_1 = k_par / k of the largest side (ties: the first of the sides
+    in the order 1, 2, 3, as a stable sort gives)."""
+    kc = -(kpar_a + kpar_b)
+    S = np.stack(np.broadcast_arrays(S1, S2, S3))
+    Z = np.stack(np.broadcast_arrays(kpar_a, kpar_b, kc))
+    k = np.argmax(S, axis=0)  # first maximum
+    s1 = np.take_along_axis(S, k[None], axis=0)[0]
+    z1 = np.take_along_axis(Z, k[None], axis=0)[0]
+    return z1 / np.sqrt(s1)
+
+
+def paired_mask(nc: int) -> np.ndarray:
+    """Delay indices whose point reflection is on the grid (all but a = -nc/2
+    of an even nc)."""
+    m = np.ones(nc, bool)
+    if nc % 2 == 0:
+        m[0] = False
+    return m
+
+
+def bs_multipoles(b3d, trips, kperp, kpar, k1_edges, n_mu: int, n_t: int, lmax: int):
+    """Binned m = 0 multipoles: sums [batch][lmax+1][n_k1][n_mu][n_t] of
+    (2l+1) P_l(mu_1) B over the paired samples of each bin, and their counts
+    [n_k1][n_mu][n_t]; B_l^0 = sums / counts (FP64 throughout)."""
+    kpar = np.asarray(kpar, np.float64)
+    kp = np.asarray(kperp, np.float64)
+    nc = kpar.size
+    n_k1 = len(k1_edges) - 1
+    nbin = n_k1 * n_mu * n_t
+    batch = b3d.shape[0]
+    sums = np.zeros((batch, lmax + 1, nbin))
+    cnt = np.zeros(nbin, np.int64)
+    pm = paired_mask(nc)
+    keep = (pm[:, None] & pm[None, :]).ravel()
+    ka = np.broadcast_to(kpar[:, None], (nc, nc))
+    kb = np.broadcast_to(kpar[None, :], (nc, nc))
+    wl = (2 * np.arange(lmax + 1) + 1)[:, None]
+    for p, (i, j, l) in enumerate(trips):
+        S1, S2, S3 = _plane_squares(kp, kpar, i, j, l)
+        k1, mu, t = triangle_shape(S1, S2, S3)
+        q = _bins(k1, mu, t, k1_edges, n_mu, n_t).ravel()
+        sel = (q >= 0) & keep
+        W = wl * legendre(lmax, _mu1(S1, S2, S3, ka, kb).ravel())  # [lmax+1][nc*nc]
+        cnt += np.bincount(q[sel], minlength=nbin)
+        for b in range(batch):
+            v = np.asarray(b3d[b, p], np.float64).ravel()
+            for ll in range(lmax + 1):
+                sums[b, ll] += np.bincount(q[sel], weights=(W[ll] * v)[sel], minlength=nbin)
+    return sums.reshape(batch, lmax + 1, n_k1, n_mu, n_t), cnt.reshape(n_k1, n_mu, n_t)
+
+
+def multipole_interval(b3d, trips, kperp, kpar, k1_edges, n_mu: int, n_t: int, lmax: int,
+                       rel_k: float, rel_s: float):
+    """As ``monopole_interval`` for the multipole sums: per bin the counts of
+    the sure and reachable samples, the sums over the sure samples, and the
+    sums of |(2l+1) P_l(mu_1) B| over the ambiguous samples that can reach
+    the bin (paired samples only)."""
+    kpar = np.asarray(kpar, np.float64)
+    kp = np.asarray(kperp, np.float64)
+    nc = kpar.size
+    n_k1 = len(k1_edges) - 1
+    nbin = n_k1 * n_mu * n_t
+    batch = b3d.shape[0]
+    c_lo = np.zeros(nbin, np.int64)
+    c_hi = np.zeros(nbin, np.int64)
+    s_sure = np.zeros((batch, lmax + 1, nbin))
+    s_amb = np.zeros((batch, lmax + 1, nbin))
+    pm = paired_mask(nc)
+    keep = (pm[:, None] & pm[None, :]).ravel()
+    ka = np.broadcast_to(kpar[:, None], (nc, nc))
+    kb = np.broadcast_to(kpar[None, :], (nc, nc))
+    wl = (2 * np.arange(lmax + 1) + 1)[:, None]
+    n_amb = 0
+    n_all = 0
+    for p, (i, j, l) in enumerate(trips):
+        S1, S2, S3 = _plane_squares(kp, kpar, i, j, l)
+        k1, mu, t = triangle_shape(S1, S2, S3)
+        q, amb, cand = bin_candidates(k1, mu, t, k1_edges, n_mu, n_t, rel_k, rel_s)
+        n_all += int(keep.sum())
+        W = wl * legendre(lmax, _mu1(S1, S2, S3, ka, kb).ravel())
+        amb_k = amb & keep
+        n_amb += int(amb_k.sum())
+        sure = (q >= 0) & ~amb & keep
+        c_lo += np.bincount(q[sure], minlength=nbin)
+        ai = np.flatnonzero(amb)            # columns of cand
+        kc = keep[ai]
+        idx = np.broadcast_to(np.arange(cand.shape[1])[None, :], cand.shape)
+        ok = (cand >= 0) & kc[None, :]
+        pairs = np.unique(np.stack([idx[ok], cand[ok]]), axis=1)
+        c_hi += np.bincount(pairs[1], minlength=nbin)
+        for b in range(batch):
+            v = np.asarray(b3d[b, p], np.float64).ravel()
+            for ll in range(lmax + 1):
+                wv = W[ll] * v
+                s_sure[b, ll] += np.bincount(q[sure], weights=wv[sure], minlength=nbin)
+                s_amb[b, ll] += np.bincount(pairs[1], weights=np.abs(wv[ai])[pairs[0]],
+                                            minlength=nbin)
+    c_hi += c_lo
+    shape = (n_k1, n_mu, n_t)
+    return {"c_lo": c_lo.reshape(shape), "c_hi": c_hi.reshape(shape),
+            "s_sure": s_sure.reshape((batch, lmax + 1) + shape),
+            "s_amb": s_amb.reshape((batch, lmax + 1) + shape), "n_amb": n_amb, "n": n_all}
 
 
 def bin_candidates(k1, mu, t, k1_edges, n_mu: int, n_t: int, rel_k: float, rel_s: float):

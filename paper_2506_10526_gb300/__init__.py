@@ -35,7 +35,7 @@ EXPORTS = ("bs_abi_version", "bs_plan_create", "bs_plan_destroy", "bs_last_error
            "bs_plan_info", "bs_plan_trip_sides", "bs_plan_set_workspace", "bs_grid_load", "bs_counts", "bs_mabs",
            "bs_delta_reset", "bs_mabs_delta", "bs_bs3d", "bs_mabs_delta_closable",
            "bs_bs3d_closable", "bs_mabs_error_bound", "bs_delta_export", "bs_delta_import", "bs_grid_visibilities", "bs_plan_ring_umean", "bs_bs_monopole",
-           "bs_bs_cylindrical", "bs_check_hermitian",
+           "bs_bs_cylindrical", "bs_bs_multipoles", "bs_check_hermitian",
            "bs_mc_create", "bs_mc_destroy", "bs_mc_last_error", "bs_mc_info", "bs_mc_set_input",
            "bs_mc_set_flags", "bs_mc_set_tuning", "bs_mc_autotune", "bs_mc_run", "bs_mc_reset",
            "bs_mc_stats", "bs_mc_tuning", "bs_mc_set_block", "bs_mc_checkpoint",
@@ -95,6 +95,10 @@ def lib() -> ctypes.CDLL:
             L.bs_delta_import.argtypes = [P, P, P, I, P]
             L.bs_counts_noalloc.argtypes = [I, I, P, P, P, P]
             L.bs_measure_peak.argtypes = [I, I, P, P]
+            L.bs_plan_ring_umean.argtypes = [P, P]
+            L.bs_bs_monopole.argtypes = [P, P, P, P, P, I, I, I, D, D, D, P, P, P]
+            L.bs_bs_multipoles.argtypes = [P, P, P, P, P, I, I, I, I, P, P, P]
+            L.bs_bs_cylindrical.argtypes = [P, P, P, P, I, P, P, P]
             L.bs_sky_create.argtypes = [I, I, D, D, D, I, ctypes.POINTER(P)]
             L.bs_sky_destroy.argtypes = [P]
             L.bs_sky_last_error.argtypes = [P]
@@ -340,6 +344,30 @@ class Plan:
             self._h, _dptr(b3d), kp.ctypes.data_as(ctypes.c_void_p),
             kz.ctypes.data_as(ctypes.c_void_p), ed.ctypes.data_as(ctypes.c_void_p), n_k1, n_mu, n_t,
             ctypes.c_double(f), ctypes.c_double(a), ctypes.c_double(pi), _dptr(sums), _dptr(cnt),
+            _stream_ptr(stream)))
+        return sums, cnt
+
+    def bs_multipoles(self, b3d, kperp, kpar, k1_edges, n_mu=5, n_t=5, lmax=4, stream=None):
+        """bs_bs_multipoles: m = 0 multipoles binned like bs_monopole.  Returns
+        (sums [batch, lmax + 1, n_k1, n_mu, n_t] float64 CUDA, counts [n_k1, n_mu, n_t]
+        int64 CUDA); B_l^0 = sums / counts."""
+        import numpy as np
+        import torch
+        kp = np.ascontiguousarray(np.asarray(kperp, np.float64))
+        kz = np.ascontiguousarray(np.asarray(kpar, np.float64))
+        ed = np.ascontiguousarray(np.asarray(k1_edges, np.float64))
+        if kp.size != self.nbins or kz.size != self.nchan:
+            raise ValueError("kperp needs nbins entries and kpar nchan entries")
+        if b3d.dtype != torch.float64 or b3d.numel() != self.batch * self.n_closable * self.nchan ** 2:
+            raise ValueError("b3d must be float64 [batch, n_closable, nchan, nchan]")
+        n_k1 = ed.size - 1
+        sums = torch.empty((self.batch, lmax + 1, n_k1, n_mu, n_t), dtype=torch.float64,
+                           device="cuda")
+        cnt = torch.empty((n_k1, n_mu, n_t), dtype=torch.int64, device="cuda")
+        P = ctypes.c_void_p
+        self._check(self._L.bs_bs_multipoles(
+            self._h, _dptr(b3d), kp.ctypes.data_as(P), kz.ctypes.data_as(P), ed.ctypes.data_as(P),
+            int(n_k1), int(n_mu), int(n_t), int(lmax), _dptr(sums), _dptr(cnt),
             _stream_ptr(stream)))
         return sums, cnt
 

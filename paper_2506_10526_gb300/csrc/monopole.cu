@@ -244,6 +244,135 @@ __global__ void __launch_bounds__(kThreads) k_mono_sum(const MonoArgs a,
   }
 }
 
+// m = 0 multipoles (Eq. bs_lm): per bin the sums of (2l+1) P_l(mu_1) B over the
+// paired samples, l = 0..LMAX, with mu_1 = k_par / k of the largest side (the
+// first of sides 1, 2, 3 on ties) and P_l by Bonnet's recursion, in FP64 with
+// the same operation order as the oracle.  Bins come from the plan's table.
+// Layout as k_mono_sum: warps walk 32 consecutive samples; lane-private
+// running sums while the warp's bin is unchanged.
+constexpr int kMaxL = 4;
+
+template <int NB, int LMAX>
+__global__ void __launch_bounds__(kThreads) k_mono_multipole(const MonoArgs a,
+                                                             const int16_t *__restrict__ bins,
+                                                             int skip0) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double *hs = reinterpret_cast<double *>(smem_raw);  // [nbatch][LMAX + 1][nbin]
+  unsigned *hc = reinterpret_cast<unsigned *>(hs + (size_t)a.nbatch * (LMAX + 1) * a.nbin);
+  const int p = blockIdx.y;
+  for (int q = threadIdx.x; q < a.nbatch * (LMAX + 1) * a.nbin; q += blockDim.x) hs[q] = 0.0;
+  for (int q = threadIdx.x; q < a.nbin; q += blockDim.x) hc[q] = 0u;
+  __syncthreads();
+  const int i = a.rings[3 * p], j = a.rings[3 * p + 1], l = a.rings[3 * p + 2];
+  const double pi2 = __dmul_rn(a.kperp64[i], a.kperp64[i]),
+               pj2 = __dmul_rn(a.kperp64[j], a.kperp64[j]),
+               pl2 = __dmul_rn(a.kperp64[l], a.kperp64[l]);
+  const int n = a.nc * a.nc;
+  const int c0 = blockIdx.x * a.chunk, c1 = min(n, c0 + a.chunk);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = kThreads / 32;
+  const int per = ((c1 - c0 + nw - 1) / nw + 31) / 32 * 32;
+  const int w0 = min(c1, c0 + warp * per), w1 = min(c1, w0 + per);
+  const int16_t *bp = bins + (long long)p * n;
+  const double *vb = a.b3d + (long long)a.b0 * a.bstride + (long long)p * n;
+  int cur = -1;
+  unsigned cnt = 0;
+  double run[NB][LMAX + 1];
+#pragma unroll
+  for (int b = 0; b < NB; ++b)
+#pragma unroll
+    for (int q = 0; q <= LMAX; ++q) run[b][q] = 0.0;
+  auto flush = [&]() {
+    if (cur >= 0) {
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        if (b >= a.nbatch) break;
+#pragma unroll
+        for (int q = 0; q <= LMAX; ++q) {
+          double x = run[b][q];
+          for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+          if (lane == 0) atomicAdd(hs + ((size_t)b * (LMAX + 1) + q) * a.nbin + cur, x);
+        }
+      }
+      if (lane == 0) atomicAdd(hc + cur, cnt);
+    }
+    cnt = 0;
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+#pragma unroll
+      for (int q = 0; q <= LMAX; ++q) run[b][q] = 0.0;
+  };
+  for (int g0 = w0; g0 < w1; g0 += 32) {
+    const int e = g0 + lane;
+    int q = -1;
+    double wl[LMAX + 1];
+    if (e < w1) {
+      const int ia = e / a.nc, ib = e - ia * a.nc;
+      q = (skip0 && (ia == 0 || ib == 0)) ? -1 : (int)bp[e];
+      if (q >= 0) {
+        const double za = a.kpar64[ia], zb = a.kpar64[ib], zc = -__dadd_rn(za, zb);
+        const double s1 = __dadd_rn(pi2, __dmul_rn(za, za)), s2 = __dadd_rn(pj2, __dmul_rn(zb, zb)),
+                     s3 = __dadd_rn(pl2, __dmul_rn(zc, zc));
+        double sm = s1, zm = za;
+        if (s2 > sm) { sm = s2; zm = zb; }
+        if (s3 > sm) { sm = s3; zm = zc; }
+        const double x = zm / sqrt(sm);
+        double pm1 = 1.0, p0 = x;
+        wl[0] = 1.0;
+        if (LMAX >= 1) wl[1] = 3.0 * x;
+#pragma unroll
+        for (int ll = 1; ll < LMAX; ++ll) {
+          const double pn = ((2 * ll + 1) * x * p0 - ll * pm1) / (ll + 1);
+          pm1 = p0;
+          p0 = pn;
+          wl[ll + 1] = (2 * ll + 3) * pn;
+        }
+      }
+    }
+    double v[NB];
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+      v[b] = (b < a.nbatch && e < w1) ? __ldg(vb + (long long)b * a.bstride + e) : 0.0;
+    const int qq = __shfl_sync(0xffffffffu, q, 0);
+    if (__all_sync(0xffffffffu, q == qq)) {
+      if (qq != cur) {
+        flush();
+        cur = qq;
+      }
+      if (cur >= 0) {
+        cnt += 32;
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+#pragma unroll
+          for (int ll = 0; ll <= LMAX; ++ll)
+            if (b < a.nbatch) run[b][ll] += wl[ll] * v[b];
+      }
+    } else {
+      flush();
+      cur = -1;
+      if (q >= 0) {
+        atomicAdd(hc + q, 1u);
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+#pragma unroll
+          for (int ll = 0; ll <= LMAX; ++ll)
+            if (b < a.nbatch)
+              atomicAdd(hs + ((size_t)b * (LMAX + 1) + ll) * a.nbin + q, wl[ll] * v[b]);
+      }
+    }
+  }
+  flush();
+  __syncthreads();
+  for (int q = threadIdx.x; q < a.nbin; q += blockDim.x) {
+    const unsigned c = hc[q];
+    if (!c) continue;
+    if (a.cnt) atomicAdd(a.cnt + q, (unsigned long long)c);
+    for (int b = 0; b < a.nbatch; ++b)
+      for (int ll = 0; ll <= LMAX; ++ll)
+        atomicAdd(a.sums + ((size_t)(a.b0 + b) * (LMAX + 1) + ll) * a.nbin + q,
+                  hs[((size_t)b * (LMAX + 1) + ll) * a.nbin + q]);
+  }
+}
+
 // The 3D bispectrum of each plane binned on an n x n grid in the (k_par1,
 // k_par2) plane (Section 5, the binning behind Fig. cylbs).  k_par grows with
 // the delay index, so the bins of rows (and of columns) are contiguous index
@@ -343,6 +472,91 @@ static size_t mono_smem(int nbin, int nbatch) {
     if (e__ != cudaSuccess) return cuda_fail(p, e__, #call);     \
   } while (0)
 
+// Geometry of the (k1, mu, t) binning shared by the monopole and the
+// multipoles: FP64 and FP32 k tables and the squared thresholds uploaded to
+// the plan, the argument fields that describe them, and the plan's cached bin
+// table (rebuilt when the geometry changed).
+static bs_status mono_geometry(bs_plan p, const double *kperp_host, const double *kpar_host,
+                               const double *k1_edges_host, int n_k1, int n_mu, int n_t,
+                               cudaStream_t s, MonoArgs &a) {
+  const int npl = (int)p->clos.size();
+  // constants: FP64 kperp [nb], kpar [nc]; FP32 kperp, kpar (rounded to nearest);
+  // squared thresholds E_q = e_q^2 [n_k1 + 1], cmu_q = 4 m_q^2 [n_mu + 1],
+  // ct_q = tau_q^2 [n_t + 1], with the acceptance limits at both ends of the
+  // shape tables (a pageable source is staged before the copy call returns)
+  const int nb = p->nb, nc = p->nc, nthr = n_k1 + n_mu + n_t + 3;
+  std::vector<unsigned char> &tab = p->mono_tab;
+  const size_t off32 = (size_t)(nb + nc) * 8;
+  tab.assign(off32 + (size_t)(nb + nc + nthr) * 4, 0);
+  std::vector<float> f32((size_t)nb + nc + nthr);
+  for (int m = 0; m < nb; ++m) f32[m] = (float)kperp_host[m];
+  for (int c = 0; c < nc; ++c) f32[nb + c] = (float)kpar_host[c];
+  float *thr = f32.data() + nb + nc;
+  const double lo = 0.5 - kShapeTol, hi = 1.0 + kShapeTol;
+  for (int q = 0; q <= n_k1; ++q) thr[q] = (float)(k1_edges_host[q] * k1_edges_host[q]);
+  thr[0] = k1_edges_host[0] > 0.0 ? thr[0] : 0.0f;  // k1 >= e_0 for every k1 > 0
+  float *cmu = thr + n_k1 + 1, *ct = cmu + n_mu + 1;
+  for (int q = 0; q <= n_mu; ++q) {
+    const double m = q == 0 ? lo : q == n_mu ? hi : 0.5 + 0.5 * q / n_mu;
+    cmu[q] = (float)(4.0 * m * m);
+  }
+  for (int q = 0; q <= n_t; ++q) {
+    const double t = q == 0 ? lo : q == n_t ? hi : 0.5 + 0.5 * q / n_t;
+    ct[q] = (float)(t * t);
+  }
+  std::memcpy(tab.data(), kperp_host, (size_t)nb * 8);
+  std::memcpy(tab.data() + (size_t)nb * 8, kpar_host, (size_t)nc * 8);
+  std::memcpy(tab.data() + off32, f32.data(), f32.size() * 4);
+  unsigned char *dtab = p->at<unsigned char>(p->L.mono);
+  MONO_CUDA(cudaMemcpyAsync(dtab, tab.data(), tab.size(), cudaMemcpyHostToDevice, s));
+  a.bstride = (long long)npl * nc * nc;
+  a.rings = p->at<int>(p->L.closrings);
+  a.kperp64 = reinterpret_cast<const double *>(dtab);
+  a.kpar64 = a.kperp64 + nb;
+  a.kperp = reinterpret_cast<const float *>(dtab + off32);
+  a.kpar = a.kperp + nb;
+  a.thr = a.kpar + nc;
+  a.nc = nc;
+  a.n_k1 = n_k1;
+  a.n_mu = n_mu;
+  a.n_t = n_t;
+  a.nbin = n_k1 * n_mu * n_t;
+  // the bin table: rebuilt only when the geometry (tables, bin counts, planes) changed
+  std::vector<unsigned char> key(tab);
+  const int dims[3] = {n_k1, n_mu, n_t};
+  key.insert(key.end(), reinterpret_cast<const unsigned char *>(dims),
+             reinterpret_cast<const unsigned char *>(dims) + sizeof(dims));
+  key.insert(key.end(), reinterpret_cast<const unsigned char *>(p->clos.data()),
+             reinterpret_cast<const unsigned char *>(p->clos.data() + p->clos.size()));
+  const long long total = (long long)npl * nc * nc;
+  if (!p->mono_bins || key != p->mono_key) {
+    if ((size_t)total > p->mono_bins_cap) {
+      if (p->mono_bins) MONO_CUDA(cudaFree(p->mono_bins));
+      p->mono_bins = nullptr;
+      p->mono_bins_cap = 0;
+      void *m = nullptr;
+      const cudaError_t e = cudaMalloc(&m, (size_t)total * sizeof(int16_t));
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(p, BS_ERR_OOM, "bin table allocation failed");
+      }
+      p->mono_bins = static_cast<int16_t *>(m);
+      p->mono_bins_cap = (size_t)total;
+    }
+    const int grid = (int)std::min<long long>((total + kThreads - 1) / kThreads, 152LL * 64);
+    k_mono_bins<<<grid, kThreads, 0, s>>>(a, total, p->mono_bins);
+    MONO_CUDA(cudaGetLastError());
+    p->mono_key.swap(key);
+  }
+  // CTAs of 64 Ki samples (8 Ki per warp): few flushes, several CTAs per plane
+  const int n = nc * nc;
+  const int per_cta = 65536;
+  const int nx = std::max(1, (n + per_cta - 1) / per_cta);
+  a.chunk = ((n + nx - 1) / nx + 255) / 256 * 256;
+  return BS_OK;
+}
+
+
 extern "C" {
 
 bs_status bs_plan_ring_umean(bs_plan p, double *umean_host) {
@@ -386,91 +600,21 @@ bs_status bs_bs_monopole(bs_plan p, const double *b3d, const double *kperp_host,
   MONO_CUDA(cudaMemsetAsync(count_dev, 0, (size_t)nbin * sizeof(int64_t), s));
   const int npl = (int)p->clos.size();
   if (npl == 0) return BS_OK;
-  // constants: FP64 kperp [nb], kpar [nc]; FP32 kperp, kpar (rounded to nearest);
-  // squared thresholds E_q = e_q^2 [n_k1 + 1], cmu_q = 4 m_q^2 [n_mu + 1],
-  // ct_q = tau_q^2 [n_t + 1], with the acceptance limits at both ends of the
-  // shape tables (a pageable source is staged before the copy call returns)
-  const int nb = p->nb, nc = p->nc, nthr = n_k1 + n_mu + n_t + 3;
-  std::vector<unsigned char> &tab = p->mono_tab;
-  const size_t off32 = (size_t)(nb + nc) * 8;
-  tab.assign(off32 + (size_t)(nb + nc + nthr) * 4, 0);
-  std::vector<float> f32((size_t)nb + nc + nthr);
-  for (int m = 0; m < nb; ++m) f32[m] = (float)kperp_host[m];
-  for (int c = 0; c < nc; ++c) f32[nb + c] = (float)kpar_host[c];
-  float *thr = f32.data() + nb + nc;
-  const double lo = 0.5 - kShapeTol, hi = 1.0 + kShapeTol;
-  for (int q = 0; q <= n_k1; ++q) thr[q] = (float)(k1_edges_host[q] * k1_edges_host[q]);
-  thr[0] = k1_edges_host[0] > 0.0 ? thr[0] : 0.0f;  // k1 >= e_0 for every k1 > 0
-  float *cmu = thr + n_k1 + 1, *ct = cmu + n_mu + 1;
-  for (int q = 0; q <= n_mu; ++q) {
-    const double m = q == 0 ? lo : q == n_mu ? hi : 0.5 + 0.5 * q / n_mu;
-    cmu[q] = (float)(4.0 * m * m);
-  }
-  for (int q = 0; q <= n_t; ++q) {
-    const double t = q == 0 ? lo : q == n_t ? hi : 0.5 + 0.5 * q / n_t;
-    ct[q] = (float)(t * t);
-  }
-  std::memcpy(tab.data(), kperp_host, (size_t)nb * 8);
-  std::memcpy(tab.data() + (size_t)nb * 8, kpar_host, (size_t)nc * 8);
-  std::memcpy(tab.data() + off32, f32.data(), f32.size() * 4);
-  unsigned char *dtab = p->at<unsigned char>(p->L.mono);
-  MONO_CUDA(cudaMemcpyAsync(dtab, tab.data(), tab.size(), cudaMemcpyHostToDevice, s));
   MONO_CUDA(smem_optin_once<k_mono_sum<1>>());
   MONO_CUDA(smem_optin_once<k_mono_sum<2>>());
   MONO_CUDA(smem_optin_once<k_mono_sum<4>>());
   MONO_CUDA(smem_optin_once<k_mono_sum<kMaxBatch>>());
   MonoArgs a{};
   a.b3d = b3d;
-  a.bstride = (long long)npl * nc * nc;
-  a.rings = p->at<int>(p->L.closrings);
-  a.kperp64 = reinterpret_cast<const double *>(dtab);
-  a.kpar64 = a.kperp64 + nb;
-  a.kperp = reinterpret_cast<const float *>(dtab + off32);
-  a.kpar = a.kperp + nb;
-  a.thr = a.kpar + nc;
-  a.nc = nc;
-  a.n_k1 = n_k1;
-  a.n_mu = n_mu;
-  a.n_t = n_t;
-  a.nbin = nbin;
+  st = mono_geometry(p, kperp_host, kpar_host, k1_edges_host, n_k1, n_mu, n_t, s, a);
+  if (st != BS_OK) return st;
   a.model = b3d ? 0 : 1;
   a.f2 = 2.0 * f_ng;
   a.p_amp = p_amp;
   a.p_half = 0.5 * p_index;
   a.sums = sum_dev;
   a.cnt = reinterpret_cast<unsigned long long *>(count_dev);
-  // the bin table: rebuilt only when the geometry (tables, bin counts, planes) changed
-  std::vector<unsigned char> key(tab);
-  const int dims[3] = {n_k1, n_mu, n_t};
-  key.insert(key.end(), reinterpret_cast<const unsigned char *>(dims),
-             reinterpret_cast<const unsigned char *>(dims) + sizeof(dims));
-  key.insert(key.end(), reinterpret_cast<const unsigned char *>(p->clos.data()),
-             reinterpret_cast<const unsigned char *>(p->clos.data() + p->clos.size()));
-  const long long total = (long long)npl * nc * nc;
-  if (!p->mono_bins || key != p->mono_key) {
-    if ((size_t)total > p->mono_bins_cap) {
-      if (p->mono_bins) MONO_CUDA(cudaFree(p->mono_bins));
-      p->mono_bins = nullptr;
-      p->mono_bins_cap = 0;
-      void *m = nullptr;
-      const cudaError_t e = cudaMalloc(&m, (size_t)total * sizeof(int16_t));
-      if (e != cudaSuccess) {
-        cudaGetLastError();
-        return fail(p, BS_ERR_OOM, "bs_bs_monopole: bin table allocation failed");
-      }
-      p->mono_bins = static_cast<int16_t *>(m);
-      p->mono_bins_cap = (size_t)total;
-    }
-    const int grid = (int)std::min<long long>((total + kThreads - 1) / kThreads, 152LL * 64);
-    k_mono_bins<<<grid, kThreads, 0, s>>>(a, total, p->mono_bins);
-    MONO_CUDA(cudaGetLastError());
-    p->mono_key.swap(key);
-  }
-  // CTAs of 64 Ki samples (8 Ki per warp): few flushes, several CTAs per plane
-  const int n = nc * nc;
-  const int per_cta = 65536;
-  const int nx = std::max(1, (n + per_cta - 1) / per_cta);
-  a.chunk = ((n + nx - 1) / nx + 255) / 256 * 256;
+  const int n = p->nc * p->nc;
   const int gx = (n + a.chunk - 1) / a.chunk;
   for (int b0 = 0; b0 < batch; b0 += per) {
     a.b0 = b0;
@@ -486,6 +630,81 @@ bs_status bs_bs_monopole(bs_plan p, const double *b3d, const double *kperp_host,
       k_mono_sum<4><<<grid, kThreads, sm, s>>>(a, p->mono_bins);
     else
       k_mono_sum<kMaxBatch><<<grid, kThreads, sm, s>>>(a, p->mono_bins);
+    MONO_CUDA(cudaGetLastError());
+  }
+  return BS_OK;
+}
+
+bs_status bs_bs_multipoles(bs_plan p, const double *b3d, const double *kperp_host,
+                           const double *kpar_host, const double *k1_edges_host, int n_k1,
+                           int n_mu, int n_t, int lmax, double *sum_dev, int64_t *count_dev,
+                           void *stream) {
+  BS_NVTX("bs_bs_multipoles");
+  using namespace bsi;
+  if (!p || !b3d || !kperp_host || !kpar_host || !k1_edges_host || !sum_dev || !count_dev)
+    return fail(p, BS_ERR_ARG, "bs_bs_multipoles: NULL argument");
+  if (lmax < 0 || lmax > kMaxL) return fail(p, BS_ERR_ARG, "bs_bs_multipoles: lmax must be in [0, 4]");
+  if (n_k1 < 1 || n_k1 > kMonoMaxK1 || n_mu < 1 || n_t < 1 || n_mu > kMonoMaxShape ||
+      n_t > kMonoMaxShape)
+    return fail(p, BS_ERR_ARG, "bs_bs_multipoles: bin counts out of range");
+  for (int q = 0; q < n_k1; ++q)
+    if (!(k1_edges_host[q + 1] > k1_edges_host[q]) || !std::isfinite(k1_edges_host[q + 1]))
+      return fail(p, BS_ERR_ARG, "bs_bs_multipoles: k1 edges must be finite and ascending");
+  if (p->general) return fail(p, BS_ERR_UNSUPPORTED, "bs_bs_multipoles: general plans");
+  if (!p->counts_ready) return fail(p, BS_ERR_STATE, "bs_bs_multipoles before the ring-triple counts");
+  for (int m = 0; m < p->nb; ++m)
+    if (!(kperp_host[m] >= 1e-8 && kperp_host[m] <= 1e8))
+      return fail(p, BS_ERR_ARG, "bs_bs_multipoles: k_perp must lie in [1e-8, 1e8]");
+  for (int c = 0; c < p->nc; ++c)
+    if (!(std::fabs(kpar_host[c]) <= 1e8))
+      return fail(p, BS_ERR_ARG, "bs_bs_multipoles: |k_par| must not exceed 1e8");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  bs_status st = prepare(p, s);
+  if (st != BS_OK) return st;
+  const int nbin = n_k1 * n_mu * n_t;
+  const int batch = p->ubatch;
+  const int per = std::min(batch, 4);
+  if ((size_t)per * (lmax + 1) * nbin * 8 + (size_t)nbin * 4 > (size_t)200 * 1024)
+    return fail(p, BS_ERR_UNSUPPORTED, "bs_bs_multipoles: too many bins for one CTA's histogram");
+  MONO_CUDA(cudaMemsetAsync(sum_dev, 0, (size_t)batch * (lmax + 1) * nbin * sizeof(double), s));
+  MONO_CUDA(cudaMemsetAsync(count_dev, 0, (size_t)nbin * sizeof(int64_t), s));
+  const int npl = (int)p->clos.size();
+  if (npl == 0) return BS_OK;
+  MonoArgs a{};
+  a.b3d = b3d;
+  st = mono_geometry(p, kperp_host, kpar_host, k1_edges_host, n_k1, n_mu, n_t, s, a);
+  if (st != BS_OK) return st;
+  a.sums = sum_dev;
+  a.cnt = reinterpret_cast<unsigned long long *>(count_dev);
+  const int n = p->nc * p->nc;
+  const int gx = (n + a.chunk - 1) / a.chunk;
+  const int skip0 = p->nc % 2 == 0;  // delay index -nc/2 has no reflection on the grid
+  for (int b0 = 0; b0 < batch; b0 += per) {
+    a.b0 = b0;
+    a.nbatch = std::min(per, batch - b0);
+    if (b0 > 0) a.cnt = nullptr;
+    const dim3 grid(gx, npl);
+    const size_t sm = (size_t)a.nbatch * (lmax + 1) * nbin * 8 + (size_t)nbin * 4;
+#define MULTIPOLE_LAUNCH(NB, L)                                                        \
+  do {                                                                                 \
+    const cudaError_t eo__ = smem_optin_once<k_mono_multipole<NB, L>>();              \
+    if (eo__ != cudaSuccess) return cuda_fail(p, eo__, "multipole smem opt-in");      \
+    k_mono_multipole<NB, L><<<grid, kThreads, sm, s>>>(a, p->mono_bins, skip0);       \
+  } while (0)
+    const int nbt = a.nbatch == 1 ? 1 : 4;
+    switch (lmax * 10 + nbt) {
+      case 1: MULTIPOLE_LAUNCH(1, 0); break;
+      case 4: MULTIPOLE_LAUNCH(4, 0); break;
+      case 11: MULTIPOLE_LAUNCH(1, 1); break;
+      case 14: MULTIPOLE_LAUNCH(4, 1); break;
+      case 21: MULTIPOLE_LAUNCH(1, 2); break;
+      case 24: MULTIPOLE_LAUNCH(4, 2); break;
+      case 31: MULTIPOLE_LAUNCH(1, 3); break;
+      case 34: MULTIPOLE_LAUNCH(4, 3); break;
+      case 41: MULTIPOLE_LAUNCH(1, 4); break;
+      default: MULTIPOLE_LAUNCH(4, 4); break;
+    }
+#undef MULTIPOLE_LAUNCH
     MONO_CUDA(cudaGetLastError());
   }
   return BS_OK;

@@ -214,3 +214,78 @@ def test_cylindrical_binning_wide_rows(nc):
     scale = np.abs(b3h).max() * np.maximum(cnt.cpu().numpy(), 1)
     assert np.all(np.abs(sums.cpu().numpy()[0] - want) <= 1e-12 * scale)
     plan.close()
+
+
+@pytest.mark.parametrize("batch,lmax,nc", [(2, 4, 24), (1, 2, 23), (5, 3, 16)])
+def test_multipoles_on_estimated_bispectrum(batch, lmax, nc):
+    """bs_bs_multipoles on the GPU's own closable 3D bispectrum: counts and
+    sums inside the oracle's interval; the odd l, which the point symmetry of
+    the real part of a Hermitian 3D bispectrum cancels, vanish to rounding;
+    one and several launches over realisations."""
+    torch = _torch()
+    import paper_2506_10526_gb300 as bs
+    nt, r, rp, dnu = 64, 900.0, 1.2, 0.16
+    edges = synth.edges_log(8, 1.5, 31.0)
+    v = np.stack([synth.sky_visibilities(nt, nc, seed=400 + s) for s in range(batch)])
+    plan = bs.Plan(nt, nc, edges, precision=1, batch=batch, r=r, rprime=rp, dnu_c=dnu,
+                   multires=True)
+    plan.grid_load(torch.from_numpy(v).cuda())
+    plan.mabs(accumulate=True)
+    tri, _ = plan.counts()
+    ncl = plan.n_closable
+    b3 = torch.empty((batch, ncl, nc, nc), dtype=torch.float64, device="cuda")
+    plan.bs3d_closable(b3)
+    kperp = 2 * np.pi * plan.ring_umean() / r
+    kpar = mo.kpar_axis(nc, rp, dnu)
+    k1e = np.geomspace(0.5 * kperp.min(), 1.2 * np.sqrt(kperp.max() ** 2 + kpar.max() ** 2), 13)
+    sums, cnt = plan.bs_multipoles(b3, kperp, kpar, k1e, 5, 5, lmax=lmax)
+    torch.cuda.synchronize()
+    b3h = b3.cpu().numpy()
+    trips = _planes_trips(tri, len(edges) - 1)
+    _, c_o = mo.bs_multipoles(b3h, trips, kperp, kpar, k1e, 5, 5, lmax)
+    iv = mo.multipole_interval(b3h, trips, kperp, kpar, k1e, 5, 5, lmax, REL_K, REL_S)
+    c = cnt.cpu().numpy()
+    s = sums.cpu().numpy()
+    assert s.shape == (batch, lmax + 1, 12, 5, 5)
+    scale = np.abs(b3h).max() * 9 * np.maximum(iv["c_hi"], 1)
+    _check_interval(c, s, iv, c_o, 1e-12 * scale)
+    # l = 0 is the monopole over the same (paired) samples
+    if nc % 2:
+        s_m, c_m = plan.bs_monopole(b3, kperp, kpar, k1e, 5, 5)
+        np.testing.assert_array_equal(c, c_m.cpu().numpy())
+        np.testing.assert_allclose(s[:, 0], s_m.cpu().numpy(), rtol=1e-12,
+                                   atol=1e-13 * scale.max())
+    if lmax >= 1:
+        # odd l of the point-symmetric part cancel; what is left comes from the
+        # antisymmetric part A of the computed planes, |odd l| <= (2l+1) max|A| count
+        lo = nc % 2 == 0
+        refl = np.r_[0, nc - np.arange(1, nc)] if lo else nc - 1 - np.arange(nc)
+        A = 0.5 * (b3h - b3h[:, :, refl][:, :, :, refl])[:, :, lo:, lo:]
+        a_max = np.abs(A).max()
+        odd = np.abs(s[:, 1::2]).max()
+        even = np.abs(s[:, 0::2]).max()
+        print(f"max |odd l| / max |even l| = {odd / even:.2e}; "
+              f"max |A| / max |B| = {a_max / np.abs(b3h).max():.2e}")
+        bound = (2 * lmax + 1) * a_max * c + 1e-12 * scale
+        assert np.all(np.abs(s[:, 1::2]) <= bound[None, None])
+        assert odd < 1e-5 * even
+    plan.close()
+
+
+def test_multipoles_argument_errors():
+    torch = _torch()
+    import paper_2506_10526_gb300 as bs
+    nt, nc = 32, 8
+    edges = synth.edges_linear(4, 11)
+    plan = bs.Plan(nt, nc, edges, precision=1)
+    plan.grid_load(torch.from_numpy(synth.sky_visibilities(nt, nc, seed=5)[None]).cuda())
+    plan.mabs()
+    plan.counts()
+    b3 = torch.zeros((1, plan.n_closable, nc, nc), dtype=torch.float64, device="cuda")
+    kperp = 2 * np.pi * plan.ring_umean()
+    kpar = mo.kpar_axis(nc)
+    with pytest.raises(bs.BsError):
+        plan.bs_multipoles(b3, kperp, kpar, [0.1, 1.0, 10.0], lmax=5)
+    with pytest.raises(bs.BsError):
+        plan.bs_multipoles(b3, kperp, kpar, [1.0, 0.1], lmax=2)
+    plan.close()

@@ -242,3 +242,142 @@ def test_interval_rejects_planted_mistakes(mistake):
                               model=(1.0, 1.0, -2.0))
     c32 = _fp32_squared_decision(trips, kperp, kpar, edges, 5, 5, mistake=mistake)
     assert not (np.all(iv["c_lo"] <= c32) and np.all(c32 <= iv["c_hi"]))
+
+
+# ---------------------------------------------------------------- multipoles
+
+def test_legendre_against_library_and_parity():
+    special = pytest.importorskip("scipy.special")
+    x = np.linspace(-1.0, 1.0, 401)
+    P = mo.legendre(6, x)
+    for l in range(7):
+        np.testing.assert_allclose(P[l], special.eval_legendre(l, x), rtol=0, atol=1e-14)
+        assert P[l][-1] == pytest.approx(1.0, abs=1e-15)            # P_l(1) = 1
+        np.testing.assert_allclose(P[l][::-1], (-1) ** l * P[l], atol=1e-15)
+    # the orthogonality that makes (2l+1) <P_l B> the coefficient of P_l
+    xg, wg = np.polynomial.legendre.leggauss(12)
+    Pg = mo.legendre(4, xg)
+    G = (Pg * wg) @ Pg.T
+    np.testing.assert_allclose(G, np.diag(2.0 / (2 * np.arange(5) + 1)), atol=1e-14)
+
+
+def test_mu1_against_explicit_vectors():
+    """mu_1 = k_par / k of the largest side, from explicit 3D vectors whose
+    sky-plane parts are random and whose third side closes the triangle."""
+    r = np.random.default_rng(41)
+    for _ in range(3000):
+        pa, pb = r.normal(size=2), r.normal(size=2) * r.uniform(0.2, 2.0)
+        za, zb = r.normal(size=2) * r.uniform(0.1, 5.0)
+        vecs = [np.r_[pa, za], np.r_[pb, zb]]
+        vecs.append(-(vecs[0] + vecs[1]))
+        big = max(vecs, key=lambda v: np.dot(v, v))
+        ref = big[2] / np.linalg.norm(big)
+        S = [np.dot(v, v) for v in vecs]
+        got = float(mo._mu1(S[0], S[1], S[2], za, zb))
+        assert got == pytest.approx(ref, abs=1e-13)
+
+
+def _brute_multipoles(b3d, trips, kperp, kpar, k1_edges, n_mu, n_t, lmax):
+    """Per-sample loops: bins by linear search, the line-of-sight cosine of
+    the longest side from its components, P_l from their closed forms."""
+    closed = [lambda x: 1.0, lambda x: x, lambda x: (3 * x * x - 1) / 2,
+              lambda x: (5 * x ** 3 - 3 * x) / 2, lambda x: (35 * x ** 4 - 30 * x * x + 3) / 8]
+    n_k1 = len(k1_edges) - 1
+    batch, _, nc, _ = b3d.shape
+    sums = np.zeros((batch, lmax + 1, n_k1, n_mu, n_t))
+    cnt = np.zeros((n_k1, n_mu, n_t), np.int64)
+    tol = mo.SHAPE_TOL
+    mu_e = [0.5 + 0.5 * q / n_mu for q in range(n_mu + 1)]
+    t_e = [0.5 + 0.5 * q / n_t for q in range(n_t + 1)]
+    lo = 1 if nc % 2 == 0 else 0  # the delay index -nc/2 has no reflection
+    for p, (i, j, l) in enumerate(trips):
+        for ia in range(lo, nc):
+            for ib in range(lo, nc):
+                z = [kpar[ia], kpar[ib], -(kpar[ia] + kpar[ib])]
+                k = [math.sqrt(kperp[m] ** 2 + zz ** 2) for m, zz in zip((i, j, l), z)]
+                order = sorted(range(3), key=lambda n: -k[n])  # stable: first of equal sides
+                k1, k2, k3 = (k[n] for n in order)
+                mu = (k1 * k1 + k2 * k2 - k3 * k3) / (2 * k1 * k2)
+                t = k2 / k1
+                if not (0.5 - tol <= mu <= 1 + tol and 0.5 - tol <= t <= 1 + tol):
+                    continue
+                mu, t = min(max(mu, 0.5), 1.0), min(max(t, 0.5), 1.0)
+                qk = next((q for q in range(n_k1) if k1_edges[q] <= k1 < k1_edges[q + 1]), None)
+                if qk is None:
+                    continue
+                qm = next(q for q in range(n_mu) if mu < mu_e[q + 1] or q == n_mu - 1)
+                qt = next(q for q in range(n_t) if t < t_e[q + 1] or q == n_t - 1)
+                x = z[order[0]] / k1
+                cnt[qk, qm, qt] += 1
+                for ll in range(lmax + 1):
+                    sums[:, ll, qk, qm, qt] += (2 * ll + 1) * closed[ll](x) * b3d[:, p, ia, ib]
+    return sums, cnt
+
+
+@pytest.mark.parametrize("nc", [10, 9])
+def test_multipoles_against_brute_force(nc):
+    r = np.random.default_rng(12 + nc)
+    nb = 4
+    kperp = np.sort(r.uniform(0.05, 0.3, nb))
+    trips = [(0, 0, 0), (0, 1, 1), (0, 1, 2), (1, 2, 3), (3, 3, 3)]
+    kpar = mo.kpar_axis(nc, rprime=30.0, dnu_c=0.05)
+    b3d = r.normal(size=(2, len(trips), nc, nc))
+    edges = np.geomspace(0.04, 2.5, 7)
+    s, c = mo.bs_multipoles(b3d, trips, kperp, kpar, edges, 5, 5, 4)
+    s_b, c_b = _brute_multipoles(b3d, trips, kperp, kpar, edges, 5, 5, 4)
+    np.testing.assert_array_equal(c, c_b)
+    np.testing.assert_allclose(s, s_b, rtol=1e-11, atol=1e-11)
+    assert c.sum() > 0 and np.abs(s[:, 1:]).max() > 0
+
+
+def test_multipole_l0_is_the_monopole_for_odd_nc():
+    """Odd nc: every delay index has its reflection, the multipole samples are
+    the monopole's, and l = 0 is the monopole sum."""
+    r = np.random.default_rng(3)
+    nb, nc = 5, 15
+    kperp = np.sort(r.uniform(0.05, 0.3, nb))
+    trips = [(0, 1, 1), (1, 2, 3), (2, 3, 4), (4, 4, 4)]
+    kpar = mo.kpar_axis(nc, rprime=20.0, dnu_c=0.05)
+    b3d = r.normal(size=(1, len(trips), nc, nc))
+    edges = np.geomspace(0.04, 2.5, 9)
+    s, c = mo.bs_multipoles(b3d, trips, kperp, kpar, edges, 5, 5, 2)
+    s0, c0 = mo.bs_monopole(b3d, trips, kperp, kpar, edges, 5, 5)
+    np.testing.assert_array_equal(c, c0)
+    np.testing.assert_allclose(s[:, 0], s0, rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("nc", [16, 15])
+def test_odd_multipoles_vanish_for_point_symmetric_b(nc):
+    """B(-a, -b) = B(a, b) (the real part of a Hermitian 3D bispectrum): the
+    reflection flips mu_1 and keeps the bin, so odd l cancel; even l do not."""
+    r = np.random.default_rng(7)
+    nb = 5
+    kperp = np.sort(r.uniform(0.05, 0.3, nb))
+    trips = [(0, 0, 1), (0, 2, 2), (1, 2, 3), (2, 4, 4)]
+    kpar = mo.kpar_axis(nc, rprime=20.0, dnu_c=0.05)
+    lo = nc % 2 == 0
+    refl = np.r_[0, nc - np.arange(1, nc)] if lo else nc - 1 - np.arange(nc)
+    np.testing.assert_array_equal(kpar[refl[lo:]], -kpar[lo:])
+    b3d = r.normal(size=(1, len(trips), nc, nc))
+    b3d = 0.5 * (b3d + b3d[:, :, refl][:, :, :, refl])
+    edges = np.geomspace(0.04, 2.5, 9)
+    s, c = mo.bs_multipoles(b3d, trips, kperp, kpar, edges, 5, 5, 4)
+    scale = np.abs(b3d).max() * max(c.max(), 1) * 9
+    assert np.abs(s[:, 1::2]).max() < 1e-13 * scale
+    assert np.abs(s[:, 2]).max() > 1e-3 * np.abs(b3d).max()
+    # the unpaired row of an even nc is left out: changing it changes nothing
+    if lo:
+        b3d[:, :, 0, :] += 1.0
+        s_bad, _ = mo.bs_multipoles(b3d, trips, kperp, kpar, edges, 5, 5, 4)
+        np.testing.assert_allclose(s_bad, s, atol=1e-12)
+
+
+def test_multipole_interval_holds_the_fp64_decision():
+    trips, kperp, kpar, edges = _interval_setup()
+    r = np.random.default_rng(9)
+    b3d = r.normal(size=(2, len(trips), kpar.size, kpar.size))
+    iv = mo.multipole_interval(b3d, trips, kperp, kpar, edges, 5, 5, 3, 2e-6, 1e-5)
+    s, c = mo.bs_multipoles(b3d, trips, kperp, kpar, edges, 5, 5, 3)
+    assert np.all(iv["c_lo"] <= c) and np.all(c <= iv["c_hi"])
+    assert np.all(np.abs(s - iv["s_sure"]) <= iv["s_amb"] + 1e-10)
+    assert iv["n_amb"] < 1e-3 * iv["n"]
