@@ -52,6 +52,9 @@ WORKLOADS = {
     "small": dict(nt=128, nc=128, nb=12, edges=("log", 2.2, 64.0), block=32, block3=128,
                   desc="profiling case: 128^2 uv grid, 128 channels, 12 log rings |U| in "
                        "[2.2, 64), no flagging"),
+    "delay768": dict(nt=64, nc=768, nb=6, edges=("log", 2.0, 32.0), block=128, block3=256,
+                     desc="profiling case: the MWA-like 768-channel delay axis on a 64^2 grid "
+                          "with 6 log rings |U| in [2, 32)"),
     "tiny": dict(nt=64, nc=16, nb=8, edges=("linear", 0.0, 32.0), block=16,
                  desc="tiny: 64^2 uv grid, 16 channels, 8 linear rings |U| < 32, no flagging"),
 }

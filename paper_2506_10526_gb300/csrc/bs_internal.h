@@ -161,6 +161,15 @@ inline cudaError_t smem_optin_once() {
 }
 
 // ---- kernels / launchers (each returns cudaGetLastError after launch) ----
+// Register-FFT variants of the two field passes (grid_reg.cu) for the image
+// sides with a register plan (has_reg_fft); the launchers below dispatch to them.
+bool has_reg_fft(int M, int nt);
+cudaError_t launch_colpass_reg(const GridGeom &g, const float2 *vis, const float *ngrid,
+                               const uint8_t *valid, const int8_t *label, const int *uext,
+                               const float2 *twM, float2 *G, cudaStream_t s);
+cudaError_t launch_rowpass_reg(const GridGeom &g, const float2 *G, const uint8_t *valid,
+                               const int *uext, const float2 *twM, float *F, uint16_t *Fhi,
+                               uint16_t *Flo, unsigned *fmax, cudaStream_t s);
 cudaError_t launch_colpass(const GridGeom &g, const float2 *vis, const float *ngrid,
                            const uint8_t *valid, const int8_t *label, const int *uext,
                            const float2 *twM, const Radices &radM, float2 *G,
@@ -197,6 +206,15 @@ cudaError_t launch_add_f64(double *y, const double *x, long long n, cudaStream_t
 cudaError_t launch_zero_planes(double *dsum, const int *trips, int ntr, int batch, int ntrip,
                                int n2, const int *box, cudaStream_t s);
 // tmp: batch * ntrip * nc^2 float2 followed by nc^2 doubles of scratch
+// Register-FFT delay transform (delta_reg.cu) for the channel counts with a
+// register plan (has_reg_dft); launch_bs3d dispatches to it.  rinv [nc][nc]:
+// FP32 reciprocal folded sampling; rowflag [nc]: rows of the periodic
+// placement with a sampled separation.
+bool has_reg_dft(int nc);
+cudaError_t launch_bs3d_reg(const double *dsum, const float *rinv, const uint8_t *rowflag,
+                            const double *tnorm, float2 *tmp, double *out, int batch, int ntrip,
+                            int nc, const float2 *twN, double scale, const int *list, int ny,
+                            cudaStream_t s);
 cudaError_t launch_bs3d(const double *dsum, const long long *nnu, const double *tnorm,
                         float2 *tmp, double *out, int batch, int ntrip, int nc,
                         const float2 *twN, const Radices &radN, double scale, const int *list,

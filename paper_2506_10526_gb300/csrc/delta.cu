@@ -95,7 +95,10 @@ __device__ void dft_direct(const float2 *x, float2 *y, int N, const float2 *tw, 
 // periodic placement of the row pass: rinv[n][m] = 1 / (N(d) + N(-d)) (N(0)
 // once) for the separation d = (n, m) taken in [-nc/2, nc/2), 0 where nothing
 // was sampled.  The same for every ring triple, so the row pass multiplies.
-__global__ void k_fold_rinv(const long long *__restrict__ nnu, int nc, double *__restrict__ rinv) {
+// rinvf (optional): the same table in FP32, written instead of rinv; rowflag
+// (optional, zeroed by the caller): rows n with a sampled separation.
+__global__ void k_fold_rinv(const long long *__restrict__ nnu, int nc, double *__restrict__ rinv,
+                            float *__restrict__ rinvf, uint8_t *__restrict__ rowflag) {
   const int n2 = 2 * nc - 1;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nc * nc; e += gridDim.x * blockDim.x) {
     const int nidx = e / nc, m = e - nidx * nc;
@@ -103,7 +106,12 @@ __global__ void k_fold_rinv(const long long *__restrict__ nnu, int nc, double *_
     const int i1 = np + nc - 1, i2 = mp + nc - 1, j1 = n2 - 1 - i1, j2 = n2 - 1 - i2;
     long long cnt = nnu[i1 * n2 + i2];
     if (j1 != i1 || j2 != i2) cnt += nnu[j1 * n2 + j2];
-    rinv[e] = cnt > 0 ? 1.0 / (double)cnt : 0.0;
+    if (rinvf) {
+      rinvf[e] = cnt > 0 ? 1.0f / (float)cnt : 0.0f;
+    } else {
+      rinv[e] = cnt > 0 ? 1.0 / (double)cnt : 0.0;
+    }
+    if (rowflag && cnt > 0) rowflag[nidx] = 1;  // every writer stores the same value
   }
 }
 
@@ -305,13 +313,25 @@ cudaError_t launch_bs3d(const double *dsum, const long long *nnu, const double *
   e = smem_optin_once<k_bs3d_cols>();
   if (e != cudaSuccess) return e;
   const int threads = nc >= 64 ? 256 : 64;
-  // the reciprocal sampling table sits after the batch's complex scratch
+  // the reciprocal sampling table and the row flags sit after the batch's
+  // complex scratch
   double *rinv = reinterpret_cast<double *>(tmp + (size_t)batch * ntrip * nc * nc);
-  k_fold_rinv<<<(nc * nc + 255) / 256, 256, 0, s>>>(nnu, nc, rinv);
+  float *rinvf = reinterpret_cast<float *>(rinv);  // the register path's FP32 table
+  uint8_t *rowflag = reinterpret_cast<uint8_t *>(rinv + (size_t)nc * nc);
+  const bool reg = has_reg_dft(nc);
+  if (reg) {
+    e = cudaMemsetAsync(rowflag, 0, (size_t)nc, s);
+    if (e != cudaSuccess) return e;
+  }
+  k_fold_rinv<<<(nc * nc + 255) / 256, 256, 0, s>>>(nnu, nc, rinv, reg ? rinvf : nullptr,
+                                                    reg ? rowflag : nullptr);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int ny = list ? nlist : ntrip;
   if (ny == 0) return cudaSuccess;
+  if (reg)
+    return launch_bs3d_reg(dsum, rinvf, rowflag, tnorm, tmp, out, batch, ntrip, nc, twN, scale,
+                           list, ny, s);
   dim3 grid((nc + rows - 1) / rows, ny, batch);
   k_bs3d_rows<<<grid, threads, smem, s>>>(dsum, rinv, tnorm, tmp, ntrip, nc, twN, radN, list, rows);
   e = cudaGetLastError();

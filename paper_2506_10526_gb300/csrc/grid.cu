@@ -350,6 +350,7 @@ __global__ void k_hermitian(const float2 *__restrict__ vis, int nc, int nt,
 cudaError_t launch_colpass(const GridGeom &g, const float2 *vis, const float *ngrid,
                            const uint8_t *valid, const int8_t *label, const int *uext,
                            const float2 *twM, const Radices &radM, float2 *G, cudaStream_t s) {
+  if (has_reg_fft(g.M, g.nt)) return launch_colpass_reg(g, vis, ngrid, valid, label, uext, twM, G, s);
   // at least two CTAs per SM (shared memory below ~110 KB)
   int UB = 16;
   auto bytes = [&](int ub) {
@@ -367,6 +368,7 @@ cudaError_t launch_colpass(const GridGeom &g, const float2 *vis, const float *ng
 cudaError_t launch_rowpass(const GridGeom &g, const float2 *G, const uint8_t *valid,
                            const int *uext, const float2 *twM, const Radices &radM, float *F,
                            uint16_t *Fhi, uint16_t *Flo, unsigned *fmax, cudaStream_t s) {
+  if (has_reg_fft(g.M, g.nt)) return launch_rowpass_reg(g, G, valid, uext, twM, F, Fhi, Flo, fmax, s);
   int RPB = 8;
   while (RPB > 1 && (size_t)(2 * RPB * g.M + g.M) * sizeof(float2) > (size_t)96 * 1024) RPB /= 2;
   const size_t smem = (size_t)(2 * RPB * g.M + g.M) * sizeof(float2);

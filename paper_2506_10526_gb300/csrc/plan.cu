@@ -133,9 +133,10 @@ void compute_layout(bs_plan p) {
   L.Flo = p->levels[0].offFlo;
   L.twM = p->levels[0].offTw;
   L.dsum = take((size_t)p->batch * p->ntrip * n2 * n2 * sizeof(double));
-  // delay-transform scratch: complex [batch][T_r][nc][nc], then a double [nc][nc] table
+  // delay-transform scratch: complex [batch][T_r][nc][nc], then a double [nc][nc]
+  // table and nc row flags
   L.tmp3d = take((size_t)p->batch * p->ntrip * (size_t)p->nc * p->nc * sizeof(float2) +
-                 (size_t)p->nc * p->nc * sizeof(double));
+                 (size_t)p->nc * p->nc * sizeof(double) + (size_t)p->nc);
   L.herm = take(2 * sizeof(float));
   L.err = take(sizeof(int));
   L.maps = take(7 * p->levels.size() * sizeof(CUtensorMap));

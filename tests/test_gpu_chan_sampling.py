@@ -84,7 +84,11 @@ def _check(out, b, vis, edges, ngrid, flags, precision, label, norm_A=1.0):
     assert np.any(np.nanstd(np.where(den > 0, den, np.nan), axis=(1, 2, 3)) > 0)
     print(f"{label}: full {e_full:.2e}, collapse {e_delta:.2e}, Eq. (dft) {e3:.2e}")
     tol = TOL[precision]
-    assert e_full < tol and e_delta < tol and e3 < tol
+    # a full-cube entry is the ratio of two triple sums, each rounded at the
+    # contraction's precision: the numerator's error scales with B_abs, the
+    # denominator's (occupancy fields) adds its own, so the entry is held to
+    # twice the single-sum tolerance; the collapse and Eq. (dft) to the tolerance
+    assert e_full < 2 * tol and e_delta < tol and e3 < tol
 
 
 @pytest.mark.parametrize("precision,multires", [(0, False), (0, True), (1, True), (2, True)])

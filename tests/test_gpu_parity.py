@@ -383,3 +383,39 @@ def test_merged_plans_equal_one_plan(precision, multires):
     assert np.abs(d2[ok] - d1[ok]).max() <= 1e-11 * np.abs(d1[ok]).max()
     for pl in plans:
         pl.close()
+
+
+@pytest.mark.parametrize("nc,block", [(24, None), (48, (0, 4, 0, 4, 0, 4)), (96, (0, 40, 8, 48, 0, 96)),
+                                      (12, None), (16, (2, 6, 0, 16, 3, 9))])
+def test_delay_transform_against_oracle(nc, block):
+    """Eq. (dft) of the library's own folded planes against the oracle's
+    transform of the same planes: channel counts with a register FFT (24, 48,
+    96, 16) and one without (12), whole-cube and partial channel blocks (rows
+    of the periodic placement with nothing sampled), non-unit scale."""
+    torch = _torch()
+    import paper_2506_10526_gb300 as bs
+    nt, r, rp, dnu = 32, 900.0, 1.2, 0.16
+    edges = synth.edges_linear(4, 15)
+    vis = synth.sky_visibilities(nt, nc, seed=900 + nc)
+    plan = bs.Plan(nt, nc, edges, precision=0, r=r, rprime=rp, dnu_c=dnu)
+    plan.grid_load(torch.from_numpy(vis[None]).cuda())
+    if block is None:
+        plan.mabs(accumulate=True)
+    else:
+        plan.mabs(block=block, accumulate=True)
+    n2 = 2 * nc - 1
+    dd = torch.empty((1, plan.ntrip, n2, n2), dtype=torch.float64, device="cuda")
+    b3 = torch.empty((1, plan.ntrip, nc, nc), dtype=torch.float64, device="cuda")
+    plan.mabs_delta(dd)
+    plan.bs3d(b3)
+    tri, _ = plan.counts()
+    torch.cuda.synchronize()
+    want = oracle.delay_dft(dd[0].cpu().numpy(), nc, r, rp, dnu).real
+    got = b3[0].cpu().numpy()
+    for k in range(plan.ntrip):
+        if tri[k] == 0:
+            assert np.all(got[k] == 0.0)
+            continue
+        err = np.abs(got[k] - want[k]).max() / np.abs(want[k]).max()
+        assert err < TOL_FP32, (k, err)
+    plan.close()

@@ -1,9 +1,11 @@
 """The split-precision readings checked on the CPU by emulating the operand
 formats with numpy (independent of the CUDA kernels): with the power-of-two
-field scales of the split-FP16 form no operand overflows FP16 and the
-triple sum errs by at most ~3 x 2^-22 of the sum of |terms|; split BF16
-(emulated by truncating the FP32 mantissa to 8 bits with rounding) errs by at
-most ~3 x 2^-17 of it."""
+field scales of the split-FP16 form no operand overflows FP16, and the
+operand rounding of the split forms alone errs by at most ~3 x 2^-22 (FP16)
+and ~3 x 2^-17 (BF16, emulated by rounding the FP32 mantissa to 8 bits) of
+the sum of |terms|.  The products are summed in FP64 here, so these bound the
+operand rounding only; the kernels' FP32 accumulation over K adds the c_acc
+term of the error bound, which the GPU error-bound tests cover."""
 import numpy as np
 
 
