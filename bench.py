@@ -97,6 +97,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-mc", action="store_true",
                     help="skip the batched Monte Carlo and surrogate measurements")
+    ap.add_argument("--only-surrogate", action="store_true",
+                    help="run only the surrogate network measurement (profiling)")
     ap.add_argument("--only-mc", action="store_true",
                     help="run only the batched Monte Carlo measurement (profiling)")
     return ap.parse_args()
@@ -749,35 +751,48 @@ def run_mc_cfg4(dev, precision, block=32, per_shape=4, total=256):
 
 
 def run_surrogate(dev, steps=200, rows=1 << 17):
-    """Training and inference rates of the surrogate network on synthetic rows."""
+    """Training and inference rates of the surrogate network on synthetic rows,
+    on the tensor-core kernels (the default) and on the FP32 SIMT checker."""
     import torch
     import paper_2506_10526_gb300 as bs
     g = torch.Generator(device=dev).manual_seed(3)
     x = torch.randn((rows, bs.MLP_FEATURES), device=dev, generator=g)
     t = torch.randn((rows,), device=dev, generator=g)
-    net = bs.Surrogate(bs.MLP_FEATURES, 128, seed=1)
-    net.fit_norm(x, t)
-    net.train(x, t, steps=10, batch=8192, lr=1e-3)
-    stream = torch.cuda.current_stream()
-    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-    torch.cuda.synchronize()
-    e[0].record(stream)
-    net.train(x, t, steps=steps, batch=8192, lr=1e-3)
-    e[1].record(stream)
-    e[2].record(stream)
-    for _ in range(10):
-        net.forward(x)
-    e[3].record(stream)
-    torch.cuda.synchronize()
-    tr_ms, inf_ms = e[0].elapsed_time(e[1]), e[2].elapsed_time(e[3]) / 10
-    net.close()
     d, w = bs.MLP_FEATURES, 128
-    fwd = 2.0 * (d * w + w * w + w)  # FLOP per row
-    return {"train_rows_per_s": steps * 8192 / (tr_ms / 1e3),
-            "inference_bins_per_s": rows / (inf_ms / 1e3),
-            "inference_tflops": rows * fwd / (inf_ms / 1e3) / 1e12,
-            "note": "3-layer tanh MLP, width 128, BF16 weights, FP32 SIMT accumulation; "
-                    "training = Adam steps on minibatches of 8192 rows"}
+    fwd = 2.0 * (d * w + w * w + w)  # FLOP per row, forward
+    trn = 2.0 * (2 * d * w + 3 * w * w + 2 * w)  # forward + dz1 + dW1 + dW2 + dw3 per row
+    out = {}
+    for kind in ("tensor", "simt"):
+        net = bs.Surrogate(d, w, seed=1)
+        net.set_kernels(kind)
+        net.fit_norm(x, t)
+        net.train(x, t, steps=10, batch=8192, lr=1e-3)
+        stream = torch.cuda.current_stream()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        nst = steps if kind == "tensor" else steps // 4
+        torch.cuda.synchronize()
+        e[0].record(stream)
+        net.train(x, t, steps=nst, batch=8192, lr=1e-3)
+        e[1].record(stream)
+        e[2].record(stream)
+        for _ in range(10):
+            net.forward(x)
+        e[3].record(stream)
+        torch.cuda.synchronize()
+        tr_ms, inf_ms = e[0].elapsed_time(e[1]), e[2].elapsed_time(e[3]) / 10
+        net.close()
+        pre = "" if kind == "tensor" else "simt_"
+        out[pre + "train_rows_per_s"] = nst * 8192 / (tr_ms / 1e3)
+        out[pre + "train_tflops"] = nst * 8192 * trn / (tr_ms / 1e3) / 1e12
+        out[pre + "inference_bins_per_s"] = rows / (inf_ms / 1e3)
+        out[pre + "inference_tflops"] = rows * fwd / (inf_ms / 1e3) / 1e12
+    out["speedup_inference"] = out["inference_tflops"] / out["simt_inference_tflops"]
+    out["speedup_train"] = out["train_tflops"] / out["simt_train_tflops"]
+    out["note"] = ("3-layer tanh MLP, width 128, BF16 weights; default kernels: BF16 mma.sync "
+                   "(m16n8k16) with activations and gradients split hi + lo, FP32 accumulation; "
+                   "simt_*: the FP32 SIMT checker; training = Adam steps on minibatches of 8192 "
+                   "rows, FLOP counted once per algorithmic product")
+    return out
 
 
 def main():
@@ -789,6 +804,10 @@ def main():
         w["block3"] = args.block3
     if args.impl == "reference":
         run_reference(args, w)
+        return
+    if args.only_surrogate:
+        import torch
+        print(json.dumps({"surrogate": run_surrogate(torch.device("cuda", 0))}), flush=True)
         return
     if args.only_mc:
         import torch

@@ -54,7 +54,7 @@
 extern "C" {
 #endif
 
-#define BS_ABI_VERSION 11
+#define BS_ABI_VERSION 12
 
 typedef struct bs_plan_s *bs_plan;
 
@@ -560,6 +560,12 @@ bs_status bs_mlp_fit_norm(bs_mlp mlp, const float *x_dev, const float *t_dev, in
                           void *cuda_stream);
 /* y_dev[n] = network(x_dev[n][d_in]). */
 bs_status bs_mlp_forward(bs_mlp mlp, const float *x_dev, int n, float *y_dev, void *cuda_stream);
+/* Kernels of the forward, backward and weight-gradient passes: kind 0 = BF16
+ * tensor cores (mma.sync m16n8k16, FP32 accumulation; activations and
+ * gradients split into BF16 hi + lo, weights exact in BF16), the default
+ * for width 128 and d_in <= 64; kind 1 = FP32 SIMT (any shape; the checker).
+ * Errors: BS_ERR_ARG (kind), BS_ERR_UNSUPPORTED (kind 0 for another shape). */
+bs_status bs_mlp_set_kernels(bs_mlp mlp, int kind);
 /* Full-batch loss (mean squared error on the normalised target) and its
  * gradient w.r.t. the weights and biases (first part of the flat vector),
  * copied to the host.  Synchronises. */

@@ -27,7 +27,7 @@ STATUS = {0: "BS_OK", 1: "BS_ERR_ARG", 2: "BS_ERR_NO_DEVICE", 3: "BS_ERR_CUDA", 
 PREC_FP32 = 0
 PREC_SPLIT_BF16 = 1
 PREC_SPLIT_FP16 = 2
-ABI_VERSION = 11     # BS_ABI_VERSION of include/bs.h
+ABI_VERSION = 12     # BS_ABI_VERSION of include/bs.h
 MLP_FEATURES = 45    # BS_MLP_FEATURES of include/bs.h
 
 # every symbol declared in include/bs.h
@@ -41,7 +41,7 @@ EXPORTS = ("bs_abi_version", "bs_plan_create", "bs_plan_destroy", "bs_last_error
            "bs_mc_stats", "bs_mc_tuning", "bs_mc_set_block", "bs_mc_checkpoint",
            "bs_mc_restore",
            "bs_mlp_features", "bs_mlp_create", "bs_mlp_destroy", "bs_mlp_last_error",
-           "bs_mlp_params", "bs_mlp_fit_norm", "bs_mlp_forward", "bs_mlp_grad", "bs_mlp_train",
+           "bs_mlp_params", "bs_mlp_fit_norm", "bs_mlp_forward", "bs_mlp_set_kernels", "bs_mlp_grad", "bs_mlp_train",
            "bs_sky_create", "bs_sky_destroy", "bs_sky_last_error", "bs_sky_generate",
            "bs_counts_noalloc", "bs_measure_peak")
 
@@ -128,6 +128,7 @@ def lib() -> ctypes.CDLL:
             L.bs_mlp_params.argtypes = [P, P, ctypes.c_int64, I]
             L.bs_mlp_fit_norm.argtypes = [P, P, P, I, P]
             L.bs_mlp_forward.argtypes = [P, P, I, P, P]
+            L.bs_mlp_set_kernels.argtypes = [P, I]
             L.bs_mlp_grad.argtypes = [P, P, P, I, P, P, P]
             L.bs_mlp_train.argtypes = [P, P, P, I, I, I, ctypes.c_float, ctypes.c_uint64, P, P]
             for name in EXPORTS:
@@ -710,6 +711,11 @@ class Surrogate:
         self._check(self._L.bs_mlp_forward(self._h, _dptr(x), int(x.shape[0]), _dptr(y),
                                            _stream_ptr(stream)))
         return y
+
+    def set_kernels(self, kind):
+        """bs_mlp_set_kernels: "tensor" (BF16 mma.sync, width 128) or "simt" (FP32)."""
+        k = {"tensor": 0, "simt": 1}[kind]
+        self._check(self._L.bs_mlp_set_kernels(self._h, k))
 
     def grad(self, x, t, stream=None):
         import numpy as np

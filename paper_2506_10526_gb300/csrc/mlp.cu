@@ -13,13 +13,16 @@
 //
 // Kernels: features per bin, column statistics, forward (one thread per row),
 // per-row backward (dz2, dz1), weight gradients (tiled reductions over rows
-// with FP32 atomics), Adam.  Minibatch rows come from a counter-based hash of
+// with FP32 atomics), Adam.  Width 128 runs the forward, backward and weight
+// gradients on the tensor cores instead (mlp_tc.cu); these FP32 SIMT kernels
+// remain for other widths and as the checker (bs_mlp_set_kernels).  Minibatch rows come from a counter-based hash of
 // (seed, step, slot).
 #include <cuda_bf16.h>
 
 #include <cmath>
 #include <vector>
 
+#include "mlp_internal.h"
 #include "plan_internal.h"
 
 using namespace bsi;
@@ -27,14 +30,6 @@ using namespace bsi;
 namespace {
 
 constexpr int kMaxD = 64, kMaxW = 128, kRows = 128;
-
-struct MlpDev {
-  int d, w;
-  float *p;       // master FP32 params, flat: W1 [w][d] | b1 | W2 [w][w] | b2 | w3 | b3
-  float *g;       // gradient, same layout
-  float *m, *v;   // Adam moments
-  float *norm;    // mu_x [d] | sd_x [d] | mu_y | sd_y
-};
 
 __device__ __forceinline__ float bf(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
@@ -305,6 +300,7 @@ struct bs_mlp_s {
   float *store = nullptr, *bw = nullptr, *loss = nullptr;
   int cap = 0;  // rows of the training scratch
   int step = 0;
+  bool tc = false;  // tensor-core kernels (width 128), else FP32 SIMT
   std::string err = "no error";
 };
 
@@ -339,6 +335,12 @@ bs_status ensure_scratch(bs_mlp m, int rows) {
 bs_status grad_batch(bs_mlp m, const float *x, const float *t, int n, const int *idx, int nrows,
                      cudaStream_t s) {
   const int d = m->dev.d, w = m->dev.w;
+  if (m->tc) {
+    ML_CUDA(mlp_tc_forward(m->dev, x, n, idx, nrows, nullptr, m->store, s));
+    ML_CUDA(mlp_tc_backward_rows(m->dev, t, idx, nrows, m->store, m->bw, m->loss, s));
+    ML_CUDA(mlp_tc_wgrad(m->dev, nrows, m->store, m->bw, s));
+    return BS_OK;
+  }
   const int blocks = (nrows + kRows - 1) / kRows;
   k_mlp_forward<<<blocks, kRows, fwd_smem(d, w), s>>>(m->dev, x, n, idx, nrows, nullptr, m->store);
   ML_CUDA(cudaGetLastError());
@@ -403,6 +405,7 @@ bs_status bs_mlp_create(int d_in, int width, uint64_t seed, bs_mlp *out) {
   cudaMemset(m->dev.m, 0, np * 4);
   cudaMemset(m->dev.v, 0, np * 4);
   cudaMemcpy(m->dev.norm, norm.data(), norm.size() * 4, cudaMemcpyHostToDevice);
+  m->tc = mlp_tc_supported(d_in, width);
   if (smem_optin_once<k_mlp_forward>() != cudaSuccess ||
       smem_optin_once<k_mlp_backward_rows>() != cudaSuccess) {
     cudaGetLastError();
@@ -462,9 +465,22 @@ bs_status bs_mlp_forward(bs_mlp m, const float *x_dev, int n, float *y_dev, void
   if (!m || !x_dev || !y_dev || n < 0) return BS_ERR_ARG;
   if (n == 0) return BS_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (m->tc) {
+    ML_CUDA(mlp_tc_forward(m->dev, x_dev, n, nullptr, n, y_dev, nullptr, s));
+    return BS_OK;
+  }
   k_mlp_forward<<<(n + kRows - 1) / kRows, kRows, fwd_smem(m->dev.d, m->dev.w), s>>>(
       m->dev, x_dev, n, nullptr, n, y_dev, nullptr);
   ML_CUDA(cudaGetLastError());
+  return BS_OK;
+}
+
+bs_status bs_mlp_set_kernels(bs_mlp m, int kind) {
+  BS_NVTX("bs_mlp_set_kernels");
+  if (!m || (kind != 0 && kind != 1)) return BS_ERR_ARG;
+  if (kind == 0 && !mlp_tc_supported(m->dev.d, m->dev.w))
+    return lfail(m, BS_ERR_UNSUPPORTED, "tensor-core kernels need width 128 and d_in <= 64");
+  m->tc = kind == 0;
   return BS_OK;
 }
 

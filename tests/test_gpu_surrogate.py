@@ -3,8 +3,10 @@
 * forward and gradient of the network against the FP64 reference
   (oracle/mlp.py) evaluated with the same BF16-rounded weights;
 * the 45 bin features against a numpy restatement of their definition;
-* accuracy: trained on Monte Carlo variances from the batched path (skies
-  drawn by the GPU generator) on training flag masks -- a coarse-band family
+* the tensor-core kernels against the FP32 SIMT checker;
+* accuracy: trained on Monte Carlo variances from 4096 realisations of the
+  batched path (skies drawn by the GPU generator, tensor-core training) on
+  training flag masks -- a coarse-band family
   (edge widths 0-3, centre on/off) plus random masks -- the predicted sigma
   of every 3D-bispectrum bin on held-out family masks is within 10% (median)
   of a 1024-realisation Monte Carlo, and beats what a 16-realisation Monte
@@ -31,14 +33,19 @@ def _torch():
     return torch
 
 
-def test_forward_and_gradient_match_fp64_reference():
+@pytest.mark.parametrize("kernels,d", [("tensor", None), ("simt", None), ("tensor", 20),
+                                       ("tensor", 64)])
+def test_forward_and_gradient_match_fp64_reference(kernels, d):
+    """Both kernel sets (BF16 tensor cores with hi / lo activations, FP32 SIMT),
+    several input widths (the tensor-core input padding), ragged row counts."""
     torch = _torch()
     import paper_2506_10526_gb300 as bs
-    d, w, n = bs.MLP_FEATURES, 128, 3000
+    d, w, n = d or bs.MLP_FEATURES, 128, 3000
     r = np.random.default_rng(11)
     x = r.standard_normal((n, d)).astype(np.float32) * 2 + 0.5
     t = (np.sin(x[:, 0]) + 0.3 * x[:, 1] * x[:, 2]).astype(np.float32)
     net = bs.Surrogate(d, w, seed=5)
+    net.set_kernels(kernels)
     xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
     net.fit_norm(xd, td)
     net.train(xd, td, steps=50, batch=512, lr=1e-3)  # move away from the initial point
@@ -55,6 +62,37 @@ def test_forward_and_gradient_match_fp64_reference():
     assert loss == pytest.approx(loss_ref, rel=1e-4)
     np.testing.assert_allclose(g, g_ref, rtol=0, atol=2e-4 * np.abs(g_ref).max())
     net.close()
+
+
+def test_tensor_and_simt_kernels_agree():
+    """The tensor-core forward and gradient against the FP32 SIMT checker on
+    the same network: forward to 2e-5 of the output scale, gradients to 2e-4
+    of the largest component; training steps with each stay close."""
+    torch = _torch()
+    import paper_2506_10526_gb300 as bs
+    d, n = bs.MLP_FEATURES, 5003
+    r = np.random.default_rng(21)
+    x = torch.from_numpy(r.standard_normal((n, d)).astype(np.float32)).cuda()
+    t = torch.from_numpy(r.standard_normal(n).astype(np.float32)).cuda()
+    a, b = bs.Surrogate(d, 128, seed=9), bs.Surrogate(d, 128, seed=9)
+    a.set_kernels("tensor")
+    b.set_kernels("simt")
+    for net in (a, b):
+        net.fit_norm(x, t)
+    ya, yb = a.forward(x).cpu().numpy(), b.forward(x).cpu().numpy()
+    np.testing.assert_allclose(ya, yb, rtol=0, atol=2e-5 * np.abs(yb).max())
+    (la, ga), (lb, gb) = a.grad(x, t), b.grad(x, t)
+    assert la == pytest.approx(lb, rel=1e-5)
+    np.testing.assert_allclose(ga, gb, rtol=0, atol=2e-4 * np.abs(gb).max())
+    la = a.train(x, t, steps=20, batch=1024, lr=1e-3)
+    lb = b.train(x, t, steps=20, batch=1024, lr=1e-3)
+    assert la == pytest.approx(lb, rel=1e-2)
+    pa, pb = a.params(), b.params()
+    assert np.abs(pa - pb).max() < 1e-3 * np.abs(pb).max()
+    with pytest.raises(bs.BsError):
+        bs.Surrogate(d, 64, seed=1).set_kernels("tensor")
+    a.close()
+    b.close()
 
 
 def _sampling_features(flags):
@@ -159,7 +197,7 @@ def test_surrogate_error_bars_on_held_out_masks():
     masks = _masks()
     perm = np.random.default_rng(5).permutation(len(masks))
     held, train = masks[perm[:4]], np.concatenate([masks[perm[4:28]], _random_masks(40, 77)])
-    var_tr = _mc_variance(train, 1024, 100000)
+    var_tr = _mc_variance(train, 4096, 100000)  # training targets from 4096 realisations
     var_ho = _mc_variance(held, 1024, 900000)
     var_16 = _mc_variance(held, 16, 500000, batch=16)
     plan = bs.Plan(NT, NC, EDGES)
