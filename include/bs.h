@@ -142,6 +142,21 @@ typedef struct {
                                 ensembles take chan_sampling = 0. */
 } bs_plan_desc;
 
+/* ---- checked build ---------------------------------------------------------
+ * A library built with -DBS_CHECKED (libbs_checked.so) checks the indices of
+ * the kernels' main global accesses against the extents of their buffers; a
+ * violation is counted, the first one recorded, and the access skipped
+ * instead of faulting.  bs_checked_build: 1 in such a library, else 0.
+ * bs_checked_status: out_host[4] = {violations since the last reset, site of
+ * the first, its index, the extent it was checked against}; reset != 0
+ * clears the counters.  Synchronises.  bs_checked_selftest: one guarded
+ * increment of element idx of an internal n-element buffer (1 <= n <= 4096),
+ * so that a test can see an out-of-range index reported (site 0x7fff).  Both
+ * return BS_ERR_UNSUPPORTED in an ordinary build. */
+int bs_checked_build(void);
+bs_status bs_checked_status(int reset, uint64_t *out_host);
+bs_status bs_checked_selftest(int64_t n, int64_t idx, void *cuda_stream);
+
 /* ABI version this library was built with (BS_ABI_VERSION). */
 int bs_abi_version(void);
 

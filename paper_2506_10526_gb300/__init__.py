@@ -19,6 +19,13 @@ import threading
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libbs.so")
+# BS_LIBRARY=checked loads the -DBS_CHECKED build (device bounds checks that
+# record a violation instead of faulting; build.build(checked=True) makes it)
+LIB_CHECKED_PATH = os.path.join(HERE, "_build_checked", "libbs_checked.so")
+
+
+def _lib_path() -> str:
+    return LIB_CHECKED_PATH if os.environ.get("BS_LIBRARY") == "checked" else LIB_PATH
 
 BS_OK = 0
 STATUS = {0: "BS_OK", 1: "BS_ERR_ARG", 2: "BS_ERR_NO_DEVICE", 3: "BS_ERR_CUDA", 4: "BS_ERR_OOM",
@@ -43,7 +50,8 @@ EXPORTS = ("bs_abi_version", "bs_plan_create", "bs_plan_destroy", "bs_last_error
            "bs_mlp_features", "bs_mlp_create", "bs_mlp_destroy", "bs_mlp_last_error",
            "bs_mlp_params", "bs_mlp_fit_norm", "bs_mlp_forward", "bs_mlp_set_kernels", "bs_mlp_grad", "bs_mlp_train",
            "bs_sky_create", "bs_sky_destroy", "bs_sky_last_error", "bs_sky_generate",
-           "bs_counts_noalloc", "bs_measure_peak")
+           "bs_counts_noalloc", "bs_measure_peak", "bs_checked_build", "bs_checked_status",
+           "bs_checked_selftest")
 
 _lib = None
 _lock = threading.Lock()
@@ -70,10 +78,11 @@ def lib() -> ctypes.CDLL:
     global _lib
     with _lock:
         if _lib is None:
-            if not os.path.exists(LIB_PATH):
-                raise RuntimeError(f"libbs.so not built ({LIB_PATH}); run "
+            path = _lib_path()
+            if not os.path.exists(path):
+                raise RuntimeError(f"{os.path.basename(path)} not built ({path}); run "
                                    "`python -c 'import __graft_entry__ as g; g.build()'`")
-            L = ctypes.CDLL(LIB_PATH)
+            L = ctypes.CDLL(path)
             P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
             L.bs_abi_version.restype = I
             L.bs_plan_create.argtypes = [ctypes.POINTER(PlanDesc), ctypes.POINTER(P)]
@@ -95,6 +104,10 @@ def lib() -> ctypes.CDLL:
             L.bs_delta_import.argtypes = [P, P, P, I, P]
             L.bs_counts_noalloc.argtypes = [I, I, P, P, P, P]
             L.bs_measure_peak.argtypes = [I, I, P, P]
+            L.bs_checked_build.restype = I
+            L.bs_checked_build.argtypes = []
+            L.bs_checked_status.argtypes = [I, P]
+            L.bs_checked_selftest.argtypes = [ctypes.c_int64, ctypes.c_int64, P]
             L.bs_plan_ring_umean.argtypes = [P, P]
             L.bs_bs_monopole.argtypes = [P, P, P, P, P, I, I, I, D, D, D, P, P, P]
             L.bs_bs_multipoles.argtypes = [P, P, P, P, P, I, I, I, I, P, P, P]
@@ -132,7 +145,7 @@ def lib() -> ctypes.CDLL:
             L.bs_mlp_grad.argtypes = [P, P, P, I, P, P, P]
             L.bs_mlp_train.argtypes = [P, P, P, I, I, I, ctypes.c_float, ctypes.c_uint64, P, P]
             for name in EXPORTS:
-                if name not in ("bs_abi_version", "bs_last_error", "bs_mc_last_error",
+                if name not in ("bs_abi_version", "bs_last_error", "bs_mc_last_error", "bs_checked_build",
                                 "bs_mlp_last_error", "bs_sky_last_error"):
                     getattr(L, name).restype = I
             _lib = L
@@ -744,3 +757,27 @@ class Surrogate:
             self.close()
         except Exception:
             pass
+
+
+def checked_build() -> bool:
+    """bs_checked_build: whether the loaded library is the -DBS_CHECKED build."""
+    return bool(lib().bs_checked_build())
+
+
+def checked_status(reset: bool = True):
+    """bs_checked_status: {"violations", "site", "index", "extent"} since the
+    last reset (checked build only)."""
+    import numpy as np
+    out = np.zeros(4, np.uint64)
+    st = lib().bs_checked_status(int(bool(reset)), out.ctypes.data_as(ctypes.c_void_p))
+    if st != BS_OK:
+        raise BsError(st, "bs_checked_status failed")
+    return {"violations": int(out[0]), "site": int(out[1]),
+            "index": int(out[2].astype(np.int64)), "extent": int(out[3])}
+
+
+def checked_selftest(n: int, idx: int, stream=None):
+    """bs_checked_selftest: one guarded access to element idx of an n-element buffer."""
+    st = lib().bs_checked_selftest(int(n), int(idx), _stream_ptr(stream))
+    if st != BS_OK:
+        raise BsError(st, "bs_checked_selftest failed")

@@ -15,6 +15,41 @@
 
 namespace bsi {
 
+// ---- checked build (-DBS_CHECKED) -------------------------------------------
+// BS_CHK(i, n, site) is true when 0 <= i < n.  In a checked build a false
+// check also records the violation in the translation unit's device error
+// word (count, first site and index, its bound) and the caller skips the
+// access, so an index error is reported instead of faulting; bs_checked_status
+// reads and clears the words of every translation unit.  In an ordinary build
+// the check is the constant true and compiles away.
+#ifdef BS_CHECKED
+static __device__ unsigned long long g_chk_word[3];
+__device__ __forceinline__ bool chk_index(long long i, long long n, int site) {
+  if (i >= 0 && i < n) return true;
+  if (atomicAdd(&g_chk_word[0], 1ull) == 0ull) {
+    g_chk_word[1] = ((unsigned long long)(unsigned)site << 48) |
+                    ((unsigned long long)i & 0xffffffffffffull);
+    g_chk_word[2] = (unsigned long long)n;
+  }
+  return false;
+}
+#define BS_CHK(i, n, site) ::bsi::chk_index((long long)(i), (long long)(n), (site))
+// reads (and with reset, clears) one translation unit's word
+using ChkReader = cudaError_t (*)(unsigned long long *w, bool reset);
+void register_chk_reader(ChkReader r);
+static cudaError_t chk_read_tu(unsigned long long *w, bool reset) {
+  cudaError_t e = cudaMemcpyFromSymbol(w, g_chk_word, sizeof(g_chk_word));
+  if (e == cudaSuccess && reset) {
+    const unsigned long long z[3] = {0, 0, 0};
+    e = cudaMemcpyToSymbol(g_chk_word, z, sizeof(z));
+  }
+  return e;
+}
+static const bool g_chk_registered = (register_chk_reader(&chk_read_tu), true);
+#else
+#define BS_CHK(i, n, site) true
+#endif
+
 // Mixed-radix factorisation of a transform length (radices 4, 2, 3, 5).
 struct Radices {
   int n = 0;

@@ -769,12 +769,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
             const long long o = (long long)b * G.dsum_bstride +
                                 ((long long)ri.z * n2 + (nu1 - ri.w + G.nc - 1)) * n2 +
                                 (nu2 - ri.w + G.nc - 1);
-            atomicAdd(G.dsum + o, (double)sv * rsc);
+            if (BS_CHK(o, (long long)G.batch * G.dsum_bstride, 31))
+              atomicAdd(G.dsum + o, (double)sv * rsc);
           }
           if (G.out_full) {
             const long long o = (long long)b * G.full_bstride +
                                 (((long long)ri.z * G.nc + nu1) * G.nc + nu2) * G.nc + ri.w;
-            atomicAdd(G.out_full + o, (double)sv * tn);
+            if (BS_CHK(o, (long long)G.batch * G.full_bstride, 34))
+              atomicAdd(G.out_full + o, (double)sv * tn);
           }
         }
       }
@@ -804,7 +806,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
             for (int e2 = e2lo + lane; e2 <= e2hi; e2 += 32) {
               const float v = rs[(r - e2) * E + e2];
               if (v == 0.f) continue;
-              atomicAdd(plane + row + (e2 + d2base), F16 ? (double)v * sc : (double)v);
+              if (BS_CHK(r + d1base, n2, 32) && BS_CHK(e2 + d2base, n2, 33))
+                atomicAdd(plane + row + (e2 + d2base), F16 ? (double)v * sc : (double)v);
             }
           }
         }

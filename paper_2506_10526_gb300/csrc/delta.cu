@@ -48,6 +48,7 @@ __global__ void k_delta_norm(const double *__restrict__ dsum, const long long *_
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < half;
        t += (long long)gridDim.x * blockDim.x) {
     const long long j = plane - 1 - t;
+    if (!BS_CHK(j, plane, 21)) continue;
     long long c = nnu[t];
     if (j != t) c += nnu[j];
     double v = nan;

@@ -92,7 +92,8 @@ __global__ void __launch_bounds__(kDelThreads) k_bs3d_rows_reg(
         const int i2 = mp + N - 1, j2 = n2s - 1 - i2;
         da[q] = 0.0;
         db[q] = 0.0;
-        if (ri[q] != 0.f) {
+        if (ri[q] != 0.f && BS_CHK((long long)i1 * n2s + i2, (long long)n2s * n2s, 11) &&
+            BS_CHK((long long)j1 * n2s + j2, (long long)n2s * n2s, 11)) {
           da[q] = ds[(long long)i1 * n2s + i2];
           if (j1 != i1 || j2 != i2) db[q] = ds[(long long)j1 * n2s + j2];
         }
@@ -128,7 +129,8 @@ __global__ void __launch_bounds__(kDelThreads) k_bs3d_rows_reg(
     // the input is real: only k <= N/2 is kept (the cols pass mirrors the rest)
 #pragma unroll
     for (int k2 = 0; k2 < N2; ++k2)
-      if (k1 + N1 * k2 <= N / 2) row[k1 + N1 * k2] = v[k2];
+      if (k1 + N1 * k2 <= N / 2 && BS_CHK((long long)nidx * N + k1 + N1 * k2, (long long)N * N, 12))
+        row[k1 + N1 * k2] = v[k2];
   }
 }
 
@@ -176,7 +178,9 @@ __global__ void __launch_bounds__(kDelThreads) k_bs3d_cols_reg(
 #pragma unroll
     for (int n1 = 0; n1 < N1; ++n1) {
       const int n = n2 + N2 * n1;
-      v[n1] = (fl[n] && c < ncol) ? tb[(long long)n * N + c] : make_float2(0.f, 0.f);
+      v[n1] = (fl[n] && c < ncol && BS_CHK((long long)n * N + k0 + c, (long long)N * N, 13))
+                  ? tb[(long long)n * N + c]
+                  : make_float2(0.f, 0.f);
     }
     freg::dft<N1, -1>(v);
 #pragma unroll
@@ -204,8 +208,11 @@ __global__ void __launch_bounds__(kDelThreads) k_bs3d_cols_reg(
       for (int k2 = 0; k2 < N2; ++k2) {
         const int a = k1 + N1 * k2;
         const double val = f32_to_f64_pow2(v[k2].x * scale_m, scale_e);
-        oc[(long long)centred(a) * N] = val;
-        if (mir) om[(long long)centred((N - a) % N) * N] = val;
+        if (BS_CHK((long long)centred(a) * N + centred(bcol), (long long)N * N, 14))
+          oc[(long long)centred(a) * N] = val;
+        if (mir && BS_CHK((long long)centred((N - a) % N) * N + centred((N - bcol) % N),
+                          (long long)N * N, 14))
+          om[(long long)centred((N - a) % N) * N] = val;
       }
     }
   }

@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(256) k_counts(int nt, int nb, const int8_t *__
       const int r3 = lab[(v3 + h) * nt + (u3 + h)];
       if (r3 < 0) continue;
       const int t = tof[(r1 * nb + r2) * nb + r3];
-      if (t >= 0) atomicAdd(&cnt[t], 1u);
+      if (t >= 0 && BS_CHK(t, ntrip, 51)) atomicAdd(&cnt[t], 1u);
     }
   }
   __syncthreads();

@@ -85,6 +85,7 @@ __global__ void __launch_bounds__(kRegThreads) k_colpass_reg(
   }
   __syncthreads();
   const int ncols = min(UB, g.UC - u0);
+  const long long gtot = (long long)g.batch * g.nslot * g.nc * N * g.UC;  // G extent
   for (int m = 0; m < g.nb; ++m) {
     const int ue = uext[m];
     const int slot = g.slot_of[m];
@@ -102,11 +103,11 @@ __global__ void __launch_bounds__(kRegThreads) k_colpass_reg(
         const int va = y, vb2 = y - N;
         if (va < h) {
           const int t = (va + h) * UB + c;
-          if (lt[t] == m) acc = xt[t];
+          if (BS_CHK(t, nt * UB, 1) && lt[t] == m) acc = xt[t];
         }
         if (vb2 >= -h) {
           const int t = (vb2 + h) * UB + c;
-          if (lt[t] == m) acc = freg::add(acc, xt[t]);
+          if (BS_CHK(t, nt * UB, 1) && lt[t] == m) acc = freg::add(acc, xt[t]);
         }
         v[n1] = acc;
       }
@@ -129,7 +130,10 @@ __global__ void __launch_bounds__(kRegThreads) k_colpass_reg(
       freg::dft<N2, 1>(v);
       if (c < ncols) {
 #pragma unroll
-        for (int k2 = 0; k2 < N2; ++k2) Gm[(long long)(k1 + N1 * k2) * g.UC + u0 + c] = v[k2];
+        for (int k2 = 0; k2 < N2; ++k2) {
+          const long long o = (long long)(k1 + N1 * k2) * g.UC + u0 + c;
+          if (BS_CHK(o + (Gm - G), gtot, 2)) Gm[o] = v[k2];
+        }
       }
     }
     __syncthreads();
@@ -173,10 +177,12 @@ __global__ void __launch_bounds__(kRegThreads) k_rowpass_reg(
     key_s[r] = key;
   }
   __syncthreads();
+  const long long gtot = (long long)g.batch * g.nslot * g.nc * N * g.UC;  // G extent
   // pass 1: (pair, n2) items, n2 fastest
   for (int it = threadIdx.x; it < RPB * N2; it += blockDim.x) {
     const int r = it / N2, n2 = it - r * N2;
-    const int ue = ue_s[r];
+    const int ue0 = ue_s[r];  // reads G rows 2p, 2p + 1 at columns below ue0
+    const int ue = (ue0 == 0 || BS_CHK(gofs[r] + g.UC + ue0 - 1, gtot, 3)) ? ue0 : 0;
     const float2 *ga = G + gofs[r];
     const float2 *gc = ga + g.UC;
     float2 v[N1];
@@ -226,6 +232,7 @@ __global__ void __launch_bounds__(kRegThreads) k_rowpass_reg(
       for (int k2 = 0; k2 < N2; ++k2) {
         const int x = k1 + N1 * k2;
         const float a = v[k2].x, c = v[k2].y;
+        if (!BS_CHK(o1 + x, 2 * npairs * N, 4)) continue;
         F[o0 + x] = a;
         F[o1 + x] = c;
         amax = max(amax, __float_as_uint(fmaxf(fabsf(a), fabsf(c))));

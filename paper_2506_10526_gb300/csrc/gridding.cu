@@ -44,6 +44,8 @@ __global__ void k_grid_vis(const double *__restrict__ uv, const float2 *__restri
     const float2 v = vis[iv_in];
     const long long o = (long long)(c / avg) * plane;
     const long long g = o + (iv + h) * nt + (iu + h), gm = o + (h - iv) * nt + (h - iu);
+    const long long ntot = (long long)(nin / avg) * plane;  // nin = avg * output channels
+    if (!BS_CHK(g, ntot, 61) || !BS_CHK(gm, ntot, 61)) continue;
     atomicAdd(&vg[g].x, v.x);
     atomicAdd(&vg[g].y, v.y);
     atomicAdd(ng + g, 1.0f);

@@ -193,6 +193,7 @@ __global__ void __launch_bounds__(kThreads) k_mono_sum(const MonoArgs a,
     for (int u = 0; u < kSumUnroll; ++u) {
       const int e = g0 + 32 * u + lane;
       q[u] = e < w1 ? (int)bp[e] : -1;
+      if (q[u] >= 0 && !BS_CHK(q[u], a.nbin, 41)) q[u] = -1;  // a bin outside the histogram
 #pragma unroll
       for (int b = 0; b < NB; ++b)
         v[u][b] = (!a.model && b < nb && e < w1) ? __ldg(vb + (long long)b * a.bstride + e) : 0.0;
@@ -308,6 +309,7 @@ __global__ void __launch_bounds__(kThreads) k_mono_multipole(const MonoArgs a,
     if (e < w1) {
       const int ia = e / a.nc, ib = e - ia * a.nc;
       q = (skip0 && (ia == 0 || ib == 0)) ? -1 : (int)bp[e];
+      if (q >= 0 && !BS_CHK(q, a.nbin, 42)) q = -1;
       if (q >= 0) {
         const double za = a.kpar64[ia], zb = a.kpar64[ib], zc = -__dadd_rn(za, zb);
         const double s1 = __dadd_rn(pi2, __dmul_rn(za, za)), s2 = __dadd_rn(pj2, __dmul_rn(zb, zb)),
