@@ -99,6 +99,11 @@ def parse():
                     help="skip the batched Monte Carlo and surrogate measurements")
     ap.add_argument("--only-surrogate", action="store_true",
                     help="run only the surrogate network measurement (profiling)")
+    ap.add_argument("--only-mc-cfg4", type=int, default=None, metavar="SHAPE",
+                    help="run only the batched Monte Carlo configuration, on one of its "
+                         "shapes (index into the drawn shapes; profiling)")
+    ap.add_argument("--cfg4-total", type=int, default=256,
+                    help="realisations of the batched Monte Carlo configuration")
     ap.add_argument("--only-mc", action="store_true",
                     help="run only the batched Monte Carlo measurement (profiling)")
     return ap.parse_args()
@@ -669,7 +674,7 @@ def cfg4_shapes(seed=4000, n=8):
             for _ in range(n)]
 
 
-def run_mc_cfg4(dev, precision, block=32, per_shape=4, total=256):
+def run_mc_cfg4(dev, precision, block=32, per_shape=4, total=256, only_shape=None):
     """The batched Monte Carlo configuration: `total` realisations of uneven
     shapes (cfg4_shapes) through graph-replayed persistent launches, with a
     declared subset of the tiles of every realisation: its channel block
@@ -682,6 +687,8 @@ def run_mc_cfg4(dev, precision, block=32, per_shape=4, total=256):
     import paper_2506_10526_gb300 as bs
     import synth
     shapes = cfg4_shapes()
+    if only_shape is not None:  # profiling: one of the shapes
+        shapes = [shapes[only_shape]]
     specs, gens, skies, bufs = [], [], [], []
     for nt, nc, nb in shapes:
         e = list(synth.edges_log(nb, 4.41 * nt / 256, nt / 2))
@@ -808,6 +815,14 @@ def main():
     if args.only_surrogate:
         import torch
         print(json.dumps({"surrogate": run_surrogate(torch.device("cuda", 0))}), flush=True)
+        return
+    if args.only_mc_cfg4 is not None:
+        import torch
+        import paper_2506_10526_gb300 as bs
+        prec = bs.PREC_SPLIT_FP16 if args.precision == "split_fp16" else bs.PREC_SPLIT_BF16
+        print(json.dumps({"mc_cfg4": run_mc_cfg4(torch.device("cuda", 0), prec,
+                                                 total=args.cfg4_total,
+                                                 only_shape=args.only_mc_cfg4)}), flush=True)
         return
     if args.only_mc:
         import torch

@@ -428,6 +428,44 @@ void accumulate_block_nnu(bs_plan p, const int *blk) {
   }
 }
 
+bs_status upload_staged(bs_plan p, cudaStream_t s, const StagedUpload *u, int n) {
+  size_t total = 0;
+  for (int k = 0; k < n; ++k) total += (u[k].bytes + 255) / 256 * 256;
+  if (p->stage_pending) {  // the previous uploads from the buffer are done
+    BS_CUDA(cudaEventSynchronize(p->stage_ev));
+    p->stage_pending = false;
+  }
+  if (!p->stage_ev) BS_CUDA(cudaEventCreateWithFlags(&p->stage_ev, cudaEventDisableTiming));
+  if (total > p->h_stage_cap) {
+    if (p->h_stage) cudaFreeHost(p->h_stage);
+    p->h_stage = nullptr;
+    p->h_stage_cap = 0;
+    void *h = nullptr;
+    if (cudaHostAlloc(&h, total + total / 4, cudaHostAllocDefault) == cudaSuccess) {
+      p->h_stage = static_cast<unsigned char *>(h);
+      p->h_stage_cap = total + total / 4;
+    } else {
+      cudaGetLastError();
+    }
+  }
+  if (!p->h_stage) {  // no pinned memory: ordinary (host-synchronous) copies
+    for (int k = 0; k < n; ++k)
+      if (u[k].bytes)
+        BS_CUDA(cudaMemcpyAsync(u[k].dst, u[k].src, u[k].bytes, cudaMemcpyHostToDevice, s));
+    return BS_OK;
+  }
+  size_t off = 0;
+  for (int k = 0; k < n; ++k) {
+    if (!u[k].bytes) continue;
+    std::memcpy(p->h_stage + off, u[k].src, u[k].bytes);
+    BS_CUDA(cudaMemcpyAsync(u[k].dst, p->h_stage + off, u[k].bytes, cudaMemcpyHostToDevice, s));
+    off += (u[k].bytes + 255) / 256 * 256;
+  }
+  BS_CUDA(cudaEventRecord(p->stage_ev, s));
+  p->stage_pending = true;
+  return BS_OK;
+}
+
 bs_status upload_nnu(bs_plan p, cudaStream_t s) {
   if (!p->nnu_dirty) return BS_OK;
   BS_CUDA(cudaMemcpyAsync(p->at<long long>(p->L.nnu), p->nnu.data(),
@@ -564,12 +602,12 @@ bs_status mabs_tc(bs_plan p, const int *blk, double *out_full, int accumulate, c
   if (p->h_tctiles.empty()) return BS_OK;
   if (p->h_tctiles.size() > p->max_tctiles || p->h_cols.size() > p->max_cols)
     return fail(p, BS_ERR_UNSUPPORTED, "tensor-core tile list exceeds the plan's capacity");
-  BS_CUDA(cudaMemcpyAsync(p->at<ColEntry>(L.cols), p->h_cols.data(),
-                          p->h_cols.size() * sizeof(ColEntry), cudaMemcpyHostToDevice, s));
-  BS_CUDA(cudaMemcpyAsync(p->at<TcTile>(L.tctiles), p->h_tctiles.data(),
-                          p->h_tctiles.size() * sizeof(TcTile), cudaMemcpyHostToDevice, s));
-  BS_CUDA(cudaMemcpyAsync(p->at<TcGroup>(L.tcgroup), p->h_groups.data(),
-                          p->h_groups.size() * sizeof(TcGroup), cudaMemcpyHostToDevice, s));
+  const StagedUpload up[3] = {
+      {p->at<ColEntry>(L.cols), p->h_cols.data(), p->h_cols.size() * sizeof(ColEntry)},
+      {p->at<TcTile>(L.tctiles), p->h_tctiles.data(), p->h_tctiles.size() * sizeof(TcTile)},
+      {p->at<TcGroup>(L.tcgroup), p->h_groups.data(), p->h_groups.size() * sizeof(TcGroup)}};
+  st = upload_staged(p, s, up, 3);
+  if (st != BS_OK) return st;
   TcArgs a{};
   a.groups = p->at<TcGroup>(L.tcgroup);
   a.maps = p->at<unsigned char>(L.maps);

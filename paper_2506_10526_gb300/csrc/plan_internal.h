@@ -93,8 +93,17 @@ struct bs_plan_s {
   // (read after a stream sync, with no copy engine involved)
   int *err_host = nullptr, *err_dev = nullptr;
   bool err_pending = false;  // a contraction ran since the last check
+  // pinned staging of the per-call work lists (tile and column lists), so that
+  // their uploads are asynchronous; stage_ev marks the last upload from it
+  unsigned char *h_stage = nullptr;
+  size_t h_stage_cap = 0;
+  cudaEvent_t stage_ev = nullptr;
+  bool stage_pending = false;
   ~bs_plan_s() {
     if (err_host) cudaFreeHost(err_host);
+    if (stage_pending && stage_ev) cudaEventSynchronize(stage_ev);
+    if (h_stage) cudaFreeHost(h_stage);
+    if (stage_ev) cudaEventDestroy(stage_ev);
   }
   std::string err = "no error";
   // workspace
@@ -131,6 +140,16 @@ void accumulate_block_nnu(bs_plan p, const int *blk);
 void add_block_sampling(int nc, const std::vector<uint8_t> &valid, const int *blk,
                         long long *plane);
 bs_status upload_nnu(bs_plan p, cudaStream_t s);
+// Host-to-device uploads of per-call work lists through the plan's pinned
+// staging buffer (asynchronous; the buffer is reused once the previous
+// uploads from it have completed).  Falls back to ordinary copies when
+// pinned memory cannot be had.
+struct StagedUpload {
+  void *dst;
+  const void *src;
+  size_t bytes;
+};
+bs_status upload_staged(bs_plan p, cudaStream_t s, const StagedUpload *u, int n);
 // Append the tensor-core work of one channel block of plan p (all
 // realisations): one shape group per image level, numbered from group_base.
 // Column entries are appended to cols, tiles to tiles (col_off relative to
