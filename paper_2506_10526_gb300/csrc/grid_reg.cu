@@ -5,9 +5,10 @@
 // outputs) as grid.cu, with one shared-memory exchange per transform.
 //
 // colpass: CTA = (UB = 16 consecutive u columns, channel, realisation), all
-//   rings in turn.  Threads take columns fastest, so the masked-visibility
-//   tile reads, the exchange tile and the G stores (u fastest) are all
-//   consecutive across a warp.
+//   rings in turn.  Threads take columns fastest, so the visibility, label and
+//   weight reads (through L1: each ring re-reads the channel's 16-column
+//   tile), the exchange tile and the G stores (u fastest) are all consecutive
+//   across a warp.  Only the exchange tile is in shared memory.
 // rowpass: CTA = RPB consecutive row pairs of the flattened
 //   [realisation][field][pair] order (pairs of several fields for small
 //   sides).  Pass 1 reads G straight from global memory (the Hermitian mirror
@@ -54,38 +55,29 @@ __global__ void __launch_bounds__(kRegThreads) k_colpass_reg(
   if (!valid[nu]) return;  // fields of a flagged channel are written as zeros by rowpass
   float2 *tw2 = reinterpret_cast<float2 *>(smem_raw);  // [N1][N2]
   float2 *Y = tw2 + N;                                   // [N1][N2][UB]
-  float2 *xt = Y + N * UB;                               // [nt][UB]
-  int8_t *lt = reinterpret_cast<int8_t *>(xt + nt * UB);  // [nt][UB]
   for (int t = threadIdx.x; t < N; t += blockDim.x) {
     const int k1 = t / N2, n2 = t - k1 * N2;
     tw2[t] = twM[(n2 * k1) % N];
   }
-  const float2 *vb = vis + ((long long)b * g.nc + nu) * (long long)nt * nt;
-  for (int t = threadIdx.x; t < nt * UB; t += blockDim.x) {
-    const int iv = t / UB, c = t - iv * UB;
-    const int u = u0 + c;
-    float2 x = make_float2(0.f, 0.f);
-    int8_t lab = -1;
-    if (u < h) {
-      const int cell = iv * nt + (u + h);
-      lab = label[cell];
-      if (lab >= 0) {
-        const float n = ngrid ? ngrid[cell] : 1.0f;
-        if (n > 0.f) {
-          const float w = 1.0f / n;
-          const float2 v = vb[cell];
-          x = make_float2(w * v.x, w * v.y);
-        } else {
-          lab = -1;
-        }
-      }
-    }
-    xt[t] = x;
-    lt[t] = lab;
-  }
   __syncthreads();
+  const float2 *vb = vis + ((long long)b * g.nc + nu) * (long long)nt * nt;
   const int ncols = min(UB, g.UC - u0);
   const long long gtot = (long long)g.batch * g.nslot * g.nc * N * g.UC;  // G extent
+  // the weighted visibility of cell (v, u) if it belongs to ring m, else 0
+  // (read through L1: the 16-column tile of a channel is re-read per ring)
+  auto cell_of = [&](int v, int u, int m) {
+    float2 x = make_float2(0.f, 0.f);
+    const int cell = (v + h) * nt + (u + h);
+    if (!BS_CHK(cell, (long long)nt * nt, 1)) return x;
+    if (__ldg(label + cell) != m) return x;
+    const float n = ngrid ? __ldg(ngrid + cell) : 1.0f;
+    if (n > 0.f) {
+      const float w = 1.0f / n;
+      const float2 vv = __ldg(vb + cell);
+      x = make_float2(w * vv.x, w * vv.y);
+    }
+    return x;
+  };
   for (int m = 0; m < g.nb; ++m) {
     const int ue = uext[m];
     const int slot = g.slot_of[m];
@@ -93,6 +85,7 @@ __global__ void __launch_bounds__(kRegThreads) k_colpass_reg(
     // pass 1: (n2, column) items, columns fastest
     for (int it = threadIdx.x; it < N2 * UB; it += blockDim.x) {
       const int n2 = it / UB, c = it - n2 * UB;
+      const int u = u0 + c;
       float2 v[N1];
 #pragma unroll
       for (int n1 = 0; n1 < N1; ++n1) {
@@ -100,14 +93,9 @@ __global__ void __launch_bounds__(kRegThreads) k_colpass_reg(
         // the rows v = y and v = y - N that reach index y (only one holds
         // cells of ring m when N exceeds the ring's diameter)
         float2 acc = make_float2(0.f, 0.f);
-        const int va = y, vb2 = y - N;
-        if (va < h) {
-          const int t = (va + h) * UB + c;
-          if (BS_CHK(t, nt * UB, 1) && lt[t] == m) acc = xt[t];
-        }
-        if (vb2 >= -h) {
-          const int t = (vb2 + h) * UB + c;
-          if (BS_CHK(t, nt * UB, 1) && lt[t] == m) acc = freg::add(acc, xt[t]);
+        if (u < h) {
+          if (y < h) acc = cell_of(y, u, m);
+          if (y - N >= -h) acc = freg::add(acc, cell_of(y - N, u, m));
         }
         v[n1] = acc;
       }
@@ -259,7 +247,8 @@ __global__ void __launch_bounds__(kRegThreads) k_rowpass_reg(
 }
 
 size_t colpass_reg_smem(int M, int nt) {
-  return (size_t)(M + M * kColUB + nt * kColUB) * sizeof(float2) + (size_t)nt * kColUB;
+  (void)nt;
+  return (size_t)(M + M * kColUB) * sizeof(float2);
 }
 
 template <int N>
@@ -294,8 +283,8 @@ cudaError_t rowpass_n(const GridGeom &g, const float2 *G, const uint8_t *valid, 
 }  // namespace
 
 bool has_reg_fft(int M, int nt) {
-  // the column pass keeps a 16-column visibility tile of nt rows in shared memory
-  if (nt > 0 && colpass_reg_smem(M, nt) > (size_t)200 * 1024) return false;
+  // the column pass keeps its exchange tile (16 columns of M) in shared memory
+  if (colpass_reg_smem(M, nt) > (size_t)200 * 1024) return false;
   switch (M) {
     case 16: case 24: case 32: case 48: case 64: case 96: case 128: case 192: case 256:
     case 384: case 512: case 768:
