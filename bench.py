@@ -674,58 +674,100 @@ def cfg4_shapes(seed=4000, n=8):
             for _ in range(n)]
 
 
-def run_mc_cfg4(dev, precision, block=32, per_shape=4, total=256, only_shape=None):
-    """The batched Monte Carlo configuration: `total` realisations of uneven
-    shapes (cfg4_shapes) through graph-replayed persistent launches, with a
-    declared subset of the tiles of every realisation: its channel block
-    [0, block)^3.  Each realisation's sky is drawn on the GPU at its full depth
-    (nt^2 x nc cells, Eq. mb1), and the group plans hold the block's channels
-    only (the full channel cube of the largest shape would need 249 GB of plan
-    workspace).  One run covers `per_shape` realisations of every shape."""
-    import numpy as np
+def cfg4_block_shapes(b=32):
+    """Candidate channel blocks of the batched Monte Carlo configuration: all
+    hold b^3 channel triples (the same evaluations per ring triple), shaped
+    for the contraction's tiles -- 32 x 16 channel pairs per tile, 256 field
+    rows of (third ring, nu3) per tile.  (b/2, b/2, 4b) would fill the rows
+    further but needs a 4b-channel plan per shape: 74 GB for the largest
+    shape, beyond the device with the others resident."""
+    return [(b, b, b), (b, b // 2, 2 * b)]
+
+
+def _mc_cfg4_setup(dev, precision, shapes, dims, per_shape):
     import torch
     import paper_2506_10526_gb300 as bs
     import synth
-    shapes = cfg4_shapes()
-    if only_shape is not None:  # profiling: one of the shapes
-        shapes = [shapes[only_shape]]
+    import numpy as np
+    nch = max(dims)
+    blk = (0, dims[0], 0, dims[1], 0, dims[2])
     specs, gens, skies, bufs = [], [], [], []
     for nt, nc, nb in shapes:
         e = list(synth.edges_log(nb, 4.41 * nt / 256, nt / 2))
-        specs.append(dict(nt=nt, nchan=block, edges=e, batch=per_shape, multires=True,
+        specs.append(dict(nt=nt, nchan=nch, edges=e, batch=per_shape, multires=True,
                           precision=precision))
         gens.append(bs.SkyGenerator(nt, nc, max_batch=per_shape))
         skies.append(torch.empty((per_shape, nc, nt, nt), dtype=torch.complex64, device=dev))
-        bufs.append(torch.empty((per_shape, block, nt, nt), dtype=torch.complex64, device=dev))
+        bufs.append(torch.empty((per_shape, nch, nt, nt), dtype=torch.complex64, device=dev))
     ens = bs.Ensemble(specs)
     for k in range(len(specs)):
         ens.set_input(k, bufs[k])
+        ens.set_block(k, blk)
     flops = 0.0
     evals = 0
+    ntrip3 = dims[0] * dims[1] * dims[2]
     for sp in specs:
-        pl = bs.Plan(sp["nt"], block, sp["edges"], precision=precision, multires=True)
-        pl.grid_load(torch.zeros((1, block, sp["nt"], sp["nt"]), dtype=torch.complex64,
+        pl = bs.Plan(sp["nt"], nch, sp["edges"], precision=precision, multires=True)
+        pl.grid_load(torch.zeros((1, nch, sp["nt"], sp["nt"]), dtype=torch.complex64,
                                  device=dev))
         tri, _ = pl.counts()
         sides = pl.trip_sides()
         ok = tri > 0
-        flops += per_shape * float(np.sum(2.0 * sides[ok].astype(np.float64) ** 2)) * block ** 3
-        evals += per_shape * int(ok.sum()) * block ** 3
+        flops += per_shape * float(np.sum(2.0 * sides[ok].astype(np.float64) ** 2)) * ntrip3
+        evals += per_shape * int(ok.sum()) * ntrip3
         pl.close()
 
     def draw(i):
-        for k, sp in enumerate(specs):
+        for k in range(len(specs)):
             gens[k].generate(44, i * per_shape, out=skies[k])
-            bufs[k].copy_(skies[k][:, :block])
+            bufs[k].copy_(skies[k][:, :nch])
 
+    def close():
+        ens.close()
+        for g in gens:
+            g.close()
+    return ens, draw, close, flops, evals
+
+
+def run_mc_cfg4(dev, precision, block=32, per_shape=4, total=256, only_shape=None):
+    """The batched Monte Carlo configuration: `total` realisations of uneven
+    shapes (cfg4_shapes) through graph-replayed persistent launches, with a
+    declared subset of the tiles of every realisation: one channel block of
+    block^3 channel triples, [0, a) x [0, b) x [0, c) with a b c = block^3.
+    Each realisation's sky is drawn on the GPU at its full depth (nt^2 x nc
+    cells, Eq. mb1), and the group plans hold the block's channels only (the
+    full channel cube of the largest shape would need 249 GB of plan
+    workspace).  One run covers `per_shape` realisations of every shape.  The
+    autotuner picks the block shape (cfg4_block_shapes, by the time of one
+    run each) and then the tiles' K extent and order (bs_mc_autotune)."""
+    import torch
+    shapes = cfg4_shapes()
+    if only_shape is not None:  # profiling: one of the shapes
+        shapes = [shapes[only_shape]]
+    stream = torch.cuda.current_stream()
+    trial = {}
+    for dims in cfg4_block_shapes(block):
+        ens, draw, close, _, _ = _mc_cfg4_setup(dev, precision, shapes, dims, per_shape)
+        draw(0)
+        ens.autotune()
+        ens.run(use_graph=True)  # capture
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        ens.run(use_graph=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        trial[dims] = e0.elapsed_time(e1)
+        close()
+    dims = min(trial, key=trial.get)
+    ens, draw, close, flops, evals = _mc_cfg4_setup(dev, precision, shapes, dims, per_shape)
     draw(0)
-    tiles = ens.autotune()
+    ens.autotune()
     tps, order = ens.tuning()
-    nper = per_shape * len(specs)
+    nper = per_shape * len(shapes)
     runs = max(1, total // nper)
     draw(1)
     ens.run(use_graph=True)  # capture
-    stream = torch.cuda.current_stream()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
            torch.cuda.Event(enable_timing=True)) for _ in range(runs)]
     torch.cuda.synchronize()
@@ -739,22 +781,23 @@ def run_mc_cfg4(dev, precision, block=32, per_shape=4, total=256, only_shape=Non
     ms = ev[0][0].elapsed_time(ev[-1][2])
     sky_ms = sum(a.elapsed_time(b) for a, b, _ in ev)
     _, _, nreal = ens.stats(0, 1)
-    ens.close()
-    for g in gens:
-        g.close()
+    close()
     peak = float(measured_peaks().get("bf16_tflops", 1900.0)) / 3
     return {"shapes": [f"{nt}^2 x {nc} ch x {nb} rings" for nt, nc, nb in shapes],
-            "declared_subset": f"channel block [0, {block})^3 of every realisation",
+            "declared_subset": f"channel block [0, {dims[0]}) x [0, {dims[1]}) x [0, {dims[2]}) "
+                               f"({block}^3 channel triples) of every realisation",
+            "block_trials_ms": {f"{a}x{b}x{c}": t for (a, b, c), t in trial.items()},
             "realisations": runs * nper, "ms": ms, "sky_generation_ms": sky_ms,
             "realisations_per_s": runs * nper / (ms / 1e3),
             "evals_per_s": runs * evals / (ms / 1e3),
-            "tuning": {"tiles_per_sm": tps, "tile_order": order},
+            "tuning": {"tiles_per_sm": tps, "tile_order": order, "block": list(dims)},
             "contraction_flops_frac_of_run": (runs * flops / (ms / 1e3) / 1e12) / peak,
             "realisations_accumulated_group0": int(nreal),
             "note": "per run: GPU sky generation of every realisation at full depth, the "
                     "block's channels copied into the group inputs, one graph replay (fields, "
                     "one persistent tensor-core launch over all groups, collapse, Eq. (dft), "
-                    "Welford statistics); frac against the measured BF16 burst peak / 3"}
+                    "Welford statistics); the block shape is picked among equal-size shapes by "
+                    "the time of one run; frac against the measured BF16 burst peak / 3"}
 
 
 def run_surrogate(dev, steps=200, rows=1 << 17):
