@@ -31,6 +31,7 @@
 #include <vector>
 
 #include "bs_internal.h"
+#include "fft_reg.cuh"
 #include "fft_smem.cuh"
 
 namespace bsi {
@@ -92,17 +93,65 @@ __device__ __forceinline__ float4 normals4(unsigned long long q, unsigned long l
   return make_float4(n01.x, n01.y, n23.x, n23.y);
 }
 
-template <int PRE, int MID>
-__global__ void __launch_bounds__(kSkyThreads) k_sky_lines(LineGeom g, SkyParams sp, float2 *data,
-                                                          const float2 *__restrict__ twg,
-                                                          Radices rad, float sign1) {
+// In-place transform of nl lines of length N (line r at buf + r LD) on the
+// register FFT (fft_reg.cuh), sign -1 by conjugating input and output:
+// pass 1 reads the lines along n2 into registers, the exchange tile Y takes
+// [line][k1][n2] (odd pitch), pass 2 writes X[k1 + N1 k2] back along the line.
+template <int N>
+__device__ __forceinline__ void reg_lines(float2 *buf, float2 *Y, const float2 *tw2, int nl, int LD,
+                                          float sign) {
+  constexpr int N1 = freg::Split<N>::N1, N2 = freg::Split<N>::N2, LDY = freg::Split<N>::LDY;
+  const float cj = sign < 0.f ? -1.f : 1.f;
+  for (int it = threadIdx.x; it < nl * N2; it += blockDim.x) {
+    const int r = it / N2, n2 = it - r * N2;
+    float2 v[N1];
+#pragma unroll
+    for (int n1 = 0; n1 < N1; ++n1) {
+      const float2 x = buf[r * LD + n2 + N2 * n1];
+      v[n1] = make_float2(x.x, cj * x.y);
+    }
+    freg::dft<N1, 1>(v);
+    float2 *Yr = Y + r * (N1 * LDY);
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) {
+      const float2 w = tw2[k1 * N2 + n2], a = v[k1];
+      Yr[k1 * LDY + n2] = make_float2(a.x * w.x - a.y * w.y, a.x * w.y + a.y * w.x);
+    }
+  }
+  __syncthreads();
+  for (int it = threadIdx.x; it < nl * N1; it += blockDim.x) {
+    const int r = it / N1, k1 = it - r * N1;
+    float2 v[N2];
+    const float2 *Yr = Y + r * (N1 * LDY) + k1 * LDY;
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) v[n2] = Yr[n2];
+    freg::dft<N2, 1>(v);
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) buf[r * LD + k1 + N1 * k2] = make_float2(v[k2].x, cj * v[k2].y);
+  }
+  __syncthreads();
+}
+
+// NR > 0: line length NR on the register FFT; NR = 0: Stockham stages.
+template <int PRE, int MID, int NR>
+__global__ void __launch_bounds__(kSkyThreads, 2) k_sky_lines(LineGeom g, SkyParams sp, float2 *data,
+                                                             const float2 *__restrict__ twg,
+                                                             Radices rad, float sign1) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int n = g.n, UB = g.UB;
+  const int n = NR > 0 ? NR : g.n, UB = g.UB;
   const int LD = n + 1;  // padded lines: strided (line-major) accesses spread over the banks
   float2 *tw = reinterpret_cast<float2 *>(smem_raw);
   float2 *bufA = tw + n;
-  float2 *bufB = bufA + UB * LD;
+  float2 *bufB = bufA + UB * LD;  // Stockham ping-pong buffer, or the register FFT's Y and tw2
+  float2 *tw2 = bufB + (NR > 0 ? UB * (n + freg::Split<(NR > 0 ? NR : 16)>::N1) : 0);
   for (int t = threadIdx.x; t < n; t += blockDim.x) tw[t] = twg[t];
+  if constexpr (NR > 0) {
+    constexpr int N2 = freg::Split<NR>::N2;
+    for (int t = threadIdx.x; t < NR; t += blockDim.x) {
+      const int k1 = t / N2, n2 = t - k1 * N2;
+      tw2[t] = twg[(n2 * k1) % NR];
+    }
+  }
   const int i0 = blockIdx.x * UB;
   const int nl = min(UB, g.ni - i0);
   const long long base =
@@ -142,7 +191,13 @@ __global__ void __launch_bounds__(kSkyThreads) k_sky_lines(LineGeom g, SkyParams
     }
   }
   __syncthreads();
-  float2 *res = stockham(bufA, bufB, nl, n, LD, rad, tw, sign1);
+  float2 *res;
+  if constexpr (NR > 0) {
+    reg_lines<NR>(bufA, bufB, tw2, nl, LD, sign1);
+    res = bufA;
+  } else {
+    res = stockham(bufA, bufB, nl, n, LD, rad, tw, sign1);
+  }
   if (MID != MID_NONE) {
     float2 *oth = (res == bufA) ? bufB : bufA;
     const int tot = nl * n;
@@ -161,7 +216,10 @@ __global__ void __launch_bounds__(kSkyThreads) k_sky_lines(LineGeom g, SkyParams
       res[l * LD + t] = v;
     }
     __syncthreads();
-    res = stockham(res, oth, nl, n, LD, rad, tw, -sign1);
+    if constexpr (NR > 0)
+      reg_lines<NR>(res, bufB, tw2, nl, LD, -sign1);
+    else
+      res = stockham(res, oth, nl, n, LD, rad, tw, -sign1);
   }
   const int tot = nl * n;
   for (int e = threadIdx.x; e < tot; e += blockDim.x) {
@@ -202,7 +260,26 @@ __global__ void k_sky_separate(const float2 *__restrict__ Z, int nt, int nc, lon
   }
 }
 
-size_t sky_smem(int n, int ub) { return (size_t)8 * (n + 2 * (size_t)ub * (n + 1)); }
+// first-pass length N1 of the register plan of n (0: none in the sky's set)
+int sky_reg_n1(int n) {
+  switch (n) {
+    case 64: return freg::Split<64>::N1;
+    case 128: return freg::Split<128>::N1;
+    case 256: return freg::Split<256>::N1;
+    case 384: return freg::Split<384>::N1;
+    case 512: return freg::Split<512>::N1;
+    case 768: return freg::Split<768>::N1;
+    default: return 0;
+  }
+}
+
+// tables + lines + (Stockham: a second line buffer; register FFT: the
+// exchange tile of ub (n + N1) and the split twiddles)
+size_t sky_smem(int n, int ub) {
+  const int n1 = sky_reg_n1(n);
+  if (n1) return (size_t)8 * (2 * (size_t)n + (size_t)ub * (n + 1) + (size_t)ub * (n + n1));
+  return (size_t)8 * (n + 2 * (size_t)ub * (n + 1));
+}
 
 int pick_ub(int n) {
   for (int ub = 16; ub > 1; ub >>= 1)
@@ -240,17 +317,41 @@ bs_status sky_fail(bs_sky s, bs_status st, const std::string &msg) {
   return st;
 }
 
-template <int PRE, int MID>
-cudaError_t launch_lines(const bs_sky_s *s, const LineGeom &g, const SkyParams &sp, int npair,
-                         const float2 *tw, const Radices &rad, float sign1, cudaStream_t st) {
+template <int PRE, int MID, int NR>
+cudaError_t launch_lines_n(const bs_sky_s *s, const LineGeom &g, const SkyParams &sp, int npair,
+                           const float2 *tw, const Radices &rad, float sign1, cudaStream_t st) {
   const size_t smem = sky_smem(g.n, g.UB);
-  cudaError_t e = cudaFuncSetAttribute(k_sky_lines<PRE, MID>,
+  cudaError_t e = cudaFuncSetAttribute(k_sky_lines<PRE, MID, NR>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const long long outer = g.ostride ? (long long)s->N / g.ostride : 1;
   dim3 grid((g.ni + g.UB - 1) / g.UB, (unsigned)outer, npair);
-  k_sky_lines<PRE, MID><<<grid, kSkyThreads, smem, st>>>(g, sp, s->work, tw, rad, sign1);
+  k_sky_lines<PRE, MID, NR><<<grid, kSkyThreads, smem, st>>>(g, sp, s->work, tw, rad, sign1);
   return cudaGetLastError();
+}
+
+// x and y lines (length nt) of every pass kind, z lines (length nchan) with the
+// filter: the register FFT for the lengths of sky_reg_n1, else Stockham
+template <int PRE, int MID>
+cudaError_t launch_lines(const bs_sky_s *s, const LineGeom &g, const SkyParams &sp, int npair,
+                         const float2 *tw, const Radices &rad, float sign1, cudaStream_t st) {
+  if constexpr (MID == MID_FILTER) {
+    switch (g.n) {
+      case 256: return launch_lines_n<PRE, MID, 256>(s, g, sp, npair, tw, rad, sign1, st);
+      case 384: return launch_lines_n<PRE, MID, 384>(s, g, sp, npair, tw, rad, sign1, st);
+      case 768: return launch_lines_n<PRE, MID, 768>(s, g, sp, npair, tw, rad, sign1, st);
+      default: break;
+    }
+  } else {
+    switch (g.n) {
+      case 64: return launch_lines_n<PRE, MID, 64>(s, g, sp, npair, tw, rad, sign1, st);
+      case 128: return launch_lines_n<PRE, MID, 128>(s, g, sp, npair, tw, rad, sign1, st);
+      case 256: return launch_lines_n<PRE, MID, 256>(s, g, sp, npair, tw, rad, sign1, st);
+      case 512: return launch_lines_n<PRE, MID, 512>(s, g, sp, npair, tw, rad, sign1, st);
+      default: break;
+    }
+  }
+  return launch_lines_n<PRE, MID, 0>(s, g, sp, npair, tw, rad, sign1, st);
 }
 
 }  // namespace
