@@ -14,7 +14,8 @@
 // The inter-pass twiddles w_N^(n2 k1) are entries (n2 k1 mod N) of the level's
 // table exp(+2 pi i t / N) (FP64 on the host, rounded to FP32).
 //
-// The in-register DFTs (lengths 2, 3, 4, 6, 8, 12, 16, 24, 32) split L = a b
+// The in-register DFTs (lengths 2, 3, 4, 5 and their products up to 32: 6, 8,
+// 9, 10, 12, 15, 16, 18, 20, 24, 25, 27, 30, 32) split L = a b
 // the same way, with every index and twiddle known at compile time; the
 // twiddles are cos / sin of 2 pi j / L evaluated at compile time by a Taylor
 // series (reduced to the first quadrant by exact symmetries) and rounded to
@@ -99,7 +100,11 @@ __host__ __device__ __forceinline__ float2 twiddle(float2 x) {
 }
 
 __host__ __device__ constexpr int first_factor(int L) {
-  return L % 8 == 0 && L > 8 ? 8 : L % 4 == 0 && L > 4 ? 4 : L % 2 == 0 && L > 2 ? 2 : 3;
+  return L % 8 == 0 && L > 8   ? 8
+         : L % 4 == 0 && L > 4 ? 4
+         : L % 2 == 0 && L > 2 ? 2
+         : L % 3 == 0 && L > 3 ? 3
+                               : 5;
 }
 
 // In-place DFT of length L held in registers, natural order in and out.
@@ -118,6 +123,22 @@ __host__ __device__ __forceinline__ void dft(float2 (&v)[L]) {
     v[0] = add(a, t);
     v[1] = add(m, rq);
     v[2] = sub(m, rq);
+  } else if constexpr (L == 5) {
+    // c1 = cos(2 pi / 5), c2 = cos(4 pi / 5), s1, s2 the sines (times S)
+    constexpr float c1 = (float)cos2pi(1, 5), c2 = (float)cos2pi(2, 5);
+    constexpr float s1 = (float)(S * sin2pi(1, 5)), s2 = (float)(S * sin2pi(2, 5));
+    const float2 a = v[0], t1 = add(v[1], v[4]), t2 = add(v[2], v[3]);
+    const float2 d1 = sub(v[1], v[4]), d2 = sub(v[2], v[3]);
+    const float2 m1 = make_float2(a.x + c1 * t1.x + c2 * t2.x, a.y + c1 * t1.y + c2 * t2.y);
+    const float2 m2 = make_float2(a.x + c2 * t1.x + c1 * t2.x, a.y + c2 * t1.y + c1 * t2.y);
+    // i (s1 d1 + s2 d2) and i (s2 d1 - s1 d2)
+    const float2 e1 = make_float2(-(s1 * d1.y + s2 * d2.y), s1 * d1.x + s2 * d2.x);
+    const float2 e2 = make_float2(-(s2 * d1.y - s1 * d2.y), s2 * d1.x - s1 * d2.x);
+    v[0] = add(a, add(t1, t2));
+    v[1] = add(m1, e1);
+    v[4] = sub(m1, e1);
+    v[2] = add(m2, e2);
+    v[3] = sub(m2, e2);
   } else if constexpr (L == 4) {
     const float2 s02 = add(v[0], v[2]), d02 = sub(v[0], v[2]);
     const float2 s13 = add(v[1], v[3]), d13 = twiddle<4, 1, S>(sub(v[1], v[3]));
@@ -158,7 +179,9 @@ template <int N>
 struct Split {
   static constexpr int N1 = N == 16 ? 4 : N == 24 ? 4 : N == 32 ? 4 : N == 48 ? 6 : N == 64 ? 8
                           : N == 96 ? 8 : N == 128 ? 8 : N == 192 ? 12 : N == 256 ? 16
-                          : N == 384 ? 16 : N == 512 ? 16 : N == 768 ? 24 : 0;
+                          : N == 384 ? 16 : N == 512 ? 16 : N == 768 ? 24
+                          // channel counts with factors 3 and 5
+                          : N == 540 ? 20 : N == 675 ? 25 : N == 729 ? 27 : N == 750 ? 25 : 0;
   static constexpr int N2 = N1 ? N / N1 : 0;
   static constexpr int LDY = N2 + 1;  // odd row pitch of the exchange tile
 };

@@ -269,6 +269,10 @@ int sky_reg_n1(int n) {
     case 384: return freg::Split<384>::N1;
     case 512: return freg::Split<512>::N1;
     case 768: return freg::Split<768>::N1;
+    case 540: return freg::Split<540>::N1;
+    case 675: return freg::Split<675>::N1;
+    case 729: return freg::Split<729>::N1;
+    case 750: return freg::Split<750>::N1;
     default: return 0;
   }
 }
@@ -340,6 +344,10 @@ cudaError_t launch_lines(const bs_sky_s *s, const LineGeom &g, const SkyParams &
       case 256: return launch_lines_n<PRE, MID, 256>(s, g, sp, npair, tw, rad, sign1, st);
       case 384: return launch_lines_n<PRE, MID, 384>(s, g, sp, npair, tw, rad, sign1, st);
       case 768: return launch_lines_n<PRE, MID, 768>(s, g, sp, npair, tw, rad, sign1, st);
+      case 540: return launch_lines_n<PRE, MID, 540>(s, g, sp, npair, tw, rad, sign1, st);
+      case 675: return launch_lines_n<PRE, MID, 675>(s, g, sp, npair, tw, rad, sign1, st);
+      case 729: return launch_lines_n<PRE, MID, 729>(s, g, sp, npair, tw, rad, sign1, st);
+      case 750: return launch_lines_n<PRE, MID, 750>(s, g, sp, npair, tw, rad, sign1, st);
       default: break;
     }
   } else {

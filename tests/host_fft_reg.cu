@@ -80,7 +80,16 @@ static bool dft_any(int L, std::vector<float2> &x) {
     case 2: run_dft<2, S>(x); return true;
     case 3: run_dft<3, S>(x); return true;
     case 4: run_dft<4, S>(x); return true;
+    case 5: run_dft<5, S>(x); return true;
     case 6: run_dft<6, S>(x); return true;
+    case 9: run_dft<9, S>(x); return true;
+    case 10: run_dft<10, S>(x); return true;
+    case 15: run_dft<15, S>(x); return true;
+    case 18: run_dft<18, S>(x); return true;
+    case 20: run_dft<20, S>(x); return true;
+    case 25: run_dft<25, S>(x); return true;
+    case 27: run_dft<27, S>(x); return true;
+    case 30: run_dft<30, S>(x); return true;
     case 8: run_dft<8, S>(x); return true;
     case 12: run_dft<12, S>(x); return true;
     case 16: run_dft<16, S>(x); return true;
@@ -104,6 +113,10 @@ static bool fft2_any(int N, std::vector<float2> &x) {
     case 384: run_fft2<384, S>(x); return true;
     case 512: run_fft2<512, S>(x); return true;
     case 768: run_fft2<768, S>(x); return true;
+    case 540: run_fft2<540, S>(x); return true;
+    case 675: run_fft2<675, S>(x); return true;
+    case 729: run_fft2<729, S>(x); return true;
+    case 750: run_fft2<750, S>(x); return true;
     default: return false;
   }
 }

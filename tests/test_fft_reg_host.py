@@ -42,9 +42,10 @@ def _ref_dft(x, sign):
     return np.fft.fft(x, axis=-1) if sign < 0 else np.fft.ifft(x, axis=-1) * x.shape[-1]
 
 
-@pytest.mark.parametrize("mode,lengths", [("dft", [2, 3, 4, 6, 8, 12, 16, 24, 32]),
+@pytest.mark.parametrize("mode,lengths", [("dft", [2, 3, 4, 5, 6, 8, 9, 10, 12, 15, 16, 18, 20,
+                                                   24, 25, 27, 30, 32]),
                                           ("fft2", [16, 24, 32, 48, 64, 96, 128, 192, 256,
-                                                    384, 512, 768])])
+                                                    384, 512, 768, 540, 675, 729, 750])])
 @pytest.mark.parametrize("sign", [1, -1])
 def test_register_dft_against_numpy(driver, tmp_path, mode, lengths, sign):
     rng = np.random.default_rng(7)

@@ -24,6 +24,17 @@ def _torch():
     (48, 10, 2, 1, 0, 0.5),       # radices 3 and 5
     (40, 1, 4, 2**40 + 3, 2**33, 1.0),  # one channel; 64-bit seed and realisation words
     (64, 16, 2, 9, 100, 0.0),     # Gaussian sky
+    # register-FFT line passes: x / y lines of 128 and 256, z lines of 256,
+    # 384, 768 and of the odd channel counts 540, 675, 729, 750
+    (128, 4, 2, 5, 7, 0.5),
+    (256, 2, 2, 6, 8, 0.5),
+    (8, 256, 2, 11, 1, 0.5),
+    (8, 384, 1, 12, 2, 0.5),
+    (8, 768, 2, 13, 3, 0.5),
+    (8, 540, 2, 14, 4, 0.5),
+    (8, 675, 2, 15, 5, 0.5),
+    (8, 729, 1, 16, 6, 0.5),
+    (8, 750, 2, 17, 7, 0.5),
 ])
 def test_generator_matches_reference(nt, nc, batch, seed, r0, f_ng):
     _torch()
