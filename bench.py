@@ -913,9 +913,9 @@ def main():
     out3d = torch.empty((1, nclos, nc, nc), dtype=torch.float64, device=dev)
     nlev = plan.info()[6]  # image sides the plan keeps fields at
     # kernels per step: column + row pass per image side (+ the FP16 split), the
-    # accumulator reset, the contraction, normalisation, the sampling table, two
-    # delay-transform passes
-    launches_per_step = (3 if args.precision == "split_fp16" else 2) * nlev + 6
+    # accumulator reset, the contraction, the folded-sampling reciprocals and the
+    # normalisation, the delay sampling table, two delay-transform passes
+    launches_per_step = (3 if args.precision == "split_fp16" else 2) * nlev + 7
     sides = plan.trip_sides()
     flops_per_chan_triple = float(np.sum(2.0 * sides[tri > 0].astype(np.float64) ** 2))
     jobs = blocks_of(nc, w["block"], w.get("block3"))

@@ -231,10 +231,11 @@ cudaError_t launch_full_finalize(double *out, long long bstride, int batch, int 
                                  int nc, const int *blk, const uint8_t *valid,
                                  const double *tnorm, cudaStream_t s);
 // list (nlist entries, or null for every ring triple): ring triples to process;
-// output plane y holds list[y] (compact layout), else plane t holds triple t
+// output plane y holds list[y] (compact layout), else plane t holds triple t.
+// scratch: ((2nc-1)^2 + 1) / 2 doubles for the reciprocal folded sampling.
 cudaError_t launch_delta_norm(const double *dsum, const long long *nnu, const double *tnorm,
                               double *out, int batch, int ntrip, int nc, const int *list,
-                              int nlist, cudaStream_t s);
+                              int nlist, double *scratch, cudaStream_t s);
 // y[k] += x[k], k < n
 cudaError_t launch_add_f64(double *y, const double *x, long long n, cudaStream_t s);
 // box = {row_lo, row_hi, col_lo, col_hi} (inclusive plane indices) to zero

@@ -26,7 +26,22 @@ namespace bsi {
 
 namespace {
 
-__global__ void k_delta_norm(const double *__restrict__ dsum, const long long *__restrict__ nnu,
+// rc[t] = 1 / (N(t) + N(plane - 1 - t)) (N(t) once at the centre), 0 where
+// nothing was sampled: the folded sampling of element t of the first half of
+// the (2 nc - 1)^2 plane, the same for every ring triple.
+__global__ void k_fold_recip(const long long *__restrict__ nnu, long long plane,
+                             double *__restrict__ rc) {
+  const long long half = (plane + 1) / 2;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < half;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long j = plane - 1 - t;
+    long long c = nnu[t];
+    if (j != t) c += nnu[j];
+    rc[t] = c > 0 ? 1.0 / (double)c : 0.0;
+  }
+}
+
+__global__ void k_delta_norm(const double *__restrict__ dsum, const double *__restrict__ rc,
                              const double *__restrict__ tnorm, double *__restrict__ out, int ntrip,
                              int nc, const int *__restrict__ list) {
   const int n2 = 2 * nc - 1;
@@ -49,13 +64,12 @@ __global__ void k_delta_norm(const double *__restrict__ dsum, const long long *_
        t += (long long)gridDim.x * blockDim.x) {
     const long long j = plane - 1 - t;
     if (!BS_CHK(j, plane, 21)) continue;
-    long long c = nnu[t];
-    if (j != t) c += nnu[j];
+    const double r = rc[t];
     double v = nan;
-    if (c > 0) {  // unsampled separations hold no sums: their reads are skipped
+    if (r != 0.0) {  // unsampled separations hold no sums: their reads are skipped
       double s = ds[t];
       if (j != t) s += ds[j];
-      v = s * tn / (double)c;
+      v = s * (tn * r);
     }
     o[t] = v;
     o[j] = v;
@@ -262,12 +276,16 @@ __global__ void k_full_finalize(double *__restrict__ out, long long bstride, int
 
 cudaError_t launch_delta_norm(const double *dsum, const long long *nnu, const double *tnorm,
                               double *out, int batch, int ntrip, int nc, const int *list,
-                              int nlist, cudaStream_t s) {
+                              int nlist, double *scratch, cudaStream_t s) {
   const long long plane = (long long)(2 * nc - 1) * (2 * nc - 1);
   const int ny = list ? nlist : ntrip;
   if (ny == 0) return cudaSuccess;
+  k_fold_recip<<<(unsigned)std::min<long long>((plane / 2 + 256) / 256, 1024), 256, 0, s>>>(
+      nnu, plane, scratch);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   dim3 grid((unsigned)std::min<long long>((plane + 255) / 256, 1024), ny, batch);
-  k_delta_norm<<<grid, 256, 0, s>>>(dsum, nnu, tnorm, out, ntrip, nc, list);
+  k_delta_norm<<<grid, 256, 0, s>>>(dsum, scratch, tnorm, out, ntrip, nc, list);
   return cudaGetLastError();
 }
 

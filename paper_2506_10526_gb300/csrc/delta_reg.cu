@@ -251,7 +251,7 @@ cudaError_t bs3d_n(const double *dsum, const float *rinv, const uint8_t *rowflag
 bool has_reg_dft(int nc) {
   switch (nc) {
     case 16: case 24: case 32: case 48: case 64: case 96: case 128: case 192: case 256:
-    case 384: case 512: case 768:
+    case 384: case 512: case 768: case 540: case 675: case 729: case 750:
       return true;
     default:
       return false;
@@ -267,7 +267,8 @@ cudaError_t launch_bs3d_reg(const double *dsum, const float *rinv, const uint8_t
   case n: return bs3d_n<n>(dsum, rinv, rowflag, tnorm, tmp, out, batch, ntrip, twN, scale, list, ny, s);
     BS_DEL_CASE(16) BS_DEL_CASE(24) BS_DEL_CASE(32) BS_DEL_CASE(48) BS_DEL_CASE(64)
     BS_DEL_CASE(96) BS_DEL_CASE(128) BS_DEL_CASE(192) BS_DEL_CASE(256) BS_DEL_CASE(384)
-    BS_DEL_CASE(512) BS_DEL_CASE(768)
+    BS_DEL_CASE(512) BS_DEL_CASE(768) BS_DEL_CASE(540) BS_DEL_CASE(675) BS_DEL_CASE(729)
+    BS_DEL_CASE(750)
 #undef BS_DEL_CASE
     default: return cudaErrorInvalidValue;
   }

@@ -217,7 +217,7 @@ bs_status mc_enqueue(bs_mc m, cudaStream_t s) {
     const WsLayout &L = p->L;
     MC_CUDA(launch_delta_norm(p->at<double>(L.dsum), p->at<long long>(L.nnu),
                               p->at<double>(L.tnorm), gr.dout, p->batch, p->ntrip, p->nc,
-                              nullptr, 0, s));
+                              nullptr, 0, p->at<double>(L.tmp3d), s));
     MC_CUDA(launch_bs3d(p->at<double>(L.dsum), p->at<long long>(L.nnu), p->at<double>(L.tnorm),
                         p->at<float2>(L.tmp3d), gr.bout, p->batch, p->ntrip, p->nc,
                         p->at<float2>(L.twN), p->radN, p->scale3d, nullptr, 0, s));

@@ -1209,7 +1209,7 @@ static bs_status delta_out(bs_plan p, double *out, bool closable, cudaStream_t s
   BS_CUDA(launch_delta_norm(p->at<double>(p->L.dsum), p->at<long long>(p->L.nnu),
                             p->at<double>(p->L.tnorm), dst, p->batch, p->ntrip, p->nc,
                             closable ? p->at<int>(p->L.clos) : nullptr,
-                            closable ? npl : 0, s));
+                            closable ? npl : 0, p->at<double>(p->L.tmp3d), s));
   if (p->general) BS_CUDA(launch_combine4(dst, per, p->ubatch, out, s));
   // per-channel sampling: (summed numerators) / (A x summed denominators)
   if (p->chans && out) BS_CUDA(launch_ratio2(dst, per, p->ubatch, 1.0 / p->normA, out, s));

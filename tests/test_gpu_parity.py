@@ -386,12 +386,15 @@ def test_merged_plans_equal_one_plan(precision, multires):
 
 
 @pytest.mark.parametrize("nc,block", [(24, None), (48, (0, 4, 0, 4, 0, 4)), (96, (0, 40, 8, 48, 0, 96)),
-                                      (12, None), (16, (2, 6, 0, 16, 3, 9))])
+                                      (12, None), (16, (2, 6, 0, 16, 3, 9)),
+                                      (540, (0, 8, 0, 8, 0, 16)), (675, (3, 11, 0, 8, 100, 116)),
+                                      (729, (0, 8, 0, 8, 0, 8)), (750, (0, 16, 0, 8, 0, 8))])
 def test_delay_transform_against_oracle(nc, block):
     """Eq. (dft) of the library's own folded planes against the oracle's
     transform of the same planes: channel counts with a register FFT (24, 48,
-    96, 16) and one without (12), whole-cube and partial channel blocks (rows
-    of the periodic placement with nothing sampled), non-unit scale."""
+    96, 16; 540, 675, 729, 750 with radix-3 and -5 factors) and one without
+    (12), whole-cube and partial channel blocks (rows of the periodic
+    placement with nothing sampled), non-unit scale."""
     torch = _torch()
     import paper_2506_10526_gb300 as bs
     nt, r, rp, dnu = 32, 900.0, 1.2, 0.16
