@@ -4,9 +4,9 @@
 // (Hermitian C2R along u, two rows per complex transform, FP32 and split
 // outputs) as grid.cu, with one shared-memory exchange per transform.
 //
-// colpass: CTA = (UB = 16 consecutive u columns, channel, realisation), all
-//   rings in turn.  Threads take columns fastest, so the visibility, label and
-//   weight reads (through L1: each ring re-reads the channel's 16-column
+// colpass: CTA = (UB = 16 consecutive u columns, channel, realisation x ring
+//   slot).  Threads take columns fastest, so the visibility, label and weight
+//   reads (through L1 / L2: the rings of a channel re-read its 16-column
 //   tile), the exchange tile and the G stores (u fastest) are all consecutive
 //   across a warp.  Only the exchange tile is in shared memory.
 // rowpass: CTA = RPB consecutive row pairs of the flattened
@@ -51,8 +51,10 @@ __global__ void __launch_bounds__(kRegThreads) k_colpass_reg(
   const int nt = g.nt, h = nt / 2;
   const int u0 = blockIdx.x * UB;
   const int nu = blockIdx.y;
-  const int b = blockIdx.z;
-  if (!valid[nu]) return;  // fields of a flagged channel are written as zeros by rowpass
+  const int b = blockIdx.z / g.nslot, slot = blockIdx.z - b * g.nslot;  // one ring per CTA
+  const int m = g.ring_of[slot];
+  const int ue = uext[m];
+  if (!valid[nu] || u0 >= ue) return;  // flagged channels: rowpass writes zeros
   float2 *tw2 = reinterpret_cast<float2 *>(smem_raw);  // [N1][N2]
   float2 *Y = tw2 + N;                                   // [N1][N2][UB]
   for (int t = threadIdx.x; t < N; t += blockDim.x) {
@@ -63,6 +65,7 @@ __global__ void __launch_bounds__(kRegThreads) k_colpass_reg(
   const float2 *vb = vis + ((long long)b * g.nc + nu) * (long long)nt * nt;
   const int ncols = min(UB, g.UC - u0);
   const long long gtot = (long long)g.batch * g.nslot * g.nc * N * g.UC;  // G extent
+  (void)gtot;  // used by the checked build's bounds checks
   // the weighted visibility of cell (v, u) if it belongs to ring m, else 0
   // (read through L1: the 16-column tile of a channel is re-read per ring)
   auto cell_of = [&](int v, int u, int m) {
@@ -78,10 +81,7 @@ __global__ void __launch_bounds__(kRegThreads) k_colpass_reg(
     }
     return x;
   };
-  for (int m = 0; m < g.nb; ++m) {
-    const int ue = uext[m];
-    const int slot = g.slot_of[m];
-    if (slot < 0 || u0 >= ue) continue;  // block-uniform
+  {
     // pass 1: (n2, column) items, columns fastest
     for (int it = threadIdx.x; it < N2 * UB; it += blockDim.x) {
       const int n2 = it / UB, c = it - n2 * UB;
@@ -166,6 +166,7 @@ __global__ void __launch_bounds__(kRegThreads) k_rowpass_reg(
   }
   __syncthreads();
   const long long gtot = (long long)g.batch * g.nslot * g.nc * N * g.UC;  // G extent
+  (void)gtot;  // used by the checked build's bounds checks
   // pass 1: (pair, n2) items, n2 fastest
   for (int it = threadIdx.x; it < RPB * N2; it += blockDim.x) {
     const int r = it / N2, n2 = it - r * N2;
@@ -258,7 +259,9 @@ cudaError_t colpass_n(const GridGeom &g, const float2 *vis, const float *ngrid,
   const size_t smem = colpass_reg_smem(N, g.nt);
   cudaError_t e = smem_optin_once<k_colpass_reg<N>>();
   if (e != cudaSuccess) return e;
-  dim3 grid((g.UC + kColUB - 1) / kColUB, g.nc, g.batch);
+  if (g.nslot == 0) return cudaSuccess;
+  if ((long long)g.batch * g.nslot > 65535) return cudaErrorInvalidValue;
+  dim3 grid((g.UC + kColUB - 1) / kColUB, g.nc, g.batch * g.nslot);
   k_colpass_reg<N><<<grid, kRegThreads, smem, s>>>(g, vis, ngrid, valid, label, uext, twM, G);
   return cudaGetLastError();
 }
