@@ -37,7 +37,9 @@ constexpr int kColsPad = 8;    // per-k1 pad of the cols exchange tile (half the
 
 template <int N>
 struct DelCfg {
-  static constexpr int R = N <= 64 ? N : 8;  // rows per rows-pass CTA
+  // rows per rows-pass CTA: few for long rows, so that more CTAs are resident
+  // to cover the latency of the dependent sampling / accumulator reads
+  static constexpr int R = N <= 64 ? N : N < 256 ? 8 : 4;
 };
 
 template <int N>
