@@ -4,8 +4,8 @@
 // (Hermitian C2R along u, two rows per complex transform, FP32 and split
 // outputs) as grid.cu, with one shared-memory exchange per transform.
 //
-// colpass: CTA = (UB = 16 consecutive u columns, channel, realisation x ring
-//   slot).  Threads take columns fastest, so the visibility, label and weight
+// colpass: CTA = (UB = 8 or 16 consecutive u columns, channel, realisation x
+//   ring slot).  Threads take columns fastest, so the visibility, label and weight
 //   reads (through L1 / L2: the rings of a channel re-read its 16-column
 //   tile), the exchange tile and the G stores (u fastest) are all consecutive
 //   across a warp.  Only the exchange tile is in shared memory.
@@ -26,7 +26,12 @@ namespace {
 using freg::Split;
 
 constexpr int kRegThreads = 128;
-constexpr int kColUB = 16;
+// u columns per column-pass CTA: 8 for the long transforms, so that the
+// exchange tile (UB x N) leaves room for more resident CTAs
+template <int N>
+struct ColCfg {
+  static constexpr int UB = N >= 256 ? 8 : 16;
+};
 
 // row pairs per row-pass CTA for each side (about one pass-2 transform per thread)
 template <int N>
@@ -46,7 +51,7 @@ __global__ void __launch_bounds__(kRegThreads) k_colpass_reg(
     GridGeom g, const float2 *__restrict__ vis, const float *__restrict__ ngrid,
     const uint8_t *__restrict__ valid, const int8_t *__restrict__ label,
     const int *__restrict__ uext, const float2 *__restrict__ twM, float2 *__restrict__ G) {
-  constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2, UB = kColUB;
+  constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2, UB = ColCfg<N>::UB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nt = g.nt, h = nt / 2;
   const int u0 = blockIdx.x * UB;
@@ -249,7 +254,7 @@ __global__ void __launch_bounds__(kRegThreads) k_rowpass_reg(
 
 size_t colpass_reg_smem(int M, int nt) {
   (void)nt;
-  return (size_t)(M + M * kColUB) * sizeof(float2);
+  return (size_t)(M + M * (M >= 256 ? 8 : 16)) * sizeof(float2);  // ColCfg<M>::UB
 }
 
 template <int N>
@@ -261,7 +266,8 @@ cudaError_t colpass_n(const GridGeom &g, const float2 *vis, const float *ngrid,
   if (e != cudaSuccess) return e;
   if (g.nslot == 0) return cudaSuccess;
   if ((long long)g.batch * g.nslot > 65535) return cudaErrorInvalidValue;
-  dim3 grid((g.UC + kColUB - 1) / kColUB, g.nc, g.batch * g.nslot);
+  constexpr int UB = ColCfg<N>::UB;
+  dim3 grid((g.UC + UB - 1) / UB, g.nc, g.batch * g.nslot);
   k_colpass_reg<N><<<grid, kRegThreads, smem, s>>>(g, vis, ngrid, valid, label, uext, twM, G);
   return cudaGetLastError();
 }
