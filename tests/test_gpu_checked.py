@@ -7,7 +7,8 @@ access instead of faulting.
   index and extent, and the library keeps working;
 * tiny grids (8^2, 16^2; plain FP32 and split BF16, one and several image
   sides, register-FFT and Stockham lengths) element by element against the
-  FP64 oracle through the checked library, with no violation recorded;
+  FP64 oracle through the checked library, then gridding of raw baselines
+  and the monopole and multipole binning, with no violation recorded;
 * the ordinary library reports that it is not the checked build.
 Runs in child processes (BS_LIBRARY selects the library at load time)."""
 import os
@@ -69,6 +70,35 @@ CHILD = textwrap.dedent("""
         print("CASE", nt, nc, prec, multires, e_full, e_d, e3)
         assert e_full < TOL[prec] and e_d < TOL[prec] and e3 < 1e-5, (nt, nc, prec, e_full, e_d, e3)
         plan.close()
+    # gridding of raw baselines (the cell checks) and the monopole binning (the
+    # bin checks) through the checked library
+    from oracle import gridding as gr, monopole as mo
+    r = np.random.default_rng(5)
+    nt, nc, nbl = 16, 4, 300
+    uv = r.uniform(-0.5 * nt - 1.0, 0.5 * nt + 1.0, size=(nbl, 2))
+    vis = (r.normal(size=(nbl, nc)) + 1j * r.normal(size=(nbl, nc))).astype(np.complex64)
+    plan = bs.Plan(nt, nc, [1.0, 4.0, 8.0])
+    vg, ng = plan.grid_visibilities(torch.from_numpy(uv).cuda(), torch.from_numpy(vis).cuda())
+    torch.cuda.synchronize()
+    vg_o, ng_o = gr.grid_visibilities(uv, vis.astype(np.complex128), None, nt)
+    assert np.array_equal(ng.cpu().numpy(), ng_o)
+    plan.close()
+    nt, nc = 16, 12
+    edges = list(synth.edges_linear(4, 8))
+    plan = bs.Plan(nt, nc, edges, precision=1)
+    plan.grid_load(torch.from_numpy(synth.sky_visibilities(nt, nc, seed=9)[None]).cuda())
+    plan.mabs(accumulate=True)
+    tri, _ = plan.counts()
+    b3 = torch.empty((1, plan.n_closable, nc, nc), dtype=torch.float64, device="cuda")
+    plan.bs3d_closable(b3)
+    kperp = 2 * np.pi * plan.ring_umean()
+    kpar = mo.kpar_axis(nc)
+    k1e = np.geomspace(0.5 * kperp.min(), 1.2 * np.sqrt(kperp.max() ** 2 + kpar.max() ** 2), 7)
+    _, cnt = plan.bs_monopole(b3, kperp, kpar, k1e, 5, 5)
+    _, cntm = plan.bs_multipoles(b3, kperp, kpar, k1e, 5, 5, lmax=2)
+    torch.cuda.synchronize()
+    assert cnt.sum().item() > 0 and cntm.sum().item() > 0
+    plan.close()
     print("AFTER", bs.checked_status())
 """).replace("ROOT", repr(ROOT))
 
