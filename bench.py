@@ -44,7 +44,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 WORKLOADS = {
-    "mwa": dict(nt=256, nc=768, nb=20, edges=("log", 4.41, 128.0), block=128, block3=256,
+    "mwa": dict(nt=256, nc=768, nb=20, edges=("log", 4.41, 128.0), block=128, block3=256, cube=256,
                 desc="MWA-like: 256^2 uv grid, 768 channels (30.72 MHz at 40 kHz), 20 log rings "
                      "|U| in [4.41, 128), no flagging"),
     "mwa64": dict(nt=256, nc=64, nb=20, edges=("log", 4.41, 128.0), block=64,
@@ -92,6 +92,9 @@ def parse():
     ap.add_argument("--block", type=int, default=0, help="channel block side (0 = workload default)")
     ap.add_argument("--block3", type=int, default=0,
                     help="channel block side along nu3 (0 = workload default)")
+    ap.add_argument("--ordinary", action="store_true",
+                    help="time ordinary channel blocks (block x block x block3) instead of "
+                         "channel-symmetric sub-band cubes")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU baseline budget")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -250,6 +253,9 @@ def measure_error(plan, vis, edges, blk, out_delta, tri, precision, closable=Tru
     clos = np.flatnonzero(tri > 0)
     pos = {int(t): k for k, t in enumerate(clos)}
     chosen = [int(t) for t in clos[:4]] + [int(clos[len(clos) // 5])]
+    # and the first closable (i, j, j), i < j: its channel orderings nu2 > nu3 are
+    # filled in from nu2 < nu3 under channel-symmetric accumulation
+    chosen += [int(t) for t in clos if trips[t][0] < trips[t][1] == trips[t][2]][:1]
     b = blk
     mid3 = (b[4] + b[5]) // 2
     picks = [(b[0], b[2]), (b[1] - 1, b[3] - 1), ((b[0] + b[1]) // 2, b[2] + 1),
@@ -880,7 +886,7 @@ def main():
     import torch.distributed as dist
 
     import paper_2506_10526_gb300 as bs
-    from paper_2506_10526_gb300.sharding import blocks_of, rank_block, reduce_step_stats
+    from paper_2506_10526_gb300.sharding import blocks_of, cubes_of, rank_block, reduce_step_stats
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -915,20 +921,39 @@ def main():
     # kernels per step: column + row pass per image side (+ the FP16 split), the
     # accumulator reset, the contraction, the folded-sampling reciprocals and the
     # normalisation, the delay sampling table, two delay-transform passes
-    launches_per_step = (3 if args.precision == "split_fp16" else 2) * nlev + 7
+    # channel-symmetric sub-band cubes (accumulate = 2): one more kernel per step fills
+    # in the channel orderings of repeated rings that the contraction leaves out
+    sym = bool(w.get("cube")) and not args.ordinary and args.precision != "fp32"
+    launches_per_step = (3 if args.precision == "split_fp16" else 2) * nlev + 7 + (1 if sym else 0)
     sides = plan.trip_sides()
-    flops_per_chan_triple = float(np.sum(2.0 * sides[tri > 0].astype(np.float64) ** 2))
-    jobs = blocks_of(nc, w["block"], w.get("block3"))
+    # ring triples in the plan's order (i <= j <= l, lexicographic); a repeated ring
+    # makes the triple symmetric under exchanging that ring's channels
+    nb = w["nb"]
+    rep = np.array([i == j or j == l for i in range(nb) for j in range(i, nb)
+                    for l in range(j, nb)])
+    jobs = cubes_of(nc, w["cube"]) if sym else blocks_of(nc, w["block"], w.get("block3"))
 
     def block_evals(b):
         return nclos * (b[1] - b[0]) * (b[3] - b[2]) * (b[5] - b[4])
+
+    def block_flops(b, symmetric):
+        """Algorithmic FLOPs of the contraction of block b: 2 M^2 per channel triple
+        of every closable ring triple; with the channel symmetry of a cube, n^2 (n + 1) / 2
+        channel triples (one ordering) for the ring triples with a repeated ring."""
+        n3 = (b[1] - b[0]) * (b[3] - b[2]) * (b[5] - b[4])
+        per = 2.0 * sides.astype(np.float64) ** 2
+        if not symmetric:
+            return float(np.sum(per[tri > 0])) * n3
+        n = b[1] - b[0]
+        half = n * n * (n + 1) / 2.0
+        return float(np.sum(per[(tri > 0) & ~rep]) * n3 + np.sum(per[(tri > 0) & rep]) * half)
 
     def step(i, ev=None, vis_in=None, out=None):
         b = rank_block(jobs, i, world, rank)
         plan.grid_load(vis_d if vis_in is None else vis_in)
         if ev is not None:
             ev[0].record(stream)
-        plan.mabs(block=b, accumulate=True)
+        plan.mabs(block=b, accumulate=True, symmetric=sym)
         if ev is not None:
             ev[1].record(stream)
         plan.mabs_delta_closable(out_delta)
@@ -999,8 +1024,8 @@ def main():
                                 + ("; FP16 has the BF16 dense rate)"
                                    if args.precision == "split_fp16" else ")"))}
     b0 = jobs[0]
-    achieved = flops_per_chan_triple * (b0[1] - b0[0]) * (b0[3] - b0[2]) * (b0[5] - b0[4]) / (
-        avg_ms / 1e3) / 1e12
+    flops_launch = block_flops(b0, sym)
+    achieved = flops_launch / (avg_ms / 1e3) / 1e12
     tr = profile_traffic(args.precision)
     roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                  "kernel": "k_contract_simt" if args.precision == "fp32" else "k_contract_tc",
@@ -1020,7 +1045,15 @@ def main():
         "data": "synthetic",
         "config": {"workload": w["desc"], "M": M, "multires": multires,
                    "image_sides": sorted(set(int(x) for x in sides[tri > 0])),
-                   "channel_block": [w["block"], w["block"], w.get("block3") or w["block"]],
+                   "channel_block": ([w["cube"]] * 3 if sym else
+                                     [w["block"], w["block"], w.get("block3") or w["block"]]),
+                   "channel_symmetry": (
+                       "each step is one sub-band's whole channel cube (bs_mabs accumulate = 2): "
+                       "for ring triples with a repeated ring only one ordering of that ring's "
+                       "channels is contracted and the other is filled in; evaluations count "
+                       "every channel triple of the cube" if sym else None),
+                   "contracted_fraction_of_cube_flops": (
+                       block_flops(jobs[0], True) / block_flops(jobs[0], False) if sym else 1.0),
                    "closable_ring_triples": nclos, "ring_triples": plan.ntrip,
                    "outputs": (f"folded MABS and 3D bispectrum planes of the {nclos} closable "
                                f"ring triples (bs_mabs_delta_closable, bs_bs3d_closable)"),
@@ -1042,6 +1075,28 @@ def main():
                                         "4 x 256 threads per SM, CUDA events"}
     contraction_rate = per_launch_evals / (avg_ms / 1e3)
     line["contraction_evals_per_s"] = contraction_rate
+    ordinary_rate = contraction_rate
+    if sym and world == 1:
+        # the ordinary accumulation (every channel triple contracted) of the
+        # 128 x 128 x 256 block, timed the same way: the like-for-like rate
+        ob = blocks_of(nc, w["block"], w.get("block3"))[0]
+        oev = []
+        for i in range(4):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            plan.grid_load(vis_d)
+            e0.record(stream)
+            plan.mabs(block=ob, accumulate=True)
+            e1.record(stream)
+            oev.append((e0, e1))
+        torch.cuda.synchronize()
+        oms = statistics.mean(a.elapsed_time(b) for a, b in oev[1:])
+        ordinary_rate = block_evals(ob) / (oms / 1e3)
+        oach = block_flops(ob, False) / (oms / 1e3) / 1e12
+        line["ordinary_block"] = {
+            "channel_block": [ob[1] - ob[0], ob[3] - ob[2], ob[5] - ob[4]],
+            "contraction_evals_per_s": ordinary_rate, "avg_launch_ms": oms,
+            "achieved_tflops": oach, "frac": oach / peak}
     plan.close()
     del out3d
     torch.cuda.empty_cache()
@@ -1093,10 +1148,13 @@ def main():
             "error": err_eq,
             "single_side": {"contraction_evals_per_s": r_one, "avg_launch_ms": ms_one,
                             "achieved_tflops": tf_one, "frac": tf_one / p32}}
-        # precision gain at equal work; the single-side ratio adds the work saved by
-        # per-triple image sides
-        line["speedup_vs_fp32"] = contraction_rate / r_eq
-        line["speedup_vs_fp32_single_side"] = contraction_rate / r_one
+        # precision gain at equal work (both contract every channel triple); the
+        # single-side ratio adds the work saved by per-triple image sides, the
+        # symmetric one the work saved by the channel symmetry of repeated rings
+        line["speedup_vs_fp32"] = ordinary_rate / r_eq
+        line["speedup_vs_fp32_single_side"] = ordinary_rate / r_one
+        if sym:
+            line["speedup_vs_fp32_with_channel_symmetry"] = contraction_rate / r_eq
     del out_delta
     torch.cuda.empty_cache()
     if rank == 0 and world == 1 and not args.no_cpu:

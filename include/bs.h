@@ -54,7 +54,7 @@
 extern "C" {
 #endif
 
-#define BS_ABI_VERSION 12
+#define BS_ABI_VERSION 13
 
 typedef struct bs_plan_s *bs_plan;
 
@@ -224,9 +224,23 @@ bs_status bs_counts(bs_plan plan, int64_t *tri_host, int64_t *nnu_host);
  *              block are overwritten with B_A (NaN where undefined); entries
  *              outside the block are left untouched.  General plans: complex128
  *              (double pairs) of the same shape.
- *  accumulate  nonzero: add the block's pixel sums and sampling to the
- *              collapse accumulators used by bs_mabs_delta / bs_bs3d.
- * Errors: BS_ERR_STATE (no grid loaded), BS_ERR_ARG (block out of range). */
+ *  accumulate  1: add the block's pixel sums and sampling to the collapse
+ *              accumulators used by bs_mabs_delta / bs_bs3d.
+ *              2: the same for a cube block S x S x S (nu1, nu2 and nu3 ranges
+ *              equal), using the symmetry of a ring triple with a repeated
+ *              ring under exchanging that ring's channels: for (i, i, l) only
+ *              nu1 <= nu2 and for (i, j, j) only nu2 <= nu3 is contracted, and
+ *              the other ordering is filled in from it before the sums are
+ *              read (the cube is closed under the exchange, so the result is
+ *              the sum over the whole cube).  Split-precision plans without
+ *              general input or per-channel sampling; out_full_dev must be
+ *              NULL.  Ordinary blocks (1) may follow symmetric cubes; a
+ *              symmetric cube after ordinary blocks needs bs_delta_reset.
+ *              0: nothing is accumulated.
+ * Errors: BS_ERR_STATE (no grid loaded; accumulate = 2 after ordinary blocks),
+ * BS_ERR_ARG (block out of range, accumulate not 0..2, accumulate = 2 with a
+ * block that is not a cube or with out_full_dev), BS_ERR_UNSUPPORTED
+ * (accumulate = 2 on an FP32, general or per-channel sampling plan). */
 bs_status bs_mabs(bs_plan plan, const int32_t *block_host, double *out_full_dev,
                   int accumulate, void *cuda_stream);
 

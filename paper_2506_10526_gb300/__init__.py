@@ -34,7 +34,7 @@ STATUS = {0: "BS_OK", 1: "BS_ERR_ARG", 2: "BS_ERR_NO_DEVICE", 3: "BS_ERR_CUDA", 
 PREC_FP32 = 0
 PREC_SPLIT_BF16 = 1
 PREC_SPLIT_FP16 = 2
-ABI_VERSION = 12     # BS_ABI_VERSION of include/bs.h
+ABI_VERSION = 13     # BS_ABI_VERSION of include/bs.h
 MLP_FEATURES = 45    # BS_MLP_FEATURES of include/bs.h
 
 # every symbol declared in include/bs.h
@@ -272,8 +272,10 @@ class Plan:
                              "elements")
         return _dptr(t)
 
-    def mabs(self, block=None, out_full=None, accumulate=True, stream=None):
-        """bs_mabs over channel block (nu1_lo, nu1_hi, nu2_lo, nu2_hi, nu3_lo, nu3_hi)."""
+    def mabs(self, block=None, out_full=None, accumulate=True, stream=None, symmetric=False):
+        """bs_mabs over channel block (nu1_lo, nu1_hi, nu2_lo, nu2_hi, nu3_lo, nu3_hi).
+        symmetric=True accumulates a cube block S x S x S with the channel symmetry
+        of repeated rings (accumulate = 2)."""
         full = None
         if out_full is not None:
             full = self._out(out_full, self.ntrip * self.nchan, self.nchan)
@@ -281,8 +283,8 @@ class Plan:
         if block is not None:
             self._blk = (ctypes.c_int32 * 6)(*[int(x) for x in block])
             blk = self._blk
-        self._check(self._L.bs_mabs(self._h, blk, full, 1 if accumulate else 0,
-                                    _stream_ptr(stream)))
+        acc = 2 if symmetric else (1 if accumulate else 0)
+        self._check(self._L.bs_mabs(self._h, blk, full, acc, _stream_ptr(stream)))
 
     def delta_reset(self, stream=None):
         self._check(self._L.bs_delta_reset(self._h, _stream_ptr(stream)))

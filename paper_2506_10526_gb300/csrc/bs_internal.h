@@ -67,7 +67,10 @@ struct ColEntry {
   int field;  // l * nchan + nu3
   int trip;   // ring-triple index of (i, j, l)
   int nu3;
-  int pad;
+  // 0: the row is (l, nu3) against pairs (nu1, nu2).  1 (channel-symmetric
+  // accumulation only): the row is (i, nu1) of ring triple (i, j, j), i < j,
+  // against pairs (nu2, nu3) of ring j; `nu3` then holds nu1
+  int swapped;
 };
 
 // A (ring pair, column tile) work item of the contraction.
@@ -116,7 +119,10 @@ struct TcTile {
   int nu1_0, nu2_0;
   int col_off, ncol, col0;
   int kseg;
-  int pad[2];
+  // 1: the pair operand is F_i F_i of one ring and only pairs nu1 <= nu2 are kept
+  // (the rectangle straddles the diagonal nu1 = nu2); 0: every pair is kept
+  int diag;
+  int pad;
 };
 
 // Per shape group (one plan): where its fields, lists and outputs live.
@@ -241,6 +247,11 @@ cudaError_t launch_add_f64(double *y, const double *x, long long n, cudaStream_t
 // box = {row_lo, row_hi, col_lo, col_hi} (inclusive plane indices) to zero
 cudaError_t launch_zero_planes(double *dsum, const int *trips, int ntr, int batch, int ntrip,
                                int n2, const int *box, cudaStream_t s);
+// Channel-symmetric accumulation: fills, inside box, the channel orderings of
+// the listed ring triples (2 t + kind; kind 0: (i, i, l), kind 1: (i, j, j))
+// that the contraction left out, from the ones it computed.
+cudaError_t launch_symmetrize(double *dsum, const int *list, int nlist, int batch, int ntrip,
+                              int nc, const int *box, cudaStream_t s);
 // tmp: batch * ntrip * nc^2 float2 followed by nc^2 doubles of scratch
 // Register-FFT delay transform (delta_reg.cu) for the channel counts with a
 // register plan (has_reg_dft); launch_bs3d dispatches to it.  rinv [nc][nc]:

@@ -43,6 +43,17 @@
 // nu2-nu3) into the idle B buffers, then FP64 global atomics into the
 // collapse sums (and, when asked, FP64 atomics into the FULL cube).
 //
+// Channel-symmetric accumulation (cube blocks S x S x S): a ring triple with a
+// repeated ring is symmetric under exchanging the channels of the repeated ring,
+// so only one ordering is contracted.  Ring pairs (i, i) keep pairs nu1 <= nu2
+// (rectangles wholly below the diagonal are not in the tile list; tiles that
+// straddle it carry `diag` and the epilogue drops pairs with nu1 > nu2).  Ring
+// triples (i, j, j), i < j, are contracted on the ring pair (j, j) with rows
+// (i, nu1) ("swapped" rows, pairs (nu2, nu3) with nu2 <= nu3), so the same
+// pair-level cut applies to them; their reduction key and flush map (pa, pb,
+// nu1) to the separations (nu1 - nu3, nu2 - nu3) accordingly.  The other
+// ordering is filled in from the computed one before the sums are read.
+//
 // Every mbarrier wait is bounded by %globaltimer.  A wait that gives up sets
 // the abort flag of both CTAs of the pair and the plan's error word; all roles
 // then run their loops to the end without waiting or issuing work, the TMA
@@ -688,7 +699,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
           int lo = c0.nu3, hi = c0.nu3, q = m;
           while (q + 1 < MROWS && colbuf[q + 1].field != -2) {
             const ColEntry cn = colbuf[q + 1];
-            if (cn.field >= 0 && cn.trip != c0.trip) break;
+            if (cn.field >= 0 && (cn.trip != c0.trip || cn.swapped != c0.swapped)) break;
             ++q;
             if (cn.field >= 0) {
               lo = min(lo, cn.nu3);
@@ -696,21 +707,28 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
             }
           }
           const int E = (P2 - 1) + (hi - lo) + 1;
+          const int sw = c0.swapped ? 1 << 16 : 0;  // E < 2^16 (hi - lo < MROWS)
           double usc = 1.0;  // undoes the split-FP16 operand scales of this ring triple
           if constexpr (F16)
             usc = exp2i_f64(-(G.kexp[b * G.nslot + t.ri] + G.kexp[b * G.nslot + t.rj] +
                               G.kexp[b * G.nslot + c0.field / G.nc]));
           if (ns < MAX_SEG) {
-            seginfo[ns] = make_int4(base, E, c0.trip, hi);
+            seginfo[ns] = make_int4(base, E | sw, c0.trip, hi);
             segscale[ns] = usc;
           }
+          // reduction key of pair (pa, pb) on row r: (dd, e2) with dd = pa - pb + P2 - 1
+          // and e2 = hi - nu3 + pb (ordinary row) or e2 = nu1 - lo + P2 - 1 - pb
+          // (swapped row); the entry is dd * E + e2 = rowinfo.x + pa E - pb (E -+ 1)
           for (int r = m; r <= q; ++r) {
             const ColEntry cr = colbuf[r];
             rowscale[r] = usc;
             if (cr.field < 0)
               rowinfo[r] = make_int4(0, 0, cr.trip, -1);
             else if (ns >= MAX_SEG)  // no reduction slot: direct atomics (total > RED_CAP)
-              rowinfo[r] = make_int4(0, 0, cr.trip, cr.nu3);
+              rowinfo[r] = make_int4(0, sw, cr.trip, cr.nu3);
+            else if (sw)
+              rowinfo[r] = make_int4(base + (P2 - 1) * E + (cr.nu3 - lo) + P2 - 1, E | sw, cr.trip,
+                                     cr.nu3);
             else
               rowinfo[r] = make_int4(base + (P2 - 1) * E + hi - cr.nu3, E, cr.trip, cr.nu3);
           }
@@ -733,14 +751,18 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
       const int m = 32 * quad + lane;
       const int4 ri = rowinfo[m];
       const bool row_ok = ri.w >= 0;
+      const bool swr = (ri.y >> 16) != 0;  // row (i, nu1) against pairs (nu2, nu3)
+      const int Er = ri.y & 0xffff, Fr = swr ? Er + 1 : Er - 1;
       const double rsc = F16 && row_ok ? rowscale[m] : 1.0;
       // the group's fields in registers: the loop below writes memory through
-      // atomics, which would otherwise make every field a reload
-      const int nu1_hi = G.nu1_hi, nu2_hi = G.nu2_hi;
+      // atomics, which would otherwise make every field a reload.  Kept pairs:
+      // inside the block, and nu1 <= nu2 (pa - pb <= dmax) on a rectangle that
+      // straddles the diagonal of a one-ring pair operand
+      const int pa_hi = G.nu1_hi - t.nu1_0, pb_hi = G.nu2_hi - t.nu2_0;
+      const int dmax = t.diag ? t.nu2_0 - t.nu1_0 : P1;
       const bool fast = use_red && G.out_full == nullptr;  // collapse only: shared reduction
       const double tn = (G.out_full && row_ok) ? G.tnorm[ri.z] * rsc : 0.0;
       const int n2 = 2 * G.nc - 1;
-      const int nu1_0 = t.nu1_0, nu2_0 = t.nu2_0;
       const uint32_t red_row = smem_u32(red) + 4u * (uint32_t)ri.x;
       for (int ch = 0; ch < 256 / 32; ++ch) {
         uint32_t v[32];
@@ -751,8 +773,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
           for (int j = 0; j < 32; ++j) {
             const int p = half * 256 + ch * 32 + j;
             const int pa = p >> 4, pb = p & 15;
-            if (nu1_0 + pa >= nu1_hi || nu2_0 + pb >= nu2_hi) continue;
-            red_add_shared(red_row + 4u * (uint32_t)((pa - pb) * ri.y + pb), __uint_as_float(v[j]));
+            if (pa >= pa_hi || pb >= pb_hi || pa - pb > dmax) continue;
+            red_add_shared(red_row + 4u * (uint32_t)(pa * Er - pb * Fr), __uint_as_float(v[j]));
           }
           continue;
         }
@@ -761,18 +783,20 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
           const int p = half * 256 + ch * 32 + j;
           const int pa = p >> 4, pb = p & 15;
           const int nu1 = t.nu1_0 + pa, nu2 = t.nu2_0 + pb;
-          if (nu1 >= G.nu1_hi || nu2 >= G.nu2_hi) continue;
+          if (pa >= pa_hi || pb >= pb_hi || pa - pb > dmax) continue;
           const float sv = __uint_as_float(v[j]);
           if (use_red) {
-            red_add_shared(red_row + 4u * (uint32_t)((pa - pb) * ri.y + pb), sv);
+            red_add_shared(red_row + 4u * (uint32_t)(pa * Er - pb * Fr), sv);
           } else if (G.dsum) {
+            // separations (nu1 - nu3, nu2 - nu3); a swapped row holds nu1 and the
+            // pair (nu2, nu3)
+            const int e1 = swr ? ri.w - nu2 : nu1 - ri.w, e2 = swr ? nu1 - nu2 : nu2 - ri.w;
             const long long o = (long long)b * G.dsum_bstride +
-                                ((long long)ri.z * n2 + (nu1 - ri.w + G.nc - 1)) * n2 +
-                                (nu2 - ri.w + G.nc - 1);
+                                ((long long)ri.z * n2 + (e1 + G.nc - 1)) * n2 + (e2 + G.nc - 1);
             if (BS_CHK(o, (long long)G.batch * G.dsum_bstride, 31))
               atomicAdd(G.dsum + o, (double)sv * rsc);
           }
-          if (G.out_full) {
+          if (G.out_full && !swr) {
             const long long o = (long long)b * G.full_bstride +
                                 (((long long)ri.z * G.nc + nu1) * G.nc + nu2) * G.nc + ri.w;
             if (BS_CHK(o, (long long)G.batch * G.full_bstride, 34))
@@ -792,9 +816,28 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
         // entry (walking the buffer linearly would step along a diagonal of the plane)
         const int ns = *nseg_s;
         for (int sg = 0; sg < ns; ++sg) {
-          const int4 si = seginfo[sg];  // (base, E, trip, hi)
-          const int E = si.y;
+          const int4 si = seginfo[sg];  // (base, E | swapped << 16, trip, hi)
+          const int E = si.y & 0xffff;
           const double sc = F16 ? segscale[sg] : 1.0;
+          if (si.y >> 16) {
+            // swapped rows: entry (dd, e2) sits at d1 = nu1 - nu3 = e2 + c1 and
+            // d2 = nu2 - nu3 = dd + c2, so plane row e2 holds the contiguous run dd
+            const int lo = si.w - (E - P2);
+            const int c1 = lo - (P2 - 1) - t.nu2_0 + G.nc - 1;
+            const int c2 = t.nu1_0 - t.nu2_0 - (P2 - 1) + G.nc - 1;
+            double *plane = G.dsum + (long long)b * G.dsum_bstride + (long long)si.z * n2 * n2;
+            const float *rs = red + si.x;
+            for (int e2 = pw; e2 < E; e2 += NPROD) {
+              const long long row = (long long)(e2 + c1) * n2;
+              for (int dd = lane; dd < P1 + P2 - 1; dd += 32) {
+                const float v = rs[dd * E + e2];
+                if (v == 0.f) continue;
+                if (BS_CHK(e2 + c1, n2, 35) && BS_CHK(dd + c2, n2, 36))
+                  atomicAdd(plane + row + (dd + c2), F16 ? (double)v * sc : (double)v);
+              }
+            }
+            continue;
+          }
           const int d1base = t.nu1_0 - (P2 - 1) - si.w + G.nc - 1;  // d1 index = dd + e2 + d1base
           const int d2base = t.nu2_0 - si.w + G.nc - 1;             // d2 index = e2 + d2base
           double *plane = G.dsum + (long long)b * G.dsum_bstride + (long long)si.z * n2 * n2;

@@ -90,6 +90,31 @@ __global__ void k_zero_planes(double *__restrict__ dsum, const int *__restrict__
   }
 }
 
+// Channel-symmetric accumulation: the orderings of a repeated ring's channels
+// that were not contracted, copied from the ones that were.  list[k] = 2 t + kind:
+//   kind 0, ring triple (i, i, l):       S(d1, d2) = S(d2, d1)       where d1 > d2
+//   kind 1, ring triple (i, j, j), i < j: S(d1, d2) = S(d1 - d2, -d2) where d2 > 0
+// (d1 = nu1 - nu3, d2 = nu2 - nu3; exchanging nu1, nu2 or nu2, nu3).  Sources are
+// never targets, so the copy is race-free; a source off the plane is 0.
+__global__ void k_symmetrize(double *__restrict__ dsum, const int *__restrict__ list, int ntrip,
+                             int nc, int r0, int nr, int c0, int ncol) {
+  const int code = list[blockIdx.y], b = blockIdx.z;
+  const int n2 = 2 * nc - 1;
+  double *o = dsum + ((long long)b * ntrip + (code >> 1)) * (long long)n2 * n2;
+  const long long n = (long long)nr * ncol;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int r = r0 + (int)(t / ncol), c = c0 + (int)(t % ncol);
+    const int d1 = r - (nc - 1), d2 = c - (nc - 1);
+    if ((code & 1) == 0) {
+      if (d1 > d2) o[(long long)r * n2 + c] = o[(long long)c * n2 + r];
+    } else if (d2 > 0) {
+      const int s1 = d1 - d2 + nc - 1;
+      o[(long long)r * n2 + c] = s1 >= 0 ? o[(long long)s1 * n2 + (nc - 1 - d2)] : 0.0;
+    }
+  }
+}
+
 __device__ void dft_direct(const float2 *x, float2 *y, int N, const float2 *tw, float sign) {
   for (int k = threadIdx.x; k < N; k += blockDim.x) {
     float2 acc = make_float2(0.f, 0.f);
@@ -296,6 +321,16 @@ cudaError_t launch_zero_planes(double *dsum, const int *trips, int ntr, int batc
   const long long n = (long long)nr * ncol;
   dim3 grid((unsigned)std::min<long long>((n + 255) / 256, 256), ntr, batch);
   k_zero_planes<<<grid, 256, 0, s>>>(dsum, trips, ntr, ntrip, n2, box[0], nr, box[2], ncol);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_symmetrize(double *dsum, const int *list, int nlist, int batch, int ntrip,
+                              int nc, const int *box, cudaStream_t s) {
+  const int nr = box[1] - box[0] + 1, ncol = box[3] - box[2] + 1;
+  if (nlist == 0 || nr <= 0 || ncol <= 0) return cudaSuccess;
+  const long long n = (long long)nr * ncol;
+  dim3 grid((unsigned)std::min<long long>((n + 255) / 256, 256), nlist, batch);
+  k_symmetrize<<<grid, 256, 0, s>>>(dsum, list, ntrip, nc, box[0], nr, box[2], ncol);
   return cudaGetLastError();
 }
 

@@ -144,6 +144,7 @@ void compute_layout(bs_plan p) {
   L.mlptab = take(((size_t)p->ntrip * 4 + 36) * sizeof(float));
   L.ztrips = take((size_t)p->ntrip * sizeof(int));
   L.clos = take((size_t)p->ntrip * sizeof(int));
+  L.symtrips = take((size_t)p->ntrip * sizeof(int));
   L.closrings = take((size_t)p->ntrip * 3 * sizeof(int));
   // monopole binning constants: FP64 kperp [nb], kpar [nc]; FP32 kperp, kpar,
   // squared k1 edges [<= 1025], mu and t thresholds [<= 1025 each]
@@ -339,11 +340,20 @@ bs_status run_counts(bs_plan p, const int8_t *lab_dev, cudaStream_t s) {
                           cudaMemcpyHostToDevice, s));
   p->clos.clear();
   p->closrings.clear();
+  p->sym_trips.clear();
   for (int t = 0; t < p->ntrip; ++t)
     if (p->T[t] > 0) {
       p->clos.push_back(t);
       for (int k = 0; k < 3; ++k) p->closrings.push_back(p->trips[3 * t + k]);
+      const int i = p->trips[3 * t], j = p->trips[3 * t + 1], l = p->trips[3 * t + 2];
+      if (i == j)
+        p->sym_trips.push_back(2 * t);
+      else if (j == l)
+        p->sym_trips.push_back(2 * t + 1);
     }
+  if (!p->sym_trips.empty())
+    BS_CUDA(cudaMemcpyAsync(p->at<int>(p->L.symtrips), p->sym_trips.data(),
+                            p->sym_trips.size() * sizeof(int), cudaMemcpyHostToDevice, s));
   if (!p->clos.empty()) {
     BS_CUDA(cudaMemcpyAsync(p->at<int>(p->L.clos), p->clos.data(), p->clos.size() * sizeof(int),
                             cudaMemcpyHostToDevice, s));
@@ -475,9 +485,18 @@ bs_status upload_nnu(bs_plan p, cudaStream_t s) {
   return BS_OK;
 }
 
+bs_status sym_fill(bs_plan p, cudaStream_t s) {
+  if (p->sym_state != 2) return BS_OK;
+  BS_CUDA(launch_symmetrize(p->at<double>(p->L.dsum), p->at<int>(p->L.symtrips),
+                            (int)p->sym_trips.size(), p->batch, p->ntrip, p->nc, p->dbox, s));
+  p->sym_state = 3;
+  return BS_OK;
+}
+
 bs_status delta_reset(bs_plan p, cudaStream_t s) {
   std::fill(p->nnu.begin(), p->nnu.end(), 0LL);
   p->nnu_dirty = true;
+  p->sym_state = 0;
   const size_t n2 = (size_t)(2 * p->nc - 1);
   if (!p->dsum_clean || !p->counts_ready) {
     BS_CUDA(cudaMemsetAsync(p->at<double>(p->L.dsum), 0,
@@ -534,6 +553,11 @@ std::vector<TcGroup> build_tc_work(bs_plan p, const int *blk, int group_base,
     G.nslot = std::max(1, L.nslot);
   }
   if (w3 == 0 || blk[1] <= blk[0] || blk[3] <= blk[2]) return groups;
+  // channel-symmetric accumulation of a cube block S x S x S: ring triples with a
+  // repeated ring are contracted for one ordering of its channels only (the
+  // ring pair (i, i) keeps nu1 <= nu2; the triple (i, j, j), i < j, moves to the
+  // ring pair (j, j) as swapped rows (i, nu1) with nu2 <= nu3)
+  const bool sym = accumulate == 2;
   // column lists per (level, ring pair): fields (l, nu3) of the level's slots,
   // runs padded to multiples of 8 so TMA boxes of 8 fields never straddle rings
   struct PairList {
@@ -542,17 +566,25 @@ std::vector<TcGroup> build_tc_work(bs_plan p, const int *blk, int group_base,
   std::vector<PairList> pl;
   for (int lv = 0; lv < nlev; ++lv) {
     const Level &L = p->levels[lv];
+    auto add_run = [&](int ring, int t, int swapped) {
+      for (int q = 0; q < run; ++q) {
+        const int n3 = blk[4] + q;
+        cols.push_back(ColEntry{q < w3 ? L.slot_of[ring] * nc + n3 : -1, t, n3, swapped});
+      }
+    };
     for (int i = 0; i < nb; ++i)
       for (int j = i; j < nb; ++j) {
         if (L.slot_of[i] < 0 || L.slot_of[j] < 0) continue;
         const int off = (int)cols.size();
-        for (int l = j; l < nb; ++l) {
+        if (sym && i == j)
+          for (int k = 0; k < i; ++k) {  // ring triples (k, i, i): rows (k, nu1)
+            const int t = p->trip_of[((size_t)k * nb + i) * nb + i];
+            if (p->T[t] > 0 && p->lev_of_trip[t] == lv) add_run(k, t, 1);
+          }
+        for (int l = (sym && i < j) ? j + 1 : j; l < nb; ++l) {
           const int t = p->trip_of[((size_t)i * nb + j) * nb + l];
           if (p->T[t] <= 0 || p->lev_of_trip[t] != lv) continue;
-          for (int q = 0; q < run; ++q) {
-            const int n3 = blk[4] + q;
-            cols.push_back(ColEntry{q < w3 ? L.slot_of[l] * nc + n3 : -1, t, n3, 0});
-          }
+          add_run(l, t, 0);
         }
         const int n = (int)cols.size() - off;
         if (n > 0) pl.push_back(PairList{lv, L.slot_of[i], L.slot_of[j], off, n});
@@ -579,10 +611,18 @@ std::vector<TcGroup> build_tc_work(bs_plan p, const int *blk, int group_base,
     for (const PairList &q : pl)
       for (int c0 = 0; c0 < q.n; c0 += 256)
         for (int a1 = 0; a1 < n1b; ++a1)
-          for (int a2 = 0; a2 < n2b; ++a2)
+          for (int a2 = 0; a2 < n2b; ++a2) {
+            const int x0 = blk[0] + 32 * a1, y0 = blk[2] + 16 * a2;
+            int diag = 0;
+            if (sym && q.si == q.sj) {  // one-ring pair operand: keep nu1 <= nu2
+              const int x1 = std::min(x0 + 31, blk[1] - 1), y1 = std::min(y0 + 15, blk[3] - 1);
+              if (x0 > y1) continue;  // every pair has nu1 > nu2
+              diag = x1 > y0 ? 1 : 0;
+            }
             for (int k = 0; k < nks[q.lv]; ++k)
-              tiles.push_back(TcTile{group_base + q.lv, b, q.si, q.sj, blk[0] + 32 * a1,
-                                     blk[2] + 16 * a2, q.off, q.n, c0, k, {0, 0}});
+              tiles.push_back(TcTile{group_base + q.lv, b, q.si, q.sj, x0, y0, q.off, q.n, c0, k,
+                                     diag, 0});
+          }
   // heaviest tiles first: static round-robin over persistent CTAs then balances
   std::stable_sort(tiles.begin() + t0, tiles.end(), [&](const TcTile &x, const TcTile &y) {
     return groups[x.group - group_base].kseg_len > groups[y.group - group_base].kseg_len;
@@ -1060,6 +1100,22 @@ bs_status bs_mabs(bs_plan p, const int32_t *block, double *out_full, int accumul
   if (p->d.precision != BS_PREC_FP32 && p->d.precision != BS_PREC_SPLIT_BF16 &&
       p->d.precision != BS_PREC_SPLIT_FP16)
     return fail(p, BS_ERR_UNSUPPORTED, "precision");
+  if (accumulate < 0 || accumulate > 2) return fail(p, BS_ERR_ARG, "accumulate must be 0, 1 or 2");
+  if (accumulate == 2) {
+    // channel-symmetric accumulation of a cube block S x S x S
+    if (out_full) return fail(p, BS_ERR_ARG, "accumulate = 2 writes the collapse sums only (out_full_dev must be NULL)");
+    if (blk[0] != blk[2] || blk[0] != blk[4] || blk[1] != blk[3] || blk[1] != blk[5])
+      return fail(p, BS_ERR_ARG, "accumulate = 2 needs a cube block (the same range on nu1, nu2, nu3)");
+    if (p->d.precision == BS_PREC_FP32 || p->general || p->chans)
+      return fail(p, BS_ERR_UNSUPPORTED,
+                  "accumulate = 2 needs a split-precision plan without general input or per-channel sampling");
+    if (p->sym_state == 1)
+      return fail(p, BS_ERR_STATE,
+                  "accumulate = 2 after ordinary blocks: reset the collapse sums first");
+  } else if (accumulate == 1) {
+    bs_status sf = sym_fill(p, s);  // ordinary blocks add to complete sums
+    if (sf != BS_OK) return sf;
+  }
   if (!out_full && !accumulate) return BS_OK;
   const WsLayout &L = p->L;
   const long long full_bstride = (long long)p->ntrip * nc * nc * nc;
@@ -1139,7 +1195,10 @@ bs_status bs_mabs(bs_plan p, const int32_t *block, double *out_full, int accumul
     BS_CUDA(launch_combine4_full(out_full, p->ubatch, p->ntrip, nc, blk, user_full, s));
   if (user_full && p->chans)  // tnorm cancels in the ratio; 1/A stays
     BS_CUDA(launch_ratio2_full(out_full, p->ubatch, p->ntrip, nc, blk, 1.0 / p->normA, user_full, s));
-  if (accumulate) accumulate_block_nnu(p, blk);
+  if (accumulate) {
+    accumulate_block_nnu(p, blk);
+    p->sym_state = accumulate == 2 ? 2 : 1;
+  }
   return BS_OK;
 }
 
@@ -1161,6 +1220,8 @@ bs_status bs_delta_export(bs_plan p, double *sums_dev, int64_t *nnu_host, void *
   if (st != BS_OK) return st;
   st = check_device_error(p, s);
   if (st != BS_OK) return st;
+  st = sym_fill(p, s);
+  if (st != BS_OK) return st;
   const size_t n2 = (size_t)(2 * p->nc - 1);
   if (sums_dev)
     BS_CUDA(cudaMemcpyAsync(sums_dev, p->at<double>(p->L.dsum),
@@ -1180,6 +1241,9 @@ bs_status bs_delta_import(bs_plan p, const double *sums_dev, const int64_t *nnu_
   if (!p->loaded) return fail(p, BS_ERR_STATE, "bs_delta_import before bs_grid_load");
   bs_status st = prepare(p, s);
   if (st != BS_OK) return st;
+  st = sym_fill(p, s);  // the imported sums add to complete ones
+  if (st != BS_OK) return st;
+  p->sym_state = 1;
   const size_t n2 = (size_t)(2 * p->nc - 1);
   const long long n = (long long)p->batch * p->ntrip * n2 * n2;
   double *d = p->at<double>(p->L.dsum);
@@ -1263,6 +1327,8 @@ bs_status bs_mabs_delta(bs_plan p, double *out, void *stream) {
   if (st != BS_OK) return st;
   st = upload_nnu(p, s);
   if (st != BS_OK) return st;
+  st = sym_fill(p, s);
+  if (st != BS_OK) return st;
   return delta_out(p, out, false, s);
 }
 
@@ -1276,6 +1342,8 @@ bs_status bs_mabs_delta_closable(bs_plan p, double *out, void *stream) {
   st = check_device_error(p, s);
   if (st != BS_OK) return st;
   st = upload_nnu(p, s);
+  if (st != BS_OK) return st;
+  st = sym_fill(p, s);
   if (st != BS_OK) return st;
   return delta_out(p, out, true, s);
 }
@@ -1291,6 +1359,8 @@ bs_status bs_bs3d(bs_plan p, double *out, void *stream) {
   if (st != BS_OK) return st;
   st = upload_nnu(p, s);
   if (st != BS_OK) return st;
+  st = sym_fill(p, s);
+  if (st != BS_OK) return st;
   return bs3d_out(p, out, false, s);
 }
 
@@ -1304,6 +1374,8 @@ bs_status bs_bs3d_closable(bs_plan p, double *out, void *stream) {
   st = check_device_error(p, s);
   if (st != BS_OK) return st;
   st = upload_nnu(p, s);
+  if (st != BS_OK) return st;
+  st = sym_fill(p, s);
   if (st != BS_OK) return st;
   return bs3d_out(p, out, true, s);
 }

@@ -13,7 +13,7 @@ namespace bsi {
 struct WsLayout {
   size_t label, efflabel, cells, uext, tripof, valid, twM, twN, tnorm, T, nnu, cols, ptiles, tctiles,
       G, F, Fhi, Flo, dsum, tmp3d, herm, err, maps, tcgroup, mlptab, ztrips, clos, closrings, mono, cyl,
-      errn, errtab, gvis, total;
+      errn, errtab, gvis, symtrips, total;
 };
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
@@ -60,6 +60,13 @@ struct bs_plan_s {
   // reset: rows [0] .. [1], columns [2] .. [3] (empty when [1] < [0])
   int dbox[4] = {0, -1, 0, -1};
   std::vector<int> zero_trips;    // closable ring triples (the only planes ever accumulated)
+  // closable ring triples with a repeated ring, 2 t + kind (0: (i, i, l), 1: (i, j, j),
+  // i < j; device copy at L.symtrips), and the state of the collapse sums since the
+  // last reset: 0 nothing accumulated, 1 ordinary blocks (or imported sums), 2
+  // channel-symmetric cubes with the left-out orderings not yet filled in, 3 the
+  // same, filled in
+  std::vector<int> sym_trips;
+  int sym_state = 0;
   std::vector<int> clos;          // ring triples with T > 0, ascending (device copy at L.clos)
   std::vector<int> closrings;     // [clos.size()][3] rings (i, j, l) of those triples
   std::vector<unsigned char> mono_tab;  // k tables and thresholds of the last monopole call
@@ -135,6 +142,8 @@ bs_status run_counts(bs_plan p, const int8_t *lab_dev, cudaStream_t s);
 bs_status ensure_tensor_maps(bs_plan p, cudaStream_t s);
 bs_status check_device_error(bs_plan p, cudaStream_t s);
 void accumulate_block_nnu(bs_plan p, const int *blk);
+// Fills in the channel orderings a symmetric accumulation left out (state 2 -> 3).
+bs_status sym_fill(bs_plan p, cudaStream_t s);
 // Adds the unfolded sampling of channel block blk under the channel validity
 // `valid` to plane[(d1 + nc - 1) * (2nc - 1) + d2 + nc - 1].
 void add_block_sampling(int nc, const std::vector<uint8_t> &valid, const int *blk,

@@ -32,6 +32,13 @@ def blocks_of(nc: int, bsz: int, bsz3: int | None = None):
     return out
 
 
+def cubes_of(nc: int, side: int):
+    """Sub-band cubes S x S x S, S = [s, s + side) (the last one ragged), as
+    blocks: the job of channel-symmetric accumulation (bs_mabs accumulate = 2),
+    which takes only cubes.  Each cube is one sub-band's whole channel cube."""
+    return [(s, min(nc, s + side)) * 3 for s in range(0, nc, side)]
+
+
 def rank_block(jobs, step: int, world: int, rank: int):
     """Block of `rank` at `step` (steps cycle through the job)."""
     return jobs[(step * world + rank) % len(jobs)]

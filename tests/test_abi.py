@@ -33,7 +33,7 @@ def test_header_declarations_exported(lib):
 
 
 def test_abi_version(lib):
-    assert lib.bs_abi_version() == bs.ABI_VERSION == 12
+    assert lib.bs_abi_version() == bs.ABI_VERSION == 13
 
 
 def test_binding_constants_match_header():

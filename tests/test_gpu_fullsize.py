@@ -8,8 +8,9 @@ the kappa-normalised error is formed with the oracle's value on |V|.  At
 every sampled point the error bound of bs_mabs_error_bound must cover the
 error, and well-conditioned points (kappa u <= tol / 10) must meet the
 tolerance in relative error.  Counts of all 1540 ring triples are compared
-exactly.  A 512^2 grid with 24 log rings (image side 768) is sampled the
-same way on a small channel block."""
+exactly.  The benchmark's channel-symmetric 256^3 cube is sampled the same
+way.  A 512^2 grid with 24 log rings (image side 768) is sampled on a small
+channel block."""
 import numpy as np
 import pytest
 
@@ -122,6 +123,48 @@ def test_bench_block_sampled_parity():
     plan.close()
     assert np.all(cnt > 0)
     _check_points(got, want, babs, beta, 1, 1e-3, "bench block 128 x 128 x 256")
+
+
+def test_bench_symmetric_cube_sampled_parity():
+    """The benchmark's exact launch: split BF16, per-triple image sides, the
+    256^3 channel cube with the channel symmetry of repeated rings
+    (accumulate = 2).  Points on (i, i, l) and (i, j, j) triples at
+    separations that the contraction computes and ones that only the fill-in
+    provides, and on triples of three different rings."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2506_10526_gb300 as bs
+    vis = synth.sky_visibilities(NT, NC, 2000, f_ng=0.5, sigma=0.5)
+    plan = bs.Plan(NT, NC, EDGES, precision=1, multires=True)
+    plan.grid_load(torch.from_numpy(vis[None]).cuda())
+    w = 256
+    plan.mabs(block=(0, w) * 3, symmetric=True)
+    n2 = 2 * NC - 1
+    out = torch.empty((1, plan.ntrip, n2, n2), dtype=torch.float64, device="cuda")
+    plan.mabs_delta(out)
+    bound, _ = plan.error_bound()
+    tri, _ = plan.counts()
+    torch.cuda.synchronize()
+    trips = oracle.ring_triples(NB)
+    pts = []
+    for kind in ("ii", "jj", "-"):
+        ks = [k for k, t in enumerate(trips) if tri[k] > 0 and
+              kind == ("ii" if t[0] == t[1] else ("jj" if t[1] == t[2] else "-"))]
+        for n, k in enumerate(ks[:2] + [ks[len(ks) // 3]]):
+            # (d1 > d2) is filled in for (i, i, l), (d2 > 0) for (i, j, j)
+            ds = [(120, -30), (-30, 120), (150, 30), (-100, -200), (0, 0), (255 - n, 1)]
+            for d in ds[:2] if n == 2 else ds:  # fewer points on the larger rings
+                pts.append((*trips[k], *d))
+    sub = vis[:w].astype(np.complex128)
+    want, cnt = oracle.delta_points(sub, EDGES, pts)
+    babs, _ = oracle.delta_points(np.abs(sub), EDGES, pts)
+    got = np.array([out[0, trips.index(tuple(p[:3])), p[3] + NC - 1, p[4] + NC - 1].item()
+                    for p in pts])
+    beta = np.array([bound[0, trips.index(tuple(p[:3]))].item() for p in pts])
+    plan.close()
+    assert np.all(cnt > 0)
+    _check_points(got, want, babs, beta, 1, 1e-3, "bench cube 256^3, channel-symmetric")
 
 
 @pytest.mark.parametrize("precision,multires", [(1, True), (0, False)])

@@ -14,7 +14,7 @@ torch = pytest.importorskip("torch")
 import torch.distributed as dist  # noqa: E402
 import torch.multiprocessing as mp  # noqa: E402
 
-from paper_2506_10526_gb300.sharding import (block_evals, blocks_of,  # noqa: E402
+from paper_2506_10526_gb300.sharding import (block_evals, blocks_of, cubes_of,  # noqa: E402
                                              merge_collapse, rank_block, reduce_step_stats)
 
 
@@ -117,3 +117,15 @@ def test_collapse_split_over_two_ranks_merges_to_the_one_rank_result():
     ok = ~np.isnan(want[keep])
     np.testing.assert_allclose(bbar[keep][ok], want[keep][ok], rtol=1e-12,
                                atol=1e-12 * np.nanmax(np.abs(want[keep])))
+
+
+def test_sub_band_cubes_are_disjoint_cubes_covering_the_band():
+    """cubes_of: every block is a cube (the same range on all three channels),
+    the sub-bands are disjoint and cover [0, nc), the last one ragged."""
+    for nc, side in [(768, 256), (20, 8), (7, 7), (5, 8)]:
+        cubes = cubes_of(nc, side)
+        for c in cubes:
+            assert c[0:2] == c[2:4] == c[4:6] and c[0] < c[1]
+        chans = [ch for c in cubes for ch in range(c[0], c[1])]
+        assert chans == list(range(nc))
+        assert sum(block_evals(c, 1) for c in cubes) == sum((c[1] - c[0]) ** 3 for c in cubes)
