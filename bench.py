@@ -924,7 +924,11 @@ def main():
     # channel-symmetric sub-band cubes (accumulate = 2): one more kernel per step fills
     # in the channel orderings of repeated rings that the contraction leaves out
     sym = bool(w.get("cube")) and not args.ordinary and args.precision != "fp32"
-    launches_per_step = (3 if args.precision == "split_fp16" else 2) * nlev + 7 + (1 if sym else 0)
+    # a symmetric cube wider than 128 channels contracts in one launch per 128 x 128
+    # sub-block of its pair plane
+    ncontract = ((w["cube"] + 127) // 128) ** 2 if sym else 1
+    launches_per_step = ((3 if args.precision == "split_fp16" else 2) * nlev + 7 + (1 if sym else 0)
+                         + ncontract - 1)
     sides = plan.trip_sides()
     # ring triples in the plan's order (i <= j <= l, lexicographic); a repeated ring
     # makes the triple symmetric under exchanging that ring's channels
@@ -1029,7 +1033,7 @@ def main():
     tr = profile_traffic(args.precision)
     roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                  "kernel": "k_contract_simt" if args.precision == "fp32" else "k_contract_tc",
-                 "avg_launch_ms": avg_ms,
+                 "avg_launch_ms": avg_ms, "launches_per_call": ncontract,
                  "traffic": None if tr is None else tr["bytes_per_unit"] * per_launch_evals})
     if args.precision != "fp32" and "bf16_tflops_sustained" in peaks:
         # the contraction runs back to back for the whole timed region: the measured

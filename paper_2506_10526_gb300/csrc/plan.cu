@@ -607,22 +607,22 @@ std::vector<TcGroup> build_tc_work(bs_plan p, const int *blk, int group_base,
     nks[lv] = (G.Kpad + G.kseg_len - 1) / G.kseg_len;
   }
   const size_t t0 = tiles.size();
+  auto add_tiles = [&](int b, const PairList &q, int c0, int a1, int a2) {
+    const int x0 = blk[0] + 32 * a1, y0 = blk[2] + 16 * a2;
+    int diag = 0;
+    if (sym && q.si == q.sj) {  // one-ring pair operand: keep nu1 <= nu2
+      const int x1 = std::min(x0 + 31, blk[1] - 1), y1 = std::min(y0 + 15, blk[3] - 1);
+      if (x0 > y1) return;  // every pair has nu1 > nu2
+      diag = x1 > y0 ? 1 : 0;
+    }
+    for (int k = 0; k < nks[q.lv]; ++k)
+      tiles.push_back(TcTile{group_base + q.lv, b, q.si, q.sj, x0, y0, q.off, q.n, c0, k, diag, 0});
+  };
   for (int b = 0; b < p->batch; ++b)
     for (const PairList &q : pl)
       for (int c0 = 0; c0 < q.n; c0 += 256)
         for (int a1 = 0; a1 < n1b; ++a1)
-          for (int a2 = 0; a2 < n2b; ++a2) {
-            const int x0 = blk[0] + 32 * a1, y0 = blk[2] + 16 * a2;
-            int diag = 0;
-            if (sym && q.si == q.sj) {  // one-ring pair operand: keep nu1 <= nu2
-              const int x1 = std::min(x0 + 31, blk[1] - 1), y1 = std::min(y0 + 15, blk[3] - 1);
-              if (x0 > y1) continue;  // every pair has nu1 > nu2
-              diag = x1 > y0 ? 1 : 0;
-            }
-            for (int k = 0; k < nks[q.lv]; ++k)
-              tiles.push_back(TcTile{group_base + q.lv, b, q.si, q.sj, x0, y0, q.off, q.n, c0, k,
-                                     diag, 0});
-          }
+          for (int a2 = 0; a2 < n2b; ++a2) add_tiles(b, q, c0, a1, a2);
   // heaviest tiles first: static round-robin over persistent CTAs then balances
   std::stable_sort(tiles.begin() + t0, tiles.end(), [&](const TcTile &x, const TcTile &y) {
     return groups[x.group - group_base].kseg_len > groups[y.group - group_base].kseg_len;
@@ -630,10 +630,10 @@ std::vector<TcGroup> build_tc_work(bs_plan p, const int *blk, int group_base,
   return groups;
 }
 
-// Tensor-core contraction of one channel block of one plan (split BF16).
-bs_status mabs_tc(bs_plan p, const int *blk, double *out_full, int accumulate, cudaStream_t s) {
-  bs_status st = ensure_tensor_maps(p, s);
-  if (st != BS_OK) return st;
+// Tensor-core contraction of one channel block of one plan (split BF16): one launch.
+static bs_status mabs_tc_launch(bs_plan p, const int *blk, double *out_full, int accumulate,
+                                cudaStream_t s) {
+  bs_status st = BS_OK;
   const WsLayout &L = p->L;
   p->h_cols.clear();
   p->h_tctiles.clear();
@@ -661,6 +661,28 @@ bs_status mabs_tc(bs_plan p, const int *blk, double *out_full, int accumulate, c
   a.f16 = p->d.precision == BS_PREC_SPLIT_FP16 ? 1 : 0;
   if (a.stall_test) a.wait_limit_ns = 50000000LL;
   BS_CUDA(launch_contract_tc(a, p->nsm, s));
+  return BS_OK;
+}
+
+// A channel-symmetric cube wider than 128 channels runs as one launch per
+// 128 x 128 sub-block of its (nu1, nu2) pair plane, rows over the whole cube:
+// each launch has the tile structure of an ordinary 128 x 128 x 256 block,
+// whose concurrently running CTA pairs share field and FP32 rows in L2
+// (measured on the 256-channel MWA-like cube: 25-47 GB of DRAM reads per
+// launch, 153 GB per cube).
+bs_status mabs_tc(bs_plan p, const int *blk, double *out_full, int accumulate, cudaStream_t s) {
+  bs_status st = ensure_tensor_maps(p, s);
+  if (st != BS_OK) return st;
+  constexpr int SUB = 128;
+  if (accumulate != 2 || blk[1] - blk[0] <= SUB)
+    return mabs_tc_launch(p, blk, out_full, accumulate, s);
+  for (int s1 = blk[0]; s1 < blk[1]; s1 += SUB)
+    for (int s2 = blk[2]; s2 < blk[3]; s2 += SUB) {
+      const int sub[6] = {s1, std::min(blk[1], s1 + SUB), s2, std::min(blk[3], s2 + SUB),
+                          blk[4], blk[5]};
+      st = mabs_tc_launch(p, sub, out_full, accumulate, s);
+      if (st != BS_OK) return st;
+    }
   return BS_OK;
 }
 

@@ -7,8 +7,9 @@ access instead of faulting.
   index and extent, and the library keeps working;
 * tiny grids (8^2, 16^2; plain FP32 and split BF16, one and several image
   sides, register-FFT and Stockham lengths) element by element against the
-  FP64 oracle through the checked library, then gridding of raw baselines
-  and the monopole and multipole binning, with no violation recorded;
+  FP64 oracle through the checked library, channel-symmetric cubes against
+  the ordinary accumulation, then gridding of raw baselines and the
+  monopole and multipole binning, with no violation recorded;
 * the ordinary library reports that it is not the checked build.
 Runs in child processes (BS_LIBRARY selects the library at load time)."""
 import os
@@ -70,6 +71,29 @@ CHILD = textwrap.dedent("""
         print("CASE", nt, nc, prec, multires, e_full, e_d, e3)
         assert e_full < TOL[prec] and e_d < TOL[prec] and e3 < 1e-5, (nt, nc, prec, e_full, e_d, e3)
         plan.close()
+    # channel-symmetric cubes (swapped rows, skipped and straddling pair
+    # rectangles, the fill-in) against the ordinary accumulation of the same cube
+    nt, nc = 16, 40
+    edges = list(synth.edges_linear(4, 8))
+    vis = torch.from_numpy(synth.sky_visibilities(nt, nc, seed=77)[None]).cuda()
+    plan = bs.Plan(nt, nc, edges, precision=1, multires=True)
+    for cube in [(0, 40) * 3, (3, 37) * 3]:
+        planes = []
+        for sym in (True, False):
+            plan.grid_load(vis)
+            plan.mabs(block=cube, accumulate=True, symmetric=sym)
+            dd = torch.empty((1, plan.ntrip, 2 * nc - 1, 2 * nc - 1), dtype=torch.float64,
+                             device="cuda")
+            plan.mabs_delta(dd)
+            planes.append(dd[0].cpu().numpy())
+        bound = plan.error_bound()[0][0].cpu().numpy()
+        tri, _ = plan.counts()
+        assert np.array_equal(np.isnan(planes[0]), np.isnan(planes[1]))
+        for k in np.flatnonzero(tri > 0):
+            d = np.abs(planes[0][k] - planes[1][k])[~np.isnan(planes[1][k])]
+            assert np.all(d <= 2 * bound[k] * (1 + 1e-9)), (cube, k)
+        print("SYMMETRIC", cube[:2], "ok")
+    plan.close()
     # gridding of raw baselines (the cell checks) and the monopole binning (the
     # bin checks) through the checked library
     from oracle import gridding as gr, monopole as mo

@@ -137,10 +137,11 @@ def _sample_points(tri, trips, lo, hi, rng):
 
 
 @pytest.mark.parametrize("precision,nc,S,nb", [(1, 48, (0, 48), 4), (2, 40, (3, 37), 5),
-                                               (1, 72, (8, 72), 4)])
+                                               (1, 72, (8, 72), 4), (1, 168, (4, 164), 4)])
 def test_symmetric_cube_sampled_against_oracle(precision, nc, S, nb):
     """Channel counts where some pair rectangles of a one-ring pair lie wholly
-    below the diagonal (not contracted) and others straddle it: sampled
+    below the diagonal (not contracted) and others straddle it, and a cube of
+    160 channels (one launch per 128 x 128 sub-block of the pair plane): sampled
     separations of the folded plane against the oracle's direct evaluation
     over the cube, the whole plane against the ordinary accumulation, and the
     exported sums of the two equal."""
