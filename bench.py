@@ -489,6 +489,24 @@ MC_GROUPS = [dict(nt=128, nchan=384, nb=12, edges=("log", 2.2, 64.0), batch=1),
              dict(nt=64, nchan=192, nb=8, edges=("linear", 0.0, 32.0), batch=2)]
 
 
+def contracted_flops(tri, sides, nb, dims, symmetric):
+    """Algorithmic FLOPs of contracting a channel block of dims = (n1, n2, n3)
+    channels: 2 M^2 per channel triple of every closable ring triple; with the
+    channel symmetry of a cube block (n channels), n^2 (n + 1) / 2 channel triples
+    (one ordering) for the ring triples with a repeated ring.  Ring triples in the
+    plan's order (i <= j <= l, lexicographic)."""
+    import numpy as np
+    per = 2.0 * np.asarray(sides, dtype=np.float64) ** 2
+    ok = np.asarray(tri) > 0
+    n3 = float(dims[0]) * dims[1] * dims[2]
+    if not symmetric:
+        return float(per[ok].sum()) * n3
+    rep = np.array([i == j or j == l for i in range(nb) for j in range(i, nb)
+                    for l in range(j, nb)])
+    n = float(dims[0])
+    return float(per[ok & ~rep].sum()) * n3 + float(per[ok & rep].sum()) * n * n * (n + 1) / 2
+
+
 def run_mc(dev, precision, iters=3):
     import numpy as np
     import torch
@@ -503,7 +521,8 @@ def run_mc(dev, precision, iters=3):
                                 dtype=torch.complex64, device=dev))
         ens.set_input(k, bufs[k])
     # algorithmic FLOPs of the contraction: sum over closable ring triples of 2 M^2 per
-    # channel triple, from a plan of the same shape
+    # channel triple, from a plan of the same shape; the full cubes of 64 channels or
+    # more run with the channel symmetry of repeated rings
     flops, evals = 0.0, 0
     for sp in specs:
         pl = bs.Plan(sp["nt"], sp["nchan"], sp["edges"], precision=precision, multires=True)
@@ -512,8 +531,10 @@ def run_mc(dev, precision, iters=3):
         tri, _ = pl.counts()
         sides = pl.trip_sides()
         ok = tri > 0
-        flops += sp["batch"] * float(np.sum(2.0 * sides[ok].astype(np.float64) ** 2)) * sp["nchan"] ** 3
-        evals += sp["batch"] * int(ok.sum()) * sp["nchan"] ** 3
+        nc = sp["nchan"]
+        flops += sp["batch"] * contracted_flops(tri, sides, len(sp["edges"]) - 1, (nc, nc, nc),
+                                                nc >= 64)
+        evals += sp["batch"] * int(ok.sum()) * nc ** 3
         pl.close()
     tiles = ens.autotune()
 
@@ -557,7 +578,7 @@ def run_mc(dev, precision, iters=3):
             for r in range(sp["batch"]):
                 gen1.generate(77, i * sp["batch"] + r, out=one_buf)
                 pl.grid_load(one_buf)
-                pl.mabs(accumulate=True)
+                pl.mabs(accumulate=True, symmetric=sp["nchan"] >= 64)  # as the ensemble
                 pl.mabs_delta_closable(dd)
                 pl.bs3d_closable(b3)
 
@@ -930,27 +951,15 @@ def main():
     launches_per_step = ((3 if args.precision == "split_fp16" else 2) * nlev + 7 + (1 if sym else 0)
                          + ncontract - 1)
     sides = plan.trip_sides()
-    # ring triples in the plan's order (i <= j <= l, lexicographic); a repeated ring
-    # makes the triple symmetric under exchanging that ring's channels
     nb = w["nb"]
-    rep = np.array([i == j or j == l for i in range(nb) for j in range(i, nb)
-                    for l in range(j, nb)])
     jobs = cubes_of(nc, w["cube"]) if sym else blocks_of(nc, w["block"], w.get("block3"))
 
     def block_evals(b):
         return nclos * (b[1] - b[0]) * (b[3] - b[2]) * (b[5] - b[4])
 
     def block_flops(b, symmetric):
-        """Algorithmic FLOPs of the contraction of block b: 2 M^2 per channel triple
-        of every closable ring triple; with the channel symmetry of a cube, n^2 (n + 1) / 2
-        channel triples (one ordering) for the ring triples with a repeated ring."""
-        n3 = (b[1] - b[0]) * (b[3] - b[2]) * (b[5] - b[4])
-        per = 2.0 * sides.astype(np.float64) ** 2
-        if not symmetric:
-            return float(np.sum(per[tri > 0])) * n3
-        n = b[1] - b[0]
-        half = n * n * (n + 1) / 2.0
-        return float(np.sum(per[(tri > 0) & ~rep]) * n3 + np.sum(per[(tri > 0) & rep]) * half)
+        return contracted_flops(tri, sides, nb, (b[1] - b[0], b[3] - b[2], b[5] - b[4]),
+                                symmetric)
 
     def step(i, ev=None, vis_in=None, out=None):
         b = rank_block(jobs, i, world, rank)

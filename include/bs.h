@@ -513,8 +513,11 @@ bs_status bs_mc_tuning(bs_mc mc, int *tiles_per_sm, int *tile_order);
  * nu1_hi, nu2_lo, nu2_hi, nu3_lo, nu3_hi} (default: the full cube): a
  * declared subset of the tiles of every realisation, for ensembles whose
  * full channel cubes are too large to run (the collapse and Eq. (dft) then
- * hold the separations of that block).  Drops prepared work and the captured
- * graph.  Errors: BS_ERR_ARG (group, NULL, block out of range or empty). */
+ * hold the separations of that block).  A cube block of 64 channels or
+ * more (the full cube included) is contracted with the channel symmetry of
+ * repeated rings, as bs_mabs with accumulate = 2.  Drops prepared work and
+ * the captured graph.  Errors: BS_ERR_ARG (group, NULL, block out of range
+ * or empty). */
 bs_status bs_mc_set_block(bs_mc mc, int group, const int32_t *block_host);
 /* One Monte Carlo step over all groups (asynchronous on cuda_stream). */
 bs_status bs_mc_run(bs_mc mc, int use_graph, void *cuda_stream);

@@ -7,7 +7,9 @@
 // only kernel launches and memsets, so it can be captured in a CUDA graph:
 //   per group  : shell masks + field FFTs (colpass, rowpass), zero the sums
 //   all groups : ONE persistent tensor-core contraction over the tiles of every
-//                group and realisation (full channel cube of each group)
+//                group and realisation (full channel cube of each group; on a
+//                cube of 64 channels or more, one ordering of a repeated
+//                ring's channels, the other filled in per group afterwards)
 //   per group  : fold/normalise (collapsed plane) and Eq. (dft), then a
 //                per-bin Welford update of mean and M2 over the realisations.
 // Tile lists, counts and the sampling N_nu depend only on the shapes and are
@@ -68,6 +70,10 @@ struct Group {
   double *stats = nullptr;      // 3 x (delta bins) then 3 x (bs3d bins): cnt, mean, m2
   long long nd = 0, nb3 = 0;    // bins per realisation
   int blk[6] = {0, 0, 0, 0, 0, 0};  // channel block each run contracts (set at create: full cube)
+  // channel symmetry of repeated rings (a cube block of 64 channels or more):
+  // the contraction covers one ordering, k_symmetrize the other, inside box
+  bool sym = false;
+  int box[4] = {0, -1, 0, -1};
 };
 
 }  // namespace
@@ -150,10 +156,22 @@ bs_status mc_prepare(bs_mc m, cudaStream_t s) {
     bs_plan p = m->groups[g].plan;
     const size_t c0 = cols.size();
     const int *blk = m->groups[g].blk;
+    // a cube block S x S x S is closed under exchanging the channels of a repeated
+    // ring: one ordering is contracted.  Below 64 channels every pair rectangle of a
+    // one-ring pair operand straddles the diagonal and nothing would be saved.
+    Group &gr = m->groups[g];
+    const int w = blk[1] - blk[0];
+    gr.sym = blk[0] == blk[2] && blk[0] == blk[4] && blk[1] == blk[3] && blk[1] == blk[5] &&
+             w >= 64 && !p->sym_trips.empty();
+    if (gr.sym) {
+      const int nc = p->nc;
+      gr.box[0] = gr.box[2] = std::max(0, nc - w);
+      gr.box[1] = gr.box[3] = std::min(2 * nc - 2, nc + w - 2);
+    }
     std::vector<ColEntry> gc;
     std::vector<TcTile> gt;
-    std::vector<TcGroup> G = build_tc_work(p, blk, (int)tgs.size(), gc, nullptr, gt, nullptr, 1,
-                                           m->min_tiles_factor * m->nsm);
+    std::vector<TcGroup> G = build_tc_work(p, blk, (int)tgs.size(), gc, nullptr, gt, nullptr,
+                                           gr.sym ? 2 : 1, m->min_tiles_factor * m->nsm);
     for (TcTile &t : gt) t.col_off += (int)c0;  // offsets into the concatenated list
     cols.insert(cols.end(), gc.begin(), gc.end());
     tiles.insert(tiles.end(), gt.begin(), gt.end());
@@ -215,6 +233,9 @@ bs_status mc_enqueue(bs_mc m, cudaStream_t s) {
   for (Group &gr : m->groups) {
     bs_plan p = gr.plan;
     const WsLayout &L = p->L;
+    if (gr.sym)
+      MC_CUDA(launch_symmetrize(p->at<double>(L.dsum), p->at<int>(L.symtrips),
+                                (int)p->sym_trips.size(), p->batch, p->ntrip, p->nc, gr.box, s));
     MC_CUDA(launch_delta_norm(p->at<double>(L.dsum), p->at<long long>(L.nnu),
                               p->at<double>(L.tnorm), gr.dout, p->batch, p->ntrip, p->nc,
                               nullptr, 0, p->at<double>(L.tmp3d), s));

@@ -230,3 +230,59 @@ def test_mc_checkpoint_and_resume(tmp_path):
     with pytest.raises(bs.BsError):
         other.restore(path)
     other.close()
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_mc_channel_symmetric_cubes_match_the_plan(precision):
+    """Groups whose channel block is a cube of 64 channels or more contract
+    one ordering of a repeated ring's channels and fill in the other: a full
+    72-channel cube, a 64-channel sub-cube (bs_mc_set_block) and an ordinary
+    24-channel group in one persistent launch.  The ensemble mean of the
+    collapsed plane equals the mean of the ordinary plan path on the same
+    realisations within the error bound, and so does the graph replay (its
+    shared-memory FP32 reductions may add in another order)."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2506_10526_gb300 as bs
+    edges = list(synth.edges_linear(4, 15))
+    specs = [dict(nt=32, nchan=72, edges=edges, batch=2, multires=True),
+             dict(nt=32, nchan=80, edges=edges, batch=1, multires=True),
+             dict(nt=32, nchan=24, edges=edges, batch=2, multires=True)]
+    blocks = [None, (8, 72) * 3, None]
+    vis = [np.stack([synth.sky_visibilities(s["nt"], s["nchan"], 8000 + 10 * g + b)
+                     for b in range(s["batch"])]) for g, s in enumerate(specs)]
+    means = []
+    for use_graph in (False, True):
+        ens = bs.Ensemble([dict(s, precision=precision) for s in specs])
+        bufs = [torch.from_numpy(v).cuda() for v in vis]
+        for g in range(len(specs)):
+            ens.set_input(g, bufs[g])
+            if blocks[g] is not None:
+                ens.set_block(g, blocks[g])
+        ens.run(use_graph=False)
+        if use_graph:
+            ens.reset()
+            ens.run(use_graph=True)
+        means.append([ens.stats(g, 0)[0] for g in range(len(specs))])
+        ens.close()
+    for g, s in enumerate(specs):
+        nc = s["nchan"]
+        planes, bounds = [], []
+        for b in range(s["batch"]):
+            plan = bs.Plan(s["nt"], nc, edges, precision=precision, multires=True)
+            plan.grid_load(torch.from_numpy(vis[g][b][None]).cuda())
+            plan.mabs(block=blocks[g], accumulate=True)
+            dd = torch.empty((1, plan.ntrip, 2 * nc - 1, 2 * nc - 1), dtype=torch.float64,
+                             device="cuda")
+            plan.mabs_delta(dd)
+            bounds.append(plan.error_bound()[0][0].cpu().numpy())
+            planes.append(dd[0].cpu().numpy())
+            plan.close()
+        want = np.mean(planes, axis=0)
+        beta = 2 * np.mean(bounds, axis=0) * (1 + 1e-9)
+        ok = ~np.isnan(want)
+        for got in (means[0][g], means[1][g]):
+            assert np.array_equal(np.isnan(got), np.isnan(want)), g
+            for k in range(want.shape[0]):
+                assert np.all(np.abs(got[k] - want[k])[ok[k]] <= beta[k]), (g, k)
