@@ -668,8 +668,8 @@ static bs_status mabs_tc_launch(bs_plan p, const int *blk, double *out_full, int
 // 128 x 128 sub-block of its (nu1, nu2) pair plane, rows over the whole cube:
 // each launch has the tile structure of an ordinary 128 x 128 x 256 block,
 // whose concurrently running CTA pairs share field and FP32 rows in L2
-// (measured on the 256-channel MWA-like cube: 25-47 GB of DRAM reads per
-// launch, 153 GB per cube).
+// (measured on the 256-channel MWA-like cube: 25-74 GB of DRAM reads per
+// launch, 153-205 GB per cube).
 bs_status mabs_tc(bs_plan p, const int *blk, double *out_full, int accumulate, cudaStream_t s) {
   bs_status st = ensure_tensor_maps(p, s);
   if (st != BS_OK) return st;
