@@ -1,6 +1,7 @@
 """The benchmark's reference arm (the FP64 CPU oracle, timed on the host)
 prints one JSON line with the keys the benchmark contract asks for; it runs
-on the CPU, so it is checked here on the tiny workload."""
+on the CPU, so it is checked here on the tiny workload.  The roofline's FLOP
+count of a channel-symmetric cube is checked against a brute-force count."""
 import json
 import os
 import subprocess
@@ -27,3 +28,31 @@ def test_reference_arm_json_line():
     assert d["e2e"] == {"value": d["value"], "unit": "evals/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
     assert d["config"]["workload"].startswith("tiny")
+
+
+def test_contracted_flops_count_one_ordering_of_repeated_rings():
+    """The roofline's FLOP count of a channel-symmetric cube: brute-force count of
+    the channel triples contracted (nu1 <= nu2 for (i, i, l), nu2 <= nu3 for
+    (i, j, j), i < j, every triple otherwise) against bench.contracted_flops."""
+    import itertools
+
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    nb, n = 3, 5
+    trips = [(i, j, l) for i in range(nb) for j in range(i, nb) for l in range(j, nb)]
+    rng = np.random.default_rng(3)
+    tri = rng.integers(0, 2, len(trips))
+    sides = rng.choice([8, 12, 16], len(trips))
+    want_sym = want_all = 0.0
+    for k, (i, j, l) in enumerate(trips):
+        if tri[k] == 0:
+            continue
+        for a, b, c in itertools.product(range(n), repeat=3):
+            f = 2.0 * sides[k] ** 2
+            want_all += f
+            if (i == j and a > b) or (i < j == l and b > c):
+                continue
+            want_sym += f
+    assert bench.contracted_flops(tri, sides, nb, (n, n, n), False) == want_all
+    assert bench.contracted_flops(tri, sides, nb, (n, n, n), True) == want_sym
