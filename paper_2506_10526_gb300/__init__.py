@@ -170,6 +170,15 @@ def _dptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _require(t, dtype, numel, what):
+    """Refuse a caller tensor whose dtype or element count differs from what the
+    entry point reads or writes, before its pointer reaches the library (the C
+    side receives bare pointers and cannot check their extent)."""
+    if t.dtype != dtype or t.numel() != numel:
+        raise ValueError(f"{what} must be {dtype} with {numel} elements "
+                         f"(got {t.dtype} with {t.numel()})")
+
+
 class Plan:
     """bs_plan_create / bs_plan_destroy.  Workspace comes from torch."""
 
@@ -281,6 +290,8 @@ class Plan:
             full = self._out(out_full, self.ntrip * self.nchan, self.nchan)
         blk = None
         if block is not None:
+            if len(block) != 6:
+                raise ValueError("block is (nu1_lo, nu1_hi, nu2_lo, nu2_hi, nu3_lo, nu3_hi)")
             self._blk = (ctypes.c_int32 * 6)(*[int(x) for x in block])
             blk = self._blk
         acc = 2 if symmetric else (1 if accumulate else 0)
@@ -462,17 +473,22 @@ class Plan:
         triangle)."""
         import numpy as np
         import torch
-        out = torch.empty((self.ntrip * self.nchan * self.nchan, MLP_FEATURES), dtype=torch.float32,
-                          device="cuda")
         fl = None
         if chan_flags is not None:
             self._mflags = np.ascontiguousarray(np.asarray(chan_flags, dtype=np.uint8))
+            if self._mflags.size != self.nchan:
+                raise ValueError("chan_flags must have nchan entries")
             fl = self._mflags.ctypes.data_as(ctypes.c_void_p)
+        out = torch.empty((self.ntrip * self.nchan * self.nchan, MLP_FEATURES), dtype=torch.float32,
+                          device="cuda")
         self._check(self._L.bs_mlp_features(self._h, fl, _dptr(out), _stream_ptr(stream)))
         return out
 
     def check_hermitian(self, vis, tol=1e-6, stream=None):
         """bs_check_hermitian; returns True when Hermitian within tol."""
+        import torch
+        _require(vis, torch.complex64, self.batch * self.nchan * self.nt ** 2,
+                 "vis [batch, nchan, nt, nt]")
         st = self._L.bs_check_hermitian(self._h, _dptr(vis), ctypes.c_double(tol),
                                         _stream_ptr(stream))
         if st == 5:
@@ -601,10 +617,13 @@ class Ensemble:
     def set_input(self, g, vis):
         """bs_mc_set_input: vis is a complex64 CUDA tensor [batch, nchan, nt, nt]
         that the caller keeps alive and refills before each run."""
+        if not 0 <= g < len(self.groups):
+            raise ValueError(f"group {g} out of range")
         spec = self.groups[g]
         want = (spec["batch"], spec["nchan"], spec["nt"], spec["nt"])
-        if tuple(vis.shape) != want:
-            raise ValueError(f"group {g} expects {want}, got {tuple(vis.shape)}")
+        if tuple(vis.shape) != want or vis.dtype != self._torch.complex64:
+            raise ValueError(f"group {g} expects complex64 {want}, got {vis.dtype} "
+                             f"{tuple(vis.shape)}")
         self._inputs = getattr(self, "_inputs", {})
         self._inputs[g] = vis
         self._check(self._L.bs_mc_set_input(self._h, g, _dptr(vis)))
@@ -612,6 +631,8 @@ class Ensemble:
     def set_flags(self, g, flags):
         """bs_mc_set_flags: uint8 [nchan] (1 = flagged) or None."""
         import numpy as np
+        if not 0 <= g < len(self.groups):
+            raise ValueError(f"group {g} out of range")
         if flags is None:
             self._check(self._L.bs_mc_set_flags(self._h, g, None))
             return
@@ -636,6 +657,8 @@ class Ensemble:
     def set_block(self, g, block):
         """bs_mc_set_block: channel block (nu1_lo, nu1_hi, nu2_lo, nu2_hi, nu3_lo, nu3_hi)
         that every run of group g contracts."""
+        if len(block) != 6:
+            raise ValueError("block is (nu1_lo, nu1_hi, nu2_lo, nu2_hi, nu3_lo, nu3_hi)")
         self._blk = (ctypes.c_int32 * 6)(*[int(x) for x in block])
         self._check(self._L.bs_mc_set_block(self._h, int(g), self._blk))
 
@@ -710,18 +733,34 @@ class Surrogate:
                                           self.n_total, 0))
         return p
 
+    def _rows(self, x, t=None):
+        """Row count of a feature matrix x float32 [n, d_in] (and targets t float32
+        [n]), refused when the kernels would read past either."""
+        import torch
+        if x.dim() != 2 or x.shape[1] != self.d:
+            raise ValueError(f"x must be [n, {self.d}]")
+        n = int(x.shape[0])
+        _require(x, torch.float32, n * self.d, f"x [n, {self.d}]")
+        if t is not None:
+            _require(t, torch.float32, n, "t [n]")
+        return n
+
     def set_params(self, p):
         import numpy as np
         p = np.ascontiguousarray(np.asarray(p, dtype=np.float32))
+        if p.size != self.n_total:
+            raise ValueError(f"params must hold {self.n_total} values")
         self._check(self._L.bs_mlp_params(self._h, p.ctypes.data_as(ctypes.c_void_p),
                                           self.n_total, 1))
 
     def fit_norm(self, x, t, stream=None):
+        self._rows(x, t)
         self._check(self._L.bs_mlp_fit_norm(self._h, _dptr(x), _dptr(t), int(x.shape[0]),
                                             _stream_ptr(stream)))
 
     def forward(self, x, stream=None):
         import torch
+        self._rows(x)
         y = torch.empty(x.shape[0], dtype=torch.float32, device="cuda")
         self._check(self._L.bs_mlp_forward(self._h, _dptr(x), int(x.shape[0]), _dptr(y),
                                            _stream_ptr(stream)))
@@ -734,6 +773,7 @@ class Surrogate:
 
     def grad(self, x, t, stream=None):
         import numpy as np
+        self._rows(x, t)
         g = np.empty(self.n_weights, np.float32)
         loss = np.zeros(1, np.float32)
         self._check(self._L.bs_mlp_grad(self._h, _dptr(x), _dptr(t), int(x.shape[0]),
@@ -743,6 +783,7 @@ class Surrogate:
 
     def train(self, x, t, steps, batch=8192, lr=2e-3, seed=7, stream=None):
         import numpy as np
+        self._rows(x, t)
         loss = np.zeros(1, np.float32)
         self._check(self._L.bs_mlp_train(self._h, _dptr(x), _dptr(t), int(x.shape[0]), int(steps),
                                          int(batch), ctypes.c_float(lr), ctypes.c_uint64(seed),

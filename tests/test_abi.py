@@ -1,10 +1,12 @@
 """CPU-side checks of the C-ABI library: it builds, loads, exports every
 symbol that include/bs.h declares, and refuses cleanly (no CPU fallback)
 when no sm_103a device is present.  No compute call runs here."""
+import contextlib
 import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 import paper_2506_10526_gb300 as bs
@@ -120,3 +122,91 @@ def test_counts_noalloc_binding_refuses_wrong_tensors():
     with pytest.raises(ValueError):
         bs.counts_noalloc(32, edges, torch.zeros(20, dtype=torch.int64),
                           ngrid=torch.ones((32, 32), dtype=torch.float64))
+
+
+class _NoLibrary:
+    """Stands in for the loaded library: any entry point that is called fails
+    the test, so a refusal must come before the call."""
+
+    def __getattr__(self, name):
+        def reached(*args):
+            raise AssertionError(f"{name} was called with unchecked arguments")
+        return reached
+
+
+def _bare(cls, **attrs):
+    """An instance of a binding class with the given attributes and no library
+    handle: the argument checks run before any call into the library."""
+    obj = object.__new__(cls)
+    obj.__dict__.update(attrs)
+    obj._h = None
+    obj._L = _NoLibrary()
+    return obj
+
+
+@contextlib.contextmanager
+def _refused():
+    """The call raises ValueError from a dtype or size check (the tensors here
+    live on the CPU, so the later 'expected a CUDA tensor' check must not be
+    what refuses them)."""
+    with pytest.raises(ValueError) as e:
+        yield
+    assert "CUDA tensor" not in str(e.value), str(e.value)
+
+
+def test_bindings_refuse_wrong_tensors_before_the_library():
+    """Entry points that read or write caller tensors through bare pointers:
+    the binding refuses a dtype or extent other than the one the kernels
+    touch, so no undersized buffer reaches the device."""
+    import torch
+    plan = _bare(bs.Plan, nt=16, nchan=4, batch=2, nbins=3, ntrip=10, general=False,
+                 chan_sampling=False)
+    with _refused():  # half the cells
+        plan.check_hermitian(torch.zeros((1, 4, 16, 16), dtype=torch.complex64))
+    with _refused():  # the right count of the wrong type
+        plan.check_hermitian(torch.zeros((2, 4, 16, 16), dtype=torch.complex128))
+    with _refused():
+        plan.grid_load(torch.zeros((2, 4, 16, 8), dtype=torch.complex64))
+    with _refused():
+        plan.grid_load(torch.zeros((2, 4, 16, 16), dtype=torch.complex64),
+                       ngrid=torch.ones((4, 16, 16), dtype=torch.float32))
+    with _refused():
+        plan.mabs(block=(0, 4, 0, 4))
+    with _refused():
+        plan.mabs_delta(torch.zeros((2, 10, 7, 7), dtype=torch.float32))
+    with _refused():
+        plan.bs3d(torch.zeros((2, 10, 4, 3), dtype=torch.float64))
+    with _refused():
+        plan.mlp_features(np.zeros(3, np.uint8))
+    with _refused():
+        plan.delta_import(torch.zeros((2, 10, 7, 6), dtype=torch.float64), np.zeros(49, np.int64))
+
+    net = _bare(bs.Surrogate, d=45, w=128, n_weights=100, n_total=192)
+    x = torch.zeros((8, 45), dtype=torch.float32)
+    t = torch.zeros(8, dtype=torch.float32)
+    for bad_x, bad_t in ((torch.zeros((8, 44), dtype=torch.float32), t),   # too few features
+                         (x.double(), t),                                  # FP64 rows
+                         (x, torch.zeros(7, dtype=torch.float32)),         # fewer targets
+                         (x, t.double())):
+        with _refused():
+            net.fit_norm(bad_x, bad_t)
+        with _refused():
+            net.grad(bad_x, bad_t)
+        with _refused():
+            net.train(bad_x, bad_t, steps=1)
+    with _refused():
+        net.forward(torch.zeros((8, 44), dtype=torch.float32))
+    with _refused():
+        net.set_params(np.zeros(191, np.float32))
+
+    ens = _bare(bs.Ensemble, groups=[dict(nt=16, nchan=4, batch=2)], _torch=torch)
+    with _refused():  # the right shape of the wrong type
+        ens.set_input(0, torch.zeros((2, 4, 16, 16), dtype=torch.float32))
+    with _refused():
+        ens.set_input(-1, torch.zeros((2, 4, 16, 16), dtype=torch.complex64))
+    with _refused():
+        ens.set_flags(1, np.zeros(4, np.uint8))
+    with _refused():
+        ens.set_flags(0, np.zeros(5, np.uint8))
+    with _refused():
+        ens.set_block(0, (0, 4, 0, 4, 0))
