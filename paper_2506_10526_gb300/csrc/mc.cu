@@ -104,7 +104,7 @@ struct bs_mc_s {
 namespace {
 
 bs_status mfail(bs_mc m, bs_status s, const std::string &msg) {
-  m->err = msg;
+  if (m) m->err = msg;  // a NULL handle has nowhere to keep the message
   return s;
 }
 

@@ -210,3 +210,41 @@ def test_bindings_refuse_wrong_tensors_before_the_library():
         ens.set_flags(0, np.zeros(5, np.uint8))
     with _refused():
         ens.set_block(0, (0, 4, 0, 4, 0))
+
+
+def test_null_handles_of_the_ensemble_surrogate_and_sky_entry_points(lib):
+    """Every entry point of the Monte Carlo ensemble, the surrogate network and
+    the sky generator refuses a NULL handle with BS_ERR_ARG (destroy accepts
+    it) on the host, without a device and without dereferencing it."""
+    c = ctypes.c_int()
+    u = ctypes.c_uint64()
+    blk = (ctypes.c_int32 * 6)(0, 1, 0, 1, 0, 1)
+    arr = (ctypes.c_int64 * 7)()
+    assert lib.bs_mc_destroy(None) == 0
+    assert lib.bs_mlp_destroy(None) == 0
+    assert lib.bs_sky_destroy(None) == 0
+    calls = [
+        lambda: lib.bs_mc_info(None, 0, arr, 7),
+        lambda: lib.bs_mc_set_input(None, 0, None),
+        lambda: lib.bs_mc_set_flags(None, 0, None),
+        lambda: lib.bs_mc_set_tuning(None, 1),
+        lambda: lib.bs_mc_autotune(None, None, ctypes.byref(c), None),
+        lambda: lib.bs_mc_tuning(None, None, None),
+        lambda: lib.bs_mc_set_block(None, 0, blk),
+        lambda: lib.bs_mc_run(None, 1, None),
+        lambda: lib.bs_mc_reset(None, None),
+        lambda: lib.bs_mc_stats(None, 0, 0, None, None, None, None),
+        lambda: lib.bs_mc_checkpoint(None, b"x", ctypes.c_uint64(0), None),
+        lambda: lib.bs_mc_restore(None, b"x", ctypes.byref(u), None),
+        lambda: lib.bs_mlp_params(None, None, ctypes.c_int64(0), 0),
+        lambda: lib.bs_mlp_fit_norm(None, None, None, 2, None),
+        lambda: lib.bs_mlp_forward(None, None, 1, None, None),
+        lambda: lib.bs_mlp_set_kernels(None, 0),
+        lambda: lib.bs_mlp_grad(None, None, None, 1, None, None, None),
+        lambda: lib.bs_mlp_train(None, None, None, 1, 1, 1, ctypes.c_float(1e-3),
+                                 ctypes.c_uint64(0), None, None),
+        lambda: lib.bs_mlp_features(None, None, None, None),
+        lambda: lib.bs_sky_generate(None, ctypes.c_uint64(0), ctypes.c_uint64(0), 1, None, None),
+    ]
+    for k, call in enumerate(calls):
+        assert call() == 1, k
