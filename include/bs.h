@@ -328,17 +328,24 @@ bs_status bs_bs3d_closable(bs_plan plan, double *out_dev, void *cuda_stream);
  *   c_acc   FP32 (1024 + ceil(M^2/1024) + 1) u; split modes
  *           2 u (3 ceil(M^2/16) + 1) (FP32 accumulation of the K16 MMAs)
  *   eps_fft (16 (ceil(log2 M) + 2) + 2) u
+ * General plans (complex estimates from the real evaluations S(t) at t = 0,
+ * 1, -1, 2): beta bounds the modulus of the complex error, the hypot of
+ * 2 b_0 + (b_1 + b_-1)/2 (real part) and (9 b_1 + b_-1 + 2 b_2 + 6 b_0)/6
+ * (imaginary part), b_t the bound above for the evaluation at t.
  *  bound_dev   double [batch][T_r], written; NaN for ring triples without a
  *              closed triangle
  *  delta_dev   NULL, or a folded plane as bs_mabs_delta (closable = 0:
  *              [batch][T_r][2nchan-1][2nchan-1]) or bs_mabs_delta_closable
  *              (closable = 1: [batch][n_c][2nchan-1][2nchan-1]) wrote it
- *  relerr_dev  NULL (with delta_dev NULL), or the same shape as delta_dev:
- *              per bin, the relative error bound beta / |B_A| (NaN where the
- *              estimate is undefined)
+ *              (double2 entries for a general plan)
+ *  relerr_dev  NULL (with delta_dev NULL), or double with the entry count of
+ *              delta_dev: per bin, the relative error bound beta / |B_A|
+ *              (modulus for a general plan; NaN where the estimate is
+ *              undefined)
  * Reads the plan's fields, so call it before the next bs_grid_load.
  * Errors: BS_ERR_ARG (NULL bound_dev, only one of delta_dev / relerr_dev),
- * BS_ERR_STATE (no grid loaded), BS_ERR_CUDA. */
+ * BS_ERR_STATE (no grid loaded), BS_ERR_UNSUPPORTED (per-channel sampling
+ * plans, whose denominators carry their own rounding), BS_ERR_CUDA. */
 bs_status bs_mabs_error_bound(bs_plan plan, double *bound_dev, const double *delta_dev,
                               int closable, double *relerr_dev, void *cuda_stream);
 

@@ -452,17 +452,19 @@ class Plan:
 
     def error_bound(self, delta=None, closable=False, stream=None):
         """bs_mabs_error_bound: float64 CUDA [batch, ntrip] bounds on |B_A error| per ring
-        triple; with ``delta`` (a folded plane from mabs_delta, or from
-        mabs_delta_closable with closable=True) also the per-bin relative bound of the
-        same shape.  Returns (bound, relerr or None)."""
+        triple (the modulus of the complex error in a general plan); with ``delta`` (a
+        folded plane from mabs_delta, or from mabs_delta_closable with closable=True) also
+        the per-bin relative bound, float64 of the same shape.  Returns (bound, relerr or
+        None)."""
         import torch
-        bound = torch.empty((self.batch, self.ntrip), dtype=torch.float64, device="cuda")
         rel = None
         if delta is not None:
             npl = self.n_closable if closable else self.ntrip
-            if delta.dtype != torch.float64 or delta.numel() != self.batch * npl * (2 * self.nchan - 1) ** 2:
-                raise ValueError("delta must be float64 [batch, planes, 2nc-1, 2nc-1]")
-            rel = torch.empty_like(delta)
+            want = torch.complex128 if self.general else torch.float64
+            _require(delta, want, self.batch * npl * (2 * self.nchan - 1) ** 2,
+                     "delta [batch, planes, 2nc-1, 2nc-1]")
+            rel = torch.empty(delta.shape, dtype=torch.float64, device="cuda")
+        bound = torch.empty((self.batch, self.ntrip), dtype=torch.float64, device="cuda")
         self._check(self._L.bs_mabs_error_bound(self._h, _dptr(bound), _dptr(delta),
                                                 int(bool(closable)), _dptr(rel),
                                                 _stream_ptr(stream)))

@@ -35,6 +35,16 @@
 // folded plane.  A factor 1.01 covers second-order terms and the FP32
 // rounding of the norms themselves.  These are worst-case bounds: the
 // measured errors lie well below them.
+//
+// General (non-Hermitian) plans evaluate the real path four times, on the
+// Hermitian inputs X_H + t Y with t = 0, 1, -1, 2, and combine the results as
+// Re S = 2 S(0) - (S(1) + S(-1)) / 2 and Im S = (9 S(1) - S(-1) - 2 S(2) -
+// 6 S(0)) / 6.  Each S(t) is an ordinary real evaluation with its own
+// computed fields, so its error has the bound above (beta_t, from the norms
+// of that evaluation's fields); the combination's weights are exact, so
+//   |d Re S| <= 2 beta_0 + (beta_1 + beta_-1) / 2,
+//   |d Im S| <= (9 beta_1 + beta_-1 + 2 beta_2 + 6 beta_0) / 6,
+// and the bound on the complex error |dS| is the hypot of the two.
 #include <cmath>
 
 #include "plan_internal.h"
@@ -107,7 +117,9 @@ struct BoundLevel {
   const double *norms;  // [batch][nslot][nc][3] of this level
   const int *slot_of;   // [nb]
   const int *kexp;      // [batch][nslot] scale exponents (split FP16), else null
-  int level, nslot, nc, batch, ntrip;
+  int level, nslot, nc, ntrip;
+  int batch;            // realisations of the output (the caller's batch)
+  int general;          // 1: four internal evaluations per realisation (t = 0, 1, -1, 2)
   double c1;            // c_term + c_acc
   double cf;            // eps_fft
   double floor16;       // 2^-25 (2^14 + 2^7) M^2 (split FP16), else 0
@@ -122,14 +134,9 @@ __device__ double ring_max(const BoundLevel &L, int b, int r, int k) {
   return m;
 }
 
-// bound[b][trip] for the ring triples of one level (table: i, j, l, level).
-__global__ void k_trip_bound(BoundLevel L, const int *__restrict__ tab,
-                             const double *__restrict__ tnorm, double *__restrict__ bound) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= L.batch * L.ntrip) return;
-  const int b = t / L.ntrip, trip = t - b * L.ntrip;
-  if (tab[4 * trip + 3] != L.level || !(tnorm[trip] > 0.0)) return;
-  const int r[3] = {tab[4 * trip], tab[4 * trip + 1], tab[4 * trip + 2]};
+// First-order bound on |dS| of one real evaluation (internal realisation b) of
+// the ring triple with rings r.
+__device__ double trip_beta(const BoundLevel &L, int b, const int r[3]) {
   double ninf[3], n2[3], n3[3];
   for (int q = 0; q < 3; ++q) {
     ninf[q] = ring_max(L, b, r[q], 0);
@@ -147,11 +154,34 @@ __global__ void k_trip_bound(BoundLevel L, const int *__restrict__ tab,
     const int ks = k[L.slot_of[r[0]]] + k[L.slot_of[r[1]]] + k[L.slot_of[r[2]]];
     beta += ldexp(L.floor16, -ks);
   }
+  return beta;
+}
+
+// bound[b][trip] for the ring triples of one level (table: i, j, l, level).
+__global__ void k_trip_bound(BoundLevel L, const int *__restrict__ tab,
+                             const double *__restrict__ tnorm, double *__restrict__ bound) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= L.batch * L.ntrip) return;
+  const int b = t / L.ntrip, trip = t - b * L.ntrip;
+  if (tab[4 * trip + 3] != L.level || !(tnorm[trip] > 0.0)) return;
+  const int r[3] = {tab[4 * trip], tab[4 * trip + 1], tab[4 * trip + 2]};
+  double beta;
+  if (!L.general) {
+    beta = trip_beta(L, b, r);
+  } else {  // evaluations t = 0, 1, -1, 2 of realisation b are internal 4b .. 4b + 3
+    const double b0 = trip_beta(L, 4 * b, r), b1 = trip_beta(L, 4 * b + 1, r),
+                 bm = trip_beta(L, 4 * b + 2, r), b2 = trip_beta(L, 4 * b + 3, r);
+    const double re = 2.0 * b0 + 0.5 * (b1 + bm);
+    const double im = (9.0 * b1 + bm + 2.0 * b2 + 6.0 * b0) / 6.0;
+    beta = sqrt(re * re + im * im);
+  }
   bound[(long long)b * L.ntrip + trip] = 1.01 * beta * tnorm[trip];
 }
 
 // relerr[b][pl][d] = bound[b][trip(pl)] / |delta[b][pl][d]|; trip(pl) = pl, or
-// clos[pl] for the closable layout.  NaN where the estimate is undefined.
+// clos[pl] for the closable layout; delta complex (modulus) for general plans.
+// NaN where the estimate is undefined.
+template <bool CPLX>
 __global__ void k_delta_relerr(const double *__restrict__ delta, const double *__restrict__ bound,
                                const int *__restrict__ clos, int nplanes, int ntrip, long long n2,
                                long long total, double *__restrict__ relerr) {
@@ -160,7 +190,8 @@ __global__ void k_delta_relerr(const double *__restrict__ delta, const double *_
     const long long bp = q / n2;
     const int b = (int)(bp / nplanes), pl = (int)(bp - (long long)b * nplanes);
     const int trip = clos ? clos[pl] : pl;
-    relerr[q] = bound[(long long)b * ntrip + trip] / fabs(delta[q]);
+    const double mag = CPLX ? hypot(delta[2 * q], delta[2 * q + 1]) : fabs(delta[q]);
+    relerr[q] = bound[(long long)b * ntrip + trip] / mag;
   }
 }
 
@@ -189,8 +220,8 @@ extern "C" bs_status bs_mabs_error_bound(bs_plan p, double *bound_dev, const dou
     return fail(p, BS_ERR_ARG, "bs_mabs_error_bound: give both delta_dev and relerr_dev, or neither");
   if (closable != 0 && closable != 1)
     return fail(p, BS_ERR_ARG, "bs_mabs_error_bound: closable must be 0 or 1");
-  if (p->general || p->chans)
-    return fail(p, BS_ERR_UNSUPPORTED, "bs_mabs_error_bound: general or per-channel sampling plans");
+  if (p->chans)
+    return fail(p, BS_ERR_UNSUPPORTED, "bs_mabs_error_bound: per-channel sampling plans");
   if (!p->loaded || !p->counts_ready)
     return fail(p, BS_ERR_STATE, "bs_mabs_error_bound before bs_grid_load");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -209,8 +240,10 @@ extern "C" bs_status bs_mabs_error_bound(bs_plan p, double *bound_dev, const dou
   }
   int *dtab = p->at<int>(p->L.errtab);
   EB_CUDA(cudaMemcpyAsync(dtab, tab.data(), tab.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  // the caller's realisations (a general plan holds four internal ones per realisation)
+  const int out_batch = p->general ? p->ubatch : p->batch;
   // NaN (all bits set) for every ring triple without a closed triangle
-  EB_CUDA(cudaMemsetAsync(bound_dev, 0xFF, (size_t)p->batch * p->ntrip * sizeof(double), s));
+  EB_CUDA(cudaMemsetAsync(bound_dev, 0xFF, (size_t)out_batch * p->ntrip * sizeof(double), s));
   double *norms = p->at<double>(p->L.errn);
   for (int li = 0; li < (int)p->levels.size(); ++li) {
     const Level &lv = p->levels[li];
@@ -226,7 +259,8 @@ extern "C" bs_status bs_mabs_error_bound(bs_plan p, double *bound_dev, const dou
     B.level = li;
     B.nslot = lv.nslot;
     B.nc = p->nc;
-    B.batch = p->batch;
+    B.batch = out_batch;
+    B.general = p->general ? 1 : 0;
     B.ntrip = p->ntrip;
     const double c_acc = prec == BS_PREC_FP32
                              ? (1024.0 + std::ceil((double)m2 / 1024.0) + 1.0) * kU
@@ -235,7 +269,7 @@ extern "C" bs_status bs_mabs_error_bound(bs_plan p, double *bound_dev, const dou
     B.cf = (2.0 * (ceil_log2(lv.M) + 2) * 8.0 + 2.0) * kU;
     B.floor16 = prec == BS_PREC_SPLIT_FP16 ? std::ldexp(1.0, -25) * (16384.0 + 128.0) * (double)m2
                                            : 0.0;
-    const int nt = p->batch * p->ntrip;
+    const int nt = out_batch * p->ntrip;
     k_trip_bound<<<(nt + 255) / 256, 256, 0, s>>>(B, dtab, p->at<double>(p->L.tnorm), bound_dev);
     EB_CUDA(cudaGetLastError());
     norms += (size_t)nfield * 3;
@@ -243,12 +277,16 @@ extern "C" bs_status bs_mabs_error_bound(bs_plan p, double *bound_dev, const dou
   if (delta_dev) {
     const int npl = closable ? (int)p->clos.size() : p->ntrip;
     const long long n2 = (long long)(2 * p->nc - 1) * (2 * p->nc - 1);
-    const long long total = (long long)p->batch * npl * n2;
+    const long long total = (long long)out_batch * npl * n2;
     if (total > 0) {
       const int grid = (int)std::min<long long>((total + 255) / 256, 152LL * 32);
-      k_delta_relerr<<<grid, 256, 0, s>>>(delta_dev, bound_dev,
-                                          closable ? p->at<int>(p->L.clos) : nullptr, npl,
-                                          p->ntrip, n2, total, relerr_dev);
+      const int *clos = closable ? p->at<int>(p->L.clos) : nullptr;
+      if (p->general)
+        k_delta_relerr<true><<<grid, 256, 0, s>>>(delta_dev, bound_dev, clos, npl, p->ntrip, n2,
+                                                  total, relerr_dev);
+      else
+        k_delta_relerr<false><<<grid, 256, 0, s>>>(delta_dev, bound_dev, clos, npl, p->ntrip, n2,
+                                                   total, relerr_dev);
       EB_CUDA(cudaGetLastError());
     }
   }

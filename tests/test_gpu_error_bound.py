@@ -33,22 +33,24 @@ def _torch():
     return torch
 
 
-def _gpu(vis, edges, precision, multires, flags=None, ngrid=None):
+def _gpu(vis, edges, precision, multires, flags=None, ngrid=None, general=False):
     torch = _torch()
     import paper_2506_10526_gb300 as bs
     if vis.ndim == 3:
         vis = vis[None]
     batch, nc, nt, _ = vis.shape
-    plan = bs.Plan(nt, nc, edges, precision=precision, multires=multires, batch=batch)
+    plan = bs.Plan(nt, nc, edges, precision=precision, multires=multires, batch=batch,
+                   general=general)
     gd = None if ngrid is None else torch.from_numpy(ngrid.astype(np.float32)).cuda()
     plan.grid_load(torch.from_numpy(np.ascontiguousarray(vis.astype(np.complex64))).cuda(),
                    ngrid=gd, chan_flags=flags)
-    full = torch.empty((batch, plan.ntrip, nc, nc, nc), dtype=torch.float64, device="cuda")
+    ct = torch.complex128 if general else torch.float64
+    full = torch.empty((batch, plan.ntrip, nc, nc, nc), dtype=ct, device="cuda")
     plan.mabs(out_full=full, accumulate=True)
     n2 = 2 * nc - 1
-    dd = torch.empty((batch, plan.ntrip, n2, n2), dtype=torch.float64, device="cuda")
+    dd = torch.empty((batch, plan.ntrip, n2, n2), dtype=ct, device="cuda")
     plan.mabs_delta(dd)
-    dc = torch.empty((batch, plan.n_closable, n2, n2), dtype=torch.float64, device="cuda")
+    dc = torch.empty((batch, plan.n_closable, n2, n2), dtype=ct, device="cuda")
     plan.mabs_delta_closable(dc)
     bound, rel = plan.error_bound(dd)
     bound2, relc = plan.error_bound(dc, closable=True)
@@ -138,3 +140,51 @@ def test_bound_covers_the_error_ragged_occupancy_batch(precision, multires):
         babs = oracle.mabs_full(np.abs(v[b]).astype(np.complex128), edges, chan_flags=flags,
                                 ngrid=ngrid)["B"].real
         _check(out, b, ref, babs, precision, f"ragged p{precision} realisation {b}")
+
+
+@pytest.mark.parametrize("precision,multires", [(0, False), (0, True), (1, True), (2, True)])
+def test_bound_covers_the_error_general_input(precision, multires):
+    """General (non-Hermitian) input: visibilities with no symmetry on an
+    asymmetric sampling grid, one flagged channel, two realisations of
+    different amplitude.  The estimates are complex, combined from four real
+    evaluations; the bound on the modulus of the complex error must cover
+    every entry of the full cube and of the folded plane, and relerr is the
+    bound over |B| in both layouts."""
+    nt, nc = 32, 6
+    edges = synth.edges_log(5, 1.5, 15.0)
+    r = synth.rng(601)
+    v = r.standard_normal((2, nc, nt, nt)) + 1j * r.standard_normal((2, nc, nt, nt))
+    v[1] *= 30.0
+    v = v.astype(np.complex64)
+    ngrid = r.integers(0, 4, size=(nt, nt)).astype(np.float32)  # no symmetry
+    flags = np.zeros(nc, np.uint8)
+    flags[2] = 1
+    out = _gpu(v, edges, precision, multires, flags=flags, ngrid=ngrid, general=True)
+    for b in range(2):
+        ref = oracle.mabs_full(v[b].astype(np.complex128), edges, ngrid=ngrid, chan_flags=flags)
+        babs = oracle.mabs_full(np.abs(v[b]).astype(np.complex128), edges, ngrid=ngrid,
+                                chan_flags=flags)["B"].real
+        B = ref["B"]
+        assert np.nanmax(np.abs(B.imag)) > 0.1 * np.nanmax(np.abs(B.real))  # really complex
+        beta = out["bound"][b]
+        np.testing.assert_array_equal(np.isnan(beta), ref["T"] == 0)
+        np.testing.assert_array_equal(out["bound2"][b], beta)
+        ok = ~np.isnan(B)
+        err = np.abs(out["full"][b] - B)
+        bb = np.broadcast_to(beta[:, None, None, None], B.shape)
+        ratio = err[ok] / bb[ok]
+        assert np.all(err[ok] <= bb[ok] + 1e-13 * babs[ok]), ratio.max()
+        bbar, _ = oracle.collapse_fold(B)
+        bbar_abs, _ = oracle.collapse_fold(babs)
+        okd = ~np.isnan(bbar)
+        errd = np.abs(out["delta"][b] - bbar)
+        betad = np.broadcast_to(beta[:, None, None], bbar.shape)
+        assert np.all(errd[okd] <= betad[okd] + 1e-13 * bbar_abs[okd])
+        with np.errstate(divide="ignore", invalid="ignore"):
+            want_rel = betad / np.abs(out["delta"][b])
+        np.testing.assert_allclose(out["rel"][b][okd], want_rel[okd], rtol=1e-15)
+        assert np.all(np.isnan(out["rel"][b][~okd]))
+        clos = np.flatnonzero(ref["T"] > 0)
+        np.testing.assert_array_equal(out["relc"][b], out["rel"][b][clos])
+        print(f"general p{precision} mr{int(multires)} realisation {b}: error/bound max "
+              f"{ratio.max():.2e} median {np.median(ratio):.2e}")
