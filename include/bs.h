@@ -409,10 +409,15 @@ bs_status bs_plan_ring_umean(bs_plan plan, double *umean_host);
  * Values, sums and the model (from FP64 squared lengths) are FP64.
  * kperp_host must lie in [1e-8, 1e8] and |kpar_host| <= 1e8 (FP32 range of
  * the squared comparisons).
+ * General plans: b3d_dev holds complex (double2) values and sum_dev complex
+ * sums in the same layout; the binning is linear, so the real and imaginary
+ * parts are binned separately (through plan scratch of about the size of
+ * b3d_dev, allocated on first use and kept).  Both pointers must then be
+ * 16-byte aligned.  The model (b3d_dev NULL) stays real.
  * Errors: BS_ERR_ARG (NULL, counts out of range, edges not ascending, k out
- * of range),
+ * of range, misaligned complex pointers),
  * BS_ERR_STATE (no counts yet), BS_ERR_UNSUPPORTED (bins x realisations
- * beyond one CTA's shared memory). */
+ * beyond one CTA's shared memory), BS_ERR_OOM (scratch of a general plan). */
 bs_status bs_bs_monopole(bs_plan plan, const double *b3d_dev, const double *kperp_host,
                          const double *kpar_host, const double *k1_edges_host, int n_k1,
                          int n_mu, int n_t, double f_ng, double p_amp, double p_index,
@@ -437,7 +442,8 @@ bs_status bs_bs_monopole(bs_plan plan, const double *b3d_dev, const double *kper
  *             (2l+1) P_l(mu_1) B over each bin's samples (overwritten)
  *  count_dev  int64 [n_k1][n_mu][n_t]: samples per bin (overwritten);
  *             B_l^0 = sum / count
- * Other arguments as bs_bs_monopole (b3d_dev required).
+ * Other arguments as bs_bs_monopole (b3d_dev required; complex values and
+ * sums for a general plan).
  * Errors: as bs_bs_monopole; BS_ERR_ARG for lmax out of range. */
 bs_status bs_bs_multipoles(bs_plan plan, const double *b3d_dev, const double *kperp_host,
                            const double *kpar_host, const double *k1_edges_host, int n_k1,
@@ -454,7 +460,10 @@ bs_status bs_bs_multipoles(bs_plan plan, const double *b3d_dev, const double *kp
  *  sum_dev     double [batch][n_c][n][n]: sum over the (a, b) in bins (q, r)
  *  count_dev   int64 [n][n]: number of those (a, b), the same for every plane
  * Both outputs are overwritten; the binned value is sum / count.
- * Errors: BS_ERR_ARG, BS_ERR_STATE (no counts yet). */
+ * General plans: complex (double2, 16-byte aligned) b3d_dev and sum_dev, as
+ * for bs_bs_monopole.
+ * Errors: BS_ERR_ARG, BS_ERR_STATE (no counts yet), BS_ERR_OOM (scratch of a
+ * general plan). */
 bs_status bs_bs_cylindrical(bs_plan plan, const double *b3d_dev, const double *kpar_host,
                             const double *edges_host, int n, double *sum_dev,
                             int64_t *count_dev, void *cuda_stream);

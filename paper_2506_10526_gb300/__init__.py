@@ -350,8 +350,8 @@ class Plan:
     def bs_monopole(self, b3d, kperp, kpar, k1_edges, n_mu=5, n_t=5, model=None, stream=None):
         """bs_bs_monopole: binned 3D-bispectrum monopole.  b3d: float64 CUDA tensor as
         bs3d_closable writes it, or None with model = (f_ng, p_amp, p_index) for the binned
-        Eq. (bsana).  Returns (sums [batch, n_k1, n_mu, n_t] float64 CUDA,
-        counts [n_k1, n_mu, n_t] int64 CUDA)."""
+        Eq. (bsana).  Returns (sums [batch, n_k1, n_mu, n_t] float64 CUDA (complex128
+        for a general plan's complex b3d), counts [n_k1, n_mu, n_t] int64 CUDA)."""
         import numpy as np
         import torch
         kp = np.ascontiguousarray(np.asarray(kperp, np.float64))
@@ -361,10 +361,12 @@ class Plan:
             raise ValueError("kperp needs nbins entries and kpar nchan entries")
         n_k1 = ed.size - 1
         batch = 1 if b3d is None else self.batch
-        if b3d is not None and (b3d.dtype != torch.float64 or
-                                b3d.numel() != batch * self.n_closable * self.nchan ** 2):
-            raise ValueError("b3d must be float64 [batch, n_closable, nchan, nchan]")
-        sums = torch.empty((batch, n_k1, n_mu, n_t), dtype=torch.float64, device="cuda")
+        vt = torch.complex128 if self.general else torch.float64  # a general plan's values
+        if b3d is not None:
+            _require(b3d, vt, batch * self.n_closable * self.nchan ** 2,
+                     "b3d [batch, n_closable, nchan, nchan]")
+        sdt = torch.float64 if b3d is None else vt
+        sums = torch.empty((batch, n_k1, n_mu, n_t), dtype=sdt, device="cuda")
         cnt = torch.empty((n_k1, n_mu, n_t), dtype=torch.int64, device="cuda")
         f, a, pi = model if model is not None else (0.0, 0.0, 0.0)
         self._check(self._L.bs_bs_monopole(
@@ -376,8 +378,8 @@ class Plan:
 
     def bs_multipoles(self, b3d, kperp, kpar, k1_edges, n_mu=5, n_t=5, lmax=4, stream=None):
         """bs_bs_multipoles: m = 0 multipoles binned like bs_monopole.  Returns
-        (sums [batch, lmax + 1, n_k1, n_mu, n_t] float64 CUDA, counts [n_k1, n_mu, n_t]
-        int64 CUDA); B_l^0 = sums / counts."""
+        (sums [batch, lmax + 1, n_k1, n_mu, n_t] float64 CUDA (complex128 for a general
+        plan), counts [n_k1, n_mu, n_t] int64 CUDA); B_l^0 = sums / counts."""
         import numpy as np
         import torch
         kp = np.ascontiguousarray(np.asarray(kperp, np.float64))
@@ -385,11 +387,11 @@ class Plan:
         ed = np.ascontiguousarray(np.asarray(k1_edges, np.float64))
         if kp.size != self.nbins or kz.size != self.nchan:
             raise ValueError("kperp needs nbins entries and kpar nchan entries")
-        if b3d.dtype != torch.float64 or b3d.numel() != self.batch * self.n_closable * self.nchan ** 2:
-            raise ValueError("b3d must be float64 [batch, n_closable, nchan, nchan]")
+        vt = torch.complex128 if self.general else torch.float64  # a general plan's values
+        _require(b3d, vt, self.batch * self.n_closable * self.nchan ** 2,
+                 "b3d [batch, n_closable, nchan, nchan]")
         n_k1 = ed.size - 1
-        sums = torch.empty((self.batch, lmax + 1, n_k1, n_mu, n_t), dtype=torch.float64,
-                           device="cuda")
+        sums = torch.empty((self.batch, lmax + 1, n_k1, n_mu, n_t), dtype=vt, device="cuda")
         cnt = torch.empty((n_k1, n_mu, n_t), dtype=torch.int64, device="cuda")
         P = ctypes.c_void_p
         self._check(self._L.bs_bs_multipoles(
@@ -400,8 +402,8 @@ class Plan:
 
     def bs_cylindrical(self, b3d, kpar, edges, stream=None):
         """bs_bs_cylindrical: the closable 3D bispectrum binned on the (k_par1, k_par2)
-        grid of the given edges.  Returns (sums [batch, n_closable, n, n] float64 CUDA,
-        counts [n, n] int64 CUDA)."""
+        grid of the given edges.  Returns (sums [batch, n_closable, n, n] float64 CUDA
+        (complex128 for a general plan), counts [n, n] int64 CUDA)."""
         import numpy as np
         import torch
         kz = np.ascontiguousarray(np.asarray(kpar, np.float64))
@@ -409,9 +411,10 @@ class Plan:
         n = ed.size - 1
         if kz.size != self.nchan:
             raise ValueError("kpar needs nchan entries")
-        if b3d.dtype != torch.float64 or b3d.numel() != self.batch * self.n_closable * self.nchan ** 2:
-            raise ValueError("b3d must be float64 [batch, n_closable, nchan, nchan]")
-        sums = torch.empty((self.batch, self.n_closable, n, n), dtype=torch.float64, device="cuda")
+        vt = torch.complex128 if self.general else torch.float64  # a general plan's values
+        _require(b3d, vt, self.batch * self.n_closable * self.nchan ** 2,
+                 "b3d [batch, n_closable, nchan, nchan]")
+        sums = torch.empty((self.batch, self.n_closable, n, n), dtype=vt, device="cuda")
         cnt = torch.empty((n, n), dtype=torch.int64, device="cuda")
         self._check(self._L.bs_bs_cylindrical(
             self._h, _dptr(b3d), kz.ctypes.data_as(ctypes.c_void_p),

@@ -459,6 +459,37 @@ __global__ void __launch_bounds__(kCylThreads) k_bs_cylindrical(
     if (acc[q] != 0.0) atomicAdd(out + q, acc[q]);
 }
 
+// General plans: the binnings are linear in the 3D bispectrum, so its complex
+// values are binned as two real realisations per realisation b: 2b the real
+// part and 2b + 1 the imaginary part of in[b] ([ub][per] double2).
+__global__ void k_split_complex(const double2 *__restrict__ in, long long per, int ub,
+                                double *__restrict__ out) {
+  const long long total = (long long)ub * per;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+       q += (long long)gridDim.x * blockDim.x) {
+    const long long b = q / per, k = q - b * per;
+    const double2 v = in[q];
+    out[2 * b * per + k] = v.x;
+    out[(2 * b + 1) * per + k] = v.y;
+  }
+}
+
+// ... and the real sums of the two parts, [2 ub][rest], back as complex sums
+// [ub][rest].
+__global__ void k_join_complex(const double *__restrict__ in, long long rest, int ub,
+                               double2 *__restrict__ out) {
+  const long long total = (long long)ub * rest;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+       q += (long long)gridDim.x * blockDim.x) {
+    const long long b = q / rest, k = q - b * rest;
+    out[q] = make_double2(in[2 * b * rest + k], in[(2 * b + 1) * rest + k]);
+  }
+}
+
+int grid_of(long long total) {
+  return (int)std::max<long long>(1, std::min<long long>((total + 255) / 256, 152LL * 32));
+}
+
 }  // namespace
 
 // Bytes of shared memory the summing kernel needs for nbatch realisations.
@@ -473,6 +504,42 @@ static size_t mono_smem(int nbin, int nbatch) {
     cudaError_t e__ = (call);                                    \
     if (e__ != cudaSuccess) return cuda_fail(p, e__, #call);     \
   } while (0)
+
+// A general plan's complex closable 3D bispectrum (per = planes x nc^2 values
+// per realisation) split into real planes in the plan's scratch, followed by
+// zeroed room for the real sums (rest per part); *planes and *sums point there.
+static bs_status split_general(bs_plan p, const double *b3d, long long per, long long rest,
+                               const double **planes, double **sums, cudaStream_t s) {
+  using namespace bsi;
+  const long long ub = p->ubatch;
+  bs_status st = general_scratch(p, &p->gbin, &p->gbin_cap, (size_t)(2 * ub * (per + rest)));
+  if (st != BS_OK) return st;
+  double *pl = p->gbin, *sm = p->gbin + 2 * ub * per;
+  if (ub * per > 0) {
+    k_split_complex<<<grid_of(ub * per), 256, 0, s>>>(reinterpret_cast<const double2 *>(b3d), per,
+                                                     (int)ub, pl);
+    MONO_CUDA(cudaGetLastError());
+  }
+  MONO_CUDA(cudaMemsetAsync(sm, 0, (size_t)(2 * ub * rest) * sizeof(double), s));
+  *planes = pl;
+  *sums = sm;
+  return BS_OK;
+}
+
+// The real sums of split_general's parts into the caller's complex sums.
+static bs_status join_general(bs_plan p, const double *sums, long long rest, double *out,
+                              cudaStream_t s) {
+  using namespace bsi;
+  const long long ub = p->ubatch;
+  if (ub * rest == 0) return BS_OK;
+  k_join_complex<<<grid_of(ub * rest), 256, 0, s>>>(sums, rest, (int)ub,
+                                                   reinterpret_cast<double2 *>(out));
+  MONO_CUDA(cudaGetLastError());
+  return BS_OK;
+}
+
+// Complex values are read and written as double2: 16-byte aligned pointers.
+static bool aligned16(const void *ptr) { return (reinterpret_cast<uintptr_t>(ptr) & 15) == 0; }
 
 // Geometry of the (k1, mu, t) binning shared by the monopole and the
 // multipoles: FP64 and FP32 k tables and the squared thresholds uploaded to
@@ -582,7 +649,10 @@ bs_status bs_bs_monopole(bs_plan p, const double *b3d, const double *kperp_host,
   for (int q = 0; q < n_k1; ++q)
     if (!(k1_edges_host[q + 1] > k1_edges_host[q]) || !std::isfinite(k1_edges_host[q + 1]))
       return fail(p, BS_ERR_ARG, "bs_bs_monopole: k1 edges must be finite and ascending");
-  if (p->general) return fail(p, BS_ERR_UNSUPPORTED, "bs_bs_monopole: general plans");
+  // a general plan's complex values: real and imaginary parts binned as two realisations
+  const bool cplx = p->general && b3d;
+  if (cplx && !(aligned16(b3d) && aligned16(sum_dev)))
+    return fail(p, BS_ERR_ARG, "bs_bs_monopole: complex b3d and sums must be 16-byte aligned");
   if (!p->counts_ready) return fail(p, BS_ERR_STATE, "bs_bs_monopole before the ring-triple counts");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   bs_status st = prepare(p, s);
@@ -594,7 +664,7 @@ bs_status bs_bs_monopole(bs_plan p, const double *b3d, const double *kperp_host,
     if (!(std::fabs(kpar_host[c]) <= 1e8))
       return fail(p, BS_ERR_ARG, "bs_bs_monopole: |k_par| must not exceed 1e8");
   const int nbin = n_k1 * n_mu * n_t;
-  const int batch = b3d ? p->ubatch : 1;
+  const int batch = b3d ? (cplx ? 2 * p->ubatch : p->ubatch) : 1;
   const int per = std::min(batch, kMaxBatch);
   if (mono_smem(nbin, per) > (size_t)200 * 1024)
     return fail(p, BS_ERR_UNSUPPORTED, "bs_bs_monopole: too many bins for one CTA's histogram");
@@ -615,6 +685,10 @@ bs_status bs_bs_monopole(bs_plan p, const double *b3d, const double *kperp_host,
   a.p_amp = p_amp;
   a.p_half = 0.5 * p_index;
   a.sums = sum_dev;
+  if (cplx) {
+    st = split_general(p, b3d, a.bstride, nbin, &a.b3d, &a.sums, s);
+    if (st != BS_OK) return st;
+  }
   a.cnt = reinterpret_cast<unsigned long long *>(count_dev);
   const int n = p->nc * p->nc;
   const int gx = (n + a.chunk - 1) / a.chunk;
@@ -634,6 +708,7 @@ bs_status bs_bs_monopole(bs_plan p, const double *b3d, const double *kperp_host,
       k_mono_sum<kMaxBatch><<<grid, kThreads, sm, s>>>(a, p->mono_bins);
     MONO_CUDA(cudaGetLastError());
   }
+  if (cplx) return join_general(p, a.sums, nbin, sum_dev, s);
   return BS_OK;
 }
 
@@ -652,7 +727,9 @@ bs_status bs_bs_multipoles(bs_plan p, const double *b3d, const double *kperp_hos
   for (int q = 0; q < n_k1; ++q)
     if (!(k1_edges_host[q + 1] > k1_edges_host[q]) || !std::isfinite(k1_edges_host[q + 1]))
       return fail(p, BS_ERR_ARG, "bs_bs_multipoles: k1 edges must be finite and ascending");
-  if (p->general) return fail(p, BS_ERR_UNSUPPORTED, "bs_bs_multipoles: general plans");
+  const bool cplx = p->general;  // complex values: real and imaginary parts as two realisations
+  if (cplx && !(aligned16(b3d) && aligned16(sum_dev)))
+    return fail(p, BS_ERR_ARG, "bs_bs_multipoles: complex b3d and sums must be 16-byte aligned");
   if (!p->counts_ready) return fail(p, BS_ERR_STATE, "bs_bs_multipoles before the ring-triple counts");
   for (int m = 0; m < p->nb; ++m)
     if (!(kperp_host[m] >= 1e-8 && kperp_host[m] <= 1e8))
@@ -664,7 +741,7 @@ bs_status bs_bs_multipoles(bs_plan p, const double *b3d, const double *kperp_hos
   bs_status st = prepare(p, s);
   if (st != BS_OK) return st;
   const int nbin = n_k1 * n_mu * n_t;
-  const int batch = p->ubatch;
+  const int batch = cplx ? 2 * p->ubatch : p->ubatch;
   const int per = std::min(batch, 4);
   if ((size_t)per * (lmax + 1) * nbin * 8 + (size_t)nbin * 4 > (size_t)200 * 1024)
     return fail(p, BS_ERR_UNSUPPORTED, "bs_bs_multipoles: too many bins for one CTA's histogram");
@@ -677,6 +754,10 @@ bs_status bs_bs_multipoles(bs_plan p, const double *b3d, const double *kperp_hos
   st = mono_geometry(p, kperp_host, kpar_host, k1_edges_host, n_k1, n_mu, n_t, s, a);
   if (st != BS_OK) return st;
   a.sums = sum_dev;
+  if (cplx) {
+    st = split_general(p, b3d, a.bstride, (long long)(lmax + 1) * nbin, &a.b3d, &a.sums, s);
+    if (st != BS_OK) return st;
+  }
   a.cnt = reinterpret_cast<unsigned long long *>(count_dev);
   const int n = p->nc * p->nc;
   const int gx = (n + a.chunk - 1) / a.chunk;
@@ -709,6 +790,7 @@ bs_status bs_bs_multipoles(bs_plan p, const double *b3d, const double *kperp_hos
 #undef MULTIPOLE_LAUNCH
     MONO_CUDA(cudaGetLastError());
   }
+  if (cplx) return join_general(p, a.sums, (long long)(lmax + 1) * nbin, sum_dev, s);
   return BS_OK;
 }
 
@@ -726,7 +808,9 @@ bs_status bs_bs_cylindrical(bs_plan p, const double *b3d, const double *kpar_hos
   for (int c = 1; c < p->nc; ++c)
     if (!(kpar_host[c] > kpar_host[c - 1]))
       return fail(p, BS_ERR_ARG, "bs_bs_cylindrical: k_par must grow with the delay index");
-  if (p->general) return fail(p, BS_ERR_UNSUPPORTED, "bs_bs_cylindrical: general plans");
+  const bool cplx = p->general;  // complex values: real and imaginary parts as two realisations
+  if (cplx && !(aligned16(b3d) && aligned16(sum_dev)))
+    return fail(p, BS_ERR_ARG, "bs_bs_cylindrical: complex b3d and sums must be 16-byte aligned");
   if (!p->counts_ready) return fail(p, BS_ERR_STATE, "bs_bs_cylindrical before the ring-triple counts");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   bs_status st = prepare(p, s);
@@ -756,21 +840,29 @@ bs_status bs_bs_cylindrical(bs_plan p, const double *b3d, const double *kpar_hos
   MONO_CUDA(cudaMemcpyAsync(dtab, tab.data(), tab.size() * sizeof(int), cudaMemcpyHostToDevice, s));
   const size_t sm = ((size_t)n * n + nc) * sizeof(double);
   MONO_CUDA(smem_optin_once<k_bs_cylindrical<16>>());
-  MONO_CUDA(cudaMemsetAsync(sum_dev, 0, (size_t)p->ubatch * npl * n * n * sizeof(double), s));
-  const dim3 grid(npl, p->ubatch, 2);  // two row ranges per plane
+  const int batch = cplx ? 2 * p->ubatch : p->ubatch;
+  const long long bst = (long long)npl * nc * nc, rest = (long long)npl * n * n;
+  double *sums = sum_dev;
+  if (cplx) {
+    st = split_general(p, b3d, bst, rest, &b3d, &sums, s);
+    if (st != BS_OK) return st;
+  } else {
+    MONO_CUDA(cudaMemsetAsync(sum_dev, 0, (size_t)batch * rest * sizeof(double), s));
+  }
+  const dim3 grid(npl, batch, 2);  // two row ranges per plane
   const int2 *seg = reinterpret_cast<const int2 *>(dtab + nc);
-  const long long bst = (long long)npl * nc * nc;
   if (nc <= kCylThreads)
-    k_bs_cylindrical<1><<<grid, kCylThreads, sm, s>>>(b3d, bst, nc, n, dtab, seg, sum_dev);
+    k_bs_cylindrical<1><<<grid, kCylThreads, sm, s>>>(b3d, bst, nc, n, dtab, seg, sums);
   else if (nc <= 2 * kCylThreads)
-    k_bs_cylindrical<2><<<grid, kCylThreads, sm, s>>>(b3d, bst, nc, n, dtab, seg, sum_dev);
+    k_bs_cylindrical<2><<<grid, kCylThreads, sm, s>>>(b3d, bst, nc, n, dtab, seg, sums);
   else if (nc <= 3 * kCylThreads)
-    k_bs_cylindrical<3><<<grid, kCylThreads, sm, s>>>(b3d, bst, nc, n, dtab, seg, sum_dev);
+    k_bs_cylindrical<3><<<grid, kCylThreads, sm, s>>>(b3d, bst, nc, n, dtab, seg, sums);
   else if (nc <= 8 * kCylThreads)
-    k_bs_cylindrical<8><<<grid, kCylThreads, sm, s>>>(b3d, bst, nc, n, dtab, seg, sum_dev);
+    k_bs_cylindrical<8><<<grid, kCylThreads, sm, s>>>(b3d, bst, nc, n, dtab, seg, sums);
   else
-    k_bs_cylindrical<16><<<grid, kCylThreads, sm, s>>>(b3d, bst, nc, n, dtab, seg, sum_dev);
+    k_bs_cylindrical<16><<<grid, kCylThreads, sm, s>>>(b3d, bst, nc, n, dtab, seg, sums);
   MONO_CUDA(cudaGetLastError());
+  if (cplx) return join_general(p, sums, rest, sum_dev, s);
   return BS_OK;
 }
 

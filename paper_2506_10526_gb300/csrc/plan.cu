@@ -686,6 +686,27 @@ bs_status mabs_tc(bs_plan p, const int *blk, double *out_full, int accumulate, c
   return BS_OK;
 }
 
+// Scratch of a general plan for the four real components of an output (grown on
+// demand with cudaMalloc, freed with the plan).
+bs_status general_scratch(bs_plan p, double **buf, size_t *cap, size_t n) {
+  if (*buf && *cap >= n) return BS_OK;
+  if (inject_fail("scratch_alloc"))
+    return fail(p, BS_ERR_OOM, "injected failure: scratch allocation (BS_INJECT_FAIL)");
+  if (*buf) cudaFree(*buf);
+  *buf = nullptr;
+  *cap = 0;
+  void *m = nullptr;
+  const cudaError_t e = cudaMalloc(&m, std::max<size_t>(1, n) * sizeof(double));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(p, BS_ERR_OOM, "scratch of " + std::to_string(n * sizeof(double)) +
+                                   " bytes for the general-input components failed");
+  }
+  *buf = static_cast<double *>(m);
+  *cap = n;
+  return BS_OK;
+}
+
 }  // namespace bsi
 
 extern "C" {
@@ -960,7 +981,7 @@ bs_status bs_plan_destroy(bs_plan p) {
     cudaSetDevice(p->device);
     cudaFree(p->mono_bins);
   }
-  for (double *g : {p->gfull, p->gdelta, p->g3d})
+  for (double *g : {p->gfull, p->gdelta, p->g3d, p->gbin})
     if (g) {
       cudaSetDevice(p->device);
       cudaFree(g);
@@ -1081,27 +1102,6 @@ bs_status bs_counts(bs_plan p, int64_t *tri, int64_t *nnu_host) {
         nnu_host[(size_t)i1 * n2 + i2] = c;
       }
   }
-  return BS_OK;
-}
-
-// Scratch of a general plan for the four real components of an output (grown on
-// demand with cudaMalloc, freed with the plan).
-static bs_status general_scratch(bs_plan p, double **buf, size_t *cap, size_t n) {
-  if (*buf && *cap >= n) return BS_OK;
-  if (inject_fail("scratch_alloc"))
-    return fail(p, BS_ERR_OOM, "injected failure: scratch allocation (BS_INJECT_FAIL)");
-  if (*buf) cudaFree(*buf);
-  *buf = nullptr;
-  *cap = 0;
-  void *m = nullptr;
-  const cudaError_t e = cudaMalloc(&m, std::max<size_t>(1, n) * sizeof(double));
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return fail(p, BS_ERR_OOM, "scratch of " + std::to_string(n * sizeof(double)) +
-                                   " bytes for the general-input components failed");
-  }
-  *buf = static_cast<double *>(m);
-  *cap = n;
   return BS_OK;
 }
 

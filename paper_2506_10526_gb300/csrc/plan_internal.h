@@ -85,6 +85,10 @@ struct bs_plan_s {
   int ubatch = 1;
   double *gfull = nullptr, *gdelta = nullptr, *g3d = nullptr;
   size_t gfull_cap = 0, gdelta_cap = 0, g3d_cap = 0;
+  // binnings of a general plan's complex 3D bispectrum: its real and imaginary
+  // planes, then their real sums (device, on demand)
+  double *gbin = nullptr;
+  size_t gbin_cap = 0;
   std::vector<int> cyl_tab;       // row bins and column ranges of the last cylindrical call
   std::vector<long long> cyl_cnt; // its per-bin counts
   std::vector<int> err_tab;       // [ntrip][4] rings (i, j, l) and level, for the error bound
@@ -149,6 +153,9 @@ bs_status sym_fill(bs_plan p, cudaStream_t s);
 void add_block_sampling(int nc, const std::vector<uint8_t> &valid, const int *blk,
                         long long *plane);
 bs_status upload_nnu(bs_plan p, cudaStream_t s);
+// Device scratch of n doubles in *buf (grown with cudaMalloc when *cap < n,
+// freed with the plan); BS_ERR_OOM when it cannot be had.
+bs_status general_scratch(bs_plan p, double **buf, size_t *cap, size_t n);
 // Host-to-device uploads of per-call work lists through the plan's pinned
 // staging buffer (asynchronous; the buffer is reused once the previous
 // uploads from it have completed).  Falls back to ordinary copies when

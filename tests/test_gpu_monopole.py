@@ -289,3 +289,53 @@ def test_multipoles_argument_errors():
     with pytest.raises(bs.BsError):
         plan.bs_multipoles(b3, kperp, kpar, [1.0, 0.1], lmax=2)
     plan.close()
+
+
+def test_binnings_of_a_general_plan():
+    """General (non-Hermitian) input, two realisations: the complex closable
+    3D bispectrum binned by the monopole, the m = 0 multipoles and the
+    (k_par1, k_par2) grid.  The binnings are linear, so the real and the
+    imaginary part of every complex sum must pass the oracle checks that real
+    values pass, with the same counts."""
+    torch = _torch()
+    import paper_2506_10526_gb300 as bs
+    nt, nc, r, rp, dnu = 48, 24, 900.0, 1.2, 0.16
+    edges = synth.edges_log(6, 1.5, 23.0)
+    g = synth.rng(611)
+    v = (g.standard_normal((2, nc, nt, nt)) + 1j * g.standard_normal((2, nc, nt, nt)))
+    plan = bs.Plan(nt, nc, edges, precision=1, batch=2, r=r, rprime=rp, dnu_c=dnu,
+                   multires=True, general=True)
+    plan.grid_load(torch.from_numpy(v.astype(np.complex64)).cuda())
+    plan.mabs(accumulate=True)
+    tri, _ = plan.counts()
+    b3 = torch.empty((2, plan.n_closable, nc, nc), dtype=torch.complex128, device="cuda")
+    plan.bs3d_closable(b3)
+    kperp = 2 * np.pi * plan.ring_umean() / r
+    kpar = mo.kpar_axis(nc, rp, dnu)
+    k1e = np.geomspace(0.5 * kperp.min(), 1.2 * np.sqrt(kperp.max() ** 2 + kpar.max() ** 2), 13)
+    ke = np.linspace(-0.8 * kpar.max(), 0.8 * kpar.max(), 11)
+    sums, cnt = plan.bs_monopole(b3, kperp, kpar, k1e, 5, 5)
+    msums, mcnt = plan.bs_multipoles(b3, kperp, kpar, k1e, 5, 5, lmax=2)
+    csums, ccnt = plan.bs_cylindrical(b3, kpar, ke)
+    torch.cuda.synchronize()
+    b3h = b3.cpu().numpy()
+    assert np.abs(b3h.imag).max() > 0.1 * np.abs(b3h.real).max()  # really complex
+    s, c = sums.cpu().numpy(), cnt.cpu().numpy()
+    ms, mc = msums.cpu().numpy(), mcnt.cpu().numpy()
+    cs, cc = csums.cpu().numpy(), ccnt.cpu().numpy()
+    assert s.dtype == ms.dtype == cs.dtype == np.complex128
+    assert s.shape == (2, 12, 5, 5) and ms.shape == (2, 3, 12, 5, 5)
+    trips = _planes_trips(tri, len(edges) - 1)
+    for part in (np.real, np.imag):
+        x = np.ascontiguousarray(part(b3h))
+        _, c_o = mo.bs_monopole(x, trips, kperp, kpar, k1e, 5, 5)
+        iv = mo.monopole_interval(x, trips, kperp, kpar, k1e, 5, 5, REL_K, REL_S)
+        _check_interval(c, part(s), iv, c_o, 1e-12 * np.abs(x).max() * np.maximum(iv["c_hi"], 1))
+        _, cm_o = mo.bs_multipoles(x, trips, kperp, kpar, k1e, 5, 5, 2)
+        ivm = mo.multipole_interval(x, trips, kperp, kpar, k1e, 5, 5, 2, REL_K, REL_S)
+        scale = np.abs(x).max() * 9 * np.maximum(ivm["c_hi"], 1)
+        _check_interval(mc, part(ms), ivm, cm_o, 1e-12 * scale)
+        s_o, cc_o = mo.bs_cylindrical(x, kpar, ke)
+        np.testing.assert_array_equal(cc, cc_o)
+        assert np.all(np.abs(part(cs) - s_o) <= 1e-12 * np.abs(x).max() * np.maximum(cc_o, 1))
+    plan.close()
