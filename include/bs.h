@@ -332,6 +332,14 @@ bs_status bs_bs3d_closable(bs_plan plan, double *out_dev, void *cuda_stream);
  * 1, -1, 2): beta bounds the modulus of the complex error, the hypot of
  * 2 b_0 + (b_1 + b_-1)/2 (real part) and (9 b_1 + b_-1 + 2 b_2 + 6 b_0)/6
  * (imaginary part), b_t the bound above for the evaluation at t.
+ * Per-channel sampling plans (R = S_D / (A S_I), collapsed as a ratio of
+ * sums): the bound is per bin of the folded plane, which must be given,
+ *   |R - R_exact| <= (b_D / A + |R| b_I) / (<S_I> - b_I)
+ * with b_D, b_I the bound above (unnormalised) for the numerator and the
+ * occupancy-field denominator and <S_I> the bin's mean computed
+ * denominator (infinite where <S_I> <= b_I); bound_dev then holds, per ring
+ * triple, the largest bin bound of that plane (it covers the folded plane,
+ * not the full cube, whose entries each have their own denominator).
  *  bound_dev   double [batch][T_r], written; NaN for ring triples without a
  *              closed triangle
  *  delta_dev   NULL, or a folded plane as bs_mabs_delta (closable = 0:
@@ -343,9 +351,9 @@ bs_status bs_bs3d_closable(bs_plan plan, double *out_dev, void *cuda_stream);
  *              (modulus for a general plan; NaN where the estimate is
  *              undefined)
  * Reads the plan's fields, so call it before the next bs_grid_load.
- * Errors: BS_ERR_ARG (NULL bound_dev, only one of delta_dev / relerr_dev),
- * BS_ERR_STATE (no grid loaded), BS_ERR_UNSUPPORTED (per-channel sampling
- * plans, whose denominators carry their own rounding), BS_ERR_CUDA. */
+ * Errors: BS_ERR_ARG (NULL bound_dev, only one of delta_dev / relerr_dev,
+ * no delta_dev for a per-channel sampling plan), BS_ERR_STATE (no grid
+ * loaded), BS_ERR_OOM (scratch of a per-channel sampling plan), BS_ERR_CUDA. */
 bs_status bs_mabs_error_bound(bs_plan plan, double *bound_dev, const double *delta_dev,
                               int closable, double *relerr_dev, void *cuda_stream);
 

@@ -457,8 +457,9 @@ class Plan:
         """bs_mabs_error_bound: float64 CUDA [batch, ntrip] bounds on |B_A error| per ring
         triple (the modulus of the complex error in a general plan); with ``delta`` (a
         folded plane from mabs_delta, or from mabs_delta_closable with closable=True) also
-        the per-bin relative bound, float64 of the same shape.  Returns (bound, relerr or
-        None)."""
+        the per-bin relative bound, float64 of the same shape.  A per-channel sampling plan
+        needs ``delta``: its bound is per bin, and ``bound`` is the largest over each ring
+        triple's bins.  Returns (bound, relerr or None)."""
         import torch
         rel = None
         if delta is not None:

@@ -45,6 +45,17 @@
 //   |d Re S| <= 2 beta_0 + (beta_1 + beta_-1) / 2,
 //   |d Im S| <= (9 beta_1 + beta_-1 + 2 beta_2 + 6 beta_0) / 6,
 // and the bound on the complex error |dS| is the hypot of the two.
+//
+// Per-channel sampling plans estimate R = S_D / (A S_I) per channel triple,
+// with S_I the triple sum of the occupancy fields, and collapse as the ratio
+// of the summed numerators and denominators over the K channel triples of a
+// bin.  With computed sums S^ = S + dS and |dS_D| <= beta_D, |dS_I| <= beta_I
+// per channel triple (the bound above on each component's own fields),
+//   R^ - R = (dS_D - A R dS_I) / (A S^_I)   (exactly), so
+//   |R^ - R| <= (beta_D / A + |R^| beta_I) / (<S^_I> - beta_I)
+// for a bin whose mean computed denominator <S^_I> exceeds beta_I (infinite
+// otherwise).  The bound is per bin of the folded plane; per ring triple the
+// largest over its bins is reported.
 #include <cmath>
 
 #include "plan_internal.h"
@@ -118,8 +129,10 @@ struct BoundLevel {
   const int *slot_of;   // [nb]
   const int *kexp;      // [batch][nslot] scale exponents (split FP16), else null
   int level, nslot, nc, ntrip;
-  int batch;            // realisations of the output (the caller's batch)
-  int general;          // 1: four internal evaluations per realisation (t = 0, 1, -1, 2)
+  int batch;            // realisations written (the caller's, or internal for mode 2)
+  int mode;             // 0 bound of S / (A M^2 T); 1 general plan: four evaluations per
+                        // realisation (t = 0, 1, -1, 2); 2 bound of each internal
+                        // evaluation's S, not normalised
   double c1;            // c_term + c_acc
   double cf;            // eps_fft
   double floor16;       // 2^-25 (2^14 + 2^7) M^2 (split FP16), else 0
@@ -165,8 +178,12 @@ __global__ void k_trip_bound(BoundLevel L, const int *__restrict__ tab,
   const int b = t / L.ntrip, trip = t - b * L.ntrip;
   if (tab[4 * trip + 3] != L.level || !(tnorm[trip] > 0.0)) return;
   const int r[3] = {tab[4 * trip], tab[4 * trip + 1], tab[4 * trip + 2]};
+  if (L.mode == 2) {
+    bound[(long long)b * L.ntrip + trip] = 1.01 * trip_beta(L, b, r);
+    return;
+  }
   double beta;
-  if (!L.general) {
+  if (L.mode == 0) {
     beta = trip_beta(L, b, r);
   } else {  // evaluations t = 0, 1, -1, 2 of realisation b are internal 4b .. 4b + 3
     const double b0 = trip_beta(L, 4 * b, r), b1 = trip_beta(L, 4 * b + 1, r),
@@ -195,6 +212,45 @@ __global__ void k_delta_relerr(const double *__restrict__ delta, const double *_
   }
 }
 
+// bound[b][trip] = 0 for ring triples with a closed triangle (the largest bin
+// bound is taken into it), NaN for the others.
+__global__ void k_bound_init(const double *__restrict__ tnorm, int ub, int ntrip,
+                             double *__restrict__ bound) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= ub * ntrip) return;
+  bound[q] = tnorm[q % ntrip] > 0.0 ? 0.0 : __longlong_as_double(0x7ff8000000000000LL);
+}
+
+// Per-channel sampling plans: relerr[b][pl][d] of the ratio R = delta[b][pl][d]
+// from the mean denominator comp[2b + 1][pl][d] (normalised by tnorm) and the
+// per-evaluation bounds beta[2b][trip] (numerator), beta[2b + 1][trip]
+// (denominator); the largest absolute bound of each ring triple into bound.
+__global__ void k_ratio_relerr(const double *__restrict__ delta, const double *__restrict__ comp,
+                               const double *__restrict__ beta, const double *__restrict__ tnorm,
+                               const int *__restrict__ clos, int nplanes, int ntrip,
+                               long long n2, long long total, double inv_a,
+                               double *__restrict__ relerr, double *__restrict__ bound) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+       q += (long long)gridDim.x * blockDim.x) {
+    const long long bp = q / n2, d = q - bp * n2;
+    const int b = (int)(bp / nplanes), pl = (int)(bp - (long long)b * nplanes);
+    const int trip = clos ? clos[pl] : pl;
+    const double R = delta[q];
+    if (!(R == R)) {  // undefined estimate
+      relerr[q] = R;
+      continue;
+    }
+    const double tn = tnorm[trip];
+    const double bd = beta[(2ll * b) * ntrip + trip] * tn,
+                 bi = beta[(2ll * b + 1) * ntrip + trip] * tn;
+    const double den = comp[((2ll * b + 1) * nplanes + pl) * n2 + d] - bi;
+    const double e = den > 0.0 ? (bd * inv_a + fabs(R) * bi) / den : INFINITY;
+    relerr[q] = e / fabs(R);
+    atomicMax(reinterpret_cast<unsigned long long *>(bound + (long long)b * ntrip + trip),
+              (unsigned long long)__double_as_longlong(e));  // e >= 0: bit order = value order
+  }
+}
+
 int ceil_log2(int m) {
   int k = 0;
   while ((1 << k) < m) ++k;
@@ -220,8 +276,10 @@ extern "C" bs_status bs_mabs_error_bound(bs_plan p, double *bound_dev, const dou
     return fail(p, BS_ERR_ARG, "bs_mabs_error_bound: give both delta_dev and relerr_dev, or neither");
   if (closable != 0 && closable != 1)
     return fail(p, BS_ERR_ARG, "bs_mabs_error_bound: closable must be 0 or 1");
-  if (p->chans)
-    return fail(p, BS_ERR_UNSUPPORTED, "bs_mabs_error_bound: per-channel sampling plans");
+  if (p->chans && !delta_dev)
+    return fail(p, BS_ERR_ARG,
+                "bs_mabs_error_bound: a per-channel sampling plan bounds a folded plane "
+                "(give delta_dev and relerr_dev)");
   if (!p->loaded || !p->counts_ready)
     return fail(p, BS_ERR_STATE, "bs_mabs_error_bound before bs_grid_load");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -240,8 +298,15 @@ extern "C" bs_status bs_mabs_error_bound(bs_plan p, double *bound_dev, const dou
   }
   int *dtab = p->at<int>(p->L.errtab);
   EB_CUDA(cudaMemcpyAsync(dtab, tab.data(), tab.size() * sizeof(int), cudaMemcpyHostToDevice, s));
-  // the caller's realisations (a general plan holds four internal ones per realisation)
-  const int out_batch = p->general ? p->ubatch : p->batch;
+  // the caller's realisations (a general plan holds four internal ones per
+  // realisation, a per-channel sampling plan two)
+  const int out_batch = p->general || p->chans ? p->ubatch : p->batch;
+  double *beta_int = nullptr;  // per-channel sampling: per-evaluation bounds [batch][ntrip]
+  if (p->chans) {
+    st = general_scratch(p, &p->gerr, &p->gerr_cap, (size_t)p->batch * p->ntrip);
+    if (st != BS_OK) return st;
+    beta_int = p->gerr;
+  }
   // NaN (all bits set) for every ring triple without a closed triangle
   EB_CUDA(cudaMemsetAsync(bound_dev, 0xFF, (size_t)out_batch * p->ntrip * sizeof(double), s));
   double *norms = p->at<double>(p->L.errn);
@@ -259,8 +324,8 @@ extern "C" bs_status bs_mabs_error_bound(bs_plan p, double *bound_dev, const dou
     B.level = li;
     B.nslot = lv.nslot;
     B.nc = p->nc;
-    B.batch = out_batch;
-    B.general = p->general ? 1 : 0;
+    B.batch = p->chans ? p->batch : out_batch;
+    B.mode = p->chans ? 2 : p->general ? 1 : 0;
     B.ntrip = p->ntrip;
     const double c_acc = prec == BS_PREC_FP32
                              ? (1024.0 + std::ceil((double)m2 / 1024.0) + 1.0) * kU
@@ -269,10 +334,32 @@ extern "C" bs_status bs_mabs_error_bound(bs_plan p, double *bound_dev, const dou
     B.cf = (2.0 * (ceil_log2(lv.M) + 2) * 8.0 + 2.0) * kU;
     B.floor16 = prec == BS_PREC_SPLIT_FP16 ? std::ldexp(1.0, -25) * (16384.0 + 128.0) * (double)m2
                                            : 0.0;
-    const int nt = out_batch * p->ntrip;
-    k_trip_bound<<<(nt + 255) / 256, 256, 0, s>>>(B, dtab, p->at<double>(p->L.tnorm), bound_dev);
+    const int nt = B.batch * p->ntrip;
+    k_trip_bound<<<(nt + 255) / 256, 256, 0, s>>>(B, dtab, p->at<double>(p->L.tnorm),
+                                                  p->chans ? beta_int : bound_dev);
     EB_CUDA(cudaGetLastError());
     norms += (size_t)nfield * 3;
+  }
+  if (p->chans) {
+    const int npl = closable ? (int)p->clos.size() : p->ntrip;
+    const long long n2 = (long long)(2 * p->nc - 1) * (2 * p->nc - 1);
+    const long long total = (long long)out_batch * npl * n2;
+    const int nb = out_batch * p->ntrip;
+    k_bound_init<<<(nb + 255) / 256, 256, 0, s>>>(p->at<double>(p->L.tnorm), out_batch, p->ntrip,
+                                                 bound_dev);
+    EB_CUDA(cudaGetLastError());
+    const double *comp = nullptr;
+    st = chans_components(p, closable != 0, s, &comp);
+    if (st != BS_OK) return st;
+    if (total > 0) {
+      const int grid = (int)std::min<long long>((total + 255) / 256, 152LL * 32);
+      k_ratio_relerr<<<grid, 256, 0, s>>>(delta_dev, comp, beta_int, p->at<double>(p->L.tnorm),
+                                          closable ? p->at<int>(p->L.clos) : nullptr, npl,
+                                          p->ntrip, n2, total, 1.0 / p->normA, relerr_dev,
+                                          bound_dev);
+      EB_CUDA(cudaGetLastError());
+    }
+    return BS_OK;
   }
   if (delta_dev) {
     const int npl = closable ? (int)p->clos.size() : p->ntrip;

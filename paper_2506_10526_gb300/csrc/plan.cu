@@ -981,7 +981,7 @@ bs_status bs_plan_destroy(bs_plan p) {
     cudaSetDevice(p->device);
     cudaFree(p->mono_bins);
   }
-  for (double *g : {p->gfull, p->gdelta, p->g3d, p->gbin})
+  for (double *g : {p->gfull, p->gdelta, p->g3d, p->gbin, p->gerr})
     if (g) {
       cudaSetDevice(p->device);
       cudaFree(g);
@@ -1423,3 +1423,13 @@ bs_status bs_check_hermitian(bs_plan p, const void *vis, double tol, void *strea
 }
 
 }  // extern "C"
+
+// The normalised collapse components of a per-channel sampling plan (summed
+// numerators and denominators, internal realisations 2b and 2b + 1) in the
+// full or the closable layout, for the error bound of the ratio.
+bs_status bsi::chans_components(bs_plan p, bool closable, cudaStream_t s, const double **comp) {
+  bs_status st = delta_out(p, nullptr, closable, s);
+  if (st != BS_OK) return st;
+  *comp = p->gdelta;
+  return BS_OK;
+}

@@ -89,6 +89,9 @@ struct bs_plan_s {
   // planes, then their real sums (device, on demand)
   double *gbin = nullptr;
   size_t gbin_cap = 0;
+  // error bound of a per-channel sampling plan: per-evaluation bounds [batch][ntrip]
+  double *gerr = nullptr;
+  size_t gerr_cap = 0;
   std::vector<int> cyl_tab;       // row bins and column ranges of the last cylindrical call
   std::vector<long long> cyl_cnt; // its per-bin counts
   std::vector<int> err_tab;       // [ntrip][4] rings (i, j, l) and level, for the error bound
@@ -156,6 +159,10 @@ bs_status upload_nnu(bs_plan p, cudaStream_t s);
 // Device scratch of n doubles in *buf (grown with cudaMalloc when *cap < n,
 // freed with the plan); BS_ERR_OOM when it cannot be had.
 bs_status general_scratch(bs_plan p, double **buf, size_t *cap, size_t n);
+// Per-channel sampling plans: the normalised collapse components [2 ubatch]
+// [planes][2nc-1][2nc-1] (numerator sums, then denominator sums, of each
+// realisation) of the full (closable = false) or closable layout, in plan scratch.
+bs_status chans_components(bs_plan p, bool closable, cudaStream_t s, const double **comp);
 // Host-to-device uploads of per-call work lists through the plan's pinned
 // staging buffer (asynchronous; the buffer is reused once the previous
 // uploads from it have completed).  Falls back to ordinary copies when

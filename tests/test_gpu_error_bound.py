@@ -188,3 +188,65 @@ def test_bound_covers_the_error_general_input(precision, multires):
         np.testing.assert_array_equal(out["relc"][b], out["rel"][b][clos])
         print(f"general p{precision} mr{int(multires)} realisation {b}: error/bound max "
               f"{ratio.max():.2e} median {np.median(ratio):.2e}")
+
+
+@pytest.mark.parametrize("precision,multires", [(0, False), (0, True), (1, True), (2, True)])
+def test_bound_covers_the_error_per_channel_sampling(precision, multires):
+    """Per-channel sampling N_g(nu): denominators that depend on the channel
+    triple and the ratio-of-sums collapse, two realisations of different
+    amplitude, a flagged channel, A != 1.  The per-bin bound of the folded
+    plane covers the oracle error on every bin, in the full and the closable
+    layout; the ring-triple bound is the largest bin bound; without a plane
+    the call is refused."""
+    torch = _torch()
+    import paper_2506_10526_gb300 as bs
+    nt, nc, A = 32, 6, 1.7
+    edges = synth.edges_log(5, 1.5, 15.0)
+    vis = np.stack([synth.sky_visibilities(nt, nc, seed=s) for s in (611, 612)])
+    vis[1] *= 40.0
+    g = synth.rng(613)
+    ngrid = g.integers(0, 4, size=(nc, nt, nt)).astype(np.float32)
+    ngrid[:, 1:, 1:] = np.maximum(ngrid[:, 1:, 1:], ngrid[:, 1:, 1:][:, ::-1, ::-1])
+    flags = np.zeros(nc, np.uint8)
+    flags[3] = 1
+    plan = bs.Plan(nt, nc, edges, precision=precision, multires=multires, batch=2,
+                   chan_sampling=True, norm_A=A)
+    plan.grid_load(torch.from_numpy(vis.astype(np.complex64)).cuda(),
+                   ngrid=torch.from_numpy(ngrid).cuda(), chan_flags=flags)
+    plan.mabs(accumulate=True)
+    n2 = 2 * nc - 1
+    dd = torch.empty((2, plan.ntrip, n2, n2), dtype=torch.float64, device="cuda")
+    plan.mabs_delta(dd)
+    dc = torch.empty((2, plan.n_closable, n2, n2), dtype=torch.float64, device="cuda")
+    plan.mabs_delta_closable(dc)
+    bound, rel = plan.error_bound(dd)
+    bound2, relc = plan.error_bound(dc, closable=True)
+    with pytest.raises(bs.BsError):
+        plan.error_bound()  # the bound is per bin: the plane is required
+    torch.cuda.synchronize()
+    tri, _ = plan.counts()
+    d, bnd, r, bnd2, rc = (x.cpu().numpy() for x in (dd, bound, rel, bound2, relc))
+    plan.close()
+    clos = np.flatnonzero(tri > 0)
+    for b in range(2):
+        ref = oracle.mabs_full(vis[b].astype(np.complex128), edges, ngrid=ngrid, chan_flags=flags,
+                               norm_A=A)
+        rab = oracle.mabs_full(np.abs(vis[b]).astype(np.complex128), edges, ngrid=ngrid,
+                               chan_flags=flags, norm_A=A)
+        R = oracle.collapse_fold_ratio(ref["num"], ref["den"], norm_A=A).real
+        Rabs = oracle.collapse_fold_ratio(rab["num"], rab["den"], norm_A=A).real
+        ok = ~np.isnan(R)
+        assert np.array_equal(np.isnan(d[b]), ~ok)
+        np.testing.assert_array_equal(np.isnan(r[b]), ~ok)
+        np.testing.assert_array_equal(np.isnan(bnd[b]), tri == 0)
+        err = np.abs(d[b] - R)
+        ebin = r[b] * np.abs(d[b])  # the absolute bound of each bin
+        ratio = err[ok] / ebin[ok]
+        assert np.all(err[ok] <= ebin[ok] + 1e-13 * Rabs[ok]), ratio.max()
+        want = np.array([np.max(ebin[t][ok[t]]) if ok[t].any() else 0.0 for t in clos])
+        np.testing.assert_allclose(bnd[b][clos], want, rtol=1e-12)
+        np.testing.assert_array_equal(rc[b], r[b][clos])
+        np.testing.assert_array_equal(bnd2[b], bnd[b])
+        print(f"per-channel p{precision} mr{int(multires)} realisation {b}: error/bound max "
+              f"{ratio.max():.2e} median {np.median(ratio):.2e}; infinite bins "
+              f"{int(np.isinf(ebin[ok]).sum())} of {int(ok.sum())}")
