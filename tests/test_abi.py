@@ -134,9 +134,12 @@ class _NoLibrary:
         return reached
 
 
-def _bare(cls, **attrs):
-    """An instance of a binding class with the given attributes and no library
+def _bare(cls, props=None, **attrs):
+    """An instance of a binding class with the given attributes (props: class
+    attributes in place of properties that ask the library) and no library
     handle: the argument checks run before any call into the library."""
+    if props:
+        cls = type("Bare" + cls.__name__, (cls,), dict(props))
     obj = object.__new__(cls)
     obj.__dict__.update(attrs)
     obj._h = None
@@ -159,8 +162,8 @@ def test_bindings_refuse_wrong_tensors_before_the_library():
     the binding refuses a dtype or extent other than the one the kernels
     touch, so no undersized buffer reaches the device."""
     import torch
-    plan = _bare(bs.Plan, nt=16, nchan=4, batch=2, nbins=3, ntrip=10, general=False,
-                 chan_sampling=False)
+    plan = _bare(bs.Plan, {"n_closable": 4}, nt=16, nchan=4, batch=2, nbins=3, ntrip=10,
+                 general=False, chan_sampling=False)
     with _refused():  # half the cells
         plan.check_hermitian(torch.zeros((1, 4, 16, 16), dtype=torch.complex64))
     with _refused():  # the right count of the wrong type
@@ -180,6 +183,23 @@ def test_bindings_refuse_wrong_tensors_before_the_library():
         plan.mlp_features(np.zeros(3, np.uint8))
     with _refused():
         plan.delta_import(torch.zeros((2, 10, 7, 6), dtype=torch.float64), np.zeros(49, np.int64))
+    with _refused():  # a plane of the wrong type for a real plan
+        plan.error_bound(torch.zeros((2, 10, 7, 7), dtype=torch.complex128))
+    kp, kz, ke = np.ones(3), np.linspace(-1, 1, 4), np.linspace(0.1, 2, 5)
+    with _refused():
+        plan.bs_monopole(torch.zeros((2, 4, 4, 3), dtype=torch.float64), kp, kz, ke)
+    with _refused():
+        plan.bs_multipoles(torch.zeros((2, 4, 4, 4), dtype=torch.float32), kp, kz, ke)
+    with _refused():
+        plan.bs_cylindrical(torch.zeros((1, 4, 4, 4), dtype=torch.float64), kz, ke)
+    gplan = _bare(bs.Plan, {"n_closable": 4}, nt=16, nchan=4, batch=2, nbins=3, ntrip=10,
+                  general=True, chan_sampling=False)
+    with _refused():  # a general plan's values are complex
+        gplan.bs_monopole(torch.zeros((2, 4, 4, 4), dtype=torch.float64), kp, kz, ke)
+    with _refused():
+        gplan.bs_cylindrical(torch.zeros((2, 4, 4, 4), dtype=torch.float64), kz, ke)
+    with _refused():
+        gplan.error_bound(torch.zeros((2, 10, 7, 7), dtype=torch.float64))
 
     net = _bare(bs.Surrogate, d=45, w=128, n_weights=100, n_total=192)
     x = torch.zeros((8, 45), dtype=torch.float32)
