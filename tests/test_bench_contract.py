@@ -56,3 +56,28 @@ def test_contracted_flops_count_one_ordering_of_repeated_rings():
             want_sym += f
     assert bench.contracted_flops(tri, sides, nb, (n, n, n), False) == want_all
     assert bench.contracted_flops(tri, sides, nb, (n, n, n), True) == want_sym
+
+
+def test_batched_monte_carlo_shapes_follow_the_configuration():
+    """The batched Monte Carlo workload draws its realisation shapes inside the
+    configuration's ranges (grids 128^2, 256^2 or 512^2; 384-768 channels,
+    each a 2^a 3^b 5^c length the sky generator's FFTs take; 12-24 log
+    rings), reproducibly by seed; the candidate channel blocks hold equal
+    numbers of channel triples and fit the tiles' 32 x 16 pair rectangle."""
+    sys.path.insert(0, ROOT)
+    import bench
+    shapes = bench.cfg4_shapes()
+    assert shapes == bench.cfg4_shapes() and len(shapes) == 8
+    assert bench.cfg4_shapes(seed=4001) != shapes
+    for nt, nc, nb in bench.cfg4_shapes(n=200):
+        assert nt in (128, 256, 512) and 384 <= nc <= 768 and 12 <= nb <= 24
+        m = nc
+        for p in (2, 3, 5):
+            while m % p == 0:
+                m //= p
+        assert m == 1, nc
+    assert len({nt for nt, _, _ in bench.cfg4_shapes(n=200)}) == 3
+    for b in (32, 64):
+        blocks = bench.cfg4_block_shapes(b)
+        assert all(x * y * z == b ** 3 for x, y, z in blocks)
+        assert all(x % 32 == 0 and y % 16 == 0 for x, y, _ in blocks)
